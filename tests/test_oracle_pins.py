@@ -1,0 +1,448 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Every check here is independent of the oracle's own code path: Runge-Kutta order conditions,
+closed-form ray solutions of the exponential profile, exact straight-line geometry at
+constant n, Fresnel energy conservation, brute-force step refinement, the accuracy class the
+paper prints (Sec. 2, accuracy study; tests/golden/paper_accuracy.json).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.analytic import C0, ExpProfile, solutions
+from paper_1810_01780_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------------------
+# Cash-Karp tableau
+# --------------------------------------------------------------------------------------
+
+def _conditions(A, b, c):
+    Ac = A @ c
+    return {
+        (1, "b"): (b.sum(), 1.0),
+        (2, "bc"): (b @ c, 1 / 2),
+        (3, "bc2"): (b @ c**2, 1 / 3),
+        (3, "bAc"): (b @ Ac, 1 / 6),
+        (4, "bc3"): (b @ c**3, 1 / 4),
+        (4, "bcAc"): (b @ (c * Ac), 1 / 8),
+        (4, "bAc2"): (b @ (A @ c**2), 1 / 12),
+        (4, "bAAc"): (b @ (A @ Ac), 1 / 24),
+        (5, "bc4"): (b @ c**4, 1 / 5),
+        (5, "bc2Ac"): (b @ (c**2 * Ac), 1 / 10),
+        (5, "b(Ac)2"): (b @ Ac**2, 1 / 20),
+        (5, "bcAc2"): (b @ (c * (A @ c**2)), 1 / 15),
+        (5, "bAc3"): (b @ (A @ c**3), 1 / 20),
+        (5, "bcAAc"): (b @ (c * (A @ Ac)), 1 / 30),
+        (5, "bA(cAc)"): (b @ (A @ (c * Ac)), 1 / 40),
+        (5, "bAAc2"): (b @ (A @ (A @ c**2)), 1 / 60),
+        (5, "bAAAc"): (b @ (A @ (A @ Ac)), 1 / 120),
+    }
+
+
+def test_tableau_order_conditions(oracle_lib):
+    c, a, b5, b4 = oracle.ck_tableau()
+    A = np.zeros((6, 6))
+    A[:, :5] = a
+    assert np.allclose(A.sum(axis=1), c, atol=1e-15, rtol=0)  # row-sum condition
+    assert np.all(np.triu(A) == 0.0)  # explicit method
+    for (order, name), (got, want) in _conditions(A, b5, c).items():
+        assert abs(got - want) < 1e-14, ("b5", name)
+    bad = 0
+    for (order, name), (got, want) in _conditions(A, b4, c).items():
+        if order <= 4:
+            assert abs(got - want) < 1e-14, ("b4", name)
+        else:
+            bad += abs(got - want) > 1e-6
+    assert bad > 0  # the embedded weights are genuinely only fourth order
+
+
+@pytest.mark.parametrize("k", range(7))
+def test_tableau_polynomial_exactness(oracle_lib, k):
+    # y' = x^k from x0 = 0.3 over h = 0.7: exact increment ((x0+h)^(k+1) - x0^(k+1)) / (k+1)
+    coef = np.zeros(k + 1)
+    coef[k] = 1.0
+    x0, h = 0.3, 0.7
+    y5, y4 = oracle.ck_poly_step(coef, x0, 0.0, h)
+    exact = ((x0 + h) ** (k + 1) - x0 ** (k + 1)) / (k + 1)
+    if k <= 4:
+        assert abs(y5 - exact) < 1e-14
+    else:
+        assert abs(y5 - exact) > 1e-8
+    if k <= 3:
+        assert abs(y4 - exact) < 1e-14
+    else:
+        assert abs(y4 - exact) > 1e-8
+
+
+def test_ray_step_local_order(oracle_lib):
+    """One step of the ray system: error vs a 4096-substep reference scales like h^6."""
+    med = oracle.OracleMedium(W.single_profile())
+    th = math.radians(100.0)
+    y0 = np.array([0.0, 0.0, 30.0, math.sin(th), 0.0, math.cos(th), 0.0])
+    errs = []
+    hs = [16.0, 8.0, 4.0]
+    for h in hs:
+        y1, _ = oracle.ck_step(med, y0, h)
+        yr = y0.copy()
+        for _ in range(4096):
+            yr, _ = oracle.ck_step(med, yr, h / 4096)
+        errs.append(np.linalg.norm(y1[:6] - yr[:6]))
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(len(hs) - 1)]
+    assert all(5.0 < s < 7.0 for s in slopes), (errs, slopes)
+
+
+# --------------------------------------------------------------------------------------
+# ray equations
+# --------------------------------------------------------------------------------------
+
+def test_rhs_projection_and_index(oracle_lib):
+    med = oracle.OracleMedium(W.single_profile())
+    t = np.array([0.6, 0.0, -0.8])
+    y = np.array([1.0, 2.0, 40.0, *t, 0.0])
+    k = oracle.rhs(med, y)
+    n = 1.788 - 0.463 * math.exp(-40.0 / 75.0)
+    g = 0.463 / 75.0 * math.exp(-40.0 / 75.0)
+    assert np.allclose(k[:3], t, rtol=0, atol=0)
+    assert abs(k[6] - n / C0) < 1e-22
+    # tangent derivative is orthogonal to t and equals the transverse part of grad n / n
+    assert abs(k[3:6] @ t) < 1e-18
+    want = (np.array([0.0, 0.0, g]) - g * t[2] * t) / n
+    assert np.allclose(k[3:6], want, rtol=1e-15, atol=0)
+    kp = oracle.rhs(med, y, rhs_form="paraxial")
+    assert np.allclose(kp[3:6], [0.0, 0.0, g / n], rtol=1e-15, atol=0)
+
+
+def test_straight_lines_constant_index(oracle_lib):
+    med = {"kind": "layered", "layers": [dict(n0=1.5, dn=0.0)]}
+    rng = np.random.default_rng(11)
+    n = 64
+    pos = rng.uniform(-100, 100, (3, n))
+    d = W.isotropic_dirs(rng, n)
+    prm = dict(W.TRACE_DEFAULTS, max_path=1234.5)
+    rays, _ = oracle.trace(med, prm, pos, d)
+    assert np.all(rays["status"] == oracle.STATUS["MAX_PATH"])
+    end = pos.T + 1234.5 * d.T
+    assert np.max(np.abs(rays["pos"] - end)) < 1e-9
+    assert np.max(np.abs(rays["dir"] - d.T)) < 1e-14
+    assert np.max(np.abs(rays["time"] / (1.5 * 1234.5 / C0) - 1.0)) < 1e-13
+    assert np.all(rays["path"] == 1234.5)
+    assert np.all(rays["n_rej"] == 0)
+
+
+def _fan_single_profile(tol, h_max=10.0, max_path=1500.0, depth=200.0, n=23):
+    med = W.single_profile()
+    pos, d, a = W.fan_xz(n, depth, 3.0, 177.0)
+    prm = dict(W.TRACE_DEFAULTS, tol=tol, h_max=h_max, h0=h_max, max_path=max_path,
+               max_generation=0)
+    rays, _ = oracle.trace(med, prm, pos, d, a)
+    return pos, d, rays
+
+
+def test_snell_invariant_conserved(oracle_lib):
+    prof = ExpProfile()
+    pos, d, rays = _fan_single_profile(1e-6)
+    p0 = prof.n(pos[2]) * np.hypot(d[0], d[1])
+    p1 = prof.n(rays["pos"][:, 2]) * np.hypot(rays["dir"][:, 0], rays["dir"][:, 1])
+    assert np.max(np.abs(p1 - p0)) < 1e-6
+
+
+def test_closed_form_range_path_time(oracle_lib):
+    """End point on the closed-form curve X(z); S and T match the closed forms."""
+    prof = ExpProfile()
+    pos, d, rays = _fan_single_profile(1e-9)
+    th = np.arctan2(d[0], d[2])
+    for i, r in enumerate(rays):
+        X, S, T = prof.ray_to_depth(pos[2, i], th[i], r["pos"][2], ends_down=r["dir"][2] > 0)
+        assert abs(r["pos"][0] - X) < 2e-7, i
+        assert abs(r["path"] - S) < 2e-7, i
+        assert abs(r["time"] - T) < 1e-15, i
+
+
+def test_error_shrinks_with_tolerance(oracle_lib):
+    """Brute force: tol 1e-12 with h_max 0.5 m as reference; the end-point error falls with tol."""
+    prof = ExpProfile()
+    _, _, ref = _fan_single_profile(1e-12, h_max=0.5, n=9)
+    errs = []
+    for tol in (1e-4, 1e-6, 1e-8):
+        _, _, r = _fan_single_profile(tol, n=9)
+        errs.append(np.max(np.linalg.norm(r["pos"] - ref["pos"], axis=1)))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-5
+    # the reference itself sits on the closed-form curve
+    pos, d, _ = W.fan_xz(9, 200.0, 3.0, 177.0)
+    th = np.arctan2(d[0], d[2])
+    for i, r in enumerate(ref):
+        X, _, _ = prof.ray_to_depth(200.0, th[i], r["pos"][2], ends_down=r["dir"][2] > 0)
+        assert abs(r["pos"][0] - X) < 1e-7
+
+
+def test_paraxial_form_is_less_accurate(oracle_lib):
+    """Eq. 2 taken literally (t' = grad n / n, t renormalised per step) drifts from the
+    closed form far more than the projected form at the same tolerance."""
+    prof = ExpProfile()
+    med = W.single_profile()
+    pos, d, a = W.fan_xz(5, 200.0, 60.0, 120.0)
+    th = np.arctan2(d[0], d[2])
+    worst = {}
+    for form in ("projected", "paraxial"):
+        prm = dict(W.TRACE_DEFAULTS, tol=1e-8, max_path=1500.0, max_generation=0, rhs_form=form)
+        rays, _ = oracle.trace(med, prm, pos, d, a)
+        e = []
+        for i, r in enumerate(rays):
+            X, _, _ = prof.ray_to_depth(200.0, th[i], r["pos"][2], ends_down=r["dir"][2] > 0)
+            e.append(abs(r["pos"][0] - X))
+        worst[form] = max(e)
+    assert worst["projected"] < 1e-5
+    assert worst["paraxial"] > 100 * worst["projected"]
+
+
+# --------------------------------------------------------------------------------------
+# boundary module
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("pol", ["s", "p", "unpol"])
+def test_fresnel_energy_conservation(oracle_lib, pol):
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        n1, n2 = rng.uniform(1.0, 2.0, 2)
+        ci = rng.uniform(0.0, 1.0)
+        s2 = (n1 / n2) ** 2 * (1 - ci * ci)
+        if s2 > 1:
+            continue
+        ct = math.sqrt(1 - s2)
+        r, tau = oracle.fresnel(n1, n2, ci, ct, pol)
+        if pol == "unpol":
+            R, T = r * r, tau * tau
+        else:
+            R, T = r * r, (n2 * ct) / (n1 * ci) * tau * tau if ci > 0 else 0.0
+        assert abs(R + T - 1.0) < 1e-12
+
+
+def test_fresnel_special_cases(oracle_lib):
+    # normal incidence
+    for pol in ("s", "p"):
+        r, tau = oracle.fresnel(1.78, 1.0, 1.0, 1.0, pol)
+        rs = (1.78 - 1.0) / (1.78 + 1.0)
+        assert abs(abs(r) - rs) < 1e-15
+        assert abs(tau - 2 * 1.78 / 2.78) < 1e-15
+    # s: r = (n1 - n2)/(n1 + n2); p has the opposite sign convention at normal incidence
+    assert oracle.fresnel(1.78, 1.0, 1.0, 1.0, "s")[0] > 0
+    assert oracle.fresnel(1.78, 1.0, 1.0, 1.0, "p")[0] < 0
+    # matched media: no reflection, full transmission, undeviated
+    t = np.array([0.3, 0.2, -math.sqrt(1 - 0.13)])
+    tr, tt, r, tau, tir = oracle.split(t, np.array([0.0, 0.0, 1.0]), 1.4, 1.4)
+    assert not tir and abs(r) < 1e-15 and abs(tau - 1) < 1e-15
+    assert np.allclose(tt, t, atol=1e-15)
+    assert np.allclose(tr, [t[0], t[1], -t[2]], atol=1e-15)
+    # Brewster angle: r_p = 0
+    n1, n2 = 1.0, 1.5
+    tb = math.atan(n2 / n1)
+    ct = math.sqrt(1 - (n1 / n2 * math.sin(tb)) ** 2)
+    assert abs(oracle.fresnel(n1, n2, math.cos(tb), ct, "p")[0]) < 1e-15
+
+
+def test_snell_vector_refraction_and_tir(oracle_lib):
+    rng = np.random.default_rng(8)
+    nrm = np.array([0.0, 0.0, 1.0])  # toward the incident side (+z, deeper)
+    for _ in range(200):
+        n1, n2 = rng.uniform(1.0, 1.9, 2)
+        t = W.isotropic_dirs(rng, 1)[:, 0]
+        t[2] = -abs(t[2])  # moving up, against the normal
+        tr, tt, r, tau, tir = oracle.split(t, nrm, n1, n2)
+        sin_i = math.hypot(t[0], t[1])
+        assert abs(np.linalg.norm(tr) - 1) < 1e-15
+        assert np.allclose(tr, [t[0], t[1], -t[2]], atol=1e-15)
+        if n1 * sin_i > n2:
+            assert tir and r == 1.0 and tau == 0.0
+            continue
+        assert not tir
+        assert abs(np.linalg.norm(tt) - 1) < 1e-15
+        sin_t = math.hypot(tt[0], tt[1])
+        assert abs(n1 * sin_i - n2 * sin_t) < 1e-14  # Snell's law
+        assert abs(np.dot(np.cross(t, nrm), tt)) < 1e-14  # plane of incidence
+        assert tt[2] < 0  # transmitted onward
+
+
+def test_boundary_split_constant_layers(oracle_lib):
+    """Straight rays in two constant layers: intersection, reflection, refraction and amplitudes
+    are exact geometry."""
+    n_air, n_ice = 1.0, 1.5
+    med = {"kind": "layered", "layers": [dict(n0=n_air, absorb=True), dict(z_top=0.0, n0=n_ice)]}
+    th = np.radians([120.0, 140.0, 160.0, 179.0, 135.0])  # all moving up toward z = 0
+    n = len(th)
+    pos = np.zeros((3, n))
+    pos[2] = 50.0
+    d = np.stack([np.sin(th), np.zeros(n), np.cos(th)])
+    prm = dict(W.TRACE_DEFAULTS, max_path=200.0)
+    rays, _ = oracle.trace(med, prm, pos, d)
+    for i in range(n):
+        ci = -d[2, i]
+        s_hit = 50.0 / ci
+        x_hit = s_hit * d[0, i]
+        prim = rays[i]
+        assert prim["n_refl"] == 1
+        # after reflection: straight on to s = 200 with t_z flipped
+        end = np.array([x_hit, 0.0, 0.0]) + (200.0 - s_hit) * np.array([d[0, i], 0.0, ci])
+        assert np.allclose(prim["pos"], end, atol=1e-8)
+        s2 = (n_ice / n_air) ** 2 * (1 - ci * ci)
+        sec = rays[(rays["parent"] == i)]
+        if s2 > 1:
+            assert abs(prim["amp"] - 1.0) < 1e-15 and len(sec) == 0
+            continue
+        ct = math.sqrt(1 - s2)
+        rs = (n_ice * ci - n_air * ct) / (n_ice * ci + n_air * ct)
+        ts = 2 * n_ice * ci / (n_ice * ci + n_air * ct)
+        assert abs(prim["amp"] - rs) < 1e-12
+        assert len(sec) == 1
+        s = sec[0]
+        assert s["status"] == oracle.STATUS["TRANSMITTED"] and s["gen"] == 1
+        assert abs(s["amp"] - ts) < 1e-12
+        assert np.allclose(s["pos"], [x_hit, 0.0, 0.0], atol=1e-8)
+        assert abs(s["path"] - s_hit) < 1e-8
+        assert abs(s["time"] - n_ice * s_hit / C0) < 1e-18
+        assert abs(n_ice * math.sqrt(1 - ci * ci) - n_air * math.hypot(*s["dir"][:2])) < 1e-12
+
+
+def test_internal_boundary_secondary_traced(oracle_lib):
+    """A traced secondary continues straight in the far layer; generation cap honoured."""
+    med = {"kind": "layered",
+           "layers": [dict(n0=1.3), dict(z_top=100.0, n0=1.5), dict(z_top=200.0, n0=1.3)]}
+    th = math.radians(30.0)
+    pos = np.array([[0.0], [0.0], [150.0]])
+    d = np.array([[math.sin(th)], [0.0], [math.cos(th)]])
+    for gmax in (0, 1, 3):
+        prm = dict(W.TRACE_DEFAULTS, max_path=400.0, max_generation=gmax)
+        rays, _ = oracle.trace(med, prm, pos, d)
+        assert rays["gen"].max() <= gmax
+        if gmax == 0:
+            assert len(rays) == 1
+    # refracted ray into the bottom layer: straight line with Snell angle
+    sec = rays[(rays["parent"] == 0) & (rays["seq"] == 0)][0]
+    st = 1.5 * math.sin(th) / 1.3
+    s_hit = 50.0 / math.cos(th)
+    x_hit = s_hit * math.sin(th)
+    L = 400.0 - s_hit
+    assert np.allclose(sec["pos"], [x_hit + L * st, 0.0, 200.0 + L * math.sqrt(1 - st * st)],
+                       atol=1e-8)
+
+
+def test_receiver_entry_point(oracle_lib):
+    med = {"kind": "layered", "layers": [dict(n0=1.7)]}
+    pos = np.array([[0.0, 0.0], [0.0, 0.0], [0.0, 0.0]])
+    d = np.array([[1.0, 0.0], [0.0, 1.0], [0.0, 0.0]])
+    ctr = np.array([[50.0, 0.3, 0.0], [30.0, 0.0, 0.0], [0.0, 70.0, 0.9]])
+    rad = np.array([1.0, 2.0, 1.0])
+    prm = dict(W.TRACE_DEFAULTS, max_path=100.0)
+    rays, hits = oracle.trace(med, prm, pos, d, receivers=(ctr, rad))
+    got = sorted((int(h["ray"]), int(h["receiver"]), float(h["path"])) for h in hits)
+    want = sorted([(0, 0, 50.0 - math.sqrt(1 - 0.09)), (0, 1, 28.0),
+                   (1, 2, 70.0 - math.sqrt(1 - 0.81))])
+    assert len(got) == 3
+    for g, w in zip(got, want):
+        assert g[:2] == w[:2] and abs(g[2] - w[2]) < 1e-9
+    for h in hits:
+        assert abs(h["time"] - 1.7 * h["path"] / C0) < 1e-18
+
+
+def test_break_conditions(oracle_lib):
+    med = {"kind": "layered", "layers": [dict(n0=1.0, absorb=True), dict(z_top=0.0, n0=1.5)]}
+    pos = np.array([[0.0], [0.0], [10.5]])
+    d = np.array([[0.0], [0.0], [-1.0]])  # straight up: partial reflection at z = 0
+    prm = dict(W.TRACE_DEFAULTS, max_path=1e4, max_time=3e-7)
+    rays, _ = oracle.trace(med, prm, pos, d)
+    assert rays[0]["status"] == oracle.STATUS["MAX_TIME"]
+    assert 3e-7 <= rays[0]["time"] < 3e-7 + 10.0 * 1.5 / C0
+    prm = dict(W.TRACE_DEFAULTS, max_path=1e4, min_amp=0.5)
+    rays, _ = oracle.trace(med, prm, pos, d)
+    assert rays[0]["status"] == oracle.STATUS["MIN_AMP"]  # |r| = 0.2 < 0.5
+    assert abs(rays[0]["path"] - 10.5) < 1e-9
+
+
+# --------------------------------------------------------------------------------------
+# gridded media
+# --------------------------------------------------------------------------------------
+
+def test_grid_trilinear_exact_on_linear_field(oracle_lib):
+    nx, ny, nz, sp = 6, 5, 7, 2.0
+    z, y, x = np.meshgrid(np.arange(nz) * sp, np.arange(ny) * sp, np.arange(nx) * sp,
+                          indexing="ij")
+    n = (1.3 + 0.01 * x - 0.02 * y + 0.03 * z).astype(np.float32)
+    med = oracle.OracleMedium({"kind": "grid", "n": n, "origin": (0.0, 0.0, 0.0), "spacing": sp})
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        r = rng.uniform(0.0, 8.0, 3)
+        val, g = med.eval(r)
+        assert abs(val - (1.3 + 0.01 * r[0] - 0.02 * r[1] + 0.03 * r[2])) < 2e-6
+        assert np.allclose(g, [0.01, -0.02, 0.03], atol=2e-6)
+
+
+def test_grid_profile_matches_analytic_tracer(oracle_lib):
+    """A grid sampled from the smooth profile reproduces the analytic-medium rays within the
+    interpolation error of the sampled profile (h^2/8 max|n''| ~ 1e-4 at 2 m spacing)."""
+    sp = 2.0
+    ny, nz = 8, 401
+    z = np.arange(nz) * sp
+    prof = (1.788 - 0.463 * np.exp(-z / 75.0)).astype(np.float32)
+    pos, d, a = W.fan_xz(7, 300.0, 30.0, 150.0)
+    # a long box in x so that every ray of the fan stays inside it
+    nx = 1001
+    n = np.empty((nz, ny, nx), np.float32)
+    n[:] = prof[:, None, None]
+    gmed = {"kind": "grid", "n": n, "origin": (-1000.0, -7.0, 0.0), "spacing": sp}
+    prm = dict(W.TRACE_DEFAULTS, tol=1e-7, max_path=300.0, max_generation=0)
+    rg, _ = oracle.trace(gmed, prm, pos, d, a)
+    ra, _ = oracle.trace(W.single_profile(), prm, pos, d, a)
+    assert np.all(rg["status"] == oracle.STATUS["MAX_PATH"])
+    assert np.max(np.linalg.norm(rg["pos"] - ra["pos"], axis=1)) < 0.05
+    assert np.max(np.abs(rg["time"] - ra["time"])) < 1e-10
+
+
+def test_grid_leaves_domain(oracle_lib):
+    n = np.full((10, 10, 10), 1.5, np.float32)
+    gmed = {"kind": "grid", "n": n, "origin": (0.0, 0.0, 0.0), "spacing": 1.0}
+    pos = np.array([[4.5], [4.5], [4.5]])
+    d = np.array([[1.0], [0.0], [0.0]])
+    prm = dict(W.TRACE_DEFAULTS, h_max=1.0, h0=1.0, max_path=100.0)
+    rays, _ = oracle.trace(gmed, prm, pos, d)
+    assert rays[0]["status"] == oracle.STATUS["LEFT_DOMAIN"]
+    assert 9.0 < rays[0]["pos"][0] <= 10.0 + 1e-9
+
+
+# --------------------------------------------------------------------------------------
+# source-receiver path finding: the paper's accuracy study
+# --------------------------------------------------------------------------------------
+
+def test_path_finding_reproduces_paper_accuracy(oracle_lib):
+    gold = json.load(open(os.path.join(GOLDEN, "paper_accuracy.json")))
+    P, acc = gold["profile"], gold["accuracy"]
+    prof = ExpProfile(P["n0"], P["dn"], P["z0_m"])
+    med = {"kind": "layered", "layers": [
+        dict(n0=P["n_above_surface"], absorb=True),
+        dict(z_top=0.0, n0=P["n0"], dn=P["dn"], z0=P["z0_m"])]}
+    z_s = gold["fig1"]["source_depth_m"]
+    L = acc["linear_distance_m"]
+    zr = np.array([300.0, 600.0, 900.0, 1200.0])  # receivers outside the shadow zone
+    D = np.sqrt(L * L - (zr - z_s) ** 2)
+    prm = dict(W.TRACE_DEFAULTS, tol=1e-8, max_path=1e4, max_generation=0)
+    count, sol = oracle.find_paths(med, prm, np.full(len(zr), z_s), zr, D,
+                                   np.full(len(zr), 512, np.int32), hit_tol=1e-4)
+    n_checked = 0
+    for i in range(len(zr)):
+        ref = solutions(prof, z_s, zr[i], D[i], n_above=P["n_above_surface"])
+        assert count[i] == len(ref), (i, count[i], [r["type"] for r in ref])
+        for j, r in enumerate(ref):
+            s = sol[i, j]
+            assert s["type"] == oracle.SOL_TYPE[r["type"]]
+            assert abs(math.degrees(s["launch"] - r["launch"])) < acc["launch_angle_deg"]
+            assert abs(s["path"] - r["path"]) < acc["path_length_m"]
+            assert abs(s["time"] - r["time"]) < acc["travel_time_s"]
+            assert abs(s["amp"] - r["amp"]) < 1e-6
+            n_checked += 1
+    assert n_checked >= 6
