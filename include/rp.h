@@ -1,0 +1,243 @@
+/*
+ * rp.h -- C ABI of the GB300-native RadioPropa ray-propagation library.
+ *
+ * The library implements the ray-propagation method of Winchen, "RadioPropa -- A Modular
+ * Raytracer for In-Matter Radio Propagation" (ARENA 2018): adaptive Cash-Karp integration
+ * of the ray equation in a refractivity field (Sec. 2, Eqs. 1-2), the separate boundary
+ * module (reflection, refraction by Snell's law, Fresnel amplitudes, a secondary ray cast
+ * from the intersection point; Sec. 2), receivers, break conditions (Sec. 2, Fig. 1 text)
+ * and source-receiver path finding (Sec. 2, accuracy study).  All computation runs in
+ * CUDA kernels for sm_103a; there is no CPU fallback.
+ *
+ * Conventions.  SI units.  z is depth, positive downward.  Angles are measured from +z.
+ * Ray arrays are structure-of-arrays: a (3, n) array stores x[0..n), y[0..n), z[0..n).
+ * Every array argument is a DEVICE pointer owned by the caller unless stated otherwise.
+ * `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls enqueue
+ * their kernels on `stream` and return after synchronising it, so the device status can be
+ * returned.
+ *
+ * Errors.  Every function returns RP_OK (0) or a negative RP_ERR_* code; rp_last_error()
+ * gives a message for the last failure on the calling thread.  No C++ exception crosses the
+ * ABI.  The library never traps, asserts or spins on the GPU: overflows are counted and
+ * reported, every per-ray loop is bounded by max_steps.
+ *
+ * Concurrency.  Calls may come from several host threads; calls on the same device are
+ * serialised internally because they share one grow-only device workspace.
+ */
+#ifndef RP_H
+#define RP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RP_OK 0
+#define RP_ERR_INVALID_ARG (-1)  /* bad argument (null pointer, size, parameter range) */
+#define RP_ERR_CUDA (-2)         /* a CUDA runtime call failed (message has the detail) */
+#define RP_ERR_OOM (-3)          /* device allocation failed */
+#define RP_ERR_OVERFLOW (-4)     /* an output buffer was too small; rp_stats has the sizes */
+#define RP_ERR_UNSUPPORTED (-5)  /* valid request this build does not provide */
+
+#define RP_MAX_LAYERS 8
+
+enum { RP_MEDIUM_LAYERED = 0, RP_MEDIUM_GRID = 1 };
+enum { RP_FP64 = 0, RP_FP32_MIXED = 1 };
+enum { RP_POL_S = 0, RP_POL_P = 1, RP_POL_UNPOL = 2 };
+enum { RP_RHS_PROJECTED = 0, RP_RHS_PARAXIAL = 1 };
+
+/* Per-ray end status. */
+enum {
+    RP_ST_ALIVE = 0,         /* never written for a finished ray */
+    RP_ST_MAX_PATH = 1,      /* reached max_path (the last step is truncated to it) */
+    RP_ST_MAX_TIME = 2,      /* travel time reached max_time (Fig. 1 text: 5 us) */
+    RP_ST_MIN_AMP = 3,       /* |A| < min_amp |A0| (Fig. 1 text: A/A0 < 0.05) */
+    RP_ST_LEFT_DOMAIN = 4,   /* left the refractivity grid */
+    RP_ST_TRANSMITTED = 5,   /* refracted into an absorbing layer (e.g. air); not traced */
+    RP_ST_REACHED_STOP = 6,  /* landed on the stop plane (path finding) */
+    RP_ST_MAX_STEPS = 7,     /* attempted-step cap reached */
+    RP_ST_BAD_INPUT = 8,     /* zero or non-finite direction */
+    RP_ST_QUEUE_FULL = 9     /* secondary dropped: work queue full (also RP_ERR_OVERFLOW) */
+};
+
+/* ------------------------------------------------------------------------------------
+ * Media (Sec. 2, Fig. 1 text and the paragraph after it)
+ * ---------------------------------------------------------------------------------- */
+
+/* Horizontal layer k spans z_top <= z < z_top of layer k+1 (layer 0's z_top is ignored and
+ * read as -inf).  Inside it n(z) = n0 - dn * exp(-z / z0) + offset; dn = 0 gives a constant
+ * index.  absorb != 0: a ray refracted into this layer is recorded with status
+ * RP_ST_TRANSMITTED and not traced (the ice-air surface). */
+typedef struct {
+    double z_top, n0, dn, z0, offset;
+    int32_t absorb, pad;
+} rp_layer;
+
+/* kind = RP_MEDIUM_LAYERED: n_layers (1..8) layers, ordered top to bottom, z_top increasing.
+ * kind = RP_MEDIUM_GRID: node values of n on an nx * ny * nz grid (x fastest), node (i,j,k)
+ *   at origin + spacing * (i,j,k); `grid_n` may be a host or a device pointer and is copied.
+ *   The library derives grad n by central differences (one-sided on the faces) and stores
+ *   (n, dn/dx, dn/dy, dn/dz) as FP32 node samples; n and grad n at a point are trilinear
+ *   interpolations of those samples.  A ray whose committed position leaves the box ends
+ *   with RP_ST_LEFT_DOMAIN.  Grid media have no boundaries. */
+typedef struct {
+    int32_t kind, n_layers;
+    rp_layer layers[RP_MAX_LAYERS];
+    int32_t nx, ny, nz, pad;
+    double origin[3];
+    double spacing;
+    const float *grid_n;
+} rp_medium_desc;
+
+typedef struct rp_medium_s *rp_medium_t;
+
+/* Validates `desc`, copies it (and the grid, with its gradient precomputed by a kernel) to
+ * the current device and returns an opaque handle in *out.  The handle owns its device
+ * memory until rp_medium_destroy.  Errors: RP_ERR_INVALID_ARG (null pointer, bad layer count,
+ * z_top not increasing, z0 <= 0 with dn != 0, grid smaller than 2 nodes per axis,
+ * spacing <= 0), RP_ERR_OOM, RP_ERR_CUDA. */
+int rp_medium_create(const rp_medium_desc *desc, void *stream, rp_medium_t *out);
+
+/* Releases the handle and its device memory.  NULL is accepted. */
+int rp_medium_destroy(rp_medium_t m);
+
+/* ------------------------------------------------------------------------------------
+ * Tracing (Sec. 2: Eqs. 1-2, Cash-Karp step control, boundary module, receivers, breaks)
+ * ---------------------------------------------------------------------------------- */
+
+/* n primaries: pos (3, n), dir (3, n; normalised by the library, a zero or non-finite
+ * direction gives status RP_ST_BAD_INPUT), amp (n; NULL means 1).  Device pointers. */
+typedef struct {
+    int64_t n;
+    const double *pos, *dir, *amp;
+} rp_rays;
+
+/* Receiver spheres: center (n, 3) row-major, radius (n).  Device pointers; n = 0 or a NULL
+ * rp_receivers pointer means none.  A hit is recorded when a committed step chord enters a
+ * sphere (chord starts outside, entry point on the chord); receivers do not absorb. */
+typedef struct {
+    int32_t n, pad;
+    const double *center, *radius;
+} rp_receivers;
+
+/* Integration parameters.
+ *   tol          Cash-Karp tolerance on the error per unit step (dimensionless, > 0)
+ *   h_min, h_max step bounds [m] (0 < h_min <= h_max); a step at h_min is always accepted
+ *   h0           first step of a primary [m] (secondaries inherit their parent's step)
+ *   max_path     arc-length limit [m]
+ *   max_time     travel-time limit [s], <= 0: none
+ *   min_amp      terminate when |A| < min_amp |A0|, <= 0: none (A0 of the root primary)
+ *   eps_b        boundary landing tolerance [m] (FP32_MIXED uses at least 2e-6 m)
+ *   stop_n, stop_d, use_stop   optional stop plane stop_n . r = stop_d (unit normal)
+ *   max_generation  secondaries are spawned while the parent's generation is below it
+ *   precision    RP_FP64 (all arithmetic in FP64) or RP_FP32_MIXED (Runge-Kutta stages in
+ *                FP32, position and direction accumulated in float-float, travel time and
+ *                path length accumulated in FP64)
+ *   polarization RP_POL_S / RP_POL_P (signed field amplitudes) or RP_POL_UNPOL (square roots
+ *                of the s/p-averaged reflectance and transmittance)
+ *   rhs_form     RP_RHS_PROJECTED: t' = (grad n - (grad n . t) t)/n, Eq. 1 for unit t;
+ *                RP_RHS_PARAXIAL: t' = grad n / n, Eq. 2, t renormalised after each step
+ *   max_steps    cap on attempted Cash-Karp steps per ray (> 0) */
+typedef struct {
+    double tol, h_min, h_max, h0, max_path, max_time, min_amp, eps_b;
+    double stop_n[3], stop_d;
+    int32_t use_stop, max_generation, precision, polarization, rhs_form, pad;
+    int64_t max_steps;
+} rp_trace_params;
+
+/* Finished rays.  Primary i is written at index i; secondaries take the following indices
+ * in the order they are created (the order between rays of one generation is not
+ * deterministic).  Arrays of length `capacity` (pos/dir: (3, capacity)); every pointer except
+ * end_pos may be NULL to skip that field.  A secondary is identified by (parent, seq): seq is
+ * the index of the split on the parent that cast it. */
+typedef struct {
+    int64_t capacity;
+    double *end_pos, *end_dir, *path, *time, *amp;
+    int32_t *status, *generation, *seq, *layer;
+    int64_t *parent;
+    int32_t *n_acc, *n_rej, *n_root, *n_refl, *n_turn;
+} rp_ray_out;
+
+/* Receiver hits, arrays of length `capacity` (pos/dir: (3, capacity)); order not
+ * deterministic.  NULL rp_hits pointer: hits are only counted. */
+typedef struct {
+    int64_t capacity;
+    int64_t *ray;
+    int32_t *receiver;
+    double *time, *path, *amp, *pos, *dir;
+} rp_hits;
+
+/* Host-side statistics of one call. */
+typedef struct {
+    int64_t rays;            /* rays finished (primaries + secondaries); output size needed */
+    int64_t hits;            /* receiver hits; hit capacity needed */
+    int64_t secondaries;     /* secondaries cast (queued or recorded as transmitted) */
+    int64_t steps_accepted, steps_rejected, steps_root;
+    int64_t queue_needed;    /* secondary records that had to be queued */
+    int32_t waves, flags;    /* flags: 1 bad input, 2 output, 4 queue, 8 hit overflow,
+                                16 a boundary search hit its iteration cap */
+    double kernel_ms;        /* device time of the tracing kernels */
+} rp_stats;
+
+/* Traces in->n primaries and every secondary they spawn, in one persistent launch per ray
+ * generation (max_generation + 1 launches).  `rx` and `hits` may be NULL, `stats` may be
+ * NULL.  Returns RP_OK, RP_ERR_INVALID_ARG (parameters, null arrays, capacity < n),
+ * RP_ERR_OVERFLOW (out, queue or hit capacity exceeded: rp_stats holds the sizes needed;
+ * everything that fitted was written), RP_ERR_OOM, RP_ERR_CUDA. */
+int rp_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp_trace_params *p,
+             rp_ray_out *out, rp_hits *hits, rp_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------------------------
+ * Source-receiver path finding (Sec. 2, accuracy study)
+ * ---------------------------------------------------------------------------------- */
+
+/* trace: integration parameters (max_path, use_stop, stop_* and max_generation are set per
+ *   pair by the library: path budget 2 (D + z_s + z_r) + 100 m, stop plane x = D, no
+ *   secondaries).  hit_tol: accept when the vertical miss at x = D is below it [m].
+ *   max_iter: bisection cap per bracket.  max_sol: solution slots per pair (1..8). */
+typedef struct {
+    rp_trace_params trace;
+    double hit_tol;
+    int32_t max_iter, max_sol;
+} rp_path_params;
+
+enum { RP_SOL_DIRECT = 0, RP_SOL_REFRACTED = 1, RP_SOL_REFLECTED = 2 };
+
+/* Solutions, device arrays: count (n_pairs); the rest (n_pairs, max_sol) row-major, slots
+ * beyond count[i] zeroed, slots sorted by travel time.  type: RP_SOL_*; launch / receive:
+ * launch and arrival angles from +z [rad]; time [s], path [m], amp (Fresnel factors);
+ * miss: vertical miss at the receiver [m]; n_iter: bisection steps. */
+typedef struct {
+    int32_t *count, *type, *n_iter;
+    double *launch, *receive, *time, *path, *amp, *miss;
+} rp_solutions;
+
+/* For each pair (z_s[i], z_r[i], D[i]) with n_angles[i] >= 2 scan angles: rays from
+ * (0, 0, z_s) at angles pi j / (n_angles - 1) in the x-z plane are traced to the plane x = D;
+ * adjacent angles whose vertical misses change sign are refined by FP64 bisection on the
+ * launch angle until |miss| < hit_tol.  A ray that exhausts its path budget before x = D
+ * scores +inf (it is far below).  D < hit_tol: the vertical ray to the receiver depth.
+ * Solution type: REFLECTED if the ray reflected off a boundary, REFRACTED if it turned
+ * (t_z changed sign), else DIRECT.  Returns RP_OK, RP_ERR_INVALID_ARG, RP_ERR_OOM,
+ * RP_ERR_CUDA. */
+int rp_find_paths(rp_medium_t m, int64_t n_pairs, const double *z_s, const double *z_r,
+                  const double *dist, const int32_t *n_angles, const rp_path_params *p,
+                  rp_solutions *sol, rp_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------------------------
+ * Misc
+ * ---------------------------------------------------------------------------------- */
+
+/* Copies the last error message of the calling thread into buf (NUL-terminated, truncated
+ * to len).  Returns the full message length. */
+int rp_last_error(char *buf, size_t len);
+
+/* Library version string (static storage). */
+const char *rp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

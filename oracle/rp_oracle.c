@@ -497,7 +497,7 @@ static void trace_one(trace_ctx *c, const start_state *st)
         if (!(e <= 1.0) && h_try > p->h_min) {
             ++n_rej;
             double fac = 0.9 * pow(e, -0.25);
-            if (fac < 0.1) fac = 0.1;
+            if (!(fac >= 0.1)) fac = 0.1;
             h = h_try * fac;
             if (h < p->h_min) h = p->h_min;
             continue;

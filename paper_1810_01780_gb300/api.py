@@ -1,0 +1,217 @@
+"""Torch-level binding of the C ABI (device memory and streams from PyTorch; no compute here).
+
+Every function marshals tensors into the structs of include/rp.h and calls the CUDA
+library.  Tensors must live on the current CUDA device; ray arrays are float64 (3, n)
+structure-of-arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi as A
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dev_f64(x, shape=None):
+    t = torch.as_tensor(x, dtype=torch.float64, device="cuda")
+    t = t.contiguous()
+    if shape is not None:
+        t = t.reshape(shape)
+    return t
+
+
+class Medium:
+    """A refractivity model on the device (rp_medium_create / rp_medium_destroy)."""
+
+    def __init__(self, desc: dict, stream=None):
+        A.lib()
+        d = A.MediumDesc()
+        self.desc = desc
+        self._keep = None
+        if desc["kind"] == "layered":
+            layers = desc["layers"]
+            if not 1 <= len(layers) <= A.MAX_LAYERS:
+                raise ValueError("1..8 layers")
+            d.kind = 0
+            d.n_layers = len(layers)
+            for k, L in enumerate(layers):
+                d.layers[k].z_top = float(L.get("z_top", -np.inf)) if k else 0.0
+                d.layers[k].n0 = float(L["n0"])
+                d.layers[k].dn = float(L.get("dn", 0.0))
+                d.layers[k].z0 = float(L.get("z0", 1.0))
+                d.layers[k].offset = float(L.get("off", 0.0))
+                d.layers[k].absorb = int(bool(L.get("absorb", False)))
+        elif desc["kind"] == "grid":
+            n = desc["n"]
+            if isinstance(n, torch.Tensor):
+                n = n.to(device="cuda", dtype=torch.float32).contiguous()
+                nz, ny, nx = n.shape
+                d.grid_n = n.data_ptr()
+            else:
+                n = np.ascontiguousarray(n, dtype=np.float32)
+                nz, ny, nx = n.shape
+                d.grid_n = n.ctypes.data
+            self._keep = n
+            d.kind = 1
+            d.n_layers = 1
+            d.nx, d.ny, d.nz = nx, ny, nz
+            for a in range(3):
+                d.origin[a] = float(desc["origin"][a])
+            d.spacing = float(desc["spacing"])
+        else:
+            raise ValueError(desc["kind"])
+        h = C.c_void_p()
+        A.check(A.lib().rp_medium_create(C.byref(d), C.c_void_p(_stream_ptr(stream)), C.byref(h)))
+        self._keep = None
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            A.lib().rp_medium_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_params(p: dict, precision: str = "fp64") -> A.TraceParams:
+    q = A.TraceParams()
+    q.tol = p["tol"]
+    q.h_min = p["h_min"]
+    q.h_max = p["h_max"]
+    q.h0 = p.get("h0", p["h_max"])
+    q.max_path = p.get("max_path", 0.0)
+    q.max_time = p.get("max_time", 0.0)
+    q.min_amp = p.get("min_amp", 0.0)
+    q.eps_b = p.get("eps_b", 1e-9)
+    stop = p.get("stop")
+    if stop is not None:
+        q.use_stop = 1
+        for a in range(3):
+            q.stop_n[a] = stop[0][a]
+        q.stop_d = stop[1]
+    q.max_generation = p.get("max_generation", 3)
+    q.precision = A.PRECISION[precision]
+    q.polarization = A.POLARIZATION[p.get("polarization", "s")]
+    q.rhs_form = A.RHS_FORM[p.get("rhs_form", "projected")]
+    q.max_steps = int(p.get("max_steps", 1_000_000))
+    return q
+
+
+RAY_FIELDS_F64 = ("path", "time", "amp")
+RAY_FIELDS_I32 = ("status", "generation", "seq", "layer", "n_acc", "n_rej", "n_root", "n_refl",
+                  "n_turn")
+
+
+class TraceBuffers:
+    """Preallocated device outputs for repeated rp_trace calls."""
+
+    def __init__(self, capacity: int, hit_capacity: int = 0, fields=None):
+        self.capacity = int(capacity)
+        self.hit_capacity = int(hit_capacity)
+        f = dict(device="cuda")
+        want = set(fields) if fields is not None else None
+
+        def need(name):
+            return want is None or name in want
+
+        self.t = {"end_pos": torch.empty((3, self.capacity), dtype=torch.float64, **f)}
+        if need("end_dir"):
+            self.t["end_dir"] = torch.empty((3, self.capacity), dtype=torch.float64, **f)
+        for k in RAY_FIELDS_F64:
+            if need(k):
+                self.t[k] = torch.empty(self.capacity, dtype=torch.float64, **f)
+        for k in RAY_FIELDS_I32:
+            if need(k):
+                self.t[k] = torch.empty(self.capacity, dtype=torch.int32, **f)
+        if need("parent"):
+            self.t["parent"] = torch.empty(self.capacity, dtype=torch.int64, **f)
+        self.out = A.RayOut()
+        self.out.capacity = self.capacity
+        for name, t in self.t.items():
+            setattr(self.out, name, t.data_ptr())
+        self.h = {}
+        self.hits = None
+        if self.hit_capacity > 0:
+            hc = self.hit_capacity
+            self.h = {
+                "ray": torch.empty(hc, dtype=torch.int64, **f),
+                "receiver": torch.empty(hc, dtype=torch.int32, **f),
+                "time": torch.empty(hc, dtype=torch.float64, **f),
+                "path": torch.empty(hc, dtype=torch.float64, **f),
+                "amp": torch.empty(hc, dtype=torch.float64, **f),
+                "pos": torch.empty((3, hc), dtype=torch.float64, **f),
+                "dir": torch.empty((3, hc), dtype=torch.float64, **f),
+            }
+            self.hits = A.Hits()
+            self.hits.capacity = hc
+            for name, t in self.h.items():
+                setattr(self.hits, name, t.data_ptr())
+
+
+class PreparedRays:
+    """Device copies of a ray batch and its receivers, marshalled once."""
+
+    def __init__(self, pos, dir, amp=None, receivers=None):
+        self.pos = _dev_f64(pos, (3, -1))
+        self.dir = _dev_f64(dir, (3, -1))
+        self.n = self.pos.shape[1]
+        self.amp = None if amp is None else _dev_f64(amp)
+        self.rays = A.Rays(self.n, self.pos.data_ptr(), self.dir.data_ptr(),
+                           0 if self.amp is None else self.amp.data_ptr())
+        self.rx = None
+        if receivers is not None and len(receivers[1]) > 0:
+            self.rx_c = _dev_f64(receivers[0], (-1, 3))
+            self.rx_r = _dev_f64(receivers[1])
+            self.rx = A.Receivers(len(self.rx_r), 0, self.rx_c.data_ptr(), self.rx_r.data_ptr())
+
+
+def trace_into(medium: Medium, rays: PreparedRays, params: A.TraceParams, buf: TraceBuffers,
+               stream=None, allow_overflow=False) -> A.Stats:
+    """One rp_trace call into preallocated buffers; returns the stats struct."""
+    st = A.Stats()
+    rc = A.lib().rp_trace(medium.handle, C.byref(rays.rays),
+                          C.byref(rays.rx) if rays.rx is not None else None, C.byref(params),
+                          C.byref(buf.out), C.byref(buf.hits) if buf.hits is not None else None,
+                          C.byref(st), C.c_void_p(_stream_ptr(stream)))
+    A.check(rc, allow_overflow=allow_overflow)
+    st.rc = rc
+    return st
+
+
+def trace(medium: Medium, pos, dir, amp=None, params: dict | None = None, receivers=None,
+          precision: str = "fp64", capacity: int | None = None, hit_capacity: int | None = None,
+          stream=None) -> dict:
+    """Traces primaries and their secondaries; grows the buffers and retries on overflow.
+
+    Returns {"rays": {field: tensor[:n_rays]}, "hits": {...}, "stats": dict}."""
+    rays = PreparedRays(pos, dir, amp, receivers)
+    prm = make_params(params, precision)
+    cap = capacity or max(16, 4 * rays.n)
+    hcap = hit_capacity if hit_capacity is not None else (max(16, rays.n) if rays.rx else 0)
+    while True:
+        buf = TraceBuffers(cap, hcap)
+        st = trace_into(medium, rays, prm, buf, stream, allow_overflow=True)
+        if st.rc == A.RP_OK:
+            break
+        cap = max(cap, int(st.rays) + 16)
+        hcap = max(hcap, int(st.hits) + 16)
+    n = int(st.rays)
+    out = {k: (v[:, :n] if v.dim() == 2 else v[:n]) for k, v in buf.t.items()}
+    nh = int(st.hits) if buf.hits is not None else 0
+    hits = {k: (v[:, :nh] if v.dim() == 2 else v[:nh]) for k, v in buf.h.items()}
+    return {"rays": out, "hits": hits, "stats": st.as_dict()}

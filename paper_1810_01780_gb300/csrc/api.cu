@@ -1,0 +1,243 @@
+// api.cu -- the C ABI entry points (rp.h): argument checks, media, workspace, errors.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+
+#include "rp_internal.h"
+
+namespace rph {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    return e == cudaErrorMemoryAllocation ? RP_ERR_OOM : RP_ERR_CUDA;
+}
+
+Workspace &workspace(int device)
+{
+    static std::mutex mu;
+    static std::map<int, Workspace *> ws;
+    std::lock_guard<std::mutex> lock(mu);
+    Workspace *&w = ws[device];
+    if (!w) w = new Workspace();
+    return *w;
+}
+
+int ensure_workspace(Workspace &w, size_t bytes)
+{
+    if (!w.host_ctrl) RP_CUDA_TRY(cudaMallocHost(&w.host_ctrl, 4096));
+    if (w.size >= bytes) return RP_OK;
+    if (w.ptr) {
+        RP_CUDA_TRY(cudaDeviceSynchronize());
+        RP_CUDA_TRY(cudaFree(w.ptr));
+        w.ptr = nullptr;
+        w.size = 0;
+    }
+    size_t sz = bytes + bytes / 4;
+    cudaError_t e = cudaMalloc(&w.ptr, sz);
+    if (e != cudaSuccess) {
+        w.ptr = nullptr;
+        return cuda_fail(e, "cudaMalloc(workspace)");
+    }
+    w.size = sz;
+    return RP_OK;
+}
+
+int sm_count(int device)
+{
+    static int cached[64] = {0};
+    if (device >= 0 && device < 64 && cached[device]) return cached[device];
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device);
+    if (n <= 0) n = 1;
+    if (device >= 0 && device < 64) cached[device] = n;
+    return n;
+}
+
+int validate_params(const rp_trace_params *p, bool path_finding)
+{
+    if (!(p->tol > 0.0) || !(p->h_min > 0.0) || !(p->h_max >= p->h_min) || !(p->h0 > 0.0)) {
+        set_error("params: need tol > 0, 0 < h_min <= h_max, h0 > 0");
+        return RP_ERR_INVALID_ARG;
+    }
+    if (!path_finding && !(p->max_path > 0.0)) {
+        set_error("params: need max_path > 0");
+        return RP_ERR_INVALID_ARG;
+    }
+    if (!(p->eps_b > 0.0) || p->max_steps <= 0 || p->max_generation < 0 ||
+        p->max_generation > 15) {
+        set_error("params: need eps_b > 0, max_steps > 0, 0 <= max_generation <= 15");
+        return RP_ERR_INVALID_ARG;
+    }
+    if (p->precision != RP_FP64 && p->precision != RP_FP32_MIXED) {
+        set_error("params: unknown precision %d", p->precision);
+        return RP_ERR_INVALID_ARG;
+    }
+    if (p->polarization < RP_POL_S || p->polarization > RP_POL_UNPOL ||
+        (p->rhs_form != RP_RHS_PROJECTED && p->rhs_form != RP_RHS_PARAXIAL)) {
+        set_error("params: bad polarization or rhs_form");
+        return RP_ERR_INVALID_ARG;
+    }
+    return RP_OK;
+}
+
+}  // namespace rph
+
+using namespace rph;
+
+extern "C" {
+
+int rp_medium_create(const rp_medium_desc *d, void *stream, rp_medium_t *out)
+{
+    if (!d || !out) {
+        set_error("rp_medium_create: null argument");
+        return RP_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    rp_medium_s *m = new (std::nothrow) rp_medium_s();
+    if (!m) return RP_ERR_OOM;
+    memset(&m->layered, 0, sizeof m->layered);
+    memset(&m->grid, 0, sizeof m->grid);
+    m->grid_dev = nullptr;
+    cudaError_t e = cudaGetDevice(&m->device);
+    if (e != cudaSuccess) {
+        delete m;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    m->kind = d->kind;
+    if (d->kind == RP_MEDIUM_LAYERED) {
+        if (d->n_layers < 1 || d->n_layers > RP_MAX_LAYERS) {
+            delete m;
+            set_error("rp_medium_create: n_layers must be 1..%d", RP_MAX_LAYERS);
+            return RP_ERR_INVALID_ARG;
+        }
+        m->layered.n_layers = d->n_layers;
+        for (int k = 0; k < d->n_layers; ++k) {
+            const rp_layer &L = d->layers[k];
+            if (k >= 2 && !(L.z_top > d->layers[k - 1].z_top)) {
+                delete m;
+                set_error("rp_medium_create: z_top must increase with the layer index");
+                return RP_ERR_INVALID_ARG;
+            }
+            if (L.dn != 0.0 && !(L.z0 > 0.0)) {
+                delete m;
+                set_error("rp_medium_create: layer %d needs z0 > 0", k);
+                return RP_ERR_INVALID_ARG;
+            }
+            if (!(L.n0 + L.offset > 0.0)) {
+                delete m;
+                set_error("rp_medium_create: layer %d has a non-positive index", k);
+                return RP_ERR_INVALID_ARG;
+            }
+            rpk::LayerC &c = m->layered.L[k];
+            c.n0 = L.n0;
+            c.dn = L.dn;
+            c.off = L.offset;
+            c.has_exp = L.dn != 0.0;
+            c.inv_z0 = c.has_exp ? 1.0 / L.z0 : 0.0;
+            c.gcoef = c.has_exp ? L.dn / L.z0 : 0.0;
+            c.n0f = (float)c.n0;
+            c.dnf = (float)c.dn;
+            c.offf = (float)c.off;
+            c.inv_z0f = (float)c.inv_z0;
+            c.gcoeff = (float)c.gcoef;
+            c.absorb = L.absorb != 0;
+            m->layered.top[k] = plane_const(k ? L.z_top : -1e300);
+        }
+    } else if (d->kind == RP_MEDIUM_GRID) {
+        if (d->nx < 2 || d->ny < 2 || d->nz < 2 || !(d->spacing > 0.0) || !d->grid_n) {
+            delete m;
+            set_error("rp_medium_create: grid needs >= 2 nodes per axis, spacing > 0, data");
+            return RP_ERR_INVALID_ARG;
+        }
+        rpk::MediumGrid &g = m->grid;
+        g.nx = d->nx;
+        g.ny = d->ny;
+        g.nz = d->nz;
+        const int dims[3] = {d->nx, d->ny, d->nz};
+        for (int a = 0; a < 3; ++a) {
+            g.org[a] = d->origin[a];
+            g.orgf[a] = (float)d->origin[a];
+            g.hi[a] = d->origin[a] + d->spacing * (double)(dims[a] - 1);
+        }
+        g.inv_sp = 1.0 / d->spacing;
+        g.inv_spf = (float)g.inv_sp;
+        int rc = build_grid(m, d->grid_n, d->spacing, (cudaStream_t)stream);
+        if (rc) {
+            if (m->grid_dev) cudaFree(m->grid_dev);
+            delete m;
+            return rc;
+        }
+        g.g = m->grid_dev;
+    } else {
+        delete m;
+        set_error("rp_medium_create: unknown kind %d", d->kind);
+        return RP_ERR_INVALID_ARG;
+    }
+    *out = m;
+    return RP_OK;
+}
+
+int rp_medium_destroy(rp_medium_t m)
+{
+    if (!m) return RP_OK;
+    if (m->grid_dev) cudaFree(m->grid_dev);
+    delete m;
+    return RP_OK;
+}
+
+int rp_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp_trace_params *p,
+             rp_ray_out *out, rp_hits *hits, rp_stats *stats, void *stream)
+{
+    if (stats) memset(stats, 0, sizeof *stats);
+    try {
+        return run_trace(m, in, rx, p, out, hits, stats, (cudaStream_t)stream);
+    } catch (...) {
+        set_error("rp_trace: internal exception");
+        return RP_ERR_CUDA;
+    }
+}
+
+int rp_find_paths(rp_medium_t m, int64_t n_pairs, const double *z_s, const double *z_r,
+                  const double *dist, const int32_t *n_angles, const rp_path_params *p,
+                  rp_solutions *sol, rp_stats *stats, void *stream)
+{
+    if (stats) memset(stats, 0, sizeof *stats);
+    try {
+        return run_find_paths(m, n_pairs, z_s, z_r, dist, n_angles, p, sol, stats,
+                              (cudaStream_t)stream);
+    } catch (...) {
+        set_error("rp_find_paths: internal exception");
+        return RP_ERR_CUDA;
+    }
+}
+
+int rp_last_error(char *buf, size_t len)
+{
+    const std::string &s = g_last_error;
+    if (buf && len) {
+        size_t k = s.size() < len - 1 ? s.size() : len - 1;
+        memcpy(buf, s.data(), k);
+        buf[k] = 0;
+    }
+    return (int)s.size();
+}
+
+const char *rp_version(void) { return "rp-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

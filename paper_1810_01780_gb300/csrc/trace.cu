@@ -1,0 +1,428 @@
+// trace.cu -- persistent, generation-ordered tracing launches (rp_trace).
+//
+// Rays of one generation are traced by one persistent launch: every thread claims rays from
+// a global counter (warp-aggregated atomics), traces its ray with the lane state machine of
+// trace_core.cuh and claims the next one as soon as it finishes, so rays with very different
+// step counts keep all lanes busy.  Secondaries cast at boundaries (Sec. 2, boundary module)
+// are appended to a device work queue; the queue segment written by generation g is the
+// input of the launch for generation g + 1.  A launch therefore never waits for work that
+// another thread has still to produce: there are no spin waits anywhere, and the whole call
+// is a fixed sequence of (max_generation + 1) launches on one stream.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "rp_internal.h"
+
+namespace cg = cooperative_groups;
+using namespace rpk;
+
+namespace rph {
+
+struct WaveIn {
+    const double *pos, *dir, *amp;
+    long long n;
+    PlaneC stop;
+    double h0;
+};
+
+__device__ __forceinline__ long long claim_index(unsigned long long *counter)
+{
+    cg::coalesced_group g = cg::coalesced_threads();
+    unsigned long long base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(counter, (unsigned long long)g.size());
+    base = g.shfl(base, 0);
+    return (long long)(base + g.thread_rank());
+}
+
+template <class P, class M>
+__device__ __forceinline__ void lane_reset(Lane<P> &L, const StepParams<P> &sp, const PlaneC &stop)
+{
+    L.mode = MODE_NORMAL;
+    L.ev = EV_NONE;
+    L.side = 0;
+    L.it = 0;
+    L.nsplit = 0;
+    L.n_acc = L.n_rej = L.n_root = L.n_refl = L.n_turn = L.root_fail = 0;
+    L.status = RP_ST_ALIVE;
+    L.stop = stop;
+    init_stop(L, sp);
+    set_trial(L, sp);
+}
+
+// Next ray of this wave for the calling lane; false when the wave's input is exhausted.
+template <class P, class M>
+__device__ bool next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, const Sinks &sk,
+                         const WaveIn &in, int wave, unsigned long long base,
+                         unsigned long long count)
+{
+    for (;;) {
+        const long long k = claim_index(&sk.ctrl->claim[wave]);
+        if (k >= (long long)count) return false;
+        double r[3], t[3];
+        if (wave == 0) {
+            const long long n = in.n;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                r[a] = in.pos[a * n + k];
+                t[a] = in.dir[a * n + k];
+            }
+            L.A = in.amp ? in.amp[k] : 1.0;
+            L.A0 = L.A;
+            L.T = 0.0;
+            L.s = 0.0;
+            L.h = P::from_d(in.h0);
+            L.id = k;
+            L.parent = -1;
+            L.gen = 0;
+            L.seq = 0;
+            if constexpr (is_layered_v<M>)
+                L.layer = layer_of(med, r[2]);
+            else
+                L.layer = 0;
+            double q = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+            const bool pos_ok = isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]);
+            if (!(q > 0.0) || !isfinite(q) || !pos_ok) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    P::set(L.r, a, r[a]);
+                    P::set(L.t, a, t[a]);
+                }
+                lane_reset<P, M>(L, sp, in.stop);
+                L.status = RP_ST_BAD_INPUT;
+                atomicOr(&sk.ctrl->flags, (unsigned)FLAG_BAD_INPUT);
+                write_ray<P>(sk.out, L.id, L, sk.ctrl);
+                continue;
+            }
+            t[0] /= q;
+            t[1] /= q;
+            t[2] /= q;
+        } else {
+            const QRec &Q = sk.queue[base + k];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                r[a] = Q.r[a];
+                t[a] = Q.t[a];
+            }
+            L.A = Q.A;
+            L.A0 = Q.A0;
+            L.T = Q.T;
+            L.s = Q.s;
+            L.h = P::from_d(Q.h);
+            L.id = Q.id;
+            L.parent = Q.parent;
+            L.gen = Q.gen;
+            L.seq = Q.seq;
+            L.layer = Q.layer;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            P::set(L.r, a, r[a]);
+            P::set(L.t, a, t[a]);
+        }
+        lane_reset<P, M>(L, sp, in.stop);
+        return true;
+    }
+}
+
+template <class P, class M>
+__global__ void __launch_bounds__(256) k_trace_wave(const M med, const StepParams<P> sp,
+                                                    const Sinks sk, const WaveIn in, int wave)
+{
+    __shared__ unsigned long long s_cnt[3];
+    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    unsigned long long base = 0, count;
+    if (wave == 0) {
+        count = (unsigned long long)in.n;
+    } else {
+        base = sk.ctrl->seg_begin[wave];
+        count = sk.ctrl->seg_end[wave] - base;
+    }
+    Lane<P> L;
+    unsigned long long acc = 0, rej = 0, root = 0;
+    bool have = next_ray<P, M>(L, med, sp, sk, in, wave, base, count);
+    while (have) {
+        if (advance<P, M>(med, L, sp, sk)) {
+            acc += (unsigned long long)L.n_acc;
+            rej += (unsigned long long)L.n_rej;
+            root += (unsigned long long)L.n_root;
+            write_ray<P>(sk.out, L.id, L, sk.ctrl);
+            have = next_ray<P, M>(L, med, sp, sk, in, wave, base, count);
+        }
+    }
+    atomicAdd(&s_cnt[0], acc);
+    atomicAdd(&s_cnt[1], rej);
+    atomicAdd(&s_cnt[2], root);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&sk.ctrl->steps_acc, s_cnt[0]);
+        atomicAdd(&sk.ctrl->steps_rej, s_cnt[1]);
+        atomicAdd(&sk.ctrl->steps_root, s_cnt[2]);
+    }
+}
+
+__global__ void k_init_ctrl(Ctrl *ctrl, long long n)
+{
+    ctrl->out_count = (unsigned long long)n;
+}
+
+// Input segment of wave w: the queue records written by wave w - 1.
+__global__ void k_prep_wave(Ctrl *ctrl, int w, unsigned long long q_cap)
+{
+    const unsigned long long tail = ctrl->q_tail < q_cap ? ctrl->q_tail : q_cap;
+    ctrl->seg_begin[w] = (w == 1) ? 0ull : ctrl->seg_end[w - 1];
+    ctrl->seg_end[w] = tail;
+}
+
+template <class P, class M>
+static int occupancy_grid(int block)
+{
+    static int cached_block = -1, cached_occ = 0;
+    if (cached_block != block) {
+        int occ = 0;
+        RP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_wave<P, M>,
+                                                                  block, 0));
+        cached_occ = occ > 0 ? occ : 1;
+        cached_block = block;
+    }
+    return cached_occ;
+}
+
+template <class P, class M>
+static int launch_waves(const M &med, const StepParams<P> &sp, const Sinks &sk, const WaveIn &in,
+                        int n_waves, int device, int block, cudaStream_t st)
+{
+    int occ = occupancy_grid<P, M>(block);
+    if (occ < 0) return occ;
+    const int grid = sm_count(device) * occ;
+    for (int w = 0; w < n_waves; ++w) {
+        if (w > 0) k_prep_wave<<<1, 1, 0, st>>>(sk.ctrl, w, sk.q_cap);
+        k_trace_wave<P, M><<<grid, block, 0, st>>>(med, sp, sk, in, w);
+    }
+    RP_CUDA_TRY(cudaGetLastError());
+    return RP_OK;
+}
+
+template <class P>
+static StepParams<P> make_step_params(const rp_trace_params *p, int axis, float dir)
+{
+    StepParams<P> sp;
+    sp.tol = (typename P::R)p->tol;
+    sp.h_min = (typename P::R)p->h_min;
+    sp.h_max = (typename P::R)p->h_max;
+    double eps = p->eps_b;
+    if (P::kFF && eps < 2e-6) eps = 2e-6;
+    sp.eps_b = (typename P::R)eps;
+    sp.max_path = p->max_path;
+    sp.max_time = p->max_time;
+    sp.min_amp = p->min_amp;
+    sp.rhs_form = p->rhs_form;
+    sp.polarization = p->polarization;
+    sp.max_generation = p->max_generation;
+    sp.use_stop = p->use_stop;
+    sp.stop_axis = axis;
+    sp.stop_dir = dir;
+    sp.max_steps = p->max_steps;
+    return sp;
+}
+
+// Stop plane stop_n . r = stop_d with stop_n = +/- a coordinate axis.
+int stop_axis_of(const rp_trace_params *p, int *axis, float *dir, double *offset)
+{
+    *axis = 0;
+    *dir = 1.0f;
+    *offset = 0.0;
+    if (!p->use_stop) return RP_OK;
+    int nz = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (p->stop_n[a] == 0.0) continue;
+        if (p->stop_n[a] != 1.0 && p->stop_n[a] != -1.0) nz = 9;
+        *axis = a;
+        *dir = (float)p->stop_n[a];
+        ++nz;
+    }
+    if (nz != 1) {
+        set_error("stop plane normal must be +/- a coordinate axis");
+        return RP_ERR_INVALID_ARG;
+    }
+    *offset = p->stop_d * (double)*dir;  // the plane is r[axis] = dir * stop_d
+    return RP_OK;
+}
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp_trace_params *p,
+              rp_ray_out *out, rp_hits *hits, rp_stats *stats, cudaStream_t st)
+{
+    if (!m || !in || !p || !out) {
+        set_error("rp_trace: null medium, rays, params or output");
+        return RP_ERR_INVALID_ARG;
+    }
+    if (in->n < 0 || (in->n > 0 && (!in->pos || !in->dir))) {
+        set_error("rp_trace: bad ray arrays");
+        return RP_ERR_INVALID_ARG;
+    }
+    if (!out->end_pos || out->capacity < in->n) {
+        set_error("rp_trace: output capacity %lld < n %lld or end_pos null",
+                  (long long)out->capacity, (long long)in->n);
+        return RP_ERR_INVALID_ARG;
+    }
+    int rc = validate_params(p, false);
+    if (rc) return rc;
+    int axis;
+    float sdir;
+    double soff;
+    if ((rc = stop_axis_of(p, &axis, &sdir, &soff))) return rc;
+    if (hits && hits->capacity > 0 && (!hits->ray || !hits->receiver)) {
+        set_error("rp_trace: hits need ray and receiver arrays");
+        return RP_ERR_INVALID_ARG;
+    }
+    int n_rx = (rx && rx->n > 0) ? rx->n : 0;
+    if (n_rx && (!rx->center || !rx->radius)) {
+        set_error("rp_trace: receiver arrays are null");
+        return RP_ERR_INVALID_ARG;
+    }
+    int dev;
+    RP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != m->device) {
+        set_error("rp_trace: medium lives on device %d, current device is %d", m->device, dev);
+        return RP_ERR_INVALID_ARG;
+    }
+
+    // receivers: sort by centre depth on the host (tiny), upload with the workspace
+    std::vector<SphereC> spheres(n_rx);
+    std::vector<float> cz(n_rx);
+    float r_max = 0.0f;
+    if (n_rx) {
+        std::vector<double> c(3 * (size_t)n_rx), rad(n_rx);
+        RP_CUDA_TRY(cudaMemcpyAsync(c.data(), rx->center, c.size() * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+        RP_CUDA_TRY(cudaMemcpyAsync(rad.data(), rx->radius, rad.size() * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+        RP_CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<int> order(n_rx);
+        for (int j = 0; j < n_rx; ++j) order[j] = j;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return c[3 * a + 2] < c[3 * b + 2]; });
+        for (int j = 0; j < n_rx; ++j) {
+            const int o = order[j];
+            if (!(rad[o] > 0.0)) {
+                set_error("rp_trace: receiver radius must be > 0");
+                return RP_ERR_INVALID_ARG;
+            }
+            for (int a = 0; a < 3; ++a) spheres[j].c[a] = plane_const(c[3 * o + a]);
+            spheres[j].R = rad[o];
+            spheres[j].Rf = (float)rad[o];
+            spheres[j].idx = o;
+            cz[j] = (float)c[3 * o + 2];
+            r_max = std::max(r_max, (float)rad[o]);
+        }
+    }
+
+    const long long q_cap = out->capacity - in->n;
+    const size_t off_ctrl = 0;
+    const size_t off_q = align_up(sizeof(Ctrl));
+    const size_t off_s = off_q + align_up(sizeof(QRec) * (size_t)std::max(q_cap, 1LL));
+    const size_t off_z = off_s + align_up(sizeof(SphereC) * (size_t)std::max(n_rx, 1));
+    const size_t total = off_z + align_up(sizeof(float) * (size_t)std::max(n_rx, 1));
+
+    Workspace &ws = workspace(dev);
+    std::lock_guard<std::mutex> lock(ws.mu);
+    if ((rc = ensure_workspace(ws, total))) return rc;
+    char *base = (char *)ws.ptr;
+    Ctrl *ctrl = (Ctrl *)(base + off_ctrl);
+
+    Sinks sk;
+    memset(&sk, 0, sizeof sk);
+    sk.ctrl = ctrl;
+    sk.queue = (QRec *)(base + off_q);
+    sk.q_cap = (unsigned long long)q_cap;
+    sk.out = *out;
+    if (hits) sk.hits = *hits;
+    sk.has_rx = n_rx > 0;
+    sk.rx.s = (const SphereC *)(base + off_s);
+    sk.rx.cz = (const float *)(base + off_z);
+    sk.rx.n = n_rx;
+    sk.rx.r_max = r_max;
+
+    RP_CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
+    if (n_rx) {
+        RP_CUDA_TRY(cudaMemcpyAsync(base + off_s, spheres.data(), sizeof(SphereC) * n_rx,
+                                    cudaMemcpyHostToDevice, st));
+        RP_CUDA_TRY(cudaMemcpyAsync(base + off_z, cz.data(), sizeof(float) * n_rx,
+                                    cudaMemcpyHostToDevice, st));
+    }
+    k_init_ctrl<<<1, 1, 0, st>>>(ctrl, in->n);
+
+    WaveIn wi;
+    wi.pos = in->pos;
+    wi.dir = in->dir;
+    wi.amp = in->amp;
+    wi.n = in->n;
+    wi.stop = plane_const(soff);
+    wi.h0 = p->h0;
+
+    cudaEvent_t e0, e1;
+    RP_CUDA_TRY(cudaEventCreate(&e0));
+    RP_CUDA_TRY(cudaEventCreate(&e1));
+    RP_CUDA_TRY(cudaEventRecord(e0, st));
+    const int n_waves = p->max_generation + 1;
+    const int block = 128;
+    if (m->kind == RP_MEDIUM_LAYERED) {
+        if (p->precision == RP_FP64)
+            rc = launch_waves<PrecF64, MediumLayered>(m->layered,
+                                                      make_step_params<PrecF64>(p, axis, sdir),
+                                                      sk, wi, n_waves, dev, block, st);
+        else
+            rc = launch_waves<PrecF32, MediumLayered>(m->layered,
+                                                      make_step_params<PrecF32>(p, axis, sdir),
+                                                      sk, wi, n_waves, dev, block, st);
+    } else {
+        if (p->precision == RP_FP64)
+            rc = launch_waves<PrecF64, MediumGrid>(m->grid, make_step_params<PrecF64>(p, axis, sdir),
+                                                   sk, wi, n_waves, dev, block, st);
+        else
+            rc = launch_waves<PrecF32, MediumGrid>(m->grid, make_step_params<PrecF32>(p, axis, sdir),
+                                                   sk, wi, n_waves, dev, block, st);
+    }
+    if (rc) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+    }
+    RP_CUDA_TRY(cudaEventRecord(e1, st));
+    Ctrl *hc = (Ctrl *)ws.host_ctrl;
+    RP_CUDA_TRY(cudaMemcpyAsync(hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    RP_CUDA_TRY(cudaStreamSynchronize(st));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+
+    unsigned flags = hc->flags;
+    if (!hits) flags &= ~(unsigned)FLAG_HIT_OVERFLOW;
+    if (stats) {
+        stats->rays = (int64_t)hc->out_count;
+        stats->hits = (int64_t)hc->n_hits;
+        stats->secondaries = (int64_t)hc->n_secondary;
+        stats->steps_accepted = (int64_t)hc->steps_acc;
+        stats->steps_rejected = (int64_t)hc->steps_rej;
+        stats->steps_root = (int64_t)hc->steps_root;
+        stats->queue_needed = (int64_t)hc->q_tail;
+        stats->waves = n_waves;
+        stats->flags = (int32_t)flags;
+        stats->kernel_ms = ms;
+    }
+    if (flags & (FLAG_OUT_OVERFLOW | FLAG_QUEUE_OVERFLOW | FLAG_HIT_OVERFLOW)) {
+        set_error("rp_trace: overflow (rays %llu / capacity %lld, hits %llu / capacity %lld)",
+                  hc->out_count, (long long)out->capacity, hc->n_hits,
+                  (long long)(hits ? hits->capacity : 0));
+        return RP_ERR_OVERFLOW;
+    }
+    return RP_OK;
+}
+
+}  // namespace rph

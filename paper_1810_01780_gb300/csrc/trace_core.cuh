@@ -1,0 +1,968 @@
+// trace_core.cuh -- device-side core of the ray tracer (sm_103a).
+//
+// One GPU thread owns one ray at a time.  Each loop iteration performs exactly one
+// Cash-Karp step evaluation (the expensive, warp-uniform part) and then a short, divergent
+// state-machine update:
+//   NORMAL  : error control (accept / reject), event detection on the planes of the ray's
+//             layer and on the stop plane, commit of the step
+//   PROBE   : the step started on a plane; first evaluation at h_min
+//   ILLINOIS: modified regula falsi on the step length until the step lands on the plane
+// so that every lane keeps executing the same Runge-Kutta code whatever phase it is in.
+//
+// Method (Sec. 2 of the paper): ray equation Eq. 1 (projected form, default) or Eq. 2
+// (paraxial form), Cash-Karp embedded RK4(5) with step control, the boundary module
+// (reflection, Snell refraction, Fresnel amplitudes, secondary ray from the intersection
+// point), receivers, break conditions (Fig. 1 text).
+//
+// Precision policies:
+//   PrecF64 : everything in FP64.
+//   PrecF32 : Runge-Kutta stages, medium evaluation and error control in FP32; position and
+//             direction accumulated in float-float (hi + lo, ~48-bit significand) on the FP32
+//             pipe; travel time and arc length accumulated in FP64.  Boundary splits are
+//             rare and done in FP64 in both policies.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "rp.h"
+
+namespace rpk {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kInvC0 = 1.0 / 299792458.0;
+constexpr int kRootMaxIter = 40;
+
+// ---------------------------------------------------------------------------------------
+// Cash-Karp (1990) embedded RK4(5) coefficients: nodes c_i, stage matrix a_ij, fifth-order
+// weights b5_i (propagated) and fourth-order weights b4_i (error estimate only).
+// Written as constexpr functions so that fully unrolled loops fold them into immediates.
+// ---------------------------------------------------------------------------------------
+__host__ __device__ constexpr double ck_a(int i, int j)
+{
+    return i == 1   ? (j == 0 ? 1.0 / 5.0 : 0.0)
+           : i == 2 ? (j == 0 ? 3.0 / 40.0 : j == 1 ? 9.0 / 40.0 : 0.0)
+           : i == 3 ? (j == 0 ? 3.0 / 10.0 : j == 1 ? -9.0 / 10.0 : j == 2 ? 6.0 / 5.0 : 0.0)
+           : i == 4 ? (j == 0   ? -11.0 / 54.0
+                       : j == 1 ? 5.0 / 2.0
+                       : j == 2 ? -70.0 / 27.0
+                       : j == 3 ? 35.0 / 27.0
+                                : 0.0)
+           : i == 5 ? (j == 0   ? 1631.0 / 55296.0
+                       : j == 1 ? 175.0 / 512.0
+                       : j == 2 ? 575.0 / 13824.0
+                       : j == 3 ? 44275.0 / 110592.0
+                       : j == 4 ? 253.0 / 4096.0
+                                : 0.0)
+                    : 0.0;
+}
+__host__ __device__ constexpr double ck_b5(int i)
+{
+    return i == 0 ? 37.0 / 378.0 : i == 2 ? 250.0 / 621.0 : i == 3 ? 125.0 / 594.0
+           : i == 5 ? 512.0 / 1771.0 : 0.0;
+}
+__host__ __device__ constexpr double ck_b4(int i)
+{
+    return i == 0   ? 2825.0 / 27648.0
+           : i == 2 ? 18575.0 / 48384.0
+           : i == 3 ? 13525.0 / 55296.0
+           : i == 4 ? 277.0 / 14336.0
+           : i == 5 ? 1.0 / 4.0
+                    : 0.0;
+}
+__host__ __device__ constexpr double ck_db(int i) { return ck_b5(i) - ck_b4(i); }
+
+// ---------------------------------------------------------------------------------------
+// float-float helpers (error-free transformations: Knuth TwoSum, FMA TwoProduct)
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float d)
+{
+    float s, e;
+    two_sum(hi, d, s, e);
+    e = __fadd_rn(e, lo);
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+// A plane offset (or any coordinate constant) in both precisions.
+struct PlaneC {
+    double d;
+    float hi, lo;
+};
+
+// ---------------------------------------------------------------------------------------
+// Precision policies
+// ---------------------------------------------------------------------------------------
+struct PrecF64 {
+    typedef double R;
+    struct V {
+        double v[3];
+    };
+    static constexpr bool kFF = false;
+    __device__ static __forceinline__ R base(const V &a, int i) { return a.v[i]; }
+    __device__ static __forceinline__ void add(V &a, int i, R d) { a.v[i] += d; }
+    __device__ static __forceinline__ double get(const V &a, int i) { return a.v[i]; }
+    __device__ static __forceinline__ void set(V &a, int i, double x) { a.v[i] = x; }
+    // (a_i + delta) - c, evaluated in the order the FP64 reference uses
+    __device__ static __forceinline__ R rel(const V &a, int i, R delta, const PlaneC &c)
+    {
+        return (a.v[i] + delta) - c.d;
+    }
+    __device__ static __forceinline__ void snap(V &a, int i, const PlaneC &c) { a.v[i] = c.d; }
+    __device__ static __forceinline__ R from_d(double x) { return x; }
+    __device__ static __forceinline__ R rcp(R x) { return 1.0 / x; }
+    __device__ static __forceinline__ R exp_(R x) { return exp(x); }
+    __device__ static __forceinline__ R sqrt_(R x) { return sqrt(x); }
+    __device__ static __forceinline__ R pow_(R x, R y) { return pow(x, y); }
+    __device__ static __forceinline__ R c(double x) { return x; }
+};
+
+struct PrecF32 {
+    typedef float R;
+    struct V {
+        float hi[3], lo[3];
+    };
+    static constexpr bool kFF = true;
+    __device__ static __forceinline__ R base(const V &a, int i) { return a.hi[i]; }
+    __device__ static __forceinline__ void add(V &a, int i, R d) { ff_add(a.hi[i], a.lo[i], d); }
+    __device__ static __forceinline__ double get(const V &a, int i)
+    {
+        return (double)a.hi[i] + (double)a.lo[i];
+    }
+    __device__ static __forceinline__ void set(V &a, int i, double x)
+    {
+        a.hi[i] = __double2float_rn(x);
+        a.lo[i] = __double2float_rn(x - (double)a.hi[i]);
+    }
+    __device__ static __forceinline__ R rel(const V &a, int i, R delta, const PlaneC &c)
+    {
+        // hi - c.hi is exact near the plane (Sterbenz); the small terms follow
+        return __fadd_rn(__fadd_rn(__fsub_rn(a.hi[i], c.hi), delta), __fsub_rn(a.lo[i], c.lo));
+    }
+    __device__ static __forceinline__ void snap(V &a, int i, const PlaneC &c)
+    {
+        a.hi[i] = c.hi;
+        a.lo[i] = c.lo;
+    }
+    __device__ static __forceinline__ R from_d(double x) { return __double2float_rn(x); }
+    __device__ static __forceinline__ R rcp(R x) { return __frcp_rn(x); }
+    __device__ static __forceinline__ R exp_(R x) { return expf(x); }
+    __device__ static __forceinline__ R sqrt_(R x) { return sqrtf(x); }
+    __device__ static __forceinline__ R pow_(R x, R y) { return exp2f(y * __log2f(x)); }
+    __device__ static __forceinline__ R c(double x) { return (float)x; }
+};
+
+// ---------------------------------------------------------------------------------------
+// Media
+// ---------------------------------------------------------------------------------------
+struct LayerC {
+    double n0, dn, off, inv_z0, gcoef;  // n = n0 - dn e + off, dn/dz = gcoef e, e = exp(-z/z0)
+    float n0f, dnf, offf, inv_z0f, gcoeff;
+    int32_t absorb, has_exp;
+};
+
+struct MediumLayered {
+    int32_t n_layers, pad;
+    LayerC L[RP_MAX_LAYERS];
+    PlaneC top[RP_MAX_LAYERS];  // top[k]: plane z = z_top of layer k (k >= 1)
+};
+
+struct MediumGrid {
+    const float4 *__restrict__ g;  // (n, dn/dx, dn/dy, dn/dz) node samples, x fastest
+    int32_t nx, ny, nz, pad;
+    double org[3], inv_sp, hi[3];
+    float orgf[3], inv_spf;
+};
+
+template <class M>
+constexpr bool is_layered_v = std::is_same<M, MediumLayered>::value;
+
+__device__ __forceinline__ int layer_of(const MediumLayered &m, double z)
+{
+    int k = 0;
+    for (int j = 1; j < m.n_layers; ++j)
+        if (z >= m.top[j].d) k = j;
+    return k;
+}
+
+// n(z) and dn/dz of layer k in FP64 (used by the boundary split in both policies).
+__device__ __forceinline__ void layer_eval_d(const MediumLayered &m, int k, double z, double &n,
+                                             double &dndz)
+{
+    const LayerC &L = m.L[k];
+    if (!L.has_exp) {
+        n = L.n0 + L.off;
+        dndz = 0.0;
+        return;
+    }
+    double e = exp(-z * L.inv_z0);
+    n = L.n0 - L.dn * e + L.off;
+    dndz = L.gcoef * e;
+}
+
+// Layered analytic medium: only the stage depth matters.
+template <class P>
+__device__ __forceinline__ void medium_eval(const MediumLayered &m, int layer,
+                                            const typename P::R r[3], typename P::R &n,
+                                            typename P::R g[3])
+{
+    typedef typename P::R R;
+    const LayerC &L = m.L[layer];
+    g[0] = R(0);
+    g[1] = R(0);
+    if (!L.has_exp) {
+        n = P::kFF ? R(L.n0f + L.offf) : R(L.n0 + L.off);
+        g[2] = R(0);
+        return;
+    }
+    if constexpr (P::kFF) {
+        float e = expf(-r[2] * L.inv_z0f);
+        n = __fadd_rn(__fmaf_rn(-L.dnf, e, L.n0f), L.offf);
+        g[2] = L.gcoeff * e;
+    } else {
+        double e = exp(-r[2] * L.inv_z0);
+        n = L.n0 - L.dn * e + L.off;
+        g[2] = L.gcoef * e;
+    }
+}
+
+// Gridded medium: trilinear interpolation of the four FP32 node channels, clamped to the box.
+template <class P>
+__device__ __forceinline__ void medium_eval(const MediumGrid &m, int /*layer*/,
+                                            const typename P::R r[3], typename P::R &n,
+                                            typename P::R g[3])
+{
+    typedef typename P::R R;
+    const int dims[3] = {m.nx, m.ny, m.nz};
+    int idx[3];
+    R w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R f;
+        if constexpr (P::kFF)
+            f = (r[a] - m.orgf[a]) * m.inv_spf;
+        else
+            f = (r[a] - m.org[a]) * m.inv_sp;
+        const R top = R(dims[a] - 1);
+        f = fmax(f, R(0));  // also maps NaN to 0: the index below always stays in the box
+        f = fmin(f, top);
+        int i = (int)floor(f);
+        if (i < 0) i = 0;
+        if (i > dims[a] - 2) i = dims[a] - 2;
+        idx[a] = i;
+        w[a] = f - R(i);
+    }
+    const size_t sx = 1, sy = (size_t)m.nx, sz = (size_t)m.nx * (size_t)m.ny;
+    const size_t b = (size_t)idx[2] * sz + (size_t)idx[1] * sy + (size_t)idx[0];
+    float4 c[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const size_t o = b + ((q >> 2) & 1) * sz + ((q >> 1) & 1) * sy + (q & 1) * sx;
+        c[q] = __ldg(&m.g[o]);
+    }
+    R v[4];
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+        R e[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {  // q = 2 dz + dy
+            float a0 = ch == 0 ? c[2 * q].x : ch == 1 ? c[2 * q].y : ch == 2 ? c[2 * q].z : c[2 * q].w;
+            float a1 = ch == 0   ? c[2 * q + 1].x
+                       : ch == 1 ? c[2 * q + 1].y
+                       : ch == 2 ? c[2 * q + 1].z
+                                 : c[2 * q + 1].w;
+            e[q] = R(a0) + w[0] * (R(a1) - R(a0));
+        }
+        R f0 = e[0] + w[1] * (e[1] - e[0]);
+        R f1 = e[2] + w[1] * (e[3] - e[2]);
+        v[ch] = f0 + w[2] * (f1 - f0);
+    }
+    n = v[0];
+    g[0] = v[1];
+    g[1] = v[2];
+    g[2] = v[3];
+}
+
+// ---------------------------------------------------------------------------------------
+// One Cash-Karp step of the ray system from (r0, t0) with step h.
+//   y = (r, t, T);  r' = t;  t' = (g - (g.t) t)/n  [projected]  or  g/n  [paraxial];
+//   T' = n / c0.
+// Outputs the fifth-order increments dr, dt, dT and the error measures
+//   er = |sum_i (b5_i - b4_i) k_r,i|,   et = h |sum_i (b5_i - b4_i) k_t,i|.
+// Sums run over the stages in ascending order, as in the FP64 reference.
+// ---------------------------------------------------------------------------------------
+template <class P, class M>
+__device__ __forceinline__ void ck_step(const M &med, int layer, int form,
+                                        const typename P::V &r0, const typename P::V &t0v,
+                                        typename P::R h, typename P::R dr[3],
+                                        typename P::R dt[3], typename P::R &dT,
+                                        typename P::R &er, typename P::R &et)
+{
+    typedef typename P::R R;
+    R t0[3] = {P::base(t0v, 0), P::base(t0v, 1), P::base(t0v, 2)};
+    R ts[6][3], kt[6][3];
+    R sr[3] = {R(0), R(0), R(0)}, st[3] = {R(0), R(0), R(0)}, sT = R(0);
+    R dr_e[3] = {R(0), R(0), R(0)}, dt_e[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        R rs[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            R ar = R(0), at = R(0);
+#pragma unroll
+            for (int j = 0; j < i; ++j) {
+                ar += P::c(ck_a(i, j)) * ts[j][c];
+                at += P::c(ck_a(i, j)) * kt[j][c];
+            }
+            rs[c] = P::base(r0, c) + h * ar;
+            ts[i][c] = t0[c] + h * at;
+        }
+        R n, g[3];
+        medium_eval<P>(med, layer, rs, n, g);
+        R inv_n = P::rcp(n);
+        if (form == RP_RHS_PROJECTED) {
+            R gt = g[0] * ts[i][0] + g[1] * ts[i][1] + g[2] * ts[i][2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) kt[i][c] = (g[c] - gt * ts[i][c]) * inv_n;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) kt[i][c] = g[c] * inv_n;
+        }
+        if (ck_b5(i) != 0.0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                sr[c] += P::c(ck_b5(i)) * ts[i][c];
+                st[c] += P::c(ck_b5(i)) * kt[i][c];
+            }
+            sT += P::c(ck_b5(i)) * n;
+        }
+        if (ck_db(i) != 0.0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dr_e[c] += P::c(ck_db(i)) * ts[i][c];
+                dt_e[c] += P::c(ck_db(i)) * kt[i][c];
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        dr[c] = h * sr[c];
+        dt[c] = h * st[c];
+    }
+    dT = h * (sT * P::c(kInvC0));
+    er = P::sqrt_(dr_e[0] * dr_e[0] + dr_e[1] * dr_e[1] + dr_e[2] * dr_e[2]);
+    et = h * P::sqrt_(dt_e[0] * dt_e[0] + dt_e[1] * dt_e[1] + dt_e[2] * dt_e[2]);
+}
+
+// ---------------------------------------------------------------------------------------
+// Boundary module in FP64 (Sec. 2): reflection, Snell refraction, Fresnel amplitudes.
+// nrm points toward the incident side.  Returns tir.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void normalise3(double v[3])
+{
+    double q = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] /= q;
+    v[1] /= q;
+    v[2] /= q;
+}
+
+__device__ __forceinline__ bool split_dirs(const double t[3], const double nrm[3], double n1,
+                                           double n2, int pol, double t_refl[3],
+                                           double t_refr[3], double &r, double &tau)
+{
+    double cos_i = -(t[0] * nrm[0] + t[1] * nrm[1] + t[2] * nrm[2]);
+    if (cos_i < 0.0) cos_i = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) t_refl[a] = t[a] + 2.0 * cos_i * nrm[a];
+    normalise3(t_refl);
+    double eta = n1 / n2;
+    double sin2_t = eta * eta * (1.0 - cos_i * cos_i);
+    if (sin2_t > 1.0) {
+        r = 1.0;  // total internal reflection: |r| = 1, phase not tracked
+        tau = 0.0;
+        return true;
+    }
+    double cos_t = sqrt(1.0 - sin2_t);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) t_refr[a] = eta * t[a] + (eta * cos_i - cos_t) * nrm[a];
+    normalise3(t_refr);
+    double rs = (n1 * cos_i - n2 * cos_t) / (n1 * cos_i + n2 * cos_t);
+    double ts = 2.0 * n1 * cos_i / (n1 * cos_i + n2 * cos_t);
+    double rp = (n2 * cos_i - n1 * cos_t) / (n2 * cos_i + n1 * cos_t);
+    double tp = 2.0 * n1 * cos_i / (n2 * cos_i + n1 * cos_t);
+    if (pol == RP_POL_S) {
+        r = rs;
+        tau = ts;
+    } else if (pol == RP_POL_P) {
+        r = rp;
+        tau = tp;
+    } else {
+        double Rr = 0.5 * (rs * rs + rp * rp);
+        r = sqrt(Rr);
+        tau = sqrt(1.0 - Rr);
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------------------
+// Receivers: spheres sorted by centre depth; a chord is tested against the spheres whose
+// depth slab it overlaps.
+// ---------------------------------------------------------------------------------------
+struct SphereC {
+    PlaneC c[3];
+    double R;
+    float Rf;
+    int32_t idx;
+};
+
+struct Receivers {
+    const SphereC *__restrict__ s;
+    const float *__restrict__ cz;  // sorted centre depths
+    int32_t n;
+    float r_max;
+};
+
+// ---------------------------------------------------------------------------------------
+// Per-call device control block (counters live in device memory, zeroed per call)
+// ---------------------------------------------------------------------------------------
+struct Ctrl {
+    unsigned long long claim[RP_MAX_LAYERS + 8];
+    unsigned long long seg_begin[RP_MAX_LAYERS + 8], seg_end[RP_MAX_LAYERS + 8];
+    unsigned long long out_count, q_tail, n_hits, n_secondary;
+    unsigned long long steps_acc, steps_rej, steps_root;
+    unsigned int flags, pad;
+};
+
+enum { FLAG_BAD_INPUT = 1, FLAG_OUT_OVERFLOW = 2, FLAG_QUEUE_OVERFLOW = 4,
+       FLAG_HIT_OVERFLOW = 8, FLAG_ROOT_CAP = 16 };
+
+// Queued secondary ray (start state).
+struct QRec {
+    double r[3], t[3];
+    double T, s, A, A0;
+    double h;
+    long long id, parent;
+    int32_t layer, gen, seq, pad;
+};
+
+// ---------------------------------------------------------------------------------------
+// Lane state
+// ---------------------------------------------------------------------------------------
+enum { MODE_NORMAL = 0, MODE_PROBE = 1, MODE_ILLINOIS = 2 };
+enum { EV_NONE = 0, EV_TOP = 1, EV_BOTTOM = 2, EV_STOP = 3 };
+
+template <class P>
+struct Lane {
+    typedef typename P::R R;
+    typename P::V r, t;
+    double T, s, A, A0;
+    R h, h_next, h_try;
+    R ra, rb, ga, gb;  // root bracket
+    PlaneC stop;       // stop plane offset along stop_axis
+    R stop_sign;
+    long long id, parent;
+    int32_t mode, ev, side, it, last;
+    int32_t layer, gen, seq, nsplit;
+    int32_t n_acc, n_rej, n_root, n_refl, n_turn, root_fail;
+    int32_t status;
+};
+
+// Parameters shared by every lane of a launch.
+template <class P>
+struct StepParams {
+    typedef typename P::R R;
+    R tol, h_min, h_max, eps_b;
+    double max_path, max_time, min_amp;
+    int32_t rhs_form, polarization, max_generation, use_stop;
+    int32_t stop_axis;  // 0, 1, 2 (the stop normal is +/- a coordinate axis)
+    float stop_dir;     // +1 or -1: sign of the normal along stop_axis
+    long long max_steps;
+};
+
+// Offset of the candidate r + dr from the stop plane along the stop axis (selected without
+// dynamic indexing so that the state stays in registers).
+template <class P>
+__device__ __forceinline__ typename P::R stop_rel(const Lane<P> &L, const StepParams<P> &sp,
+                                                  const typename P::R dr[3])
+{
+    return sp.stop_axis == 0   ? P::rel(L.r, 0, dr[0], L.stop)
+           : sp.stop_axis == 1 ? P::rel(L.r, 1, dr[1], L.stop)
+                               : P::rel(L.r, 2, dr[2], L.stop);
+}
+
+template <class P>
+__device__ __forceinline__ void set_trial(Lane<P> &L, const StepParams<P> &sp)
+{
+    typedef typename P::R R;
+    L.last = 0;
+    double rem = sp.max_path - L.s;
+    if (L.s + (double)L.h >= sp.max_path) {
+        L.h_try = P::from_d(rem);
+        L.last = 1;
+    } else {
+        L.h_try = L.h;
+    }
+    L.mode = MODE_NORMAL;
+}
+
+// Signed distance to an event plane for the candidate state r + dr (positive on the ray's
+// own side).
+template <class P>
+__device__ __forceinline__ typename P::R event_g(const MediumLayered &m, const Lane<P> &L,
+                                                 const StepParams<P> &sp, int kind,
+                                                 const typename P::R dr[3])
+{
+    typedef typename P::R R;
+    if (kind == EV_TOP) return P::rel(L.r, 2, dr[2], m.top[L.layer]);
+    if (kind == EV_BOTTOM) return -P::rel(L.r, 2, dr[2], m.top[L.layer + 1]);
+    return L.stop_sign * (R(sp.stop_dir) * stop_rel(L, sp, dr));
+}
+template <class P>
+__device__ __forceinline__ typename P::R event_g(const MediumGrid &, const Lane<P> &L,
+                                                 const StepParams<P> &sp, int,
+                                                 const typename P::R dr[3])
+{
+    typedef typename P::R R;
+    return L.stop_sign * (R(sp.stop_dir) * stop_rel(L, sp, dr));
+}
+
+__device__ __forceinline__ bool is_layered(const MediumLayered &) { return true; }
+__device__ __forceinline__ bool is_layered(const MediumGrid &) { return false; }
+__device__ __forceinline__ int n_layers(const MediumLayered &m) { return m.n_layers; }
+__device__ __forceinline__ int n_layers(const MediumGrid &) { return 1; }
+
+// Stop-plane side sign at the start of a ray: positive side is where the ray starts.
+template <class P>
+__device__ __forceinline__ void init_stop(Lane<P> &L, const StepParams<P> &sp)
+{
+    typedef typename P::R R;
+    if (sp.use_stop) {
+        const R zero[3] = {R(0), R(0), R(0)};
+        R f = R(sp.stop_dir) * stop_rel(L, sp, zero);
+        L.stop_sign = (f <= R(0)) ? R(-1) : R(1);
+    } else {
+        L.stop_sign = R(1);
+    }
+}
+
+// Hooks the kernels provide: where a secondary goes and what a receiver hit writes.
+struct Sinks {
+    Ctrl *ctrl;
+    QRec *queue;
+    unsigned long long q_cap;
+    // output arrays for rays recorded directly (transmitted into absorbing layers)
+    rp_ray_out out;
+    // hits
+    rp_hits hits;
+    Receivers rx;
+    int32_t has_rx;
+};
+
+// Writes one finished ray record.
+template <class P>
+__device__ __forceinline__ void write_ray(const rp_ray_out &o, long long id, const Lane<P> &L,
+                                          Ctrl *ctrl)
+{
+    if (id >= o.capacity) {
+        atomicOr(&ctrl->flags, (unsigned)FLAG_OUT_OVERFLOW);
+        return;
+    }
+    const long long cap = o.capacity;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) o.end_pos[a * cap + id] = P::get(L.r, a);
+    if (o.end_dir) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) o.end_dir[a * cap + id] = P::get(L.t, a);
+    }
+    if (o.path) o.path[id] = L.s;
+    if (o.time) o.time[id] = L.T;
+    if (o.amp) o.amp[id] = L.A;
+    if (o.status) o.status[id] = L.status;
+    if (o.generation) o.generation[id] = L.gen;
+    if (o.seq) o.seq[id] = L.seq;
+    if (o.layer) o.layer[id] = L.layer;
+    if (o.parent) o.parent[id] = L.parent;
+    if (o.n_acc) o.n_acc[id] = L.n_acc;
+    if (o.n_rej) o.n_rej[id] = L.n_rej;
+    if (o.n_root) o.n_root[id] = L.n_root;
+    if (o.n_refl) o.n_refl[id] = L.n_refl;
+    if (o.n_turn) o.n_turn[id] = L.n_turn;
+}
+
+// Receiver test on the committed chord (state L before the commit -> r1 = r + dr).
+template <class P>
+__device__ void receivers_on_chord(const Sinks &sk, const Lane<P> &L, const typename P::R dr[3],
+                                   const typename P::R dt[3], double T1, double s1)
+{
+    typedef typename P::R R;
+    const Receivers &rx = sk.rx;
+    double z0 = P::get(L.r, 2);
+    float za = (float)z0, zb = (float)(z0 + (double)dr[2]);
+    float zlo = fminf(za, zb) - rx.r_max - 1e-3f * (1.0f + fabsf(za));
+    float zhi = fmaxf(za, zb) + rx.r_max + 1e-3f * (1.0f + fabsf(za));
+    // first sphere with centre depth >= zlo
+    int lo = 0, hi = rx.n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(&rx.cz[mid]) < zlo)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    const R zero = R(0);
+    for (int j = lo; j < rx.n && __ldg(&rx.cz[j]) <= zhi; ++j) {
+        const SphereC &S = rx.s[j];
+        R w[3], d[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            w[a] = P::rel(L.r, a, zero, S.c[a]);  // r0 - c
+            R w1 = P::rel(L.r, a, dr[a], S.c[a]);  // r1 - c
+            d[a] = P::kFF ? (w1 - w[a]) : dr[a];
+        }
+        R Rs = P::kFF ? R(S.Rf) : R(S.R);
+        R qa = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        R qb = R(2) * (d[0] * w[0] + d[1] * w[1] + d[2] * w[2]);
+        R qc = w[0] * w[0] + w[1] * w[1] + w[2] * w[2] - Rs * Rs;
+        if (qc <= R(0) || qa == R(0)) continue;
+        R disc = qb * qb - R(4) * qa * qc;
+        if (disc < R(0)) continue;
+        R lam = (-qb - P::sqrt_(disc)) / (R(2) * qa);
+        if (lam < R(0) || lam > R(1)) continue;
+        unsigned long long k = atomicAdd(&sk.ctrl->n_hits, 1ull);
+        if (k >= (unsigned long long)sk.hits.capacity) {
+            atomicOr(&sk.ctrl->flags, (unsigned)FLAG_HIT_OVERFLOW);
+            continue;
+        }
+        const long long cap = sk.hits.capacity;
+        const double l = (double)lam;
+        if (sk.hits.ray) sk.hits.ray[k] = L.id;
+        if (sk.hits.receiver) sk.hits.receiver[k] = S.idx;
+        if (sk.hits.time) sk.hits.time[k] = L.T + l * (T1 - L.T);
+        if (sk.hits.path) sk.hits.path[k] = L.s + l * (s1 - L.s);
+        if (sk.hits.amp) sk.hits.amp[k] = L.A;
+        double dir[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double r0 = P::get(L.r, a);
+            if (sk.hits.pos) sk.hits.pos[a * cap + k] = r0 + l * (double)d[a];
+            double t0 = P::get(L.t, a);
+            double t1 = t0 + (double)dt[a];
+            dir[a] = t0 + l * (t1 - t0);
+        }
+        if (sk.hits.dir) {
+            normalise3(dir);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) sk.hits.dir[a * cap + k] = dir[a];
+        }
+    }
+}
+
+// Float-float renormalisation of a direction whose norm is 1 + delta (paraxial form).
+__device__ __forceinline__ void ff_renormalise(PrecF32::V &t)
+{
+    float S = 0.0f, E = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float p = t.hi[a] * t.hi[a];
+        float e = __fmaf_rn(t.hi[a], t.hi[a], -p);
+        float s, e2;
+        two_sum(S, p, s, e2);
+        S = s;
+        E += e + e2 + 2.0f * t.hi[a] * t.lo[a];
+    }
+    float delta = (S - 1.0f) + E;  // |t|^2 - 1
+    float q = sqrtf(1.0f + delta);
+    float phi = -delta / (q * (1.0f + q));  // 1/|t| - 1
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ff_add(t.hi[a], t.lo[a], t.hi[a] * phi);
+}
+
+// Commit of the candidate state (r + dr, t + dt, T + dT) after a step of length hc; ev is the
+// event the step landed on (EV_NONE: an ordinary accepted step).  Performs receivers, split,
+// stop and break conditions.  Returns true if the ray finished.
+template <class P, class M>
+__device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParams<P> &sp,
+                                       const Sinks &sk, typename P::R hc,
+                                       const typename P::R dr_in[3], const typename P::R dt[3],
+                                       typename P::R dT, int ev)
+{
+    typedef typename P::R R;
+    R dr[3] = {dr_in[0], dr_in[1], dr_in[2]};
+    // landing: move the candidate onto the plane by adjusting the increment
+    if (ev == EV_TOP || ev == EV_BOTTOM) {
+        if constexpr (is_layered_v<M>) {
+            const PlaneC &pl = (ev == EV_TOP) ? med.top[L.layer] : med.top[L.layer + 1];
+            dr[2] = dr[2] - P::rel(L.r, 2, dr[2], pl);
+        }
+    } else if (ev == EV_STOP) {
+        const R off = stop_rel(L, sp, dr);
+        if (sp.stop_axis == 0)
+            dr[0] -= off;
+        else if (sp.stop_axis == 1)
+            dr[1] -= off;
+        else
+            dr[2] -= off;
+    }
+    const double T1 = L.T + (double)dT;
+    const double s1 = (L.last && ev == EV_NONE) ? sp.max_path : L.s + (double)hc;
+    if (sk.has_rx) receivers_on_chord<P>(sk, L, dr, dt, T1, s1);
+    {
+        R tz1 = P::base(L.t, 2) + dt[2];
+        if ((P::base(L.t, 2) > R(0)) != (tz1 > R(0))) ++L.n_turn;
+    }
+    // apply
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        P::add(L.r, a, dr[a]);
+        P::add(L.t, a, dt[a]);
+    }
+    if (ev == EV_TOP || ev == EV_BOTTOM) {
+        if constexpr (is_layered_v<M>) {
+            P::snap(L.r, 2, (ev == EV_TOP) ? med.top[L.layer] : med.top[L.layer + 1]);
+        }
+    } else if (ev == EV_STOP) {
+        if (sp.stop_axis == 0)
+            P::snap(L.r, 0, L.stop);
+        else if (sp.stop_axis == 1)
+            P::snap(L.r, 1, L.stop);
+        else
+            P::snap(L.r, 2, L.stop);
+    }
+    if constexpr (P::kFF) {
+        if (sp.rhs_form == RP_RHS_PARAXIAL) ff_renormalise(L.t);
+    } else {
+        double q = sqrt(L.t.v[0] * L.t.v[0] + L.t.v[1] * L.t.v[1] + L.t.v[2] * L.t.v[2]);
+        L.t.v[0] /= q;
+        L.t.v[1] /= q;
+        L.t.v[2] /= q;
+    }
+    L.T = T1;
+    L.s = s1;
+    ++L.n_acc;
+    L.h = L.h_next;
+
+    if (ev == EV_TOP || ev == EV_BOTTOM) {
+        if constexpr (is_layered_v<M>) {
+            const int other = (ev == EV_TOP) ? L.layer - 1 : L.layer + 1;
+            const double zb = P::get(L.r, 2);
+            double n1, n2, dd;
+            layer_eval_d(med, L.layer, zb, n1, dd);
+            layer_eval_d(med, other, zb, n2, dd);
+            const double nrm[3] = {0.0, 0.0, (ev == EV_TOP) ? 1.0 : -1.0};
+            double t[3] = {P::get(L.t, 0), P::get(L.t, 1), P::get(L.t, 2)};
+            double t_refl[3], t_refr[3], rr, tau;
+            bool tir = split_dirs(t, nrm, n1, n2, sp.polarization, t_refl, t_refr, rr, tau);
+            if (!tir && L.gen < sp.max_generation) {
+                const unsigned long long id = atomicAdd(&sk.ctrl->out_count, 1ull);
+                atomicAdd(&sk.ctrl->n_secondary, 1ull);
+                if (med.L[other].absorb) {
+                    // refracted into an absorbing layer: recorded, not traced
+                    Lane<P> S = L;
+                    S.id = (long long)id;
+                    S.parent = L.id;
+                    S.seq = L.nsplit;
+                    S.gen = L.gen + 1;
+                    S.layer = other;
+                    S.A = L.A * tau;
+                    S.status = RP_ST_TRANSMITTED;
+                    S.n_acc = S.n_rej = S.n_root = S.n_refl = S.n_turn = 0;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) P::set(S.t, a, t_refr[a]);
+                    write_ray<P>(sk.out, S.id, S, sk.ctrl);
+                } else {
+                    const unsigned long long q = atomicAdd(&sk.ctrl->q_tail, 1ull);
+                    if (q < sk.q_cap) {
+                        QRec &Q = sk.queue[q];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            Q.r[a] = P::get(L.r, a);
+                            Q.t[a] = t_refr[a];
+                        }
+                        Q.T = L.T;
+                        Q.s = L.s;
+                        Q.A = L.A * tau;
+                        Q.A0 = L.A0;
+                        Q.id = (long long)id;
+                        Q.parent = L.id;
+                        Q.h = (double)L.h;
+                        Q.layer = other;
+                        Q.gen = L.gen + 1;
+                        Q.seq = L.nsplit;
+                    } else {
+                        atomicOr(&sk.ctrl->flags, (unsigned)FLAG_QUEUE_OVERFLOW);
+                        Lane<P> S = L;
+                        S.id = (long long)id;
+                        S.parent = L.id;
+                        S.seq = L.nsplit;
+                        S.gen = L.gen + 1;
+                        S.layer = other;
+                        S.A = L.A * tau;
+                        S.status = RP_ST_QUEUE_FULL;
+                        S.n_acc = S.n_rej = S.n_root = S.n_refl = S.n_turn = 0;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) P::set(S.t, a, t_refr[a]);
+                        write_ray<P>(sk.out, S.id, S, sk.ctrl);
+                    }
+                }
+            }
+            ++L.nsplit;
+            ++L.n_refl;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) P::set(L.t, a, t_refl[a]);
+            L.A *= rr;
+        }
+    } else if (ev == EV_STOP) {
+        L.status = RP_ST_REACHED_STOP;
+        return true;
+    }
+    if (L.last && ev == EV_NONE) {
+        L.status = RP_ST_MAX_PATH;
+    } else if (sp.max_time > 0.0 && L.T >= sp.max_time) {
+        L.status = RP_ST_MAX_TIME;
+    } else if (sp.min_amp > 0.0 && fabs(L.A) < sp.min_amp * fabs(L.A0)) {
+        L.status = RP_ST_MIN_AMP;
+    } else if constexpr (!is_layered_v<M>) {
+        bool inside = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double v = P::get(L.r, a);
+            inside = inside && !(v < med.org[a] || v > med.hi[a]);
+        }
+        if (!inside) L.status = RP_ST_LEFT_DOMAIN;
+    }
+    if (L.status != RP_ST_ALIVE) return true;
+    set_trial(L, sp);
+    return false;
+}
+
+// Regula-falsi point of the current bracket (bisection if it falls outside).
+template <class P>
+__device__ __forceinline__ typename P::R rf_point(const Lane<P> &L)
+{
+    typedef typename P::R R;
+    R c = L.rb - L.gb * (L.rb - L.ra) / (L.gb - L.ga);
+    if (!(c > L.ra && c < L.rb)) c = R(0.5) * (L.ra + L.rb);
+    return c;
+}
+
+// One iteration of a lane: one Cash-Karp evaluation and the state-machine update.
+// Returns true when the ray has finished (L.status set).
+template <class P, class M>
+__device__ __forceinline__ bool advance(const M &med, Lane<P> &L, const StepParams<P> &sp,
+                                        const Sinks &sk)
+{
+    typedef typename P::R R;
+    if (L.mode == MODE_NORMAL && (long long)L.n_acc + L.n_rej + L.n_root >= sp.max_steps) {
+        L.status = RP_ST_MAX_STEPS;
+        return true;
+    }
+    const R hc = L.h_try;
+    R dr[3], dt[3], dT, er, et;
+    ck_step<P, M>(med, L.layer, sp.rhs_form, L.r, L.t, hc, dr, dt, dT, er, et);
+
+    if (L.mode == MODE_NORMAL) {
+        const R e = (er > et ? er : et) / sp.tol;
+        if (!(e <= R(1)) && hc > sp.h_min) {
+            ++L.n_rej;
+            R fac = R(0.9) * P::pow_(e, R(-0.25));
+            if (!(fac >= R(0.1))) fac = R(0.1);
+            R hn = hc * fac;
+            L.h = hn < sp.h_min ? sp.h_min : hn;
+            set_trial(L, sp);
+            return false;
+        }
+        R grow = (e == R(0)) ? R(5) : R(0.9) * P::pow_(e, R(-0.2));
+        if (grow > R(5)) grow = R(5);
+        R hn = hc * grow;
+        hn = hn < sp.h_min ? sp.h_min : hn;
+        hn = hn > sp.h_max ? sp.h_max : hn;
+        L.h_next = hn;
+
+        // event detection: earliest crossed plane by linear fraction
+        int ev = EV_NONE;
+        R ev_frac = R(2), ev_g0 = R(0), ev_g1 = R(0);
+        const R zero3[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int kind = EV_TOP; kind <= EV_STOP; ++kind) {
+            if (kind == EV_TOP && !(is_layered(med) && L.layer > 0)) continue;
+            if (kind == EV_BOTTOM && !(is_layered(med) && L.layer < n_layers(med) - 1)) continue;
+            if (kind == EV_STOP && !sp.use_stop) continue;
+            R g0 = event_g<P>(med, L, sp, kind, zero3);
+            R g1 = event_g<P>(med, L, sp, kind, dr);
+            if (g1 < R(0) || (g1 <= sp.eps_b && g0 > sp.eps_b)) {
+                R fr = (g0 > R(0)) ? g0 / (g0 - g1) : R(0);
+                if (fr < ev_frac) {
+                    ev = kind;
+                    ev_frac = fr;
+                    ev_g0 = g0;
+                    ev_g1 = g1;
+                }
+            }
+        }
+        if (ev == EV_NONE) return commit<P, M>(med, L, sp, sk, hc, dr, dt, dT, EV_NONE);
+        L.ev = ev;
+        if (fabs(ev_g1) <= sp.eps_b) return commit<P, M>(med, L, sp, sk, hc, dr, dt, dT, ev);
+        if (ev_g0 <= sp.eps_b) {
+            if (hc <= sp.h_min) return commit<P, M>(med, L, sp, sk, hc, dr, dt, dT, ev);
+            L.mode = MODE_PROBE;
+            L.rb = hc;
+            L.gb = ev_g1;
+            L.h_try = sp.h_min;
+            return false;
+        }
+        L.mode = MODE_ILLINOIS;
+        L.ra = R(0);
+        L.ga = ev_g0;
+        L.rb = hc;
+        L.gb = ev_g1;
+        L.side = 0;
+        L.it = 1;
+        L.h_try = rf_point(L);
+        return false;
+    }
+
+    // root-search evaluation at hc
+    ++L.n_root;
+    const R gc = event_g<P>(med, L, sp, L.ev, dr);
+    if (L.mode == MODE_PROBE) {
+        if (gc <= sp.eps_b) return commit<P, M>(med, L, sp, sk, hc, dr, dt, dT, L.ev);
+        L.ra = hc;
+        L.ga = gc;
+        L.mode = MODE_ILLINOIS;
+        L.side = 0;
+        L.it = 1;
+        L.h_try = rf_point(L);
+        return false;
+    }
+    if (fabs(gc) <= sp.eps_b) return commit<P, M>(med, L, sp, sk, hc, dr, dt, dT, L.ev);
+    if (gc > R(0)) {
+        L.ra = hc;
+        L.ga = gc;
+        if (L.side == 1) L.gb *= R(0.5);
+        L.side = 1;
+    } else {
+        L.rb = hc;
+        L.gb = gc;
+        if (L.side == -1) L.ga *= R(0.5);
+        L.side = -1;
+    }
+    if (L.it == kRootMaxIter) {
+        L.root_fail = 1;
+        atomicOr(&sk.ctrl->flags, (unsigned)FLAG_ROOT_CAP);
+        return commit<P, M>(med, L, sp, sk, hc, dr, dt, dT, L.ev);
+    }
+    ++L.it;
+    L.h_try = rf_point(L);
+    return false;
+}
+
+}  // namespace rpk

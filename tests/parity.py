@@ -1,0 +1,84 @@
+"""Helpers for comparing CUDA-path outputs with the oracle (test infrastructure).
+
+Secondary rays are created in a non-deterministic order on the GPU, so rays are matched by
+their position in the split tree: a primary is keyed by its index, a secondary by its
+parent's key plus the index of the split on the parent that cast it."""
+from __future__ import annotations
+
+import numpy as np
+
+
+def gpu_rays(res) -> dict:
+    r = res["rays"]
+    out = {
+        "pos": r["end_pos"].cpu().numpy().T.copy(),
+        "dir": r["end_dir"].cpu().numpy().T.copy(),
+    }
+    for k in ("path", "time", "amp", "status", "generation", "seq", "layer", "parent", "n_acc",
+              "n_rej", "n_root", "n_refl", "n_turn"):
+        out[k] = r[k].cpu().numpy()
+    return out
+
+
+def oracle_rays(rays) -> dict:
+    return {
+        "pos": rays["pos"], "dir": rays["dir"], "path": rays["path"], "time": rays["time"],
+        "amp": rays["amp"], "status": rays["status"], "generation": rays["gen"],
+        "seq": rays["seq"], "layer": rays["layer"], "parent": rays["parent"],
+        "n_acc": rays["n_acc"], "n_rej": rays["n_rej"], "n_root": rays["n_root"],
+        "n_refl": rays["n_refl"], "n_turn": rays["n_turn"],
+    }
+
+
+def tree_keys(parent, seq):
+    """Key of every ray; a parent always has a smaller index than its secondaries."""
+    keys = []
+    for i in range(len(parent)):
+        p = int(parent[i])
+        if p < 0:
+            keys.append((i,))
+        else:
+            assert p < i, (i, p)
+            keys.append(keys[p] + (int(seq[i]),))
+    return keys
+
+
+def match(g: dict, o: dict):
+    """Index arrays (gi, oi) of rays present in both, plus the unmatched key sets."""
+    kg = tree_keys(g["parent"], g["seq"])
+    ko = tree_keys(o["parent"], o["seq"])
+    mo = {k: i for i, k in enumerate(ko)}
+    gi, oi, only_g = [], [], []
+    for i, k in enumerate(kg):
+        j = mo.pop(k, None)
+        if j is None:
+            only_g.append(k)
+        else:
+            gi.append(i)
+            oi.append(j)
+    return np.array(gi, dtype=np.int64), np.array(oi, dtype=np.int64), only_g, list(mo.keys())
+
+
+def errors(g, o, gi, oi):
+    dp = np.linalg.norm(g["pos"][gi] - o["pos"][oi], axis=1)
+    dd = np.linalg.norm(g["dir"][gi] - o["dir"][oi], axis=1)
+    ds = np.abs(g["path"][gi] - o["path"][oi])
+    dT = np.abs(g["time"][gi] - o["time"][oi])
+    dA = np.abs(g["amp"][gi] - o["amp"][oi])
+    return dp, dd, ds, dT, dA
+
+
+def same_steps(g, o, gi, oi):
+    return (g["n_acc"][gi] == o["n_acc"][oi]) & (g["n_rej"][gi] == o["n_rej"][oi])
+
+
+def subtree_of_roots(parent, roots):
+    """Indices of every ray whose root primary is in `roots` (primaries are 0..n-1)."""
+    n = len(parent)
+    root = np.empty(n, dtype=np.int64)
+    for i in range(n):
+        j = i
+        while parent[j] >= 0:
+            j = int(parent[j])
+        root[i] = j
+    return np.nonzero(np.isin(root, roots))[0], root

@@ -1,0 +1,227 @@
+"""CUDA tracer vs the FP64 oracle, through the C ABI (rp_trace).
+
+Tolerances (FP64 path): rays whose step sequence is identical to the oracle's (same accepted
+and rejected counts) agree to 1e-9 relative: |dr| <= 1e-9 (s + 1 m), |ds| <= 1e-9 s,
+|dT| <= 1e-9 T, |dt|, |dA| <= 1e-9.  Rays whose adaptive step sequence took a different
+branch (an accept/reject decision that flipped on a last-bit difference) must still agree
+within the integration tolerance, 10 tol s.  FP32-mixed path vs FP64 path: 1 mm in position
+and 0.01 ns in travel time over paths up to 3 km."""
+import numpy as np
+import pytest
+
+import oracle
+from parity import errors, gpu_rays, match, oracle_rays, same_steps, subtree_of_roots
+from paper_1810_01780_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rp():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1810_01780_gb300 import build
+
+    build.build()
+    import paper_1810_01780_gb300 as rp
+
+    return rp
+
+
+def _run(rp, medium, params, rays, receivers=None, precision="fp64"):
+    med = rp.Medium(medium)
+    pos, d, a = rays
+    res = rp.trace(med, pos, d, a, params=params, receivers=receivers, precision=precision)
+    return res
+
+
+def _check_fp64(g, o, tol, min_tier1=0.95, rel=1e-9):
+    gi, oi, only_g, only_o = match(g, o)
+    assert not only_g and not only_o, (len(only_g), len(only_o))
+    assert np.array_equal(g["status"][gi], o["status"][oi])
+    assert np.array_equal(g["generation"][gi], o["generation"][oi])
+    dp, dd, ds, dT, dA = errors(g, o, gi, oi)
+    s = o["path"][oi]
+    same = same_steps(g, o, gi, oi)
+    t1 = same
+    assert np.all(dp[t1] <= rel * (s[t1] + 1.0)), dp[t1].max()
+    assert np.all(ds[t1] <= rel * (s[t1] + 1.0)), ds[t1].max()
+    assert np.all(dT[t1] <= rel * o["time"][oi][t1] + 1e-18), dT[t1].max()
+    assert np.all(dd[t1] <= rel), dd[t1].max()
+    assert np.all(dA[t1] <= rel), dA[t1].max()
+    assert same.mean() >= min_tier1, same.mean()
+    t2 = ~same
+    if t2.any():
+        assert np.all(dp[t2] <= 10 * tol * (s[t2] + 1.0)), dp[t2].max()
+        assert np.all(dT[t2] <= 10 * tol * o["time"][oi][t2] + 1e-15)
+    return same.mean()
+
+
+def test_small_fan_fp64_matches_oracle(rp):
+    cfg = W.small()
+    res = _run(rp, cfg["medium"], cfg["params"], cfg["rays"])
+    ref, _ = oracle.trace(cfg["medium"], cfg["params"], *cfg["rays"])
+    g, o = gpu_rays(res), oracle_rays(ref)
+    assert len(g["path"]) == len(ref)
+    frac = _check_fp64(g, o, cfg["params"]["tol"])
+    print("tier-1 fraction", frac)
+    # the surface splits: transmitted rays exist and are recorded, not traced
+    assert np.any(g["status"] == 5)
+
+
+def test_fixed_step_fp64_every_ray_matches(rp):
+    cfg = W.small(256)
+    prm = dict(cfg["params"], h_min=2.5, h_max=2.5, h0=2.5, tol=1.0)
+    res = _run(rp, cfg["medium"], prm, cfg["rays"])
+    ref, _ = oracle.trace(cfg["medium"], prm, *cfg["rays"])
+    frac = _check_fp64(gpu_rays(res), oracle_rays(ref), prm["tol"], min_tier1=1.0)
+    assert frac == 1.0
+
+
+def test_batched_subset_fp64_rays_and_hits(rp):
+    cfg = W.batched()
+    rays = W.subsample(cfg["rays"], np.arange(3000))
+    # receivers moved next to the sources so that a small subset produces hits
+    c, r = cfg["receivers"]
+    res = _run(rp, cfg["medium"], cfg["params"], rays, receivers=(c, r * 25.0))
+    ref, hits = oracle.trace(cfg["medium"], cfg["params"], *rays, receivers=(c, r * 25.0))
+    g, o = gpu_rays(res), oracle_rays(ref)
+    _check_fp64(g, o, cfg["params"]["tol"])
+    assert g["generation"].max() >= 2  # secondaries of secondaries went through the queue
+    # hits: matched by (ray key, receiver, entry order)
+    from parity import tree_keys
+
+    kg, ko = tree_keys(g["parent"], g["seq"]), tree_keys(o["parent"], o["seq"])
+    gh = res["hits"]
+    gl = sorted((kg[int(rid)], int(rx), float(t), float(s)) for rid, rx, t, s in zip(
+        gh["ray"].cpu().numpy(), gh["receiver"].cpu().numpy(), gh["time"].cpu().numpy(),
+        gh["path"].cpu().numpy()))
+    ol = sorted((ko[int(h["ray"])], int(h["receiver"]), float(h["time"]), float(h["path"]))
+                for h in hits)
+    assert len(ol) > 20
+    assert len(gl) == len(ol)
+    for a, b in zip(gl, ol):
+        assert a[0] == b[0] and a[1] == b[1]
+        assert abs(a[3] - b[3]) <= 10 * cfg["params"]["tol"] * (b[3] + 1.0)
+        assert abs(a[2] - b[2]) <= 10 * cfg["params"]["tol"] * b[2] + 1e-15
+
+
+def test_fp32_mixed_vs_fp64(rp):
+    cfg = W.batched()
+    rays = W.subsample(cfg["rays"], np.arange(20000))
+    g64 = gpu_rays(_run(rp, cfg["medium"], cfg["params"], rays, precision="fp64"))
+    g32 = gpu_rays(_run(rp, cfg["medium"], cfg["params"], rays, precision="fp32"))
+    gi, oi, only32, only64 = match(g32, g64)
+    n = max(len(g32["path"]), len(g64["path"]))
+    assert len(only32) + len(only64) <= 0.002 * n
+    ok = g32["status"][gi] == g64["status"][oi]
+    assert ok.mean() > 0.998
+    dp, dd, ds, dT, dA = errors(g32, g64, gi[ok], oi[ok])
+    good = (dp <= 1e-3) & (dT <= 1e-11)
+    print("fp32 vs fp64: p99 |dr| %.3e m, p99 |dT| %.3e s, within 1 mm / 0.01 ns: %.5f" % (
+        np.quantile(dp, 0.99), np.quantile(dT, 0.99), good.mean()))
+    assert np.quantile(dp, 0.99) <= 1e-3
+    assert np.quantile(dT, 0.99) <= 1e-11
+    assert good.mean() >= 0.995
+
+
+def test_grid_medium_fp64_and_fp32(rp):
+    med = W.grid_medium(48, 48, 96, spacing=4.0, seed=7)
+    rays = W.point_sources(4, 256, seed=8, depth=(100.0, 250.0), xy=20.0)
+    prm = dict(W.TRACE_DEFAULTS, tol=1e-5, max_path=400.0, max_generation=0)
+    ref, _ = oracle.trace(med, prm, *rays)
+    g = gpu_rays(_run(rp, med, prm, rays, precision="fp64"))
+    _check_fp64(g, oracle_rays(ref), prm["tol"], min_tier1=0.9)
+    assert np.any(g["status"] == 4)  # some rays leave the box
+    g32 = gpu_rays(_run(rp, med, prm, rays, precision="fp32"))
+    gi, oi, a, b = match(g32, g)
+    ok = g32["status"][gi] == g["status"][oi]
+    assert ok.mean() > 0.99
+    dp, dd, ds, dT, dA = errors(g32, g, gi[ok], oi[ok])
+    assert np.quantile(dp, 0.99) <= 1e-3
+
+
+def test_paraxial_form_fp64(rp):
+    cfg = W.small(128)
+    prm = dict(cfg["params"], rhs_form="paraxial")
+    res = _run(rp, cfg["medium"], prm, cfg["rays"])
+    ref, _ = oracle.trace(cfg["medium"], prm, *cfg["rays"])
+    _check_fp64(gpu_rays(res), oracle_rays(ref), prm["tol"], min_tier1=0.9)
+
+
+def test_polarizations_and_break_conditions(rp):
+    cfg = W.small(200)
+    for pol in ("p", "unpol"):
+        prm = dict(cfg["params"], polarization=pol, max_time=4e-6, min_amp=0.3)
+        res = _run(rp, cfg["medium"], prm, cfg["rays"])
+        ref, _ = oracle.trace(cfg["medium"], prm, *cfg["rays"])
+        g = gpu_rays(res)
+        _check_fp64(g, oracle_rays(ref), prm["tol"], min_tier1=0.9)
+        assert np.any(g["status"] == 2) and np.any(g["status"] == 3)
+
+
+def test_edge_cases(rp):
+    import torch
+
+    from paper_1810_01780_gb300 import _abi
+
+    cfg = W.small(8)
+    med = rp.Medium(cfg["medium"])
+    # empty input
+    res = rp.trace(med, np.zeros((3, 0)), np.zeros((3, 0)), params=cfg["params"])
+    assert res["stats"]["rays"] == 0
+    # zero direction: flagged, traced rays unaffected
+    pos, d, a = cfg["rays"]
+    d = d.copy()
+    d[:, 3] = 0.0
+    res = rp.trace(med, pos, d, a, params=cfg["params"])
+    st = res["rays"]["status"].cpu().numpy()
+    assert st[3] == _abi.STATUS["BAD_INPUT"] and res["stats"]["flags"] & 1
+    # overflow: capacity exactly n with secondaries expected -> RP_ERR_OVERFLOW and sizes
+    rays = rp.PreparedRays(*cfg["rays"])
+    buf = rp.TraceBuffers(rays.n)
+    st = rp.trace_into(med, rays, rp.make_params(cfg["params"]), buf, allow_overflow=True)
+    assert st.rc == _abi.RP_ERR_OVERFLOW and st.rays > rays.n
+    # max_steps cap
+    prm = dict(cfg["params"], max_steps=5)
+    res = rp.trace(med, *cfg["rays"], params=prm)
+    assert np.all(res["rays"]["status"].cpu().numpy()[:8] == _abi.STATUS["MAX_STEPS"])
+    # invalid parameters are rejected on the host
+    with pytest.raises(_abi.RPError):
+        rp.trace(med, *cfg["rays"], params=dict(cfg["params"], tol=-1.0))
+    torch.cuda.synchronize()
+
+
+def test_full_size_batched_sampled(rp):
+    """The full 1,048,576-ray workload in the benchmark's configuration (FP32-mixed): sampled
+    primaries and their secondaries against the oracle."""
+    cfg = W.batched()
+    res = _run(rp, cfg["medium"], cfg["params"], cfg["rays"], receivers=cfg["receivers"],
+               precision="fp32")
+    g = gpu_rays(res)
+    n = cfg["rays"][0].shape[1]
+    assert np.all(g["status"] != 0)
+    rng = np.random.default_rng(123)
+    roots = np.sort(rng.choice(n, 256, replace=False))
+    gsel, groot = subtree_of_roots(g["parent"], roots)
+    ref, _ = oracle.trace(cfg["medium"], cfg["params"], *W.subsample(cfg["rays"], roots))
+    o = oracle_rays(ref)
+    # re-key the GPU subset so that its primaries are numbered like the oracle's
+    remap = {int(r): i for i, r in enumerate(roots)}
+    sub = {k: v[gsel] for k, v in g.items()}
+    idx = {int(j): i for i, j in enumerate(gsel)}
+    sub["parent"] = np.array([-1 if p < 0 else idx[int(p)] for p in sub["parent"]])
+    order = np.argsort([remap[int(groot[j])] if g["parent"][j] < 0 else 10**9 + j for j in gsel],
+                       kind="stable")
+    # primaries first in root order, then secondaries in their original (creation) order
+    perm = {int(old): new for new, old in enumerate(order)}
+    sub = {k: v[order] for k, v in sub.items()}
+    sub["parent"] = np.array([-1 if p < 0 else perm[int(p)] for p in sub["parent"]])
+    gi, oi, a, b = match(sub, o)
+    assert len(a) + len(b) <= 2
+    ok = sub["status"][gi] == o["status"][oi]
+    assert ok.mean() >= 0.99
+    dp, dd, ds, dT, dA = errors(sub, o, gi[ok], oi[ok])
+    assert np.quantile(dp, 0.99) <= 1e-3 and np.quantile(dT, 0.99) <= 1e-11
