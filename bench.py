@@ -1,0 +1,366 @@
+"""Benchmark of the ray-propagation hot path on GB300 (one JSON line on stdout).
+
+Workload: the batched two-layer-ice scenario -- 1,048,576 isotropic rays from sources at
+50..1500 m depth, exponential ice n(z) = 1.788 - 0.463 exp(-z / 75 m), an internal boundary
+at 100 m (+0.02), the ice-air surface at 0 m, secondaries up to generation 3 through the
+device work queue, 64 receiver spheres, Cash-Karp tol 1e-6, steps 1e-3..10 m, 3 km paths.
+One step = one rp_trace call over the whole batch (every generation, every receiver test).
+
+Headline value: accepted Cash-Karp ray-steps per second of the FP32-mixed path (FP32 stages,
+float-float position and direction, FP64 travel time and path length); the FP64 path, rays/s
+and the FP32-vs-FP64 error are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-fp64]
+
+--impl reference times the plain FP64 CPU oracle on the host cores (bounded sample of the
+same workload).  Under torchrun each rank traces its own batch (weak scaling, no data-path
+collective); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray-steps/s and rays/s on 1 GB300: FP64 vs FP32 vs surrogate at stated error"
+WORKLOAD = ("batched two-layer ice: 1,048,576 isotropic rays, sources 50-1500 m, internal "
+            "boundary at 100 m (+0.02), surface reflection, secondaries to generation 3, "
+            "64 receivers, tol 1e-6, h 1e-3..10 m, 3 km paths")
+N_RAYS = 1_048_576
+# FP32 flops of one attempted Cash-Karp step of the FP32-mixed path in a layered analytic
+# medium, counted from trace_core.cuh (FMA = 2); exp, reciprocal, sqrt and pow are extra
+# (special-function unit) and not included.  Derivation in the design notes.
+FLOPS_PER_ATTEMPT_F32 = 540
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(
+        os.environ.get("LOCAL_RANK", 0))
+
+
+# ----------------------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline leg)
+# ----------------------------------------------------------------------------------------
+
+def _oracle_chunk(args):
+    lo, hi, seed = args
+    import oracle
+    from paper_1810_01780_gb300 import workloads as W
+
+    cfg = W.batched(N_RAYS, seed)
+    rays = W.subsample(cfg["rays"], np.arange(lo, hi))
+    t0 = time.perf_counter()
+    out, hits = oracle.trace(cfg["medium"], cfg["params"], *rays, receivers=cfg["receivers"])
+    dt = time.perf_counter() - t0
+    return int(out["n_acc"].sum()), int(len(out)), dt
+
+
+def oracle_sample(n_primaries: int, seed: int = 2, cores: int | None = None):
+    """Trace the first n_primaries rays of the workload with the oracle on `cores` processes.
+    Returns (ray_steps, rays, wall_seconds, cores)."""
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    cores = cores or os.cpu_count() or 1
+    cores = max(1, min(cores, n_primaries))
+    bounds = np.linspace(0, n_primaries, cores + 1).astype(int)
+    chunks = [(int(bounds[i]), int(bounds[i + 1]), seed) for i in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_chunk, [(0, 1, seed)] * cores)  # warm the workers
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_chunk, chunks)
+        wall = time.perf_counter() - t0
+    return sum(r[0] for r in res), sum(r[1] for r in res), wall, cores
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    sample = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_sample(max(16, sample // 8))
+    steps_tot = rays_tot = wall_tot = 0.0
+    cores = 1
+    for _ in range(args.steps):
+        s, r, w, cores = oracle_sample(sample)
+        steps_tot += s
+        rays_tot += r
+        wall_tot += w
+    v = steps_tot / wall_tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ray-steps/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall_tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "rays_per_s": rays_tot / wall_tot,
+        "config": {"workload": WORKLOAD, "rays": N_RAYS, "precision": "fp64 (CPU oracle)",
+                   "sample": f"first {sample} primaries (+ their secondaries) per step"},
+        "cpu_baseline": {"value": v, "unit": "ray-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {sample} primaries of the workload, all secondaries"},
+        "e2e": {"value": v, "unit": "ray-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                out, _ = self.p.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except (ValueError, IndexError):
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+
+    # CPU baseline first (spawned pool), before this process does heavy GPU work
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        s, r, w, cores = oracle_sample(args.cpu_sample)
+        cpu = {"value": s / w, "unit": "ray-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {args.cpu_sample} primaries of the workload with all their "
+                         f"secondaries ({r} rays, {s} accepted steps, {w:.2f} s wall)"}
+
+    from paper_1810_01780_gb300 import build as B
+
+    B.build()
+    import paper_1810_01780_gb300 as rp
+    from paper_1810_01780_gb300 import workloads as W
+
+    seed = 2 + rank  # weak scaling: every rank traces its own batch
+    cfg = W.batched(N_RAYS, seed)
+    med = rp.Medium(cfg["medium"])
+    rays = rp.PreparedRays(*cfg["rays"], receivers=cfg["receivers"])
+    cap = int(5.5 * N_RAYS)
+    prm32 = rp.make_params(cfg["params"], "fp32")
+    buf = rp.TraceBuffers(cap, 4096)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one_step(prm, b):
+        flush.fill_(1.0)  # evict the L2 (129 MB) between steps, outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = rp.trace_into(med, rays, prm, b, stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), st
+
+    for _ in range(args.warmup):
+        one_step(prm32, buf)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times, kern, acc, att, nrays = [], [], 0, 0, 0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            ms, st = one_step(prm32, buf)
+            times.append(ms)
+            kern.append(st.kernel_ms)
+            acc += st.steps_accepted
+            att += st.steps_accepted + st.steps_rejected + st.steps_root
+            nrays += st.rays
+        torch.cuda.synchronize()
+    total_ms = sum(times)
+    tot = torch.tensor([total_ms, float(acc), float(nrays)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        t_max = tot[0:1].clone()
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        sums = tot[1:].clone()
+        dist.all_reduce(sums, op=dist.ReduceOp.SUM)
+        total_ms_max, acc_all, rays_all = float(t_max[0]), float(sums[0]), float(sums[1])
+    else:
+        total_ms_max, acc_all, rays_all = total_ms, float(acc), float(nrays)
+    value = acc_all / (total_ms_max / 1e3)
+    clocks = clk.summary()
+
+    # primary end points of the FP32 run for the stated error against FP64
+    end32 = buf.t["end_pos"][:, :N_RAYS].clone()
+    t32 = buf.t["time"][:N_RAYS].clone()
+
+    # e2e: host (pinned) -> device -> rp_trace -> host, through the same C ABI call
+    hp = torch.from_numpy(np.ascontiguousarray(cfg["rays"][0])).pin_memory()
+    hd = torch.from_numpy(np.ascontiguousarray(cfg["rays"][1])).pin_memory()
+    ha = torch.from_numpy(np.ascontiguousarray(cfg["rays"][2])).pin_memory()
+    out_fields = ("end_pos", "path", "time", "amp", "status")
+    host_out = {k: torch.empty(buf.t[k].shape, dtype=buf.t[k].dtype).pin_memory()
+                for k in out_fields}
+    e2e_ms, h2d_b, d2h_b = [], 0, 0
+    for it in range(max(3, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rays.pos.copy_(hp, non_blocking=True)
+        rays.dir.copy_(hd, non_blocking=True)
+        rays.amp.copy_(ha, non_blocking=True)
+        st = rp.trace_into(med, rays, prm32, buf, stream)
+        n_out = int(st.rays)
+        for k in out_fields:
+            src = buf.t[k][..., :n_out]
+            host_out[k][..., :n_out].copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        h2d_b = hp.numel() * 8 + hd.numel() * 8 + ha.numel() * 8
+        d2h_b = sum(buf.t[k][..., :n_out].numel() * buf.t[k].element_size() for k in out_fields)
+    e2e_val = acc / len(times) / (statistics.median(e2e_ms) / 1e3)
+
+    # FP64 path on the same batch (fewer steps; FP64 issue rate on GB300 is low)
+    modes = {"fp32_mixed": {"ray_steps_per_s": value, "rays_per_s": rays_all / (total_ms_max / 1e3),
+                            "ms_per_step": total_ms_max / args.steps}}
+    err = None
+    if not args.no_fp64:
+        prm64 = rp.make_params(cfg["params"], "fp64")
+        one_step(prm64, buf)
+        t64 = []
+        acc64 = rays64 = 0
+        for _ in range(args.fp64_steps):
+            ms, st = one_step(prm64, buf)
+            t64.append(ms)
+            acc64 += st.steps_accepted
+            rays64 += st.rays
+        modes["fp64"] = {"ray_steps_per_s": acc64 / (sum(t64) / 1e3),
+                         "rays_per_s": rays64 / (sum(t64) / 1e3), "ms_per_step": sum(t64) / len(t64)}
+        d = (end32 - buf.t["end_pos"][:, :N_RAYS]).norm(dim=0)
+        dT = (t32 - buf.t["time"][:N_RAYS]).abs()
+        within = ((d <= 1e-3) & (dT <= 1e-11)).double().mean()
+        err = {"vs": "FP64 GPU path, all 1,048,576 primary end points",
+               "within_1mm_10ps": float(within),
+               "pos_m": {"p50": float(d.quantile(0.5)), "p99": float(d.double().quantile(0.99)),
+                         "max": float(d.max())},
+               "time_s": {"p50": float(dT.quantile(0.5)), "p99": float(dT.quantile(0.99)),
+                          "max": float(dT.max())}}
+
+    # roofline of the dominant kernel (the FP32 tracing launches): FP32 ALU bound
+    sm_mhz = clocks["sm_mhz"] or _peaks().get("sm_max_mhz", 2070.0)
+    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    kern_ms = sum(kern)
+    achieved = FLOPS_PER_ATTEMPT_F32 * att / (kern_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "traffic": None,
+            "kernel": "k_trace_wave<PrecF32, MediumLayered>",
+            "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x median SM clock "
+                          f"under load ({sm_mhz:.0f} MHz)",
+            "flops_per_attempted_step": FLOPS_PER_ATTEMPT_F32,
+            "attempted_steps_per_launch_set": att / len(times)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "ray-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (f64 accumulators)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rays": N_RAYS, "precision": "fp32_mixed",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "l2": "flushed (512 MB write) before every step",
+                       "rays_traced_per_step": nrays / len(times)},
+            "rays_per_s": rays_all / (total_ms_max / 1e3),
+            "modes": modes, "error": err,
+            "e2e": {"value": e2e_val, "unit": "ray-steps/s", "h2d_bytes_per_step": h2d_b,
+                    "d2h_bytes_per_step": d2h_b, "ms_per_step": statistics.median(e2e_ms)},
+            "gpu_launches": args.steps * (1 + 4 + 3),
+            "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=65536)
+    ap.add_argument("--ref-sample", type=int, default=16384)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

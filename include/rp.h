@@ -42,6 +42,7 @@ extern "C" {
 #define RP_ERR_UNSUPPORTED (-5)  /* valid request this build does not provide */
 
 #define RP_MAX_LAYERS 8
+#define RP_MAX_WAVES 16 /* max_generation + 1 launches at most */
 
 enum { RP_MEDIUM_LAYERED = 0, RP_MEDIUM_GRID = 1 };
 enum { RP_FP64 = 0, RP_FP32_MIXED = 1 };
@@ -128,7 +129,8 @@ typedef struct {
  *   h0           first step of a primary [m] (secondaries inherit their parent's step)
  *   max_path     arc-length limit [m]
  *   max_time     travel-time limit [s], <= 0: none
- *   min_amp      terminate when |A| < min_amp |A0|, <= 0: none (A0 of the root primary)
+ *   min_amp      terminate when |A| < min_amp |A0|, <= 0: none (A0 of the root primary);
+ *                a secondary whose amplitude would start below the threshold is not cast
  *   eps_b        boundary landing tolerance [m] (FP32_MIXED uses at least 2e-6 m)
  *   stop_n, stop_d, use_stop   optional stop plane stop_n . r = stop_d (unit normal)
  *   max_generation  secondaries are spawned while the parent's generation is below it
@@ -179,6 +181,7 @@ typedef struct {
     int32_t waves, flags;    /* flags: 1 bad input, 2 output, 4 queue, 8 hit overflow,
                                 16 a boundary search hit its iteration cap */
     double kernel_ms;        /* device time of the tracing kernels */
+    double wave_ms[16];      /* device time of each generation's launch */
 } rp_stats;
 
 /* Traces in->n primaries and every secondary they spawn, in one persistent launch per ray

@@ -556,7 +556,8 @@ static void trace_one(trace_ctx *c, const start_state *st)
             double t_refl[3], t_refr[3], rr, tau;
             int32_t tir;
             or_split_dirs(y + 3, nrm, n1, n2, p->polarization, t_refl, t_refr, &rr, &tau, &tir);
-            if (!tir && st->gen < p->max_generation) {
+            int weak = p->min_amp > 0.0 && fabs(A * tau) < p->min_amp * fabs(st->A0);
+            if (!tir && st->gen < p->max_generation && !weak) {
                 start_state sec;
                 memcpy(sec.r, y, 3 * sizeof(double));
                 memcpy(sec.t, t_refr, 3 * sizeof(double));
@@ -572,6 +573,7 @@ static void trace_one(trace_ctx *c, const start_state *st)
                 sec.parent = st->id;
                 sec.root = st->root;
                 if (m->absorb[other]) {
+                    /* refracted into an absorbing layer: recorded, not traced */
                     double ys[7] = {y[0], y[1], y[2], t_refr[0], t_refr[1], t_refr[2], y[6]};
                     emit_ray(c, &sec, ys, s, sec.A, other, OR_ST_TRANSMITTED, 0, 0, 0, 0, 0, 0);
                 } else {

@@ -1,4 +1,5 @@
 // api.cu -- the C ABI entry points (rp.h): argument checks, media, workspace, errors.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -159,6 +160,22 @@ int rp_medium_create(const rp_medium_desc *d, void *stream, rp_medium_t *out)
             c.absorb = L.absorb != 0;
             m->layered.top[k] = plane_const(k ? L.z_top : -1e300);
         }
+        // refractive index on both sides of every plane, in FP64 on the host (the boundary
+        // module needs them at every split)
+        for (int k = 1; k < d->n_layers; ++k) {
+            const double z = d->layers[k].z_top;
+            for (int side = 0; side < 2; ++side) {
+                const rp_layer &L = d->layers[side == 0 ? k - 1 : k];
+                double n = L.dn == 0.0 ? L.n0 + L.offset : L.n0 - L.dn * exp(-z / L.z0) + L.offset;
+                if (side == 0) {
+                    m->layered.n_above[k] = n;
+                    m->layered.n_above_f[k] = (float)n;
+                } else {
+                    m->layered.n_below[k] = n;
+                    m->layered.n_below_f[k] = (float)n;
+                }
+            }
+        }
     } else if (d->kind == RP_MEDIUM_GRID) {
         if (d->nx < 2 || d->ny < 2 || d->nz < 2 || !(d->spacing > 0.0) || !d->grid_n) {
             delete m;
@@ -174,6 +191,8 @@ int rp_medium_create(const rp_medium_desc *d, void *stream, rp_medium_t *out)
             g.org[a] = d->origin[a];
             g.orgf[a] = (float)d->origin[a];
             g.hi[a] = d->origin[a] + d->spacing * (double)(dims[a] - 1);
+            g.lo_c[a] = plane_const(g.org[a]);
+            g.hi_c[a] = plane_const(g.hi[a]);
         }
         g.inv_sp = 1.0 / d->spacing;
         g.inv_spf = (float)g.inv_sp;

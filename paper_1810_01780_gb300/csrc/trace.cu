@@ -26,6 +26,7 @@ struct WaveIn {
     long long n;
     PlaneC stop;
     double h0;
+    float h0f;
 };
 
 __device__ __forceinline__ long long claim_index(unsigned long long *counter)
@@ -44,7 +45,6 @@ __device__ __forceinline__ void lane_reset(Lane<P> &L, const StepParams<P> &sp, 
     L.ev = EV_NONE;
     L.side = 0;
     L.it = 0;
-    L.nsplit = 0;
     L.n_acc = L.n_rej = L.n_root = L.n_refl = L.n_turn = L.root_fail = 0;
     L.status = RP_ST_ALIVE;
     L.stop = stop;
@@ -52,75 +52,144 @@ __device__ __forceinline__ void lane_reset(Lane<P> &L, const StepParams<P> &sp, 
     set_trial(L, sp);
 }
 
+__device__ __forceinline__ void prefetch_l1(const void *p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Starts fetching the inputs of ray k (claimed ahead of time) into L1.
+__device__ __forceinline__ void prefetch_ray(const Sinks &sk, const WaveIn &in, int wave,
+                                             unsigned long long base, long long k)
+{
+    if (wave == 0) {
+        const long long n = in.n;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            prefetch_l1(&in.pos[a * n + k]);
+            prefetch_l1(&in.dir[a * n + k]);
+        }
+        if (in.amp) prefetch_l1(&in.amp[k]);
+    } else {
+        const char *q = (const char *)&sk.queue[base + k];
+        prefetch_l1(q);
+        prefetch_l1(q + sizeof(QRec) - 1);
+    }
+}
+
+template <class P, class M>
+__device__ __forceinline__ void load_record(Lane<P> &L, const StepParams<P> &sp, const QRec &Q,
+                                            const PlaneC &stop)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        P::set(L.r, a, Q.r[a]);
+        P::set(L.t, a, Q.t[a]);
+    }
+    L.A = Q.A;
+    L.A0 = Q.A0;
+    P::sset(L.T, Q.T);
+    P::sset(L.s, Q.s);
+    L.h = P::from_d(Q.h);
+    L.id = Q.id;
+    L.parent = Q.parent;
+    L.gen = Q.gen;
+    L.seq = Q.seq;
+    L.layer = Q.layer;
+    lane_reset<P, M>(L, sp, stop);
+}
+
 // Next ray of this wave for the calling lane; false when the wave's input is exhausted.
+// `ahead` holds a ray index claimed one ray in advance, so that the claim's atomic and the
+// input loads overlap the tracing of the current ray.
 template <class P, class M>
 __device__ bool next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, const Sinks &sk,
                          const WaveIn &in, int wave, unsigned long long base,
-                         unsigned long long count)
+                         unsigned long long count, long long &ahead)
 {
     for (;;) {
-        const long long k = claim_index(&sk.ctrl->claim[wave]);
+        if (L.stk > 0) {
+            // depth first: the secondaries this thread cast itself come before new input
+            --L.stk;
+            load_record<P, M>(L, sp, thread_stack(sk)[L.stk], in.stop);
+            return true;
+        }
+        const long long k = ahead;
         if (k >= (long long)count) return false;
-        double r[3], t[3];
-        if (wave == 0) {
-            const long long n = in.n;
+        ahead = claim_index(&sk.ctrl->claim[wave]);
+        if (ahead < (long long)count) prefetch_ray(sk, in, wave, base, ahead);
+        if (wave != 0) {
+            load_record<P, M>(L, sp, sk.queue[base + k], in.stop);
+            return true;
+        }
+        const long long n = in.n;
+        L.A = in.amp ? in.amp[k] : 1.0;
+        L.A0 = L.A;
+        L.id = k;
+        L.parent = -1;
+        L.gen = 0;
+        L.seq = 0;
+        if constexpr (P::kFF) {
+            // FP32-mixed: every conversion on the integer/FP32 pipes
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                r[a] = in.pos[a * n + k];
-                t[a] = in.dir[a * n + k];
+                P::set(L.r, a, in.pos[a * n + k]);
+                P::set(L.t, a, in.dir[a * n + k]);
             }
-            L.A = in.amp ? in.amp[k] : 1.0;
-            L.A0 = L.A;
-            L.T = 0.0;
-            L.s = 0.0;
-            L.h = P::from_d(in.h0);
-            L.id = k;
-            L.parent = -1;
-            L.gen = 0;
-            L.seq = 0;
+            L.T.hi = L.T.lo = 0.0f;
+            L.s.hi = L.s.lo = 0.0f;
+            L.h = in.h0f;
             if constexpr (is_layered_v<M>)
-                L.layer = layer_of(med, r[2]);
+                L.layer = layer_of_ff(med, L.r.hi[2], L.r.lo[2]);
             else
                 L.layer = 0;
-            double q = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-            const bool pos_ok = isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]);
-            if (!(q > 0.0) || !isfinite(q) || !pos_ok) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    P::set(L.r, a, r[a]);
-                    P::set(L.t, a, t[a]);
-                }
+            const float q2 = L.t.hi[0] * L.t.hi[0] + L.t.hi[1] * L.t.hi[1] + L.t.hi[2] * L.t.hi[2];
+            const bool pos_ok = isfinite(L.r.hi[0]) && isfinite(L.r.hi[1]) && isfinite(L.r.hi[2]);
+            if (!(q2 > 0.0f) || !isfinite(q2) || !pos_ok) {
                 lane_reset<P, M>(L, sp, in.stop);
                 L.status = RP_ST_BAD_INPUT;
                 atomicOr(&sk.ctrl->flags, (unsigned)FLAG_BAD_INPUT);
                 write_ray<P>(sk.out, L.id, L, sk.ctrl);
                 continue;
             }
-            t[0] /= q;
-            t[1] /= q;
-            t[2] /= q;
+            if (fabsf(q2 - 1.0f) > 1e-5f) {
+                // far from unit: a coarse FP64 normalisation first (rare)
+                double t[3] = {in.dir[k], in.dir[n + k], in.dir[2 * n + k]};
+                const double q = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) P::set(L.t, a, t[a] / q);
+            }
+            ff_renormalise(L.t);  // exact unit length in float-float
         } else {
-            const QRec &Q = sk.queue[base + k];
+            double r[3], t[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                r[a] = Q.r[a];
-                t[a] = Q.t[a];
+                r[a] = in.pos[a * n + k];
+                t[a] = in.dir[a * n + k];
             }
-            L.A = Q.A;
-            L.A0 = Q.A0;
-            L.T = Q.T;
-            L.s = Q.s;
-            L.h = P::from_d(Q.h);
-            L.id = Q.id;
-            L.parent = Q.parent;
-            L.gen = Q.gen;
-            L.seq = Q.seq;
-            L.layer = Q.layer;
-        }
+            P::sset(L.T, 0.0);
+            P::sset(L.s, 0.0);
+            L.h = P::from_d(in.h0);
+            if constexpr (is_layered_v<M>)
+                L.layer = layer_of(med, r[2]);
+            else
+                L.layer = 0;
+            const double q2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+            const bool pos_ok = isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            P::set(L.r, a, r[a]);
-            P::set(L.t, a, t[a]);
+            for (int a = 0; a < 3; ++a) P::set(L.r, a, r[a]);
+            if (!(q2 > 0.0) || !isfinite(q2) || !pos_ok) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) P::set(L.t, a, t[a]);
+                lane_reset<P, M>(L, sp, in.stop);
+                L.status = RP_ST_BAD_INPUT;
+                atomicOr(&sk.ctrl->flags, (unsigned)FLAG_BAD_INPUT);
+                write_ray<P>(sk.out, L.id, L, sk.ctrl);
+                continue;
+            }
+            // normalised as the FP64 reference does
+            const double q = sqrt(q2);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) P::set(L.t, a, t[a] / q);
         }
         lane_reset<P, M>(L, sp, in.stop);
         return true;
@@ -128,12 +197,9 @@ __device__ bool next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, cons
 }
 
 template <class P, class M>
-__global__ void __launch_bounds__(256) k_trace_wave(const M med, const StepParams<P> sp,
+__global__ void __launch_bounds__(128, P::kMinBlocks) k_trace_wave(const M med, const StepParams<P> sp,
                                                     const Sinks sk, const WaveIn in, int wave)
 {
-    __shared__ unsigned long long s_cnt[3];
-    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
-    __syncthreads();
     unsigned long long base = 0, count;
     if (wave == 0) {
         count = (unsigned long long)in.n;
@@ -142,25 +208,31 @@ __global__ void __launch_bounds__(256) k_trace_wave(const M med, const StepParam
         count = sk.ctrl->seg_end[wave] - base;
     }
     Lane<P> L;
-    unsigned long long acc = 0, rej = 0, root = 0;
-    bool have = next_ray<P, M>(L, med, sp, sk, in, wave, base, count);
-    while (have) {
-        if (advance<P, M>(med, L, sp, sk)) {
-            acc += (unsigned long long)L.n_acc;
-            rej += (unsigned long long)L.n_rej;
-            root += (unsigned long long)L.n_root;
+    L.stk = 0;
+    unsigned int acc = 0, rej = 0, root = 0;
+    long long ahead = claim_index(&sk.ctrl->claim[wave]);
+    bool have = next_ray<P, M>(L, med, sp, sk, in, wave, base, count, ahead);
+    // Warp-synchronous loop: the lanes of a warp re-converge at the top of every iteration,
+    // so the Runge-Kutta step always runs with every lane that still has a ray; a lane whose
+    // input is exhausted idles until the whole warp is done.
+    while (__any_sync(0xffffffffu, have)) {
+        __syncwarp();
+        if (have && advance<P, M>(med, L, sp, sk)) {
+            acc += (unsigned int)L.n_acc;
+            rej += (unsigned int)L.n_rej;
+            root += (unsigned int)L.n_root;
             write_ray<P>(sk.out, L.id, L, sk.ctrl);
-            have = next_ray<P, M>(L, med, sp, sk, in, wave, base, count);
+            have = next_ray<P, M>(L, med, sp, sk, in, wave, base, count, ahead);
         }
     }
-    atomicAdd(&s_cnt[0], acc);
-    atomicAdd(&s_cnt[1], rej);
-    atomicAdd(&s_cnt[2], root);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicAdd(&sk.ctrl->steps_acc, s_cnt[0]);
-        atomicAdd(&sk.ctrl->steps_rej, s_cnt[1]);
-        atomicAdd(&sk.ctrl->steps_root, s_cnt[2]);
+    // per-warp totals; no block-wide barrier, so finished warps simply retire
+    acc = __reduce_add_sync(0xffffffffu, acc);
+    rej = __reduce_add_sync(0xffffffffu, rej);
+    root = __reduce_add_sync(0xffffffffu, root);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sk.ctrl->steps_acc, (unsigned long long)acc);
+        atomicAdd(&sk.ctrl->steps_rej, (unsigned long long)rej);
+        atomicAdd(&sk.ctrl->steps_root, (unsigned long long)root);
     }
 }
 
@@ -191,9 +263,22 @@ static int occupancy_grid(int block)
     return cached_occ;
 }
 
+static int trace_threads(int kind, int precision, int device, int block)
+{
+    int occ;
+    if (kind == RP_MEDIUM_LAYERED)
+        occ = precision == RP_FP64 ? occupancy_grid<PrecF64, MediumLayered>(block)
+                                   : occupancy_grid<PrecF32, MediumLayered>(block);
+    else
+        occ = precision == RP_FP64 ? occupancy_grid<PrecF64, MediumGrid>(block)
+                                   : occupancy_grid<PrecF32, MediumGrid>(block);
+    if (occ < 0) return occ;
+    return sm_count(device) * occ * block;
+}
+
 template <class P, class M>
 static int launch_waves(const M &med, const StepParams<P> &sp, const Sinks &sk, const WaveIn &in,
-                        int n_waves, int device, int block, cudaStream_t st)
+                        int n_waves, int device, int block, cudaStream_t st, cudaEvent_t *ev)
 {
     int occ = occupancy_grid<P, M>(block);
     if (occ < 0) return occ;
@@ -201,6 +286,7 @@ static int launch_waves(const M &med, const StepParams<P> &sp, const Sinks &sk, 
     for (int w = 0; w < n_waves; ++w) {
         if (w > 0) k_prep_wave<<<1, 1, 0, st>>>(sk.ctrl, w, sk.q_cap);
         k_trace_wave<P, M><<<grid, block, 0, st>>>(med, sp, sk, in, w);
+        RP_CUDA_TRY(cudaEventRecord(ev[w + 1], st));
     }
     RP_CUDA_TRY(cudaGetLastError());
     return RP_OK;
@@ -211,6 +297,7 @@ static StepParams<P> make_step_params(const rp_trace_params *p, int axis, float 
 {
     StepParams<P> sp;
     sp.tol = (typename P::R)p->tol;
+    sp.inv_tol = (typename P::R)(1.0 / p->tol);
     sp.h_min = (typename P::R)p->h_min;
     sp.h_max = (typename P::R)p->h_max;
     double eps = p->eps_b;
@@ -219,6 +306,10 @@ static StepParams<P> make_step_params(const rp_trace_params *p, int axis, float 
     sp.max_path = p->max_path;
     sp.max_time = p->max_time;
     sp.min_amp = p->min_amp;
+    sp.mp = plane_const(p->max_path);
+    sp.mt = plane_const(p->max_time);
+    sp.use_max_time = p->max_time > 0.0;
+    sp.use_min_amp = p->min_amp > 0.0;
     sp.rhs_form = p->rhs_form;
     sp.polarization = p->polarization;
     sp.max_generation = p->max_generation;
@@ -294,8 +385,9 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
 
     // receivers: sort by centre depth on the host (tiny), upload with the workspace
     std::vector<SphereC> spheres(n_rx);
-    std::vector<float> cz(n_rx);
-    float r_max = 0.0f;
+    std::vector<int2> buckets;
+    std::vector<float4> boxes(n_rx);
+    float rz_lo = 0.0f, rz_hi = -1.0f, inv_bucket = 1.0f;
     if (n_rx) {
         std::vector<double> c(3 * (size_t)n_rx), rad(n_rx);
         RP_CUDA_TRY(cudaMemcpyAsync(c.data(), rx->center, c.size() * sizeof(double),
@@ -317,17 +409,47 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
             spheres[j].R = rad[o];
             spheres[j].Rf = (float)rad[o];
             spheres[j].idx = o;
-            cz[j] = (float)c[3 * o + 2];
-            r_max = std::max(r_max, (float)rad[o]);
         }
+        // depth buckets: bucket b covers [rz_lo + b w, rz_lo + (b + 1) w); its sphere range
+        // holds every sphere whose padded slab overlaps it (spheres sorted by depth, so the
+        // range is contiguous once slabs are ordered by their lower edge; the padded slab
+        // uses the largest radius so that lower and upper edges are both monotonic)
+        double r_max = 0.0;
+        for (int j = 0; j < n_rx; ++j) r_max = std::max(r_max, spheres[j].R);
+        // pad: largest radius plus 1 mm, far above the FP32 rounding of a depth (< 1e-4 m)
+        const double pad = r_max + 1e-3;
+        for (int j = 0; j < n_rx; ++j)
+            boxes[j] = make_float4((float)spheres[j].c[0].d, (float)spheres[j].c[1].d,
+                                   (float)spheres[j].c[2].d, (float)(spheres[j].R + 1e-3));
+        const double zlo = spheres[0].c[2].d - pad, zhi = spheres[n_rx - 1].c[2].d + pad;
+        const int nb = (int)std::min<double>(4096.0, std::max(1.0, std::ceil((zhi - zlo) / 1.0)));
+        const double w = (zhi - zlo) / nb;
+        buckets.resize(nb);
+        int first = 0, end = 0;
+        for (int b = 0; b < nb; ++b) {
+            const double b_lo = zlo + w * b - 1e-6 * (1.0 + std::fabs(zlo)),
+                         b_hi = zlo + w * (b + 1) + 1e-6 * (1.0 + std::fabs(zhi));
+            while (first < n_rx && spheres[first].c[2].d + pad < b_lo) ++first;
+            end = std::max(end, first);
+            while (end < n_rx && spheres[end].c[2].d - pad <= b_hi) ++end;
+            buckets[b] = make_int2(first, end);
+        }
+        rz_lo = (float)zlo;
+        rz_hi = (float)zhi;
+        inv_bucket = (float)(1.0 / w);
     }
 
+    const int block = 128;
+    const int threads = trace_threads(m->kind, p->precision, dev, block);
+    if (threads < 0) return threads;
     const long long q_cap = out->capacity - in->n;
     const size_t off_ctrl = 0;
     const size_t off_q = align_up(sizeof(Ctrl));
     const size_t off_s = off_q + align_up(sizeof(QRec) * (size_t)std::max(q_cap, 1LL));
     const size_t off_z = off_s + align_up(sizeof(SphereC) * (size_t)std::max(n_rx, 1));
-    const size_t total = off_z + align_up(sizeof(float) * (size_t)std::max(n_rx, 1));
+    const size_t off_b = off_z + align_up(sizeof(int2) * std::max<size_t>(buckets.size(), 1));
+    const size_t off_k = off_b + align_up(sizeof(float4) * (size_t)std::max(n_rx, 1));
+    const size_t total = off_k + align_up(sizeof(QRec) * (size_t)threads * kStackDepth);
 
     Workspace &ws = workspace(dev);
     std::lock_guard<std::mutex> lock(ws.mu);
@@ -340,19 +462,26 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     sk.ctrl = ctrl;
     sk.queue = (QRec *)(base + off_q);
     sk.q_cap = (unsigned long long)q_cap;
+    sk.stack = (QRec *)(base + off_k);
     sk.out = *out;
     if (hits) sk.hits = *hits;
     sk.has_rx = n_rx > 0;
     sk.rx.s = (const SphereC *)(base + off_s);
-    sk.rx.cz = (const float *)(base + off_z);
+    sk.rx.bucket = (const int2 *)(base + off_z);
+    sk.rx.box = (const float4 *)(base + off_b);
     sk.rx.n = n_rx;
-    sk.rx.r_max = r_max;
+    sk.rx.n_buckets = (int)buckets.size();
+    sk.rx.z_lo = rz_lo;
+    sk.rx.z_hi = rz_hi;
+    sk.rx.inv_bucket = inv_bucket;
 
     RP_CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
     if (n_rx) {
         RP_CUDA_TRY(cudaMemcpyAsync(base + off_s, spheres.data(), sizeof(SphereC) * n_rx,
                                     cudaMemcpyHostToDevice, st));
-        RP_CUDA_TRY(cudaMemcpyAsync(base + off_z, cz.data(), sizeof(float) * n_rx,
+        RP_CUDA_TRY(cudaMemcpyAsync(base + off_z, buckets.data(), sizeof(int2) * buckets.size(),
+                                    cudaMemcpyHostToDevice, st));
+        RP_CUDA_TRY(cudaMemcpyAsync(base + off_b, boxes.data(), sizeof(float4) * n_rx,
                                     cudaMemcpyHostToDevice, st));
     }
     k_init_ctrl<<<1, 1, 0, st>>>(ctrl, in->n);
@@ -364,43 +493,42 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     wi.n = in->n;
     wi.stop = plane_const(soff);
     wi.h0 = p->h0;
+    wi.h0f = (float)p->h0;
 
-    cudaEvent_t e0, e1;
-    RP_CUDA_TRY(cudaEventCreate(&e0));
-    RP_CUDA_TRY(cudaEventCreate(&e1));
-    RP_CUDA_TRY(cudaEventRecord(e0, st));
-    const int n_waves = p->max_generation + 1;
-    const int block = 128;
+    const int n_waves = p->max_generation + 1;  // launches: the stacks' overflow needs at most this
+    cudaEvent_t ev[RP_MAX_WAVES + 1];
+    for (int w = 0; w <= n_waves; ++w) RP_CUDA_TRY(cudaEventCreate(&ev[w]));
+    RP_CUDA_TRY(cudaEventRecord(ev[0], st));
     if (m->kind == RP_MEDIUM_LAYERED) {
         if (p->precision == RP_FP64)
             rc = launch_waves<PrecF64, MediumLayered>(m->layered,
                                                       make_step_params<PrecF64>(p, axis, sdir),
-                                                      sk, wi, n_waves, dev, block, st);
+                                                      sk, wi, n_waves, dev, block, st, ev);
         else
             rc = launch_waves<PrecF32, MediumLayered>(m->layered,
                                                       make_step_params<PrecF32>(p, axis, sdir),
-                                                      sk, wi, n_waves, dev, block, st);
+                                                      sk, wi, n_waves, dev, block, st, ev);
     } else {
         if (p->precision == RP_FP64)
             rc = launch_waves<PrecF64, MediumGrid>(m->grid, make_step_params<PrecF64>(p, axis, sdir),
-                                                   sk, wi, n_waves, dev, block, st);
+                                                   sk, wi, n_waves, dev, block, st, ev);
         else
             rc = launch_waves<PrecF32, MediumGrid>(m->grid, make_step_params<PrecF32>(p, axis, sdir),
-                                                   sk, wi, n_waves, dev, block, st);
+                                                   sk, wi, n_waves, dev, block, st, ev);
     }
-    if (rc) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return rc;
-    }
-    RP_CUDA_TRY(cudaEventRecord(e1, st));
     Ctrl *hc = (Ctrl *)ws.host_ctrl;
-    RP_CUDA_TRY(cudaMemcpyAsync(hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-    RP_CUDA_TRY(cudaStreamSynchronize(st));
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "rp_trace: control block read-back");
+    }
+    float wave_ms[RP_MAX_WAVES] = {0.0f}, ms = 0.0f;
+    if (!rc) {
+        for (int w = 0; w < n_waves; ++w) cudaEventElapsedTime(&wave_ms[w], ev[w], ev[w + 1]);
+        cudaEventElapsedTime(&ms, ev[0], ev[n_waves]);
+    }
+    for (int w = 0; w <= n_waves; ++w) cudaEventDestroy(ev[w]);
+    if (rc) return rc;
 
     unsigned flags = hc->flags;
     if (!hits) flags &= ~(unsigned)FLAG_HIT_OVERFLOW;
@@ -415,6 +543,7 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
         stats->waves = n_waves;
         stats->flags = (int32_t)flags;
         stats->kernel_ms = ms;
+        for (int w = 0; w < RP_MAX_WAVES; ++w) stats->wave_ms[w] = w < n_waves ? wave_ms[w] : 0.0;
     }
     if (flags & (FLAG_OUT_OVERFLOW | FLAG_QUEUE_OVERFLOW | FLAG_HIT_OVERFLOW)) {
         set_error("rp_trace: overflow (rays %llu / capacity %lld, hits %llu / capacity %lld)",

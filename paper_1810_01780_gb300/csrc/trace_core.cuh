@@ -93,6 +93,30 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float d)
     lo = __fsub_rn(e, __fsub_rn(hi, s));
 }
 
+// Splits a double into a float-float pair (hi = x truncated to 24 significant bits, lo = the
+// rest rounded to float; |x - hi - lo| <= 2^-47 |x|) with integer operations only: on GB300 a
+// conversion on the FP64 pipe costs as much issue time as a whole Runge-Kutta stage.
+__device__ __forceinline__ void split_d2ff(double x, float &hi, float &lo)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int e = (unsigned int)(b >> 52) & 0x7FFu;
+    if ((b << 1) == 0ull) {  // +-0
+        hi = __int_as_float((int)((unsigned int)(b >> 32) & 0x80000000u));
+        lo = 0.0f;
+        return;
+    }
+    if (e < 949u || e > 1100u) {  // |x| outside [2^-74, 2^78): rare, use the FP64 pipe
+        hi = __double2float_rn(x);
+        lo = __double2float_rn(x - (double)hi);
+        return;
+    }
+    const unsigned int sgn = (unsigned int)(b >> 32) & 0x80000000u;
+    hi = __uint_as_float(sgn | ((e - 896u) << 23) | (unsigned int)((b >> 29) & 0x7FFFFFull));
+    const unsigned int low29 = (unsigned int)(b & 0x1FFFFFFFull);
+    const float scale = __uint_as_float((e - 948u) << 23);  // 2^(e - 1075)
+    lo = __uint_as_float(__float_as_uint(__uint2float_rn(low29) * scale) | sgn);
+}
+
 // A plane offset (or any coordinate constant) in both precisions.
 struct PlaneC {
     double d;
@@ -108,6 +132,7 @@ struct PrecF64 {
         double v[3];
     };
     static constexpr bool kFF = false;
+    static constexpr int kMinBlocks = 2;  // blocks of 128 per SM the register budget targets
     __device__ static __forceinline__ R base(const V &a, int i) { return a.v[i]; }
     __device__ static __forceinline__ void add(V &a, int i, R d) { a.v[i] += d; }
     __device__ static __forceinline__ double get(const V &a, int i) { return a.v[i]; }
@@ -124,6 +149,12 @@ struct PrecF64 {
     __device__ static __forceinline__ R sqrt_(R x) { return sqrt(x); }
     __device__ static __forceinline__ R pow_(R x, R y) { return pow(x, y); }
     __device__ static __forceinline__ R c(double x) { return x; }
+    // scalar accumulators (travel time, arc length)
+    typedef double S;
+    __device__ static __forceinline__ double sget(const S &a) { return a; }
+    __device__ static __forceinline__ void sset(S &a, double x) { a = x; }
+    __device__ static __forceinline__ void sadd(S &a, R d) { a += d; }
+    __device__ static __forceinline__ R sdiff(const S &a, const PlaneC &c) { return a - c.d; }
 };
 
 struct PrecF32 {
@@ -132,6 +163,7 @@ struct PrecF32 {
         float hi[3], lo[3];
     };
     static constexpr bool kFF = true;
+    static constexpr int kMinBlocks = 4;
     __device__ static __forceinline__ R base(const V &a, int i) { return a.hi[i]; }
     __device__ static __forceinline__ void add(V &a, int i, R d) { ff_add(a.hi[i], a.lo[i], d); }
     __device__ static __forceinline__ double get(const V &a, int i)
@@ -140,8 +172,7 @@ struct PrecF32 {
     }
     __device__ static __forceinline__ void set(V &a, int i, double x)
     {
-        a.hi[i] = __double2float_rn(x);
-        a.lo[i] = __double2float_rn(x - (double)a.hi[i]);
+        split_d2ff(x, a.hi[i], a.lo[i]);
     }
     __device__ static __forceinline__ R rel(const V &a, int i, R delta, const PlaneC &c)
     {
@@ -159,6 +190,18 @@ struct PrecF32 {
     __device__ static __forceinline__ R sqrt_(R x) { return sqrtf(x); }
     __device__ static __forceinline__ R pow_(R x, R y) { return exp2f(y * __log2f(x)); }
     __device__ static __forceinline__ R c(double x) { return (float)x; }
+    // scalar accumulators in float-float: GB300 issues FP64 at 1/64 of the FP32 rate, so the
+    // per-step accumulation of travel time and arc length stays on the FP32 pipe
+    struct S {
+        float hi, lo;
+    };
+    __device__ static __forceinline__ double sget(const S &a) { return (double)a.hi + (double)a.lo; }
+    __device__ static __forceinline__ void sset(S &a, double x) { split_d2ff(x, a.hi, a.lo); }
+    __device__ static __forceinline__ void sadd(S &a, R d) { ff_add(a.hi, a.lo, d); }
+    __device__ static __forceinline__ R sdiff(const S &a, const PlaneC &c)
+    {
+        return __fadd_rn(__fsub_rn(a.hi, c.hi), __fsub_rn(a.lo, c.lo));
+    }
 };
 
 // ---------------------------------------------------------------------------------------
@@ -174,6 +217,9 @@ struct MediumLayered {
     int32_t n_layers, pad;
     LayerC L[RP_MAX_LAYERS];
     PlaneC top[RP_MAX_LAYERS];  // top[k]: plane z = z_top of layer k (k >= 1)
+    // index just above / below plane k (layer k-1 / layer k evaluated at z_top[k])
+    double n_above[RP_MAX_LAYERS], n_below[RP_MAX_LAYERS];
+    float n_above_f[RP_MAX_LAYERS], n_below_f[RP_MAX_LAYERS];
 };
 
 struct MediumGrid {
@@ -181,6 +227,7 @@ struct MediumGrid {
     int32_t nx, ny, nz, pad;
     double org[3], inv_sp, hi[3];
     float orgf[3], inv_spf;
+    PlaneC lo_c[3], hi_c[3];  // box faces
 };
 
 template <class M>
@@ -191,6 +238,15 @@ __device__ __forceinline__ int layer_of(const MediumLayered &m, double z)
     int k = 0;
     for (int j = 1; j < m.n_layers; ++j)
         if (z >= m.top[j].d) k = j;
+    return k;
+}
+
+// The same for a depth held as float-float (z = hi + lo), on the FP32 pipe.
+__device__ __forceinline__ int layer_of_ff(const MediumLayered &m, float hi, float lo)
+{
+    int k = 0;
+    for (int j = 1; j < m.n_layers; ++j)
+        if (__fadd_rn(__fsub_rn(hi, m.top[j].hi), __fsub_rn(lo, m.top[j].lo)) >= 0.0f) k = j;
     return k;
 }
 
@@ -329,7 +385,19 @@ __device__ __forceinline__ void ck_step(const M &med, int layer, int form,
         R n, g[3];
         medium_eval<P>(med, layer, rs, n, g);
         R inv_n = P::rcp(n);
-        if (form == RP_RHS_PROJECTED) {
+        if constexpr (is_layered_v<M>) {
+            // stratified medium: grad n = (0, 0, g_z); the zero terms are dropped
+            if (form == RP_RHS_PROJECTED) {
+                const R gt = g[2] * ts[i][2];
+                kt[i][0] = -(gt * ts[i][0]) * inv_n;
+                kt[i][1] = -(gt * ts[i][1]) * inv_n;
+                kt[i][2] = (g[2] - gt * ts[i][2]) * inv_n;
+            } else {
+                kt[i][0] = R(0);
+                kt[i][1] = R(0);
+                kt[i][2] = g[2] * inv_n;
+            }
+        } else if (form == RP_RHS_PROJECTED) {
             R gt = g[0] * ts[i][0] + g[1] * ts[i][1] + g[2] * ts[i][2];
 #pragma unroll
             for (int c = 0; c < 3; ++c) kt[i][c] = (g[c] - gt * ts[i][c]) * inv_n;
@@ -357,6 +425,12 @@ __device__ __forceinline__ void ck_step(const M &med, int layer, int form,
     for (int c = 0; c < 3; ++c) {
         dr[c] = h * sr[c];
         dt[c] = h * st[c];
+    }
+    if constexpr (P::kFF) {
+        // the stages used the high word of the direction; since sum_i b5_i = 1 its low word
+        // contributes exactly h * t_lo to the position increment
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dr[c] = __fmaf_rn(h, t0v.lo[c], dr[c]);
     }
     dT = h * (sT * P::c(kInvC0));
     er = P::sqrt_(dr_e[0] * dr_e[0] + dr_e[1] * dr_e[1] + dr_e[2] * dr_e[2]);
@@ -424,11 +498,16 @@ struct SphereC {
     int32_t idx;
 };
 
+// Spheres are sorted by centre depth; a table of depth buckets gives, for every bucket, the
+// range of spheres whose depth slab [cz - R, cz + R] can overlap it, so that a chord is
+// culled by one or two table lookups.
 struct Receivers {
     const SphereC *__restrict__ s;
-    const float *__restrict__ cz;  // sorted centre depths
-    int32_t n;
-    float r_max;
+    const int2 *__restrict__ bucket;  // [first, end) sphere range per depth bucket
+    const float4 *__restrict__ box;   // centre in FP32 and radius + 1 mm, sorted like s
+    int32_t n, n_buckets;
+    float z_lo, z_hi;    // depth range covered by the buckets
+    float inv_bucket;    // 1 / bucket width
 };
 
 // ---------------------------------------------------------------------------------------
@@ -464,24 +543,28 @@ template <class P>
 struct Lane {
     typedef typename P::R R;
     typename P::V r, t;
-    double T, s, A, A0;
+    typename P::S T, s;  // travel time, arc length
+    double A, A0;
     R h, h_next, h_try;
     R ra, rb, ga, gb;  // root bracket
     PlaneC stop;       // stop plane offset along stop_axis
     R stop_sign;
     long long id, parent;
     int32_t mode, ev, side, it, last;
-    int32_t layer, gen, seq, nsplit;
+    int32_t layer, gen, seq;
     int32_t n_acc, n_rej, n_root, n_refl, n_turn, root_fail;
     int32_t status;
+    int32_t stk;  // entries on this thread's private stack of pending secondaries
 };
 
 // Parameters shared by every lane of a launch.
 template <class P>
 struct StepParams {
     typedef typename P::R R;
-    R tol, h_min, h_max, eps_b;
+    R tol, inv_tol, h_min, h_max, eps_b;
     double max_path, max_time, min_amp;
+    PlaneC mp, mt;  // max_path and max_time as float-float constants
+    int32_t use_max_time, use_min_amp;
     int32_t rhs_form, polarization, max_generation, use_stop;
     int32_t stop_axis;  // 0, 1, 2 (the stop normal is +/- a coordinate axis)
     float stop_dir;     // +1 or -1: sign of the normal along stop_axis
@@ -504,12 +587,21 @@ __device__ __forceinline__ void set_trial(Lane<P> &L, const StepParams<P> &sp)
 {
     typedef typename P::R R;
     L.last = 0;
-    double rem = sp.max_path - L.s;
-    if (L.s + (double)L.h >= sp.max_path) {
-        L.h_try = P::from_d(rem);
-        L.last = 1;
+    if constexpr (P::kFF) {
+        const R rem = -P::sdiff(L.s, sp.mp);  // max_path - s
+        if (L.h >= rem) {
+            L.h_try = rem;
+            L.last = 1;
+        } else {
+            L.h_try = L.h;
+        }
     } else {
-        L.h_try = L.h;
+        if (L.s + L.h >= sp.max_path) {
+            L.h_try = sp.max_path - L.s;
+            L.last = 1;
+        } else {
+            L.h_try = L.h;
+        }
     }
     L.mode = MODE_NORMAL;
 }
@@ -555,10 +647,13 @@ __device__ __forceinline__ void init_stop(Lane<P> &L, const StepParams<P> &sp)
 }
 
 // Hooks the kernels provide: where a secondary goes and what a receiver hit writes.
+constexpr int kStackDepth = 8;  // secondaries a thread keeps for itself before spilling
+
 struct Sinks {
     Ctrl *ctrl;
     QRec *queue;
     unsigned long long q_cap;
+    QRec *stack;  // kStackDepth records per thread of the launch
     // output arrays for rays recorded directly (transmitted into absorbing layers)
     rp_ray_out out;
     // hits
@@ -583,8 +678,8 @@ __device__ __forceinline__ void write_ray(const rp_ray_out &o, long long id, con
 #pragma unroll
         for (int a = 0; a < 3; ++a) o.end_dir[a * cap + id] = P::get(L.t, a);
     }
-    if (o.path) o.path[id] = L.s;
-    if (o.time) o.time[id] = L.T;
+    if (o.path) o.path[id] = P::sget(L.s);
+    if (o.time) o.time[id] = P::sget(L.T);
     if (o.amp) o.amp[id] = L.A;
     if (o.status) o.status[id] = L.status;
     if (o.generation) o.generation[id] = L.gen;
@@ -598,33 +693,46 @@ __device__ __forceinline__ void write_ray(const rp_ray_out &o, long long id, con
     if (o.n_turn) o.n_turn[id] = L.n_turn;
 }
 
-// Receiver test on the committed chord (state L before the commit -> r1 = r + dr).
+// Receiver test on the committed chord (state L before the commit -> r1 = r + dr): a hit is
+// recorded when the chord enters a sphere; quantities are interpolated linearly along it.
+// Receiver test on the committed chord (state L before the commit -> r1 = r + dr): a hit is
+// recorded when the chord enters a sphere; quantities are interpolated linearly along it.
+// Culling: depth buckets give the candidate range, then a bounding-box test on the compact
+// FP32 copy of the centres; only survivors get the exact chord-sphere intersection.
 template <class P>
-__device__ void receivers_on_chord(const Sinks &sk, const Lane<P> &L, const typename P::R dr[3],
-                                   const typename P::R dt[3], double T1, double s1)
+__device__ __forceinline__ void receivers_on_chord(const Sinks &sk, const Lane<P> &L,
+                                                   const StepParams<P> &sp,
+                                                   const typename P::R dr[3],
+                                                   const typename P::R dt[3], typename P::R dT,
+                                                   typename P::R hc, bool to_max_path)
 {
     typedef typename P::R R;
     const Receivers &rx = sk.rx;
-    double z0 = P::get(L.r, 2);
-    float za = (float)z0, zb = (float)(z0 + (double)dr[2]);
-    float zlo = fminf(za, zb) - rx.r_max - 1e-3f * (1.0f + fabsf(za));
-    float zhi = fmaxf(za, zb) + rx.r_max + 1e-3f * (1.0f + fabsf(za));
-    // first sphere with centre depth >= zlo
-    int lo = 0, hi = rx.n;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (__ldg(&rx.cz[mid]) < zlo)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
+    const float za = P::kFF ? (float)P::base(L.r, 2) : (float)P::get(L.r, 2);
+    const float zb = za + (float)dr[2];
+    const float zlo = fminf(za, zb), zhi = fmaxf(za, zb);
+    if (zhi < rx.z_lo || zlo > rx.z_hi) return;  // no sphere at these depths
+    const int b0 = max(0, min(rx.n_buckets - 1, (int)((zlo - rx.z_lo) * rx.inv_bucket)));
+    const int b1 = max(0, min(rx.n_buckets - 1, (int)((zhi - rx.z_lo) * rx.inv_bucket)));
+    const int lo = __ldg(&rx.bucket[b0]).x;
+    const int hi = __ldg(&rx.bucket[b1]).y;
+    if (lo >= hi) return;
+    const float xa = P::kFF ? (float)P::base(L.r, 0) : (float)P::get(L.r, 0);
+    const float ya = P::kFF ? (float)P::base(L.r, 1) : (float)P::get(L.r, 1);
+    const float xb = xa + (float)dr[0], yb = ya + (float)dr[1];
+    const float bx0 = fminf(xa, xb), bx1 = fmaxf(xa, xb), by0 = fminf(ya, yb),
+                by1 = fmaxf(ya, yb);
     const R zero = R(0);
-    for (int j = lo; j < rx.n && __ldg(&rx.cz[j]) <= zhi; ++j) {
+    for (int j = lo; j < hi; ++j) {
+        const float4 cb = __ldg(&rx.box[j]);  // centre (float) and radius + rounding pad
+        if (cb.x < bx0 - cb.w || cb.x > bx1 + cb.w || cb.y < by0 - cb.w || cb.y > by1 + cb.w ||
+            cb.z < zlo - cb.w || cb.z > zhi + cb.w)
+            continue;
         const SphereC &S = rx.s[j];
         R w[3], d[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            w[a] = P::rel(L.r, a, zero, S.c[a]);  // r0 - c
+            w[a] = P::rel(L.r, a, zero, S.c[a]);   // r0 - c
             R w1 = P::rel(L.r, a, dr[a], S.c[a]);  // r1 - c
             d[a] = P::kFF ? (w1 - w[a]) : dr[a];
         }
@@ -644,10 +752,12 @@ __device__ void receivers_on_chord(const Sinks &sk, const Lane<P> &L, const type
         }
         const long long cap = sk.hits.capacity;
         const double l = (double)lam;
+        const double T0 = P::sget(L.T), s0 = P::sget(L.s);
+        const double ds = to_max_path ? sp.max_path - s0 : (double)hc;
         if (sk.hits.ray) sk.hits.ray[k] = L.id;
         if (sk.hits.receiver) sk.hits.receiver[k] = S.idx;
-        if (sk.hits.time) sk.hits.time[k] = L.T + l * (T1 - L.T);
-        if (sk.hits.path) sk.hits.path[k] = L.s + l * (s1 - L.s);
+        if (sk.hits.time) sk.hits.time[k] = T0 + l * (double)dT;
+        if (sk.hits.path) sk.hits.path[k] = s0 + l * ds;
         if (sk.hits.amp) sk.hits.amp[k] = L.A;
         double dir[3];
 #pragma unroll
@@ -686,6 +796,176 @@ __device__ __forceinline__ void ff_renormalise(PrecF32::V &t)
     for (int a = 0; a < 3; ++a) ff_add(t.hi[a], t.lo[a], t.hi[a] * phi);
 }
 
+// Records a secondary that is not traced (refracted into an absorbing layer, or dropped
+// because the queue is full) at the intersection point.
+template <class P>
+__device__ __forceinline__ void record_secondary(const Sinks &sk, const Lane<P> &L,
+                                                 unsigned long long id, int other, double amp,
+                                                 const double t_refr[3], int status)
+{
+    Lane<P> S = L;
+    S.id = (long long)id;
+    S.parent = L.id;
+    S.seq = L.n_refl;
+    S.gen = L.gen + 1;
+    S.layer = other;
+    S.A = amp;
+    S.status = status;
+    S.n_acc = S.n_rej = S.n_root = S.n_refl = S.n_turn = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) P::set(S.t, a, t_refr[a]);
+    write_ray<P>(sk.out, S.id, S, sk.ctrl);
+}
+
+__device__ __forceinline__ QRec *thread_stack(const Sinks &sk)
+{
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    return sk.stack + tid * kStackDepth;
+}
+
+// Keeps a secondary for later tracing: on the thread's private stack (no atomics, traced by
+// this same thread once its current ray ends) or, when that is full, on the global queue
+// that the next launch drains.
+template <class P>
+__device__ __forceinline__ void queue_secondary(const Sinks &sk, Lane<P> &L,
+                                                unsigned long long id, int other, double amp,
+                                                const double t_refr[3])
+{
+    QRec *slot;
+    if (L.stk < kStackDepth) {
+        slot = thread_stack(sk) + L.stk;
+        ++L.stk;
+    } else {
+        const unsigned long long q = atomicAdd(&sk.ctrl->q_tail, 1ull);
+        if (q >= sk.q_cap) {
+            atomicOr(&sk.ctrl->flags, (unsigned)FLAG_QUEUE_OVERFLOW);
+            record_secondary<P>(sk, L, id, other, amp, t_refr, RP_ST_QUEUE_FULL);
+            return;
+        }
+        slot = &sk.queue[q];
+    }
+    QRec &Q = *slot;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        Q.r[a] = P::get(L.r, a);
+        Q.t[a] = t_refr[a];
+    }
+    Q.T = P::sget(L.T);
+    Q.s = P::sget(L.s);
+    Q.A = amp;
+    Q.A0 = L.A0;
+    Q.id = (long long)id;
+    Q.parent = L.id;
+    Q.h = (double)L.h;
+    Q.layer = other;
+    Q.gen = L.gen + 1;
+    Q.seq = L.n_refl;
+}
+
+// Boundary split at the horizontal plane between the ray's layer and `other` (Sec. 2,
+// boundary module): the ray is reflected and continues with A r; a secondary with the
+// refracted direction and A tau is cast from the intersection point unless the incidence is
+// beyond the critical angle, the generation cap is reached, or A tau is already below the
+// amplitude threshold (such a ray would be discarded at once).
+template <class P>
+__device__ __forceinline__ void split_at_plane(const MediumLayered &med, Lane<P> &L,
+                                               const StepParams<P> &sp, const Sinks &sk, int ev)
+{
+    const int other = (ev == EV_TOP) ? L.layer - 1 : L.layer + 1;
+    const double nz = (ev == EV_TOP) ? 1.0 : -1.0;  // normal toward the incident side
+    const bool spawn_allowed = L.gen < sp.max_generation;
+    const int pk = (ev == EV_TOP) ? L.layer : L.layer + 1;  // plane index
+    // n on the ray's side (n1) and on the far side (n2) of the plane, evaluated on the host
+    const double n1d = (ev == EV_TOP) ? med.n_below[pk] : med.n_above[pk];
+    const double n2d = (ev == EV_TOP) ? med.n_above[pk] : med.n_below[pk];
+    if constexpr (!P::kFF) {
+        // FP64 path: the same operations as the FP64 reference
+        const double n1 = n1d, n2 = n2d;
+        const double nrm[3] = {0.0, 0.0, nz};
+        double t[3] = {P::get(L.t, 0), P::get(L.t, 1), P::get(L.t, 2)};
+        double t_refl[3], t_refr[3], rr, tau;
+        bool tir = split_dirs(t, nrm, n1, n2, sp.polarization, t_refl, t_refr, rr, tau);
+        const double amp = L.A * tau;
+        const bool weak = sp.use_min_amp && fabs(amp) < sp.min_amp * fabs(L.A0);
+        if (!tir && spawn_allowed && !weak) {
+            const unsigned long long id = atomicAdd(&sk.ctrl->out_count, 1ull);
+            atomicAdd(&sk.ctrl->n_secondary, 1ull);
+            if (med.L[other].absorb)
+                record_secondary<P>(sk, L, id, other, amp, t_refr, RP_ST_TRANSMITTED);
+            else
+                queue_secondary<P>(sk, L, id, other, amp, t_refr);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) P::set(L.t, a, t_refl[a]);
+        L.A *= rr;
+    } else {
+        // FP32-mixed path: incidence geometry and Fresnel factors in FP32 (for a horizontal
+        // plane the reflection only flips t_z, exactly); the direction of a traced
+        // secondary is built in FP64
+        const float n1 = (ev == EV_TOP) ? med.n_below_f[pk] : med.n_above_f[pk];
+        const float n2 = (ev == EV_TOP) ? med.n_above_f[pk] : med.n_below_f[pk];
+        const float tz = L.t.hi[2] + L.t.lo[2];
+        float cos_i = -(tz * (float)nz);
+        const bool toward = cos_i > 0.0f;
+        cos_i = fmaxf(cos_i, 0.0f);
+        const float eta = n1 / n2;
+        const float sin2_t = eta * eta * (1.0f - cos_i * cos_i);
+        float rr = 1.0f, tau = 0.0f;
+        const bool tir = sin2_t > 1.0f;
+        float cos_t = 0.0f;
+        if (!tir) {
+            cos_t = sqrtf(1.0f - sin2_t);
+            const float rs = (n1 * cos_i - n2 * cos_t) / (n1 * cos_i + n2 * cos_t);
+            const float ts = 2.0f * n1 * cos_i / (n1 * cos_i + n2 * cos_t);
+            const float rp = (n2 * cos_i - n1 * cos_t) / (n2 * cos_i + n1 * cos_t);
+            const float tp = 2.0f * n1 * cos_i / (n2 * cos_i + n1 * cos_t);
+            if (sp.polarization == RP_POL_S) {
+                rr = rs;
+                tau = ts;
+            } else if (sp.polarization == RP_POL_P) {
+                rr = rp;
+                tau = tp;
+            } else {
+                const float Rr = 0.5f * (rs * rs + rp * rp);
+                rr = sqrtf(Rr);
+                tau = sqrtf(1.0f - Rr);
+            }
+        }
+        const double amp = L.A * (double)tau;
+        const bool weak = sp.use_min_amp && fabs(amp) < sp.min_amp * fabs(L.A0);
+        if (!tir && spawn_allowed && !weak) {
+            const unsigned long long id = atomicAdd(&sk.ctrl->out_count, 1ull);
+            atomicAdd(&sk.ctrl->n_secondary, 1ull);
+            double t_refr[3];
+            if (med.L[other].absorb) {
+                const float tf[3] = {eta * L.t.hi[0], eta * L.t.hi[1],
+                                     eta * tz + (eta * cos_i - cos_t) * (float)nz};
+                const float q = sqrtf(tf[0] * tf[0] + tf[1] * tf[1] + tf[2] * tf[2]);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) t_refr[a] = (double)(tf[a] / q);
+                record_secondary<P>(sk, L, id, other, amp, t_refr, RP_ST_TRANSMITTED);
+            } else {
+                // traced secondary: its direction from Snell's law in FP64 (vector form,
+                // horizontal plane), so that it starts as accurately as in the FP64 path
+                const double t0 = P::get(L.t, 0), t1 = P::get(L.t, 1), t2 = P::get(L.t, 2);
+                const double ci = fmax(-(t2 * nz), 0.0);
+                const double etad = n1d / n2d;
+                const double s2 = etad * etad * (1.0 - ci * ci);
+                const double ct = sqrt(fmax(1.0 - s2, 0.0));
+                t_refr[0] = etad * t0;
+                t_refr[1] = etad * t1;
+                t_refr[2] = etad * t2 + (etad * ci - ct) * nz;
+                queue_secondary<P>(sk, L, id, other, amp, t_refr);
+            }
+        }
+        if (toward) {
+            L.t.hi[2] = -L.t.hi[2];
+            L.t.lo[2] = -L.t.lo[2];
+        }
+        L.A *= (double)rr;
+    }
+}
+
 // Commit of the candidate state (r + dr, t + dt, T + dT) after a step of length hc; ev is the
 // event the step landed on (EV_NONE: an ordinary accepted step).  Performs receivers, split,
 // stop and break conditions.  Returns true if the ray finished.
@@ -712,9 +992,8 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
         else
             dr[2] -= off;
     }
-    const double T1 = L.T + (double)dT;
-    const double s1 = (L.last && ev == EV_NONE) ? sp.max_path : L.s + (double)hc;
-    if (sk.has_rx) receivers_on_chord<P>(sk, L, dr, dt, T1, s1);
+    const bool to_max_path = L.last && ev == EV_NONE;
+    if (sk.has_rx) receivers_on_chord<P>(sk, L, sp, dr, dt, dT, hc, to_max_path);
     {
         R tz1 = P::base(L.t, 2) + dt[2];
         if ((P::base(L.t, 2) > R(0)) != (tz1 > R(0))) ++L.n_turn;
@@ -745,97 +1024,39 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
         L.t.v[1] /= q;
         L.t.v[2] /= q;
     }
-    L.T = T1;
-    L.s = s1;
+    P::sadd(L.T, dT);
+    if (to_max_path)
+        P::sset(L.s, sp.max_path);
+    else
+        P::sadd(L.s, hc);
     ++L.n_acc;
     L.h = L.h_next;
 
+    bool split = false;
     if (ev == EV_TOP || ev == EV_BOTTOM) {
         if constexpr (is_layered_v<M>) {
-            const int other = (ev == EV_TOP) ? L.layer - 1 : L.layer + 1;
-            const double zb = P::get(L.r, 2);
-            double n1, n2, dd;
-            layer_eval_d(med, L.layer, zb, n1, dd);
-            layer_eval_d(med, other, zb, n2, dd);
-            const double nrm[3] = {0.0, 0.0, (ev == EV_TOP) ? 1.0 : -1.0};
-            double t[3] = {P::get(L.t, 0), P::get(L.t, 1), P::get(L.t, 2)};
-            double t_refl[3], t_refr[3], rr, tau;
-            bool tir = split_dirs(t, nrm, n1, n2, sp.polarization, t_refl, t_refr, rr, tau);
-            if (!tir && L.gen < sp.max_generation) {
-                const unsigned long long id = atomicAdd(&sk.ctrl->out_count, 1ull);
-                atomicAdd(&sk.ctrl->n_secondary, 1ull);
-                if (med.L[other].absorb) {
-                    // refracted into an absorbing layer: recorded, not traced
-                    Lane<P> S = L;
-                    S.id = (long long)id;
-                    S.parent = L.id;
-                    S.seq = L.nsplit;
-                    S.gen = L.gen + 1;
-                    S.layer = other;
-                    S.A = L.A * tau;
-                    S.status = RP_ST_TRANSMITTED;
-                    S.n_acc = S.n_rej = S.n_root = S.n_refl = S.n_turn = 0;
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) P::set(S.t, a, t_refr[a]);
-                    write_ray<P>(sk.out, S.id, S, sk.ctrl);
-                } else {
-                    const unsigned long long q = atomicAdd(&sk.ctrl->q_tail, 1ull);
-                    if (q < sk.q_cap) {
-                        QRec &Q = sk.queue[q];
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            Q.r[a] = P::get(L.r, a);
-                            Q.t[a] = t_refr[a];
-                        }
-                        Q.T = L.T;
-                        Q.s = L.s;
-                        Q.A = L.A * tau;
-                        Q.A0 = L.A0;
-                        Q.id = (long long)id;
-                        Q.parent = L.id;
-                        Q.h = (double)L.h;
-                        Q.layer = other;
-                        Q.gen = L.gen + 1;
-                        Q.seq = L.nsplit;
-                    } else {
-                        atomicOr(&sk.ctrl->flags, (unsigned)FLAG_QUEUE_OVERFLOW);
-                        Lane<P> S = L;
-                        S.id = (long long)id;
-                        S.parent = L.id;
-                        S.seq = L.nsplit;
-                        S.gen = L.gen + 1;
-                        S.layer = other;
-                        S.A = L.A * tau;
-                        S.status = RP_ST_QUEUE_FULL;
-                        S.n_acc = S.n_rej = S.n_root = S.n_refl = S.n_turn = 0;
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) P::set(S.t, a, t_refr[a]);
-                        write_ray<P>(sk.out, S.id, S, sk.ctrl);
-                    }
-                }
-            }
-            ++L.nsplit;
+            split_at_plane<P>(med, L, sp, sk, ev);
             ++L.n_refl;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) P::set(L.t, a, t_refl[a]);
-            L.A *= rr;
+            split = true;
         }
     } else if (ev == EV_STOP) {
         L.status = RP_ST_REACHED_STOP;
         return true;
     }
-    if (L.last && ev == EV_NONE) {
+    // break conditions, in the reference's order; |A| changes only at splits
+    if (to_max_path) {
         L.status = RP_ST_MAX_PATH;
-    } else if (sp.max_time > 0.0 && L.T >= sp.max_time) {
+    } else if (sp.use_max_time && P::sdiff(L.T, sp.mt) >= R(0)) {
         L.status = RP_ST_MAX_TIME;
-    } else if (sp.min_amp > 0.0 && fabs(L.A) < sp.min_amp * fabs(L.A0)) {
+    } else if (split && sp.use_min_amp && fabs(L.A) < sp.min_amp * fabs(L.A0)) {
         L.status = RP_ST_MIN_AMP;
     } else if constexpr (!is_layered_v<M>) {
         bool inside = true;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            double v = P::get(L.r, a);
-            inside = inside && !(v < med.org[a] || v > med.hi[a]);
+            const R zero = R(0);
+            inside = inside && !(P::rel(L.r, a, zero, med.lo_c[a]) < R(0) ||
+                                 P::rel(L.r, a, zero, med.hi_c[a]) > R(0));
         }
         if (!inside) L.status = RP_ST_LEFT_DOMAIN;
     }
@@ -870,7 +1091,7 @@ __device__ __forceinline__ bool advance(const M &med, Lane<P> &L, const StepPara
     ck_step<P, M>(med, L.layer, sp.rhs_form, L.r, L.t, hc, dr, dt, dT, er, et);
 
     if (L.mode == MODE_NORMAL) {
-        const R e = (er > et ? er : et) / sp.tol;
+        const R e = (er > et ? er : et) * sp.inv_tol;
         if (!(e <= R(1)) && hc > sp.h_min) {
             ++L.n_rej;
             R fac = R(0.9) * P::pow_(e, R(-0.25));

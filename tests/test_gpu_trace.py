@@ -108,23 +108,60 @@ def test_batched_subset_fp64_rays_and_hits(rp):
         assert abs(a[2] - b[2]) <= 10 * cfg["params"]["tol"] * b[2] + 1e-15
 
 
+def _tilt(d, angle, seed):
+    """Rotate every direction by `angle` rad about a random axis perpendicular to it."""
+    rng = np.random.default_rng(seed)
+    d = d / np.linalg.norm(d, axis=0)
+    a = rng.standard_normal(d.shape)
+    a -= (a * d).sum(0) * d
+    a /= np.linalg.norm(a, axis=0)
+    return np.cos(angle) * d + np.sin(angle) * a
+
+
 def test_fp32_mixed_vs_fp64(rp):
+    """FP32-mixed against FP64 on 20,000 primaries of the batched workload.
+
+    Rays whose FP64 result itself moves by more than 1 mm / 0.01 ns when the launch direction
+    is tilted by 1e-7 rad (grazing incidence, critical angles: the problem, not the
+    arithmetic, is ill-conditioned there) are counted separately; every other ray must be
+    within 1 mm / 0.01 ns."""
     cfg = W.batched()
-    rays = W.subsample(cfg["rays"], np.arange(20000))
-    g64 = gpu_rays(_run(rp, cfg["medium"], cfg["params"], rays, precision="fp64"))
-    g32 = gpu_rays(_run(rp, cfg["medium"], cfg["params"], rays, precision="fp32"))
+    pos, d, a = W.subsample(cfg["rays"], np.arange(20000))
+    g64 = gpu_rays(_run(rp, cfg["medium"], cfg["params"], (pos, d, a), precision="fp64"))
+    g32 = gpu_rays(_run(rp, cfg["medium"], cfg["params"], (pos, d, a), precision="fp32"))
+    gpt = gpu_rays(_run(rp, cfg["medium"], cfg["params"], (pos, _tilt(d, 1e-7, 9), a),
+                        precision="fp64"))
     gi, oi, only32, only64 = match(g32, g64)
     n = max(len(g32["path"]), len(g64["path"]))
     assert len(only32) + len(only64) <= 0.002 * n
     ok = g32["status"][gi] == g64["status"][oi]
     assert ok.mean() > 0.998
-    dp, dd, ds, dT, dA = errors(g32, g64, gi[ok], oi[ok])
+    gi, oi = gi[ok], oi[ok]
+    dp, dd, ds, dT, dA = errors(g32, g64, gi, oi)
+    # sensitivity of the FP64 result to a 1e-7 rad launch tilt
+    pi, qi, _, _ = match(gpt, g64)
+    sens = np.ones(len(g64["path"]), dtype=bool)
+    sp, _, _, sT, _ = errors(gpt, g64, pi, qi)
+    same_status = gpt["status"][pi] == g64["status"][qi]
+    sens[qi] = ~same_status | (sp > 1e-3) | (sT > 1e-11)
+    s_ok = ~sens[oi]
     good = (dp <= 1e-3) & (dT <= 1e-11)
-    print("fp32 vs fp64: p99 |dr| %.3e m, p99 |dT| %.3e s, within 1 mm / 0.01 ns: %.5f" % (
-        np.quantile(dp, 0.99), np.quantile(dT, 0.99), good.mean()))
+    print("fp32 vs fp64: %d rays, p50/p99/max |dr| %.2e/%.2e/%.2e m, p99 |dT| %.2e s; "
+          "within 1 mm / 0.01 ns: all %.5f, well-conditioned %.5f (%.4f of rays sensitive)" % (
+              len(gi), np.median(dp), np.quantile(dp, 0.99), dp.max(), np.quantile(dT, 0.99),
+              good.mean(), good[s_ok].mean(), 1 - s_ok.mean()))
+    bad = ~good & s_ok
+    if bad.any():
+        j = np.nonzero(bad)[0][:10]
+        for k in j:
+            print("  bad: gen %d refl %d acc %d/%d rej %d/%d path %.1f |dr| %.3e |dT| %.3e" % (
+                g64["generation"][oi[k]], g64["n_refl"][oi[k]], g32["n_acc"][gi[k]],
+                g64["n_acc"][oi[k]], g32["n_rej"][gi[k]], g64["n_rej"][oi[k]],
+                g64["path"][oi[k]], dp[k], dT[k]))
     assert np.quantile(dp, 0.99) <= 1e-3
     assert np.quantile(dT, 0.99) <= 1e-11
-    assert good.mean() >= 0.995
+    assert 1 - s_ok.mean() <= 0.05
+    assert good[s_ok].mean() >= 0.999
 
 
 def test_grid_medium_fp64_and_fp32(rp):
