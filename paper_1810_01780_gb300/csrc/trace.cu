@@ -39,14 +39,17 @@ __device__ __forceinline__ long long claim_index(unsigned long long *counter)
 }
 
 template <class P, class M>
-__device__ __forceinline__ void lane_reset(Lane<P> &L, const StepParams<P> &sp, const PlaneC &stop)
+__device__ __forceinline__ void lane_reset(Lane<P> &L, const M &med, const StepParams<P> &sp,
+                                           const PlaneC &stop)
 {
+    load_layer<P>(L.lc, med, L.layer);
     L.mode = MODE_NORMAL;
     L.ev = EV_NONE;
     L.side = 0;
     L.it = 0;
     L.n_acc = L.n_rej = L.n_root = L.n_refl = L.n_turn = L.root_fail = 0;
     L.status = RP_ST_ALIVE;
+    L.pend = 0;
     L.stop = stop;
     init_stop(L, sp);
     set_trial(L, sp);
@@ -77,8 +80,8 @@ __device__ __forceinline__ void prefetch_ray(const Sinks &sk, const WaveIn &in, 
 }
 
 template <class P, class M>
-__device__ __forceinline__ void load_record(Lane<P> &L, const StepParams<P> &sp, const QRec &Q,
-                                            const PlaneC &stop)
+__device__ __forceinline__ void load_record(Lane<P> &L, const M &med, const StepParams<P> &sp,
+                                            const QRec &Q, const PlaneC &stop)
 {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -95,7 +98,7 @@ __device__ __forceinline__ void load_record(Lane<P> &L, const StepParams<P> &sp,
     L.gen = Q.gen;
     L.seq = Q.seq;
     L.layer = Q.layer;
-    lane_reset<P, M>(L, sp, stop);
+    lane_reset<P, M>(L, med, sp, stop);
 }
 
 // Next ray of this wave for the calling lane; false when the wave's input is exhausted.
@@ -110,7 +113,7 @@ __device__ bool next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, cons
         if (L.stk > 0) {
             // depth first: the secondaries this thread cast itself come before new input
             --L.stk;
-            load_record<P, M>(L, sp, thread_stack(sk)[L.stk], in.stop);
+            load_record<P, M>(L, med, sp, thread_stack(sk)[L.stk], in.stop);
             return true;
         }
         const long long k = ahead;
@@ -118,7 +121,7 @@ __device__ bool next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, cons
         ahead = claim_index(&sk.ctrl->claim[wave]);
         if (ahead < (long long)count) prefetch_ray(sk, in, wave, base, ahead);
         if (wave != 0) {
-            load_record<P, M>(L, sp, sk.queue[base + k], in.stop);
+            load_record<P, M>(L, med, sp, sk.queue[base + k], in.stop);
             return true;
         }
         const long long n = in.n;
@@ -145,7 +148,7 @@ __device__ bool next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, cons
             const float q2 = L.t.hi[0] * L.t.hi[0] + L.t.hi[1] * L.t.hi[1] + L.t.hi[2] * L.t.hi[2];
             const bool pos_ok = isfinite(L.r.hi[0]) && isfinite(L.r.hi[1]) && isfinite(L.r.hi[2]);
             if (!(q2 > 0.0f) || !isfinite(q2) || !pos_ok) {
-                lane_reset<P, M>(L, sp, in.stop);
+                lane_reset<P, M>(L, med, sp, in.stop);
                 L.status = RP_ST_BAD_INPUT;
                 atomicOr(&sk.ctrl->flags, (unsigned)FLAG_BAD_INPUT);
                 write_ray<P>(sk.out, L.id, L, sk.ctrl);
@@ -180,7 +183,7 @@ __device__ bool next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, cons
             if (!(q2 > 0.0) || !isfinite(q2) || !pos_ok) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) P::set(L.t, a, t[a]);
-                lane_reset<P, M>(L, sp, in.stop);
+                lane_reset<P, M>(L, med, sp, in.stop);
                 L.status = RP_ST_BAD_INPUT;
                 atomicOr(&sk.ctrl->flags, (unsigned)FLAG_BAD_INPUT);
                 write_ray<P>(sk.out, L.id, L, sk.ctrl);
@@ -191,10 +194,13 @@ __device__ bool next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, cons
 #pragma unroll
             for (int a = 0; a < 3; ++a) P::set(L.t, a, t[a] / q);
         }
-        lane_reset<P, M>(L, sp, in.stop);
+        lane_reset<P, M>(L, med, sp, in.stop);
         return true;
     }
 }
+
+constexpr int kServiceBatch = 4;
+constexpr unsigned int kServicePeriod = 4;  // power of two
 
 template <class P, class M>
 __global__ void __launch_bounds__(128, P::kMinBlocks) k_trace_wave(const M med, const StepParams<P> sp,
@@ -211,18 +217,39 @@ __global__ void __launch_bounds__(128, P::kMinBlocks) k_trace_wave(const M med, 
     L.stk = 0;
     unsigned int acc = 0, rej = 0, root = 0;
     long long ahead = claim_index(&sk.ctrl->claim[wave]);
-    bool have = next_ray<P, M>(L, med, sp, sk, in, wave, base, count, ahead);
-    // Warp-synchronous loop: the lanes of a warp re-converge at the top of every iteration,
-    // so the Runge-Kutta step always runs with every lane that still has a ray; a lane whose
-    // input is exhausted idles until the whole warp is done.
-    while (__any_sync(0xffffffffu, have)) {
+    bool active = next_ray<P, M>(L, med, sp, sk, in, wave, base, count, ahead);
+    bool done = false;
+    unsigned int iter = 0;
+    // Warp-synchronous loop.  Every iteration runs one Runge-Kutta step on each lane whose
+    // ray is stepping.  The rare, long code paths -- a boundary split with its secondary,
+    // writing a finished ray and loading the next one -- are parked and serviced together,
+    // when kServiceBatch lanes wait, every kServicePeriod iterations, or when no lane can
+    // step; so they run seldom, with many lanes at once, and stay out of the hot loop's
+    // instruction working set.
+    while (__any_sync(0xffffffffu, active || done)) {
         __syncwarp();
-        if (have && advance<P, M>(med, L, sp, sk)) {
-            acc += (unsigned int)L.n_acc;
-            rej += (unsigned int)L.n_rej;
-            root += (unsigned int)L.n_root;
-            write_ray<P>(sk.out, L.id, L, sk.ctrl);
-            have = next_ray<P, M>(L, med, sp, sk, in, wave, base, count, ahead);
+        const bool stepping = active && L.pend == 0;
+        if (stepping && advance<P, M>(med, L, sp, sk)) {
+            active = false;
+            done = true;
+        }
+        const bool waits = done || (active && L.pend != 0);
+        const unsigned int wait = __ballot_sync(0xffffffffu, waits);
+        const unsigned int step_mask = __ballot_sync(0xffffffffu, active && L.pend == 0);
+        if (wait != 0u && (__popc(wait) >= kServiceBatch ||
+                           ((++iter) & (kServicePeriod - 1)) == 0u || step_mask == 0u)) {
+            if (active && L.pend != 0 && finish_split<P>(med, L, sp, sk)) {
+                active = false;
+                done = true;
+            }
+            if (done) {
+                acc += (unsigned int)L.n_acc;
+                rej += (unsigned int)L.n_rej;
+                root += (unsigned int)L.n_root;
+                write_ray<P>(sk.out, L.id, L, sk.ctrl);
+                done = false;
+                active = next_ray<P, M>(L, med, sp, sk, in, wave, base, count, ahead);
+            }
         }
     }
     // per-warp totals; no block-wide barrier, so finished warps simply retire
@@ -385,9 +412,10 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
 
     // receivers: sort by centre depth on the host (tiny), upload with the workspace
     std::vector<SphereC> spheres(n_rx);
-    std::vector<int2> buckets;
-    std::vector<float4> boxes(n_rx);
-    float rz_lo = 0.0f, rz_hi = -1.0f, inv_bucket = 1.0f;
+    std::vector<int2> cells;
+    std::vector<int> items;
+    float g_org[3] = {0, 0, 0}, g_hi[3] = {0, 0, 0}, g_inv = 1.0f;
+    int g_dims[3] = {1, 1, 1};
     if (n_rx) {
         std::vector<double> c(3 * (size_t)n_rx), rad(n_rx);
         RP_CUDA_TRY(cudaMemcpyAsync(c.data(), rx->center, c.size() * sizeof(double),
@@ -395,48 +423,58 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
         RP_CUDA_TRY(cudaMemcpyAsync(rad.data(), rx->radius, rad.size() * sizeof(double),
                                     cudaMemcpyDeviceToHost, st));
         RP_CUDA_TRY(cudaStreamSynchronize(st));
-        std::vector<int> order(n_rx);
-        for (int j = 0; j < n_rx; ++j) order[j] = j;
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int a, int b) { return c[3 * a + 2] < c[3 * b + 2]; });
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, r_max = 0.0;
         for (int j = 0; j < n_rx; ++j) {
-            const int o = order[j];
-            if (!(rad[o] > 0.0)) {
+            if (!(rad[j] > 0.0)) {
                 set_error("rp_trace: receiver radius must be > 0");
                 return RP_ERR_INVALID_ARG;
             }
-            for (int a = 0; a < 3; ++a) spheres[j].c[a] = plane_const(c[3 * o + a]);
-            spheres[j].R = rad[o];
-            spheres[j].Rf = (float)rad[o];
-            spheres[j].idx = o;
+            for (int a = 0; a < 3; ++a) {
+                spheres[j].c[a] = plane_const(c[3 * j + a]);
+                lo[a] = std::min(lo[a], c[3 * j + a]);
+                hi[a] = std::max(hi[a], c[3 * j + a]);
+            }
+            spheres[j].R = rad[j];
+            spheres[j].Rf = (float)rad[j];
+            spheres[j].idx = j;
+            r_max = std::max(r_max, rad[j]);
         }
-        // depth buckets: bucket b covers [rz_lo + b w, rz_lo + (b + 1) w); its sphere range
-        // holds every sphere whose padded slab overlaps it (spheres sorted by depth, so the
-        // range is contiguous once slabs are ordered by their lower edge; the padded slab
-        // uses the largest radius so that lower and upper edges are both monotonic)
-        double r_max = 0.0;
-        for (int j = 0; j < n_rx; ++j) r_max = std::max(r_max, spheres[j].R);
-        // pad: largest radius plus 1 mm, far above the FP32 rounding of a depth (< 1e-4 m)
-        const double pad = r_max + 1e-3;
-        for (int j = 0; j < n_rx; ++j)
-            boxes[j] = make_float4((float)spheres[j].c[0].d, (float)spheres[j].c[1].d,
-                                   (float)spheres[j].c[2].d, (float)(spheres[j].R + 1e-3));
-        const double zlo = spheres[0].c[2].d - pad, zhi = spheres[n_rx - 1].c[2].d + pad;
-        const int nb = (int)std::min<double>(4096.0, std::max(1.0, std::ceil((zhi - zlo) / 1.0)));
-        const double w = (zhi - zlo) / nb;
-        buckets.resize(nb);
-        int first = 0, end = 0;
-        for (int b = 0; b < nb; ++b) {
-            const double b_lo = zlo + w * b - 1e-6 * (1.0 + std::fabs(zlo)),
-                         b_hi = zlo + w * (b + 1) + 1e-6 * (1.0 + std::fabs(zhi));
-            while (first < n_rx && spheres[first].c[2].d + pad < b_lo) ++first;
-            end = std::max(end, first);
-            while (end < n_rx && spheres[end].c[2].d - pad <= b_hi) ++end;
-            buckets[b] = make_int2(first, end);
+        // inflation: radius + half the longest chord + a pad far above FP32 rounding
+        double amax = 0.0;
+        for (int a = 0; a < 3; ++a) amax = std::max(amax, std::max(std::fabs(lo[a]), std::fabs(hi[a])));
+        const double infl = r_max + 0.5 * p->h_max + 1e-2 + 1e-6 * amax;
+        double ext = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            lo[a] -= infl;
+            hi[a] += infl;
+            ext = std::max(ext, hi[a] - lo[a]);
         }
-        rz_lo = (float)zlo;
-        rz_hi = (float)zhi;
-        inv_bucket = (float)(1.0 / w);
+        const double cell = std::max(2.0 * infl, ext / 64.0);
+        for (int a = 0; a < 3; ++a) {
+            g_dims[a] = std::max(1, std::min(64, (int)std::ceil((hi[a] - lo[a]) / cell)));
+            g_org[a] = (float)lo[a];
+            g_hi[a] = (float)(lo[a] + cell * g_dims[a]);
+        }
+        g_inv = (float)(1.0 / cell);
+        const size_t n_cells = (size_t)g_dims[0] * g_dims[1] * g_dims[2];
+        std::vector<std::vector<int>> lists(n_cells);
+        for (int j = 0; j < n_rx; ++j) {
+            int i0[3], i1[3];
+            for (int a = 0; a < 3; ++a) {
+                i0[a] = std::max(0, (int)std::floor((c[3 * j + a] - infl - lo[a]) / cell));
+                i1[a] = std::min(g_dims[a] - 1, (int)std::floor((c[3 * j + a] + infl - lo[a]) / cell));
+            }
+            for (int z = i0[2]; z <= i1[2]; ++z)
+                for (int y = i0[1]; y <= i1[1]; ++y)
+                    for (int x = i0[0]; x <= i1[0]; ++x)
+                        lists[((size_t)z * g_dims[1] + y) * g_dims[0] + x].push_back(j);
+        }
+        cells.resize(n_cells);
+        for (size_t q = 0; q < n_cells; ++q) {
+            cells[q].x = (int)items.size();
+            items.insert(items.end(), lists[q].begin(), lists[q].end());
+            cells[q].y = (int)items.size();
+        }
     }
 
     const int block = 128;
@@ -447,8 +485,8 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     const size_t off_q = align_up(sizeof(Ctrl));
     const size_t off_s = off_q + align_up(sizeof(QRec) * (size_t)std::max(q_cap, 1LL));
     const size_t off_z = off_s + align_up(sizeof(SphereC) * (size_t)std::max(n_rx, 1));
-    const size_t off_b = off_z + align_up(sizeof(int2) * std::max<size_t>(buckets.size(), 1));
-    const size_t off_k = off_b + align_up(sizeof(float4) * (size_t)std::max(n_rx, 1));
+    const size_t off_b = off_z + align_up(sizeof(int2) * std::max<size_t>(cells.size(), 1));
+    const size_t off_k = off_b + align_up(sizeof(int) * std::max<size_t>(items.size(), 1));
     const size_t total = off_k + align_up(sizeof(QRec) * (size_t)threads * kStackDepth);
 
     Workspace &ws = workspace(dev);
@@ -467,22 +505,27 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     if (hits) sk.hits = *hits;
     sk.has_rx = n_rx > 0;
     sk.rx.s = (const SphereC *)(base + off_s);
-    sk.rx.bucket = (const int2 *)(base + off_z);
-    sk.rx.box = (const float4 *)(base + off_b);
+    sk.rx.cell = (const int2 *)(base + off_z);
+    sk.rx.items = (const int *)(base + off_b);
     sk.rx.n = n_rx;
-    sk.rx.n_buckets = (int)buckets.size();
-    sk.rx.z_lo = rz_lo;
-    sk.rx.z_hi = rz_hi;
-    sk.rx.inv_bucket = inv_bucket;
+    sk.rx.nx = g_dims[0];
+    sk.rx.ny = g_dims[1];
+    sk.rx.nz = g_dims[2];
+    for (int a = 0; a < 3; ++a) {
+        sk.rx.org[a] = g_org[a];
+        sk.rx.hi[a] = g_hi[a];
+    }
+    sk.rx.inv_cell = g_inv;
 
     RP_CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
     if (n_rx) {
         RP_CUDA_TRY(cudaMemcpyAsync(base + off_s, spheres.data(), sizeof(SphereC) * n_rx,
                                     cudaMemcpyHostToDevice, st));
-        RP_CUDA_TRY(cudaMemcpyAsync(base + off_z, buckets.data(), sizeof(int2) * buckets.size(),
+        RP_CUDA_TRY(cudaMemcpyAsync(base + off_z, cells.data(), sizeof(int2) * cells.size(),
                                     cudaMemcpyHostToDevice, st));
-        RP_CUDA_TRY(cudaMemcpyAsync(base + off_b, boxes.data(), sizeof(float4) * n_rx,
-                                    cudaMemcpyHostToDevice, st));
+        if (!items.empty())
+            RP_CUDA_TRY(cudaMemcpyAsync(base + off_b, items.data(), sizeof(int) * items.size(),
+                                        cudaMemcpyHostToDevice, st));
     }
     k_init_ctrl<<<1, 1, 0, st>>>(ctrl, in->n);
 

@@ -265,35 +265,72 @@ __device__ __forceinline__ void layer_eval_d(const MediumLayered &m, int k, doub
     dndz = L.gcoef * e;
 }
 
+// The constants of the layer a ray travels in and of the two planes bounding it, held in
+// registers for the ray's whole life (a ray never changes layer: crossing a plane casts a
+// secondary in the other layer).  Lanes of a warp in different layers then never read the
+// medium description with divergent indices in the per-step loop.
+template <class P>
+struct LayerR {
+    typename P::R n0, mdn, off, minv, gcoef;  // n = n0 + mdn e + off, dn/dz = gcoef e,
+                                              // e = exp(minv z); constant layer: mdn = minv = 0
+    PlaneC top, bot;                          // planes above / below (+-1e30 when absent)
+};
+
+template <class P>
+__device__ __forceinline__ void load_layer(LayerR<P> &c, const MediumLayered &m, int k)
+{
+    const LayerC &L = m.L[k];
+    if constexpr (P::kFF) {
+        c.n0 = L.n0f;
+        c.mdn = L.has_exp ? -L.dnf : 0.0f;
+        c.off = L.offf;
+        c.minv = L.has_exp ? -L.inv_z0f : 0.0f;
+        c.gcoef = L.has_exp ? L.gcoeff : 0.0f;
+    } else {
+        c.n0 = L.n0;
+        c.mdn = L.has_exp ? -L.dn : 0.0;
+        c.off = L.off;
+        c.minv = L.has_exp ? -L.inv_z0 : 0.0;
+        c.gcoef = L.has_exp ? L.gcoef : 0.0;
+    }
+    PlaneC none_top, none_bot;
+    none_top.d = -1e30;
+    none_top.hi = -1e30f;
+    none_top.lo = 0.0f;
+    none_bot.d = 1e30;
+    none_bot.hi = 1e30f;
+    none_bot.lo = 0.0f;
+    c.top = k > 0 ? m.top[k] : none_top;
+    c.bot = k + 1 < m.n_layers ? m.top[k + 1] : none_bot;
+}
+template <class P>
+__device__ __forceinline__ void load_layer(LayerR<P> &, const MediumGrid &, int)
+{
+}
+
 // Layered analytic medium: only the stage depth matters.
 template <class P>
-__device__ __forceinline__ void medium_eval(const MediumLayered &m, int layer,
+__device__ __forceinline__ void medium_eval(const MediumLayered &, const LayerR<P> &c,
                                             const typename P::R r[3], typename P::R &n,
                                             typename P::R g[3])
 {
     typedef typename P::R R;
-    const LayerC &L = m.L[layer];
     g[0] = R(0);
     g[1] = R(0);
-    if (!L.has_exp) {
-        n = P::kFF ? R(L.n0f + L.offf) : R(L.n0 + L.off);
-        g[2] = R(0);
-        return;
-    }
     if constexpr (P::kFF) {
-        float e = expf(-r[2] * L.inv_z0f);
-        n = __fadd_rn(__fmaf_rn(-L.dnf, e, L.n0f), L.offf);
-        g[2] = L.gcoeff * e;
+        const float e = expf(r[2] * c.minv);
+        n = __fadd_rn(__fmaf_rn(c.mdn, e, c.n0), c.off);
+        g[2] = c.gcoef * e;
     } else {
-        double e = exp(-r[2] * L.inv_z0);
-        n = L.n0 - L.dn * e + L.off;
-        g[2] = L.gcoef * e;
+        const double e = exp(r[2] * c.minv);
+        n = c.n0 + c.mdn * e + c.off;
+        g[2] = c.gcoef * e;
     }
 }
 
 // Gridded medium: trilinear interpolation of the four FP32 node channels, clamped to the box.
 template <class P>
-__device__ __forceinline__ void medium_eval(const MediumGrid &m, int /*layer*/,
+__device__ __forceinline__ void medium_eval(const MediumGrid &m, const LayerR<P> &,
                                             const typename P::R r[3], typename P::R &n,
                                             typename P::R g[3])
 {
@@ -357,7 +394,7 @@ __device__ __forceinline__ void medium_eval(const MediumGrid &m, int /*layer*/,
 // Sums run over the stages in ascending order, as in the FP64 reference.
 // ---------------------------------------------------------------------------------------
 template <class P, class M>
-__device__ __forceinline__ void ck_step(const M &med, int layer, int form,
+__device__ __forceinline__ void ck_step(const M &med, const LayerR<P> &lc, int form,
                                         const typename P::V &r0, const typename P::V &t0v,
                                         typename P::R h, typename P::R dr[3],
                                         typename P::R dt[3], typename P::R &dT,
@@ -383,7 +420,7 @@ __device__ __forceinline__ void ck_step(const M &med, int layer, int form,
             ts[i][c] = t0[c] + h * at;
         }
         R n, g[3];
-        medium_eval<P>(med, layer, rs, n, g);
+        medium_eval<P>(med, lc, rs, n, g);
         R inv_n = P::rcp(n);
         if constexpr (is_layered_v<M>) {
             // stratified medium: grad n = (0, 0, g_z); the zero terms are dropped
@@ -498,16 +535,17 @@ struct SphereC {
     int32_t idx;
 };
 
-// Spheres are sorted by centre depth; a table of depth buckets gives, for every bucket, the
-// range of spheres whose depth slab [cz - R, cz + R] can overlap it, so that a chord is
-// culled by one or two table lookups.
+// Receivers are binned in a uniform grid of cells; every sphere is listed in each cell that
+// its centre box, inflated by R + h_max / 2 (+ rounding pad), overlaps.  A step chord is no
+// longer than h_max, so a sphere it meets has its centre within R + h_max / 2 of the chord's
+// midpoint: the midpoint's cell lists every candidate, usually none.
 struct Receivers {
     const SphereC *__restrict__ s;
-    const int2 *__restrict__ bucket;  // [first, end) sphere range per depth bucket
-    const float4 *__restrict__ box;   // centre in FP32 and radius + 1 mm, sorted like s
-    int32_t n, n_buckets;
-    float z_lo, z_hi;    // depth range covered by the buckets
-    float inv_bucket;    // 1 / bucket width
+    const int2 *__restrict__ cell;  // [begin, end) into items, per cell (x fastest)
+    const int *__restrict__ items;  // sphere indices
+    int32_t n, nx, ny, nz;
+    float org[3], inv_cell;
+    float hi[3];                    // far corner of the grid
 };
 
 // ---------------------------------------------------------------------------------------
@@ -554,7 +592,9 @@ struct Lane {
     int32_t layer, gen, seq;
     int32_t n_acc, n_rej, n_root, n_refl, n_turn, root_fail;
     int32_t status;
-    int32_t stk;  // entries on this thread's private stack of pending secondaries
+    int32_t stk;   // entries on this thread's private stack of pending secondaries
+    int32_t pend;  // boundary event waiting for its split (EV_TOP / EV_BOTTOM), else 0
+    LayerR<P> lc;  // the ray's layer and its bounding planes
 };
 
 // Parameters shared by every lane of a launch.
@@ -614,8 +654,8 @@ __device__ __forceinline__ typename P::R event_g(const MediumLayered &m, const L
                                                  const typename P::R dr[3])
 {
     typedef typename P::R R;
-    if (kind == EV_TOP) return P::rel(L.r, 2, dr[2], m.top[L.layer]);
-    if (kind == EV_BOTTOM) return -P::rel(L.r, 2, dr[2], m.top[L.layer + 1]);
+    if (kind == EV_TOP) return P::rel(L.r, 2, dr[2], L.lc.top);
+    if (kind == EV_BOTTOM) return -P::rel(L.r, 2, dr[2], L.lc.bot);
     return L.stop_sign * (R(sp.stop_dir) * stop_rel(L, sp, dr));
 }
 template <class P>
@@ -697,8 +737,8 @@ __device__ __forceinline__ void write_ray(const rp_ray_out &o, long long id, con
 // recorded when the chord enters a sphere; quantities are interpolated linearly along it.
 // Receiver test on the committed chord (state L before the commit -> r1 = r + dr): a hit is
 // recorded when the chord enters a sphere; quantities are interpolated linearly along it.
-// Culling: depth buckets give the candidate range, then a bounding-box test on the compact
-// FP32 copy of the centres; only survivors get the exact chord-sphere intersection.
+// Culling: the receiver grid cell of the chord's midpoint lists the candidates; only they get
+// the exact chord-sphere intersection.
 template <class P>
 __device__ __forceinline__ void receivers_on_chord(const Sinks &sk, const Lane<P> &L,
                                                    const StepParams<P> &sp,
@@ -708,26 +748,20 @@ __device__ __forceinline__ void receivers_on_chord(const Sinks &sk, const Lane<P
 {
     typedef typename P::R R;
     const Receivers &rx = sk.rx;
-    const float za = P::kFF ? (float)P::base(L.r, 2) : (float)P::get(L.r, 2);
-    const float zb = za + (float)dr[2];
-    const float zlo = fminf(za, zb), zhi = fmaxf(za, zb);
-    if (zhi < rx.z_lo || zlo > rx.z_hi) return;  // no sphere at these depths
-    const int b0 = max(0, min(rx.n_buckets - 1, (int)((zlo - rx.z_lo) * rx.inv_bucket)));
-    const int b1 = max(0, min(rx.n_buckets - 1, (int)((zhi - rx.z_lo) * rx.inv_bucket)));
-    const int lo = __ldg(&rx.bucket[b0]).x;
-    const int hi = __ldg(&rx.bucket[b1]).y;
-    if (lo >= hi) return;
-    const float xa = P::kFF ? (float)P::base(L.r, 0) : (float)P::get(L.r, 0);
-    const float ya = P::kFF ? (float)P::base(L.r, 1) : (float)P::get(L.r, 1);
-    const float xb = xa + (float)dr[0], yb = ya + (float)dr[1];
-    const float bx0 = fminf(xa, xb), bx1 = fmaxf(xa, xb), by0 = fminf(ya, yb),
-                by1 = fmaxf(ya, yb);
+    float m[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        m[a] = (P::kFF ? (float)P::base(L.r, a) : (float)P::get(L.r, a)) + 0.5f * (float)dr[a];
+    if (m[0] < rx.org[0] || m[1] < rx.org[1] || m[2] < rx.org[2] || m[0] >= rx.hi[0] ||
+        m[1] >= rx.hi[1] || m[2] >= rx.hi[2])
+        return;  // outside every receiver's reach
+    const int ix = min(rx.nx - 1, (int)((m[0] - rx.org[0]) * rx.inv_cell));
+    const int iy = min(rx.ny - 1, (int)((m[1] - rx.org[1]) * rx.inv_cell));
+    const int iz = min(rx.nz - 1, (int)((m[2] - rx.org[2]) * rx.inv_cell));
+    const int2 span = __ldg(&rx.cell[((size_t)iz * rx.ny + iy) * rx.nx + ix]);
     const R zero = R(0);
-    for (int j = lo; j < hi; ++j) {
-        const float4 cb = __ldg(&rx.box[j]);  // centre (float) and radius + rounding pad
-        if (cb.x < bx0 - cb.w || cb.x > bx1 + cb.w || cb.y < by0 - cb.w || cb.y > by1 + cb.w ||
-            cb.z < zlo - cb.w || cb.z > zhi + cb.w)
-            continue;
+    for (int q = span.x; q < span.y; ++q) {
+        const int j = __ldg(&rx.items[q]);
         const SphereC &S = rx.s[j];
         R w[3], d[3];
 #pragma unroll
@@ -980,7 +1014,7 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
     // landing: move the candidate onto the plane by adjusting the increment
     if (ev == EV_TOP || ev == EV_BOTTOM) {
         if constexpr (is_layered_v<M>) {
-            const PlaneC &pl = (ev == EV_TOP) ? med.top[L.layer] : med.top[L.layer + 1];
+            const PlaneC &pl = (ev == EV_TOP) ? L.lc.top : L.lc.bot;
             dr[2] = dr[2] - P::rel(L.r, 2, dr[2], pl);
         }
     } else if (ev == EV_STOP) {
@@ -1006,7 +1040,7 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
     }
     if (ev == EV_TOP || ev == EV_BOTTOM) {
         if constexpr (is_layered_v<M>) {
-            P::snap(L.r, 2, (ev == EV_TOP) ? med.top[L.layer] : med.top[L.layer + 1]);
+            P::snap(L.r, 2, (ev == EV_TOP) ? L.lc.top : L.lc.bot);
         }
     } else if (ev == EV_STOP) {
         if (sp.stop_axis == 0)
@@ -1032,24 +1066,21 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
     ++L.n_acc;
     L.h = L.h_next;
 
-    bool split = false;
     if (ev == EV_TOP || ev == EV_BOTTOM) {
         if constexpr (is_layered_v<M>) {
-            split_at_plane<P>(med, L, sp, sk, ev);
-            ++L.n_refl;
-            split = true;
+            // the split itself is done by finish_split, batched across the warp
+            L.pend = ev;
+            return false;
         }
     } else if (ev == EV_STOP) {
         L.status = RP_ST_REACHED_STOP;
         return true;
     }
-    // break conditions, in the reference's order; |A| changes only at splits
+    // break conditions, in the reference's order (|A| changes only at splits)
     if (to_max_path) {
         L.status = RP_ST_MAX_PATH;
     } else if (sp.use_max_time && P::sdiff(L.T, sp.mt) >= R(0)) {
         L.status = RP_ST_MAX_TIME;
-    } else if (split && sp.use_min_amp && fabs(L.A) < sp.min_amp * fabs(L.A0)) {
-        L.status = RP_ST_MIN_AMP;
     } else if constexpr (!is_layered_v<M>) {
         bool inside = true;
 #pragma unroll
@@ -1063,6 +1094,32 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
     if (L.status != RP_ST_ALIVE) return true;
     set_trial(L, sp);
     return false;
+}
+
+// Boundary split of a ray parked on a plane by commit (Sec. 2, boundary module), followed by
+// the break conditions that the reference checks after a split.  Returns true if the ray
+// finished.
+template <class P>
+__device__ __forceinline__ bool finish_split(const MediumLayered &med, Lane<P> &L,
+                                             const StepParams<P> &sp, const Sinks &sk)
+{
+    typedef typename P::R R;
+    split_at_plane<P>(med, L, sp, sk, L.pend);
+    ++L.n_refl;
+    L.pend = 0;
+    if (sp.use_max_time && P::sdiff(L.T, sp.mt) >= R(0))
+        L.status = RP_ST_MAX_TIME;
+    else if (sp.use_min_amp && fabs(L.A) < sp.min_amp * fabs(L.A0))
+        L.status = RP_ST_MIN_AMP;
+    if (L.status != RP_ST_ALIVE) return true;
+    set_trial(L, sp);
+    return false;
+}
+template <class P>
+__device__ __forceinline__ bool finish_split(const MediumGrid &, Lane<P> &, const StepParams<P> &,
+                                             const Sinks &)
+{
+    return false;  // gridded media have no boundaries
 }
 
 // Regula-falsi point of the current bracket (bisection if it falls outside).
@@ -1088,7 +1145,7 @@ __device__ __forceinline__ bool advance(const M &med, Lane<P> &L, const StepPara
     }
     const R hc = L.h_try;
     R dr[3], dt[3], dT, er, et;
-    ck_step<P, M>(med, L.layer, sp.rhs_form, L.r, L.t, hc, dr, dt, dT, er, et);
+    ck_step<P, M>(med, L.lc, sp.rhs_form, L.r, L.t, hc, dr, dt, dT, er, et);
 
     if (L.mode == MODE_NORMAL) {
         const R e = (er > et ? er : et) * sp.inv_tol;
@@ -1114,8 +1171,7 @@ __device__ __forceinline__ bool advance(const M &med, Lane<P> &L, const StepPara
         const R zero3[3] = {R(0), R(0), R(0)};
 #pragma unroll
         for (int kind = EV_TOP; kind <= EV_STOP; ++kind) {
-            if (kind == EV_TOP && !(is_layered(med) && L.layer > 0)) continue;
-            if (kind == EV_BOTTOM && !(is_layered(med) && L.layer < n_layers(med) - 1)) continue;
+            if ((kind == EV_TOP || kind == EV_BOTTOM) && !is_layered(med)) continue;
             if (kind == EV_STOP && !sp.use_stop) continue;
             R g0 = event_g<P>(med, L, sp, kind, zero3);
             R g1 = event_g<P>(med, L, sp, kind, dr);
