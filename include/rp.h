@@ -182,6 +182,7 @@ typedef struct {
                                 16 a boundary search hit its iteration cap */
     double kernel_ms;        /* device time of the tracing kernels */
     double wave_ms[16];      /* device time of each generation's launch */
+    double warp_end_ms[3];   /* first launch: earliest, median and last warp end [ms] */
 } rp_stats;
 
 /* Traces in->n primaries and every secondary they spawn, in one persistent launch per ray

@@ -80,11 +80,13 @@ class Stats(C.Structure):
     _fields_ = [("rays", C.c_int64), ("hits", C.c_int64), ("secondaries", C.c_int64),
                 ("steps_accepted", C.c_int64), ("steps_rejected", C.c_int64),
                 ("steps_root", C.c_int64), ("queue_needed", C.c_int64), ("waves", C.c_int32),
-                ("flags", C.c_int32), ("kernel_ms", C.c_double), ("wave_ms", C.c_double * 16)]
+                ("flags", C.c_int32), ("kernel_ms", C.c_double), ("wave_ms", C.c_double * 16),
+                ("warp_end_ms", C.c_double * 3)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
         d["wave_ms"] = list(self.wave_ms)[: self.waves]
+        d["warp_end_ms"] = list(self.warp_end_ms)
         return d
 
 

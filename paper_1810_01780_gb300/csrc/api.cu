@@ -39,6 +39,17 @@ Workspace &workspace(int device)
     return *w;
 }
 
+int ensure_host_clock(Workspace &w, size_t bytes)
+{
+    if (w.host_clock_size >= bytes) return RP_OK;
+    if (w.host_clock) cudaFreeHost(w.host_clock);
+    w.host_clock = nullptr;
+    w.host_clock_size = 0;
+    RP_CUDA_TRY(cudaMallocHost(&w.host_clock, bytes));
+    w.host_clock_size = bytes;
+    return RP_OK;
+}
+
 int ensure_workspace(Workspace &w, size_t bytes)
 {
     if (!w.host_ctrl) RP_CUDA_TRY(cudaMallocHost(&w.host_ctrl, 4096));
@@ -175,6 +186,8 @@ int rp_medium_create(const rp_medium_desc *d, void *stream, rp_medium_t *out)
                     m->layered.n_below_f[k] = (float)n;
                 }
             }
+            m->layered.eta_down[k] = m->layered.n_above[k] / m->layered.n_below[k];
+            m->layered.eta_up[k] = m->layered.n_below[k] / m->layered.n_above[k];
         }
     } else if (d->kind == RP_MEDIUM_GRID) {
         if (d->nx < 2 || d->ny < 2 || d->nz < 2 || !(d->spacing > 0.0) || !d->grid_n) {

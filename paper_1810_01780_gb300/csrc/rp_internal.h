@@ -35,9 +35,12 @@ struct Workspace {
     void *ptr = nullptr;
     size_t size = 0;
     void *host_ctrl = nullptr;  // pinned copy of the control block
+    void *host_clock = nullptr; // pinned copy of the per-warp clocks
+    size_t host_clock_size = 0;
 };
 Workspace &workspace(int device);
 int ensure_workspace(Workspace &w, size_t bytes);
+int ensure_host_clock(Workspace &w, size_t bytes);
 
 int sm_count(int device);
 

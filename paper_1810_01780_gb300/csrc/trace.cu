@@ -11,6 +11,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -53,6 +54,13 @@ __device__ __forceinline__ void lane_reset(Lane<P> &L, const M &med, const StepP
     L.stop = stop;
     init_stop(L, sp);
     set_trial(L, sp);
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 __device__ __forceinline__ void prefetch_l1(const void *p)
@@ -99,13 +107,17 @@ __device__ __forceinline__ void load_record(Lane<P> &L, const M &med, const Step
     L.seq = Q.seq;
     L.layer = Q.layer;
     lane_reset<P, M>(L, med, sp, stop);
+    L.status = Q.status;  // RP_ST_ALIVE, or a record that only has to be written out
 }
 
-// Next ray of this wave for the calling lane; false when the wave's input is exhausted.
+enum { NEXT_NONE = 0, NEXT_TRACE = 1, NEXT_RECORD = 2 };
+
+// Next ray of this wave for the calling lane: NEXT_TRACE, NEXT_RECORD (a finished record to
+// write out, e.g. a ray refracted into air) or NEXT_NONE when the wave's input is exhausted.
 // `ahead` holds a ray index claimed one ray in advance, so that the claim's atomic and the
 // input loads overlap the tracing of the current ray.
 template <class P, class M>
-__device__ bool next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, const Sinks &sk,
+__device__ int next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, const Sinks &sk,
                          const WaveIn &in, int wave, unsigned long long base,
                          unsigned long long count, long long &ahead)
 {
@@ -114,15 +126,17 @@ __device__ bool next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, cons
             // depth first: the secondaries this thread cast itself come before new input
             --L.stk;
             load_record<P, M>(L, med, sp, thread_stack(sk)[L.stk], in.stop);
-            return true;
+            L.tail = ahead >= (long long)count;
+            return L.status == RP_ST_ALIVE ? NEXT_TRACE : NEXT_RECORD;
         }
         const long long k = ahead;
-        if (k >= (long long)count) return false;
+        if (k >= (long long)count) return NEXT_NONE;
         ahead = claim_index(&sk.ctrl->claim[wave]);
         if (ahead < (long long)count) prefetch_ray(sk, in, wave, base, ahead);
         if (wave != 0) {
             load_record<P, M>(L, med, sp, sk.queue[base + k], in.stop);
-            return true;
+            L.tail = ahead >= (long long)count;
+            return L.status == RP_ST_ALIVE ? NEXT_TRACE : NEXT_RECORD;
         }
         const long long n = in.n;
         L.A = in.amp ? in.amp[k] : 1.0;
@@ -195,12 +209,10 @@ __device__ bool next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, cons
             for (int a = 0; a < 3; ++a) P::set(L.t, a, t[a] / q);
         }
         lane_reset<P, M>(L, med, sp, in.stop);
-        return true;
+        L.tail = ahead >= (long long)count;
+        return NEXT_TRACE;
     }
 }
-
-constexpr int kServiceBatch = 4;
-constexpr unsigned int kServicePeriod = 4;  // power of two
 
 template <class P, class M>
 __global__ void __launch_bounds__(128, P::kMinBlocks) k_trace_wave(const M med, const StepParams<P> sp,
@@ -213,12 +225,13 @@ __global__ void __launch_bounds__(128, P::kMinBlocks) k_trace_wave(const M med, 
         base = sk.ctrl->seg_begin[wave];
         count = sk.ctrl->seg_end[wave] - base;
     }
+    const unsigned long long t_start = global_ns();
     Lane<P> L;
     L.stk = 0;
     unsigned int acc = 0, rej = 0, root = 0;
     long long ahead = claim_index(&sk.ctrl->claim[wave]);
-    bool active = next_ray<P, M>(L, med, sp, sk, in, wave, base, count, ahead);
-    bool done = false;
+    int nx = next_ray<P, M>(L, med, sp, sk, in, wave, base, count, ahead);
+    bool active = nx == NEXT_TRACE, done = nx == NEXT_RECORD;
     unsigned int iter = 0;
     // Warp-synchronous loop.  Every iteration runs one Runge-Kutta step on each lane whose
     // ray is stepping.  The rare, long code paths -- a boundary split with its secondary,
@@ -236,19 +249,20 @@ __global__ void __launch_bounds__(128, P::kMinBlocks) k_trace_wave(const M med, 
         const bool waits = done || (active && L.pend != 0);
         const unsigned int wait = __ballot_sync(0xffffffffu, waits);
         const unsigned int step_mask = __ballot_sync(0xffffffffu, active && L.pend == 0);
-        if (wait != 0u && (__popc(wait) >= kServiceBatch ||
-                           ((++iter) & (kServicePeriod - 1)) == 0u || step_mask == 0u)) {
+        if (wait != 0u && (__popc(wait) >= sp.service_batch ||
+                           ((++iter) & sp.service_mask) == 0u || step_mask == 0u)) {
             if (active && L.pend != 0 && finish_split<P>(med, L, sp, sk)) {
                 active = false;
                 done = true;
             }
-            if (done) {
+            while (done) {
                 acc += (unsigned int)L.n_acc;
                 rej += (unsigned int)L.n_rej;
                 root += (unsigned int)L.n_root;
                 write_ray<P>(sk.out, L.id, L, sk.ctrl);
-                done = false;
-                active = next_ray<P, M>(L, med, sp, sk, in, wave, base, count, ahead);
+                nx = next_ray<P, M>(L, med, sp, sk, in, wave, base, count, ahead);
+                active = nx == NEXT_TRACE;
+                done = nx == NEXT_RECORD;
             }
         }
     }
@@ -257,6 +271,11 @@ __global__ void __launch_bounds__(128, P::kMinBlocks) k_trace_wave(const M med, 
     rej = __reduce_add_sync(0xffffffffu, rej);
     root = __reduce_add_sync(0xffffffffu, root);
     if ((threadIdx.x & 31) == 0) {
+        if (wave == 0) {
+            const size_t w = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+            sk.warp_clock[2 * w] = t_start;
+            sk.warp_clock[2 * w + 1] = global_ns();
+        }
         atomicAdd(&sk.ctrl->steps_acc, (unsigned long long)acc);
         atomicAdd(&sk.ctrl->steps_rej, (unsigned long long)rej);
         atomicAdd(&sk.ctrl->steps_root, (unsigned long long)root);
@@ -319,6 +338,23 @@ static int launch_waves(const M &med, const StepParams<P> &sp, const Sinks &sk, 
     return RP_OK;
 }
 
+// Service-phase batching (see k_trace_wave): lanes waiting before a service, and the period
+// in iterations (a power of two).  RP_SERVICE_BATCH / RP_SERVICE_PERIOD override them.
+static int env_int(const char *name, int dflt, int lo, int hi)
+{
+    const char *v = getenv(name);
+    if (!v || !*v) return dflt;
+    int x = atoi(v);
+    return x < lo ? lo : (x > hi ? hi : x);
+}
+static int service_batch() { return env_int("RP_SERVICE_BATCH", 8, 1, 32); }
+static int service_period()
+{
+    int p = env_int("RP_SERVICE_PERIOD", 16, 1, 1024), q = 1;
+    while (q < p) q <<= 1;
+    return q;
+}
+
 template <class P>
 static StepParams<P> make_step_params(const rp_trace_params *p, int axis, float dir)
 {
@@ -344,6 +380,8 @@ static StepParams<P> make_step_params(const rp_trace_params *p, int axis, float 
     sp.stop_axis = axis;
     sp.stop_dir = dir;
     sp.max_steps = p->max_steps;
+    sp.service_batch = service_batch();
+    sp.service_mask = service_period() - 1;
     return sp;
 }
 
@@ -487,7 +525,8 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     const size_t off_z = off_s + align_up(sizeof(SphereC) * (size_t)std::max(n_rx, 1));
     const size_t off_b = off_z + align_up(sizeof(int2) * std::max<size_t>(cells.size(), 1));
     const size_t off_k = off_b + align_up(sizeof(int) * std::max<size_t>(items.size(), 1));
-    const size_t total = off_k + align_up(sizeof(QRec) * (size_t)threads * kStackDepth);
+    const size_t off_w = off_k + align_up(sizeof(QRec) * (size_t)threads * kStackDepth);
+    const size_t total = off_w + align_up(sizeof(unsigned long long) * 2 * (size_t)(threads / 32));
 
     Workspace &ws = workspace(dev);
     std::lock_guard<std::mutex> lock(ws.mu);
@@ -501,6 +540,7 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     sk.queue = (QRec *)(base + off_q);
     sk.q_cap = (unsigned long long)q_cap;
     sk.stack = (QRec *)(base + off_k);
+    sk.warp_clock = (unsigned long long *)(base + off_w);
     sk.out = *out;
     if (hits) sk.hits = *hits;
     sk.has_rx = n_rx > 0;
@@ -560,11 +600,17 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
                                                    sk, wi, n_waves, dev, block, st, ev);
     }
     Ctrl *hc = (Ctrl *)ws.host_ctrl;
+    const size_t n_clk = 2 * (size_t)(threads / 32);
+    if (!rc) rc = ensure_host_clock(ws, n_clk * sizeof(unsigned long long));
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ws.host_clock, sk.warp_clock, n_clk * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = cuda_fail(e, "rp_trace: control block read-back");
     }
+    const unsigned long long *wclk = (const unsigned long long *)ws.host_clock;
     float wave_ms[RP_MAX_WAVES] = {0.0f}, ms = 0.0f;
     if (!rc) {
         for (int w = 0; w < n_waves; ++w) cudaEventElapsedTime(&wave_ms[w], ev[w], ev[w + 1]);
@@ -587,6 +633,18 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
         stats->flags = (int32_t)flags;
         stats->kernel_ms = ms;
         for (int w = 0; w < RP_MAX_WAVES; ++w) stats->wave_ms[w] = w < n_waves ? wave_ms[w] : 0.0;
+        // tail of the first launch: warp end times after the earliest warp start
+        const size_t nw = n_clk / 2;
+        if (nw) {
+            unsigned long long t0 = ~0ull;
+            std::vector<double> ends(nw);
+            for (size_t w = 0; w < nw; ++w) t0 = std::min(t0, wclk[2 * w]);
+            for (size_t w = 0; w < nw; ++w) ends[w] = (double)(wclk[2 * w + 1] - t0) * 1e-6;
+            std::sort(ends.begin(), ends.end());
+            stats->warp_end_ms[0] = ends.front();
+            stats->warp_end_ms[1] = ends[nw / 2];
+            stats->warp_end_ms[2] = ends.back();
+        }
     }
     if (flags & (FLAG_OUT_OVERFLOW | FLAG_QUEUE_OVERFLOW | FLAG_HIT_OVERFLOW)) {
         set_error("rp_trace: overflow (rays %llu / capacity %lld, hits %llu / capacity %lld)",

@@ -220,6 +220,8 @@ struct MediumLayered {
     // index just above / below plane k (layer k-1 / layer k evaluated at z_top[k])
     double n_above[RP_MAX_LAYERS], n_below[RP_MAX_LAYERS];
     float n_above_f[RP_MAX_LAYERS], n_below_f[RP_MAX_LAYERS];
+    // index ratios n1 / n2 for a ray crossing plane k downward and upward
+    double eta_down[RP_MAX_LAYERS], eta_up[RP_MAX_LAYERS];
 };
 
 struct MediumGrid {
@@ -568,7 +570,8 @@ struct QRec {
     double T, s, A, A0;
     double h;
     long long id, parent;
-    int32_t layer, gen, seq, pad;
+    int32_t layer, gen, seq;
+    int32_t status;  // RP_ST_ALIVE: to be traced; otherwise a finished record to write out
 };
 
 // ---------------------------------------------------------------------------------------
@@ -594,6 +597,8 @@ struct Lane {
     int32_t status;
     int32_t stk;   // entries on this thread's private stack of pending secondaries
     int32_t pend;  // boundary event waiting for its split (EV_TOP / EV_BOTTOM), else 0
+    int32_t tail;  // the launch's input was exhausted when this ray started: secondaries go
+                   // to the global queue, spreading the last chains over the next launch
     LayerR<P> lc;  // the ray's layer and its bounding planes
 };
 
@@ -609,6 +614,8 @@ struct StepParams {
     int32_t stop_axis;  // 0, 1, 2 (the stop normal is +/- a coordinate axis)
     float stop_dir;     // +1 or -1: sign of the normal along stop_axis
     long long max_steps;
+    int32_t service_batch;          // lanes waiting before a service phase
+    unsigned int service_mask;      // service period - 1 (period is a power of two)
 };
 
 // Offset of the candidate r + dr from the stop plane along the stop axis (selected without
@@ -694,6 +701,7 @@ struct Sinks {
     QRec *queue;
     unsigned long long q_cap;
     QRec *stack;  // kStackDepth records per thread of the launch
+    unsigned long long *warp_clock;  // per warp of wave 0: start and end (globaltimer, ns)
     // output arrays for rays recorded directly (transmitted into absorbing layers)
     rp_ray_out out;
     // hits
@@ -863,10 +871,10 @@ __device__ __forceinline__ QRec *thread_stack(const Sinks &sk)
 template <class P>
 __device__ __forceinline__ void queue_secondary(const Sinks &sk, Lane<P> &L,
                                                 unsigned long long id, int other, double amp,
-                                                const double t_refr[3])
+                                                const double t_refr[3], int status)
 {
     QRec *slot;
-    if (L.stk < kStackDepth) {
+    if (L.stk < kStackDepth && (!L.tail || status != RP_ST_ALIVE)) {
         slot = thread_stack(sk) + L.stk;
         ++L.stk;
     } else {
@@ -894,6 +902,7 @@ __device__ __forceinline__ void queue_secondary(const Sinks &sk, Lane<P> &L,
     Q.layer = other;
     Q.gen = L.gen + 1;
     Q.seq = L.n_refl;
+    Q.status = status;
 }
 
 // Boundary split at the horizontal plane between the ray's layer and `other` (Sec. 2,
@@ -924,10 +933,8 @@ __device__ __forceinline__ void split_at_plane(const MediumLayered &med, Lane<P>
         if (!tir && spawn_allowed && !weak) {
             const unsigned long long id = atomicAdd(&sk.ctrl->out_count, 1ull);
             atomicAdd(&sk.ctrl->n_secondary, 1ull);
-            if (med.L[other].absorb)
-                record_secondary<P>(sk, L, id, other, amp, t_refr, RP_ST_TRANSMITTED);
-            else
-                queue_secondary<P>(sk, L, id, other, amp, t_refr);
+            queue_secondary<P>(sk, L, id, other, amp, t_refr,
+                               med.L[other].absorb ? RP_ST_TRANSMITTED : RP_ST_ALIVE);
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) P::set(L.t, a, t_refl[a]);
@@ -977,19 +984,17 @@ __device__ __forceinline__ void split_at_plane(const MediumLayered &med, Lane<P>
                 const float q = sqrtf(tf[0] * tf[0] + tf[1] * tf[1] + tf[2] * tf[2]);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) t_refr[a] = (double)(tf[a] / q);
-                record_secondary<P>(sk, L, id, other, amp, t_refr, RP_ST_TRANSMITTED);
+                queue_secondary<P>(sk, L, id, other, amp, t_refr, RP_ST_TRANSMITTED);
             } else {
-                // traced secondary: its direction from Snell's law in FP64 (vector form,
-                // horizontal plane), so that it starts as accurately as in the FP64 path
-                const double t0 = P::get(L.t, 0), t1 = P::get(L.t, 1), t2 = P::get(L.t, 2);
-                const double ci = fmax(-(t2 * nz), 0.0);
-                const double etad = n1d / n2d;
-                const double s2 = etad * etad * (1.0 - ci * ci);
-                const double ct = sqrt(fmax(1.0 - s2, 0.0));
-                t_refr[0] = etad * t0;
-                t_refr[1] = etad * t1;
-                t_refr[2] = etad * t2 + (etad * ci - ct) * nz;
-                queue_secondary<P>(sk, L, id, other, amp, t_refr);
+                // traced secondary: Snell's law in FP64 (horizontal plane: the tangential
+                // part scales by n1/n2, the normal part is -cos(theta_t) along the normal)
+                const double etad = (ev == EV_TOP) ? med.eta_up[pk] : med.eta_down[pk];
+                const double ci = fmax(-(P::get(L.t, 2) * nz), 0.0);
+                const double ct = sqrt(fmax(1.0 - etad * etad * (1.0 - ci * ci), 0.0));
+                t_refr[0] = etad * P::get(L.t, 0);
+                t_refr[1] = etad * P::get(L.t, 1);
+                t_refr[2] = -ct * nz;
+                queue_secondary<P>(sk, L, id, other, amp, t_refr, RP_ST_ALIVE);
             }
         }
         if (toward) {

@@ -176,11 +176,11 @@ def batched(n=1_048_576, seed=2):
 
     Break conditions: the 3 km path limit and the amplitude threshold A/A0 < 0.05 of the
     paper's Fig. 1 example (without it, rays grazing the internal boundary cast a secondary
-    of near-zero amplitude at every one of thousands of bounces); at most 2,000 attempted
+    of near-zero amplitude at every one of thousands of bounces); at most 1,000 attempted
     steps per ray (an ordinary ray needs at most ~330; only rays trapped at grazing incidence
     against the internal boundary reach the cap)."""
     return dict(name="batched", medium=two_layer_ice(),
-                params=dict(TRACE_DEFAULTS, max_path=3000.0, min_amp=0.05, max_steps=2_000),
+                params=dict(TRACE_DEFAULTS, max_path=3000.0, min_amp=0.05, max_steps=1_000),
                 rays=isotropic_sources(n, seed), receivers=receiver_lattice())
 
 
