@@ -193,6 +193,33 @@ typedef struct {
 int rp_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp_trace_params *p,
              rp_ray_out *out, rp_hits *hits, rp_stats *stats, void *stream);
 
+/* Size of the fixed device scratch array used by rp_trace_static, and the largest inputs
+ * it accepts. */
+#define RP_STATIC_SCRATCH_BYTES (32u << 20) /* 32 MiB, held by every device that loads the library */
+#define RP_STATIC_MAX_RAYS (1 << 20)
+#define RP_STATIC_MAX_RECEIVERS 1024
+
+/* rp_trace without any device allocation (the paper has no counterpart: this is a deployment
+ * variant).  For callers that cannot allocate device memory while they trace -- a process
+ * whose device memory is owned by another allocator's pool, a service that forbids
+ * cudaMalloc / cudaFree after start-up because they can synchronise the device, a tool with a
+ * fixed memory budget.  Same arguments, semantics and results as rp_trace; its scratch space
+ * (control block, receiver grid, per-thread secondary stacks, overflow queue) comes from one
+ * static device array of RP_STATIC_SCRATCH_BYTES that every device using the library holds
+ * until the process exits.  The call allocates no device or pinned host memory.
+ *   - The first call on a device resolves the array's device address (cudaGetSymbolAddress,
+ *     with that device current); make that first call before any stream capture.
+ *   - All calls on a device share the array; they are serialised by a host lock, and calls
+ *     that overlap on the GPU (e.g. from several processes' views of it) would race.  The
+ *     control block is cleared at the start of every call; the rest is overwritten.
+ *   - Limits: in->n <= RP_STATIC_MAX_RAYS and rx->n <= RP_STATIC_MAX_RECEIVERS
+ *     (RP_ERR_INVALID_ARG beyond).  The secondary-ray queue is smaller than rp_trace's; if it
+ *     fills, the call returns RP_ERR_OVERFLOW with rp_stats as for rp_trace.
+ *   - rp_stats.warp_end_ms is not filled (its read-back would need pinned host memory). */
+int rp_trace_static(rp_medium_t m, const rp_rays *in, const rp_receivers *rx,
+                    const rp_trace_params *p, rp_ray_out *out, rp_hits *hits, rp_stats *stats,
+                    void *stream);
+
 /* ------------------------------------------------------------------------------------
  * Source-receiver path finding (Sec. 2, accuracy study)
  * ---------------------------------------------------------------------------------- */

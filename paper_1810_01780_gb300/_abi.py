@@ -107,6 +107,9 @@ SIGNATURES = {
     "rp_trace": (C.c_int, [C.c_void_p, C.POINTER(Rays), C.POINTER(Receivers),
                            C.POINTER(TraceParams), C.POINTER(RayOut), C.POINTER(Hits),
                            C.POINTER(Stats), C.c_void_p]),
+    "rp_trace_static": (C.c_int, [C.c_void_p, C.POINTER(Rays), C.POINTER(Receivers),
+                                  C.POINTER(TraceParams), C.POINTER(RayOut), C.POINTER(Hits),
+                                  C.POINTER(Stats), C.c_void_p]),
     "rp_find_paths": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.POINTER(PathParams), C.POINTER(Solutions),
                                 C.POINTER(Stats), C.c_void_p]),

@@ -56,9 +56,17 @@ inline rpk::PlaneC plane_const(double d)
 
 int validate_params(const rp_trace_params *p, bool path_finding);
 
-// Tracing driver (trace.cu).
+// A caller-provided device scratch region used instead of the grow-only workspace.
+struct FixedScratch {
+    void *ptr;
+    size_t size;
+    std::mutex *mu;  // serialises the calls that share the region
+};
+
+// Tracing driver (trace.cu).  fs == nullptr: the grow-only workspace of the device.
 int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp_trace_params *p,
-              rp_ray_out *out, rp_hits *hits, rp_stats *stats, cudaStream_t st);
+              rp_ray_out *out, rp_hits *hits, rp_stats *stats, cudaStream_t st,
+              const FixedScratch *fs = nullptr);
 
 // Path-finding driver (pathfind.cu).
 int run_find_paths(rp_medium_t m, int64_t n_pairs, const double *zs, const double *zr,

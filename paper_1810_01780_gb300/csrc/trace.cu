@@ -411,7 +411,8 @@ int stop_axis_of(const rp_trace_params *p, int *axis, float *dir, double *offset
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp_trace_params *p,
-              rp_ray_out *out, rp_hits *hits, rp_stats *stats, cudaStream_t st)
+              rp_ray_out *out, rp_hits *hits, rp_stats *stats, cudaStream_t st,
+              const FixedScratch *fs)
 {
     if (!m || !in || !p || !out) {
         set_error("rp_trace: null medium, rays, params or output");
@@ -518,20 +519,38 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     const int block = 128;
     const int threads = trace_threads(m->kind, p->precision, dev, block);
     if (threads < 0) return threads;
-    const long long q_cap = out->capacity - in->n;
+    // scratch layout: control block, receivers, per-thread stacks, warp clocks, queue last
+    long long q_cap = out->capacity - in->n;
+    int depth = kStackDepth;
     const size_t off_ctrl = 0;
-    const size_t off_q = align_up(sizeof(Ctrl));
-    const size_t off_s = off_q + align_up(sizeof(QRec) * (size_t)std::max(q_cap, 1LL));
+    const size_t off_s = align_up(sizeof(Ctrl));
     const size_t off_z = off_s + align_up(sizeof(SphereC) * (size_t)std::max(n_rx, 1));
     const size_t off_b = off_z + align_up(sizeof(int2) * std::max<size_t>(cells.size(), 1));
     const size_t off_k = off_b + align_up(sizeof(int) * std::max<size_t>(items.size(), 1));
-    const size_t off_w = off_k + align_up(sizeof(QRec) * (size_t)threads * kStackDepth);
-    const size_t total = off_w + align_up(sizeof(unsigned long long) * 2 * (size_t)(threads / 32));
+    const size_t clk_bytes = align_up(sizeof(unsigned long long) * 2 * (size_t)(threads / 32));
+    if (fs) {
+        // fixed scratch: at most half of it for the stacks, the rest (after the fixed parts)
+        // for the queue
+        if (off_k + clk_bytes + align_up(sizeof(QRec) * (size_t)threads) + 4096 > fs->size) {
+            set_error("rp_trace: %d receivers need more than the %zu-byte fixed scratch", n_rx,
+                      fs->size);
+            return RP_ERR_INVALID_ARG;
+        }
+        while (depth > 1 && off_k + clk_bytes + sizeof(QRec) * (size_t)threads * depth > fs->size / 2)
+            --depth;
+    }
+    const size_t off_w = off_k + align_up(sizeof(QRec) * (size_t)threads * depth);
+    const size_t off_q = off_w + clk_bytes;
+    if (fs) {
+        const long long fit = (long long)((fs->size - off_q) / sizeof(QRec));
+        q_cap = std::min(q_cap, fit);
+    }
+    const size_t total = off_q + align_up(sizeof(QRec) * (size_t)std::max(q_cap, 1LL));
 
     Workspace &ws = workspace(dev);
-    std::lock_guard<std::mutex> lock(ws.mu);
-    if ((rc = ensure_workspace(ws, total))) return rc;
-    char *base = (char *)ws.ptr;
+    std::unique_lock<std::mutex> lock(fs ? *fs->mu : ws.mu);
+    if (!fs && (rc = ensure_workspace(ws, total))) return rc;
+    char *base = fs ? (char *)fs->ptr : (char *)ws.ptr;
     Ctrl *ctrl = (Ctrl *)(base + off_ctrl);
 
     Sinks sk;
@@ -540,6 +559,7 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     sk.queue = (QRec *)(base + off_q);
     sk.q_cap = (unsigned long long)q_cap;
     sk.stack = (QRec *)(base + off_k);
+    sk.stack_depth = depth;
     sk.warp_clock = (unsigned long long *)(base + off_w);
     sk.out = *out;
     if (hits) sk.hits = *hits;
@@ -599,12 +619,15 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
             rc = launch_waves<PrecF32, MediumGrid>(m->grid, make_step_params<PrecF32>(p, axis, sdir),
                                                    sk, wi, n_waves, dev, block, st, ev);
     }
-    Ctrl *hc = (Ctrl *)ws.host_ctrl;
-    const size_t n_clk = 2 * (size_t)(threads / 32);
-    if (!rc) rc = ensure_host_clock(ws, n_clk * sizeof(unsigned long long));
+    // read-back: pinned buffers of the workspace, or (fixed scratch) pageable host memory and
+    // no warp clocks, so that nothing is allocated
+    Ctrl ctrl_local;
+    Ctrl *hc = fs ? &ctrl_local : (Ctrl *)ws.host_ctrl;
+    const size_t n_clk = fs ? 0 : 2 * (size_t)(threads / 32);
+    if (!rc && !fs) rc = ensure_host_clock(ws, n_clk * sizeof(unsigned long long));
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && n_clk)
             e = cudaMemcpyAsync(ws.host_clock, sk.warp_clock, n_clk * sizeof(unsigned long long),
                                 cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);

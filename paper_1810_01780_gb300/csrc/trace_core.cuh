@@ -695,12 +695,14 @@ __device__ __forceinline__ void init_stop(Lane<P> &L, const StepParams<P> &sp)
 
 // Hooks the kernels provide: where a secondary goes and what a receiver hit writes.
 constexpr int kStackDepth = 8;  // secondaries a thread keeps for itself before spilling
+                                // (the fixed-scratch entry point may use fewer)
 
 struct Sinks {
     Ctrl *ctrl;
     QRec *queue;
     unsigned long long q_cap;
-    QRec *stack;  // kStackDepth records per thread of the launch
+    QRec *stack;  // stack_depth records per thread of the launch
+    int32_t stack_depth;
     unsigned long long *warp_clock;  // per warp of wave 0: start and end (globaltimer, ns)
     // output arrays for rays recorded directly (transmitted into absorbing layers)
     rp_ray_out out;
@@ -862,7 +864,7 @@ __device__ __forceinline__ void record_secondary(const Sinks &sk, const Lane<P> 
 __device__ __forceinline__ QRec *thread_stack(const Sinks &sk)
 {
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    return sk.stack + tid * kStackDepth;
+    return sk.stack + tid * (size_t)sk.stack_depth;
 }
 
 // Keeps a secondary for later tracing: on the thread's private stack (no atomics, traced by
@@ -874,7 +876,7 @@ __device__ __forceinline__ void queue_secondary(const Sinks &sk, Lane<P> &L,
                                                 const double t_refr[3], int status)
 {
     QRec *slot;
-    if (L.stk < kStackDepth && (!L.tail || status != RP_ST_ALIVE)) {
+    if (L.stk < sk.stack_depth && (!L.tail || status != RP_ST_ALIVE)) {
         slot = thread_stack(sk) + L.stk;
         ++L.stk;
     } else {
