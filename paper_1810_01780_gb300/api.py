@@ -215,3 +215,58 @@ def trace(medium: Medium, pos, dir, amp=None, params: dict | None = None, receiv
     nh = int(st.hits) if buf.hits is not None else 0
     hits = {k: (v[:, :nh] if v.dim() == 2 else v[:nh]) for k, v in buf.h.items()}
     return {"rays": out, "hits": hits, "stats": st.as_dict()}
+
+
+SOL_FIELDS = (("type", torch.int32), ("n_iter", torch.int32), ("launch", torch.float64),
+              ("receive", torch.float64), ("time", torch.float64), ("path", torch.float64),
+              ("amp", torch.float64), ("miss", torch.float64))
+
+
+class PathBuffers:
+    """Device inputs and outputs of rp_find_paths for a batch of pairs."""
+
+    def __init__(self, zs, zr, dist, n_angles, max_sol: int = 4):
+        self.zs = _dev_f64(zs)
+        self.zr = _dev_f64(zr)
+        self.dist = _dev_f64(dist)
+        self.n_angles = torch.as_tensor(n_angles, dtype=torch.int32, device="cuda").contiguous()
+        self.n = self.zs.numel()
+        self.max_sol = int(max_sol)
+        self.count = torch.zeros(self.n, dtype=torch.int32, device="cuda")
+        self.t = {k: torch.zeros((self.n, self.max_sol), dtype=dt, device="cuda")
+                  for k, dt in SOL_FIELDS}
+        self.sol = A.Solutions(self.count.data_ptr(), *[self.t[k].data_ptr() for k, _ in SOL_FIELDS])
+
+
+def make_path_params(p: dict, precision: str = "fp64", hit_tol: float = 0.1, max_iter: int = 60,
+                     max_sol: int = 4) -> A.PathParams:
+    q = A.PathParams()
+    q.trace = make_params(dict(p, max_path=p.get("max_path", 1.0)), precision)
+    q.hit_tol = hit_tol
+    q.max_iter = max_iter
+    q.max_sol = max_sol
+    return q
+
+
+def find_paths_into(medium: Medium, buf: PathBuffers, prm: A.PathParams, stream=None,
+                    allow_overflow=False) -> A.Stats:
+    st = A.Stats()
+    rc = A.lib().rp_find_paths(medium.handle, buf.n, C.c_void_p(buf.zs.data_ptr()),
+                               C.c_void_p(buf.zr.data_ptr()), C.c_void_p(buf.dist.data_ptr()),
+                               C.c_void_p(buf.n_angles.data_ptr()), C.byref(prm),
+                               C.byref(buf.sol), C.byref(st), C.c_void_p(_stream_ptr(stream)))
+    A.check(rc, allow_overflow=allow_overflow)
+    st.rc = rc
+    return st
+
+
+def find_paths(medium: Medium, zs, zr, dist, n_angles, params: dict, precision: str = "fp64",
+               hit_tol: float = 0.1, max_iter: int = 60, max_sol: int = 4, stream=None) -> dict:
+    """Batched source-receiver path finding; returns count, per-slot solution fields, stats."""
+    buf = PathBuffers(zs, zr, dist, n_angles, max_sol)
+    prm = make_path_params(params, precision, hit_tol, max_iter, max_sol)
+    st = find_paths_into(medium, buf, prm, stream)
+    out = {"count": buf.count}
+    out.update(buf.t)
+    out["stats"] = st.as_dict()
+    return out

@@ -1,12 +1,614 @@
-// pathfind.cu -- batched source-receiver path finding (placeholder until the kernels land).
+// pathfind.cu -- batched source-receiver path finding (rp_find_paths).
+//
+// Sec. 2 of the paper checks the tracer against analytic solutions by finding the launch
+// angles that connect a source with an observation point.  For a batch of pairs
+// (z_s, z_r, D) this runs, entirely on the GPU:
+//   1. k_prefix   exclusive prefix sum of the per-pair scan sizes (uneven: 32..512 angles)
+//   2. k_scan     one persistent launch over all (pair, angle) rays: each ray leaves
+//                 (0, 0, z_s) in the x-z plane and stops on the plane x = D; its vertical miss
+//                 z - z_r is stored (+inf if the path budget ran out first: the ray is far
+//                 below; NaN for any other end)
+//   3. k_brackets adjacent angles of one pair whose misses change sign become brackets
+//   4. k_bisect   one persistent launch over all brackets: each lane bisects its bracket in
+//                 FP64 on the launch angle, one full trace per step, until |miss| < hit_tol
+//   5. k_finalize per pair: candidate solutions sorted by travel time into the output slots
+// Rays use the same lane state machine as rp_trace (trace_core.cuh) with a per-ray stop plane
+// and path budget 2 (D + z_s + z_r) + 100 m; no secondaries are cast.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cstring>
+
 #include "rp_internal.h"
 
+namespace cg = cooperative_groups;
+using namespace rpk;
+
 namespace rph {
-int run_find_paths(rp_medium_t, int64_t, const double *, const double *, const double *,
-                   const int32_t *, const rp_path_params *, rp_solutions *, rp_stats *,
-                   cudaStream_t)
+
+namespace {
+
+constexpr int kMaxCand = 16;  // candidate solutions kept per pair before sorting
+
+struct PairIn {
+    const double *zs, *zr, *dist;
+    const int32_t *n_angles;
+    long long n_pairs;
+    double hit_tol;
+    int32_t max_iter, max_sol;
+};
+
+struct Bracket {
+    double tha, thb, ma;
+    int32_t pair, pad;
+};
+
+struct Cand {
+    double launch, receive, time, path, amp, miss;
+    int32_t type, n_iter;
+};
+
+struct PfCtrl {
+    unsigned long long claim_scan, claim_bisect, n_brackets, rays;
+    unsigned long long steps_acc, steps_rej, steps_root;
+    unsigned int flags, pad;
+};
+
+__device__ __forceinline__ long long pf_claim(unsigned long long *counter)
 {
-    set_error("rp_find_paths: not built yet");
-    return RP_ERR_UNSUPPORTED;
+    cg::coalesced_group g = cg::coalesced_threads();
+    unsigned long long base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(counter, (unsigned long long)g.size());
+    base = g.shfl(base, 0);
+    return (long long)(base + g.thread_rank());
 }
+
+__device__ __forceinline__ int scan_items(const PairIn &pi, long long i)
+{
+    if (pi.dist[i] < pi.hit_tol) return 1;
+    const int n = pi.n_angles[i];
+    return n < 2 ? 2 : n;
+}
+
+// Exclusive prefix sum of the scan sizes, one block of 1024 threads: each thread sums a
+// contiguous chunk, the 1024 partial sums are scanned in shared memory.
+__global__ void __launch_bounds__(1024) k_prefix(const PairIn pi, long long *prefix)
+{
+    __shared__ long long part[1024];
+    const long long n = pi.n_pairs;
+    const long long chunk = (n + 1023) / 1024;
+    const long long lo = threadIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+    long long s = 0;
+    for (long long i = lo; i < hi; ++i) s += scan_items(pi, i);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    long long run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    for (long long i = lo; i < hi; ++i) {
+        prefix[i] = run;
+        run += scan_items(pi, i);
+    }
+    if (threadIdx.x == 1023) prefix[n] = part[1023];
+}
+
+// pair of a global scan item (prefix is exclusive, n_pairs + 1 entries)
+__device__ __forceinline__ long long pair_of(const long long *prefix, long long n_pairs, long long k)
+{
+    long long lo = 0, hi = n_pairs;  // invariant: prefix[lo] <= k < prefix[hi]
+    while (hi - lo > 1) {
+        const long long mid = (lo + hi) >> 1;
+        if (prefix[mid] <= k)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Sets a lane up for the ray of pair i launched at angle th (from +z, in the x-z plane).
+template <class P>
+__device__ __forceinline__ void launch_ray(Lane<P> &L, const MediumLayered &med,
+                                           const StepParams<P> &sp, const PairIn &pi, double h0,
+                                           long long i, double th, bool vertical, long long id)
+{
+    const double zs = pi.zs[i], zr = pi.zr[i], D = pi.dist[i];
+    const double t[3] = {sin(th), 0.0, cos(th)};
+    const double q = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    P::set(L.r, 0, 0.0);
+    P::set(L.r, 1, 0.0);
+    P::set(L.r, 2, zs);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) P::set(L.t, a, t[a] / q);
+    L.A = 1.0;
+    L.A0 = 1.0;
+    P::sset(L.T, 0.0);
+    P::sset(L.s, 0.0);
+    L.h = P::from_d(h0);
+    L.id = id;
+    L.parent = -1;
+    L.gen = 0;
+    L.seq = 0;
+    L.layer = layer_of(med, zs);
+    L.mode = MODE_NORMAL;
+    L.ev = EV_NONE;
+    L.side = 0;
+    L.it = 0;
+    L.n_acc = L.n_rej = L.n_root = L.n_refl = L.n_turn = L.root_fail = 0;
+    L.status = RP_ST_ALIVE;
+    L.pend = 0;
+    L.tail = 0;
+    load_layer<P>(L.lc, med, L.layer);
+    L.stop_axis = vertical ? 2 : 0;
+    L.stop = plane_of(vertical ? zr : D);
+    L.mp = plane_of(2.0 * (D + zs + zr) + 100.0);
+    init_stop(L, sp);
+    set_trial(L, sp);
+}
+
+// vertical miss at the stop plane: z - z_r; +inf when the path budget ran out first (the ray
+// is far below), NaN for any other end
+template <class P>
+__device__ __forceinline__ double miss_of(const Lane<P> &L, double zr)
+{
+    if (L.status == RP_ST_REACHED_STOP) return P::get(L.r, 2) - zr;
+    if (L.status == RP_ST_MAX_PATH) return __longlong_as_double(0x7ff0000000000000ll);
+    return __longlong_as_double(0x7ff8000000000000ll);
+}
+
+template <class P>
+__device__ __forceinline__ void add_candidate(const Lane<P> &L, long long i, double th,
+                                              int it, double miss, int *cand_n, Cand *cand,
+                                              PfCtrl *ctrl)
+{
+    const int c = atomicAdd(&cand_n[i], 1);
+    if (c >= kMaxCand) {
+        atomicOr(&ctrl->flags, 4u);
+        return;
+    }
+    Cand &o = cand[i * kMaxCand + c];
+    o.type = L.n_refl > 0 ? RP_SOL_REFLECTED : (L.n_turn > 0 ? RP_SOL_REFRACTED : RP_SOL_DIRECT);
+    o.n_iter = it;
+    o.launch = th;
+    o.receive = acos(fmax(-1.0, fmin(1.0, P::get(L.t, 2))));
+    o.time = P::sget(L.T);
+    o.path = P::sget(L.s);
+    o.amp = L.A;
+    o.miss = miss;
+}
+
+struct ScanArgs {
+    PairIn pi;
+    const long long *prefix;
+    double *miss;
+    int *cand_n;
+    Cand *cand;
+    PfCtrl *ctrl;
+    double h0;
+};
+
+// Warp-synchronous driver shared by the scan and the bisection: `next` gives a lane its next
+// ray (false: no more work), `done` consumes a finished ray; between them every lane that
+// still traces takes one Cash-Karp step per iteration; splits and finished rays are serviced
+// in batches as in k_trace_wave.
+template <class P, class Next, class Done>
+__device__ __forceinline__ void drive(const MediumLayered &med, const StepParams<P> &sp,
+                                      const Sinks &sk, PfCtrl *ctrl, Next next, Done done_fn)
+{
+    Lane<P> L;
+    L.stk = 0;
+    unsigned int acc = 0, rej = 0, root = 0, rays = 0;
+    bool active = next(L), done = false;
+    unsigned int iter = 0;
+    while (__any_sync(0xffffffffu, active || done)) {
+        __syncwarp();
+        if (active && L.pend == 0 && advance<P, MediumLayered>(med, L, sp, sk)) {
+            active = false;
+            done = true;
+        }
+        const bool waits = done || (active && L.pend != 0);
+        const unsigned int wait = __ballot_sync(0xffffffffu, waits);
+        const unsigned int step_mask = __ballot_sync(0xffffffffu, active && L.pend == 0);
+        if (wait != 0u && (__popc(wait) >= sp.service_batch ||
+                           ((++iter) & sp.service_mask) == 0u || step_mask == 0u)) {
+            if (active && L.pend != 0 && finish_split<P>(med, L, sp, sk)) {
+                active = false;
+                done = true;
+            }
+            if (done) {
+                acc += (unsigned int)L.n_acc;
+                rej += (unsigned int)L.n_rej;
+                root += (unsigned int)L.n_root;
+                ++rays;
+                done_fn(L);
+                done = false;
+                active = next(L);
+            }
+        }
+    }
+    __syncwarp();
+    acc = __reduce_add_sync(0xffffffffu, acc);
+    rej = __reduce_add_sync(0xffffffffu, rej);
+    root = __reduce_add_sync(0xffffffffu, root);
+    rays = __reduce_add_sync(0xffffffffu, rays);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&ctrl->steps_acc, (unsigned long long)acc);
+        atomicAdd(&ctrl->steps_rej, (unsigned long long)rej);
+        atomicAdd(&ctrl->steps_root, (unsigned long long)root);
+        atomicAdd(&ctrl->rays, (unsigned long long)rays);
+    }
+}
+
+template <class P>
+__global__ void __launch_bounds__(128, P::kMinBlocks)
+    k_scan(const MediumLayered med, const StepParams<P> sp, const Sinks sk, const ScanArgs a)
+{
+    const long long total = a.prefix[a.pi.n_pairs];
+    long long cur = -1, cur_pair = 0;
+    int cur_j = 0;
+    bool cur_vert = false;
+    auto next = [&](Lane<P> &L) -> bool {
+        cur = pf_claim(&a.ctrl->claim_scan);
+        if (cur >= total) return false;
+        cur_pair = pair_of(a.prefix, a.pi.n_pairs, cur);
+        cur_j = (int)(cur - a.prefix[cur_pair]);
+        cur_vert = a.pi.dist[cur_pair] < a.pi.hit_tol;
+        const double pi_ = 3.14159265358979323846;
+        double th;
+        if (cur_vert) {
+            th = a.pi.zr[cur_pair] >= a.pi.zs[cur_pair] ? 0.0 : pi_;
+        } else {
+            const int na = scan_items(a.pi, cur_pair);
+            th = pi_ * (double)cur_j / (double)(na - 1);
+        }
+        launch_ray<P>(L, med, sp, a.pi, a.h0, cur_pair, th, cur_vert, cur);
+        return true;
+    };
+    auto done = [&](Lane<P> &L) {
+        const double m = miss_of<P>(L, a.pi.zr[cur_pair]);
+        a.miss[cur] = m;
+        if (cur_vert && L.status == RP_ST_REACHED_STOP) {
+            const double th = a.pi.zr[cur_pair] >= a.pi.zs[cur_pair] ? 0.0 : 3.14159265358979323846;
+            add_candidate<P>(L, cur_pair, th, 0, 0.0, a.cand_n, a.cand, a.ctrl);
+        }
+    };
+    drive<P>(med, sp, sk, a.ctrl, next, done);
+}
+
+struct BracketArgs {
+    PairIn pi;
+    const long long *prefix;
+    const double *miss;
+    Bracket *br;
+    unsigned long long br_cap;
+    PfCtrl *ctrl;
+};
+
+// adjacent scan angles of one pair with misses of opposite sign (NaN never brackets)
+__global__ void k_brackets(const BracketArgs a)
+{
+    const long long total = a.prefix[a.pi.n_pairs];
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long i = pair_of(a.prefix, a.pi.n_pairs, k);
+        if (a.pi.dist[i] < a.pi.hit_tol) continue;
+        const int na = scan_items(a.pi, i);
+        const int j = (int)(k - a.prefix[i]);
+        if (j + 1 >= na) continue;
+        const double ma = a.miss[k], mb = a.miss[k + 1];
+        if (!((ma > 0.0 && mb < 0.0) || (ma < 0.0 && mb > 0.0))) continue;
+        const unsigned long long b = atomicAdd(&a.ctrl->n_brackets, 1ull);
+        if (b >= a.br_cap) {
+            atomicOr(&a.ctrl->flags, 8u);
+            continue;
+        }
+        const double pi_ = 3.14159265358979323846;
+        Bracket &o = a.br[b];
+        o.tha = pi_ * (double)j / (double)(na - 1);
+        o.thb = pi_ * (double)(j + 1) / (double)(na - 1);
+        o.ma = ma;
+        o.pair = (int)i;
+        o.pad = 0;
+    }
+}
+
+struct BisectArgs {
+    PairIn pi;
+    const Bracket *br;
+    unsigned long long br_cap;
+    int *cand_n;
+    Cand *cand;
+    PfCtrl *ctrl;
+    double h0;
+};
+
+// FP64 bisection on the launch angle, one bracket per lane at a time
+template <class P>
+__global__ void __launch_bounds__(128, P::kMinBlocks)
+    k_bisect(const MediumLayered med, const StepParams<P> sp, const Sinks sk, const BisectArgs a)
+{
+    const unsigned long long nb0 = a.ctrl->n_brackets;
+    const long long nb = (long long)(nb0 < a.br_cap ? nb0 : a.br_cap);
+    double tha = 0.0, thb = 0.0, ma = 0.0, thm = 0.0;
+    int it = 0, pair = 0;
+    // starts the next bisection trace of the current bracket; false if the bracket is done
+    auto step_bracket = [&](Lane<P> &L) -> bool {
+        if (it > a.pi.max_iter) return false;
+        thm = 0.5 * (tha + thb);
+        if (!(thm > tha && thm < thb)) return false;  // bracket exhausted
+        launch_ray<P>(L, med, sp, a.pi, a.h0, pair, thm, false, -1);
+        return true;
+    };
+    auto next = [&](Lane<P> &L) -> bool {
+        for (;;) {
+            const long long b = pf_claim(&a.ctrl->claim_bisect);
+            if (b >= nb) return false;
+            const Bracket &B = a.br[b];
+            tha = B.tha;
+            thb = B.thb;
+            ma = B.ma;
+            pair = B.pair;
+            it = 1;
+            if (step_bracket(L)) return true;
+        }
+    };
+    bool resume = false;  // set by done(): the current bracket continues with a new trace
+    auto done = [&](Lane<P> &L) {
+        const double mm = miss_of<P>(L, a.pi.zr[pair]);
+        resume = false;
+        if (isnan(mm)) return;
+        if (fabs(mm) < a.pi.hit_tol) {
+            add_candidate<P>(L, pair, thm, it, mm, a.cand_n, a.cand, a.ctrl);
+            return;
+        }
+        if ((mm > 0.0) == (ma > 0.0)) {
+            tha = thm;
+            ma = mm;
+        } else {
+            thb = thm;
+        }
+        ++it;
+        resume = true;
+    };
+    auto next_or_resume = [&](Lane<P> &L) -> bool {
+        if (resume) {
+            resume = false;
+            if (step_bracket(L)) return true;
+        }
+        return next(L);
+    };
+    drive<P>(med, sp, sk, a.ctrl, next_or_resume, done);
+}
+
+// per pair: candidates sorted by travel time into the max_sol output slots
+__global__ void k_finalize(const PairIn pi, const int *cand_n, const Cand *cand,
+                           rp_solutions sol)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < pi.n_pairs;
+         i += (long long)gridDim.x * blockDim.x) {
+        int nc = cand_n[i] < kMaxCand ? cand_n[i] : kMaxCand;
+        int order[kMaxCand];
+        for (int c = 0; c < nc; ++c) order[c] = c;
+        for (int c = 1; c < nc; ++c) {  // insertion sort by time, ties by launch angle
+            const int key = order[c];
+            const Cand &K = cand[i * kMaxCand + key];
+            int d = c - 1;
+            while (d >= 0) {
+                const Cand &X = cand[i * kMaxCand + order[d]];
+                if (X.time > K.time || (X.time == K.time && X.launch > K.launch)) {
+                    order[d + 1] = order[d];
+                    --d;
+                } else {
+                    break;
+                }
+            }
+            order[d + 1] = key;
+        }
+        const int keep = nc < pi.max_sol ? nc : pi.max_sol;
+        sol.count[i] = keep;
+        for (int c = 0; c < pi.max_sol; ++c) {
+            const long long o = i * pi.max_sol + c;
+            if (c < keep) {
+                const Cand &X = cand[i * kMaxCand + order[c]];
+                if (sol.type) sol.type[o] = X.type;
+                if (sol.n_iter) sol.n_iter[o] = X.n_iter;
+                if (sol.launch) sol.launch[o] = X.launch;
+                if (sol.receive) sol.receive[o] = X.receive;
+                if (sol.time) sol.time[o] = X.time;
+                if (sol.path) sol.path[o] = X.path;
+                if (sol.amp) sol.amp[o] = X.amp;
+                if (sol.miss) sol.miss[o] = X.miss;
+            } else {
+                if (sol.type) sol.type[o] = 0;
+                if (sol.n_iter) sol.n_iter[o] = 0;
+                if (sol.launch) sol.launch[o] = 0.0;
+                if (sol.receive) sol.receive[o] = 0.0;
+                if (sol.time) sol.time[o] = 0.0;
+                if (sol.path) sol.path[o] = 0.0;
+                if (sol.amp) sol.amp[o] = 0.0;
+                if (sol.miss) sol.miss[o] = 0.0;
+            }
+        }
+    }
+}
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int occ_of(const void *fn)
+{
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 128, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+    return occ > 0 ? occ : 1;
+}
+
+template <class P>
+int run_pf(rp_medium_t m, const PairIn &pi, const rp_trace_params *tp, rp_solutions *sol,
+           rp_stats *stats, cudaStream_t st, int dev)
+{
+    StepParams<P> sp = step_params<P>(tp, 0, 1.0f);
+    sp.use_stop = 1;
+    sp.max_generation = 0;
+    const int occ_s = occ_of((const void *)k_scan<P>);
+    const int occ_b = occ_of((const void *)k_bisect<P>);
+    if (occ_s < 0) return occ_s;
+    if (occ_b < 0) return occ_b;
+    const int sms = sm_count(dev);
+    const long long np = pi.n_pairs;
+    // workspace: path-finding control, tracer control block (for the split code's flags),
+    // prefix sums, candidates and their counts, brackets, then one miss per scan ray
+    const size_t off_pf = 0;
+    const size_t off_tc = al(sizeof(PfCtrl));
+    const size_t off_pre = off_tc + al(sizeof(Ctrl));
+    const size_t off_cn = off_pre + al(sizeof(long long) * (size_t)(np + 1));
+    const size_t off_c = off_cn + al(sizeof(int) * (size_t)np);
+    const size_t br_cap = (size_t)np * 16 + 1024;
+    const size_t off_br = off_c + al(sizeof(Cand) * (size_t)np * kMaxCand);
+    const size_t off_miss = off_br + al(sizeof(Bracket) * br_cap);
+
+    Workspace &ws = workspace(dev);
+    std::lock_guard<std::mutex> lock(ws.mu);
+    int rc = ensure_workspace(ws, off_miss + (8u << 20));
+    if (rc) return rc;
+    long long total = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        char *base = (char *)ws.ptr;
+        RP_CUDA_TRY(cudaMemsetAsync(base, 0, off_pre, st));  // both control blocks
+        k_prefix<<<1, 1024, 0, st>>>(pi, (long long *)(base + off_pre));
+        RP_CUDA_TRY(cudaGetLastError());
+        RP_CUDA_TRY(cudaMemcpyAsync(&total, (long long *)(base + off_pre) + np, sizeof(long long),
+                                    cudaMemcpyDeviceToHost, st));
+        RP_CUDA_TRY(cudaStreamSynchronize(st));
+        const size_t need = off_miss + al(sizeof(double) * (size_t)std::max(total, 1LL));
+        if (need <= ws.size) break;
+        if ((rc = ensure_workspace(ws, need))) return rc;  // grown: contents are gone, redo
+    }
+    char *base = (char *)ws.ptr;
+    PfCtrl *ctrl = (PfCtrl *)(base + off_pf);
+    const long long *prefix = (const long long *)(base + off_pre);
+    int *cand_n = (int *)(base + off_cn);
+    Cand *cand = (Cand *)(base + off_c);
+    Bracket *br = (Bracket *)(base + off_br);
+    double *miss = (double *)(base + off_miss);
+    RP_CUDA_TRY(cudaMemsetAsync(cand_n, 0, sizeof(int) * (size_t)std::max(np, 1LL), st));
+
+    Sinks sk;
+    memset(&sk, 0, sizeof sk);
+    sk.ctrl = (Ctrl *)(base + off_tc);  // flags only: path-finding rays cast no secondaries
+    sk.stack_depth = 0;
+
+    cudaEvent_t ev[3];
+    for (int k = 0; k < 3; ++k) RP_CUDA_TRY(cudaEventCreate(&ev[k]));
+    RP_CUDA_TRY(cudaEventRecord(ev[0], st));
+    ScanArgs sa;
+    sa.pi = pi;
+    sa.prefix = prefix;
+    sa.miss = miss;
+    sa.cand_n = cand_n;
+    sa.cand = cand;
+    sa.ctrl = ctrl;
+    sa.h0 = tp->h0;
+    k_scan<P><<<sms * occ_s, 128, 0, st>>>(m->layered, sp, sk, sa);
+    BracketArgs ba;
+    ba.pi = pi;
+    ba.prefix = prefix;
+    ba.miss = miss;
+    ba.br = br;
+    ba.br_cap = br_cap;
+    ba.ctrl = ctrl;
+    k_brackets<<<sms * 8, 256, 0, st>>>(ba);
+    RP_CUDA_TRY(cudaEventRecord(ev[1], st));
+    BisectArgs bb;
+    bb.pi = pi;
+    bb.br = br;
+    bb.br_cap = br_cap;
+    bb.cand_n = cand_n;
+    bb.cand = cand;
+    bb.ctrl = ctrl;
+    bb.h0 = tp->h0;
+    k_bisect<P><<<sms * occ_b, 128, 0, st>>>(m->layered, sp, sk, bb);
+    k_finalize<<<std::max(1, (int)std::min<long long>((np + 255) / 256, (long long)sms * 8)), 256,
+                 0, st>>>(pi, cand_n, cand, *sol);
+    RP_CUDA_TRY(cudaEventRecord(ev[2], st));
+    RP_CUDA_TRY(cudaGetLastError());
+    PfCtrl hc;
+    unsigned int tflags = 0;
+    RP_CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof hc, cudaMemcpyDeviceToHost, st));
+    RP_CUDA_TRY(cudaMemcpyAsync(&tflags, &sk.ctrl->flags, sizeof tflags, cudaMemcpyDeviceToHost, st));
+    RP_CUDA_TRY(cudaStreamSynchronize(st));
+    float ms_scan = 0.0f, ms_all = 0.0f;
+    cudaEventElapsedTime(&ms_scan, ev[0], ev[1]);
+    cudaEventElapsedTime(&ms_all, ev[0], ev[2]);
+    for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[k]);
+    if (stats) {
+        stats->rays = (int64_t)hc.rays;
+        stats->steps_accepted = (int64_t)hc.steps_acc;
+        stats->steps_rejected = (int64_t)hc.steps_rej;
+        stats->steps_root = (int64_t)hc.steps_root;
+        stats->queue_needed = (int64_t)hc.n_brackets;
+        stats->waves = 2;
+        stats->flags = (int32_t)(hc.flags | tflags);
+        stats->kernel_ms = ms_all;
+        stats->wave_ms[0] = ms_scan;
+        stats->wave_ms[1] = ms_all - ms_scan;
+    }
+    if (hc.flags & 12u) {
+        set_error("rp_find_paths: more than %d candidate solutions of a pair or more than %zu "
+                  "brackets; the kept solutions may not be the earliest",
+                  kMaxCand, br_cap);
+        return RP_ERR_OVERFLOW;
+    }
+    return RP_OK;
+}
+
+}  // namespace
+
+int run_find_paths(rp_medium_t m, int64_t n_pairs, const double *zs, const double *zr,
+                   const double *dist, const int32_t *n_angles, const rp_path_params *p,
+                   rp_solutions *sol, rp_stats *stats, cudaStream_t st)
+{
+    if (!m || !p || !sol || n_pairs < 0) {
+        set_error("rp_find_paths: null medium, params or solutions, or n_pairs < 0");
+        return RP_ERR_INVALID_ARG;
+    }
+    if (m->kind != RP_MEDIUM_LAYERED) {
+        set_error("rp_find_paths: path finding needs a layered medium");
+        return RP_ERR_INVALID_ARG;
+    }
+    if (n_pairs == 0) return RP_OK;
+    if (!zs || !zr || !dist || !n_angles || !sol->count) {
+        set_error("rp_find_paths: null pair or count array");
+        return RP_ERR_INVALID_ARG;
+    }
+    if (!(p->hit_tol > 0.0) || p->max_iter < 1 || p->max_iter > 200 || p->max_sol < 1 ||
+        p->max_sol > 8) {
+        set_error("rp_find_paths: need hit_tol > 0, 1 <= max_iter <= 200, 1 <= max_sol <= 8");
+        return RP_ERR_INVALID_ARG;
+    }
+    int rc = validate_params(&p->trace, true);
+    if (rc) return rc;
+    int dev;
+    RP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != m->device) {
+        set_error("rp_find_paths: medium lives on device %d, current device is %d", m->device, dev);
+        return RP_ERR_INVALID_ARG;
+    }
+    PairIn pi;
+    pi.zs = zs;
+    pi.zr = zr;
+    pi.dist = dist;
+    pi.n_angles = n_angles;
+    pi.n_pairs = n_pairs;
+    pi.hit_tol = p->hit_tol;
+    pi.max_iter = p->max_iter;
+    pi.max_sol = p->max_sol;
+    if (p->trace.precision == RP_FP64)
+        return run_pf<PrecF64>(m, pi, &p->trace, sol, stats, st, dev);
+    return run_pf<PrecF32>(m, pi, &p->trace, sol, stats, st, dev);
+}
+
 }  // namespace rph

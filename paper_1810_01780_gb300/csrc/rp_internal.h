@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <cstdlib>
 #include <mutex>
 
 #include "rp.h"
@@ -55,6 +56,54 @@ inline rpk::PlaneC plane_const(double d)
 }
 
 int validate_params(const rp_trace_params *p, bool path_finding);
+
+// Service-phase batching (see k_trace_wave): lanes waiting before a service, and the period
+// in iterations (a power of two).  RP_SERVICE_BATCH / RP_SERVICE_PERIOD override them.
+inline int env_int(const char *name, int dflt, int lo, int hi)
+{
+    const char *v = getenv(name);
+    if (!v || !*v) return dflt;
+    int x = atoi(v);
+    return x < lo ? lo : (x > hi ? hi : x);
+}
+inline int service_batch() { return env_int("RP_SERVICE_BATCH", 8, 1, 32); }
+inline int service_period()
+{
+    int p = env_int("RP_SERVICE_PERIOD", 16, 1, 1024), q = 1;
+    while (q < p) q <<= 1;
+    return q;
+}
+
+template <class P>
+inline rpk::StepParams<P> step_params(const rp_trace_params *p, int axis, float dir)
+{
+    rpk::StepParams<P> sp;
+    sp.tol = (typename P::R)p->tol;
+    sp.inv_tol = (typename P::R)(1.0 / p->tol);
+    sp.h_min = (typename P::R)p->h_min;
+    sp.h_max = (typename P::R)p->h_max;
+    double eps = p->eps_b;
+    if (P::kFF && eps < 2e-6) eps = 2e-6;
+    sp.eps_b = (typename P::R)eps;
+    sp.max_path = p->max_path;
+    sp.max_time = p->max_time;
+    sp.min_amp = p->min_amp;
+    sp.mp = plane_const(p->max_path);
+    sp.mt = plane_const(p->max_time);
+    sp.use_max_time = p->max_time > 0.0;
+    sp.use_min_amp = p->min_amp > 0.0;
+    sp.rhs_form = p->rhs_form;
+    sp.polarization = p->polarization;
+    sp.max_generation = p->max_generation;
+    sp.use_stop = p->use_stop;
+    sp.stop_axis = axis;
+    sp.stop_dir = dir;
+    sp.max_steps = p->max_steps;
+    sp.service_batch = service_batch();
+    sp.service_mask = service_period() - 1;
+    return sp;
+}
+
 
 // A caller-provided device scratch region used instead of the grow-only workspace.
 struct FixedScratch {

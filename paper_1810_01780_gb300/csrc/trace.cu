@@ -52,6 +52,8 @@ __device__ __forceinline__ void lane_reset(Lane<P> &L, const M &med, const StepP
     L.status = RP_ST_ALIVE;
     L.pend = 0;
     L.stop = stop;
+    L.stop_axis = sp.stop_axis;
+    L.mp = sp.mp;
     init_stop(L, sp);
     set_trial(L, sp);
 }
@@ -338,53 +340,6 @@ static int launch_waves(const M &med, const StepParams<P> &sp, const Sinks &sk, 
     return RP_OK;
 }
 
-// Service-phase batching (see k_trace_wave): lanes waiting before a service, and the period
-// in iterations (a power of two).  RP_SERVICE_BATCH / RP_SERVICE_PERIOD override them.
-static int env_int(const char *name, int dflt, int lo, int hi)
-{
-    const char *v = getenv(name);
-    if (!v || !*v) return dflt;
-    int x = atoi(v);
-    return x < lo ? lo : (x > hi ? hi : x);
-}
-static int service_batch() { return env_int("RP_SERVICE_BATCH", 8, 1, 32); }
-static int service_period()
-{
-    int p = env_int("RP_SERVICE_PERIOD", 16, 1, 1024), q = 1;
-    while (q < p) q <<= 1;
-    return q;
-}
-
-template <class P>
-static StepParams<P> make_step_params(const rp_trace_params *p, int axis, float dir)
-{
-    StepParams<P> sp;
-    sp.tol = (typename P::R)p->tol;
-    sp.inv_tol = (typename P::R)(1.0 / p->tol);
-    sp.h_min = (typename P::R)p->h_min;
-    sp.h_max = (typename P::R)p->h_max;
-    double eps = p->eps_b;
-    if (P::kFF && eps < 2e-6) eps = 2e-6;
-    sp.eps_b = (typename P::R)eps;
-    sp.max_path = p->max_path;
-    sp.max_time = p->max_time;
-    sp.min_amp = p->min_amp;
-    sp.mp = plane_const(p->max_path);
-    sp.mt = plane_const(p->max_time);
-    sp.use_max_time = p->max_time > 0.0;
-    sp.use_min_amp = p->min_amp > 0.0;
-    sp.rhs_form = p->rhs_form;
-    sp.polarization = p->polarization;
-    sp.max_generation = p->max_generation;
-    sp.use_stop = p->use_stop;
-    sp.stop_axis = axis;
-    sp.stop_dir = dir;
-    sp.max_steps = p->max_steps;
-    sp.service_batch = service_batch();
-    sp.service_mask = service_period() - 1;
-    return sp;
-}
-
 // Stop plane stop_n . r = stop_d with stop_n = +/- a coordinate axis.
 int stop_axis_of(const rp_trace_params *p, int *axis, float *dir, double *offset)
 {
@@ -605,18 +560,18 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     if (m->kind == RP_MEDIUM_LAYERED) {
         if (p->precision == RP_FP64)
             rc = launch_waves<PrecF64, MediumLayered>(m->layered,
-                                                      make_step_params<PrecF64>(p, axis, sdir),
+                                                      step_params<PrecF64>(p, axis, sdir),
                                                       sk, wi, n_waves, dev, block, st, ev);
         else
             rc = launch_waves<PrecF32, MediumLayered>(m->layered,
-                                                      make_step_params<PrecF32>(p, axis, sdir),
+                                                      step_params<PrecF32>(p, axis, sdir),
                                                       sk, wi, n_waves, dev, block, st, ev);
     } else {
         if (p->precision == RP_FP64)
-            rc = launch_waves<PrecF64, MediumGrid>(m->grid, make_step_params<PrecF64>(p, axis, sdir),
+            rc = launch_waves<PrecF64, MediumGrid>(m->grid, step_params<PrecF64>(p, axis, sdir),
                                                    sk, wi, n_waves, dev, block, st, ev);
         else
-            rc = launch_waves<PrecF32, MediumGrid>(m->grid, make_step_params<PrecF32>(p, axis, sdir),
+            rc = launch_waves<PrecF32, MediumGrid>(m->grid, step_params<PrecF32>(p, axis, sdir),
                                                    sk, wi, n_waves, dev, block, st, ev);
     }
     // read-back: pinned buffers of the workspace, or (fixed scratch) pageable host memory and

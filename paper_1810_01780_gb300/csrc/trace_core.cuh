@@ -123,6 +123,15 @@ struct PlaneC {
     float hi, lo;
 };
 
+__host__ __device__ __forceinline__ PlaneC plane_of(double d)
+{
+    PlaneC c;
+    c.d = d;
+    c.hi = (float)d;
+    c.lo = (float)(d - (double)c.hi);
+    return c;
+}
+
 // ---------------------------------------------------------------------------------------
 // Precision policies
 // ---------------------------------------------------------------------------------------
@@ -589,7 +598,9 @@ struct Lane {
     R h, h_next, h_try;
     R ra, rb, ga, gb;  // root bracket
     PlaneC stop;       // stop plane offset along stop_axis
-    R stop_sign;
+    R stop_sign;       // orientation: the event distance is stop_sign * (r[axis] - offset)
+    PlaneC mp;         // path budget of this ray (max_path)
+    int32_t stop_axis;
     long long id, parent;
     int32_t mode, ev, side, it, last;
     int32_t layer, gen, seq;
@@ -621,12 +632,12 @@ struct StepParams {
 // Offset of the candidate r + dr from the stop plane along the stop axis (selected without
 // dynamic indexing so that the state stays in registers).
 template <class P>
-__device__ __forceinline__ typename P::R stop_rel(const Lane<P> &L, const StepParams<P> &sp,
+__device__ __forceinline__ typename P::R stop_rel(const Lane<P> &L, const StepParams<P> &,
                                                   const typename P::R dr[3])
 {
-    return sp.stop_axis == 0   ? P::rel(L.r, 0, dr[0], L.stop)
-           : sp.stop_axis == 1 ? P::rel(L.r, 1, dr[1], L.stop)
-                               : P::rel(L.r, 2, dr[2], L.stop);
+    return L.stop_axis == 0   ? P::rel(L.r, 0, dr[0], L.stop)
+           : L.stop_axis == 1 ? P::rel(L.r, 1, dr[1], L.stop)
+                              : P::rel(L.r, 2, dr[2], L.stop);
 }
 
 template <class P>
@@ -635,7 +646,7 @@ __device__ __forceinline__ void set_trial(Lane<P> &L, const StepParams<P> &sp)
     typedef typename P::R R;
     L.last = 0;
     if constexpr (P::kFF) {
-        const R rem = -P::sdiff(L.s, sp.mp);  // max_path - s
+        const R rem = -P::sdiff(L.s, L.mp);  // max_path - s
         if (L.h >= rem) {
             L.h_try = rem;
             L.last = 1;
@@ -643,8 +654,8 @@ __device__ __forceinline__ void set_trial(Lane<P> &L, const StepParams<P> &sp)
             L.h_try = L.h;
         }
     } else {
-        if (L.s + L.h >= sp.max_path) {
-            L.h_try = sp.max_path - L.s;
+        if (L.s + L.h >= L.mp.d) {
+            L.h_try = L.mp.d - L.s;
             L.last = 1;
         } else {
             L.h_try = L.h;
@@ -663,15 +674,14 @@ __device__ __forceinline__ typename P::R event_g(const MediumLayered &m, const L
     typedef typename P::R R;
     if (kind == EV_TOP) return P::rel(L.r, 2, dr[2], L.lc.top);
     if (kind == EV_BOTTOM) return -P::rel(L.r, 2, dr[2], L.lc.bot);
-    return L.stop_sign * (R(sp.stop_dir) * stop_rel(L, sp, dr));
+    return L.stop_sign * stop_rel(L, sp, dr);
 }
 template <class P>
 __device__ __forceinline__ typename P::R event_g(const MediumGrid &, const Lane<P> &L,
                                                  const StepParams<P> &sp, int,
                                                  const typename P::R dr[3])
 {
-    typedef typename P::R R;
-    return L.stop_sign * (R(sp.stop_dir) * stop_rel(L, sp, dr));
+    return L.stop_sign * stop_rel(L, sp, dr);
 }
 
 __device__ __forceinline__ bool is_layered(const MediumLayered &) { return true; }
@@ -685,9 +695,10 @@ __device__ __forceinline__ void init_stop(Lane<P> &L, const StepParams<P> &sp)
 {
     typedef typename P::R R;
     if (sp.use_stop) {
+        // the start side counts as positive; f = n . r - d with n = stop_dir along the axis
         const R zero[3] = {R(0), R(0), R(0)};
-        R f = R(sp.stop_dir) * stop_rel(L, sp, zero);
-        L.stop_sign = (f <= R(0)) ? R(-1) : R(1);
+        const R f = R(sp.stop_dir) * stop_rel(L, sp, zero);
+        L.stop_sign = ((f <= R(0)) ? R(-1) : R(1)) * R(sp.stop_dir);
     } else {
         L.stop_sign = R(1);
     }
@@ -797,7 +808,7 @@ __device__ __forceinline__ void receivers_on_chord(const Sinks &sk, const Lane<P
         const long long cap = sk.hits.capacity;
         const double l = (double)lam;
         const double T0 = P::sget(L.T), s0 = P::sget(L.s);
-        const double ds = to_max_path ? sp.max_path - s0 : (double)hc;
+        const double ds = to_max_path ? L.mp.d - s0 : (double)hc;
         if (sk.hits.ray) sk.hits.ray[k] = L.id;
         if (sk.hits.receiver) sk.hits.receiver[k] = S.idx;
         if (sk.hits.time) sk.hits.time[k] = T0 + l * (double)dT;
@@ -1026,9 +1037,9 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
         }
     } else if (ev == EV_STOP) {
         const R off = stop_rel(L, sp, dr);
-        if (sp.stop_axis == 0)
+        if (L.stop_axis == 0)
             dr[0] -= off;
-        else if (sp.stop_axis == 1)
+        else if (L.stop_axis == 1)
             dr[1] -= off;
         else
             dr[2] -= off;
@@ -1050,9 +1061,9 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
             P::snap(L.r, 2, (ev == EV_TOP) ? L.lc.top : L.lc.bot);
         }
     } else if (ev == EV_STOP) {
-        if (sp.stop_axis == 0)
+        if (L.stop_axis == 0)
             P::snap(L.r, 0, L.stop);
-        else if (sp.stop_axis == 1)
+        else if (L.stop_axis == 1)
             P::snap(L.r, 1, L.stop);
         else
             P::snap(L.r, 2, L.stop);
@@ -1067,7 +1078,7 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
     }
     P::sadd(L.T, dT);
     if (to_max_path)
-        P::sset(L.s, sp.max_path);
+        P::sset(L.s, L.mp.d);
     else
         P::sadd(L.s, hc);
     ++L.n_acc;
