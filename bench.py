@@ -306,6 +306,61 @@ def run_gpu(args):
                "time_s": {"p50": float(dT.quantile(0.5)), "p99": float(dT.quantile(0.99)),
                           "max": float(dT.max())}}
 
+    # gridded medium: 256 x 256 x 512 FP32 grid, 4,194,304 rays (FP32-mixed), its own
+    # figures (memory-bound path: algorithmic bytes = 8 float4 corner samples per medium
+    # evaluation, 6 evaluations per attempted step)
+    if not args.no_grid:
+        gcfg = W.gridded()
+        gmed = rp.Medium(gcfg["medium"])
+        grays = rp.PreparedRays(*gcfg["rays"])
+        gbuf = rp.TraceBuffers(grays.n + 16, 0, fields=("end_pos", "path", "time", "status"))
+        gprm = rp.make_params(gcfg["params"], "fp32")
+        rp.trace_into(gmed, grays, gprm, gbuf)  # warm-up
+        gt, gatt, gacc, gr = [], 0, 0, 0
+        for _ in range(args.grid_steps):
+            flush.fill_(1.0)
+            st = rp.trace_into(gmed, grays, gprm, gbuf)
+            gt.append(st.kernel_ms)
+            gacc += st.steps_accepted
+            gatt += st.steps_accepted + st.steps_rejected + st.steps_root
+            gr += st.rays
+        gsec = sum(gt) / 1e3
+        bytes_alg = 768.0 * gatt
+        modes["grid_fp32_mixed"] = {
+            "workload": "256x256x512 FP32 grid (4 m), 4,194,304 rays from 16 sources, tol 1e-5",
+            "ray_steps_per_s": gacc / gsec, "rays_per_s": gr / gsec,
+            "ms_per_step": 1e3 * gsec / len(gt),
+            "algorithmic_GBps": bytes_alg / gsec / 1e9,
+            "algorithmic_bytes_per_attempted_step": 768,
+            "hbm_peak_GBps": _peaks().get("hbm_gbs"),
+        }
+        del gmed, grays, gbuf
+
+    # source-receiver path finding: 65,536 pairs, 32..512 scan angles each, FP64 bisection
+    if not args.no_paths:
+        pcfg = W.paths()
+        P = pcfg["pairs"]
+        pbuf = rp.PathBuffers(P["zs"], P["zr"], P["dist"], P["n_angles"], pcfg["max_sol"])
+        pprm = rp.make_path_params(pcfg["params"], "fp32", pcfg["hit_tol"], pcfg["max_iter"],
+                                   pcfg["max_sol"])
+        rp.find_paths_into(med_paths := rp.Medium(pcfg["medium"]), pbuf, pprm)  # warm-up
+        pt, nsol, prays, pacc = [], 0, 0, 0
+        for _ in range(args.paths_steps):
+            flush.fill_(1.0)
+            st = rp.find_paths_into(med_paths, pbuf, pprm)
+            pt.append(st.kernel_ms)
+            nsol += int(pbuf.count.sum())
+            prays += st.rays
+            pacc += st.steps_accepted
+        psec = sum(pt) / 1e3
+        modes["paths_fp32_mixed"] = {
+            "workload": "65,536 source-receiver pairs, 32..512 scan angles, FP64 bisection to "
+                        "0.1 m, up to 4 solutions per pair",
+            "solutions_per_s": nsol / psec, "pairs_per_s": len(P["zs"]) * len(pt) / psec,
+            "rays_per_s": prays / psec, "ray_steps_per_s": pacc / psec,
+            "ms_per_step": 1e3 * psec / len(pt),
+        }
+
     # roofline of the dominant kernel (the FP32 tracing launches): FP32 ALU bound
     sm_mhz = clocks["sm_mhz"] or _peaks().get("sm_max_mhz", 2070.0)
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
@@ -349,6 +404,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-grid", action="store_true")
+    ap.add_argument("--no-paths", action="store_true")
+    ap.add_argument("--paths-steps", type=int, default=3)
+    ap.add_argument("--grid-steps", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=65536)
