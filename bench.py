@@ -37,10 +37,12 @@ WORKLOAD = ("batched two-layer ice: 1,048,576 isotropic rays, sources 50-1500 m,
             "boundary at 100 m (+0.02), surface reflection, secondaries to generation 3, "
             "64 receivers, tol 1e-6, h 1e-3..10 m, 3 km paths")
 N_RAYS = 1_048_576
-# FP32 flops of one attempted Cash-Karp step of the FP32-mixed path in a layered analytic
-# medium, counted from trace_core.cuh (FMA = 2); exp, reciprocal, sqrt and pow are extra
-# (special-function unit) and not included.  Derivation in the design notes.
-FLOPS_PER_ATTEMPT_F32 = 540
+# Algorithmic FP32 flops of one attempted Cash-Karp step of the FP32-mixed path in a layered
+# analytic medium, counted from trace_core.cuh (FMA = 2, a sum of m products = 2m - 1): stage
+# combinations 100, stage states 40, medium 30, projection 48, fifth-order sums 49, error sums
+# 54, increments 14, error norms 11, control 3, event tests 10, float-float state update 80.
+# The 6 exp, 6 reciprocals, 2 square roots and the pow of the step control are not counted.
+FLOPS_PER_ATTEMPT_F32 = 439
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
