@@ -196,3 +196,39 @@ def paths(n=65_536, seed=4):
     return dict(name="paths", medium=ice_with_surface(),
                 params=dict(TRACE_DEFAULTS, max_path=10000.0, max_generation=0),
                 pairs=pairs(n, seed), hit_tol=0.1, max_iter=60, max_sol=4)
+
+
+# ---------------------------------------------------------------------------------------
+# surrogate network: layer sizes and seeded initial weights (inputs of both sides)
+# ---------------------------------------------------------------------------------------
+
+MLP_DIMS = (3, 256, 256, 256, 256, 12)
+
+
+def mlp_init(seed: int = 0, dims=MLP_DIMS):
+    """Seeded initial weights W[l] (in, out) float32, uniform in +-sqrt(6 / fan_in) for the
+    hidden layers and +-sqrt(1 / fan_in) for the output layer; zero biases."""
+    rng = np.random.default_rng(seed)
+    W, b = [], []
+    for i in range(len(dims) - 1):
+        lim = math.sqrt(6.0 / dims[i]) if i < len(dims) - 2 else math.sqrt(1.0 / dims[i])
+        W.append(rng.uniform(-lim, lim, (dims[i], dims[i + 1])).astype(np.float32))
+        b.append(np.zeros(dims[i + 1], dtype=np.float32))
+    return W, b
+
+
+def mlp_flatten(W, b):
+    """Flat float32 parameter vector in the library's order: W0, b0, W1, b1, ..., W4, b4."""
+    return np.concatenate([np.concatenate([w.ravel(), c.ravel()]) for w, c in zip(W, b)]).astype(
+        np.float32)
+
+
+def mlp_unflatten(flat, dims=MLP_DIMS):
+    W, b, o = [], [], 0
+    for i in range(len(dims) - 1):
+        n = dims[i] * dims[i + 1]
+        W.append(np.asarray(flat[o:o + n], dtype=np.float32).reshape(dims[i], dims[i + 1]))
+        o += n
+        b.append(np.asarray(flat[o:o + dims[i + 1]], dtype=np.float32))
+        o += dims[i + 1]
+    return W, b
