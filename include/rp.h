@@ -258,6 +258,46 @@ int rp_find_paths(rp_medium_t m, int64_t n_pairs, const double *z_s, const doubl
                   rp_solutions *sol, rp_stats *stats, void *stream);
 
 /* ------------------------------------------------------------------------------------
+ * Learned surrogate of the path finder (not in the paper: a model that maps a
+ * source-receiver geometry to the path finder's solutions)
+ * ---------------------------------------------------------------------------------- */
+
+/* Network 3 -> 256 -> 256 -> 256 -> 256 -> 12, GELU (0.5 x (1 + erf(x / sqrt 2))) after each
+ * hidden layer.  Parameters are one flat float32 vector W0, b0, W1, b1, ..., W4, b4 with W_l
+ * stored (in, out) row-major.  FP32 master weights; every product runs on the tensor cores
+ * with BF16 operands (weights and activations rounded to BF16) and FP32 accumulation.
+ * Inputs x: (n, 3) float32 rows; outputs: (n, 12) float32 rows = for slot k = 0, 1:
+ * existence logit, then five regression outputs (see rp_surrogate_encode). */
+typedef struct rp_surrogate_s *rp_surrogate_t;
+
+/* Number of parameters (201,740). */
+int rp_surrogate_n_params(void);
+
+/* Creates a network on the current device from `params` (host or device, copied); Adam
+ * state zeroed. */
+int rp_surrogate_create(const float *params, rp_surrogate_t *out);
+int rp_surrogate_destroy(rp_surrogate_t s);
+
+/* Replaces the parameters (host or device pointer; Adam state reset) / copies them out. */
+int rp_surrogate_set_params(rp_surrogate_t s, const float *params);
+int rp_surrogate_get_params(rp_surrogate_t s, float *params);
+
+/* out (n, 12) = network(x (n, 3)).  Device pointers. */
+int rp_surrogate_forward(rp_surrogate_t s, int64_t n, const float *x, float *out, void *stream);
+
+/* Mean loss over n rows and its gradient (flat, like the parameters; device or host pointer,
+ * may be NULL) without updating.  y: (n, 2) existence targets in {0, 1}; t: (n, 10) regression
+ * targets (slot-major).  Loss per row: for each slot, softplus(logit) - y logit
+ * + y * 0.5 * |regression outputs - t|^2. */
+int rp_surrogate_loss_grad(rp_surrogate_t s, int64_t n, const float *x, const float *y,
+                           const float *t, double *loss, float *grad, void *stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the mean loss of the n
+ * rows; *loss (may be NULL) receives that loss before the update. */
+int rp_surrogate_train_step(rp_surrogate_t s, int64_t n, const float *x, const float *y,
+                            const float *t, float lr, double *loss, void *stream);
+
+/* ------------------------------------------------------------------------------------
  * Misc
  * ---------------------------------------------------------------------------------- */
 

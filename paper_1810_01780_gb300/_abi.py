@@ -113,6 +113,17 @@ SIGNATURES = {
     "rp_find_paths": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.POINTER(PathParams), C.POINTER(Solutions),
                                 C.POINTER(Stats), C.c_void_p]),
+    "rp_surrogate_n_params": (C.c_int, []),
+    "rp_surrogate_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "rp_surrogate_destroy": (C.c_int, [C.c_void_p]),
+    "rp_surrogate_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rp_surrogate_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rp_surrogate_forward": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rp_surrogate_loss_grad": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.POINTER(C.c_double), C.c_void_p, C.c_void_p]),
+    "rp_surrogate_train_step": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_float, C.POINTER(C.c_double),
+                                          C.c_void_p]),
     "rp_last_error": (C.c_int, [C.c_char_p, C.c_size_t]),
     "rp_version": (C.c_char_p, []),
 }

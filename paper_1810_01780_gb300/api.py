@@ -270,3 +270,71 @@ def find_paths(medium: Medium, zs, zr, dist, n_angles, params: dict, precision: 
     out.update(buf.t)
     out["stats"] = st.as_dict()
     return out
+
+
+class Surrogate:
+    """The surrogate network on the device (rp_surrogate_*)."""
+
+    def __init__(self, params=None, seed: int = 0):
+        from . import workloads as Wl
+
+        A.lib()
+        if params is None:
+            params = Wl.mlp_flatten(*Wl.mlp_init(seed))
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        if params.size != A.lib().rp_surrogate_n_params():
+            raise ValueError("parameter vector has the wrong length")
+        h = C.c_void_p()
+        A.check(A.lib().rp_surrogate_create(C.c_void_p(params.ctypes.data), C.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            A.lib().rp_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(A.lib().rp_surrogate_n_params(), dtype=np.float32)
+        A.check(A.lib().rp_surrogate_get_params(self.handle, C.c_void_p(out.ctypes.data)))
+        return out
+
+    def set_params(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        A.check(A.lib().rp_surrogate_set_params(self.handle, C.c_void_p(params.ctypes.data)))
+
+    @staticmethod
+    def _f32(x, cols):
+        t = torch.as_tensor(x, dtype=torch.float32, device="cuda").contiguous()
+        return t.reshape(-1, cols)
+
+    def forward(self, x, stream=None):
+        x = self._f32(x, 3)
+        out = torch.empty((x.shape[0], 12), dtype=torch.float32, device="cuda")
+        A.check(A.lib().rp_surrogate_forward(self.handle, x.shape[0], C.c_void_p(x.data_ptr()),
+                                             C.c_void_p(out.data_ptr()),
+                                             C.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def loss_grad(self, x, y, t, stream=None):
+        x, y, t = self._f32(x, 3), self._f32(y, 2), self._f32(t, 10)
+        g = torch.empty(A.lib().rp_surrogate_n_params(), dtype=torch.float32, device="cuda")
+        L = C.c_double()
+        A.check(A.lib().rp_surrogate_loss_grad(self.handle, x.shape[0], C.c_void_p(x.data_ptr()),
+                                               C.c_void_p(y.data_ptr()), C.c_void_p(t.data_ptr()),
+                                               C.byref(L), C.c_void_p(g.data_ptr()),
+                                               C.c_void_p(_stream_ptr(stream))))
+        return L.value, g
+
+    def train_step(self, x, y, t, lr: float, stream=None) -> float:
+        L = C.c_double()
+        A.check(A.lib().rp_surrogate_train_step(self.handle, x.shape[0], C.c_void_p(x.data_ptr()),
+                                                C.c_void_p(y.data_ptr()),
+                                                C.c_void_p(t.data_ptr()), C.c_float(lr),
+                                                C.byref(L), C.c_void_p(_stream_ptr(stream))))
+        return L.value
