@@ -180,6 +180,103 @@ def _peaks():
         return {}
 
 
+MLP_FLOPS_FWD = 2 * (3 * 256 + 3 * 256 * 256 + 256 * 12)  # per row, multiply-adds x 2
+
+
+def _sync_time(fn):
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, out
+
+
+def surrogate_leg(rp, W, args, rank, flush):
+    import torch
+
+    scfg = W.surrogate(n_train=args.sur_train, n_query=args.sur_queries, seed=5 + 16 * rank)
+    med = rp.Medium(scfg["medium"])
+    P, tr, q = scfg["params"], scfg["train"], scfg["queries"]
+    t_lab, lab = _sync_time(lambda: rp.find_paths(
+        med, tr["zs"], tr["zr"], tr["dist"], tr["n_angles"], P, "fp32",
+        hit_tol=scfg["label_hit_tol"], max_iter=scfg["max_iter"], max_sol=scfg["max_sol"]))
+    x, y, t = rp.encode(tr["zs"], tr["zr"], tr["dist"], lab)
+    del lab
+    net = rp.Surrogate(seed=0)
+    sch = scfg["schedule"]
+    t_train, loss = _sync_time(lambda: net.train(x, y, t, epochs=sch["epochs"], batch=sch["batch"],
+                                                 lr=sch["lr"], lr_final=sch["lr_final"],
+                                                 seed=sch["seed"]))
+    n_steps = sch["epochs"] * (len(tr["zs"]) // sch["batch"])
+    del x, y, t
+    buf = rp.PathBuffers(q["zs"], q["zr"], q["dist"], q["n_angles"], scfg["max_sol"])
+    pprm = rp.make_path_params(P, "fp32", scfg["hit_tol"], scfg["max_iter"], scfg["max_sol"])
+    sprm = rp.make_surrogate_params(**scfg["infer"])
+    net.find_paths_into(med, buf, pprm, sprm)  # warm-up (sizes the buffers)
+    t_inf, n_sol, agg = [], 0, {}
+    for _ in range(args.paths_steps):
+        flush.fill_(1.0)
+        dt, st = _sync_time(lambda: net.find_paths_into(med, buf, pprm, sprm))
+        t_inf.append(dt)
+        n_sol += int(buf.count.sum())
+        for k, v in st.as_dict().items():
+            agg[k] = agg.get(k, 0) + v
+    sur = {k: buf.t[k][:args.sur_check].cpu().numpy() for k in ("launch", "time")}
+    sur_count = buf.count[:args.sur_check].cpu().numpy()
+    sec = sum(t_inf)
+    sol_s = n_sol / sec
+    # the plain path finder on the same queries, same tolerance
+    flush.fill_(1.0)
+    t_plain, _ = _sync_time(lambda: rp.find_paths_into(med, buf, pprm))
+    plain_sol_s = int(buf.count.sum()) / t_plain
+    # error against the FP64 path finder (0.1 mm) on the first queries; count mismatches
+    # decided by an 8192-angle FP64 scan
+    m = args.sur_check
+    truth = rp.find_paths(med, q["zs"][:m], q["zr"][:m], q["dist"][:m], q["n_angles"][:m], P,
+                          "fp64", hit_tol=1e-4, max_iter=80, max_sol=scfg["max_sol"])
+    tc = truth["count"].cpu().numpy()
+    tl, tt = truth["launch"].cpu().numpy(), truth["time"].cpu().numpy()
+    bad = np.nonzero(sur_count != tc)[0]
+    adj = tc.copy()
+    if len(bad):
+        fine = rp.find_paths(med, q["zs"][bad], q["zr"][bad], q["dist"][bad],
+                             np.full(len(bad), 8192, np.int32), P, "fp64", hit_tol=1e-4,
+                             max_iter=80, max_sol=scfg["max_sol"])
+        adj[bad] = fine["count"].cpu().numpy()
+    errs = []
+    for i in np.nonzero((sur_count > 0) & (tc > 0))[0]:
+        for j in range(sur_count[i]):
+            k = int(np.argmin(np.abs(tl[i, :tc[i]] - sur["launch"][i, j])))
+            errs.append(abs(sur["time"][i, j] - tt[i, k]))
+    errs = np.array(errs) if errs else np.zeros(1)
+    nq = len(q["zs"]) * len(t_inf)
+    return {
+        "workload": f"MLP 3-256x4-12 trained on {len(tr['zs']):,} path-finder-labelled pairs; "
+                    f"inference on {len(q['zs']):,} queries, secant/Illinois refinement to a "
+                    "5 mm receiver miss, fallback to the path finder",
+        "solutions_per_s": sol_s, "pairs_per_s": nq / sec,
+        "plain_path_finder_solutions_per_s": plain_sol_s, "gain_vs_plain": sol_s / plain_sol_s,
+        "ms_per_step": 1e3 * sec / len(t_inf),
+        "fallback_fraction": agg["fallback"] / agg["queries"],
+        "refine_rays_per_query": agg["refine_rays"] / agg["queries"],
+        "ray_steps_per_s": (agg["refine_steps"] + agg["fallback_steps"]) / sec,
+        "ms_phases": {k: agg[k] / len(t_inf) for k in ("ms_forward", "ms_refine", "ms_fallback",
+                                                       "ms_fallback_scan")},
+        "mlp_forward_tflops": MLP_FLOPS_FWD * len(q["zs"]) / (agg["ms_forward"] / len(t_inf) / 1e3)
+                              / 1e12,
+        "error": {"vs": f"FP64 path finder (0.1 mm) on the first {m:,} queries",
+                  "time_s": {"p50": float(np.median(errs)), "p99": float(np.percentile(errs, 99)),
+                             "max": float(errs.max())},
+                  "count_agreement_adjudicated": float((sur_count == adj).mean()),
+                  "count_agreement_vs_coarse_scan": float((sur_count == tc).mean())},
+        "training": {"label_s": t_lab, "train_s": t_train, "adam_steps": n_steps,
+                     "batch": sch["batch"], "epochs": sch["epochs"], "final_loss": loss,
+                     "train_tflops": 3 * MLP_FLOPS_FWD * sch["batch"] * n_steps / t_train / 1e12},
+    }
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -363,6 +460,12 @@ def run_gpu(args):
             "ms_per_step": 1e3 * psec / len(pt),
         }
 
+    # learned surrogate of the path finder: labels from the FP32 path finder, native training,
+    # inference on 1,048,576 queries with refinement and fallback, against the plain path
+    # finder at the same 5 mm receiver tolerance and the FP64 path finder on a sample
+    if not args.no_surrogate:
+        modes["surrogate"] = surrogate_leg(rp, W, args, rank, flush)
+
     # roofline of the dominant kernel (the FP32 tracing launches): FP32 ALU bound
     sm_mhz = clocks["sm_mhz"] or _peaks().get("sm_max_mhz", 2070.0)
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
@@ -409,6 +512,10 @@ def main():
     ap.add_argument("--no-grid", action="store_true")
     ap.add_argument("--no-paths", action="store_true")
     ap.add_argument("--paths-steps", type=int, default=3)
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sur-train", type=int, default=4_194_304)
+    ap.add_argument("--sur-queries", type=int, default=1_048_576)
+    ap.add_argument("--sur-check", type=int, default=16_384)
     ap.add_argument("--grid-steps", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -286,7 +286,7 @@ int rp_surrogate_get_params(rp_surrogate_t s, float *params);
 int rp_surrogate_forward(rp_surrogate_t s, int64_t n, const float *x, float *out, void *stream);
 
 /* Mean loss over n rows and its gradient (flat, like the parameters; device or host pointer,
- * may be NULL) without updating.  y: (n, 2) existence targets in {0, 1}; t: (n, 10) regression
+ * may be NULL) without updating.  y: (n, 2) existence targets in [0, 1]; t: (n, 10) regression
  * targets (slot-major).  Loss per row: for each slot, softplus(logit) - y logit
  * + y * 0.5 * |regression outputs - t|^2. */
 int rp_surrogate_loss_grad(rp_surrogate_t s, int64_t n, const float *x, const float *y,
@@ -296,6 +296,96 @@ int rp_surrogate_loss_grad(rp_surrogate_t s, int64_t n, const float *x, const fl
  * rows; *loss (may be NULL) receives that loss before the update. */
 int rp_surrogate_train_step(rp_surrogate_t s, int64_t n, const float *x, const float *y,
                             const float *t, float lr, double *loss, void *stream);
+
+/* Checkpoint: writes the parameters, the Adam moments and the step count to a host file /
+ * creates a network on the current device from such a file.  Binary little-endian layout:
+ * 8-byte magic "RPSUR001", int64 parameter count, int64 Adam step, then the float32 vectors
+ * params, m, v.  RP_ERR_INVALID_ARG for a missing, short or foreign file. */
+int rp_surrogate_save(rp_surrogate_t s, const char *path);
+int rp_surrogate_load(const char *path, rp_surrogate_t *out);
+
+/* Training schedule for rp_surrogate_train.  The n rows are split into floor(n / batch)
+ * contiguous batches (a trailing partial batch is not used); each epoch visits them in an
+ * order drawn from `seed`, one Adam step per batch, with the learning rate decayed from lr to
+ * lr_final along a half cosine over all steps.  Rows must already be in random order (the
+ * batches are contiguous). */
+typedef struct {
+    int32_t epochs, batch;
+    float lr, lr_final;
+    uint64_t seed;
+} rp_train_params;
+
+/* Runs the whole schedule on the device (device pointers x (n, 3), y (n, 2), t (n, 10)).
+ * *loss (may be NULL): mean of the batch losses of the last epoch, each taken before its
+ * update.  The Adam state carries over between calls. */
+int rp_surrogate_train(rp_surrogate_t s, int64_t n, const float *x, const float *y,
+                       const float *t, const rp_train_params *p, double *loss, void *stream);
+
+/* Normalisation shared by training data and inference.
+ *   x = (2 z_s / RP_SUR_ZS_MAX - 1, 2 z_r / RP_SUR_ZR_MAX - 1, 2 D / RP_SUR_D_MAX - 1);
+ *   slot k holds the k-th earliest solution; y_k = 1 if it exists, 0 if not, and 0.5 for both
+ *   slots of a pair with more than two solutions (the network cannot hold them, so it is
+ *   taught to be unsure there and such pairs go to the path finder);
+ *   t_k = (2 launch / pi - 1, 2 receive / pi - 1, (c T / RP_SUR_N_REF - L) / RP_SUR_LEN_SCALE,
+ *          (path - L) / RP_SUR_LEN_SCALE, amp), L the straight source-receiver distance,
+ *   zero for an empty slot. */
+#define RP_SUR_ZS_MAX 2000.0
+#define RP_SUR_ZR_MAX 200.0
+#define RP_SUR_D_MAX 4000.0
+#define RP_SUR_N_REF 1.78
+#define RP_SUR_LEN_SCALE 100.0
+
+/* Encodes n pairs (device arrays) into network inputs x (n, 3); with y and t non-NULL also the
+ * targets y (n, 2) and t (n, 10) from the path finder's solutions `sol` (max_sol >= 2 slots
+ * per pair). */
+int rp_surrogate_encode(int64_t n, const double *z_s, const double *z_r, const double *dist,
+                        const rp_solutions *sol, int32_t max_sol, float *x, float *y, float *t,
+                        void *stream);
+
+/* Inference with the tracer as judge and fallback.
+ *   conf: a slot whose existence probability sigmoid(logit) is <= 1 - conf is taken to be
+ *     absent (0.5 < conf < 1); every other slot is refined, and exists only if its
+ *     refinement converges.  A pair whose slot 0 is taken to be absent but slot 1 not goes to
+ *     the path finder.
+ *   refine_tol: a refined solution is accepted when its vertical miss |z - z_r| < refine_tol
+ *     [m]; travel time, path, angles, amplitude and type then come from that trace.
+ *   refine_step: the second secant point is launch + refine_step [rad].
+ *   max_step: a secant step (before a sign change brackets the root) longer than this [rad]
+ *     gives up on the slot.
+ *   refine_iters: traces per slot at most. */
+typedef struct {
+    double conf, refine_tol, refine_step, max_step;
+    int32_t refine_iters, pad;
+} rp_surrogate_params;
+
+typedef struct {
+    int64_t queries;       /* pairs */
+    int64_t tasks;         /* slots refined from the network's launch angle */
+    int64_t tasks_failed;  /* of them: did not converge (their pair fell back) */
+    int64_t fail_end;      /*   ... a trace ended before the receiver plane */
+    int64_t fail_iters;    /*   ... refine_iters traces without convergence */
+    int64_t fail_step;     /*   ... a step longer than max_step or leaving (0, pi) */
+    int64_t duplicates;    /* pairs whose two slots converged to the same ray (fell back) */
+    int64_t fallback;      /* pairs solved by the path finder */
+    int64_t refine_rays, refine_steps;      /* traces (and accepted steps) of the refinement */
+    int64_t fallback_rays, fallback_steps;  /* traces (and accepted steps) of the fallback */
+    float ms_forward, ms_refine, ms_fallback, ms_total;  /* device time per phase */
+    float ms_fallback_scan;  /* of ms_fallback: the path finder's angle scan */
+} rp_surrogate_stats;
+
+/* Solves n pairs like rp_find_paths: the network predicts, per pair, which of the two
+ * earliest solutions exist and their launch angles; each solution not ruled out is refined
+ * from its predicted launch angle (secant steps, then Illinois false position once a sign
+ * change brackets the root; one full trace per step) until its miss is below refine_tol.
+ * Pairs with a slot that does not converge, two slots that converge to the same ray, or
+ * D < p->hit_tol are solved by rp_find_paths with `p` instead (up to p->max_sol solutions;
+ * network-served pairs have at most two).  Output as for
+ * rp_find_paths (n_iter = traces of the refinement).  p->max_sol >= 2.  Returns RP_OK,
+ * RP_ERR_INVALID_ARG, RP_ERR_OOM, RP_ERR_CUDA, or RP_ERR_OVERFLOW from the fallback. */
+int rp_surrogate_find_paths(rp_surrogate_t s, rp_medium_t m, int64_t n, const double *z_s,
+                            const double *z_r, const double *dist, const int32_t *n_angles,
+                            const rp_path_params *p, const rp_surrogate_params *sp,
+                            rp_solutions *sol, rp_surrogate_stats *stats, void *stream);
 
 /* ------------------------------------------------------------------------------------
  * Misc

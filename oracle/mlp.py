@@ -5,7 +5,7 @@ The surrogate maps a source-receiver geometry (z_s, z_r, D) to, for up to two so
 receive angle, travel time, path length, amplitude; see ``paper_1810_01780_gb300.surrogate`` for
 the normalisation).  Network: 3 -> 256 -> 256 -> 256 -> 256 -> 12, GELU (erf form) after every
 hidden layer, linear output.  Loss per sample: for each slot k, the logistic loss of the
-existence logit against y_k in {0, 1}, plus y_k times half the squared error of the five
+existence logit against y_k in [0, 1], plus y_k times half the squared error of the five
 regression outputs.  Mean over the batch.
 
 Everything here is plain numpy in float64, layer by layer, with no fusion; weights are taken
@@ -61,7 +61,8 @@ def forward(W, b, X):
 
 
 def loss_and_grad_out(out, y, t):
-    """Loss and dL/d(out).  y: (B, 2) existence in {0,1}; t: (B, 2, 5) regression targets."""
+    """Loss and dL/d(out).  y: (B, 2) existence targets in [0, 1] (1 or 0, or 0.5 where the
+    pair has more solutions than slots); t: (B, 2, 5) regression targets."""
     B = out.shape[0]
     o = out.reshape(B, N_SLOT, 1 + N_REG)
     logit, reg = o[:, :, 0], o[:, :, 1:]

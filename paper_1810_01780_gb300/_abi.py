@@ -100,6 +100,28 @@ class Solutions(C.Structure):
                                           "path", "amp", "miss")]
 
 
+class TrainParams(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float),
+                ("lr_final", C.c_float), ("seed", C.c_uint64)]
+
+
+class SurrogateParams(C.Structure):
+    _fields_ = [("conf", C.c_double), ("refine_tol", C.c_double), ("refine_step", C.c_double),
+                ("max_step", C.c_double), ("refine_iters", C.c_int32), ("pad", C.c_int32)]
+
+
+class SurrogateStats(C.Structure):
+    _fields_ = [(f, C.c_int64) for f in ("queries", "tasks", "tasks_failed", "fail_end",
+                                         "fail_iters", "fail_step", "duplicates", "fallback",
+                                         "refine_rays", "refine_steps", "fallback_rays",
+                                         "fallback_steps")] + \
+               [(f, C.c_float) for f in ("ms_forward", "ms_refine", "ms_fallback", "ms_total",
+                                         "ms_fallback_scan")]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 # every entry point the header declares, with its ctypes signature
 SIGNATURES = {
     "rp_medium_create": (C.c_int, [C.POINTER(MediumDesc), C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -123,6 +145,18 @@ SIGNATURES = {
                                          C.POINTER(C.c_double), C.c_void_p, C.c_void_p]),
     "rp_surrogate_train_step": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_float, C.POINTER(C.c_double),
+                                          C.c_void_p]),
+    "rp_surrogate_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "rp_surrogate_load": (C.c_int, [C.c_char_p, C.POINTER(C.c_void_p)]),
+    "rp_surrogate_train": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.POINTER(TrainParams), C.POINTER(C.c_double), C.c_void_p]),
+    "rp_surrogate_encode": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.POINTER(Solutions), C.c_int32, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p]),
+    "rp_surrogate_find_paths": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.POINTER(PathParams), C.POINTER(SurrogateParams),
+                                          C.POINTER(Solutions), C.POINTER(SurrogateStats),
                                           C.c_void_p]),
     "rp_last_error": (C.c_int, [C.c_char_p, C.c_size_t]),
     "rp_version": (C.c_char_p, []),

@@ -7,6 +7,7 @@ structure-of-arrays.
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 import torch
@@ -338,3 +339,82 @@ class Surrogate:
                                                 C.c_void_p(t.data_ptr()), C.c_float(lr),
                                                 C.byref(L), C.c_void_p(_stream_ptr(stream))))
         return L.value
+
+    def train(self, x, y, t, epochs: int, batch: int, lr: float, lr_final: float = 0.0,
+              seed: int = 0, stream=None) -> float:
+        """rp_surrogate_train: the whole schedule on the device; returns the last epoch's loss."""
+        x, y, t = self._f32(x, 3), self._f32(y, 2), self._f32(t, 10)
+        p = A.TrainParams(int(epochs), int(batch), float(lr), float(lr_final), int(seed))
+        L = C.c_double()
+        A.check(A.lib().rp_surrogate_train(self.handle, x.shape[0], C.c_void_p(x.data_ptr()),
+                                           C.c_void_p(y.data_ptr()), C.c_void_p(t.data_ptr()),
+                                           C.byref(p), C.byref(L),
+                                           C.c_void_p(_stream_ptr(stream))))
+        return L.value
+
+    def save(self, path: str):
+        A.check(A.lib().rp_surrogate_save(self.handle, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str) -> "Surrogate":
+        A.lib()
+        h = C.c_void_p()
+        A.check(A.lib().rp_surrogate_load(os.fsencode(path), C.byref(h)))
+        obj = cls.__new__(cls)
+        obj.handle = h
+        return obj
+
+    def find_paths_into(self, medium: Medium, buf: PathBuffers, prm: A.PathParams,
+                        sprm: A.SurrogateParams, stream=None,
+                        allow_overflow=False) -> A.SurrogateStats:
+        st = A.SurrogateStats()
+        rc = A.lib().rp_surrogate_find_paths(
+            self.handle, medium.handle, buf.n, C.c_void_p(buf.zs.data_ptr()),
+            C.c_void_p(buf.zr.data_ptr()), C.c_void_p(buf.dist.data_ptr()),
+            C.c_void_p(buf.n_angles.data_ptr()), C.byref(prm), C.byref(sprm), C.byref(buf.sol),
+            C.byref(st), C.c_void_p(_stream_ptr(stream)))
+        A.check(rc, allow_overflow=allow_overflow)
+        return st
+
+    def find_paths(self, medium: Medium, zs, zr, dist, n_angles, params: dict,
+                   precision: str = "fp32", hit_tol: float = 0.005, max_iter: int = 60,
+                   max_sol: int = 4, stream=None, **surrogate) -> dict:
+        """rp_surrogate_find_paths; keyword arguments as in make_surrogate_params."""
+        buf = PathBuffers(zs, zr, dist, n_angles, max_sol)
+        prm = make_path_params(params, precision, hit_tol, max_iter, max_sol)
+        st = self.find_paths_into(medium, buf, prm, make_surrogate_params(**surrogate), stream)
+        out = {"count": buf.count}
+        out.update(buf.t)
+        out["stats"] = st.as_dict()
+        return out
+
+
+def make_surrogate_params(conf: float = 0.95, refine_tol: float = 0.005,
+                          refine_step: float = 1e-3, max_step: float = 0.05,
+                          refine_iters: int = 8) -> A.SurrogateParams:
+    return A.SurrogateParams(conf, refine_tol, refine_step, max_step, int(refine_iters), 0)
+
+
+def encode(zs, zr, dist, sol=None, stream=None):
+    """rp_surrogate_encode: network inputs x (n, 3) and, given path-finder solutions
+    (a PathBuffers or the dict of find_paths), targets y (n, 2) and t (n, 10)."""
+    zs, zr, dist = _dev_f64(zs), _dev_f64(zr), _dev_f64(dist)
+    n = zs.numel()
+    x = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    y = t = None
+    sref, max_sol = None, 0
+    if sol is not None:
+        if isinstance(sol, PathBuffers):
+            sref, max_sol = sol.sol, sol.max_sol
+        else:
+            fields = [sol["count"]] + [sol[k] for k, _ in SOL_FIELDS]
+            sref = A.Solutions(*[f.data_ptr() for f in fields])
+            max_sol = sol["launch"].shape[1]
+        y = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+        t = torch.empty((n, 10), dtype=torch.float32, device="cuda")
+    A.check(A.lib().rp_surrogate_encode(
+        n, C.c_void_p(zs.data_ptr()), C.c_void_p(zr.data_ptr()), C.c_void_p(dist.data_ptr()),
+        C.byref(sref) if sref is not None else None, int(max_sol), C.c_void_p(x.data_ptr()),
+        C.c_void_p(y.data_ptr() if y is not None else 0),
+        C.c_void_p(t.data_ptr() if t is not None else 0), C.c_void_p(_stream_ptr(stream))))
+    return x, y, t

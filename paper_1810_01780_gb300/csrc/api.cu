@@ -259,6 +259,27 @@ int rp_find_paths(rp_medium_t m, int64_t n_pairs, const double *z_s, const doubl
     }
 }
 
+int rp_surrogate_encode(int64_t n, const double *z_s, const double *z_r, const double *dist,
+                        const rp_solutions *sol, int32_t max_sol, float *x, float *y, float *t,
+                        void *stream)
+{
+    return run_surrogate_encode(n, z_s, z_r, dist, sol, max_sol, x, y, t, (cudaStream_t)stream);
+}
+
+int rp_surrogate_find_paths(rp_surrogate_t s, rp_medium_t m, int64_t n, const double *z_s,
+                            const double *z_r, const double *dist, const int32_t *n_angles,
+                            const rp_path_params *p, const rp_surrogate_params *sp,
+                            rp_solutions *sol, rp_surrogate_stats *stats, void *stream)
+{
+    try {
+        return run_surrogate_paths(s, m, n, z_s, z_r, dist, n_angles, p, sp, sol, stats,
+                                   (cudaStream_t)stream);
+    } catch (...) {
+        set_error("rp_surrogate_find_paths: internal exception");
+        return RP_ERR_OOM;
+    }
+}
+
 int rp_last_error(char *buf, size_t len)
 {
     const std::string &s = g_last_error;

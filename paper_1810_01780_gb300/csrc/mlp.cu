@@ -9,9 +9,12 @@
 // accumulation with atomics (weight gradients, K = batch).
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "rp_internal.h"
 
@@ -226,17 +229,6 @@ long long n_params() { return layer_w(kLayers); }
 
 }  // namespace
 
-struct rp_surrogate_s {
-    int device;
-    long long step;
-    float *p, *m, *v, *grad;
-    __nv_bfloat16 *pb;
-    // activations for a batch of up to `cap` rows
-    long long cap;
-    float *Z[4], *H[5], *out, *g0, *g1;
-    double *loss;
-};
-
 namespace rph {
 
 static void free_acts(rp_surrogate_s *s)
@@ -256,7 +248,7 @@ static void free_acts(rp_surrogate_s *s)
     s->cap = 0;
 }
 
-static int ensure_acts(rp_surrogate_s *s, long long n)
+int ensure_acts(rp_surrogate_s *s, long long n)
 {
     if (n <= s->cap) return RP_OK;
     RP_CUDA_TRY(cudaDeviceSynchronize());
@@ -282,7 +274,7 @@ static int gemm(const GemmArgs &g, cudaStream_t st)
 }
 
 // forward pass of n rows; keeps pre-activations when `train`
-static int forward(rp_surrogate_s *s, long long n, const float *x, float *out, bool train,
+int forward(rp_surrogate_s *s, long long n, const float *x, float *out, bool train,
                    cudaStream_t st)
 {
     const float *h = x;
@@ -383,6 +375,33 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
     return RP_OK;
 }
 
+// loss[1] += loss[0] / n: the running sum of batch losses of an epoch
+__global__ void k_acc_loss(double *loss, double inv_n) { loss[1] += loss[0] * inv_n; }
+
+// one Adam step at learning rate lr on the gradient in s->grad
+static int adam_step(rp_surrogate_s *s, float lr, cudaStream_t st)
+{
+    s->step += 1;
+    const float c1 = (float)(1.0 / (1.0 - pow(0.9, (double)s->step)));
+    const float c2 = (float)(1.0 / (1.0 - pow(0.999, (double)s->step)));
+    const long long np = n_params();
+    k_adam<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(s->p, s->pb, s->grad, s->m, s->v, np, lr,
+                                                          c1, c2);
+    RP_CUDA_TRY(cudaGetLastError());
+    return RP_OK;
+}
+
+// splitmix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number generators", 2014)
+static uint64_t splitmix64(uint64_t &state)
+{
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static const char kMagic[8] = {'R', 'P', 'S', 'U', 'R', '0', '0', '1'};
+
 }  // namespace rph
 
 using namespace rph;
@@ -408,7 +427,7 @@ int rp_surrogate_create(const float *params, rp_surrogate_t *out)
     if (e == cudaSuccess) e = cudaMalloc(&s->v, sizeof(float) * np);
     if (e == cudaSuccess) e = cudaMalloc(&s->grad, sizeof(float) * np);
     if (e == cudaSuccess) e = cudaMalloc(&s->pb, sizeof(__nv_bfloat16) * np);
-    if (e == cudaSuccess) e = cudaMalloc(&s->loss, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s->loss, 2 * sizeof(double));
     if (e != cudaSuccess) {
         rp_surrogate_destroy(s);
         return cuda_fail(e, "rp_surrogate_create");
@@ -425,6 +444,7 @@ int rp_surrogate_create(const float *params, rp_surrogate_t *out)
 int rp_surrogate_destroy(rp_surrogate_t s)
 {
     if (!s) return RP_OK;
+    free_pipe(s);
     free_acts(s);
     cudaFree(s->p);
     cudaFree(s->m);
@@ -509,14 +529,116 @@ int rp_surrogate_train_step(rp_surrogate_t s, int64_t n, const float *x, const f
     cudaStream_t st = (cudaStream_t)stream;
     int rc = loss_grad(s, n, x, y, t, loss, st);
     if (rc) return rc;
-    s->step += 1;
-    const float c1 = (float)(1.0 / (1.0 - pow(0.9, (double)s->step)));
-    const float c2 = (float)(1.0 / (1.0 - pow(0.999, (double)s->step)));
-    const long long np = n_params();
-    k_adam<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(s->p, s->pb, s->grad, s->m, s->v, np, lr,
-                                                          c1, c2);
-    RP_CUDA_TRY(cudaGetLastError());
+    if ((rc = adam_step(s, lr, st))) return rc;
     if (!loss) RP_CUDA_TRY(cudaStreamSynchronize(st));
+    return RP_OK;
+}
+
+int rp_surrogate_train(rp_surrogate_t s, int64_t n, const float *x, const float *y,
+                       const float *t, const rp_train_params *p, double *loss, void *stream)
+{
+    if (!s || !p || !x || !y || !t || p->epochs < 1 || p->batch < 1 || n < p->batch ||
+        !(p->lr > 0.0f) || !(p->lr_final >= 0.0f)) {
+        set_error("rp_surrogate_train: bad arguments (need epochs >= 1, 1 <= batch <= n, lr > 0)");
+        return RP_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long nb = n / p->batch, B = p->batch;
+    int rc = ensure_acts(s, B);
+    if (rc) return rc;
+    std::vector<long long> order(nb);
+    for (long long b = 0; b < nb; ++b) order[b] = b;
+    uint64_t rng = p->seed;
+    const double total = (double)p->epochs * (double)nb;
+    long long k = 0;
+    for (int e = 0; e < p->epochs; ++e) {
+        for (long long b = nb - 1; b > 0; --b) {  // Fisher-Yates shuffle of the batch order
+            const long long j = (long long)(splitmix64(rng) % (uint64_t)(b + 1));
+            std::swap(order[b], order[j]);
+        }
+        RP_CUDA_TRY(cudaMemsetAsync(s->loss + 1, 0, sizeof(double), st));
+        for (long long b = 0; b < nb; ++b, ++k) {
+            const long long r0 = order[b] * B;
+            const double c = 0.5 * (1.0 + cos(3.14159265358979323846 * (double)k / total));
+            const float lr = (float)(p->lr_final + (p->lr - p->lr_final) * c);
+            if ((rc = loss_grad(s, B, x + 3 * r0, y + 2 * r0, t + 10 * r0, nullptr, st))) return rc;
+            k_acc_loss<<<1, 1, 0, st>>>(s->loss, 1.0 / ((double)B * (double)nb));
+            RP_CUDA_TRY(cudaGetLastError());
+            if ((rc = adam_step(s, lr, st))) return rc;
+        }
+    }
+    double L = 0.0;
+    RP_CUDA_TRY(cudaMemcpyAsync(&L, s->loss + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    RP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (loss) *loss = L;
+    return RP_OK;
+}
+
+int rp_surrogate_save(rp_surrogate_t s, const char *path)
+{
+    if (!s || !path) {
+        set_error("rp_surrogate_save: null argument");
+        return RP_ERR_INVALID_ARG;
+    }
+    const long long np = n_params();
+    std::vector<float> buf((size_t)(3 * np));
+    RP_CUDA_TRY(cudaDeviceSynchronize());
+    RP_CUDA_TRY(cudaMemcpy(buf.data(), s->p, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    RP_CUDA_TRY(cudaMemcpy(buf.data() + np, s->m, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    RP_CUDA_TRY(cudaMemcpy(buf.data() + 2 * np, s->v, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    FILE *f = fopen(path, "wb");
+    if (!f) {
+        set_error("rp_surrogate_save: cannot open %s", path);
+        return RP_ERR_INVALID_ARG;
+    }
+    const int64_t hdr[2] = {(int64_t)np, (int64_t)s->step};
+    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof(int64_t), 2, f) == 2 &&
+              fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) {
+        set_error("rp_surrogate_save: write to %s failed", path);
+        return RP_ERR_INVALID_ARG;
+    }
+    return RP_OK;
+}
+
+int rp_surrogate_load(const char *path, rp_surrogate_t *out)
+{
+    if (!path || !out) {
+        set_error("rp_surrogate_load: null argument");
+        return RP_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) {
+        set_error("rp_surrogate_load: cannot open %s", path);
+        return RP_ERR_INVALID_ARG;
+    }
+    const long long np = n_params();
+    char magic[8];
+    int64_t hdr[2] = {0, 0};
+    std::vector<float> buf((size_t)(3 * np));
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 8) == 0 &&
+              fread(hdr, sizeof(int64_t), 2, f) == 2 && hdr[0] == np && hdr[1] >= 0 &&
+              fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    fclose(f);
+    if (!ok) {
+        set_error("rp_surrogate_load: %s is not a surrogate checkpoint of %lld parameters", path,
+                  np);
+        return RP_ERR_INVALID_ARG;
+    }
+    rp_surrogate_t s = nullptr;
+    int rc = rp_surrogate_create(buf.data(), &s);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpy(s->m, buf.data() + np, sizeof(float) * np, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(s->v, buf.data() + 2 * np, sizeof(float) * np, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        rp_surrogate_destroy(s);
+        return cuda_fail(e, "rp_surrogate_load");
+    }
+    s->step = hdr[1];
+    *out = s;
     return RP_OK;
 }
 

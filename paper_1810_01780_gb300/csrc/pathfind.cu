@@ -45,6 +45,7 @@ struct Bracket {
 
 struct Cand {
     double launch, receive, time, path, amp, miss;
+    double dth;  // refinement only: launch-angle uncertainty tol / |d miss / d launch|
     int32_t type, n_iter;
 };
 
@@ -179,6 +180,7 @@ __device__ __forceinline__ void add_candidate(const Lane<P> &L, long long i, dou
     o.path = P::sget(L.s);
     o.amp = L.A;
     o.miss = miss;
+    o.dth = 0.0;
 }
 
 struct ScanArgs {
@@ -565,7 +567,552 @@ int run_pf(rp_medium_t m, const PairIn &pi, const rp_trace_params *tp, rp_soluti
     return RP_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// Surrogate pipeline: geometry encoding, inference planning, secant refinement with the
+// tracer, and fallback to the path finder
+// ---------------------------------------------------------------------------------------
+
+// network input of a pair: each of z_s, z_r, D mapped linearly from its range onto [-1, 1]
+__device__ __forceinline__ void encode_x(double zs, double zr, double D, float *x)
+{
+    x[0] = (float)(2.0 * zs / RP_SUR_ZS_MAX - 1.0);
+    x[1] = (float)(2.0 * zr / RP_SUR_ZR_MAX - 1.0);
+    x[2] = (float)(2.0 * D / RP_SUR_D_MAX - 1.0);
+}
+
+__global__ void k_encode(long long n, const double *zs, const double *zr, const double *D,
+                         const rp_solutions sol, int max_sol, float *x, float *y, float *t)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        encode_x(zs[i], zr[i], D[i], x + 3 * i);
+        if (!y) continue;
+        const int cnt = sol.count[i];
+        const double L = sqrt(D[i] * D[i] + (zs[i] - zr[i]) * (zs[i] - zr[i]));
+        const double pi_ = 3.14159265358979323846;
+        for (int k = 0; k < 2; ++k) {
+            const long long o = i * max_sol + k;
+            const bool ex = k < cnt;
+            y[2 * i + k] = cnt > 2 ? 0.5f : (ex ? 1.0f : 0.0f);
+            float *tk = t + 10 * i + 5 * k;
+            if (!ex) {
+                for (int j = 0; j < 5; ++j) tk[j] = 0.0f;
+                continue;
+            }
+            tk[0] = (float)(2.0 * sol.launch[o] / pi_ - 1.0);
+            tk[1] = (float)(2.0 * sol.receive[o] / pi_ - 1.0);
+            tk[2] = (float)((kC0 * sol.time[o] / RP_SUR_N_REF - L) / RP_SUR_LEN_SCALE);
+            tk[3] = (float)((sol.path[o] - L) / RP_SUR_LEN_SCALE);
+            tk[4] = (float)sol.amp[o];
+        }
+    }
+}
+
+struct RTask {
+    long long q;
+    int32_t slot, pad;
+    double th0;
+};
+
+struct SurCtrl {
+    unsigned long long n_tasks, claim, n_fallback, failed;
+    unsigned long long fail_end, fail_iters, fail_step, duplicates;
+};
+
+// slot states in `cok`: absent (trusted), refining, refined
+enum { SLOT_ABSENT = 0, SLOT_PENDING = 2, SLOT_OK = 1 };
+
+// Per query: a slot whose existence probability is <= 1 - conf is trusted to be absent; every
+// other slot becomes a refinement task from the network's launch angle.  Vertical pairs, and
+// pairs whose slot 0 is absent but slot 1 is not, go to the path finder.
+__global__ void k_plan(long long n, const float *out, double conf, const PairIn pi, RTask *tasks,
+                       SurCtrl *sc, int *qflag, int *cok)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        bool ex[2];
+        for (int k = 0; k < 2; ++k) {
+            const double p = 1.0 / (1.0 + exp(-(double)out[12 * i + 6 * k]));
+            ex[k] = p > 1.0 - conf;
+        }
+        const int flag = (pi.dist[i] < pi.hit_tol || (ex[1] && !ex[0])) ? 1 : 0;
+        qflag[i] = flag;
+        for (int k = 0; k < 2; ++k) cok[2 * i + k] = (ex[k] && !flag) ? SLOT_PENDING : SLOT_ABSENT;
+        if (flag) continue;
+        for (int k = 0; k < 2; ++k) {
+            if (!ex[k]) continue;
+            const unsigned long long t = atomicAdd(&sc->n_tasks, 1ull);
+            RTask &T = tasks[t];
+            T.q = i;
+            T.slot = k;
+            T.pad = 0;
+            double th = 0.5 * 3.14159265358979323846 * ((double)out[12 * i + 6 * k + 1] + 1.0);
+            T.th0 = fmin(fmax(th, 1e-6), 3.14159265358979323846 - 1e-6);
+        }
+    }
+}
+
+struct RefArgs {
+    PairIn pi;
+    const RTask *tasks;
+    SurCtrl *sc;
+    Cand *cand;
+    int *cok, *qflag;
+    PfCtrl *ctrl;
+    double h0, tol, step0, max_step;
+    int32_t iters, pad;
+};
+
+// Root search on the launch angle from the network's prediction, one full trace per step:
+// secant steps (the second point at launch + step0) until two misses of opposite sign
+// bracket the root, then Illinois false position inside the bracket, until |miss| < tol.
+// A ray that does not reach the receiver plane, a secant step longer than max_step or
+// leaving (0, pi), or `iters` traces without convergence send the query to the path finder.
+template <class P>
+__global__ void __launch_bounds__(128, P::kMinBlocks)
+    k_refine(const MediumLayered med, const StepParams<P> sp, const Sinks sk, const RefArgs a)
+{
+    const long long nt = (long long)a.sc->n_tasks;
+    const double pi_ = 3.14159265358979323846;
+    long long q = 0;
+    int slot = 0, it = 0, side = 0;
+    bool br = false;
+    double th_prev = 0.0, m_prev = 0.0, th_cur = 0.0, ta = 0.0, ma = 0.0, tb = 0.0, mb = 0.0;
+    bool resume = false;
+    auto fail = [&](unsigned long long *why) {
+        atomicExch(&a.qflag[q], 1);
+        atomicAdd(&a.sc->failed, 1ull);
+        atomicAdd(why, 1ull);
+    };
+    auto next = [&](Lane<P> &L) -> bool {
+        if (resume) {
+            resume = false;
+            launch_ray<P>(L, med, sp, a.pi, a.h0, q, th_cur, false, -1);
+            return true;
+        }
+        const long long t = pf_claim(&a.sc->claim);
+        if (t >= nt) return false;
+        const RTask &T = a.tasks[t];
+        q = T.q;
+        slot = T.slot;
+        th_cur = T.th0;
+        it = 0;
+        br = false;
+        side = 0;
+        launch_ray<P>(L, med, sp, a.pi, a.h0, q, th_cur, false, -1);
+        return true;
+    };
+    auto done = [&](Lane<P> &L) {
+        const double m = miss_of<P>(L, a.pi.zr[q]);
+        if (!isfinite(m)) {
+            fail(&a.sc->fail_end);
+            return;
+        }
+        if (fabs(m) < a.tol) {
+            Cand &o = a.cand[2 * q + slot];
+            o.type = L.n_refl > 0 ? RP_SOL_REFLECTED
+                                  : (L.n_turn > 0 ? RP_SOL_REFRACTED : RP_SOL_DIRECT);
+            o.n_iter = it + 1;
+            o.launch = th_cur;
+            o.receive = acos(fmax(-1.0, fmin(1.0, P::get(L.t, 2))));
+            o.time = P::sget(L.T);
+            o.path = P::sget(L.s);
+            o.amp = L.A;
+            o.miss = m;
+            o.dth = it > 0 ? a.tol * fabs((th_cur - th_prev) / (m - m_prev)) : 0.0;
+            a.cok[2 * q + slot] = SLOT_OK;
+            return;
+        }
+        ++it;
+        if (it >= a.iters) {
+            fail(&a.sc->fail_iters);
+            return;
+        }
+        double th_new;
+        if (br) {  // th_cur lies inside the bracket: keep the end of opposite sign
+            if ((m > 0.0) == (ma > 0.0)) {
+                ta = th_cur;
+                ma = m;
+                if (side == -1) mb *= 0.5;
+                side = -1;
+            } else {
+                tb = th_cur;
+                mb = m;
+                if (side == 1) ma *= 0.5;
+                side = 1;
+            }
+            th_new = (ta * mb - tb * ma) / (mb - ma);
+        } else if (it == 1) {
+            th_new = th_cur + a.step0;
+        } else if ((m > 0.0) != (m_prev > 0.0)) {
+            br = true;
+            ta = th_prev;
+            ma = m_prev;
+            tb = th_cur;
+            mb = m;
+            side = 0;
+            th_new = (ta * mb - tb * ma) / (mb - ma);
+        } else {
+            th_new = th_cur - m * (th_cur - th_prev) / (m - m_prev);
+            if (!(fabs(th_new - th_cur) <= a.max_step)) {
+                fail(&a.sc->fail_step);
+                return;
+            }
+        }
+        if (!(th_new > 0.0 && th_new < pi_)) {
+            fail(&a.sc->fail_step);
+            return;
+        }
+        th_prev = th_cur;
+        m_prev = m;
+        th_cur = th_new;
+        resume = true;
+    };
+    drive<P>(med, sp, sk, a.ctrl, next, done);
+}
+
+// Queries served by the network: their refined slots sorted by travel time into the outputs;
+// a failed slot, or two slots refined to the same ray, send the query to the fallback list.
+__global__ void k_collect(long long n, int max_sol, const int *cok, const Cand *cand,
+                          const int *qflag, rp_solutions sol, long long *fb, SurCtrl *sc)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        bool to_fb = qflag[i] != 0;
+        int cnt = 0;
+        int idx[2];
+        if (!to_fb) {
+            for (int k = 0; k < 2; ++k) {
+                if (cok[2 * i + k] == SLOT_PENDING) to_fb = true;
+                if (cok[2 * i + k] == SLOT_OK) idx[cnt++] = k;
+            }
+            // the same ray twice: same type, launch angles within their uncertainties
+            if (!to_fb && cnt == 2 && cand[2 * i].type == cand[2 * i + 1].type &&
+                fabs(cand[2 * i].launch - cand[2 * i + 1].launch) <=
+                    fmax(1e-5, 2.0 * (cand[2 * i].dth + cand[2 * i + 1].dth))) {
+                to_fb = true;
+                atomicAdd(&sc->duplicates, 1ull);
+            }
+        }
+        if (to_fb) {
+            const unsigned long long f = atomicAdd(&sc->n_fallback, 1ull);
+            fb[f] = i;
+            continue;
+        }
+        if (cnt == 2 && cand[2 * i + idx[1]].time < cand[2 * i + idx[0]].time) {
+            const int tmp = idx[0];
+            idx[0] = idx[1];
+            idx[1] = tmp;
+        }
+        const int keep = cnt < max_sol ? cnt : max_sol;
+        sol.count[i] = keep;
+        for (int c = 0; c < max_sol; ++c) {
+            const long long o = i * max_sol + c;
+            const bool has = c < keep;
+            const Cand &X = cand[2 * i + (has ? idx[c] : 0)];
+            if (sol.type) sol.type[o] = has ? X.type : 0;
+            if (sol.n_iter) sol.n_iter[o] = has ? X.n_iter : 0;
+            if (sol.launch) sol.launch[o] = has ? X.launch : 0.0;
+            if (sol.receive) sol.receive[o] = has ? X.receive : 0.0;
+            if (sol.time) sol.time[o] = has ? X.time : 0.0;
+            if (sol.path) sol.path[o] = has ? X.path : 0.0;
+            if (sol.amp) sol.amp[o] = has ? X.amp : 0.0;
+            if (sol.miss) sol.miss[o] = has ? X.miss : 0.0;
+        }
+    }
+}
+
+__global__ void k_gather(const long long *fb, long long nf, const PairIn pi, double *zs, double *zr,
+                         double *D, int32_t *na)
+{
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nf;
+         j += (long long)gridDim.x * blockDim.x) {
+        const long long i = fb[j];
+        zs[j] = pi.zs[i];
+        zr[j] = pi.zr[i];
+        D[j] = pi.dist[i];
+        na[j] = pi.n_angles[i];
+    }
+}
+
+__global__ void k_scatter(const long long *fb, long long nf, int max_sol, const rp_solutions src,
+                          rp_solutions dst)
+{
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nf;
+         j += (long long)gridDim.x * blockDim.x) {
+        const long long i = fb[j];
+        dst.count[i] = src.count[j];
+        for (int c = 0; c < max_sol; ++c) {
+            const long long o = i * max_sol + c, p = j * max_sol + c;
+            if (dst.type) dst.type[o] = src.type[p];
+            if (dst.n_iter) dst.n_iter[o] = src.n_iter[p];
+            if (dst.launch) dst.launch[o] = src.launch[p];
+            if (dst.receive) dst.receive[o] = src.receive[p];
+            if (dst.time) dst.time[o] = src.time[p];
+            if (dst.path) dst.path[o] = src.path[p];
+            if (dst.amp) dst.amp[o] = src.amp[p];
+            if (dst.miss) dst.miss[o] = src.miss[p];
+        }
+    }
+}
+
+// device buffers of the pipeline, grown on demand, owned by the surrogate handle
+struct SurPipe {
+    long long cap = 0;
+    float *x = nullptr, *out = nullptr;
+    RTask *tasks = nullptr;
+    Cand *cand = nullptr;
+    int *cok = nullptr, *qflag = nullptr;
+    long long *fb = nullptr;
+    double *zs = nullptr, *zr = nullptr, *D = nullptr;
+    int32_t *na = nullptr;
+    rp_solutions tmp;
+    int32_t *tmp_i[3] = {nullptr, nullptr, nullptr};
+    double *tmp_d[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    SurCtrl *sc = nullptr;
+    PfCtrl *pc = nullptr;
+    Ctrl *tc = nullptr;
+};
+
+void pipe_free(SurPipe *p)
+{
+    if (!p) return;
+    cudaFree(p->x);
+    cudaFree(p->out);
+    cudaFree(p->tasks);
+    cudaFree(p->cand);
+    cudaFree(p->cok);
+    cudaFree(p->qflag);
+    cudaFree(p->fb);
+    cudaFree(p->zs);
+    cudaFree(p->zr);
+    cudaFree(p->D);
+    cudaFree(p->na);
+    for (int k = 0; k < 3; ++k) cudaFree(p->tmp_i[k]);
+    for (int k = 0; k < 6; ++k) cudaFree(p->tmp_d[k]);
+    cudaFree(p->sc);
+    cudaFree(p->pc);
+    cudaFree(p->tc);
+    delete p;
+}
+
+int pipe_ensure(rp_surrogate_s *s, long long n, int max_sol)
+{
+    SurPipe *p = (SurPipe *)s->pipe;
+    if (p && p->cap >= n) return RP_OK;
+    RP_CUDA_TRY(cudaDeviceSynchronize());
+    pipe_free(p);
+    s->pipe = nullptr;
+    p = new SurPipe();
+    s->pipe = p;
+    const long long c = n + n / 4 + 16;
+    p->cap = c;
+    RP_CUDA_TRY(cudaMalloc(&p->x, sizeof(float) * 3 * c));
+    RP_CUDA_TRY(cudaMalloc(&p->out, sizeof(float) * 12 * c));
+    RP_CUDA_TRY(cudaMalloc(&p->tasks, sizeof(RTask) * 2 * c));
+    RP_CUDA_TRY(cudaMalloc(&p->cand, sizeof(Cand) * 2 * c));
+    RP_CUDA_TRY(cudaMalloc(&p->cok, sizeof(int) * 2 * c));
+    RP_CUDA_TRY(cudaMalloc(&p->qflag, sizeof(int) * c));
+    RP_CUDA_TRY(cudaMalloc(&p->fb, sizeof(long long) * c));
+    RP_CUDA_TRY(cudaMalloc(&p->zs, sizeof(double) * c));
+    RP_CUDA_TRY(cudaMalloc(&p->zr, sizeof(double) * c));
+    RP_CUDA_TRY(cudaMalloc(&p->D, sizeof(double) * c));
+    RP_CUDA_TRY(cudaMalloc(&p->na, sizeof(int32_t) * c));
+    RP_CUDA_TRY(cudaMalloc(&p->tmp_i[0], sizeof(int32_t) * c));
+    RP_CUDA_TRY(cudaMalloc(&p->tmp_i[1], sizeof(int32_t) * c * 8));
+    RP_CUDA_TRY(cudaMalloc(&p->tmp_i[2], sizeof(int32_t) * c * 8));
+    for (int k = 0; k < 6; ++k) RP_CUDA_TRY(cudaMalloc(&p->tmp_d[k], sizeof(double) * c * 8));
+    RP_CUDA_TRY(cudaMalloc(&p->sc, sizeof(SurCtrl)));
+    RP_CUDA_TRY(cudaMalloc(&p->pc, sizeof(PfCtrl)));
+    RP_CUDA_TRY(cudaMalloc(&p->tc, sizeof(Ctrl)));
+    p->tmp.count = p->tmp_i[0];
+    p->tmp.type = p->tmp_i[1];
+    p->tmp.n_iter = p->tmp_i[2];
+    p->tmp.launch = p->tmp_d[0];
+    p->tmp.receive = p->tmp_d[1];
+    p->tmp.time = p->tmp_d[2];
+    p->tmp.path = p->tmp_d[3];
+    p->tmp.amp = p->tmp_d[4];
+    p->tmp.miss = p->tmp_d[5];
+    (void)max_sol;
+    return RP_OK;
+}
+
+template <class P>
+int run_surrogate(rp_surrogate_s *s, rp_medium_t m, const PairIn &pi, const rp_trace_params *tp,
+                  const rp_surrogate_params *sp_in, rp_solutions *sol, rp_surrogate_stats *stats,
+                  cudaStream_t st, int dev)
+{
+    const long long n = pi.n_pairs;
+    int rc = pipe_ensure(s, n, pi.max_sol);
+    if (rc) return rc;
+    if ((rc = ensure_acts(s, n))) return rc;
+    SurPipe *p = (SurPipe *)s->pipe;
+    cudaEvent_t ev[5];
+    for (int k = 0; k < 5; ++k) RP_CUDA_TRY(cudaEventCreate(&ev[k]));
+    const int sms = sm_count(dev);
+    const int gblocks = std::max(1, (int)std::min<long long>((n + 255) / 256, (long long)sms * 8));
+    RP_CUDA_TRY(cudaEventRecord(ev[0], st));
+    RP_CUDA_TRY(cudaMemsetAsync(p->sc, 0, sizeof(SurCtrl), st));
+    RP_CUDA_TRY(cudaMemsetAsync(p->pc, 0, sizeof(PfCtrl), st));
+    RP_CUDA_TRY(cudaMemsetAsync(p->tc, 0, sizeof(Ctrl), st));
+    rp_solutions none;
+    memset(&none, 0, sizeof none);
+    k_encode<<<gblocks, 256, 0, st>>>(n, pi.zs, pi.zr, pi.dist, none, 0, p->x, nullptr, nullptr);
+    RP_CUDA_TRY(cudaGetLastError());
+    if ((rc = forward(s, n, p->x, p->out, false, st))) return rc;
+    RP_CUDA_TRY(cudaEventRecord(ev[1], st));
+    k_plan<<<gblocks, 256, 0, st>>>(n, p->out, sp_in->conf, pi, p->tasks, p->sc, p->qflag, p->cok);
+    RP_CUDA_TRY(cudaGetLastError());
+    StepParams<P> sp = step_params<P>(tp, 0, 1.0f);
+    sp.use_stop = 1;
+    sp.max_generation = 0;
+    Sinks sk;
+    memset(&sk, 0, sizeof sk);
+    sk.ctrl = p->tc;
+    RefArgs ra;
+    ra.pi = pi;
+    ra.tasks = p->tasks;
+    ra.sc = p->sc;
+    ra.cand = p->cand;
+    ra.cok = p->cok;
+    ra.qflag = p->qflag;
+    ra.ctrl = p->pc;
+    ra.h0 = tp->h0;
+    ra.tol = sp_in->refine_tol;
+    ra.step0 = sp_in->refine_step;
+    ra.max_step = sp_in->max_step;
+    ra.iters = sp_in->refine_iters;
+    ra.pad = 0;
+    const int occ = occ_of((const void *)k_refine<P>);
+    if (occ < 0) return occ;
+    k_refine<P><<<sms * occ, 128, 0, st>>>(m->layered, sp, sk, ra);
+    RP_CUDA_TRY(cudaGetLastError());
+    k_collect<<<gblocks, 256, 0, st>>>(n, pi.max_sol, p->cok, p->cand, p->qflag, *sol, p->fb,
+                                       p->sc);
+    RP_CUDA_TRY(cudaGetLastError());
+    RP_CUDA_TRY(cudaEventRecord(ev[2], st));
+    SurCtrl hs;
+    PfCtrl hp;
+    RP_CUDA_TRY(cudaMemcpyAsync(&hs, p->sc, sizeof hs, cudaMemcpyDeviceToHost, st));
+    RP_CUDA_TRY(cudaMemcpyAsync(&hp, p->pc, sizeof hp, cudaMemcpyDeviceToHost, st));
+    RP_CUDA_TRY(cudaStreamSynchronize(st));
+    const long long nf = (long long)hs.n_fallback;
+    rp_stats fs;
+    memset(&fs, 0, sizeof fs);
+    if (nf > 0) {
+        k_gather<<<std::max(1, (int)std::min<long long>((nf + 255) / 256, (long long)sms * 8)), 256,
+                   0, st>>>(p->fb, nf, pi, p->zs, p->zr, p->D, p->na);
+        RP_CUDA_TRY(cudaGetLastError());
+        PairIn sub = pi;
+        sub.zs = p->zs;
+        sub.zr = p->zr;
+        sub.dist = p->D;
+        sub.n_angles = p->na;
+        sub.n_pairs = nf;
+        rc = run_pf<P>(m, sub, tp, &p->tmp, &fs, st, dev);
+        if (rc && rc != RP_ERR_OVERFLOW) return rc;
+        k_scatter<<<std::max(1, (int)std::min<long long>((nf + 255) / 256, (long long)sms * 8)), 256,
+                    0, st>>>(p->fb, nf, pi.max_sol, p->tmp, *sol);
+        RP_CUDA_TRY(cudaGetLastError());
+    }
+    RP_CUDA_TRY(cudaEventRecord(ev[3], st));
+    RP_CUDA_TRY(cudaEventSynchronize(ev[3]));
+    float t_fwd = 0, t_ref = 0, t_all = 0;
+    cudaEventElapsedTime(&t_fwd, ev[0], ev[1]);
+    cudaEventElapsedTime(&t_ref, ev[1], ev[2]);
+    cudaEventElapsedTime(&t_all, ev[0], ev[3]);
+    for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+    if (stats) {
+        stats->queries = n;
+        stats->fallback = nf;
+        stats->tasks = (int64_t)hs.n_tasks;
+        stats->tasks_failed = (int64_t)hs.failed;
+        stats->fail_end = (int64_t)hs.fail_end;
+        stats->fail_iters = (int64_t)hs.fail_iters;
+        stats->fail_step = (int64_t)hs.fail_step;
+        stats->duplicates = (int64_t)hs.duplicates;
+        stats->refine_rays = (int64_t)hp.rays;
+        stats->refine_steps = (int64_t)hp.steps_acc;
+        stats->fallback_rays = fs.rays;
+        stats->fallback_steps = fs.steps_accepted;
+        stats->ms_forward = t_fwd;
+        stats->ms_refine = t_ref;
+        stats->ms_total = t_all;
+        stats->ms_fallback = t_all - t_fwd - t_ref;
+        stats->ms_fallback_scan = fs.wave_ms[0];
+    }
+    return rc;
+}
+
 }  // namespace
+
+void free_pipe(rp_surrogate_s *s)
+{
+    if (s && s->pipe) {
+        pipe_free((SurPipe *)s->pipe);
+        s->pipe = nullptr;
+    }
+}
+
+int run_surrogate_paths(rp_surrogate_s *s, rp_medium_t m, int64_t n, const double *zs,
+                        const double *zr, const double *dist, const int32_t *n_angles,
+                        const rp_path_params *p, const rp_surrogate_params *sp,
+                        rp_solutions *sol, rp_surrogate_stats *stats, cudaStream_t st)
+{
+    if (!s || !m || !p || !sp || !sol || n < 0 || m->kind != RP_MEDIUM_LAYERED) {
+        set_error("rp_surrogate_find_paths: bad arguments (layered medium required)");
+        return RP_ERR_INVALID_ARG;
+    }
+    if (stats) memset(stats, 0, sizeof *stats);
+    if (n == 0) return RP_OK;
+    if (!zs || !zr || !dist || !n_angles || !sol->count || p->max_sol < 2 || p->max_sol > 8 ||
+        !(sp->conf > 0.5 && sp->conf < 1.0) || !(sp->refine_tol > 0.0) || sp->refine_iters < 1 ||
+        !(sp->refine_step > 0.0) || !(sp->max_step > 0.0) || !(p->hit_tol > 0.0)) {
+        set_error("rp_surrogate_find_paths: bad arrays or parameters (max_sol 2..8, 0.5 < conf < 1)");
+        return RP_ERR_INVALID_ARG;
+    }
+    int rc = validate_params(&p->trace, true);
+    if (rc) return rc;
+    int dev;
+    RP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != m->device || dev != s->device) {
+        set_error("rp_surrogate_find_paths: medium (device %d), network (device %d) and current "
+                  "device %d differ", m->device, s->device, dev);
+        return RP_ERR_INVALID_ARG;
+    }
+    PairIn pi;
+    pi.zs = zs;
+    pi.zr = zr;
+    pi.dist = dist;
+    pi.n_angles = n_angles;
+    pi.n_pairs = n;
+    pi.hit_tol = p->hit_tol;
+    pi.max_iter = p->max_iter;
+    pi.max_sol = p->max_sol;
+    if (p->trace.precision == RP_FP64)
+        return run_surrogate<PrecF64>(s, m, pi, &p->trace, sp, sol, stats, st, dev);
+    return run_surrogate<PrecF32>(s, m, pi, &p->trace, sp, sol, stats, st, dev);
+}
+
+int run_surrogate_encode(int64_t n, const double *zs, const double *zr, const double *dist,
+                         const rp_solutions *sol, int max_sol, float *x, float *y, float *t,
+                         cudaStream_t st)
+{
+    if (n < 0 || (n > 0 && (!zs || !zr || !dist || !x)) || (y && (!t || !sol || !sol->count)) ||
+        (y && max_sol < 2)) {
+        set_error("rp_surrogate_encode: bad arguments");
+        return RP_ERR_INVALID_ARG;
+    }
+    if (n == 0) return RP_OK;
+    rp_solutions none;
+    memset(&none, 0, sizeof none);
+    k_encode<<<std::max(1, (int)std::min<long long>((n + 255) / 256, 4096)), 256, 0, st>>>(
+        n, zs, zr, dist, y ? *sol : none, max_sol, x, y, t);
+    RP_CUDA_TRY(cudaGetLastError());
+    RP_CUDA_TRY(cudaStreamSynchronize(st));
+    return RP_OK;
+}
 
 int run_find_paths(rp_medium_t m, int64_t n_pairs, const double *zs, const double *zr,
                    const double *dist, const int32_t *n_angles, const rp_path_params *p,

@@ -10,6 +10,20 @@
 #include "rp.h"
 #include "trace_core.cuh"
 
+#include <cuda_bf16.h>
+
+struct rp_surrogate_s {
+    int device;
+    long long step;
+    float *p, *m, *v, *grad;
+    __nv_bfloat16 *pb;
+    // activations for a batch of up to `cap` rows
+    long long cap;
+    float *Z[4], *H[5], *out, *g0, *g1;
+    double *loss;
+    void *pipe;  // buffers of the surrogate path-finding pipeline (pathfind.cu)
+};
+
 struct rp_medium_s {
     int device;
     int kind;
@@ -121,6 +135,19 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
 int run_find_paths(rp_medium_t m, int64_t n_pairs, const double *zs, const double *zr,
                    const double *dist, const int32_t *n_angles, const rp_path_params *p,
                    rp_solutions *sol, rp_stats *stats, cudaStream_t st);
+
+// Surrogate network (mlp.cu) and its path-finding pipeline buffers (pathfind.cu).
+int ensure_acts(rp_surrogate_s *s, long long n);
+int forward(rp_surrogate_s *s, long long n, const float *x, float *out, bool train,
+            cudaStream_t st);
+void free_pipe(rp_surrogate_s *s);
+int run_surrogate_paths(rp_surrogate_s *s, rp_medium_t m, int64_t n, const double *zs,
+                        const double *zr, const double *dist, const int32_t *n_angles,
+                        const rp_path_params *p, const rp_surrogate_params *sp,
+                        rp_solutions *sol, rp_surrogate_stats *stats, cudaStream_t st);
+int run_surrogate_encode(int64_t n, const double *zs, const double *zr, const double *dist,
+                         const rp_solutions *sol, int max_sol, float *x, float *y, float *t,
+                         cudaStream_t st);
 
 // Grid gradient precompute (medium.cu).
 int build_grid(rp_medium_s *m, const float *n_src, double spacing, cudaStream_t st);

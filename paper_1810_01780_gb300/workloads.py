@@ -198,6 +198,19 @@ def paths(n=65_536, seed=4):
                 pairs=pairs(n, seed), hit_tol=0.1, max_iter=60, max_sol=4)
 
 
+def surrogate(n_train=4_194_304, n_query=1_048_576, seed=5):
+    """Learned surrogate of the path finder: training pairs and queries drawn like ``paths``
+    (independent seeds); training labels from the FP32 path finder at hit_tol 0.1 m; inference
+    refines to a 5 mm miss and falls back to the path finder at the same tolerance."""
+    base = paths(1)
+    return dict(name="surrogate", medium=base["medium"], params=base["params"],
+                train=pairs(n_train, seed), queries=pairs(n_query, seed + 1),
+                label_hit_tol=0.1, hit_tol=0.005, max_iter=60, max_sol=4,
+                schedule=dict(epochs=12, batch=8192, lr=2e-3, lr_final=2e-5, seed=seed),
+                infer=dict(conf=0.99, refine_tol=0.005, refine_step=1e-3, max_step=0.05,
+                           refine_iters=8))
+
+
 # ---------------------------------------------------------------------------------------
 # surrogate network: layer sizes and seeded initial weights (inputs of both sides)
 # ---------------------------------------------------------------------------------------

@@ -32,7 +32,7 @@ def rp():
 def _batch(n, seed):
     rng = np.random.default_rng(seed)
     X = rng.uniform(-1, 1, (n, 3)).astype(np.float32)
-    y = (rng.uniform(size=(n, 2)) > 0.4).astype(np.float32)
+    y = rng.choice(np.array([0.0, 0.5, 1.0], np.float32), size=(n, 2), p=[0.4, 0.1, 0.5])
     t = rng.normal(0, 0.5, (n, 10)).astype(np.float32)
     return X, y, t
 

@@ -16,7 +16,7 @@ def _small(seed=1):
     Ws = [w.astype(np.float64) for w in Ws]
     bs = [rng.normal(0, 0.1, c.shape) for c in bs]
     X = rng.uniform(-1, 1, (5, 3))
-    y = (rng.uniform(size=(5, 2)) > 0.5).astype(np.float64)
+    y = rng.choice([0.0, 0.5, 1.0], size=(5, 2))  # 0.5: the label of an ambiguous pair
     t = rng.normal(0, 1, (5, 2, 5))
     return Ws, bs, X, y, t
 
