@@ -23,7 +23,6 @@ import json
 import math
 import os
 import statistics
-import subprocess
 import sys
 import time
 
@@ -125,52 +124,78 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------------
 
 class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event reasons of this process's GPU, sampled every 5 ms by a thread
+    through NVML (read-only queries) while the timed region runs."""
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.p = None
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index: int):
+        self.cuda_index = cuda_index
+        self.samples, self.max_mhz, self.err, self.how = [], None, None, None
+
+    def _handle(self, nv):
+        import ctypes as C
+        import torch
+
+        h = C.c_void_p()
+        uuid = getattr(torch.cuda.get_device_properties(self.cuda_index), "uuid", None)
+        if uuid is not None:
+            key = ("GPU-" + str(uuid)).encode()
+            if nv.nvmlDeviceGetHandleByUUID(key, C.byref(h)) == 0:
+                self.how = "uuid"
+                return h
+        if nv.nvmlDeviceGetHandleByIndex_v2(self.cuda_index, C.byref(h)) == 0:
+            self.how = "index"
+            return h
+        raise OSError("no NVML handle")
 
     def __enter__(self):
+        import ctypes as C
+        import threading
+
+        self.stop = threading.Event()
+        self.thread = None
         try:
-            self.p = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
-                stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.p = None
+            nv = C.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            h = self._handle(nv)
+            mx = C.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx)) == 0:  # 1: SM clock
+                self.max_mhz = float(mx.value)
+            get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        except (OSError, AttributeError) as e:
+            self.err = str(e)
+            return self
+
+        def run():
+            clk, rs = C.c_uint(), C.c_ulonglong()
+            while not self.stop.is_set():
+                if nv.nvmlDeviceGetClockInfo(h, 1, C.byref(clk)) == 0 and \
+                        get_reasons(h, C.byref(rs)) == 0:
+                    self.samples.append((float(clk.value), int(rs.value)))
+                self.stop.wait(0.005)
+
+        self.thread = threading.Thread(target=run, daemon=True)
+        self.thread.start()
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
-        if self.p is not None:
-            self.p.terminate()
-            try:
-                out, _ = self.p.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.p.kill()
-                out, _ = self.p.communicate()
-            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        self.stop.set()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
 
     def summary(self):
-        sm, mx, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in getattr(self, "lines", []):
-            f = [x.strip() for x in ln.split(",")]
-            try:
-                sm.append(float(f[0]))
-                mx = max(mx, float(f[1]))
-            except (ValueError, IndexError):
-                continue
-            for nm, val in zip(names, f[4:8]):
-                if val.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz,
+                    "reasons": ["unsampled" + (f": {self.err}" if self.err else "")], "samples": 0}
+        reasons = sorted({nm for _, r in self.samples for bit, nm in self.REASONS.items()
+                          if r & bit})
+        return {"sm_mhz": statistics.median(c for c, _ in self.samples),
+                "sm_max_mhz": self.max_mhz, "reasons": reasons, "samples": len(self.samples),
+                "source": f"NVML every 5 ms during the timed region (device by {self.how})"}
 
 
 def _peaks():
@@ -181,6 +206,11 @@ def _peaks():
 
 
 MLP_FLOPS_FWD = 2 * (3 * 256 + 3 * 256 * 256 + 256 * 12)  # per row, multiply-adds x 2
+
+# DRAM bytes (read + write) of the four k_trace_wave<PrecF32, MediumLayered> launches of one
+# step of the 1,048,576-ray batched workload, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the current kernel; to be re-measured whenever the kernel changes
+TRACE_DRAM_BYTES_PER_STEP = 517_744_384
 
 
 def _sync_time(fn):
@@ -302,11 +332,12 @@ def run_gpu(args):
     import paper_1810_01780_gb300 as rp
     from paper_1810_01780_gb300 import workloads as W
 
+    n_rays = args.rays
     seed = 2 + rank  # weak scaling: every rank traces its own batch
-    cfg = W.batched(N_RAYS, seed)
+    cfg = W.batched(n_rays, seed)
     med = rp.Medium(cfg["medium"])
     rays = rp.PreparedRays(*cfg["rays"], receivers=cfg["receivers"])
-    cap = int(5.5 * N_RAYS)
+    cap = int(5.5 * n_rays)
     prm32 = rp.make_params(cfg["params"], "fp32")
     buf = rp.TraceBuffers(cap, 4096)
     stream = torch.cuda.current_stream()
@@ -351,8 +382,8 @@ def run_gpu(args):
     clocks = clk.summary()
 
     # primary end points of the FP32 run for the stated error against FP64
-    end32 = buf.t["end_pos"][:, :N_RAYS].clone()
-    t32 = buf.t["time"][:N_RAYS].clone()
+    end32 = buf.t["end_pos"][:, :n_rays].clone()
+    t32 = buf.t["time"][:n_rays].clone()
 
     # e2e: host (pinned) -> device -> rp_trace -> host, through the same C ABI call
     hp = torch.from_numpy(np.ascontiguousarray(cfg["rays"][0])).pin_memory()
@@ -395,10 +426,10 @@ def run_gpu(args):
             rays64 += st.rays
         modes["fp64"] = {"ray_steps_per_s": acc64 / (sum(t64) / 1e3),
                          "rays_per_s": rays64 / (sum(t64) / 1e3), "ms_per_step": sum(t64) / len(t64)}
-        d = (end32 - buf.t["end_pos"][:, :N_RAYS]).norm(dim=0)
-        dT = (t32 - buf.t["time"][:N_RAYS]).abs()
+        d = (end32 - buf.t["end_pos"][:, :n_rays]).norm(dim=0)
+        dT = (t32 - buf.t["time"][:n_rays]).abs()
         within = ((d <= 1e-3) & (dT <= 1e-11)).double().mean()
-        err = {"vs": "FP64 GPU path, all 1,048,576 primary end points",
+        err = {"vs": f"FP64 GPU path, all {n_rays:,} primary end points",
                "within_1mm_10ps": float(within),
                "pos_m": {"p50": float(d.quantile(0.5)), "p99": float(d.double().quantile(0.99)),
                          "max": float(d.max())},
@@ -472,7 +503,9 @@ def run_gpu(args):
     kern_ms = sum(kern)
     achieved = FLOPS_PER_ATTEMPT_F32 * att / (kern_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "traffic": None,
+            "frac": achieved / peak_tflops,
+            "traffic": TRACE_DRAM_BYTES_PER_STEP if n_rays == N_RAYS else None,
+            "traffic_unit": "bytes per step (all launches of the step)",
             "kernel": "k_trace_wave<PrecF32, MediumLayered>",
             "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x median SM clock "
                           f"under load ({sm_mhz:.0f} MHz)",
@@ -485,7 +518,7 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (f64 accumulators)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rays": N_RAYS, "precision": "fp32_mixed",
+            "config": {"workload": WORKLOAD, "rays": n_rays, "precision": "fp32_mixed",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "flushed (512 MB write) before every step",
                        "rays_traced_per_step": nrays / len(times)},
@@ -512,6 +545,8 @@ def main():
     ap.add_argument("--no-grid", action="store_true")
     ap.add_argument("--no-paths", action="store_true")
     ap.add_argument("--paths-steps", type=int, default=3)
+    ap.add_argument("--rays", type=int, default=N_RAYS,
+                    help="primaries of the batched workload (the bench workload is 1,048,576)")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sur-train", type=int, default=4_194_304)
     ap.add_argument("--sur-queries", type=int, default=1_048_576)
