@@ -270,7 +270,7 @@ int rp_find_paths(rp_medium_t m, int64_t n_pairs, const double *z_s, const doubl
  * existence logit, then five regression outputs (see rp_surrogate_encode). */
 typedef struct rp_surrogate_s *rp_surrogate_t;
 
-/* Number of parameters (201,740). */
+/* Number of parameters (201,484). */
 int rp_surrogate_n_params(void);
 
 /* Creates a network on the current device from `params` (host or device, copied); Adam

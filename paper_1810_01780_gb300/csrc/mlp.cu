@@ -225,6 +225,42 @@ long long layer_w(int l)
     return o;
 }
 long long layer_b(int l) { return layer_w(l) + (long long)kDims[l] * kDims[l + 1]; }
+
+struct LayerOffs {
+    long long w[kLayers], b[kLayers];  // offsets of W_l and b_l in the flat parameter vector
+};
+
+// Inference operands of the fused kernel (layout: kPackW, kPackF and PF_* in rp_internal.h):
+// the hidden layers' weights W1..W3 as BF16 B operands (B[n][k] = W[k][n]) in the tensor
+// cores' no-swizzle K-major shared-memory image (8 x 8 core matrices of 128 contiguous bytes;
+// core (k/8, n/8) at ((k/8) * 32 + n/8) * 128), then the FP32 block.
+using rph::kPackF;
+using rph::kPackW;
+__global__ void k_pack(const float *__restrict__ p, unsigned char *__restrict__ pack, const LayerOffs L)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < 3 * 65536) {
+        const int l = (int)(i / 65536), e = (int)(i % 65536), k = e / 256, n = e % 256;
+        const float w = p[L.w[l + 1] + (long long)k * 256 + n];
+        const long long off = l * kPackW + ((k >> 3) * 32 + (n >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2;
+        *(__nv_bfloat16 *)(pack + off) = __float2bfloat16_rn(w);
+        return;
+    }
+    const long long j = i - 3 * 65536;
+    if (j >= kPackF) return;
+    float v = 0.0f;
+    if (j < rph::PF_B0)
+        v = __bfloat162float(__float2bfloat16_rn(p[L.w[0] + (j - rph::PF_W0)]));
+    else if (j < rph::PF_B1)
+        v = p[L.b[0] + (j - rph::PF_B0)];
+    else if (j < rph::PF_W4)
+        v = p[L.b[1 + (int)((j - rph::PF_B1) / 256)] + (j - rph::PF_B1) % 256];
+    else if (j < rph::PF_B4)
+        v = __bfloat162float(__float2bfloat16_rn(p[L.w[4] + (j - rph::PF_W4)]));
+    else if (j < rph::PF_B4 + 12)
+        v = p[L.b[4] + (j - rph::PF_B4)];
+    ((float *)(pack + 3 * kPackW))[j] = v;
+}
 long long n_params() { return layer_w(kLayers); }
 
 }  // namespace
@@ -378,10 +414,30 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
 // loss[1] += loss[0] / n: the running sum of batch losses of an epoch
 __global__ void k_acc_loss(double *loss, double inv_n) { loss[1] += loss[0] * inv_n; }
 
+int ensure_pack(rp_surrogate_s *s, cudaStream_t st)
+{
+    if (!s->pack) {
+        RP_CUDA_TRY(cudaMalloc(&s->pack, 3 * kPackW + sizeof(float) * kPackF));
+        s->pack_version = -1;
+    }
+    if (s->pack_version == s->version) return RP_OK;
+    const long long total = 3 * 65536 + kPackF;
+    LayerOffs L;
+    for (int l = 0; l < kLayers; ++l) {
+        L.w[l] = layer_w(l);
+        L.b[l] = layer_b(l);
+    }
+    k_pack<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(s->p, s->pack, L);
+    RP_CUDA_TRY(cudaGetLastError());
+    s->pack_version = s->version;
+    return RP_OK;
+}
+
 // one Adam step at learning rate lr on the gradient in s->grad
 static int adam_step(rp_surrogate_s *s, float lr, cudaStream_t st)
 {
     s->step += 1;
+    s->version += 1;
     const float c1 = (float)(1.0 / (1.0 - pow(0.9, (double)s->step)));
     const float c2 = (float)(1.0 / (1.0 - pow(0.999, (double)s->step)));
     const long long np = n_params();
@@ -428,6 +484,7 @@ int rp_surrogate_create(const float *params, rp_surrogate_t *out)
     if (e == cudaSuccess) e = cudaMalloc(&s->grad, sizeof(float) * np);
     if (e == cudaSuccess) e = cudaMalloc(&s->pb, sizeof(__nv_bfloat16) * np);
     if (e == cudaSuccess) e = cudaMalloc(&s->loss, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s->fflag, sizeof(int));
     if (e != cudaSuccess) {
         rp_surrogate_destroy(s);
         return cuda_fail(e, "rp_surrogate_create");
@@ -452,6 +509,8 @@ int rp_surrogate_destroy(rp_surrogate_t s)
     cudaFree(s->grad);
     cudaFree(s->pb);
     cudaFree(s->loss);
+    cudaFree(s->pack);
+    cudaFree(s->fflag);
     delete s;
     return RP_OK;
 }
@@ -470,6 +529,7 @@ int rp_surrogate_set_params(rp_surrogate_t s, const float *params)
     RP_CUDA_TRY(cudaGetLastError());
     RP_CUDA_TRY(cudaDeviceSynchronize());
     s->step = 0;
+    s->version += 1;
     return RP_OK;
 }
 
@@ -491,12 +551,10 @@ int rp_surrogate_forward(rp_surrogate_t s, int64_t n, const float *x, float *out
         return RP_ERR_INVALID_ARG;
     }
     if (n == 0) return RP_OK;
-    int rc = ensure_acts(s, n);
-    if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    if ((rc = forward(s, n, x, out, false, st))) return rc;
-    RP_CUDA_TRY(cudaStreamSynchronize(st));
-    return RP_OK;
+    int rc = forward_fused(s, n, x, out, st);
+    if (rc) return rc;
+    return fused_status(s, st);
 }
 
 int rp_surrogate_loss_grad(rp_surrogate_t s, int64_t n, const float *x, const float *y,

@@ -1,0 +1,331 @@
+// mlp_fused.cu -- surrogate inference in one persistent kernel on the 5th-generation tensor
+// cores.
+//
+// Per tile of 128 rows a CTA of 256 threads computes all five layers without the activations
+// leaving the SM:
+//   layer 0 (3 -> 256) on the CUDA cores, written as BF16 into the A operand tile (64 KB);
+//   layers 1..3 (256 -> 256): the layer's packed BF16 weights (128 KB) arrive in shared memory
+//     by bulk copy (cp.async.bulk, completion on an mbarrier); one thread issues 16
+//     tcgen05.mma (M = 128, N = 256, K = 16 each, FP32 accumulators in tensor memory) and
+//     commits them to a second mbarrier; the eight warps read the accumulators back
+//     (tcgen05.ld, warp w reads lanes 32 (w % 4) .. + 31 and columns 128 (w / 4) .. + 127),
+//     add the bias, apply GELU and write the BF16 result into the A tile for the next layer;
+//   layer 4 (256 -> 12) on the CUDA cores from the last layer's BF16-rounded activations.
+// Operand images use the no-swizzle K-major layout of the tensor cores: 8 x 8 core matrices of
+// 128 contiguous bytes; for A (128 rows x 256 k) core (k/8, row/8) sits at
+// ((k/8) * 16 + row/8) * 128 (K-direction stride 2048 B, 8-row stride 128 B); for B (256 n x 256
+// k) core (k/8, n/8) at ((k/8) * 32 + n/8) * 128 (4096 B, 128 B).  Arithmetic is that of the
+// unfused path: BF16 operands, FP32 products and sums, FP32 bias and GELU.
+// Every wait on an mbarrier is bounded (about two seconds); a CTA that gives up sets the error
+// flag, waits (bounded) for its work in flight, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "rp_internal.h"
+
+namespace rph {
+
+namespace {
+
+constexpr int kTile = 128;
+constexpr uint32_t kWBytes = (uint32_t)kPackW;
+// shared memory map (bytes)
+constexpr uint32_t SM_A = 0;
+constexpr uint32_t SM_B = 65536;
+constexpr uint32_t SM_F = SM_B + kWBytes;
+constexpr uint32_t SM_P = SM_F + kPackF * 4;
+constexpr uint32_t SM_BAR = SM_P + kTile * 12 * 4;
+constexpr uint32_t SM_TOTAL = SM_BAR + 32;
+static_assert(SM_TOTAL <= 227 * 1024, "shared memory map exceeds a CTA's limit");
+static_assert(SM_F % 16 == 0 && SM_P % 16 == 0 && SM_BAR % 8 == 0, "alignment");
+
+// instruction descriptor: D FP32, A and B BF16, both K-major, N = 256, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) |
+                            ((128u >> 4) << 24);
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at the maximum SM clock
+
+__device__ __forceinline__ uint32_t su32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor, no swizzle: start, K-direction core stride (lbo), 8-row
+// core stride (sbo), descriptor version 1
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred P;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, P;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+// byte offset of the 8 consecutive k (k0 % 8 == 0) of row `row` in the A tile
+__device__ __forceinline__ uint32_t a_off(int row, int k0)
+{
+    return (uint32_t)(((k0 >> 3) * 16 + (row >> 3)) * 128 + (row & 7) * 16);
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_mlp_fused(const unsigned char *__restrict__ pack, const float *__restrict__ x,
+                float *__restrict__ out, long long n, int *flag)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *sA = sm + SM_A;
+    float *sF = reinterpret_cast<float *>(sm + SM_F);
+    float *sP = reinterpret_cast<float *>(sm + SM_P);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + SM_BAR);  // [0] weights in, [1] MMAs done
+    uint32_t *slot = reinterpret_cast<uint32_t *>(sm + SM_BAR + 16);
+    volatile int *abort_cta = reinterpret_cast<volatile int *>(sm + SM_BAR + 20);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t bar_ld = su32(&bar[0]), bar_mma = su32(&bar[1]);
+    const uint32_t a_base = su32(sm + SM_A), b_base = su32(sm + SM_B);
+
+    const float4 *gF = reinterpret_cast<const float4 *>(pack + 3 * kPackW);
+    for (int i = tid; i < kPackF / 4; i += 256) reinterpret_cast<float4 *>(sF)[i] = gF[i];
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_ld) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_mma) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_cta = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)),
+                     "r"(256u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *slot;
+
+    uint32_t ph_ld = 0, ph_mma = 0;
+    bool ld_pending = false, mma_pending = false;  // thread 0: async work not yet waited for
+    const long long n_tiles = (n + kTile - 1) / kTile;
+    const int row0 = tid & 127, half = tid >> 7;  // layer 0: row and column half
+    const int q = warp & 3, ch = warp >> 2;       // epilogue: lane quarter and column half
+    const int erow = q * 32 + lane;
+    bool failed = false;
+
+    for (long long tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+        const long long g0 = tile * kTile;
+        {  // layer 0 on the CUDA cores
+            const long long gr = g0 + row0;
+            float x0 = 0.0f, x1 = 0.0f, x2 = 0.0f;
+            if (gr < n) {
+                x0 = bf16r(x[3 * gr]);
+                x1 = bf16r(x[3 * gr + 1]);
+                x2 = bf16r(x[3 * gr + 2]);
+            }
+#pragma unroll 2
+            for (int c = 0; c < 16; ++c) {
+                const int k0 = half * 128 + c * 8;
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float h[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int j = k0 + 2 * e + u;
+                        float z = x0 * sF[PF_W0 + j];
+                        z = fmaf(x1, sF[PF_W0 + 256 + j], z);
+                        z = fmaf(x2, sF[PF_W0 + 512 + j], z);
+                        h[u] = gelu(z + sF[PF_B0 + j]);
+                    }
+                    w[e] = pack2(h[0], h[1]);
+                }
+                *reinterpret_cast<uint4 *>(sA + a_off(row0, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        float acc[12];
+#pragma unroll
+        for (int o = 0; o < 12; ++o) acc[o] = 0.0f;
+
+        for (int l = 0; l < 3; ++l) {
+            if (tid == 0) {  // this layer's weights into sB (every earlier MMA has completed)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_ld),
+                             "r"(kWBytes)
+                             : "memory");
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], "
+                        "%2, [%3];" ::"r"(b_base + c * 32768u),
+                        "l"(pack + l * kPackW + c * 32768), "r"(32768u), "r"(bar_ld)
+                        : "memory");
+                ld_pending = true;
+            }
+            // the A tile written by this CTA's threads becomes visible to the tensor cores
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            fence_before();
+            __syncthreads();
+            fence_after();
+            if (tid == 0) {
+                if (mbar_wait(bar_ld, ph_ld)) {
+                    ld_pending = false;
+#pragma unroll
+                    for (int s = 0; s < 16; ++s) {
+                        const uint64_t ad = sdesc(a_base + s * 4096u, 2048u, 128u);
+                        const uint64_t bd = sdesc(b_base + s * 8192u, 4096u, 128u);
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                            "l"(ad), "l"(bd), "r"(kIdesc), "r"(s)
+                            : "memory");
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            bar_mma)
+                        : "memory");
+                    mma_pending = true;
+                } else {
+                    *abort_cta = 1;
+                }
+            }
+            ph_ld ^= 1u;
+            if (!mbar_wait(bar_mma, ph_mma)) *abort_cta = 1;
+            ph_mma ^= 1u;
+            fence_after();
+            __syncthreads();
+            if (*abort_cta) {
+                failed = true;
+                break;
+            }
+            if (tid == 0) mma_pending = false;
+
+            const float *bias = sF + PF_B1 + l * 256;
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                const int col0 = ch * 128 + c * 32;
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, v);
+                if (l < 2) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int j = e * 8 + 2 * u;
+                            w[u] = pack2(gelu(__uint_as_float(v[j]) + bias[col0 + j]),
+                                         gelu(__uint_as_float(v[j + 1]) + bias[col0 + j + 1]));
+                        }
+                        *reinterpret_cast<uint4 *>(sA + a_off(erow, col0 + e * 8)) =
+                            make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float h = bf16r(gelu(__uint_as_float(v[j]) + bias[col0 + j]));
+                        const float *w4 = sF + PF_W4 + (col0 + j) * 12;
+#pragma unroll
+                        for (int o = 0; o < 12; ++o) acc[o] = fmaf(h, w4[o], acc[o]);
+                    }
+                }
+            }
+            fence_before();  // the next __syncthreads orders these reads before the next MMA
+        }
+        if (failed) break;
+        // layer 4: the two column halves of each row are summed through shared memory
+        if (ch == 1) {
+#pragma unroll
+            for (int o = 0; o < 12; ++o) sP[erow * 12 + o] = acc[o];
+        }
+        __syncthreads();
+        if (ch == 0) {
+            const long long gr = g0 + erow;
+            if (gr < n) {
+#pragma unroll
+                for (int o = 0; o < 12; ++o) out[gr * 12 + o] = acc[o] + sP[erow * 12 + o] + sF[PF_B4 + o];
+            }
+        }
+        __syncthreads();
+    }
+
+    if (failed && tid == 0) {
+        atomicExch(flag, 1);
+        // let work already issued finish before the memory it targets goes away
+        if (ld_pending) mbar_wait(bar_ld, ph_ld ^ 1u);
+        if (mma_pending) mbar_wait(bar_mma, ph_mma ^ 1u);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+int forward_fused(rp_surrogate_s *s, long long n, const float *x, float *out, cudaStream_t st)
+{
+    if (n <= 0) return RP_OK;
+    int rc = ensure_pack(s, st);
+    if (rc) return rc;
+    int dev;
+    RP_CUDA_TRY(cudaGetDevice(&dev));
+    RP_CUDA_TRY(cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SM_TOTAL));
+    RP_CUDA_TRY(cudaMemsetAsync(s->fflag, 0, sizeof(int), st));
+    const long long tiles = (n + kTile - 1) / kTile;
+    const int grid = (int)std::min<long long>(tiles, (long long)sm_count(dev));
+    k_mlp_fused<<<grid, 256, SM_TOTAL, st>>>(s->pack, x, out, n, s->fflag);
+    RP_CUDA_TRY(cudaGetLastError());
+    return RP_OK;
+}
+
+int fused_status(rp_surrogate_s *s, cudaStream_t st)
+{
+    int f = 0;
+    RP_CUDA_TRY(cudaMemcpyAsync(&f, s->fflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (f) {
+        set_error("surrogate inference: a wait of the fused kernel gave up (tensor-core work did "
+                  "not complete)");
+        return RP_ERR_CUDA;
+    }
+    return RP_OK;
+}
+
+}  // namespace rph

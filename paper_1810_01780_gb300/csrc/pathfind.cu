@@ -946,7 +946,6 @@ int run_surrogate(rp_surrogate_s *s, rp_medium_t m, const PairIn &pi, const rp_t
     const long long n = pi.n_pairs;
     int rc = pipe_ensure(s, n, pi.max_sol);
     if (rc) return rc;
-    if ((rc = ensure_acts(s, n))) return rc;
     SurPipe *p = (SurPipe *)s->pipe;
     cudaEvent_t ev[5];
     for (int k = 0; k < 5; ++k) RP_CUDA_TRY(cudaEventCreate(&ev[k]));
@@ -960,7 +959,7 @@ int run_surrogate(rp_surrogate_s *s, rp_medium_t m, const PairIn &pi, const rp_t
     memset(&none, 0, sizeof none);
     k_encode<<<gblocks, 256, 0, st>>>(n, pi.zs, pi.zr, pi.dist, none, 0, p->x, nullptr, nullptr);
     RP_CUDA_TRY(cudaGetLastError());
-    if ((rc = forward(s, n, p->x, p->out, false, st))) return rc;
+    if ((rc = forward_fused(s, n, p->x, p->out, st))) return rc;
     RP_CUDA_TRY(cudaEventRecord(ev[1], st));
     k_plan<<<gblocks, 256, 0, st>>>(n, p->out, sp_in->conf, pi, p->tasks, p->sc, p->qflag, p->cok);
     RP_CUDA_TRY(cudaGetLastError());
@@ -996,7 +995,7 @@ int run_surrogate(rp_surrogate_s *s, rp_medium_t m, const PairIn &pi, const rp_t
     PfCtrl hp;
     RP_CUDA_TRY(cudaMemcpyAsync(&hs, p->sc, sizeof hs, cudaMemcpyDeviceToHost, st));
     RP_CUDA_TRY(cudaMemcpyAsync(&hp, p->pc, sizeof hp, cudaMemcpyDeviceToHost, st));
-    RP_CUDA_TRY(cudaStreamSynchronize(st));
+    if ((rc = fused_status(s, st))) return rc;  // synchronises the stream
     const long long nf = (long long)hs.n_fallback;
     rp_stats fs;
     memset(&fs, 0, sizeof fs);

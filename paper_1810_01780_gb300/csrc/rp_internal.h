@@ -22,6 +22,10 @@ struct rp_surrogate_s {
     float *Z[4], *H[5], *out, *g0, *g1;
     double *loss;
     void *pipe;  // buffers of the surrogate path-finding pipeline (pathfind.cu)
+    // inference operands for the fused kernel (mlp_fused.cu), rebuilt when the weights change
+    unsigned char *pack;
+    long long version, pack_version;
+    int *fflag;  // set by the fused kernel when a bounded wait gave up
 };
 
 struct rp_medium_s {
@@ -136,11 +140,22 @@ int run_find_paths(rp_medium_t m, int64_t n_pairs, const double *zs, const doubl
                    const double *dist, const int32_t *n_angles, const rp_path_params *p,
                    rp_solutions *sol, rp_stats *stats, cudaStream_t st);
 
+// Operands of the fused inference kernel (built by mlp.cu, read by mlp_fused.cu): the hidden
+// layers' weights W1..W3 as three BF16 images of kPackW bytes, then kPackF floats: W0 (3 x 256,
+// BF16-rounded) at PF_W0, b0 at PF_B0, b1..b3 from PF_B1 (256 each), W4 (256 x 12,
+// BF16-rounded) at PF_W4, b4 at PF_B4 (12, padded to 16).
+constexpr long long kPackW = 256LL * 256 * 2;
+constexpr int kPackF = 768 + 4 * 256 + 3072 + 16;
+enum { PF_W0 = 0, PF_B0 = 768, PF_B1 = 1024, PF_W4 = 1792, PF_B4 = 4864 };
+
 // Surrogate network (mlp.cu) and its path-finding pipeline buffers (pathfind.cu).
 int ensure_acts(rp_surrogate_s *s, long long n);
 int forward(rp_surrogate_s *s, long long n, const float *x, float *out, bool train,
             cudaStream_t st);
 void free_pipe(rp_surrogate_s *s);
+int ensure_pack(rp_surrogate_s *s, cudaStream_t st);
+int forward_fused(rp_surrogate_s *s, long long n, const float *x, float *out, cudaStream_t st);
+int fused_status(rp_surrogate_s *s, cudaStream_t st);  // syncs st; RP_ERR_CUDA if flagged
 int run_surrogate_paths(rp_surrogate_s *s, rp_medium_t m, int64_t n, const double *zs,
                         const double *zr, const double *dist, const int32_t *n_angles,
                         const rp_path_params *p, const rp_surrogate_params *sp,

@@ -94,3 +94,45 @@ def test_adam_step_matches_oracle_and_training_learns(rp):
     xd, yd, td = (torch.as_tensor(a, device="cuda") for a in (Xs, ys, ts))
     losses = [net.train_step(xd, yd, td, 1e-3) for _ in range(300)]
     assert losses[-1] < 0.2 * losses[0], (losses[0], losses[-1])
+
+
+def _oracle_forward_bf16_acts(Wo, bo, X):
+    """The oracle's layers with every layer input rounded to BF16, as the tensor cores take it."""
+    h = mlp.bf16_round(X.astype(np.float32))
+    for l in range(len(Wo)):
+        z = h @ Wo[l] + bo[l]
+        if l == len(Wo) - 1:
+            return z
+        h = mlp.bf16_round(mlp.gelu(z).astype(np.float32))
+
+
+@pytest.mark.parametrize("n", [1, 127, 129, 1000, 300_000])
+def test_fused_inference_matches_oracle_with_bf16_activations(rp, n):
+    """rp_surrogate_forward runs the fused tcgen05 kernel: one tile of 128 rows per CTA pass,
+    ragged last tile; against the oracle's layers with BF16-rounded layer inputs."""
+    net = rp.Surrogate(seed=11)
+    X, _, _ = _batch(n, 12)
+    got = net.forward(X).cpu().numpy()
+    assert got.shape == (n, 12) and np.isfinite(got).all()
+    Wo, bo = _oracle_params(net.get_params())
+    rows = np.arange(n) if n <= 1000 else np.random.default_rng(0).choice(n, 2000, replace=False)
+    ref = _oracle_forward_bf16_acts(Wo, bo, X[rows].astype(np.float64))
+    scale = np.abs(ref).max()
+    # FP32 accumulation in a different order may flip a BF16 rounding of an activation
+    assert np.max(np.abs(got[rows] - ref)) <= 2e-2 * scale
+    assert np.median(np.abs(got[rows] - ref)) <= 1e-3 * scale
+
+
+def test_fused_inference_agrees_with_training_forward(rp):
+    """The loss of the fused kernel's outputs (computed by the oracle's loss) equals the loss
+    that the training path's own forward pass (mma.sync GEMMs) reports."""
+    import torch
+
+    net = rp.Surrogate(seed=13)
+    X, y, t = _batch(4096, 14)
+    net.train(torch.as_tensor(X, device="cuda"), torch.as_tensor(y, device="cuda"),
+              torch.as_tensor(t, device="cuda"), epochs=2, batch=1024, lr=1e-3, seed=1)
+    out = net.forward(X).cpu().numpy().astype(np.float64)
+    L_fused, _ = mlp.loss_and_grad_out(out, y.astype(np.float64), t.astype(np.float64).reshape(-1, 2, 5))
+    L_train, _ = net.loss_grad(X, y, t)
+    assert abs(L_fused - L_train) <= 2e-3 * abs(L_train), (L_fused, L_train)
