@@ -1,14 +1,15 @@
 // mlp_fused.cu -- surrogate inference in one persistent kernel on the 5th-generation tensor
 // cores.
 //
-// Per tile of 128 rows a CTA of 256 threads computes all five layers without the activations
+// Per tile of 128 rows a CTA of 512 threads computes all five layers without the activations
 // leaving the SM:
 //   layer 0 (3 -> 256) on the CUDA cores, written as BF16 into the A operand tile (64 KB);
 //   layers 1..3 (256 -> 256): the layer's packed BF16 weights (128 KB) arrive in shared memory
-//     by bulk copy (cp.async.bulk, completion on an mbarrier); one thread issues 16
-//     tcgen05.mma (M = 128, N = 256, K = 16 each, FP32 accumulators in tensor memory) and
-//     commits them to a second mbarrier; the eight warps read the accumulators back
-//     (tcgen05.ld, warp w reads lanes 32 (w % 4) .. + 31 and columns 128 (w / 4) .. + 127),
+//     by bulk copy (cp.async.bulk, completion on an mbarrier), issued as soon as the previous
+//     layer's MMAs have released the B tile so that the copy overlaps the epilogue; one thread
+//     issues 16 tcgen05.mma (M = 128, N = 256, K = 16 each, FP32 accumulators in tensor memory)
+//     and commits them to a second mbarrier; the sixteen warps read the accumulators back
+//     (tcgen05.ld, warp w reads lanes 32 (w % 4) .. + 31 and columns 64 (w / 4) .. + 63),
 //     add the bias, apply GELU and write the BF16 result into the A tile for the next layer;
 //   layer 4 (256 -> 12) on the CUDA cores from the last layer's BF16-rounded activations.
 // Operand images use the no-swizzle K-major layout of the tensor cores: 8 x 8 core matrices of
@@ -29,16 +30,19 @@ namespace rph {
 namespace {
 
 constexpr int kTile = 128;
+constexpr int kThreads = 512;             // 16 warps: 4 column groups per TMEM lane quarter
+constexpr int kGroups = kThreads / 128;   // column groups of a row
+constexpr int kGroupCols = 256 / kGroups;
 constexpr uint32_t kWBytes = (uint32_t)kPackW;
 // shared memory map (bytes)
 constexpr uint32_t SM_A = 0;
 constexpr uint32_t SM_B = 65536;
 constexpr uint32_t SM_F = SM_B + kWBytes;
-constexpr uint32_t SM_P = SM_F + kPackF * 4;
-constexpr uint32_t SM_BAR = SM_P + kTile * 12 * 4;
+constexpr uint32_t SM_BAR = SM_F + kPackF * 4;
 constexpr uint32_t SM_TOTAL = SM_BAR + 32;
 static_assert(SM_TOTAL <= 227 * 1024, "shared memory map exceeds a CTA's limit");
-static_assert(SM_F % 16 == 0 && SM_P % 16 == 0 && SM_BAR % 8 == 0, "alignment");
+static_assert(SM_F % 16 == 0 && SM_BAR % 8 == 0, "alignment");
+static_assert((kGroups - 1) * kTile * 12 * 4 <= 65536, "layer-4 partial sums reuse the A tile");
 
 // instruction descriptor: D FP32, A and B BF16, both K-major, N = 256, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) |
@@ -91,6 +95,20 @@ __device__ __forceinline__ uint32_t a_off(int row, int k0)
     return (uint32_t)(((k0 >> 3) * 16 + (row >> 3)) * 128 + (row & 7) * 16);
 }
 
+// one hidden layer's packed weights (kWBytes) into the B tile, completion on `bar`
+__device__ __forceinline__ void load_weights(uint32_t b_base, const unsigned char *src, uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kWBytes)
+                 : "memory");
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                b_base + c * 32768u),
+            "l"(src + c * 32768), "r"(32768u), "r"(bar)
+            : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
 {
     asm volatile(
@@ -105,14 +123,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     k_mlp_fused(const unsigned char *__restrict__ pack, const float *__restrict__ x,
                 float *__restrict__ out, long long n, int *flag)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *sA = sm + SM_A;
     float *sF = reinterpret_cast<float *>(sm + SM_F);
-    float *sP = reinterpret_cast<float *>(sm + SM_P);
+    float *sP = reinterpret_cast<float *>(sm + SM_A);  // layer-4 partials, after the last MMA
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + SM_BAR);  // [0] weights in, [1] MMAs done
     uint32_t *slot = reinterpret_cast<uint32_t *>(sm + SM_BAR + 16);
     volatile int *abort_cta = reinterpret_cast<volatile int *>(sm + SM_BAR + 20);
@@ -121,7 +139,7 @@ __global__ void __launch_bounds__(256, 1)
     const uint32_t a_base = su32(sm + SM_A), b_base = su32(sm + SM_B);
 
     const float4 *gF = reinterpret_cast<const float4 *>(pack + 3 * kPackW);
-    for (int i = tid; i < kPackF / 4; i += 256) reinterpret_cast<float4 *>(sF)[i] = gF[i];
+    for (int i = tid; i < kPackF / 4; i += kThreads) reinterpret_cast<float4 *>(sF)[i] = gF[i];
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_ld) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_mma) : "memory");
@@ -142,10 +160,14 @@ __global__ void __launch_bounds__(256, 1)
     uint32_t ph_ld = 0, ph_mma = 0;
     bool ld_pending = false, mma_pending = false;  // thread 0: async work not yet waited for
     const long long n_tiles = (n + kTile - 1) / kTile;
-    const int row0 = tid & 127, half = tid >> 7;  // layer 0: row and column half
-    const int q = warp & 3, ch = warp >> 2;       // epilogue: lane quarter and column half
+    const int row0 = tid & 127, grp0 = tid >> 7;  // layer 0: row and column group
+    const int q = warp & 3, ch = warp >> 2;       // epilogue: lane quarter and column group
     const int erow = q * 32 + lane;
     bool failed = false;
+    if (tid == 0 && blockIdx.x < n_tiles) {  // the first layer's weights, during layer 0
+        load_weights(b_base, pack, bar_ld);
+        ld_pending = true;
+    }
 
     for (long long tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
         const long long g0 = tile * kTile;
@@ -158,8 +180,8 @@ __global__ void __launch_bounds__(256, 1)
                 x2 = bf16r(x[3 * gr + 2]);
             }
 #pragma unroll 2
-            for (int c = 0; c < 16; ++c) {
-                const int k0 = half * 128 + c * 8;
+            for (int c = 0; c < kGroupCols / 8; ++c) {
+                const int k0 = grp0 * kGroupCols + c * 8;
                 uint32_t w[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -182,19 +204,6 @@ __global__ void __launch_bounds__(256, 1)
         for (int o = 0; o < 12; ++o) acc[o] = 0.0f;
 
         for (int l = 0; l < 3; ++l) {
-            if (tid == 0) {  // this layer's weights into sB (every earlier MMA has completed)
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_ld),
-                             "r"(kWBytes)
-                             : "memory");
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], "
-                        "%2, [%3];" ::"r"(b_base + c * 32768u),
-                        "l"(pack + l * kPackW + c * 32768), "r"(32768u), "r"(bar_ld)
-                        : "memory");
-                ld_pending = true;
-            }
             // the A tile written by this CTA's threads becomes visible to the tensor cores
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             fence_before();
@@ -231,12 +240,22 @@ __global__ void __launch_bounds__(256, 1)
                 failed = true;
                 break;
             }
-            if (tid == 0) mma_pending = false;
+            if (tid == 0) {
+                mma_pending = false;
+                // the B tile is free: the next weights load during this epilogue
+                if (l < 2) {
+                    load_weights(b_base, pack + (l + 1) * kPackW, bar_ld);
+                    ld_pending = true;
+                } else if (tile + gridDim.x < n_tiles) {
+                    load_weights(b_base, pack, bar_ld);
+                    ld_pending = true;
+                }
+            }
 
             const float *bias = sF + PF_B1 + l * 256;
 #pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
-                const int col0 = ch * 128 + c * 32;
+            for (int c = 0; c < kGroupCols / 32; ++c) {
+                const int col0 = ch * kGroupCols + c * 32;
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, v);
                 if (l < 2) {
@@ -265,17 +284,22 @@ __global__ void __launch_bounds__(256, 1)
             fence_before();  // the next __syncthreads orders these reads before the next MMA
         }
         if (failed) break;
-        // layer 4: the two column halves of each row are summed through shared memory
-        if (ch == 1) {
+        // layer 4: the column groups' partial sums of each row meet in shared memory (the A
+        // tile, free once the last MMA has completed)
+        if (ch > 0) {
 #pragma unroll
-            for (int o = 0; o < 12; ++o) sP[erow * 12 + o] = acc[o];
+            for (int o = 0; o < 12; ++o) sP[((ch - 1) * kTile + erow) * 12 + o] = acc[o];
         }
         __syncthreads();
         if (ch == 0) {
             const long long gr = g0 + erow;
             if (gr < n) {
 #pragma unroll
-                for (int o = 0; o < 12; ++o) out[gr * 12 + o] = acc[o] + sP[erow * 12 + o] + sF[PF_B4 + o];
+                for (int o = 0; o < 12; ++o) {
+                    float v = acc[o];
+                    for (int g = 1; g < kGroups; ++g) v += sP[((g - 1) * kTile + erow) * 12 + o];
+                    out[gr * 12 + o] = v + sF[PF_B4 + o];
+                }
             }
         }
         __syncthreads();
@@ -310,7 +334,7 @@ int forward_fused(rp_surrogate_s *s, long long n, const float *x, float *out, cu
     RP_CUDA_TRY(cudaMemsetAsync(s->fflag, 0, sizeof(int), st));
     const long long tiles = (n + kTile - 1) / kTile;
     const int grid = (int)std::min<long long>(tiles, (long long)sm_count(dev));
-    k_mlp_fused<<<grid, 256, SM_TOTAL, st>>>(s->pack, x, out, n, s->fflag);
+    k_mlp_fused<<<grid, kThreads, SM_TOTAL, st>>>(s->pack, x, out, n, s->fflag);
     RP_CUDA_TRY(cudaGetLastError());
     return RP_OK;
 }
