@@ -350,22 +350,25 @@ int rp_surrogate_encode(int64_t n, const double *z_s, const double *z_r, const d
  *   refine_tol: a refined solution is accepted when its vertical miss |z - z_r| < refine_tol
  *     [m]; travel time, path, angles, amplitude and type then come from that trace.
  *   refine_step: the second secant point is launch + refine_step [rad].
- *   max_step: a secant step (before a sign change brackets the root) longer than this [rad]
- *     gives up on the slot.
+ *   max_step: secant steps (before a sign change brackets the root) are clamped to this
+ *     length [rad]; a ray that exhausts its path budget sends the search halfway back.
  *   refine_iters: traces per slot at most. */
 typedef struct {
     double conf, refine_tol, refine_step, max_step;
-    int32_t refine_iters, pad;
+    int32_t refine_iters;
+    int32_t deflate;  /* 1: slot 1's search runs on the miss with slot 0's root deflated away
+                         (miss / (launch - root)); 0: on the miss itself */
 } rp_surrogate_params;
 
 typedef struct {
     int64_t queries;       /* pairs */
-    int64_t tasks;         /* slots refined from the network's launch angle */
-    int64_t tasks_failed;  /* of them: did not converge (their pair fell back) */
+    int64_t tasks;         /* queries refined from the network's launch angles */
+    int64_t tasks_failed;  /* of them: a slot did not converge (the pair fell back) */
     int64_t fail_end;      /*   ... a trace ended before the receiver plane */
     int64_t fail_iters;    /*   ... refine_iters traces without convergence */
     int64_t fail_step;     /*   ... a step longer than max_step or leaving (0, pi) */
     int64_t duplicates;    /* pairs whose two slots converged to the same ray (fell back) */
+    int64_t deflated;      /* slot-1 searches run on the deflated miss */
     int64_t fallback;      /* pairs solved by the path finder */
     int64_t refine_rays, refine_steps;      /* traces (and accepted steps) of the refinement */
     int64_t fallback_rays, fallback_steps;  /* traces (and accepted steps) of the fallback */
@@ -376,9 +379,10 @@ typedef struct {
 /* Solves n pairs like rp_find_paths: the network predicts, per pair, which of the two
  * earliest solutions exist and their launch angles; each solution not ruled out is refined
  * from its predicted launch angle (secant steps, then Illinois false position once a sign
- * change brackets the root; one full trace per step) until its miss is below refine_tol.
- * Pairs with a slot that does not converge, two slots that converge to the same ray, or
- * D < p->hit_tol are solved by rp_find_paths with `p` instead (up to p->max_sol solutions;
+ * change brackets the root; one full trace per step) until its miss is below refine_tol, slot
+ * 0 first and slot 1 on the miss with slot 0's root deflated away.  Pairs with a slot that does
+ * not converge, two slots on the same ray, or D < p->hit_tol are solved by rp_find_paths with
+ * `p` instead (up to p->max_sol solutions;
  * network-served pairs have at most two).  Output as for
  * rp_find_paths (n_iter = traces of the refinement).  p->max_sol >= 2.  Returns RP_OK,
  * RP_ERR_INVALID_ARG, RP_ERR_OOM, RP_ERR_CUDA, or RP_ERR_OVERFLOW from the fallback. */

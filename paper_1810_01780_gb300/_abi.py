@@ -107,12 +107,13 @@ class TrainParams(C.Structure):
 
 class SurrogateParams(C.Structure):
     _fields_ = [("conf", C.c_double), ("refine_tol", C.c_double), ("refine_step", C.c_double),
-                ("max_step", C.c_double), ("refine_iters", C.c_int32), ("pad", C.c_int32)]
+                ("max_step", C.c_double), ("refine_iters", C.c_int32), ("deflate", C.c_int32)]
 
 
 class SurrogateStats(C.Structure):
     _fields_ = [(f, C.c_int64) for f in ("queries", "tasks", "tasks_failed", "fail_end",
-                                         "fail_iters", "fail_step", "duplicates", "fallback",
+                                         "fail_iters", "fail_step", "duplicates",
+                                         "deflated", "fallback",
                                          "refine_rays", "refine_steps", "fallback_rays",
                                          "fallback_steps")] + \
                [(f, C.c_float) for f in ("ms_forward", "ms_refine", "ms_fallback", "ms_total",

@@ -389,10 +389,11 @@ class Surrogate:
         return out
 
 
-def make_surrogate_params(conf: float = 0.95, refine_tol: float = 0.005,
+def make_surrogate_params(conf: float = 0.99, refine_tol: float = 0.005,
                           refine_step: float = 1e-3, max_step: float = 0.05,
-                          refine_iters: int = 8) -> A.SurrogateParams:
-    return A.SurrogateParams(conf, refine_tol, refine_step, max_step, int(refine_iters), 0)
+                          refine_iters: int = 16, deflate: bool = True) -> A.SurrogateParams:
+    return A.SurrogateParams(conf, refine_tol, refine_step, max_step, int(refine_iters),
+                             int(bool(deflate)))
 
 
 def encode(zs, zr, dist, sol=None, stream=None):

@@ -610,24 +610,25 @@ __global__ void k_encode(long long n, const double *zs, const double *zr, const 
 
 struct RTask {
     long long q;
-    int32_t slot, pad;
-    double th0;
+    int32_t mask, pad;  // bit k: slot k is to be searched
+    double th0[2];      // the network's launch angles of the two slots
 };
 
 struct SurCtrl {
     unsigned long long n_tasks, claim, n_fallback, failed;
-    unsigned long long fail_end, fail_iters, fail_step, duplicates;
+    unsigned long long fail_end, fail_iters, fail_step, duplicates, deflated;
 };
 
 // slot states in `cok`: absent (trusted), refining, refined
 enum { SLOT_ABSENT = 0, SLOT_PENDING = 2, SLOT_OK = 1 };
 
-// Per query: a slot whose existence probability is <= 1 - conf is trusted to be absent; every
-// other slot becomes a refinement task from the network's launch angle.  Vertical pairs, and
-// pairs whose slot 0 is absent but slot 1 is not, go to the path finder.
+// Per query: a slot whose existence probability is <= 1 - conf is trusted to be absent; the
+// other slots of the query form one refinement task.  Vertical pairs, and pairs whose slot 0
+// is absent but slot 1 is not, go to the path finder.
 __global__ void k_plan(long long n, const float *out, double conf, const PairIn pi, RTask *tasks,
                        SurCtrl *sc, int *qflag, int *cok)
 {
+    const double pi_ = 3.14159265358979323846;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         bool ex[2];
@@ -638,16 +639,15 @@ __global__ void k_plan(long long n, const float *out, double conf, const PairIn 
         const int flag = (pi.dist[i] < pi.hit_tol || (ex[1] && !ex[0])) ? 1 : 0;
         qflag[i] = flag;
         for (int k = 0; k < 2; ++k) cok[2 * i + k] = (ex[k] && !flag) ? SLOT_PENDING : SLOT_ABSENT;
-        if (flag) continue;
+        if (flag || !ex[0]) continue;
+        const unsigned long long t = atomicAdd(&sc->n_tasks, 1ull);
+        RTask &T = tasks[t];
+        T.q = i;
+        T.mask = (ex[0] ? 1 : 0) | (ex[1] ? 2 : 0);
+        T.pad = 0;
         for (int k = 0; k < 2; ++k) {
-            if (!ex[k]) continue;
-            const unsigned long long t = atomicAdd(&sc->n_tasks, 1ull);
-            RTask &T = tasks[t];
-            T.q = i;
-            T.slot = k;
-            T.pad = 0;
-            double th = 0.5 * 3.14159265358979323846 * ((double)out[12 * i + 6 * k + 1] + 1.0);
-            T.th0 = fmin(fmax(th, 1e-6), 3.14159265358979323846 - 1e-6);
+            const double th = 0.5 * pi_ * ((double)out[12 * i + 6 * k + 1] + 1.0);
+            T.th0[k] = fmin(fmax(th, 1e-6), pi_ - 1e-6);
         }
     }
 }
@@ -660,13 +660,16 @@ struct RefArgs {
     int *cok, *qflag;
     PfCtrl *ctrl;
     double h0, tol, step0, max_step;
-    int32_t iters, pad;
+    int32_t iters, deflate;
 };
 
-// Root search on the launch angle from the network's prediction, one full trace per step:
-// secant steps (the second point at launch + step0) until two misses of opposite sign
-// bracket the root, then Illinois false position inside the bracket, until |miss| < tol.
-// A ray that does not reach the receiver plane, a secant step longer than max_step or
+// Root searches on the launch angle, one lane per query, slot 0 first: from the network's
+// launch angle, one full trace per step, secant steps (the second point at launch + step0,
+// steps clamped to max_step) until two misses of opposite sign bracket the root, then Illinois
+// false position inside the bracket, until |miss| < tol.  Slot 1's search runs on the deflated
+// miss, miss / (launch - r0), where r0 is the root slot 0 found, so it cannot converge to that
+// ray again.  A ray that exhausts its path budget (far below the receiver) sends the search
+// halfway back to the previous angle.  Any other end short of the receiver plane, a step
 // leaving (0, pi), or `iters` traces without convergence send the query to the path finder.
 template <class P>
 __global__ void __launch_bounds__(128, P::kMinBlocks)
@@ -675,14 +678,26 @@ __global__ void __launch_bounds__(128, P::kMinBlocks)
     const long long nt = (long long)a.sc->n_tasks;
     const double pi_ = 3.14159265358979323846;
     long long q = 0;
-    int slot = 0, it = 0, side = 0;
-    bool br = false;
-    double th_prev = 0.0, m_prev = 0.0, th_cur = 0.0, ta = 0.0, ma = 0.0, tb = 0.0, mb = 0.0;
-    bool resume = false;
+    int slot = 0, mask = 0, it = 0, side = 0;
+    bool br = false, have_prev = false, defl = false, resume = false, next_slot = false;
+    double th_prev = 0.0, m_prev = 0.0, raw_prev = 0.0, th_cur = 0.0;
+    double ta = 0.0, ma = 0.0, tb = 0.0, mb = 0.0, th_d = 0.0, th1 = 0.0;
     auto fail = [&](unsigned long long *why) {
-        atomicExch(&a.qflag[q], 1);
+        a.qflag[q] = 1;
         atomicAdd(&a.sc->failed, 1ull);
         atomicAdd(why, 1ull);
+        next_slot = false;
+    };
+    auto start = [&](Lane<P> &L, int k, double th, bool deflated, double r) {
+        slot = k;
+        th_cur = th;
+        defl = deflated;
+        th_d = r;
+        it = 0;
+        side = 0;
+        br = false;
+        have_prev = false;
+        launch_ray<P>(L, med, sp, a.pi, a.h0, q, th_cur, false, -1);
     };
     auto next = [&](Lane<P> &L) -> bool {
         if (resume) {
@@ -690,21 +705,27 @@ __global__ void __launch_bounds__(128, P::kMinBlocks)
             launch_ray<P>(L, med, sp, a.pi, a.h0, q, th_cur, false, -1);
             return true;
         }
+        if (next_slot) {  // slot 1 after slot 0 converged
+            next_slot = false;
+            const double r0 = a.cand[2 * q].launch;
+            double th = th1;
+            if (a.deflate && fabs(th - r0) < 1e-3) th = r0 + copysign(1e-3, th - r0);
+            if (a.deflate) atomicAdd(&a.sc->deflated, 1ull);
+            start(L, 1, fmin(fmax(th, 1e-6), pi_ - 1e-6), a.deflate != 0, r0);
+            return true;
+        }
         const long long t = pf_claim(&a.sc->claim);
         if (t >= nt) return false;
         const RTask &T = a.tasks[t];
         q = T.q;
-        slot = T.slot;
-        th_cur = T.th0;
-        it = 0;
-        br = false;
-        side = 0;
-        launch_ray<P>(L, med, sp, a.pi, a.h0, q, th_cur, false, -1);
+        mask = T.mask;
+        th1 = T.th0[1];
+        start(L, 0, T.th0[0], false, 0.0);
         return true;
     };
     auto done = [&](Lane<P> &L) {
         const double m = miss_of<P>(L, a.pi.zr[q]);
-        if (!isfinite(m)) {
+        if (isnan(m) || (isinf(m) && !have_prev)) {
             fail(&a.sc->fail_end);
             return;
         }
@@ -719,8 +740,9 @@ __global__ void __launch_bounds__(128, P::kMinBlocks)
             o.path = P::sget(L.s);
             o.amp = L.A;
             o.miss = m;
-            o.dth = it > 0 ? a.tol * fabs((th_cur - th_prev) / (m - m_prev)) : 0.0;
+            o.dth = have_prev ? a.tol * fabs((th_cur - th_prev) / (m - raw_prev)) : 0.0;
             a.cok[2 * q + slot] = SLOT_OK;
+            next_slot = slot == 0 && (mask & 2);
             return;
         }
         ++it;
@@ -729,50 +751,70 @@ __global__ void __launch_bounds__(128, P::kMinBlocks)
             return;
         }
         double th_new;
-        if (br) {  // th_cur lies inside the bracket: keep the end of opposite sign
-            if ((m > 0.0) == (ma > 0.0)) {
-                ta = th_cur;
-                ma = m;
-                if (side == -1) mb *= 0.5;
-                side = -1;
-            } else {
-                tb = th_cur;
-                mb = m;
-                if (side == 1) ma *= 0.5;
-                side = 1;
-            }
-            th_new = (ta * mb - tb * ma) / (mb - ma);
-        } else if (it == 1) {
-            th_new = th_cur + a.step0;
-        } else if ((m > 0.0) != (m_prev > 0.0)) {
-            br = true;
-            ta = th_prev;
-            ma = m_prev;
-            tb = th_cur;
-            mb = m;
-            side = 0;
-            th_new = (ta * mb - tb * ma) / (mb - ma);
+        if (isinf(m)) {  // far below: back toward the last angle that reached the receiver plane
+            th_new = 0.5 * (th_cur + th_prev);
         } else {
-            th_new = th_cur - m * (th_cur - th_prev) / (m - m_prev);
-            if (!(fabs(th_new - th_cur) <= a.max_step)) {
-                fail(&a.sc->fail_step);
-                return;
+            double g = m;
+            if (defl) {
+                const double d = th_cur - th_d;
+                if (fabs(d) < 1e-12) {
+                    fail(&a.sc->fail_step);
+                    return;
+                }
+                g = m / d;
             }
+            if (br) {  // th_cur lies inside the bracket: keep the end of opposite sign
+                if ((g > 0.0) == (ma > 0.0)) {
+                    ta = th_cur;
+                    ma = g;
+                    if (side == -1) mb *= 0.5;
+                    side = -1;
+                } else {
+                    tb = th_cur;
+                    mb = g;
+                    if (side == 1) ma *= 0.5;
+                    side = 1;
+                }
+                th_new = (ta * mb - tb * ma) / (mb - ma);
+            } else if (!have_prev) {
+                th_new = th_cur + a.step0;
+            } else if ((g > 0.0) != (m_prev > 0.0)) {
+                br = true;
+                ta = th_prev;
+                ma = m_prev;
+                tb = th_cur;
+                mb = g;
+                side = 0;
+                th_new = (ta * mb - tb * ma) / (mb - ma);
+            } else {
+                th_new = th_cur - g * (th_cur - th_prev) / (g - m_prev);
+                if (isfinite(th_new) && fabs(th_new - th_cur) > a.max_step)
+                    th_new = th_cur + copysign(a.max_step, th_new - th_cur);
+            }
+            th_prev = th_cur;
+            m_prev = g;  // the searched function: the miss, or the deflated miss
+            raw_prev = m;
+            have_prev = true;
         }
         if (!(th_new > 0.0 && th_new < pi_)) {
             fail(&a.sc->fail_step);
             return;
         }
-        th_prev = th_cur;
-        m_prev = m;
         th_cur = th_new;
         resume = true;
     };
     drive<P>(med, sp, sk, a.ctrl, next, done);
 }
 
+// two refined slots of a pair land on the same ray: same type, launch angles within twice the
+// sum of their uncertainties (at least 1e-5 rad)
+__device__ __forceinline__ bool same_ray(const Cand &A, const Cand &B)
+{
+    return A.type == B.type && fabs(A.launch - B.launch) <= fmax(1e-5, 2.0 * (A.dth + B.dth));
+}
+
 // Queries served by the network: their refined slots sorted by travel time into the outputs;
-// a failed slot, or two slots refined to the same ray, send the query to the fallback list.
+// a failed slot, or two slots on the same ray, send the query to the fallback list.
 __global__ void k_collect(long long n, int max_sol, const int *cok, const Cand *cand,
                           const int *qflag, rp_solutions sol, long long *fb, SurCtrl *sc)
 {
@@ -780,16 +822,13 @@ __global__ void k_collect(long long n, int max_sol, const int *cok, const Cand *
          i += (long long)gridDim.x * blockDim.x) {
         bool to_fb = qflag[i] != 0;
         int cnt = 0;
-        int idx[2];
+        int idx[2] = {0, 0};
         if (!to_fb) {
             for (int k = 0; k < 2; ++k) {
                 if (cok[2 * i + k] == SLOT_PENDING) to_fb = true;
                 if (cok[2 * i + k] == SLOT_OK) idx[cnt++] = k;
             }
-            // the same ray twice: same type, launch angles within their uncertainties
-            if (!to_fb && cnt == 2 && cand[2 * i].type == cand[2 * i + 1].type &&
-                fabs(cand[2 * i].launch - cand[2 * i + 1].launch) <=
-                    fmax(1e-5, 2.0 * (cand[2 * i].dth + cand[2 * i + 1].dth))) {
+            if (!to_fb && cnt == 2 && same_ray(cand[2 * i], cand[2 * i + 1])) {
                 to_fb = true;
                 atomicAdd(&sc->duplicates, 1ull);
             }
@@ -909,7 +948,7 @@ int pipe_ensure(rp_surrogate_s *s, long long n, int max_sol)
     p->cap = c;
     RP_CUDA_TRY(cudaMalloc(&p->x, sizeof(float) * 3 * c));
     RP_CUDA_TRY(cudaMalloc(&p->out, sizeof(float) * 12 * c));
-    RP_CUDA_TRY(cudaMalloc(&p->tasks, sizeof(RTask) * 2 * c));
+    RP_CUDA_TRY(cudaMalloc(&p->tasks, sizeof(RTask) * c));
     RP_CUDA_TRY(cudaMalloc(&p->cand, sizeof(Cand) * 2 * c));
     RP_CUDA_TRY(cudaMalloc(&p->cok, sizeof(int) * 2 * c));
     RP_CUDA_TRY(cudaMalloc(&p->qflag, sizeof(int) * c));
@@ -982,7 +1021,7 @@ int run_surrogate(rp_surrogate_s *s, rp_medium_t m, const PairIn &pi, const rp_t
     ra.step0 = sp_in->refine_step;
     ra.max_step = sp_in->max_step;
     ra.iters = sp_in->refine_iters;
-    ra.pad = 0;
+    ra.deflate = sp_in->deflate;
     const int occ = occ_of((const void *)k_refine<P>);
     if (occ < 0) return occ;
     k_refine<P><<<sms * occ, 128, 0, st>>>(m->layered, sp, sk, ra);
@@ -1031,6 +1070,7 @@ int run_surrogate(rp_surrogate_s *s, rp_medium_t m, const PairIn &pi, const rp_t
         stats->fail_iters = (int64_t)hs.fail_iters;
         stats->fail_step = (int64_t)hs.fail_step;
         stats->duplicates = (int64_t)hs.duplicates;
+        stats->deflated = (int64_t)hs.deflated;
         stats->refine_rays = (int64_t)hp.rays;
         stats->refine_steps = (int64_t)hp.steps_acc;
         stats->fallback_rays = fs.rays;
@@ -1067,7 +1107,8 @@ int run_surrogate_paths(rp_surrogate_s *s, rp_medium_t m, int64_t n, const doubl
     if (n == 0) return RP_OK;
     if (!zs || !zr || !dist || !n_angles || !sol->count || p->max_sol < 2 || p->max_sol > 8 ||
         !(sp->conf > 0.5 && sp->conf < 1.0) || !(sp->refine_tol > 0.0) || sp->refine_iters < 1 ||
-        !(sp->refine_step > 0.0) || !(sp->max_step > 0.0) || !(p->hit_tol > 0.0)) {
+        !(sp->refine_step > 0.0) || !(sp->max_step > 0.0) || !(p->hit_tol > 0.0) ||
+        (sp->deflate != 0 && sp->deflate != 1)) {
         set_error("rp_surrogate_find_paths: bad arrays or parameters (max_sol 2..8, 0.5 < conf < 1)");
         return RP_ERR_INVALID_ARG;
     }
