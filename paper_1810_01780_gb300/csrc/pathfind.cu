@@ -40,7 +40,9 @@ struct PairIn {
 
 struct Bracket {
     double tha, thb, ma;
-    int32_t pair, pad;
+    int32_t pair;
+    int32_t it, active;  // speculative rounds: bisection step of the next midpoint; still open
+    int32_t pad;
 };
 
 struct Cand {
@@ -52,6 +54,7 @@ struct Cand {
 struct PfCtrl {
     unsigned long long claim_scan, claim_bisect, n_brackets, rays;
     unsigned long long steps_acc, steps_rej, steps_root;
+    unsigned long long open;  // speculative rounds: brackets still open
     unsigned int flags, pad;
 };
 
@@ -314,6 +317,8 @@ __global__ void k_brackets(const BracketArgs a)
         o.thb = pi_ * (double)(j + 1) / (double)(na - 1);
         o.ma = ma;
         o.pair = (int)i;
+        o.it = 1;
+        o.active = 1;
         o.pad = 0;
     }
 }
@@ -384,6 +389,145 @@ __global__ void __launch_bounds__(128, P::kMinBlocks)
         return next(L);
     };
     drive<P>(med, sp, sk, a.ctrl, next_or_resume, done);
+}
+
+// Speculative bisection for few brackets.  One round evaluates, for every open bracket, the
+// G = 2^J - 1 midpoints of J consecutive bisection steps at once -- every point the sequential
+// bisection could visit next, as the nodes of a binary tree in heap order, each computed by the
+// same nested midpoints 0.5 (lo + hi) that the sequential steps compute -- one trace per lane;
+// k_bisect_resolve then walks the tree along the signs exactly as J sequential steps would and
+// keeps the same stopping rules, so the result equals k_bisect's, bit for bit, in J times fewer
+// rounds of trace latency and about G / J times the traces.
+struct NodeRec {
+    double thm, miss, receive, time, path, amp;
+    int32_t type, flag;  // flag: 0 traced, 1 not taken (step cap or exhausted bracket)
+};
+
+struct RoundArgs {
+    PairIn pi;
+    Bracket *br;
+    long long nb;
+    int32_t J, G;
+    NodeRec *rec;
+    PfCtrl *ctrl;
+    double h0;
+};
+
+// the heap node h (1-based) of a bracket's tree: its angle, depth, and whether it lies strictly
+// inside its interval
+__device__ __forceinline__ void tree_node(const Bracket &B, int h, double &thm, int &depth,
+                                          bool &inside)
+{
+    double lo = B.tha, hi = B.thb;
+    depth = 31 - __clz(h);
+    for (int d = depth - 1; d >= 0; --d) {
+        const double mid = 0.5 * (lo + hi);
+        if ((h >> d) & 1)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    thm = 0.5 * (lo + hi);
+    inside = thm > lo && thm < hi;
+}
+
+template <class P>
+__global__ void __launch_bounds__(128, P::kMinBlocks)
+    k_bisect_round(const MediumLayered med, const StepParams<P> sp, const Sinks sk, const RoundArgs a)
+{
+    const long long items = a.nb * a.G;
+    long long cur = 0;
+    auto next = [&](Lane<P> &L) -> bool {
+        for (;;) {
+            cur = pf_claim(&a.ctrl->claim_bisect);
+            if (cur >= items) return false;
+            const long long b = cur / a.G;
+            const Bracket &B = a.br[b];
+            if (!B.active) continue;
+            const int h = (int)(cur % a.G) + 1;
+            double thm;
+            int depth;
+            bool inside;
+            tree_node(B, h, thm, depth, inside);
+            NodeRec &R = a.rec[cur];
+            R.thm = thm;
+            if (B.it + depth > a.pi.max_iter || !inside) {
+                R.flag = 1;
+                continue;
+            }
+            R.flag = 0;
+            launch_ray<P>(L, med, sp, a.pi, a.h0, B.pair, thm, false, -1);
+            return true;
+        }
+    };
+    auto done = [&](Lane<P> &L) {
+        const long long b = cur / a.G;
+        NodeRec &R = a.rec[cur];
+        R.miss = miss_of<P>(L, a.pi.zr[a.br[b].pair]);
+        R.type = L.n_refl > 0 ? RP_SOL_REFLECTED : (L.n_turn > 0 ? RP_SOL_REFRACTED : RP_SOL_DIRECT);
+        R.receive = acos(fmax(-1.0, fmin(1.0, P::get(L.t, 2))));
+        R.time = P::sget(L.T);
+        R.path = P::sget(L.s);
+        R.amp = L.A;
+    };
+    drive<P>(med, sp, sk, a.ctrl, next, done);
+}
+
+// Walks each open bracket's tree as the sequential bisection would: stop on a NaN miss, on a
+// hit (|miss| < hit_tol: a candidate), at the step cap or when the interval is exhausted;
+// otherwise keep the half whose ends still differ in sign.  Counts the brackets still open.
+__global__ void k_bisect_resolve(const RoundArgs a, int *cand_n, Cand *cand,
+                                 unsigned long long *open)
+{
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < a.nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        Bracket &B = a.br[b];
+        if (!B.active) continue;
+        double lo = B.tha, hi = B.thb;
+        int h = 1;
+        bool open_ = true;
+        for (int d = 0; d < a.J; ++d) {
+            const NodeRec &R = a.rec[b * a.G + (h - 1)];
+            if (R.flag || isnan(R.miss)) {
+                open_ = false;
+                break;
+            }
+            if (fabs(R.miss) < a.pi.hit_tol) {
+                const int c = atomicAdd(&cand_n[B.pair], 1);
+                if (c >= kMaxCand) {
+                    atomicOr(&a.ctrl->flags, 4u);
+                } else {
+                    Cand &o = cand[(long long)B.pair * kMaxCand + c];
+                    o.type = R.type;
+                    o.n_iter = B.it + d;
+                    o.launch = R.thm;
+                    o.receive = R.receive;
+                    o.time = R.time;
+                    o.path = R.path;
+                    o.amp = R.amp;
+                    o.miss = R.miss;
+                    o.dth = 0.0;
+                }
+                open_ = false;
+                break;
+            }
+            if ((R.miss > 0.0) == (B.ma > 0.0)) {
+                lo = R.thm;
+                h = 2 * h + 1;
+            } else {
+                hi = R.thm;
+                h = 2 * h;
+            }
+        }
+        if (open_) {
+            B.tha = lo;
+            B.thb = hi;
+            B.it += a.J;
+            atomicAdd(open, 1ull);
+        } else {
+            B.active = 0;
+        }
+    }
 }
 
 // per pair: candidates sorted by travel time into the max_sol output slots
@@ -457,12 +601,17 @@ int run_pf(rp_medium_t m, const PairIn &pi, const rp_trace_params *tp, rp_soluti
     sp.max_generation = 0;
     const int occ_s = occ_of((const void *)k_scan<P>);
     const int occ_b = occ_of((const void *)k_bisect<P>);
+    const int occ_r = occ_of((const void *)k_bisect_round<P>);
     if (occ_s < 0) return occ_s;
     if (occ_b < 0) return occ_b;
+    if (occ_r < 0) return occ_r;
     const int sms = sm_count(dev);
     const long long np = pi.n_pairs;
+    const long long lanes = (long long)sms * occ_r * 128;
+    const size_t rec_cap = (size_t)(lanes + lanes / 4) + 4096;  // tree nodes of one round
     // workspace: path-finding control, tracer control block (for the split code's flags),
-    // prefix sums, candidates and their counts, brackets, then one miss per scan ray
+    // prefix sums, candidates and their counts, brackets, speculative tree nodes, then one miss
+    // per scan ray
     const size_t off_pf = 0;
     const size_t off_tc = al(sizeof(PfCtrl));
     const size_t off_pre = off_tc + al(sizeof(Ctrl));
@@ -470,7 +619,8 @@ int run_pf(rp_medium_t m, const PairIn &pi, const rp_trace_params *tp, rp_soluti
     const size_t off_c = off_cn + al(sizeof(int) * (size_t)np);
     const size_t br_cap = (size_t)np * 16 + 1024;
     const size_t off_br = off_c + al(sizeof(Cand) * (size_t)np * kMaxCand);
-    const size_t off_miss = off_br + al(sizeof(Bracket) * br_cap);
+    const size_t off_rec = off_br + al(sizeof(Bracket) * br_cap);
+    const size_t off_miss = off_rec + al(sizeof(NodeRec) * rec_cap);
 
     Workspace &ws = workspace(dev);
     std::lock_guard<std::mutex> lock(ws.mu);
@@ -495,6 +645,7 @@ int run_pf(rp_medium_t m, const PairIn &pi, const rp_trace_params *tp, rp_soluti
     int *cand_n = (int *)(base + off_cn);
     Cand *cand = (Cand *)(base + off_c);
     Bracket *br = (Bracket *)(base + off_br);
+    NodeRec *rec = (NodeRec *)(base + off_rec);
     double *miss = (double *)(base + off_miss);
     RP_CUDA_TRY(cudaMemsetAsync(cand_n, 0, sizeof(int) * (size_t)std::max(np, 1LL), st));
 
@@ -524,15 +675,55 @@ int run_pf(rp_medium_t m, const PairIn &pi, const rp_trace_params *tp, rp_soluti
     ba.ctrl = ctrl;
     k_brackets<<<sms * 8, 256, 0, st>>>(ba);
     RP_CUDA_TRY(cudaEventRecord(ev[1], st));
-    BisectArgs bb;
-    bb.pi = pi;
-    bb.br = br;
-    bb.br_cap = br_cap;
-    bb.cand_n = cand_n;
-    bb.cand = cand;
-    bb.ctrl = ctrl;
-    bb.h0 = tp->h0;
-    k_bisect<P><<<sms * occ_b, 128, 0, st>>>(m->layered, sp, sk, bb);
+    // Few brackets for the lanes: speculative rounds of J bisection steps (J as large as the
+    // lanes allow, at most 5); otherwise one lane per bracket, bisecting on its own.
+    unsigned long long nb_raw = 0;
+    RP_CUDA_TRY(cudaMemcpyAsync(&nb_raw, &ctrl->n_brackets, sizeof nb_raw, cudaMemcpyDeviceToHost,
+                                st));
+    RP_CUDA_TRY(cudaStreamSynchronize(st));
+    const long long nb = (long long)std::min<unsigned long long>(nb_raw, br_cap);
+    int J = 1;
+    while (J < 5 && nb > 0 && nb * ((1LL << (J + 1)) - 1) <= (long long)rec_cap &&
+           nb * ((1LL << (J + 1)) - 1) <= lanes + lanes / 4)
+        ++J;
+    int rounds = 0;
+    if (J == 1) {
+        BisectArgs bb;
+        bb.pi = pi;
+        bb.br = br;
+        bb.br_cap = br_cap;
+        bb.cand_n = cand_n;
+        bb.cand = cand;
+        bb.ctrl = ctrl;
+        bb.h0 = tp->h0;
+        k_bisect<P><<<sms * occ_b, 128, 0, st>>>(m->layered, sp, sk, bb);
+    } else {
+        RoundArgs ra;
+        ra.pi = pi;
+        ra.br = br;
+        ra.nb = nb;
+        ra.J = J;
+        ra.G = (1 << J) - 1;
+        ra.rec = rec;
+        ra.ctrl = ctrl;
+        ra.h0 = tp->h0;
+        const int max_rounds = pi.max_iter / J + 2;
+        const int rblocks = std::max(1, (int)std::min<long long>((nb + 255) / 256, (long long)sms * 8));
+        for (; rounds < max_rounds; ++rounds) {
+            RP_CUDA_TRY(cudaMemsetAsync(&ctrl->claim_bisect, 0, sizeof(unsigned long long), st));
+            RP_CUDA_TRY(cudaMemsetAsync(&ctrl->open, 0, sizeof(unsigned long long), st));
+            k_bisect_round<P><<<sms * occ_r, 128, 0, st>>>(m->layered, sp, sk, ra);
+            k_bisect_resolve<<<rblocks, 256, 0, st>>>(ra, cand_n, cand, &ctrl->open);
+            RP_CUDA_TRY(cudaGetLastError());
+            unsigned long long open = 0;
+            RP_CUDA_TRY(cudaMemcpyAsync(&open, &ctrl->open, sizeof open, cudaMemcpyDeviceToHost, st));
+            RP_CUDA_TRY(cudaStreamSynchronize(st));
+            if (open == 0) {
+                ++rounds;
+                break;
+            }
+        }
+    }
     k_finalize<<<std::max(1, (int)std::min<long long>((np + 255) / 256, (long long)sms * 8)), 256,
                  0, st>>>(pi, cand_n, cand, *sol);
     RP_CUDA_TRY(cudaEventRecord(ev[2], st));
@@ -552,7 +743,7 @@ int run_pf(rp_medium_t m, const PairIn &pi, const rp_trace_params *tp, rp_soluti
         stats->steps_rejected = (int64_t)hc.steps_rej;
         stats->steps_root = (int64_t)hc.steps_root;
         stats->queue_needed = (int64_t)hc.n_brackets;
-        stats->waves = 2;
+        stats->waves = 2 + rounds;
         stats->flags = (int32_t)(hc.flags | tflags);
         stats->kernel_ms = ms_all;
         stats->wave_ms[0] = ms_scan;

@@ -148,3 +148,24 @@ def test_paths_vertical_and_edge_pairs(rp):
     for i in range(2):  # vertical pairs: straight up / down, T = integral of n dz / c0
         assert g["count"][i] == 1 and g["type"][i, 0] == 0
         assert abs(g["time"][i, 0] - osol[i, 0]["time"]) < 1e-18
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_speculative_bisection_equals_per_lane_bisection(rp, precision):
+    """A batch with few brackets per lane takes speculative rounds of several bisection steps
+    (one tree of midpoints per bracket per round); a full batch bisects one bracket per lane.
+    The pairs of a small batch, solved alone and inside the full batch, give identical
+    solutions field by field."""
+    cfg = W.paths()
+    P = cfg["pairs"]
+    kw = dict(hit_tol=0.005, max_iter=cfg["max_iter"], max_sol=cfg["max_sol"])
+    med = rp.Medium(cfg["medium"])
+    full = _np(rp.find_paths(med, P["zs"], P["zr"], P["dist"], P["n_angles"], cfg["params"],
+                             precision, **kw))
+    sub = np.arange(0, len(P["zs"]), 97)[:512]
+    small = _np(rp.find_paths(med, P["zs"][sub], P["zr"][sub], P["dist"][sub],
+                              P["n_angles"][sub], cfg["params"], precision, **kw))
+    assert small["stats"]["waves"] > 2 and full["stats"]["waves"] == 2  # rounds vs per lane
+    np.testing.assert_array_equal(small["count"], full["count"][sub])
+    for k in ("type", "n_iter", "launch", "receive", "time", "path", "amp", "miss"):
+        np.testing.assert_array_equal(small[k], full[k][sub], err_msg=k)
