@@ -307,6 +307,20 @@ def surrogate_leg(rp, W, args, rank, flush):
     }
 
 
+def reduce_over_ranks(total_ms, counts, device):
+    """Whole-job figures of a timed region: the slowest rank's time (every rank's work counts
+    only when all are done) and the sums of the ranks' work counters.  One rank: unchanged."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(v) for v in counts], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t[0]), [float(v) for v in c]
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -368,16 +382,7 @@ def run_gpu(args):
             att += st.steps_accepted + st.steps_rejected + st.steps_root
             nrays += st.rays
         torch.cuda.synchronize()
-    total_ms = sum(times)
-    tot = torch.tensor([total_ms, float(acc), float(nrays)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        t_max = tot[0:1].clone()
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        sums = tot[1:].clone()
-        dist.all_reduce(sums, op=dist.ReduceOp.SUM)
-        total_ms_max, acc_all, rays_all = float(t_max[0]), float(sums[0]), float(sums[1])
-    else:
-        total_ms_max, acc_all, rays_all = total_ms, float(acc), float(nrays)
+    total_ms_max, (acc_all, rays_all) = reduce_over_ranks(sum(times), [acc, nrays], "cuda")
     value = acc_all / (total_ms_max / 1e3)
     clocks = clk.summary()
 
