@@ -471,6 +471,39 @@ def run_gpu(args):
         }
         del gmed, grays, gbuf
 
+    # the paper's Fig. 1 example as a 1,048,576-ray fan: firn layer over ice, 5 us, A/A0 cut
+    if not args.no_fig1:
+        fcfg = W.fig1()
+        fmed = rp.Medium(fcfg["medium"])
+        frays = rp.PreparedRays(*fcfg["rays"])
+        fbuf = rp.TraceBuffers(3 * frays.n, 0, fields=("end_pos", "path", "time", "status"))
+        leg, ends = {"workload": "Fig. 1 example: 1,048,576 rays from 240 m in the x-z plane, "
+                                 "10 m of n = 1.5 over exponential ice (z0 = 71.4 m), 5 us, "
+                                 "A/A0 < 0.05 discarded, generations <= 8"}, {}
+        for prec in ("fp32", "fp64"):
+            fprm = rp.make_params(fcfg["params"], prec)
+            rp.trace_into(fmed, frays, fprm, fbuf)  # warm-up
+            ft, facc, fr = [], 0, 0
+            for _ in range(args.grid_steps):
+                flush.fill_(1.0)
+                st = rp.trace_into(fmed, frays, fprm, fbuf)
+                ft.append(st.kernel_ms)
+                facc += st.steps_accepted
+                fr += st.rays
+            fsec = sum(ft) / 1e3
+            key = "fp32_mixed" if prec == "fp32" else "fp64"
+            leg[key] = {"ray_steps_per_s": facc / fsec, "rays_per_s": fr / fsec,
+                        "ms_per_step": 1e3 * fsec / len(ft)}
+            ends[prec] = (fbuf.t["end_pos"][:, :frays.n].clone(), fbuf.t["time"][:frays.n].clone())
+        fd = (ends["fp32"][0] - ends["fp64"][0]).norm(dim=0)
+        fT = (ends["fp32"][1] - ends["fp64"][1]).abs()
+        leg["error_fp32_vs_fp64"] = {
+            "primaries": frays.n, "pos_m_p99": float(fd.double().quantile(0.99)),
+            "time_s_p99": float(fT.double().quantile(0.99)),
+            "within_1mm_10ps": float(((fd <= 1e-3) & (fT <= 1e-11)).double().mean())}
+        modes["fig1"] = leg
+        del fmed, frays, fbuf, ends
+
     # source-receiver path finding: 65,536 pairs, 32..512 scan angles each, FP64 bisection
     if not args.no_paths:
         pcfg = W.paths()
@@ -553,6 +586,7 @@ def main():
     ap.add_argument("--rays", type=int, default=N_RAYS,
                     help="primaries of the batched workload (the bench workload is 1,048,576)")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-fig1", action="store_true")
     ap.add_argument("--sur-train", type=int, default=4_194_304)
     ap.add_argument("--sur-queries", type=int, default=1_048_576)
     ap.add_argument("--sur-check", type=int, default=16_384)

@@ -13,6 +13,8 @@ workloads:
                 4,194,304 isotropic rays from 16 sources
   ``paths``     65,536 source-receiver pairs with 32..512 scan angles each
   ``surrogate`` 4,194,304 training pairs and 1,048,576 query pairs of the ``paths`` distribution
+  ``fig1``      the paper's Fig. 1 example (firn layer over exponential ice, 5 us, A/A0 cut) as
+                a fan of 1,048,576 rays
 
 Conventions: z = depth (positive downward), angles from +z, positions in metres; ray arrays
 are SoA with shape (3, n).
@@ -51,6 +53,17 @@ def two_layer_ice(z_int: float = 100.0, jump: float = 0.02) -> dict:
 def single_profile(n0=1.788, dn=0.463, z0=75.0) -> dict:
     """One exponential layer continued to all depths (no boundary)."""
     return {"kind": "layered", "layers": [dict(n0=n0, dn=dn, z0=z0, off=0.0, absorb=False)]}
+
+
+def firn_over_ice(n_firn: float = 1.5, z_firn: float = 10.0, z0: float = 71.4,
+                  n_air: float = 1.0) -> dict:
+    """The medium of the paper's Fig. 1: air (absorbing) above z = 0, a layer of constant index
+    n_firn from 0 to z_firn, the exponential profile n0 - dn exp(-z/z0) below (z0 = 71.4 m)."""
+    return {"kind": "layered", "layers": [
+        dict(n0=n_air, dn=0.0, z0=1.0, off=0.0, absorb=True),
+        dict(z_top=0.0, n0=n_firn, dn=0.0, z0=1.0, off=0.0, absorb=False),
+        dict(z_top=z_firn, n0=ICE["n0"], dn=ICE["dn"], z0=z0, off=0.0, absorb=False),
+    ]}
 
 
 def gaussian_random_field(shape, spacing, sigma, corr_len, seed) -> np.ndarray:
@@ -196,6 +209,17 @@ def paths(n=65_536, seed=4):
     return dict(name="paths", medium=ice_with_surface(),
                 params=dict(TRACE_DEFAULTS, max_path=10000.0, max_generation=0),
                 pairs=pairs(n, seed), hit_tol=0.1, max_iter=60, max_sol=4)
+
+
+def fig1(n=1_048_576):
+    """The example of the paper's Fig. 1: rays in the x-z plane from 240 m depth (launch
+    angles 0..180 deg), the firn-over-ice medium, followed to a propagation time of 5 us;
+    rays whose amplitude falls below 0.05 of the initial one are discarded.  Secondaries up to
+    generation 8 (the paper shows multiple reflections and states no cap)."""
+    return dict(name="fig1", medium=firn_over_ice(),
+                params=dict(TRACE_DEFAULTS, max_path=3000.0, max_time=5e-6, min_amp=0.05,
+                            max_generation=8),
+                rays=fan_xz(n, 240.0), receivers=None)
 
 
 def surrogate(n_train=4_194_304, n_query=1_048_576, seed=5):

@@ -82,3 +82,35 @@ def subtree_of_roots(parent, roots):
             j = int(parent[j])
         root[i] = j
     return np.nonzero(np.isin(root, roots))[0], root
+
+
+def check_fp64(g, o, tol, min_tier1=0.95, rel=1e-9):
+    gi, oi, only_g, only_o = match(g, o)
+    assert not only_g and not only_o, (len(only_g), len(only_o))
+    assert np.array_equal(g["status"][gi], o["status"][oi])
+    assert np.array_equal(g["generation"][gi], o["generation"][oi])
+    dp, dd, ds, dT, dA = errors(g, o, gi, oi)
+    s = o["path"][oi]
+    same = same_steps(g, o, gi, oi)
+    t1 = same
+    assert np.all(dp[t1] <= rel * (s[t1] + 1.0)), dp[t1].max()
+    assert np.all(ds[t1] <= rel * (s[t1] + 1.0)), ds[t1].max()
+    assert np.all(dT[t1] <= rel * o["time"][oi][t1] + 1e-18), dT[t1].max()
+    assert np.all(dd[t1] <= rel), dd[t1].max()
+    assert np.all(dA[t1] <= rel), dA[t1].max()
+    assert same.mean() >= min_tier1, same.mean()
+    t2 = ~same
+    if t2.any():
+        assert np.all(dp[t2] <= 10 * tol * (s[t2] + 1.0)), dp[t2].max()
+        assert np.all(dT[t2] <= 10 * tol * o["time"][oi][t2] + 1e-15)
+    return same.mean()
+
+
+def tilt(d, angle, seed):
+    """Rotate every direction by `angle` rad about a random axis perpendicular to it."""
+    rng = np.random.default_rng(seed)
+    d = d / np.linalg.norm(d, axis=0)
+    a = rng.standard_normal(d.shape)
+    a -= (a * d).sum(0) * d
+    a /= np.linalg.norm(a, axis=0)
+    return np.cos(angle) * d + np.sin(angle) * a

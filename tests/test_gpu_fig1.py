@@ -1,0 +1,93 @@
+"""The paper's Fig. 1 example on the GPU (Sec. 2, Fig. 1 text): a fan of rays in the x-z plane
+from 240 m depth in a 10 m layer of n = 1.5 over the exponential ice (z0 = 71.4 m), air above,
+followed for 5 us with rays below A/A0 = 0.05 discarded.  FP64 path against the oracle with the
+tolerances of test_gpu_trace; FP32-mixed against FP64 within 1 mm / 0.01 ns for every ray whose
+FP64 result is itself stable under a 1e-7 rad launch tilt; the break conditions."""
+import numpy as np
+import pytest
+
+import oracle
+from parity import check_fp64, errors, gpu_rays, match, oracle_rays, tilt
+from paper_1810_01780_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+C0 = 299792458.0
+ST = oracle.STATUS
+
+
+@pytest.fixture(scope="module")
+def rp():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1810_01780_gb300 import build
+
+    build.build()
+    import paper_1810_01780_gb300 as rp
+
+    return rp
+
+
+def _run(rp, cfg, rays, precision):
+    pos, d, a = rays
+    return gpu_rays(rp.trace(rp.Medium(cfg["medium"]), pos, d, a, params=cfg["params"],
+                             precision=precision))
+
+
+def test_fig1_fp64_matches_oracle(rp):
+    cfg = W.fig1(1024)
+    g = _run(rp, cfg, cfg["rays"], "fp64")
+    ref, _ = oracle.trace(cfg["medium"], cfg["params"], *cfg["rays"])
+    o = oracle_rays(ref)
+    assert len(g["path"]) == len(ref)
+    frac = check_fp64(g, o, cfg["params"]["tol"])
+    print("tier-1 fraction", frac)
+    # every end is a break condition of the example: 5 us, the amplitude cut, or air
+    assert set(np.unique(g["status"])) <= {ST["MAX_TIME"], ST["MIN_AMP"], ST["TRANSMITTED"]}
+    assert np.any(g["n_refl"] >= 5)  # multiple reflections in the firn layer
+
+
+def test_fig1_break_conditions(rp):
+    cfg = W.fig1(65536)
+    g = _run(rp, cfg, cfg["rays"], "fp32")
+    p = cfg["params"]
+    t_max = p["max_time"]
+    mt = g["status"] == ST["MAX_TIME"]
+    # the time limit ends the ray after the step that crosses it: at most one step beyond
+    assert np.all(g["time"][mt] >= t_max)
+    assert np.all(g["time"][mt] <= t_max + p["h_max"] * 1.8 / C0)
+    assert np.all(g["time"][~mt] < t_max + 1e-15)
+    ma = g["status"] == ST["MIN_AMP"]
+    assert ma.any() and np.all(np.abs(g["amp"][ma]) < p["min_amp"])
+    tr = g["status"] == ST["TRANSMITTED"]
+    assert tr.any() and np.all(np.abs(g["pos"][tr, 2]) < 1e-3)  # recorded at the surface
+    assert g["generation"].max() <= p["max_generation"]
+
+
+def test_fig1_fp32_mixed_vs_fp64(rp):
+    cfg = W.fig1(65536)
+    pos, d, a = cfg["rays"]
+    g64 = _run(rp, cfg, (pos, d, a), "fp64")
+    g32 = _run(rp, cfg, (pos, d, a), "fp32")
+    gpt = _run(rp, cfg, (pos, tilt(d, 1e-7, 3), a), "fp64")
+    gi, oi, only32, only64 = match(g32, g64)
+    n = max(len(g32["path"]), len(g64["path"]))
+    assert len(only32) + len(only64) <= 0.002 * n
+    ok = g32["status"][gi] == g64["status"][oi]
+    assert ok.mean() > 0.998
+    gi, oi = gi[ok], oi[ok]
+    dp, dd, ds, dT, dA = errors(g32, g64, gi, oi)
+    pi, qi, _, _ = match(gpt, g64)
+    sens = np.ones(len(g64["path"]), dtype=bool)
+    sp, _, _, sT, _ = errors(gpt, g64, pi, qi)
+    sens[qi] = ~(gpt["status"][pi] == g64["status"][qi]) | (sp > 1e-3) | (sT > 1e-11)
+    s_ok = ~sens[oi]
+    good = (dp <= 1e-3) & (dT <= 1e-11)
+    print("fig1 fp32 vs fp64: %d rays, p99 |dr| %.2e m, p99 |dT| %.2e s, well-conditioned "
+          "within 1 mm / 0.01 ns %.5f (%.4f sensitive)" % (
+              len(gi), np.quantile(dp, 0.99), np.quantile(dT, 0.99), good[s_ok].mean(),
+              1 - s_ok.mean()))
+    assert np.quantile(dp, 0.99) <= 1e-3
+    assert good[s_ok].mean() >= 0.999
+    assert (1 - s_ok.mean()) <= 0.05

@@ -10,7 +10,8 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import errors, gpu_rays, match, oracle_rays, same_steps, subtree_of_roots
+from parity import (check_fp64, errors, gpu_rays, match, oracle_rays, same_steps,
+                    subtree_of_roots, tilt)
 from paper_1810_01780_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -37,35 +38,13 @@ def _run(rp, medium, params, rays, receivers=None, precision="fp64"):
     return res
 
 
-def _check_fp64(g, o, tol, min_tier1=0.95, rel=1e-9):
-    gi, oi, only_g, only_o = match(g, o)
-    assert not only_g and not only_o, (len(only_g), len(only_o))
-    assert np.array_equal(g["status"][gi], o["status"][oi])
-    assert np.array_equal(g["generation"][gi], o["generation"][oi])
-    dp, dd, ds, dT, dA = errors(g, o, gi, oi)
-    s = o["path"][oi]
-    same = same_steps(g, o, gi, oi)
-    t1 = same
-    assert np.all(dp[t1] <= rel * (s[t1] + 1.0)), dp[t1].max()
-    assert np.all(ds[t1] <= rel * (s[t1] + 1.0)), ds[t1].max()
-    assert np.all(dT[t1] <= rel * o["time"][oi][t1] + 1e-18), dT[t1].max()
-    assert np.all(dd[t1] <= rel), dd[t1].max()
-    assert np.all(dA[t1] <= rel), dA[t1].max()
-    assert same.mean() >= min_tier1, same.mean()
-    t2 = ~same
-    if t2.any():
-        assert np.all(dp[t2] <= 10 * tol * (s[t2] + 1.0)), dp[t2].max()
-        assert np.all(dT[t2] <= 10 * tol * o["time"][oi][t2] + 1e-15)
-    return same.mean()
-
-
 def test_small_fan_fp64_matches_oracle(rp):
     cfg = W.small()
     res = _run(rp, cfg["medium"], cfg["params"], cfg["rays"])
     ref, _ = oracle.trace(cfg["medium"], cfg["params"], *cfg["rays"])
     g, o = gpu_rays(res), oracle_rays(ref)
     assert len(g["path"]) == len(ref)
-    frac = _check_fp64(g, o, cfg["params"]["tol"])
+    frac = check_fp64(g, o, cfg["params"]["tol"])
     print("tier-1 fraction", frac)
     # the surface splits: transmitted rays exist and are recorded, not traced
     assert np.any(g["status"] == 5)
@@ -76,7 +55,7 @@ def test_fixed_step_fp64_every_ray_matches(rp):
     prm = dict(cfg["params"], h_min=2.5, h_max=2.5, h0=2.5, tol=1.0)
     res = _run(rp, cfg["medium"], prm, cfg["rays"])
     ref, _ = oracle.trace(cfg["medium"], prm, *cfg["rays"])
-    frac = _check_fp64(gpu_rays(res), oracle_rays(ref), prm["tol"], min_tier1=1.0)
+    frac = check_fp64(gpu_rays(res), oracle_rays(ref), prm["tol"], min_tier1=1.0)
     assert frac == 1.0
 
 
@@ -88,7 +67,7 @@ def test_batched_subset_fp64_rays_and_hits(rp):
     res = _run(rp, cfg["medium"], cfg["params"], rays, receivers=(c, r * 25.0))
     ref, hits = oracle.trace(cfg["medium"], cfg["params"], *rays, receivers=(c, r * 25.0))
     g, o = gpu_rays(res), oracle_rays(ref)
-    _check_fp64(g, o, cfg["params"]["tol"])
+    check_fp64(g, o, cfg["params"]["tol"])
     assert g["generation"].max() >= 2  # secondaries of secondaries went through the queue
     # hits: matched by (ray key, receiver, entry order)
     from parity import tree_keys
@@ -108,16 +87,6 @@ def test_batched_subset_fp64_rays_and_hits(rp):
         assert abs(a[2] - b[2]) <= 10 * cfg["params"]["tol"] * b[2] + 1e-15
 
 
-def _tilt(d, angle, seed):
-    """Rotate every direction by `angle` rad about a random axis perpendicular to it."""
-    rng = np.random.default_rng(seed)
-    d = d / np.linalg.norm(d, axis=0)
-    a = rng.standard_normal(d.shape)
-    a -= (a * d).sum(0) * d
-    a /= np.linalg.norm(a, axis=0)
-    return np.cos(angle) * d + np.sin(angle) * a
-
-
 def test_fp32_mixed_vs_fp64(rp):
     """FP32-mixed against FP64 on 20,000 primaries of the batched workload.
 
@@ -129,7 +98,7 @@ def test_fp32_mixed_vs_fp64(rp):
     pos, d, a = W.subsample(cfg["rays"], np.arange(20000))
     g64 = gpu_rays(_run(rp, cfg["medium"], cfg["params"], (pos, d, a), precision="fp64"))
     g32 = gpu_rays(_run(rp, cfg["medium"], cfg["params"], (pos, d, a), precision="fp32"))
-    gpt = gpu_rays(_run(rp, cfg["medium"], cfg["params"], (pos, _tilt(d, 1e-7, 9), a),
+    gpt = gpu_rays(_run(rp, cfg["medium"], cfg["params"], (pos, tilt(d, 1e-7, 9), a),
                         precision="fp64"))
     gi, oi, only32, only64 = match(g32, g64)
     n = max(len(g32["path"]), len(g64["path"]))
@@ -170,7 +139,7 @@ def test_grid_medium_fp64_and_fp32(rp):
     prm = dict(W.TRACE_DEFAULTS, tol=1e-5, max_path=400.0, max_generation=0)
     ref, _ = oracle.trace(med, prm, *rays)
     g = gpu_rays(_run(rp, med, prm, rays, precision="fp64"))
-    _check_fp64(g, oracle_rays(ref), prm["tol"], min_tier1=0.9)
+    check_fp64(g, oracle_rays(ref), prm["tol"], min_tier1=0.9)
     assert np.any(g["status"] == 4)  # some rays leave the box
     g32 = gpu_rays(_run(rp, med, prm, rays, precision="fp32"))
     gi, oi, a, b = match(g32, g)
@@ -185,7 +154,7 @@ def test_paraxial_form_fp64(rp):
     prm = dict(cfg["params"], rhs_form="paraxial")
     res = _run(rp, cfg["medium"], prm, cfg["rays"])
     ref, _ = oracle.trace(cfg["medium"], prm, *cfg["rays"])
-    _check_fp64(gpu_rays(res), oracle_rays(ref), prm["tol"], min_tier1=0.9)
+    check_fp64(gpu_rays(res), oracle_rays(ref), prm["tol"], min_tier1=0.9)
 
 
 def test_polarizations_and_break_conditions(rp):
@@ -195,7 +164,7 @@ def test_polarizations_and_break_conditions(rp):
         res = _run(rp, cfg["medium"], prm, cfg["rays"])
         ref, _ = oracle.trace(cfg["medium"], prm, *cfg["rays"])
         g = gpu_rays(res)
-        _check_fp64(g, oracle_rays(ref), prm["tol"], min_tier1=0.9)
+        check_fp64(g, oracle_rays(ref), prm["tol"], min_tier1=0.9)
         assert np.any(g["status"] == 2) and np.any(g["status"] == 3)
 
 
