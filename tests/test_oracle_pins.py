@@ -446,3 +446,31 @@ def test_path_finding_reproduces_paper_accuracy(oracle_lib):
             assert abs(s["amp"] - r["amp"]) < 1e-6
             n_checked += 1
     assert n_checked >= 6
+
+
+def test_path_finder_matches_closed_forms_on_workload_pairs(oracle_lib):
+    """64 pairs of the path-finding workload (its own medium, scan sizes and surface
+    reflection) against the closed-form solutions in the Snell invariant: the same solutions
+    (count, type), travel times within 1 ps and launch angles within 1e-6 rad at a 0.1 mm
+    receiver tolerance.  Two closed-form roots inside one scan interval cannot be bracketed
+    by the scan; such roots are left out of the count."""
+    cfg = W.paths(64, seed=4)
+    P = cfg["pairs"]
+    prof = ExpProfile(W.ICE["n0"], W.ICE["dn"], W.ICE["z0"])
+    prm = dict(cfg["params"], tol=1e-8)
+    count, sol = oracle.find_paths(cfg["medium"], prm, P["zs"], P["zr"], P["dist"],
+                                   P["n_angles"], hit_tol=1e-4, max_iter=80)
+    n_sol = 0
+    for i in range(len(count)):
+        ref = solutions(prof, P["zs"][i], P["zr"][i], P["dist"][i], n_above=W.N_AIR)
+        dth = math.pi / (P["n_angles"][i] - 1)
+        cells = [int(r["launch"] // dth) for r in ref]
+        ref = [r for r, c in zip(ref, cells) if cells.count(c) == 1]
+        assert count[i] == len(ref), (i, count[i], len(ref))
+        for j, r in enumerate(ref):
+            s = sol[i, j]
+            assert s["type"] == oracle.SOL_TYPE[r["type"]], (i, j)
+            assert abs(s["time"] - r["time"]) < 1e-12, (i, j)
+            assert abs(s["launch"] - r["launch"]) < 1e-6, (i, j)
+            n_sol += 1
+    assert n_sol >= 60
