@@ -24,6 +24,7 @@ SRC = [os.path.join(HERE, "rp_oracle.c")]
 HDR = os.path.join(HERE, "rp_oracle.h")
 
 MAX_LAYERS = 8
+MAX_SPHERES = 4
 RHS = {"projected": 0, "paraxial": 1}
 POL = {"s": 0, "p": 1, "unpol": 2}
 STATUS = {
@@ -55,6 +56,11 @@ class Medium(C.Structure):
         ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("pad", C.c_int32),
         ("origin", C.c_double * 3), ("spacing", C.c_double),
         ("grid4", C.POINTER(C.c_float)),
+        ("n_spheres", C.c_int32), ("pad2", C.c_int32),
+        ("sph_c", (C.c_double * 3) * MAX_SPHERES), ("sph_R", C.c_double * MAX_SPHERES),
+        ("sph_n0", C.c_double * MAX_SPHERES), ("sph_dn", C.c_double * MAX_SPHERES),
+        ("sph_z0", C.c_double * MAX_SPHERES), ("sph_off", C.c_double * MAX_SPHERES),
+        ("sph_absorb", C.c_int32 * MAX_SPHERES),
     ]
 
 
@@ -145,6 +151,19 @@ class OracleMedium:
                 m.z0[k] = float(L.get("z0", 1.0))
                 m.off[k] = float(L.get("off", 0.0))
                 m.absorb[k] = int(bool(L.get("absorb", False)))
+            spheres = desc.get("spheres", [])
+            if len(spheres) > MAX_SPHERES:
+                raise ValueError("at most %d spheres" % MAX_SPHERES)
+            m.n_spheres = len(spheres)
+            for j, S in enumerate(spheres):
+                for a in range(3):
+                    m.sph_c[j][a] = float(S["center"][a])
+                m.sph_R[j] = float(S["radius"])
+                m.sph_n0[j] = float(S["n0"])
+                m.sph_dn[j] = float(S.get("dn", 0.0))
+                m.sph_z0[j] = float(S.get("z0", 1.0))
+                m.sph_off[j] = float(S.get("off", 0.0))
+                m.sph_absorb[j] = int(bool(S.get("absorb", False)))
             self.grid4 = None
         elif desc["kind"] == "grid":
             n = np.ascontiguousarray(desc["n"], dtype=np.float32)  # (nz, ny, nx)

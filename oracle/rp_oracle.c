@@ -71,17 +71,47 @@ int32_t or_layer_of(const or_medium *m, double z)
     return k;
 }
 
-/* n(z) = n0 - dn exp(-z/z0) + off and dn/dz = (dn/z0) exp(-z/z0)  (Sec. 2, Fig. 1 text). */
+/* Region containing r: inside sphere j -> OR_MAX_LAYERS + j, else the layer of its depth. */
+int32_t or_region_of(const or_medium *m, const double *r)
+{
+    for (int32_t j = 0; j < m->n_spheres; ++j) {
+        double d2 = 0.0;
+        for (int a = 0; a < 3; ++a) d2 += (r[a] - m->sph_c[j][a]) * (r[a] - m->sph_c[j][a]);
+        if (d2 < m->sph_R[j] * m->sph_R[j]) return OR_MAX_LAYERS + j;
+    }
+    return or_layer_of(m, r[2]);
+}
+
+/* n(z) = n0 - dn exp(-z/z0) + off and dn/dz = (dn/z0) exp(-z/z0) of region k (a layer, or
+ * the inside of a sphere)  (Sec. 2, Fig. 1 text). */
 static void layer_eval(const or_medium *m, int32_t k, double z, double *n, double *dndz)
 {
-    if (m->dn[k] == 0.0) {
-        *n = m->n0[k] + m->off[k];
+    double n0, dn, z0, off;
+    if (k >= OR_MAX_LAYERS) {
+        const int32_t j = k - OR_MAX_LAYERS;
+        n0 = m->sph_n0[j];
+        dn = m->sph_dn[j];
+        z0 = m->sph_z0[j];
+        off = m->sph_off[j];
+    } else {
+        n0 = m->n0[k];
+        dn = m->dn[k];
+        z0 = m->z0[k];
+        off = m->off[k];
+    }
+    if (dn == 0.0) {
+        *n = n0 + off;
         *dndz = 0.0;
         return;
     }
-    double e = exp(-z / m->z0[k]);
-    *n = m->n0[k] - m->dn[k] * e + m->off[k];
-    *dndz = m->dn[k] / m->z0[k] * e;
+    double e = exp(-z / z0);
+    *n = n0 - dn * e + off;
+    *dndz = dn / z0 * e;
+}
+
+static int32_t region_absorbs(const or_medium *m, int32_t k)
+{
+    return k >= OR_MAX_LAYERS ? m->sph_absorb[k - OR_MAX_LAYERS] : m->absorb[k];
 }
 
 static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -294,9 +324,19 @@ typedef struct {
     int64_t q_cap, q_len, q_head;
 } trace_ctx;
 
-enum { EV_NONE = 0, EV_TOP = 1, EV_BOTTOM = 2, EV_STOP = 3 };
+/* Event kinds: the planes above and below the ray's layer, the stop plane, and sphere j's
+ * surface (EV_SPHERE + j). */
+enum { EV_NONE = 0, EV_TOP = 1, EV_BOTTOM = 2, EV_STOP = 3, EV_SPHERE = 4 };
 
-/* Signed distance to an event plane, positive on the ray's own side. */
+/* distance of r from sphere j's centre */
+static double sphere_dist(const or_medium *m, int32_t j, const double *y)
+{
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) d2 += (y[a] - m->sph_c[j][a]) * (y[a] - m->sph_c[j][a]);
+    return sqrt(d2);
+}
+
+/* Signed distance to an event surface, positive on the ray's own side. */
 static double event_g(const trace_ctx *c, int32_t layer, int kind, double stop_sign,
                       const double *y)
 {
@@ -304,10 +344,17 @@ static double event_g(const trace_ctx *c, int32_t layer, int kind, double stop_s
     const or_params *p = c->p;
     if (kind == EV_TOP) return y[2] - m->z_top[layer];
     if (kind == EV_BOTTOM) return m->z_top[layer + 1] - y[2];
+    if (kind >= EV_SPHERE) {
+        const int32_t j = kind - EV_SPHERE;
+        const double g = sphere_dist(m, j, y) - m->sph_R[j];
+        return layer == OR_MAX_LAYERS + j ? -g : g;
+    }
     double f = p->stop_n[0] * y[0] + p->stop_n[1] * y[1] + p->stop_n[2] * y[2] - p->stop_d;
     return stop_sign * f;
 }
 
+/* Puts the landing point exactly on the surface: the plane's depth, the stop plane by its
+ * normal, the sphere radially. */
 static void snap_to_plane(const trace_ctx *c, int32_t layer, int kind, double *y)
 {
     const or_params *p = c->p;
@@ -315,6 +362,10 @@ static void snap_to_plane(const trace_ctx *c, int32_t layer, int kind, double *y
         y[2] = c->m->z_top[layer];
     } else if (kind == EV_BOTTOM) {
         y[2] = c->m->z_top[layer + 1];
+    } else if (kind >= EV_SPHERE) {
+        const int32_t j = kind - EV_SPHERE;
+        const double q = c->m->sph_R[j] / sphere_dist(c->m, j, y);
+        for (int a = 0; a < 3; ++a) y[a] = c->m->sph_c[j][a] + q * (y[a] - c->m->sph_c[j][a]);
     } else {
         double f = p->stop_n[0] * y[0] + p->stop_n[1] * y[1] + p->stop_n[2] * y[2] - p->stop_d;
         for (int a = 0; a < 3; ++a) y[a] -= f * p->stop_n[a];
@@ -512,10 +563,14 @@ static void trace_one(trace_ctx *c, const start_state *st)
         /* event detection: earliest crossed plane, by linear fraction along the step */
         int ev = EV_NONE;
         double ev_frac = 2.0, ev_g0 = 0.0, ev_g1 = 0.0;
-        for (int kind = EV_TOP; kind <= EV_STOP; ++kind) {
-            if (kind == EV_TOP && !(layered && layer > 0)) continue;
-            if (kind == EV_BOTTOM && !(layered && layer < m->n_layers - 1)) continue;
+        const int in_sphere = layer >= OR_MAX_LAYERS;
+        for (int kind = EV_TOP; kind < EV_SPHERE + m->n_spheres; ++kind) {
+            if (kind == EV_TOP && !(layered && !in_sphere && layer > 0)) continue;
+            if (kind == EV_BOTTOM && !(layered && !in_sphere && layer < m->n_layers - 1)) continue;
             if (kind == EV_STOP && !p->use_stop) continue;
+            /* a ray inside a sphere meets only that sphere's surface */
+            if (kind >= EV_SPHERE && in_sphere && layer != OR_MAX_LAYERS + kind - EV_SPHERE)
+                continue;
             double g0 = event_g(c, layer, kind, stop_sign, y);
             double g1 = event_g(c, layer, kind, stop_sign, y1);
             /* crossed, or arrived within eps_b of the plane from the ray's own side */
@@ -546,13 +601,24 @@ static void trace_one(trace_ctx *c, const start_state *st)
         ++n_acc;
         h = h_next;
 
-        if (ev == EV_TOP || ev == EV_BOTTOM) {
-            /* split at the plane between `layer` and its neighbour */
-            int32_t other = (ev == EV_TOP) ? layer - 1 : layer + 1;
+        if (ev == EV_TOP || ev == EV_BOTTOM || ev >= EV_SPHERE) {
+            /* split at the plane between `layer` and its neighbour, or at a sphere's surface;
+             * nrm: the unit normal pointing toward the incident side */
+            int32_t other;
+            double nrm[3] = {0.0, 0.0, (ev == EV_TOP) ? 1.0 : -1.0};
+            if (ev >= EV_SPHERE) {
+                const int32_t j = ev - EV_SPHERE;
+                const int inside = layer == OR_MAX_LAYERS + j;
+                const double d = sphere_dist(m, j, y);
+                for (int a = 0; a < 3; ++a)
+                    nrm[a] = (inside ? -1.0 : 1.0) * (y[a] - m->sph_c[j][a]) / d;
+                other = inside ? or_layer_of(m, y[2]) : OR_MAX_LAYERS + j;
+            } else {
+                other = (ev == EV_TOP) ? layer - 1 : layer + 1;
+            }
             double zb = y[2], n1, n2, dd;
             layer_eval(m, layer, zb, &n1, &dd);
             layer_eval(m, other, zb, &n2, &dd);
-            double nrm[3] = {0.0, 0.0, (ev == EV_TOP) ? 1.0 : -1.0};
             double t_refl[3], t_refr[3], rr, tau;
             int32_t tir;
             or_split_dirs(y + 3, nrm, n1, n2, p->polarization, t_refl, t_refr, &rr, &tau, &tir);
@@ -572,8 +638,8 @@ static void trace_one(trace_ctx *c, const start_state *st)
                 sec.id = c->n_out++;
                 sec.parent = st->id;
                 sec.root = st->root;
-                if (m->absorb[other]) {
-                    /* refracted into an absorbing layer: recorded, not traced */
+                if (region_absorbs(m, other)) {
+                    /* refracted into an absorbing region: recorded, not traced */
                     double ys[7] = {y[0], y[1], y[2], t_refr[0], t_refr[1], t_refr[2], y[6]};
                     emit_ray(c, &sec, ys, s, sec.A, other, OR_ST_TRANSMITTED, 0, 0, 0, 0, 0, 0);
                 } else {
@@ -633,7 +699,7 @@ int64_t or_trace(const or_medium *m, const or_params *p, int64_t n, const double
         st.A = amp[i];
         st.A0 = amp[i];
         st.h = p->h0;
-        st.layer = (m->kind == OR_MEDIUM_LAYERED) ? or_layer_of(m, st.r[2]) : 0;
+        st.layer = (m->kind == OR_MEDIUM_LAYERED) ? or_region_of(m, st.r) : 0;
         st.gen = 0;
         st.seq = 0;
         st.id = i;

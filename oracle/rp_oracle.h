@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #define OR_MAX_LAYERS 8
+#define OR_MAX_SPHERES 4
 
 enum { OR_MEDIUM_LAYERED = 0, OR_MEDIUM_GRID = 1 };
 enum { OR_RHS_PROJECTED = 0, OR_RHS_PARAXIAL = 1 };
@@ -33,6 +34,11 @@ enum { OR_SOL_DIRECT = 0, OR_SOL_REFRACTED = 1, OR_SOL_REFLECTED = 2 };
  * inside layer k,  n(z) = n0[k] - dn[k] * exp(-z / z0[k]) + off[k]   (Sec. 2, Fig. 1 text);
  * dn[k] == 0 gives a constant layer.  absorb[k] != 0: rays refracted into layer k are recorded
  * as terminated (status TRANSMITTED) and not traced further.
+ * Curved boundaries (the paragraph after Fig. 1): up to OR_MAX_SPHERES spheres in a layered
+ * medium, sphere j of centre sph_c[j] and radius sph_R[j], with its own index formula inside,
+ * n = sph_n0 - sph_dn exp(-z / sph_z0) + sph_off, and sph_absorb as for layers.  A sphere lies
+ * inside one layer and spheres do not overlap.  Regions: a ray in layer k outside every sphere
+ * is in region k, a ray inside sphere j in region OR_MAX_LAYERS + j.
  * GRID: node samples (n, dn/dx, dn/dy, dn/dz) as float4, x fastest, node (i,j,k) at
  * origin + spacing*(i,j,k); trilinear interpolation of all four channels.  No boundaries. */
 typedef struct {
@@ -43,6 +49,10 @@ typedef struct {
     int32_t nx, ny, nz, pad;
     double origin[3], spacing;
     const float *grid4;
+    int32_t n_spheres, pad2;
+    double sph_c[OR_MAX_SPHERES][3], sph_R[OR_MAX_SPHERES], sph_n0[OR_MAX_SPHERES],
+           sph_dn[OR_MAX_SPHERES], sph_z0[OR_MAX_SPHERES], sph_off[OR_MAX_SPHERES];
+    int32_t sph_absorb[OR_MAX_SPHERES];
 } or_medium;
 
 /* Integration and termination parameters. */
@@ -58,7 +68,7 @@ typedef struct {
     int64_t max_steps; /* cap on attempted Cash-Karp steps per ray */
 } or_params;
 
-/* One finished ray (primary or secondary). */
+/* One finished ray (primary or secondary); `layer` is the ray's region (see or_medium). */
 typedef struct {
     int64_t parent, root;      /* parent ray index (-1 for primaries), root primary index */
     int32_t seq, gen, status, layer;  /* seq: index of the split on the parent that made it */
@@ -96,12 +106,15 @@ extern const double or_ck_b4[6];
 void or_ck_poly_step(const double *coef, int32_t n_coef, double x0, double y0, double h,
                      double *y5, double *y4);
 
-/* n and grad n of the medium at r for a ray in `layer` (layered: that layer's formula,
- * continued smoothly beyond its planes; grid: trilinear, clamped to the box). */
+/* n and grad n of the medium at r for a ray in region `layer` (layered: that region's
+ * formula, continued smoothly beyond its boundaries; grid: trilinear, clamped to the box). */
 void or_medium_eval(const or_medium *m, int32_t layer, const double *r, double *n, double *g);
 
 /* Layer index containing depth z. */
 int32_t or_layer_of(const or_medium *m, double z);
+
+/* Region containing r: OR_MAX_LAYERS + j inside sphere j, else the layer of r[2]. */
+int32_t or_region_of(const or_medium *m, const double *r);
 
 /* FP32 node samples (n, grad n) from FP32 node values of n: central differences inside,
  * one-sided differences on the faces, evaluated in double and rounded to float. */

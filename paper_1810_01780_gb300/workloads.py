@@ -13,6 +13,7 @@ workloads:
                 4,194,304 isotropic rays from 16 sources
   ``paths``     65,536 source-receiver pairs with 32..512 scan angles each
   ``surrogate`` 4,194,304 training pairs and 1,048,576 query pairs of the ``paths`` distribution
+  ``spheres``   curved boundaries: two spherical inclusions in the ice, 1,048,576 rays
   ``fig1``      the paper's Fig. 1 example (firn layer over exponential ice, 5 us, A/A0 cut) as
                 a fan of 1,048,576 rays
 
@@ -64,6 +65,20 @@ def firn_over_ice(n_firn: float = 1.5, z_firn: float = 10.0, z0: float = 71.4,
         dict(z_top=0.0, n0=n_firn, dn=0.0, z0=1.0, off=0.0, absorb=False),
         dict(z_top=z_firn, n0=ICE["n0"], dn=ICE["dn"], z0=z0, off=0.0, absorb=False),
     ]}
+
+
+def ice_with_inclusions(n_air: float = N_AIR) -> dict:
+    """Curved boundaries: the surface-bounded exponential ice with two spherical inclusions -- a
+    lens of denser ice (the profile + 0.05) of radius 40 m centred at 300 m depth, and an air
+    pocket (n = 1.0, traced) of radius 25 m at (150, 0, 500) m."""
+    m = ice_with_surface(n_air=n_air)
+    m["spheres"] = [
+        dict(center=(0.0, 0.0, 300.0), radius=40.0, n0=ICE["n0"], dn=ICE["dn"], z0=ICE["z0"],
+             off=0.05, absorb=False),
+        dict(center=(150.0, 0.0, 500.0), radius=25.0, n0=1.0, dn=0.0, z0=1.0, off=0.0,
+             absorb=False),
+    ]
+    return m
 
 
 def gaussian_random_field(shape, spacing, sigma, corr_len, seed) -> np.ndarray:
@@ -220,6 +235,19 @@ def fig1(n=1_048_576):
                 params=dict(TRACE_DEFAULTS, max_path=3000.0, max_time=5e-6, min_amp=0.05,
                             max_generation=8),
                 rays=fan_xz(n, 240.0), receivers=None)
+
+
+def spheres(n=1_048_576, seed=7):
+    """Rays from sources around the two inclusions of ``ice_with_inclusions``: x uniform in
+    -60..210 m, y in +-60 m, depth in 250..550 m, directions uniform on the sphere;
+    generations <= 3, 2 km paths, the amplitude cut A/A0 < 0.05."""
+    rng = np.random.default_rng(seed)
+    pos = np.stack([rng.uniform(-60.0, 210.0, n), rng.uniform(-60.0, 60.0, n),
+                    rng.uniform(250.0, 550.0, n)])
+    return dict(name="spheres", medium=ice_with_inclusions(),
+                params=dict(TRACE_DEFAULTS, max_path=2000.0, min_amp=0.05, max_generation=3,
+                            max_steps=1000),
+                rays=(pos, isotropic_dirs(rng, n), np.ones(n)), receivers=None)
 
 
 def surrogate(n_train=4_194_304, n_query=1_048_576, seed=5):

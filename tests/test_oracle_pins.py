@@ -474,3 +474,86 @@ def test_path_finder_matches_closed_forms_on_workload_pairs(oracle_lib):
             assert abs(s["launch"] - r["launch"]) < 1e-6, (i, j)
             n_sol += 1
     assert n_sol >= 60
+
+
+def _sphere_medium(n_out, n_in, ctr, R, absorb=False):
+    return {"kind": "layered", "layers": [dict(n0=n_out)],
+            "spheres": [dict(center=ctr, radius=R, n0=n_in, absorb=absorb)]}
+
+
+def test_sphere_entry_reflection_refraction_exact(oracle_lib):
+    """Straight rays (constant indices) meeting a sphere of higher index: the entry point, the
+    reflected primary, the refracted secondary and both amplitudes are exact geometry with the
+    local normal (curved boundaries, the paragraph after Fig. 1)."""
+    n_out, n_in, R = 1.3, 1.8, 50.0
+    ctr = np.array([0.0, 0.0, 500.0])
+    med = _sphere_medium(n_out, n_in, ctr, R)
+    b = np.array([0.0, 10.0, -25.0, 40.0, 49.0])  # impact parameters in the x-z plane
+    n = len(b)
+    pos = np.zeros((3, n))
+    pos[0] = -200.0
+    pos[2] = ctr[2] + b
+    d = np.tile(np.array([[1.0], [0.0], [0.0]]), (1, n))
+    S = 200.0  # every ray reaches the sphere; no refracted ray reaches the far side
+    prm = dict(W.TRACE_DEFAULTS, tol=1e-9, max_path=S, max_generation=1)
+    rays, _ = oracle.trace(med, prm, pos, d)
+    for i in range(n):
+        xe = -math.sqrt(R * R - b[i] ** 2)
+        entry = np.array([xe, 0.0, ctr[2] + b[i]])
+        s1 = xe + 200.0
+        N = (entry - ctr) / R  # outward normal; the ray comes from outside
+        t = np.array([1.0, 0.0, 0.0])
+        ci = -t @ N
+        t_r = t + 2 * ci * N
+        st = (n_out / n_in) ** 2 * (1 - ci * ci)
+        ct = math.sqrt(1 - st)
+        eta = n_out / n_in
+        t_t = eta * t + (eta * ci - ct) * N
+        rs = (n_out * ci - n_in * ct) / (n_out * ci + n_in * ct)
+        ts = 2 * n_out * ci / (n_out * ci + n_in * ct)
+        prim = rays[i]
+        assert prim["n_refl"] == 1 and prim["layer"] == 0
+        assert np.allclose(prim["pos"], entry + (S - s1) * t_r, atol=1e-7), i
+        # landing within eps_b (1e-9 m) of the surface moves the local normal by ~1e-11 rad
+        assert abs(prim["amp"] - rs) < 1e-9
+        assert abs(prim["time"] - (n_out * S) / C0) < 1e-15
+        sec = rays[rays["parent"] == i]
+        assert len(sec) == 1
+        s = sec[0]
+        assert s["gen"] == 1 and s["layer"] == oracle.MAX_LAYERS  # inside sphere 0
+        assert abs(s["amp"] - ts) < 1e-9
+        assert np.allclose(s["pos"], entry + (S - s1) * t_t, atol=1e-7), i
+        assert abs(s["time"] - (n_out * s1 + n_in * (S - s1)) / C0) < 1e-15
+        assert np.linalg.norm(s["pos"] - ctr) < R
+
+
+def test_sphere_total_internal_reflection_and_exit(oracle_lib):
+    """A ray inside a sphere of higher index: beyond the critical angle it reflects totally
+    (amplitude kept, nothing transmitted); at normal incidence it leaves through the surface
+    into an absorbing outside only as a transmitted record."""
+    n_out, n_in, R = 1.3, 1.8, 50.0
+    ctr = np.array([0.0, 0.0, 500.0])
+    med = _sphere_medium(n_out, n_in, ctr, R)
+    a = 0.8 * R  # sin(incidence) = 0.8 > n_out / n_in = 0.722
+    pos = np.array([[0.0], [0.0], [ctr[2] + a]])
+    d = np.array([[1.0], [0.0], [0.0]])
+    x_hit = math.sqrt(R * R - a * a)
+    prm = dict(W.TRACE_DEFAULTS, tol=1e-9, max_path=x_hit + 40.0, max_generation=3)
+    rays, _ = oracle.trace(med, prm, pos, d)
+    assert len(rays) == 1
+    r = rays[0]
+    hit = np.array([x_hit, 0.0, ctr[2] + a])
+    N = (hit - ctr) / R
+    t_r = d[:, 0] - 2 * (d[:, 0] @ N) * N
+    assert r["n_refl"] == 1 and abs(r["amp"] - 1.0) < 1e-15
+    assert np.allclose(r["pos"], hit + 40.0 * t_r, atol=1e-7)
+    assert r["layer"] == oracle.MAX_LAYERS
+    # from the centre outward: normal incidence into the layer outside
+    med2 = {"kind": "layered", "layers": [dict(n0=n_out, absorb=True)],
+            "spheres": [dict(center=ctr, radius=R, n0=n_in)]}
+    rays, _ = oracle.trace(med2, dict(prm, max_path=120.0), ctr.reshape(3, 1), d)
+    sec = rays[rays["parent"] == 0]
+    assert len(sec) == 1 and sec[0]["status"] == oracle.STATUS["TRANSMITTED"]
+    assert np.allclose(sec[0]["pos"], ctr + R * d[:, 0], atol=1e-8)
+    assert abs(sec[0]["amp"] - 2 * n_in / (n_in + n_out)) < 1e-12
+    assert abs(rays[0]["amp"] - (n_in - n_out) / (n_in + n_out)) < 1e-12
