@@ -321,6 +321,36 @@ def reduce_over_ranks(total_ms, counts, device):
     return float(t[0]), [float(v) for v in c]
 
 
+def fp32_fp64_leg(rp, cfg, flush, steps, workload):
+    """One trace workload in both precisions: ray-steps/s and rays/s (kernel time, L2 flushed
+    before each call) and the FP32-mixed end points of the primaries against FP64."""
+    med = rp.Medium(cfg["medium"])
+    rays = rp.PreparedRays(*cfg["rays"])
+    buf = rp.TraceBuffers(3 * rays.n, 0, fields=("end_pos", "path", "time", "status"))
+    leg, ends = {"workload": workload}, {}
+    for prec in ("fp32", "fp64"):
+        prm = rp.make_params(cfg["params"], prec)
+        rp.trace_into(med, rays, prm, buf)  # warm-up
+        ts, acc, nr = [], 0, 0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            st = rp.trace_into(med, rays, prm, buf)
+            ts.append(st.kernel_ms)
+            acc += st.steps_accepted
+            nr += st.rays
+        sec = sum(ts) / 1e3
+        leg["fp32_mixed" if prec == "fp32" else "fp64"] = {
+            "ray_steps_per_s": acc / sec, "rays_per_s": nr / sec, "ms_per_step": 1e3 * sec / len(ts)}
+        ends[prec] = (buf.t["end_pos"][:, :rays.n].clone(), buf.t["time"][:rays.n].clone())
+    dpos = (ends["fp32"][0] - ends["fp64"][0]).norm(dim=0)
+    dt = (ends["fp32"][1] - ends["fp64"][1]).abs()
+    leg["error_fp32_vs_fp64"] = {
+        "primaries": rays.n, "pos_m_p99": float(dpos.double().quantile(0.99)),
+        "time_s_p99": float(dt.double().quantile(0.99)),
+        "within_1mm_10ps": float(((dpos <= 1e-3) & (dt <= 1e-11)).double().mean())}
+    return leg
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -473,36 +503,17 @@ def run_gpu(args):
 
     # the paper's Fig. 1 example as a 1,048,576-ray fan: firn layer over ice, 5 us, A/A0 cut
     if not args.no_fig1:
-        fcfg = W.fig1()
-        fmed = rp.Medium(fcfg["medium"])
-        frays = rp.PreparedRays(*fcfg["rays"])
-        fbuf = rp.TraceBuffers(3 * frays.n, 0, fields=("end_pos", "path", "time", "status"))
-        leg, ends = {"workload": "Fig. 1 example: 1,048,576 rays from 240 m in the x-z plane, "
-                                 "10 m of n = 1.5 over exponential ice (z0 = 71.4 m), 5 us, "
-                                 "A/A0 < 0.05 discarded, generations <= 8"}, {}
-        for prec in ("fp32", "fp64"):
-            fprm = rp.make_params(fcfg["params"], prec)
-            rp.trace_into(fmed, frays, fprm, fbuf)  # warm-up
-            ft, facc, fr = [], 0, 0
-            for _ in range(args.grid_steps):
-                flush.fill_(1.0)
-                st = rp.trace_into(fmed, frays, fprm, fbuf)
-                ft.append(st.kernel_ms)
-                facc += st.steps_accepted
-                fr += st.rays
-            fsec = sum(ft) / 1e3
-            key = "fp32_mixed" if prec == "fp32" else "fp64"
-            leg[key] = {"ray_steps_per_s": facc / fsec, "rays_per_s": fr / fsec,
-                        "ms_per_step": 1e3 * fsec / len(ft)}
-            ends[prec] = (fbuf.t["end_pos"][:, :frays.n].clone(), fbuf.t["time"][:frays.n].clone())
-        fd = (ends["fp32"][0] - ends["fp64"][0]).norm(dim=0)
-        fT = (ends["fp32"][1] - ends["fp64"][1]).abs()
-        leg["error_fp32_vs_fp64"] = {
-            "primaries": frays.n, "pos_m_p99": float(fd.double().quantile(0.99)),
-            "time_s_p99": float(fT.double().quantile(0.99)),
-            "within_1mm_10ps": float(((fd <= 1e-3) & (fT <= 1e-11)).double().mean())}
-        modes["fig1"] = leg
-        del fmed, frays, fbuf, ends
+        modes["fig1"] = fp32_fp64_leg(
+            rp, W.fig1(), flush, args.grid_steps,
+            "Fig. 1 example: 1,048,576 rays from 240 m in the x-z plane, 10 m of n = 1.5 over "
+            "exponential ice (z0 = 71.4 m), 5 us, A/A0 < 0.05 discarded, generations <= 8")
+    # curved boundaries: two spherical inclusions in the ice, 1,048,576 isotropic rays
+    if not args.no_spheres:
+        modes["spheres"] = fp32_fp64_leg(
+            rp, W.spheres(), flush, args.grid_steps,
+            "spherical inclusions: 1,048,576 isotropic rays around a denser-ice lens (R 40 m) "
+            "and an air pocket (R 25 m) in the surface-bounded ice, 2 km, A/A0 < 0.05, "
+            "generations <= 3")
 
     # source-receiver path finding: 65,536 pairs, 32..512 scan angles each, FP64 bisection
     if not args.no_paths:
@@ -587,6 +598,7 @@ def main():
                     help="primaries of the batched workload (the bench workload is 1,048,576)")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-fig1", action="store_true")
+    ap.add_argument("--no-spheres", action="store_true")
     ap.add_argument("--sur-train", type=int, default=4_194_304)
     ap.add_argument("--sur-queries", type=int, default=1_048_576)
     ap.add_argument("--sur-check", type=int, default=16_384)

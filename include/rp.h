@@ -42,6 +42,7 @@ extern "C" {
 #define RP_ERR_UNSUPPORTED (-5)  /* valid request this build does not provide */
 
 #define RP_MAX_LAYERS 8
+#define RP_MAX_SPHERES 4
 #define RP_MAX_WAVES 16 /* max_generation + 1 launches at most */
 
 enum { RP_MEDIUM_LAYERED = 0, RP_MEDIUM_GRID = 1 };
@@ -76,7 +77,18 @@ typedef struct {
     int32_t absorb, pad;
 } rp_layer;
 
-/* kind = RP_MEDIUM_LAYERED: n_layers (1..8) layers, ordered top to bottom, z_top increasing.
+/* Spherical boundary inside a layered medium (curved boundaries, the paragraph after Fig. 1):
+ * centre and radius [m]; inside it n(z) = n0 - dn * exp(-z / z0) + offset (dn = 0: constant);
+ * absorb as for layers.  A ray inside sphere j is reported in region RP_MAX_LAYERS + j (the
+ * `layer` output); outside every sphere its region is its layer.  The boundary split at the
+ * sphere uses the local normal (r - centre) / radius. */
+typedef struct {
+    double center[3], radius, n0, dn, z0, offset;
+    int32_t absorb, pad;
+} rp_sphere;
+
+/* kind = RP_MEDIUM_LAYERED: n_layers (1..8) layers, ordered top to bottom, z_top increasing,
+ *   and n_spheres (0..4) spheres, each strictly inside one layer, none overlapping another.
  * kind = RP_MEDIUM_GRID: node values of n on an nx * ny * nz grid (x fastest), node (i,j,k)
  *   at origin + spacing * (i,j,k); `grid_n` may be a host or a device pointer and is copied.
  *   The library derives grad n by central differences (one-sided on the faces) and stores
@@ -90,6 +102,8 @@ typedef struct {
     double origin[3];
     double spacing;
     const float *grid_n;
+    int32_t n_spheres, pad2;
+    rp_sphere spheres[RP_MAX_SPHERES];
 } rp_medium_desc;
 
 typedef struct rp_medium_s *rp_medium_t;
@@ -98,7 +112,8 @@ typedef struct rp_medium_s *rp_medium_t;
  * the current device and returns an opaque handle in *out.  The handle owns its device
  * memory until rp_medium_destroy.  Errors: RP_ERR_INVALID_ARG (null pointer, bad layer count,
  * z_top not increasing, z0 <= 0 with dn != 0, grid smaller than 2 nodes per axis,
- * spacing <= 0), RP_ERR_OOM, RP_ERR_CUDA. */
+ * spacing <= 0, a sphere of radius <= 0, crossing a layer plane or overlapping another),
+ * RP_ERR_OOM, RP_ERR_CUDA. */
 int rp_medium_create(const rp_medium_desc *desc, void *stream, rp_medium_t *out);
 
 /* Releases the handle and its device memory.  NULL is accepted. */
@@ -250,8 +265,8 @@ typedef struct {
  * adjacent angles whose vertical misses change sign are refined by FP64 bisection on the
  * launch angle until |miss| < hit_tol.  A ray that exhausts its path budget before x = D
  * scores +inf (it is far below).  D < hit_tol: the vertical ray to the receiver depth.
- * Solution type: REFLECTED if the ray reflected off a boundary, REFRACTED if it turned
- * (t_z changed sign), else DIRECT.  Returns RP_OK, RP_ERR_INVALID_ARG, RP_ERR_OOM,
+ * Layered media without spheres only.  Solution type: REFLECTED if the ray reflected off a
+ * boundary, REFRACTED if it turned (t_z changed sign), else DIRECT.  Returns RP_OK, RP_ERR_INVALID_ARG, RP_ERR_OOM,
  * RP_ERR_CUDA. */
 int rp_find_paths(rp_medium_t m, int64_t n_pairs, const double *z_s, const double *z_r,
                   const double *dist, const int32_t *n_angles, const rp_path_params *p,

@@ -18,6 +18,7 @@ ERRORS = {-1: "RP_ERR_INVALID_ARG", -2: "RP_ERR_CUDA", -3: "RP_ERR_OOM", -4: "RP
           -5: "RP_ERR_UNSUPPORTED"}
 RP_ERR_OVERFLOW = -4
 MAX_LAYERS = 8
+MAX_SPHERES = 4
 MEDIUM_KIND = {"layered": 0, "grid": 1}
 PRECISION = {"fp64": 0, "fp32": 1}
 POLARIZATION = {"s": 0, "p": 1, "unpol": 2}
@@ -39,11 +40,18 @@ class Layer(C.Structure):
                 ("pad", C.c_int32)]
 
 
+class Sphere(C.Structure):
+    _fields_ = [("center", C.c_double * 3), ("radius", C.c_double), ("n0", C.c_double),
+                ("dn", C.c_double), ("z0", C.c_double), ("offset", C.c_double),
+                ("absorb", C.c_int32), ("pad", C.c_int32)]
+
+
 class MediumDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_layers", C.c_int32), ("layers", Layer * MAX_LAYERS),
                 ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("pad", C.c_int32),
                 ("origin", C.c_double * 3), ("spacing", C.c_double),
-                ("grid_n", C.c_void_p)]
+                ("grid_n", C.c_void_p), ("n_spheres", C.c_int32), ("pad2", C.c_int32),
+                ("spheres", Sphere * MAX_SPHERES)]
 
 
 class Rays(C.Structure):

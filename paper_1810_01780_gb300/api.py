@@ -53,6 +53,19 @@ class Medium:
                 d.layers[k].z0 = float(L.get("z0", 1.0))
                 d.layers[k].offset = float(L.get("off", 0.0))
                 d.layers[k].absorb = int(bool(L.get("absorb", False)))
+            spheres = desc.get("spheres", [])
+            if len(spheres) > A.MAX_SPHERES:
+                raise ValueError("at most %d spheres" % A.MAX_SPHERES)
+            d.n_spheres = len(spheres)
+            for j, S in enumerate(spheres):
+                for a in range(3):
+                    d.spheres[j].center[a] = float(S["center"][a])
+                d.spheres[j].radius = float(S["radius"])
+                d.spheres[j].n0 = float(S["n0"])
+                d.spheres[j].dn = float(S.get("dn", 0.0))
+                d.spheres[j].z0 = float(S.get("z0", 1.0))
+                d.spheres[j].offset = float(S.get("off", 0.0))
+                d.spheres[j].absorb = int(bool(S.get("absorb", False)))
         elif desc["kind"] == "grid":
             n = desc["n"]
             if isinstance(n, torch.Tensor):

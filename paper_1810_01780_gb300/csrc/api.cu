@@ -189,6 +189,58 @@ int rp_medium_create(const rp_medium_desc *d, void *stream, rp_medium_t *out)
             m->layered.eta_down[k] = m->layered.n_above[k] / m->layered.n_below[k];
             m->layered.eta_up[k] = m->layered.n_below[k] / m->layered.n_above[k];
         }
+        // spheres: each strictly inside one layer, none overlapping another
+        if (d->n_spheres < 0 || d->n_spheres > RP_MAX_SPHERES) {
+            delete m;
+            set_error("rp_medium_create: n_spheres must be 0..%d", RP_MAX_SPHERES);
+            return RP_ERR_INVALID_ARG;
+        }
+        m->layered.n_sph = d->n_spheres;
+        for (int j = 0; j < d->n_spheres; ++j) {
+            const rp_sphere &S = d->spheres[j];
+            bool ok = S.radius > 0.0 && std::isfinite(S.radius) && (S.n0 + S.offset > 0.0) &&
+                      (S.dn == 0.0 || S.z0 > 0.0);
+            for (int a = 0; a < 3; ++a) ok = ok && std::isfinite(S.center[a]);
+            for (int k = 1; ok && k < d->n_layers; ++k)  // no plane cuts the sphere
+                ok = fabs(S.center[2] - d->layers[k].z_top) > S.radius;
+            for (int i = 0; ok && i < j; ++i) {
+                const rp_sphere &T = d->spheres[i];
+                double d2 = 0.0;
+                for (int a = 0; a < 3; ++a)
+                    d2 += (S.center[a] - T.center[a]) * (S.center[a] - T.center[a]);
+                ok = sqrt(d2) > S.radius + T.radius;
+            }
+            if (!ok) {
+                delete m;
+                set_error("rp_medium_create: sphere %d: needs radius > 0, a positive index, z0 > "
+                          "0 with dn != 0, no layer plane through it and no overlap", j);
+                return RP_ERR_INVALID_ARG;
+            }
+            rpk::LayerC &c = m->layered.L[RP_MAX_LAYERS + j];
+            c.n0 = S.n0;
+            c.dn = S.dn;
+            c.off = S.offset;
+            c.has_exp = S.dn != 0.0;
+            c.inv_z0 = c.has_exp ? 1.0 / S.z0 : 0.0;
+            c.gcoef = c.has_exp ? S.dn / S.z0 : 0.0;
+            c.n0f = (float)c.n0;
+            c.dnf = (float)c.dn;
+            c.offf = (float)c.off;
+            c.inv_z0f = (float)c.inv_z0;
+            c.gcoeff = (float)c.gcoef;
+            c.absorb = S.absorb != 0;
+            rpk::SphereB &B = m->layered.S[j];
+            for (int a = 0; a < 3; ++a) {
+                B.c[a] = S.center[a];
+                B.cc[a] = plane_const(S.center[a]);
+            }
+            B.R = S.radius;
+            const double R2 = S.radius * S.radius;
+            B.R2h = (float)R2;
+            B.R2l = (float)(R2 - (double)B.R2h);
+            B.Rf = (float)S.radius;
+            B.pad = 0.0f;
+        }
     } else if (d->kind == RP_MEDIUM_GRID) {
         if (d->nx < 2 || d->ny < 2 || d->nz < 2 || !(d->spacing > 0.0) || !d->grid_n) {
             delete m;

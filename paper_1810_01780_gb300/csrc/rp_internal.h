@@ -31,7 +31,7 @@ struct rp_surrogate_s {
 struct rp_medium_s {
     int device;
     int kind;
-    rpk::MediumLayered layered;
+    rpk::MediumSpheres layered;  // n_sph = 0: a plain layered medium
     rpk::MediumGrid grid;
     float4 *grid_dev;
 };

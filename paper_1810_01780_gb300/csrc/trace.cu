@@ -157,10 +157,14 @@ __device__ int next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, const
             L.T.hi = L.T.lo = 0.0f;
             L.s.hi = L.s.lo = 0.0f;
             L.h = in.h0f;
-            if constexpr (is_layered_v<M>)
+            if constexpr (has_spheres_v<M>) {
+                const double r0[3] = {in.pos[k], in.pos[n + k], in.pos[2 * n + k]};
+                L.layer = region_of(med, r0);
+            } else if constexpr (is_layered_v<M>) {
                 L.layer = layer_of_ff(med, L.r.hi[2], L.r.lo[2]);
-            else
+            } else {
                 L.layer = 0;
+            }
             const float q2 = L.t.hi[0] * L.t.hi[0] + L.t.hi[1] * L.t.hi[1] + L.t.hi[2] * L.t.hi[2];
             const bool pos_ok = isfinite(L.r.hi[0]) && isfinite(L.r.hi[1]) && isfinite(L.r.hi[2]);
             if (!(q2 > 0.0f) || !isfinite(q2) || !pos_ok) {
@@ -188,7 +192,9 @@ __device__ int next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, const
             P::sset(L.T, 0.0);
             P::sset(L.s, 0.0);
             L.h = P::from_d(in.h0);
-            if constexpr (is_layered_v<M>)
+            if constexpr (has_spheres_v<M>)
+                L.layer = region_of(med, r);
+            else if constexpr (is_layered_v<M>)
                 L.layer = layer_of(med, r[2]);
             else
                 L.layer = 0;
@@ -311,10 +317,13 @@ static int occupancy_grid(int block)
     return cached_occ;
 }
 
-static int trace_threads(int kind, int precision, int device, int block)
+static int trace_threads(int kind, bool spheres, int precision, int device, int block)
 {
     int occ;
-    if (kind == RP_MEDIUM_LAYERED)
+    if (kind == RP_MEDIUM_LAYERED && spheres)
+        occ = precision == RP_FP64 ? occupancy_grid<PrecF64, MediumSpheres>(block)
+                                   : occupancy_grid<PrecF32, MediumSpheres>(block);
+    else if (kind == RP_MEDIUM_LAYERED)
         occ = precision == RP_FP64 ? occupancy_grid<PrecF64, MediumLayered>(block)
                                    : occupancy_grid<PrecF32, MediumLayered>(block);
     else
@@ -472,7 +481,8 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     }
 
     const int block = 128;
-    const int threads = trace_threads(m->kind, p->precision, dev, block);
+    const int threads = trace_threads(m->kind, m->kind == RP_MEDIUM_LAYERED && m->layered.n_sph > 0,
+                                      p->precision, dev, block);
     if (threads < 0) return threads;
     // scratch layout: control block, receivers, per-thread stacks, warp clocks, queue last
     long long q_cap = out->capacity - in->n;
@@ -557,7 +567,16 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     cudaEvent_t ev[RP_MAX_WAVES + 1];
     for (int w = 0; w <= n_waves; ++w) RP_CUDA_TRY(cudaEventCreate(&ev[w]));
     RP_CUDA_TRY(cudaEventRecord(ev[0], st));
-    if (m->kind == RP_MEDIUM_LAYERED) {
+    if (m->kind == RP_MEDIUM_LAYERED && m->layered.n_sph > 0) {
+        if (p->precision == RP_FP64)
+            rc = launch_waves<PrecF64, MediumSpheres>(m->layered,
+                                                      step_params<PrecF64>(p, axis, sdir),
+                                                      sk, wi, n_waves, dev, block, st, ev);
+        else
+            rc = launch_waves<PrecF32, MediumSpheres>(m->layered,
+                                                      step_params<PrecF32>(p, axis, sdir),
+                                                      sk, wi, n_waves, dev, block, st, ev);
+    } else if (m->kind == RP_MEDIUM_LAYERED) {
         if (p->precision == RP_FP64)
             rc = launch_waves<PrecF64, MediumLayered>(m->layered,
                                                       step_params<PrecF64>(p, axis, sdir),

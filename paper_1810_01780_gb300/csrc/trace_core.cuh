@@ -222,9 +222,13 @@ struct LayerC {
     int32_t absorb, has_exp;
 };
 
+// Regions of a layered medium: layer k (k < RP_MAX_LAYERS) outside every sphere, or the inside
+// of sphere j, region RP_MAX_LAYERS + j; L[region] holds the region's index formula.
+constexpr int kRegions = RP_MAX_LAYERS + RP_MAX_SPHERES;
+
 struct MediumLayered {
     int32_t n_layers, pad;
-    LayerC L[RP_MAX_LAYERS];
+    LayerC L[kRegions];
     PlaneC top[RP_MAX_LAYERS];  // top[k]: plane z = z_top of layer k (k >= 1)
     // index just above / below plane k (layer k-1 / layer k evaluated at z_top[k])
     double n_above[RP_MAX_LAYERS], n_below[RP_MAX_LAYERS];
@@ -241,8 +245,24 @@ struct MediumGrid {
     PlaneC lo_c[3], hi_c[3];  // box faces
 };
 
+// Spherical boundary (curved boundaries, the paragraph after Fig. 1): centre, radius, and the
+// same as float-float constants for the FP32 path.
+struct SphereB {
+    double c[3], R;
+    PlaneC cc[3];
+    float R2h, R2l, Rf, pad;
+};
+
+// A layered medium with spherical inclusions, each inside one layer, none overlapping.
+struct MediumSpheres : MediumLayered {
+    int32_t n_sph, pad2;
+    SphereB S[RP_MAX_SPHERES];
+};
+
 template <class M>
-constexpr bool is_layered_v = std::is_same<M, MediumLayered>::value;
+constexpr bool is_layered_v = std::is_base_of<MediumLayered, M>::value;
+template <class M>
+constexpr bool has_spheres_v = std::is_same<M, MediumSpheres>::value;
 
 __device__ __forceinline__ int layer_of(const MediumLayered &m, double z)
 {
@@ -259,6 +279,19 @@ __device__ __forceinline__ int layer_of_ff(const MediumLayered &m, float hi, flo
     for (int j = 1; j < m.n_layers; ++j)
         if (__fadd_rn(__fsub_rn(hi, m.top[j].hi), __fsub_rn(lo, m.top[j].lo)) >= 0.0f) k = j;
     return k;
+}
+
+// Region containing r (FP64; once per ray): inside sphere j, else the layer of the depth.
+__device__ __forceinline__ int region_of(const MediumSpheres &m, const double r[3])
+{
+    for (int j = 0; j < m.n_sph; ++j) {
+        const SphereB &S = m.S[j];
+        double d2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) d2 = __dadd_rn(d2, __dmul_rn(r[a] - S.c[a], r[a] - S.c[a]));
+        if (d2 < __dmul_rn(S.R, S.R)) return RP_MAX_LAYERS + j;
+    }
+    return layer_of(m, r[2]);
 }
 
 // n(z) and dn/dz of layer k in FP64 (used by the boundary split in both policies).
@@ -311,7 +344,8 @@ __device__ __forceinline__ void load_layer(LayerR<P> &c, const MediumLayered &m,
     none_bot.d = 1e30;
     none_bot.hi = 1e30f;
     none_bot.lo = 0.0f;
-    c.top = k > 0 ? m.top[k] : none_top;
+    // a sphere's inside (k >= RP_MAX_LAYERS) has no planes: the ray meets its sphere first
+    c.top = (k > 0 && k < RP_MAX_LAYERS) ? m.top[k] : none_top;
     c.bot = k + 1 < m.n_layers ? m.top[k + 1] : none_bot;
 }
 template <class P>
@@ -587,7 +621,7 @@ struct QRec {
 // Lane state
 // ---------------------------------------------------------------------------------------
 enum { MODE_NORMAL = 0, MODE_PROBE = 1, MODE_ILLINOIS = 2 };
-enum { EV_NONE = 0, EV_TOP = 1, EV_BOTTOM = 2, EV_STOP = 3 };
+enum { EV_NONE = 0, EV_TOP = 1, EV_BOTTOM = 2, EV_STOP = 3, EV_SPH = 4 };  // EV_SPH + j: sphere j
 
 template <class P>
 struct Lane {
@@ -682,6 +716,58 @@ __device__ __forceinline__ typename P::R event_g(const MediumGrid &, const Lane<
                                                  const typename P::R dr[3])
 {
     return L.stop_sign * stop_rel(L, sp, dr);
+}
+
+// Distance |r + dr - c| - R of a candidate point from sphere S's surface.  FP64: the operations
+// of the FP64 reference, unfused.  FP32-mixed: |w|^2 accumulated in float-float from the
+// float-float position (w = r - c + dr with the rounding of r.hi - c.hi kept), then
+// (|w|^2 - R^2) / (|w| + R), accurate to a few ulps of the distance itself.
+template <class P>
+__device__ __forceinline__ typename P::R sphere_dist(const typename P::V &r,
+                                                     const typename P::R dr[3], const SphereB &S)
+{
+    if constexpr (!P::kFF) {
+        double d2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double w = __dsub_rn(__dadd_rn(r.v[a], dr[a]), S.c[a]);
+            d2 = __dadd_rn(d2, __dmul_rn(w, w));
+        }
+        return __dsub_rn(sqrt(d2), S.R);
+    } else {
+        float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float d0, e0;
+            two_sum(r.hi[a], -S.cc[a].hi, d0, e0);
+            const float wl0 = __fadd_rn(__fadd_rn(__fsub_rn(r.lo[a], S.cc[a].lo), dr[a]), e0);
+            float wh, wl;
+            two_sum(d0, wl0, wh, wl);
+            const float p = __fmul_rn(wh, wh);
+            const float pe = __fmaf_rn(wh, wh, -p);
+            float s1, e1;
+            two_sum(sh, p, s1, e1);
+            sh = s1;
+            sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(e1, pe), __fmul_rn(2.0f * wh, wl)));
+        }
+        const float g2 = __fadd_rn(__fsub_rn(sh, S.R2h), __fsub_rn(sl, S.R2l));
+        return g2 / __fadd_rn(sqrtf(sh), S.Rf);
+    }
+}
+
+// Signed distance to an event surface of a medium with spheres: the sphere's surface,
+// positive on the ray's own side (outside, or inside its own sphere), or a plane as above.
+template <class P>
+__device__ __forceinline__ typename P::R event_g(const MediumSpheres &m, const Lane<P> &L,
+                                                 const StepParams<P> &sp, int kind,
+                                                 const typename P::R dr[3])
+{
+    if (kind >= EV_SPH) {
+        const int j = kind - EV_SPH;
+        const typename P::R g = sphere_dist<P>(L.r, dr, m.S[j]);
+        return (L.layer == RP_MAX_LAYERS + j) ? -g : g;
+    }
+    return event_g<P>(static_cast<const MediumLayered &>(m), L, sp, kind, dr);
 }
 
 __device__ __forceinline__ bool is_layered(const MediumLayered &) { return true; }
@@ -1018,6 +1104,63 @@ __device__ __forceinline__ void split_at_plane(const MediumLayered &med, Lane<P>
     }
 }
 
+// The landing point r + dr put radially onto sphere S (the FP64 reference's operations).
+template <class P>
+__device__ __forceinline__ void sphere_snap(const SphereB &S, const typename P::V &r,
+                                            const typename P::R dr[3], double out[3])
+{
+    double w[3], d2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        w[a] = __dsub_rn(__dadd_rn(P::get(r, a), (double)dr[a]), S.c[a]);
+        d2 = __dadd_rn(d2, __dmul_rn(w[a], w[a]));
+    }
+    const double q = S.R / sqrt(d2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[a] = __dadd_rn(S.c[a], __dmul_rn(q, w[a]));
+}
+
+// Boundary split at sphere j's surface (curved boundaries, the paragraph after Fig. 1), in
+// FP64 for both policies (splits are rare): the local normal (r - c) / |r - c| turned toward
+// the incident side, the indices of the two regions at the point, Snell and Fresnel as at a
+// plane; the reflected ray continues, the refracted secondary starts in the other region.
+template <class P>
+__device__ __forceinline__ void split_at_sphere(const MediumSpheres &med, Lane<P> &L,
+                                                const StepParams<P> &sp, const Sinks &sk, int j)
+{
+    const SphereB &S = med.S[j];
+    const bool inside = L.layer == RP_MAX_LAYERS + j;
+    double r[3], w[3], d2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        r[a] = P::get(L.r, a);
+        w[a] = __dsub_rn(r[a], S.c[a]);
+        d2 = __dadd_rn(d2, __dmul_rn(w[a], w[a]));
+    }
+    const double d = sqrt(d2);
+    double nrm[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) nrm[a] = (inside ? -1.0 : 1.0) * w[a] / d;
+    const int other = inside ? layer_of(med, r[2]) : RP_MAX_LAYERS + j;
+    double n1, n2, dd;
+    layer_eval_d(med, L.layer, r[2], n1, dd);
+    layer_eval_d(med, other, r[2], n2, dd);
+    double t[3] = {P::get(L.t, 0), P::get(L.t, 1), P::get(L.t, 2)};
+    double t_refl[3], t_refr[3], rr, tau;
+    const bool tir = split_dirs(t, nrm, n1, n2, sp.polarization, t_refl, t_refr, rr, tau);
+    const double amp = L.A * tau;
+    const bool weak = sp.use_min_amp && fabs(amp) < sp.min_amp * fabs(L.A0);
+    if (!tir && L.gen < sp.max_generation && !weak) {
+        const unsigned long long id = atomicAdd(&sk.ctrl->out_count, 1ull);
+        atomicAdd(&sk.ctrl->n_secondary, 1ull);
+        queue_secondary<P>(sk, L, id, other, amp, t_refr,
+                           med.L[other].absorb ? RP_ST_TRANSMITTED : RP_ST_ALIVE);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) P::set(L.t, a, t_refl[a]);
+    L.A *= rr;
+}
+
 // Commit of the candidate state (r + dr, t + dt, T + dT) after a step of length hc; ev is the
 // event the step landed on (EV_NONE: an ordinary accepted step).  Performs receivers, split,
 // stop and break conditions.  Returns true if the ray finished.
@@ -1044,6 +1187,14 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
         else
             dr[2] -= off;
     }
+    double sn[3] = {0.0, 0.0, 0.0};  // a sphere landing: the point put on the surface
+    if constexpr (has_spheres_v<M>) {
+        if (ev >= EV_SPH) {
+            sphere_snap<P>(med.S[ev - EV_SPH], L.r, dr, sn);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) dr[a] = (R)(sn[a] - P::get(L.r, a));
+        }
+    }
     const bool to_max_path = L.last && ev == EV_NONE;
     if (sk.has_rx) receivers_on_chord<P>(sk, L, sp, dr, dt, dT, hc, to_max_path);
     {
@@ -1068,6 +1219,12 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
         else
             P::snap(L.r, 2, L.stop);
     }
+    if constexpr (has_spheres_v<M>) {
+        if (ev >= EV_SPH) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) P::set(L.r, a, sn[a]);
+        }
+    }
     if constexpr (P::kFF) {
         if (sp.rhs_form == RP_RHS_PARAXIAL) ff_renormalise(L.t);
     } else {
@@ -1084,7 +1241,7 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
     ++L.n_acc;
     L.h = L.h_next;
 
-    if (ev == EV_TOP || ev == EV_BOTTOM) {
+    if (ev == EV_TOP || ev == EV_BOTTOM || ev >= EV_SPH) {
         if constexpr (is_layered_v<M>) {
             // the split itself is done by finish_split, batched across the warp
             L.pend = ev;
@@ -1123,6 +1280,25 @@ __device__ __forceinline__ bool finish_split(const MediumLayered &med, Lane<P> &
 {
     typedef typename P::R R;
     split_at_plane<P>(med, L, sp, sk, L.pend);
+    ++L.n_refl;
+    L.pend = 0;
+    if (sp.use_max_time && P::sdiff(L.T, sp.mt) >= R(0))
+        L.status = RP_ST_MAX_TIME;
+    else if (sp.use_min_amp && fabs(L.A) < sp.min_amp * fabs(L.A0))
+        L.status = RP_ST_MIN_AMP;
+    if (L.status != RP_ST_ALIVE) return true;
+    set_trial(L, sp);
+    return false;
+}
+template <class P>
+__device__ __forceinline__ bool finish_split(const MediumSpheres &med, Lane<P> &L,
+                                             const StepParams<P> &sp, const Sinks &sk)
+{
+    typedef typename P::R R;
+    if (L.pend >= EV_SPH)
+        split_at_sphere<P>(med, L, sp, sk, L.pend - EV_SPH);
+    else
+        split_at_plane<P>(med, L, sp, sk, L.pend);
     ++L.n_refl;
     L.pend = 0;
     if (sp.use_max_time && P::sdiff(L.T, sp.mt) >= R(0))
@@ -1200,6 +1376,24 @@ __device__ __forceinline__ bool advance(const M &med, Lane<P> &L, const StepPara
                     ev_frac = fr;
                     ev_g0 = g0;
                     ev_g1 = g1;
+                }
+            }
+        }
+        if constexpr (has_spheres_v<M>) {
+            // sphere surfaces: every sphere from outside, only its own from inside one
+            const bool inside = L.layer >= RP_MAX_LAYERS;
+            for (int j = 0; j < med.n_sph; ++j) {
+                if (inside && L.layer != RP_MAX_LAYERS + j) continue;
+                R g0 = event_g<P>(med, L, sp, EV_SPH + j, zero3);
+                R g1 = event_g<P>(med, L, sp, EV_SPH + j, dr);
+                if (g1 < R(0) || (g1 <= sp.eps_b && g0 > sp.eps_b)) {
+                    R fr = (g0 > R(0)) ? g0 / (g0 - g1) : R(0);
+                    if (fr < ev_frac) {
+                        ev = EV_SPH + j;
+                        ev_frac = fr;
+                        ev_g0 = g0;
+                        ev_g1 = g1;
+                    }
                 }
             }
         }
