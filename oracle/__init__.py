@@ -25,7 +25,7 @@ HDR = os.path.join(HERE, "rp_oracle.h")
 
 MAX_LAYERS = 8
 MAX_SPHERES = 4
-RHS = {"projected": 0, "paraxial": 1}
+RHS = {"projected": 0, "paraxial": 1, "momentum": 2}
 POL = {"s": 0, "p": 1, "unpol": 2}
 STATUS = {
     "ALIVE": 0, "MAX_PATH": 1, "MAX_TIME": 2, "MIN_AMP": 3, "LEFT_DOMAIN": 4,

@@ -206,6 +206,16 @@ void or_rhs(const or_medium *m, int32_t layer, int32_t form, const double *y, do
 {
     double n, g[3];
     or_medium_eval(m, layer, y, &n, g);
+    if (form == OR_RHS_MOMENTUM) {
+        /* d/ds (n t) = grad n with p = n t:  r' = p / |p|,  p' = grad n */
+        const double q = sqrt(y[3] * y[3] + y[4] * y[4] + y[5] * y[5]);
+        for (int i = 0; i < 3; ++i) {
+            k[i] = y[3 + i] / q;
+            k[3 + i] = g[i];
+        }
+        k[6] = n / C0;
+        return;
+    }
     k[0] = y[3];
     k[1] = y[4];
     k[2] = y[5];
@@ -218,10 +228,16 @@ void or_rhs(const or_medium *m, int32_t layer, int32_t form, const double *y, do
     k[6] = n / C0;
 }
 
-double or_ck_step(const or_medium *m, int32_t layer, int32_t form, const double *y0, double h,
-                  double *y5)
+double or_ck_step(const or_medium *m, int32_t layer, int32_t form, const double *y0_in,
+                  double h, double *y5)
 {
-    double k[6][7], ys[7];
+    double k[6][7], ys[7], y0[7], n0 = 1.0;
+    for (int c = 0; c < 7; ++c) y0[c] = y0_in[c];
+    if (form == OR_RHS_MOMENTUM) { /* the stages run on p = n(r0) t0 */
+        double g[3];
+        or_medium_eval(m, layer, y0_in, &n0, g);
+        for (int c = 3; c < 6; ++c) y0[c] = n0 * y0_in[c];
+    }
     for (int i = 0; i < 6; ++i) {
         for (int c = 0; c < 7; ++c) {
             double acc = 0.0;
@@ -243,7 +259,7 @@ double or_ck_step(const or_medium *m, int32_t layer, int32_t form, const double 
         else if (c < 6)
             et2 += (h * d) * (h * d);
     }
-    return fmax(sqrt(er2), sqrt(et2));
+    return fmax(sqrt(er2), sqrt(et2) / n0);
 }
 
 static void normalise3(double *v)

@@ -21,7 +21,7 @@
 #define OR_MAX_SPHERES 4
 
 enum { OR_MEDIUM_LAYERED = 0, OR_MEDIUM_GRID = 1 };
-enum { OR_RHS_PROJECTED = 0, OR_RHS_PARAXIAL = 1 };
+enum { OR_RHS_PROJECTED = 0, OR_RHS_PARAXIAL = 1, OR_RHS_MOMENTUM = 2 };
 enum { OR_POL_S = 0, OR_POL_P = 1, OR_POL_UNPOL = 2 };
 enum {
     OR_ST_ALIVE = 0, OR_ST_MAX_PATH = 1, OR_ST_MAX_TIME = 2, OR_ST_MIN_AMP = 3,
@@ -121,11 +121,14 @@ int32_t or_region_of(const or_medium *m, const double *r);
 void or_grid_prepare(const float *n, int32_t nx, int32_t ny, int32_t nz, double spacing,
                      float *out4);
 
-/* Right-hand side of the ray equations (PROJECTED = Eq. 1 for unit t; PARAXIAL = Eq. 2). */
+/* Right-hand side of the ray equations (PROJECTED = Eq. 1 for unit t; PARAXIAL = Eq. 2;
+ * MOMENTUM = Eq. 1 as written, on the state (r, p = n t, T): r' = p / |p|, p' = grad n). */
 void or_rhs(const or_medium *m, int32_t layer, int32_t form, const double *y, double *k);
 
 /* One Cash-Karp step of the ray system; returns the unscaled error measure
- * max(|sum (b5-b4) k_r|, h |sum (b5-b4) k_t|); y5 is the 5th-order state (t not normalised). */
+ * max(|sum (b5-b4) k_r|, h |sum (b5-b4) k_t|); y5 is the 5th-order state (t not normalised).
+ * MOMENTUM: the stages run on p = n(r0) t0; y5 holds p5 in place of t (its direction is t) and
+ * the direction error is h |sum (b5-b4) k_p| / n(r0). */
 double or_ck_step(const or_medium *m, int32_t layer, int32_t form, const double *y0, double h,
                   double *y5);
 
