@@ -48,7 +48,7 @@ extern "C" {
 enum { RP_MEDIUM_LAYERED = 0, RP_MEDIUM_GRID = 1 };
 enum { RP_FP64 = 0, RP_FP32_MIXED = 1 };
 enum { RP_POL_S = 0, RP_POL_P = 1, RP_POL_UNPOL = 2 };
-enum { RP_RHS_PROJECTED = 0, RP_RHS_PARAXIAL = 1 };
+enum { RP_RHS_PROJECTED = 0, RP_RHS_PARAXIAL = 1, RP_RHS_MOMENTUM = 2 };
 
 /* Per-ray end status. */
 enum {
@@ -156,6 +156,8 @@ typedef struct {
  *                of the s/p-averaged reflectance and transmittance)
  *   rhs_form     RP_RHS_PROJECTED: t' = (grad n - (grad n . t) t)/n, Eq. 1 for unit t;
  *                RP_RHS_PARAXIAL: t' = grad n / n, Eq. 2, t renormalised after each step
+ *                RP_RHS_MOMENTUM: Eq. 1 as written on p = n t (r' = p/|p|, p' = grad n), a
+ *                cross-check of the projected form; RP_FP64 only (RP_ERR_INVALID_ARG else)
  *   max_steps    cap on attempted Cash-Karp steps per ray (> 0) */
 typedef struct {
     double tol, h_min, h_max, h0, max_path, max_time, min_amp, eps_b;

@@ -22,7 +22,7 @@ MAX_SPHERES = 4
 MEDIUM_KIND = {"layered": 0, "grid": 1}
 PRECISION = {"fp64": 0, "fp32": 1}
 POLARIZATION = {"s": 0, "p": 1, "unpol": 2}
-RHS_FORM = {"projected": 0, "paraxial": 1}
+RHS_FORM = {"projected": 0, "paraxial": 1, "momentum": 2}
 STATUS = {
     "ALIVE": 0, "MAX_PATH": 1, "MAX_TIME": 2, "MIN_AMP": 3, "LEFT_DOMAIN": 4, "TRANSMITTED": 5,
     "REACHED_STOP": 6, "MAX_STEPS": 7, "BAD_INPUT": 8, "QUEUE_FULL": 9,

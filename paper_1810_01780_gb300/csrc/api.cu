@@ -101,8 +101,13 @@ int validate_params(const rp_trace_params *p, bool path_finding)
         return RP_ERR_INVALID_ARG;
     }
     if (p->polarization < RP_POL_S || p->polarization > RP_POL_UNPOL ||
-        (p->rhs_form != RP_RHS_PROJECTED && p->rhs_form != RP_RHS_PARAXIAL)) {
+        (p->rhs_form != RP_RHS_PROJECTED && p->rhs_form != RP_RHS_PARAXIAL &&
+         p->rhs_form != RP_RHS_MOMENTUM)) {
         set_error("params: bad polarization or rhs_form");
+        return RP_ERR_INVALID_ARG;
+    }
+    if (p->rhs_form == RP_RHS_MOMENTUM && p->precision != RP_FP64) {
+        set_error("params: the momentum form runs in RP_FP64 only");
         return RP_ERR_INVALID_ARG;
     }
     return RP_OK;

@@ -438,6 +438,69 @@ __device__ __forceinline__ void medium_eval(const MediumGrid &m, const LayerR<P>
 //   er = |sum_i (b5_i - b4_i) k_r,i|,   et = h |sum_i (b5_i - b4_i) k_t,i|.
 // Sums run over the stages in ascending order, as in the FP64 reference.
 // ---------------------------------------------------------------------------------------
+// Cash-Karp step of Eq. 1 as written, d/ds (n t) = grad n, on the state (r, p = n t, T):
+// r' = p / |p|, p' = grad n, T' = n / c0 (FP64 only: a cross-check of the projected form).
+// The stages run on p from p0 = n(r0) t0 (n(r0) is stage 0's index); the direction increment
+// is p5 / |p5| - t0 and the direction error h |sum (b5 - b4) k_p| / n(r0).
+template <class P, class M>
+__device__ __forceinline__ void ck_step_momentum(const M &med, const LayerR<P> &lc,
+                                                 const typename P::V &r0, const typename P::V &t0v,
+                                                 double h, double dr[3], double dt[3],
+                                                 double &dT, double &er, double &et)
+{
+    double p0[3] = {0.0, 0.0, 0.0}, kr[6][3], kp[6][3], n0 = 1.0;
+    double sr[3] = {0.0, 0.0, 0.0}, sp_[3] = {0.0, 0.0, 0.0}, sT = 0.0;
+    double dr_e[3] = {0.0, 0.0, 0.0}, dp_e[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double rs[3], ps[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double ar = 0.0, ap = 0.0;
+#pragma unroll
+            for (int j = 0; j < i; ++j) {
+                ar += ck_a(i, j) * kr[j][c];
+                ap += ck_a(i, j) * kp[j][c];
+            }
+            rs[c] = P::get(r0, c) + h * ar;
+            ps[c] = p0[c] + h * ap;
+        }
+        double n, g[3];
+        medium_eval<P>(med, lc, rs, n, g);
+        if (i == 0) {
+            n0 = n;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ps[c] = p0[c] = n0 * P::get(t0v, c);
+        }
+        const double q = sqrt(ps[0] * ps[0] + ps[1] * ps[1] + ps[2] * ps[2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            kr[i][c] = ps[c] / q;
+            kp[i][c] = g[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            sr[c] += ck_b5(i) * kr[i][c];
+            sp_[c] += ck_b5(i) * kp[i][c];
+            dr_e[c] += ck_db(i) * kr[i][c];
+            dp_e[c] += ck_db(i) * kp[i][c];
+        }
+        sT += ck_b5(i) * n;
+    }
+    double p5[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        dr[c] = h * sr[c];
+        p5[c] = p0[c] + h * sp_[c];
+    }
+    const double q5 = sqrt(p5[0] * p5[0] + p5[1] * p5[1] + p5[2] * p5[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dt[c] = p5[c] / q5 - P::get(t0v, c);
+    dT = h * (sT * kInvC0);
+    er = sqrt(dr_e[0] * dr_e[0] + dr_e[1] * dr_e[1] + dr_e[2] * dr_e[2]);
+    et = h * sqrt(dp_e[0] * dp_e[0] + dp_e[1] * dp_e[1] + dp_e[2] * dp_e[2]) / n0;
+}
+
 template <class P, class M>
 __device__ __forceinline__ void ck_step(const M &med, const LayerR<P> &lc, int form,
                                         const typename P::V &r0, const typename P::V &t0v,
@@ -446,6 +509,12 @@ __device__ __forceinline__ void ck_step(const M &med, const LayerR<P> &lc, int f
                                         typename P::R &er, typename P::R &et)
 {
     typedef typename P::R R;
+    if constexpr (!P::kFF) {
+        if (form == RP_RHS_MOMENTUM) {
+            ck_step_momentum<P, M>(med, lc, r0, t0v, h, dr, dt, dT, er, et);
+            return;
+        }
+    }
     R t0[3] = {P::base(t0v, 0), P::base(t0v, 1), P::base(t0v, 2)};
     R ts[6][3], kt[6][3];
     R sr[3] = {R(0), R(0), R(0)}, st[3] = {R(0), R(0), R(0)}, sT = R(0);

@@ -157,6 +157,21 @@ def test_paraxial_form_fp64(rp):
     check_fp64(gpu_rays(res), oracle_rays(ref), prm["tol"], min_tier1=0.9)
 
 
+def test_momentum_form_fp64(rp):
+    """Eq. 1 integrated as written (p = n t) on the GPU against the oracle, on the small fan
+    (surface splits) and on the batched two-layer ice; the FP32-mixed path refuses it."""
+    for cfg in (W.small(256), dict(W.batched(), rays=W.subsample(W.batched()["rays"],
+                                                                  np.arange(2000)))):
+        prm = dict(cfg["params"], rhs_form="momentum")
+        res = _run(rp, cfg["medium"], prm, cfg["rays"], receivers=cfg.get("receivers"))
+        ref, _ = oracle.trace(cfg["medium"], prm, *cfg["rays"], receivers=cfg.get("receivers"))
+        check_fp64(gpu_rays(res), oracle_rays(ref), prm["tol"], min_tier1=0.9)
+    from paper_1810_01780_gb300._abi import RPError
+
+    with pytest.raises(RPError):
+        _run(rp, cfg["medium"], prm, cfg["rays"], precision="fp32")
+
+
 def test_polarizations_and_break_conditions(rp):
     cfg = W.small(200)
     for pol in ("p", "unpol"):
