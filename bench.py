@@ -470,6 +470,27 @@ def run_gpu(args):
                          "max": float(d.max())},
                "time_s": {"p50": float(dT.quantile(0.5)), "p99": float(dT.quantile(0.99)),
                           "max": float(dT.max())}}
+        # Eq. 1 integrated as written (momentum form, FP64 only): the same batch, end points
+        # against the projected FP64 run just made
+        end64 = buf.t["end_pos"][:, :n_rays].clone()
+        t64e = buf.t["time"][:n_rays].clone()
+        prmm = rp.make_params(dict(cfg["params"], rhs_form="momentum"), "fp64")
+        one_step(prmm, buf)
+        tm, accm, raysm = [], 0, 0
+        for _ in range(args.fp64_steps):
+            ms, st = one_step(prmm, buf)
+            tm.append(ms)
+            accm += st.steps_accepted
+            raysm += st.rays
+        dm = (end64 - buf.t["end_pos"][:, :n_rays]).norm(dim=0)
+        dTm = (t64e - buf.t["time"][:n_rays]).abs()
+        modes["fp64_momentum"] = {
+            "ray_steps_per_s": accm / (sum(tm) / 1e3), "rays_per_s": raysm / (sum(tm) / 1e3),
+            "ms_per_step": sum(tm) / len(tm),
+            "vs_projected_fp64": {"pos_m_p99": float(dm.double().quantile(0.99)),
+                                  "time_s_p99": float(dTm.double().quantile(0.99)),
+                                  "within_1mm_10ps": float(((dm <= 1e-3) & (dTm <= 1e-11))
+                                                           .double().mean())}}
 
     # gridded medium: 256 x 256 x 512 FP32 grid, 4,194,304 rays (FP32-mixed), its own
     # figures (memory-bound path: algorithmic bytes = 8 float4 corner samples per medium

@@ -1453,8 +1453,9 @@ __device__ __forceinline__ bool advance(const M &med, Lane<P> &L, const StepPara
             const bool inside = L.layer >= RP_MAX_LAYERS;
             for (int j = 0; j < med.n_sph; ++j) {
                 if (inside && L.layer != RP_MAX_LAYERS + j) continue;
-                R g0 = event_g<P>(med, L, sp, EV_SPH + j, zero3);
                 R g1 = event_g<P>(med, L, sp, EV_SPH + j, dr);
+                if (g1 > sp.eps_b) continue;  // no event whatever g0 is: spare its evaluation
+                R g0 = event_g<P>(med, L, sp, EV_SPH + j, zero3);
                 if (g1 < R(0) || (g1 <= sp.eps_b && g0 > sp.eps_b)) {
                     R fr = (g0 > R(0)) ? g0 / (g0 - g1) : R(0);
                     if (fr < ev_frac) {
