@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstddef>
 #include <cstdlib>
 #include <mutex>
@@ -98,6 +99,7 @@ inline rpk::StepParams<P> step_params(const rp_trace_params *p, int axis, float 
     rpk::StepParams<P> sp;
     sp.tol = (typename P::R)p->tol;
     sp.inv_tol = (typename P::R)(1.0 / p->tol);
+    sp.inv_tol2 = (typename P::R)std::min(1.0 / (p->tol * p->tol), 1e30);
     sp.h_min = (typename P::R)p->h_min;
     sp.h_max = (typename P::R)p->h_max;
     double eps = p->eps_b;

@@ -587,8 +587,15 @@ __device__ __forceinline__ void ck_step(const M &med, const LayerR<P> &lc, int f
         for (int c = 0; c < 3; ++c) dr[c] = __fmaf_rn(h, t0v.lo[c], dr[c]);
     }
     dT = h * (sT * P::c(kInvC0));
-    er = P::sqrt_(dr_e[0] * dr_e[0] + dr_e[1] * dr_e[1] + dr_e[2] * dr_e[2]);
-    et = h * P::sqrt_(dt_e[0] * dt_e[0] + dt_e[1] * dt_e[1] + dt_e[2] * dt_e[2]);
+    if constexpr (P::kFF) {
+        // FP32-mixed: squared norms (the step control compares and scales squares, sparing two
+        // square roots per step)
+        er = dr_e[0] * dr_e[0] + dr_e[1] * dr_e[1] + dr_e[2] * dr_e[2];
+        et = (h * h) * (dt_e[0] * dt_e[0] + dt_e[1] * dt_e[1] + dt_e[2] * dt_e[2]);
+    } else {
+        er = P::sqrt_(dr_e[0] * dr_e[0] + dr_e[1] * dr_e[1] + dr_e[2] * dr_e[2]);
+        et = h * P::sqrt_(dt_e[0] * dt_e[0] + dt_e[1] * dt_e[1] + dt_e[2] * dt_e[2]);
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -723,7 +730,7 @@ struct Lane {
 template <class P>
 struct StepParams {
     typedef typename P::R R;
-    R tol, inv_tol, h_min, h_max, eps_b;
+    R tol, inv_tol, inv_tol2, h_min, h_max, eps_b;  // inv_tol2 = 1/tol^2, capped at 1e30
     double max_path, max_time, min_amp;
     PlaneC mp, mt;  // max_path and max_time as float-float constants
     int32_t use_max_time, use_min_amp;
@@ -1414,17 +1421,20 @@ __device__ __forceinline__ bool advance(const M &med, Lane<P> &L, const StepPara
     ck_step<P, M>(med, L.lc, sp.rhs_form, L.r, L.t, hc, dr, dt, dT, er, et);
 
     if (L.mode == MODE_NORMAL) {
-        const R e = (er > et ? er : et) * sp.inv_tol;
+        // e = max(er, et) / tol; the FP32-mixed step returns squared norms, so there e holds
+        // e^2 and the exponents of the step law are halved
+        constexpr R kq = P::kFF ? R(0.5) : R(1);
+        const R e = (er > et ? er : et) * (P::kFF ? sp.inv_tol2 : sp.inv_tol);
         if (!(e <= R(1)) && hc > sp.h_min) {
             ++L.n_rej;
-            R fac = R(0.9) * P::pow_(e, R(-0.25));
+            R fac = R(0.9) * P::pow_(e, R(-0.25) * kq);
             if (!(fac >= R(0.1))) fac = R(0.1);
             R hn = hc * fac;
             L.h = hn < sp.h_min ? sp.h_min : hn;
             set_trial(L, sp);
             return false;
         }
-        R grow = (e == R(0)) ? R(5) : R(0.9) * P::pow_(e, R(-0.2));
+        R grow = (e == R(0)) ? R(5) : R(0.9) * P::pow_(e, R(-0.2) * kq);
         if (grow > R(5)) grow = R(5);
         R hn = hc * grow;
         hn = hn < sp.h_min ? sp.h_min : hn;
