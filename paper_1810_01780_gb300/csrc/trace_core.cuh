@@ -921,8 +921,6 @@ __device__ __forceinline__ void write_ray(const rp_ray_out &o, long long id, con
 
 // Receiver test on the committed chord (state L before the commit -> r1 = r + dr): a hit is
 // recorded when the chord enters a sphere; quantities are interpolated linearly along it.
-// Receiver test on the committed chord (state L before the commit -> r1 = r + dr): a hit is
-// recorded when the chord enters a sphere; quantities are interpolated linearly along it.
 // Culling: the receiver grid cell of the chord's midpoint lists the candidates; only they get
 // the exact chord-sphere intersection.
 template <class P>
@@ -1406,7 +1404,8 @@ __device__ __forceinline__ typename P::R rf_point(const Lane<P> &L)
 }
 
 // One iteration of a lane: one Cash-Karp evaluation and the state-machine update.
-// Returns true when the ray has finished (L.status set).
+// Returns true when the ray has finished (L.status set).  Every branch that accepts the step
+// leads to the one call of commit at the end, so that its code is inlined once.
 template <class P, class M>
 __device__ __forceinline__ bool advance(const M &med, Lane<P> &L, const StepParams<P> &sp,
                                         const Sinks &sk)
@@ -1420,6 +1419,7 @@ __device__ __forceinline__ bool advance(const M &med, Lane<P> &L, const StepPara
     R dr[3], dt[3], dT, er, et;
     ck_step<P, M>(med, L.lc, sp.rhs_form, L.r, L.t, hc, dr, dt, dT, er, et);
 
+    int cev = -1;  // the event the accepted step lands on (EV_NONE: none); -1: no commit
     if (L.mode == MODE_NORMAL) {
         // e = max(er, et) / tol; the FP32-mixed step returns squared norms, so there e holds
         // e^2 and the exponents of the step law are halved
@@ -1480,61 +1480,69 @@ __device__ __forceinline__ bool advance(const M &med, Lane<P> &L, const StepPara
                 }
             }
         }
-        if (ev == EV_NONE) return commit<P, M>(med, L, sp, sk, hc, dr, dt, dT, EV_NONE);
-        L.ev = ev;
-        if (fabs(ev_g1) <= sp.eps_b) return commit<P, M>(med, L, sp, sk, hc, dr, dt, dT, ev);
-        if (ev_g0 <= sp.eps_b) {
-            if (hc <= sp.h_min) return commit<P, M>(med, L, sp, sk, hc, dr, dt, dT, ev);
-            L.mode = MODE_PROBE;
-            L.rb = hc;
-            L.gb = ev_g1;
-            L.h_try = sp.h_min;
-            return false;
+        if (ev == EV_NONE) {
+            cev = EV_NONE;
+        } else {
+            L.ev = ev;
+            if (fabs(ev_g1) <= sp.eps_b || (ev_g0 <= sp.eps_b && hc <= sp.h_min)) {
+                cev = ev;
+            } else if (ev_g0 <= sp.eps_b) {
+                L.mode = MODE_PROBE;
+                L.rb = hc;
+                L.gb = ev_g1;
+                L.h_try = sp.h_min;
+            } else {
+                L.mode = MODE_ILLINOIS;
+                L.ra = R(0);
+                L.ga = ev_g0;
+                L.rb = hc;
+                L.gb = ev_g1;
+                L.side = 0;
+                L.it = 1;
+                L.h_try = rf_point(L);
+            }
         }
-        L.mode = MODE_ILLINOIS;
-        L.ra = R(0);
-        L.ga = ev_g0;
-        L.rb = hc;
-        L.gb = ev_g1;
-        L.side = 0;
-        L.it = 1;
-        L.h_try = rf_point(L);
-        return false;
-    }
-
-    // root-search evaluation at hc
-    ++L.n_root;
-    const R gc = event_g<P>(med, L, sp, L.ev, dr);
-    if (L.mode == MODE_PROBE) {
-        if (gc <= sp.eps_b) return commit<P, M>(med, L, sp, sk, hc, dr, dt, dT, L.ev);
-        L.ra = hc;
-        L.ga = gc;
-        L.mode = MODE_ILLINOIS;
-        L.side = 0;
-        L.it = 1;
-        L.h_try = rf_point(L);
-        return false;
-    }
-    if (fabs(gc) <= sp.eps_b) return commit<P, M>(med, L, sp, sk, hc, dr, dt, dT, L.ev);
-    if (gc > R(0)) {
-        L.ra = hc;
-        L.ga = gc;
-        if (L.side == 1) L.gb *= R(0.5);
-        L.side = 1;
     } else {
-        L.rb = hc;
-        L.gb = gc;
-        if (L.side == -1) L.ga *= R(0.5);
-        L.side = -1;
+        // root-search evaluation at hc
+        ++L.n_root;
+        const R gc = event_g<P>(med, L, sp, L.ev, dr);
+        if (L.mode == MODE_PROBE) {
+            if (gc <= sp.eps_b) {
+                cev = L.ev;
+            } else {
+                L.ra = hc;
+                L.ga = gc;
+                L.mode = MODE_ILLINOIS;
+                L.side = 0;
+                L.it = 1;
+                L.h_try = rf_point(L);
+            }
+        } else if (fabs(gc) <= sp.eps_b) {
+            cev = L.ev;
+        } else {
+            if (gc > R(0)) {
+                L.ra = hc;
+                L.ga = gc;
+                if (L.side == 1) L.gb *= R(0.5);
+                L.side = 1;
+            } else {
+                L.rb = hc;
+                L.gb = gc;
+                if (L.side == -1) L.ga *= R(0.5);
+                L.side = -1;
+            }
+            if (L.it == kRootMaxIter) {
+                L.root_fail = 1;
+                atomicOr(&sk.ctrl->flags, (unsigned)FLAG_ROOT_CAP);
+                cev = L.ev;
+            } else {
+                ++L.it;
+                L.h_try = rf_point(L);
+            }
+        }
     }
-    if (L.it == kRootMaxIter) {
-        L.root_fail = 1;
-        atomicOr(&sk.ctrl->flags, (unsigned)FLAG_ROOT_CAP);
-        return commit<P, M>(med, L, sp, sk, hc, dr, dt, dT, L.ev);
-    }
-    ++L.it;
-    L.h_try = rf_point(L);
-    return false;
+    if (cev < 0) return false;
+    return commit<P, M>(med, L, sp, sk, hc, dr, dt, dT, cev);
 }
 
 }  // namespace rpk
