@@ -207,15 +207,17 @@ __device__ __forceinline__ void drive(const MediumLayered &med, const StepParams
     Lane<P> L;
     L.stk = 0;
     unsigned int acc = 0, rej = 0, root = 0, rays = 0;
-    bool active = next(L), done = false;
+    // fetch: the lane wants its next ray (the first one too comes from a service phase, so
+    // that `next` is inlined once)
+    bool active = false, done = false, fetch = true;
     unsigned int iter = 0;
-    while (__any_sync(0xffffffffu, active || done)) {
+    while (__any_sync(0xffffffffu, active || done || fetch)) {
         __syncwarp();
         if (active && L.pend == 0 && advance<P, MediumLayered>(med, L, sp, sk)) {
             active = false;
             done = true;
         }
-        const bool waits = done || (active && L.pend != 0);
+        const bool waits = done || fetch || (active && L.pend != 0);
         const unsigned int wait = __ballot_sync(0xffffffffu, waits);
         const unsigned int step_mask = __ballot_sync(0xffffffffu, active && L.pend == 0);
         if (wait != 0u && (__popc(wait) >= sp.service_batch ||
@@ -224,13 +226,15 @@ __device__ __forceinline__ void drive(const MediumLayered &med, const StepParams
                 active = false;
                 done = true;
             }
-            if (done) {
-                acc += (unsigned int)L.n_acc;
-                rej += (unsigned int)L.n_rej;
-                root += (unsigned int)L.n_root;
-                ++rays;
-                done_fn(L);
-                done = false;
+            if (done || fetch) {
+                if (done) {
+                    acc += (unsigned int)L.n_acc;
+                    rej += (unsigned int)L.n_rej;
+                    root += (unsigned int)L.n_root;
+                    ++rays;
+                    done_fn(L);
+                }
+                done = fetch = false;
                 active = next(L);
             }
         }

@@ -89,9 +89,10 @@ __device__ __forceinline__ void prefetch_ray(const Sinks &sk, const WaveIn &in, 
     }
 }
 
-template <class P, class M>
-__device__ __forceinline__ void load_record(Lane<P> &L, const M &med, const StepParams<P> &sp,
-                                            const QRec &Q, const PlaneC &stop)
+// Copies a queued record (a secondary cast at a boundary, or a finished record to write out)
+// into the lane; the lane's per-ray state is reset by the caller.
+template <class P>
+__device__ __forceinline__ void load_record(Lane<P> &L, const QRec &Q)
 {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -108,118 +109,121 @@ __device__ __forceinline__ void load_record(Lane<P> &L, const M &med, const Step
     L.gen = Q.gen;
     L.seq = Q.seq;
     L.layer = Q.layer;
-    lane_reset<P, M>(L, med, sp, stop);
     L.status = Q.status;  // RP_ST_ALIVE, or a record that only has to be written out
+}
+
+// Fills the lane with primary k of the input.  Sets L.status to RP_ST_ALIVE, or to
+// RP_ST_BAD_INPUT (and the launch's flag) for a non-finite position or a zero, non-finite
+// direction; such a ray is written out as it is.
+template <class P, class M>
+__device__ __forceinline__ void load_primary(Lane<P> &L, const M &med, const Sinks &sk,
+                                             const WaveIn &in, long long k)
+{
+    const long long n = in.n;
+    L.A = in.amp ? in.amp[k] : 1.0;
+    L.A0 = L.A;
+    L.id = k;
+    L.parent = -1;
+    L.gen = 0;
+    L.seq = 0;
+    L.status = RP_ST_ALIVE;
+    if constexpr (P::kFF) {
+        // FP32-mixed: every conversion on the integer/FP32 pipes
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            P::set(L.r, a, in.pos[a * n + k]);
+            P::set(L.t, a, in.dir[a * n + k]);
+        }
+        L.T.hi = L.T.lo = 0.0f;
+        L.s.hi = L.s.lo = 0.0f;
+        L.h = in.h0f;
+        if constexpr (has_spheres_v<M>) {
+            const double r0[3] = {in.pos[k], in.pos[n + k], in.pos[2 * n + k]};
+            L.layer = region_of(med, r0);
+        } else if constexpr (is_layered_v<M>) {
+            L.layer = layer_of_ff(med, L.r.hi[2], L.r.lo[2]);
+        } else {
+            L.layer = 0;
+        }
+        const float q2 = L.t.hi[0] * L.t.hi[0] + L.t.hi[1] * L.t.hi[1] + L.t.hi[2] * L.t.hi[2];
+        const bool pos_ok = isfinite(L.r.hi[0]) && isfinite(L.r.hi[1]) && isfinite(L.r.hi[2]);
+        if (!(q2 > 0.0f) || !isfinite(q2) || !pos_ok) {
+            L.status = RP_ST_BAD_INPUT;
+            atomicOr(&sk.ctrl->flags, (unsigned)FLAG_BAD_INPUT);
+            return;
+        }
+        if (fabsf(q2 - 1.0f) > 1e-5f) {
+            // far from unit: a coarse FP64 normalisation first (rare)
+            double t[3] = {in.dir[k], in.dir[n + k], in.dir[2 * n + k]};
+            const double q = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) P::set(L.t, a, t[a] / q);
+        }
+        ff_renormalise(L.t);  // exact unit length in float-float
+    } else {
+        double r[3], t[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r[a] = in.pos[a * n + k];
+            t[a] = in.dir[a * n + k];
+        }
+        P::sset(L.T, 0.0);
+        P::sset(L.s, 0.0);
+        L.h = P::from_d(in.h0);
+        if constexpr (has_spheres_v<M>)
+            L.layer = region_of(med, r);
+        else if constexpr (is_layered_v<M>)
+            L.layer = layer_of(med, r[2]);
+        else
+            L.layer = 0;
+        const double q2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+        const bool pos_ok = isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) P::set(L.r, a, r[a]);
+        if (!(q2 > 0.0) || !isfinite(q2) || !pos_ok) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) P::set(L.t, a, t[a]);
+            L.status = RP_ST_BAD_INPUT;
+            atomicOr(&sk.ctrl->flags, (unsigned)FLAG_BAD_INPUT);
+            return;
+        }
+        // normalised as the FP64 reference does
+        const double q = sqrt(q2);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) P::set(L.t, a, t[a] / q);
+    }
 }
 
 enum { NEXT_NONE = 0, NEXT_TRACE = 1, NEXT_RECORD = 2 };
 
 // Next ray of this wave for the calling lane: NEXT_TRACE, NEXT_RECORD (a finished record to
-// write out, e.g. a ray refracted into air) or NEXT_NONE when the wave's input is exhausted.
-// `ahead` holds a ray index claimed one ray in advance, so that the claim's atomic and the
-// input loads overlap the tracing of the current ray.
+// write out: a ray refracted into air, or an invalid input) or NEXT_NONE when the wave's
+// input is exhausted.  `ahead` holds a ray index claimed one ray in advance, so that the
+// claim's atomic and the input loads overlap the tracing of the current ray.
 template <class P, class M>
 __device__ int next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, const Sinks &sk,
-                         const WaveIn &in, int wave, unsigned long long base,
-                         unsigned long long count, long long &ahead)
+                        const WaveIn &in, int wave, unsigned long long base,
+                        unsigned long long count, long long &ahead)
 {
-    for (;;) {
-        if (L.stk > 0) {
-            // depth first: the secondaries this thread cast itself come before new input
-            --L.stk;
-            load_record<P, M>(L, med, sp, thread_stack(sk)[L.stk], in.stop);
-            L.tail = ahead >= (long long)count;
-            return L.status == RP_ST_ALIVE ? NEXT_TRACE : NEXT_RECORD;
-        }
+    if (L.stk > 0) {
+        // depth first: the secondaries this thread cast itself come before new input
+        --L.stk;
+        load_record<P>(L, thread_stack(sk)[L.stk]);
+    } else {
         const long long k = ahead;
         if (k >= (long long)count) return NEXT_NONE;
         ahead = claim_index(&sk.ctrl->claim[wave]);
         if (ahead < (long long)count) prefetch_ray(sk, in, wave, base, ahead);
-        if (wave != 0) {
-            load_record<P, M>(L, med, sp, sk.queue[base + k], in.stop);
-            L.tail = ahead >= (long long)count;
-            return L.status == RP_ST_ALIVE ? NEXT_TRACE : NEXT_RECORD;
-        }
-        const long long n = in.n;
-        L.A = in.amp ? in.amp[k] : 1.0;
-        L.A0 = L.A;
-        L.id = k;
-        L.parent = -1;
-        L.gen = 0;
-        L.seq = 0;
-        if constexpr (P::kFF) {
-            // FP32-mixed: every conversion on the integer/FP32 pipes
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                P::set(L.r, a, in.pos[a * n + k]);
-                P::set(L.t, a, in.dir[a * n + k]);
-            }
-            L.T.hi = L.T.lo = 0.0f;
-            L.s.hi = L.s.lo = 0.0f;
-            L.h = in.h0f;
-            if constexpr (has_spheres_v<M>) {
-                const double r0[3] = {in.pos[k], in.pos[n + k], in.pos[2 * n + k]};
-                L.layer = region_of(med, r0);
-            } else if constexpr (is_layered_v<M>) {
-                L.layer = layer_of_ff(med, L.r.hi[2], L.r.lo[2]);
-            } else {
-                L.layer = 0;
-            }
-            const float q2 = L.t.hi[0] * L.t.hi[0] + L.t.hi[1] * L.t.hi[1] + L.t.hi[2] * L.t.hi[2];
-            const bool pos_ok = isfinite(L.r.hi[0]) && isfinite(L.r.hi[1]) && isfinite(L.r.hi[2]);
-            if (!(q2 > 0.0f) || !isfinite(q2) || !pos_ok) {
-                lane_reset<P, M>(L, med, sp, in.stop);
-                L.status = RP_ST_BAD_INPUT;
-                atomicOr(&sk.ctrl->flags, (unsigned)FLAG_BAD_INPUT);
-                write_ray<P>(sk.out, L.id, L, sk.ctrl);
-                continue;
-            }
-            if (fabsf(q2 - 1.0f) > 1e-5f) {
-                // far from unit: a coarse FP64 normalisation first (rare)
-                double t[3] = {in.dir[k], in.dir[n + k], in.dir[2 * n + k]};
-                const double q = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) P::set(L.t, a, t[a] / q);
-            }
-            ff_renormalise(L.t);  // exact unit length in float-float
-        } else {
-            double r[3], t[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                r[a] = in.pos[a * n + k];
-                t[a] = in.dir[a * n + k];
-            }
-            P::sset(L.T, 0.0);
-            P::sset(L.s, 0.0);
-            L.h = P::from_d(in.h0);
-            if constexpr (has_spheres_v<M>)
-                L.layer = region_of(med, r);
-            else if constexpr (is_layered_v<M>)
-                L.layer = layer_of(med, r[2]);
-            else
-                L.layer = 0;
-            const double q2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
-            const bool pos_ok = isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) P::set(L.r, a, r[a]);
-            if (!(q2 > 0.0) || !isfinite(q2) || !pos_ok) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) P::set(L.t, a, t[a]);
-                lane_reset<P, M>(L, med, sp, in.stop);
-                L.status = RP_ST_BAD_INPUT;
-                atomicOr(&sk.ctrl->flags, (unsigned)FLAG_BAD_INPUT);
-                write_ray<P>(sk.out, L.id, L, sk.ctrl);
-                continue;
-            }
-            // normalised as the FP64 reference does
-            const double q = sqrt(q2);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) P::set(L.t, a, t[a] / q);
-        }
-        lane_reset<P, M>(L, med, sp, in.stop);
-        L.tail = ahead >= (long long)count;
-        return NEXT_TRACE;
+        if (wave != 0)
+            load_record<P>(L, sk.queue[base + k]);
+        else
+            load_primary<P, M>(L, med, sk, in, k);
     }
+    const int32_t st = L.status;
+    lane_reset<P, M>(L, med, sp, in.stop);
+    L.status = st;
+    L.tail = ahead >= (long long)count;
+    return st == RP_ST_ALIVE ? NEXT_TRACE : NEXT_RECORD;
 }
 
 template <class P, class M>
@@ -238,8 +242,9 @@ __global__ void __launch_bounds__(128, P::kMinBlocks) k_trace_wave(const M med, 
     L.stk = 0;
     unsigned int acc = 0, rej = 0, root = 0;
     long long ahead = claim_index(&sk.ctrl->claim[wave]);
-    int nx = next_ray<P, M>(L, med, sp, sk, in, wave, base, count, ahead);
-    bool active = nx == NEXT_TRACE, done = nx == NEXT_RECORD;
+    // fetch: the lane wants its next ray (its first one comes from the first service phase,
+    // so that next_ray is inlined once)
+    bool active = false, done = false, fetch = true;
     unsigned int iter = 0;
     // Warp-synchronous loop.  Every iteration runs one Runge-Kutta step on each lane whose
     // ray is stepping.  The rare, long code paths -- a boundary split with its secondary,
@@ -247,14 +252,14 @@ __global__ void __launch_bounds__(128, P::kMinBlocks) k_trace_wave(const M med, 
     // when kServiceBatch lanes wait, every kServicePeriod iterations, or when no lane can
     // step; so they run seldom, with many lanes at once, and stay out of the hot loop's
     // instruction working set.
-    while (__any_sync(0xffffffffu, active || done)) {
+    while (__any_sync(0xffffffffu, active || done || fetch)) {
         __syncwarp();
         const bool stepping = active && L.pend == 0;
         if (stepping && advance<P, M>(med, L, sp, sk)) {
             active = false;
             done = true;
         }
-        const bool waits = done || (active && L.pend != 0);
+        const bool waits = done || fetch || (active && L.pend != 0);
         const unsigned int wait = __ballot_sync(0xffffffffu, waits);
         const unsigned int step_mask = __ballot_sync(0xffffffffu, active && L.pend == 0);
         if (wait != 0u && (__popc(wait) >= sp.service_batch ||
@@ -263,12 +268,15 @@ __global__ void __launch_bounds__(128, P::kMinBlocks) k_trace_wave(const M med, 
                 active = false;
                 done = true;
             }
-            while (done) {
-                acc += (unsigned int)L.n_acc;
-                rej += (unsigned int)L.n_rej;
-                root += (unsigned int)L.n_root;
-                write_ray<P>(sk.out, L.id, L, sk.ctrl);
-                nx = next_ray<P, M>(L, med, sp, sk, in, wave, base, count, ahead);
+            while (done || fetch) {
+                if (done) {
+                    acc += (unsigned int)L.n_acc;
+                    rej += (unsigned int)L.n_rej;
+                    root += (unsigned int)L.n_root;
+                    write_ray<P>(sk.out, L.id, L, sk.ctrl);
+                }
+                const int nx = next_ray<P, M>(L, med, sp, sk, in, wave, base, count, ahead);
+                fetch = false;
                 active = nx == NEXT_TRACE;
                 done = nx == NEXT_RECORD;
             }
