@@ -37,11 +37,12 @@ WORKLOAD = ("batched two-layer ice: 1,048,576 isotropic rays, sources 50-1500 m,
             "64 receivers, tol 1e-6, h 1e-3..10 m, 3 km paths")
 N_RAYS = 1_048_576
 # Algorithmic FP32 flops of one attempted Cash-Karp step of the FP32-mixed path in a layered
-# analytic medium, counted from trace_core.cuh (FMA = 2, a sum of m products = 2m - 1): stage
-# combinations 100, stage states 40, medium 30, projection 48, fifth-order sums 49, error sums
-# 54, increments 14, error norms 11, control 3, event tests 10, float-float state update 80.
-# The 6 exp, 6 reciprocals, 2 square roots and the pow of the step control are not counted.
-FLOPS_PER_ATTEMPT_F32 = 439
+# analytic medium, counted from trace_core.cuh (ck_step_vgrad and the step's control, event
+# test and commit; FMA = 2, a sum of m products = 2m - 1): stage combinations 75, stage states
+# 30, medium 30, projection 36, fifth-order sums 35, error sums 36, increments 16, error norms
+# 13, control 3, event tests 10, float-float state update 80.  The 6 exp, 6 reciprocals and
+# the pow of the step control are not counted.
+FLOPS_PER_ATTEMPT_F32 = 364
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -210,7 +211,7 @@ MLP_FLOPS_FWD = 2 * (3 * 256 + 3 * 256 * 256 + 256 * 12)  # per row, multiply-ad
 # DRAM bytes (read + write) of the four k_trace_wave<PrecF32, MediumLayered> launches of one
 # step of the 1,048,576-ray batched workload, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the current kernel; to be re-measured whenever the kernel changes
-TRACE_DRAM_BYTES_PER_STEP = 519_358_976
+TRACE_DRAM_BYTES_PER_STEP = None
 
 
 def _sync_time(fn):

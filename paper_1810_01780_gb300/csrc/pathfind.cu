@@ -210,7 +210,7 @@ __device__ __forceinline__ void drive(const MediumLayered &med, const StepParams
     // fetch: the lane wants its next ray (the first one too comes from a service phase, so
     // that `next` is inlined once)
     bool active = false, done = false, fetch = true;
-    unsigned int iter = 0;
+    unsigned int idle = 0;  // waiting lane-iterations since the last service phase
     while (__any_sync(0xffffffffu, active || done || fetch)) {
         __syncwarp();
         if (active && L.pend == 0 && advance<P, MediumLayered>(med, L, sp, sk)) {
@@ -220,8 +220,9 @@ __device__ __forceinline__ void drive(const MediumLayered &med, const StepParams
         const bool waits = done || fetch || (active && L.pend != 0);
         const unsigned int wait = __ballot_sync(0xffffffffu, waits);
         const unsigned int step_mask = __ballot_sync(0xffffffffu, active && L.pend == 0);
-        if (wait != 0u && (__popc(wait) >= sp.service_batch ||
-                           ((++iter) & sp.service_mask) == 0u || step_mask == 0u)) {
+        idle += (unsigned int)__popc(wait);
+        if (wait != 0u && (idle >= sp.service_idle || step_mask == 0u)) {
+            idle = 0;
             if (active && L.pend != 0 && finish_split<P>(med, L, sp, sk)) {
                 active = false;
                 done = true;

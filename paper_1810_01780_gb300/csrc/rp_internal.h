@@ -76,8 +76,10 @@ inline rpk::PlaneC plane_const(double d)
 
 int validate_params(const rp_trace_params *p, bool path_finding);
 
-// Service-phase batching (see k_trace_wave): lanes waiting before a service, and the period
-// in iterations (a power of two).  RP_SERVICE_BATCH / RP_SERVICE_PERIOD override them.
+// Service-phase batching (see k_trace_wave): a warp services its waiting lanes once the idle
+// lane-iterations summed since its last service reach this threshold.  An FP64 step costs far
+// more than an FP32-mixed one against the same service phase, so FP64 lanes wait less.
+// RP_SERVICE_IDLE / RP_SERVICE_IDLE_F64 override the two.
 inline int env_int(const char *name, int dflt, int lo, int hi)
 {
     const char *v = getenv(name);
@@ -85,12 +87,10 @@ inline int env_int(const char *name, int dflt, int lo, int hi)
     int x = atoi(v);
     return x < lo ? lo : (x > hi ? hi : x);
 }
-inline int service_batch() { return env_int("RP_SERVICE_BATCH", 8, 1, 32); }
-inline int service_period()
+inline int service_idle(bool fp32)
 {
-    int p = env_int("RP_SERVICE_PERIOD", 16, 1, 1024), q = 1;
-    while (q < p) q <<= 1;
-    return q;
+    return fp32 ? env_int("RP_SERVICE_IDLE", 192, 1, 1 << 20)
+                : env_int("RP_SERVICE_IDLE_F64", 8, 1, 1 << 20);
 }
 
 template <class P>
@@ -119,8 +119,7 @@ inline rpk::StepParams<P> step_params(const rp_trace_params *p, int axis, float 
     sp.stop_axis = axis;
     sp.stop_dir = dir;
     sp.max_steps = p->max_steps;
-    sp.service_batch = service_batch();
-    sp.service_mask = service_period() - 1;
+    sp.service_idle = (unsigned int)service_idle(P::kFF);
     return sp;
 }
 

@@ -245,11 +245,12 @@ __global__ void __launch_bounds__(128, P::kMinBlocks) k_trace_wave(const M med, 
     // fetch: the lane wants its next ray (its first one comes from the first service phase,
     // so that next_ray is inlined once)
     bool active = false, done = false, fetch = true;
-    unsigned int iter = 0;
+    unsigned int idle = 0;  // waiting lane-iterations since the last service phase
     // Warp-synchronous loop.  Every iteration runs one Runge-Kutta step on each lane whose
     // ray is stepping.  The rare, long code paths -- a boundary split with its secondary,
-    // writing a finished ray and loading the next one -- are parked and serviced together,
-    // when kServiceBatch lanes wait, every kServicePeriod iterations, or when no lane can
+    // writing a finished ray and loading the next one -- are parked and serviced together:
+    // once the lane-iterations spent waiting since the last service reach sp.service_idle
+    // (many waiting lanes are served soon, a single one waits longer), or when no lane can
     // step; so they run seldom, with many lanes at once, and stay out of the hot loop's
     // instruction working set.
     while (__any_sync(0xffffffffu, active || done || fetch)) {
@@ -262,8 +263,9 @@ __global__ void __launch_bounds__(128, P::kMinBlocks) k_trace_wave(const M med, 
         const bool waits = done || fetch || (active && L.pend != 0);
         const unsigned int wait = __ballot_sync(0xffffffffu, waits);
         const unsigned int step_mask = __ballot_sync(0xffffffffu, active && L.pend == 0);
-        if (wait != 0u && (__popc(wait) >= sp.service_batch ||
-                           ((++iter) & sp.service_mask) == 0u || step_mask == 0u)) {
+        idle += (unsigned int)__popc(wait);
+        if (wait != 0u && (idle >= sp.service_idle || step_mask == 0u)) {
+            idle = 0;
             if (active && L.pend != 0 && finish_split<P>(med, L, sp, sk)) {
                 active = false;
                 done = true;

@@ -504,6 +504,80 @@ __device__ __forceinline__ void ck_step_momentum(const M &med, const LayerR<P> &
     et = h * sqrt(dp_e[0] * dp_e[0] + dp_e[1] * dp_e[1] + dp_e[2] * dp_e[2]) / n0;
 }
 
+// FP32-mixed Cash-Karp step for stratified media (planes and spheres whose regions have
+// z-only index profiles), where grad n = (0, 0, g).  The horizontal direction components
+// then obey the same linear equation, t_c' = kap t_c with kap = -(g t_z / n) (projected form;
+// 0 for the paraxial one), so every stage's horizontal components are the step's start
+// values times one common factor, t_c,i = t0_c phi_i with phi_i = 1 + h sum_j a_ij kap_j, and
+// their slopes are t0_c kap_i.  The stages carry the scalars (phi, kap, t_z, t_z') instead of
+// two more vector components: the same Runge-Kutta step in exact arithmetic, with fewer
+// operations and registers.  The error measures are returned squared, as by ck_step.
+template <class P, class M>
+__device__ __forceinline__ void ck_step_vgrad(const M &med, const LayerR<P> &lc, int form,
+                                              const typename P::V &r0, const typename P::V &t0v,
+                                              typename P::R h, typename P::R dr[3],
+                                              typename P::R dt[3], typename P::R &dT,
+                                              typename P::R &er, typename P::R &et)
+{
+    typedef typename P::R R;
+    const R tx = P::base(t0v, 0), ty = P::base(t0v, 1), tz0 = P::base(t0v, 2);
+    R kap[6], tz[6], ktz[6];
+    R s_phi = R(0), s_kap = R(0), s_tz = R(0), s_ktz = R(0), sT = R(0);
+    R e_phi = R(0), e_kap = R(0), e_tz = R(0), e_ktz = R(0);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        R a_kap = R(0), a_tz = R(0), a_ktz = R(0);
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            a_kap += P::c(ck_a(i, j)) * kap[j];
+            a_tz += P::c(ck_a(i, j)) * tz[j];
+            a_ktz += P::c(ck_a(i, j)) * ktz[j];
+        }
+        const R phi = R(1) + h * a_kap;
+        tz[i] = tz0 + h * a_ktz;
+        const R rs[3] = {R(0), R(0), P::base(r0, 2) + h * a_tz};
+        R n, g[3];
+        medium_eval<P>(med, lc, rs, n, g);
+        const R inv_n = P::rcp(n);
+        if (form == RP_RHS_PROJECTED) {
+            const R gt = g[2] * tz[i];
+            kap[i] = -(gt * phi) * inv_n;
+            ktz[i] = (g[2] - gt * tz[i]) * inv_n;
+        } else {
+            kap[i] = R(0);
+            ktz[i] = g[2] * inv_n;
+        }
+        if (ck_b5(i) != 0.0) {
+            s_phi += P::c(ck_b5(i)) * phi;
+            s_kap += P::c(ck_b5(i)) * kap[i];
+            s_tz += P::c(ck_b5(i)) * tz[i];
+            s_ktz += P::c(ck_b5(i)) * ktz[i];
+            sT += P::c(ck_b5(i)) * n;
+        }
+        if (ck_db(i) != 0.0) {
+            e_phi += P::c(ck_db(i)) * phi;
+            e_kap += P::c(ck_db(i)) * kap[i];
+            e_tz += P::c(ck_db(i)) * tz[i];
+            e_ktz += P::c(ck_db(i)) * ktz[i];
+        }
+    }
+    const R hphi = h * s_phi, hkap = h * s_kap;
+    dr[0] = tx * hphi;
+    dr[1] = ty * hphi;
+    dr[2] = h * s_tz;
+    dt[0] = tx * hkap;
+    dt[1] = ty * hkap;
+    dt[2] = h * s_ktz;
+    // the stages used the high word of the direction; since sum_i b5_i = 1 its low word
+    // contributes exactly h * t_lo to the position increment
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dr[c] = __fmaf_rn(h, t0v.lo[c], dr[c]);
+    dT = h * (sT * P::c(kInvC0));
+    const R th2 = tx * tx + ty * ty;
+    er = th2 * (e_phi * e_phi) + e_tz * e_tz;
+    et = (h * h) * (th2 * (e_kap * e_kap) + e_ktz * e_ktz);
+}
+
 template <class P, class M>
 __device__ __forceinline__ void ck_step(const M &med, const LayerR<P> &lc, int form,
                                         const typename P::V &r0, const typename P::V &t0v,
@@ -517,6 +591,10 @@ __device__ __forceinline__ void ck_step(const M &med, const LayerR<P> &lc, int f
             ck_step_momentum<P, M>(med, lc, r0, t0v, h, dr, dt, dT, er, et);
             return;
         }
+    }
+    if constexpr (P::kFF && is_layered_v<M>) {
+        ck_step_vgrad<P, M>(med, lc, form, r0, t0v, h, dr, dt, dT, er, et);
+        return;
     }
     R t0[3] = {P::base(t0v, 0), P::base(t0v, 1), P::base(t0v, 2)};
     R ts[6][3], kt[6][3];
@@ -738,8 +816,7 @@ struct StepParams {
     int32_t stop_axis;  // 0, 1, 2 (the stop normal is +/- a coordinate axis)
     float stop_dir;     // +1 or -1: sign of the normal along stop_axis
     long long max_steps;
-    int32_t service_batch;          // lanes waiting before a service phase
-    unsigned int service_mask;      // service period - 1 (period is a power of two)
+    unsigned int service_idle;      // idle lane-iterations that trigger a service phase
 };
 
 // Offset of the candidate r + dr from the stop plane along the stop axis (selected without
