@@ -79,7 +79,9 @@ int validate_params(const rp_trace_params *p, bool path_finding);
 // Service-phase batching (see k_trace_wave): a warp services its waiting lanes once the idle
 // lane-iterations summed since its last service reach this threshold.  An FP64 step costs far
 // more than an FP32-mixed one against the same service phase, so FP64 lanes wait less.
-// RP_SERVICE_IDLE / RP_SERVICE_IDLE_F64 override the two.
+// RP_SERVICE_IDLE / RP_SERVICE_IDLE_F64 override the two.  Once a wave's input has run out, a
+// thread hands the rest of its secondary stack to the next launch when at least 2 records
+// remain below the one it takes (RP_FLUSH_MIN overrides the 2).
 inline int env_int(const char *name, int dflt, int lo, int hi)
 {
     const char *v = getenv(name);
@@ -120,6 +122,7 @@ inline rpk::StepParams<P> step_params(const rp_trace_params *p, int axis, float 
     sp.stop_dir = dir;
     sp.max_steps = p->max_steps;
     sp.service_idle = (unsigned int)service_idle(P::kFF);
+    sp.flush_min = env_int("RP_FLUSH_MIN", 2, 1, 1 << 20);
     return sp;
 }
 

@@ -1,13 +1,15 @@
-// trace.cu -- persistent, generation-ordered tracing launches (rp_trace).
+// trace.cu -- persistent tracing launches (rp_trace).
 //
-// Rays of one generation are traced by one persistent launch: every thread claims rays from
-// a global counter (warp-aggregated atomics), traces its ray with the lane state machine of
-// trace_core.cuh and claims the next one as soon as it finishes, so rays with very different
-// step counts keep all lanes busy.  Secondaries cast at boundaries (Sec. 2, boundary module)
-// are appended to a device work queue; the queue segment written by generation g is the
-// input of the launch for generation g + 1.  A launch therefore never waits for work that
-// another thread has still to produce: there are no spin waits anywhere, and the whole call
-// is a fixed sequence of (max_generation + 1) launches on one stream.
+// Every thread of a launch claims rays from a global counter (warp-aggregated atomics),
+// traces its ray with the lane state machine of trace_core.cuh and claims the next one as soon
+// as it finishes, so rays with very different step counts keep all lanes busy.  Secondaries
+// cast at boundaries (Sec. 2, boundary module) go on the thread's own stack and are traced by
+// the same thread, depth first, before it claims new input.  Once the launch's input has run
+// out, new secondaries and the rest of a thread's stack go to a device work queue instead; the
+// queue segment written by launch w is the input of launch w + 1.  Every queued record is at
+// least one generation younger than the launch that wrote it, so max_generation + 1 launches
+// on one stream trace everything, and no launch ever waits for work that another thread has
+// still to produce: there are no spin waits anywhere.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -194,6 +196,32 @@ __device__ __forceinline__ void load_primary(Lane<P> &L, const M &med, const Sin
     }
 }
 
+// Moves m records of a thread's stack to the global queue, which the next launch drains with
+// all its threads; false (nothing moved) when the queue has no room for them.  The room is
+// reserved with a bounded compare-and-swap loop: each failed attempt means another thread's
+// reservation succeeded, and after 64 the records simply stay on the stack.
+__device__ __forceinline__ bool flush_to_queue(const Sinks &sk, const QRec *src, int m)
+{
+    unsigned long long cur = *(volatile unsigned long long *)&sk.ctrl->q_tail, q = 0;
+    bool ok = false;
+    for (int attempt = 0; attempt < 64 && cur + (unsigned long long)m <= sk.q_cap; ++attempt) {
+        const unsigned long long old = atomicCAS(&sk.ctrl->q_tail, cur, cur + (unsigned long long)m);
+        if (old == cur) {
+            q = cur;
+            ok = true;
+            break;
+        }
+        cur = old;
+    }
+    if (!ok) return false;
+    static_assert(sizeof(QRec) % sizeof(long long) == 0, "QRec copies by 8-byte words");
+    constexpr int kWords = (int)(sizeof(QRec) / sizeof(long long));
+    const long long *from = (const long long *)src;
+    long long *to = (long long *)&sk.queue[q];
+    for (int w = 0; w < m * kWords; ++w) to[w] = from[w];
+    return true;
+}
+
 enum { NEXT_NONE = 0, NEXT_TRACE = 1, NEXT_RECORD = 2 };
 
 // Next ray of this wave for the calling lane: NEXT_TRACE, NEXT_RECORD (a finished record to
@@ -205,10 +233,22 @@ __device__ int next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, const
                         const WaveIn &in, int wave, unsigned long long base,
                         unsigned long long count, long long &ahead)
 {
+    // the wave's input has run out once the shared claim counter has passed its end (this
+    // thread's own look-ahead claim can be old: a thread working through its stack claims
+    // nothing)
+    bool input_out = ahead >= (long long)count;
+    if (!input_out)
+        input_out = *(volatile const unsigned long long *)&sk.ctrl->claim[wave] >= count;
     if (L.stk > 0) {
         // depth first: the secondaries this thread cast itself come before new input
-        --L.stk;
-        load_record<P>(L, thread_stack(sk)[L.stk]);
+        const int top = --L.stk;
+        const QRec *stk = thread_stack(sk);
+        // once the input has run out, the rest of the stack (at least sp.flush_min records)
+        // goes to the next launch, where all threads share it: a primary that cast many
+        // secondaries would otherwise keep this one thread busy for all of them while the
+        // others idle
+        if (top >= sp.flush_min && input_out && flush_to_queue(sk, stk, top)) L.stk = 0;
+        load_record<P>(L, stk[top]);
     } else {
         const long long k = ahead;
         if (k >= (long long)count) return NEXT_NONE;
@@ -222,7 +262,7 @@ __device__ int next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, const
     const int32_t st = L.status;
     lane_reset<P, M>(L, med, sp, in.stop);
     L.status = st;
-    L.tail = ahead >= (long long)count;
+    L.tail = input_out || ahead >= (long long)count;
     return st == RP_ST_ALIVE ? NEXT_TRACE : NEXT_RECORD;
 }
 

@@ -817,6 +817,8 @@ struct StepParams {
     float stop_dir;     // +1 or -1: sign of the normal along stop_axis
     long long max_steps;
     unsigned int service_idle;      // idle lane-iterations that trigger a service phase
+    int32_t flush_min;              // stack records left that a thread hands to the queue
+                                    // once the wave's input has run out
 };
 
 // Offset of the candidate r + dr from the stop plane along the stop axis (selected without
