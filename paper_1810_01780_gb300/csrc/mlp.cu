@@ -2,7 +2,9 @@
 // BF16 weights and activations into the tensor cores, FP32 accumulation, FP32 master weights
 // with Adam.  Forward, loss, backward and the optimiser step are all kernels of this file.
 //
-// GEMM: C[M x N] = A[M x K] * B[K x N] with arbitrary strides for A and B (so that the same
+// The three hidden 256 x 256 layers train on the 5th-generation tensor cores
+// (mlp_train_tc.cu).  The thin first (3 -> 256) and last (256 -> 12) layers use the GEMM
+// below: C[M x N] = A[M x K] * B[K x N] with arbitrary strides for A and B (so that the same
 // kernel computes X W, dZ W^T and X^T dZ), 64 x 64 x 32 block tiles staged in shared memory
 // as BF16, four warps of 32 x 32, mma.sync m16n8k16 (bf16 x bf16 -> f32).  Epilogues: bias,
 // bias + GELU (keeping the pre-activation for the backward pass), times GELU'(Z), or split-K
@@ -309,12 +311,22 @@ static int gemm(const GemmArgs &g, cudaStream_t st)
     return RP_OK;
 }
 
-// forward pass of n rows; keeps pre-activations when `train`
+// forward pass of n rows for training, keeping the pre-activations: layers 1..3 (256 -> 256)
+// on the tensor cores, layers 0 (3 -> 256) and 4 (256 -> 12) with the kernel above
 int forward(rp_surrogate_s *s, long long n, const float *x, float *out, bool train,
                    cudaStream_t st)
 {
+    int rc = ensure_pack(s, st);
+    if (rc) return rc;
     const float *h = x;
     for (int l = 0; l < kLayers; ++l) {
+        if (l >= 1 && l <= 3) {
+            if ((rc = tc_dense(true, h, n, s->pack + (l - 1) * kPackW, s->p + layer_b(l), nullptr,
+                               train ? s->Z[l] : nullptr, s->H[l + 1], s->fflag, st)))
+                return rc;
+            h = s->H[l + 1];
+            continue;
+        }
         GemmArgs g;
         memset(&g, 0, sizeof g);
         g.M = (int)n;
@@ -329,7 +341,6 @@ int forward(rp_surrogate_s *s, long long n, const float *x, float *out, bool tra
         g.b_bf16 = 1;
         g.ldc = kDims[l + 1];
         g.bias = s->p + layer_b(l);
-        int rc;
         if (l < kLayers - 1) {
             g.Z = train ? s->Z[l] : nullptr;
             g.H = s->H[l + 1];
@@ -361,6 +372,21 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
     for (int l = kLayers - 1; l >= 0; --l) {
         const int in = kDims[l], outd = kDims[l + 1];
         const float *h = l == 0 ? x : s->H[l];
+        if (l >= 1 && l <= 3) {
+            // hidden 256 x 256 layers on the tensor cores: dW_l = H_l^T g, then
+            // g_{l-1} = (g W_l^T) * GELU'(Z_{l-1})
+            if ((rc = tc_wgrad(h, g_cur, n, s->grad + layer_w(l), s->fflag, st))) return rc;
+            dim3 cg((outd + 127) / 128, 64);
+            k_colsum<<<cg, 128, 0, st>>>(g_cur, n, outd, s->grad + layer_b(l));
+            RP_CUDA_TRY(cudaGetLastError());
+            if ((rc = tc_dense(false, g_cur, n, s->pack_t + (l - 1) * kPackW, nullptr, s->Z[l - 1],
+                               nullptr, g_next, s->fflag, st)))
+                return rc;
+            float *tmp = g_cur;
+            g_cur = g_next;
+            g_next = tmp;
+            continue;
+        }
         // dW_l = H_l^T g  (split over the batch)
         GemmArgs g;
         memset(&g, 0, sizeof g);
@@ -405,7 +431,7 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
     }
     if (loss_host) {
         RP_CUDA_TRY(cudaMemcpyAsync(loss_host, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
-        RP_CUDA_TRY(cudaStreamSynchronize(st));
+        if ((rc = fused_status(s, st))) return rc;  // syncs st
         *loss_host /= (double)n;
     }
     return RP_OK;
@@ -420,6 +446,10 @@ int ensure_pack(rp_surrogate_s *s, cudaStream_t st)
         RP_CUDA_TRY(cudaMalloc(&s->pack, 3 * kPackW + sizeof(float) * kPackF));
         s->pack_version = -1;
     }
+    if (!s->pack_t) {
+        RP_CUDA_TRY(cudaMalloc(&s->pack_t, 3 * kPackW));
+        s->pack_version = -1;
+    }
     if (s->pack_version == s->version) return RP_OK;
     const long long total = 3 * 65536 + kPackF;
     LayerOffs L;
@@ -429,6 +459,8 @@ int ensure_pack(rp_surrogate_s *s, cudaStream_t st)
     }
     k_pack<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(s->p, s->pack, L);
     RP_CUDA_TRY(cudaGetLastError());
+    int rc = tc_pack_backward(s->p, s->pack_t, L.w[1], L.w[2], L.w[3], st);
+    if (rc) return rc;
     s->pack_version = s->version;
     return RP_OK;
 }
@@ -485,6 +517,7 @@ int rp_surrogate_create(const float *params, rp_surrogate_t *out)
     if (e == cudaSuccess) e = cudaMalloc(&s->pb, sizeof(__nv_bfloat16) * np);
     if (e == cudaSuccess) e = cudaMalloc(&s->loss, 2 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&s->fflag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(s->fflag, 0, sizeof(int));
     if (e != cudaSuccess) {
         rp_surrogate_destroy(s);
         return cuda_fail(e, "rp_surrogate_create");
@@ -510,6 +543,7 @@ int rp_surrogate_destroy(rp_surrogate_t s)
     cudaFree(s->pb);
     cudaFree(s->loss);
     cudaFree(s->pack);
+    cudaFree(s->pack_t);
     cudaFree(s->fflag);
     delete s;
     return RP_OK;
@@ -588,7 +622,7 @@ int rp_surrogate_train_step(rp_surrogate_t s, int64_t n, const float *x, const f
     int rc = loss_grad(s, n, x, y, t, loss, st);
     if (rc) return rc;
     if ((rc = adam_step(s, lr, st))) return rc;
-    if (!loss) RP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!loss) return fused_status(s, st);  // syncs st
     return RP_OK;
 }
 
@@ -627,7 +661,7 @@ int rp_surrogate_train(rp_surrogate_t s, int64_t n, const float *x, const float 
     }
     double L = 0.0;
     RP_CUDA_TRY(cudaMemcpyAsync(&L, s->loss + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
-    RP_CUDA_TRY(cudaStreamSynchronize(st));
+    if ((rc = fused_status(s, st))) return rc;  // syncs st
     if (loss) *loss = L;
     return RP_OK;
 }

@@ -24,10 +24,13 @@
 #include <algorithm>
 
 #include "rp_internal.h"
+#include "tc_common.cuh"
 
 namespace rph {
 
 namespace {
+
+using namespace tc;
 
 constexpr int kTile = 128;
 constexpr int kThreads = 512;             // 16 warps: 4 column groups per TMEM lane quarter
@@ -47,53 +50,6 @@ static_assert((kGroups - 1) * kTile * 12 * 4 <= 65536, "layer-4 partial sums reu
 // instruction descriptor: D FP32, A and B BF16, both K-major, N = 256, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) |
                             ((128u >> 4) << 24);
-constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at the maximum SM clock
-
-__device__ __forceinline__ uint32_t su32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// shared-memory matrix descriptor, no swizzle: start, K-direction core stride (lbo), 8-row
-// core stride (sbo), descriptor version 1
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase)
-{
-    const long long t0 = clock64();
-    for (;;) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred P;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, P;\n\t}"
-            : "=r"(ok)
-            : "r"(bar), "r"(phase)
-            : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
-    }
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
-__device__ __forceinline__ uint32_t pack2(float lo, float hi)
-{
-    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&h);
-}
-// byte offset of the 8 consecutive k (k0 % 8 == 0) of row `row` in the A tile
-__device__ __forceinline__ uint32_t a_off(int row, int k0)
-{
-    return (uint32_t)(((k0 >> 3) * 16 + (row >> 3)) * 128 + (row & 7) * 16);
-}
 
 // one hidden layer's packed weights (kWBytes) into the B tile, completion on `bar`
 __device__ __forceinline__ void load_weights(uint32_t b_base, const unsigned char *src, uint32_t bar)
@@ -107,20 +63,6 @@ __device__ __forceinline__ void load_weights(uint32_t b_base, const unsigned cha
                 b_base + c * 32768u),
             "l"(src + c * 32768), "r"(32768u), "r"(bar)
             : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -345,8 +287,8 @@ int fused_status(rp_surrogate_s *s, cudaStream_t st)
     RP_CUDA_TRY(cudaMemcpyAsync(&f, s->fflag, sizeof(int), cudaMemcpyDeviceToHost, st));
     RP_CUDA_TRY(cudaStreamSynchronize(st));
     if (f) {
-        set_error("surrogate inference: a wait of the fused kernel gave up (tensor-core work did "
-                  "not complete)");
+        set_error("surrogate: a bounded wait of a tensor-core kernel gave up (its work did not "
+                  "complete)");
         return RP_ERR_CUDA;
     }
     return RP_OK;

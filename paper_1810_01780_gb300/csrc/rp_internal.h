@@ -25,8 +25,9 @@ struct rp_surrogate_s {
     void *pipe;  // buffers of the surrogate path-finding pipeline (pathfind.cu)
     // inference operands for the fused kernel (mlp_fused.cu), rebuilt when the weights change
     unsigned char *pack;
+    unsigned char *pack_t;  // training: W1..W3 as the backward pass's B images (mlp_train_tc.cu)
     long long version, pack_version;
-    int *fflag;  // set by the fused kernel when a bounded wait gave up
+    int *fflag;  // set by a tensor-core kernel when a bounded wait gave up
 };
 
 struct rp_medium_s {
@@ -160,6 +161,14 @@ void free_pipe(rp_surrogate_s *s);
 int ensure_pack(rp_surrogate_s *s, cudaStream_t st);
 int forward_fused(rp_surrogate_s *s, long long n, const float *x, float *out, cudaStream_t st);
 int fused_status(rp_surrogate_s *s, cudaStream_t st);  // syncs st; RP_ERR_CUDA if flagged
+// training on the tensor cores (mlp_train_tc.cu): the hidden layers' forward (z = A W + b,
+// gelu(z)) or backward data pass (C = g W^T times gelu'(Zin)), and their weight gradients
+int tc_pack_backward(const float *p, unsigned char *img, long long w1, long long w2, long long w3,
+                     cudaStream_t st);
+int tc_dense(bool forward, const float *A, long long n, const unsigned char *Bimg,
+             const float *bias, const float *Zin, float *Zout, float *Out, int *flag,
+             cudaStream_t st);
+int tc_wgrad(const float *H, const float *G, long long n, float *dW, int *flag, cudaStream_t st);
 int run_surrogate_paths(rp_surrogate_s *s, rp_medium_t m, int64_t n, const double *zs,
                         const double *zr, const double *dist, const int32_t *n_angles,
                         const rp_path_params *p, const rp_surrogate_params *sp,
