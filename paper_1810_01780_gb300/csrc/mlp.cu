@@ -1,14 +1,11 @@
 // mlp.cu -- the surrogate network: 3 -> 256 -> 256 -> 256 -> 256 -> 12, GELU (erf form),
-// BF16 weights and activations into the tensor cores, FP32 accumulation, FP32 master weights
-// with Adam.  Forward, loss, backward and the optimiser step are all kernels of this file.
+// BF16 weights and operands, FP32 accumulation, FP32 master weights with Adam: the thin layers'
+// kernels, the loss, the optimiser step, the native training loop and checkpoints.
 //
-// The three hidden 256 x 256 layers train on the 5th-generation tensor cores
-// (mlp_train_tc.cu).  The thin first (3 -> 256) and last (256 -> 12) layers use the GEMM
-// below: C[M x N] = A[M x K] * B[K x N] with arbitrary strides for A and B (so that the same
-// kernel computes X W, dZ W^T and X^T dZ), 64 x 64 x 32 block tiles staged in shared memory
-// as BF16, four warps of 32 x 32, mma.sync m16n8k16 (bf16 x bf16 -> f32).  Epilogues: bias,
-// bias + GELU (keeping the pre-activation for the backward pass), times GELU'(Z), or split-K
-// accumulation with atomics (weight gradients, K = batch).
+// The three hidden 256 x 256 layers run on the 5th-generation tensor cores (mlp_fused.cu for
+// inference, mlp_train_tc.cu for training).  The thin first (3 -> 256) and last (256 -> 12)
+// layers, whose contractions are too narrow for a tensor-core tile, run on the CUDA cores
+// with the same arithmetic: BF16-rounded operands, FP32 products and sums.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -24,24 +21,8 @@ namespace {
 
 constexpr int kLayers = 5;
 constexpr int kDims[kLayers + 1] = {3, 256, 256, 256, 256, 12};
-constexpr int BM = 64, BN = 64, BK = 32, kThreads = 128;
 
-enum { EPI_BIAS = 0, EPI_BIAS_GELU = 1, EPI_GELU_GRAD = 2, EPI_ATOMIC = 3 };
-
-struct GemmArgs {
-    int M, N, K;
-    const float *A;
-    long long sAi, sAk;
-    const void *B;
-    long long sBk, sBj;
-    int b_bf16;
-    float *C;
-    long long ldc;
-    const float *bias;
-    float *Z;  // EPI_BIAS_GELU: pre-activation out (may be null); EPI_GELU_GRAD: Z in
-    float *H;  // EPI_BIAS_GELU: activation out
-    int k_chunk;
-};
+enum { EPI_BIAS = 0, EPI_BIAS_GELU = 1, EPI_GELU_GRAD = 2 };
 
 __device__ __forceinline__ float gelu_f(float x)
 {
@@ -54,115 +35,167 @@ __device__ __forceinline__ float gelu_grad_f(float x)
            x * expf(-0.5f * x * x) * 0.39894228040143268f;
 }
 
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
+// Forward and backward-data passes of the thin layers on the CUDA cores (BF16-rounded
+// operands, FP32 products and sums):
+//   first layer (3 -> 256): z[s][j] = sum_i x[s][i] W0[i][j] + b0[j], keeping z and gelu(z)
+//     (one thread per output element);
+//   last layer (256 -> 12) forward: out[s][o] = sum_i H[s][i] W4[i][o] + b4[o] (one warp per
+//     row, W4 in shared memory, each lane 8 inputs, the 12 sums reduced across the warp);
+//   last layer backward: g[s][i] = (sum_o g4[s][o] W4[i][o]) gelu'(Z3[s][i]) (thread i with
+//     row i of W4 in registers, the rows of g4 staged in shared memory).
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+constexpr int kBwdRows = 32;  // rows of g4 a CTA of k_last_bwd stages at a time
+
+__global__ void __launch_bounds__(256) k_first_fwd(const float *__restrict__ x, long long n,
+                                                   const __nv_bfloat16 *__restrict__ W,
+                                                   const float *__restrict__ b,
+                                                   float *__restrict__ Z, float *__restrict__ H)
 {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= n * 256) return;
+    const long long r = e >> 8;
+    const int j = (int)(e & 255);
+    float z = bf16r(x[3 * r]) * __bfloat162float(W[j]);
+    z = fmaf(bf16r(x[3 * r + 1]), __bfloat162float(W[256 + j]), z);
+    z = fmaf(bf16r(x[3 * r + 2]), __bfloat162float(W[512 + j]), z);
+    z += b[j];
+    if (Z) Z[e] = z;
+    H[e] = gelu_f(z);
 }
 
-template <int EPI>
-__global__ void __launch_bounds__(kThreads) k_gemm(const GemmArgs g)
+__global__ void __launch_bounds__(256) k_last_fwd(const float *__restrict__ H, long long n,
+                                                  const __nv_bfloat16 *__restrict__ W,
+                                                  const float *__restrict__ b,
+                                                  float *__restrict__ out)
 {
-    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + 8];
-    __shared__ __align__(16) __nv_bfloat16 Bt[BN][BK + 8];  // B tile stored n-major
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp >> 1, wn = warp & 1;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    int k_begin = 0, k_end = g.K;
-    if (EPI == EPI_ATOMIC) {
-        k_begin = blockIdx.z * g.k_chunk;
-        k_end = min(g.K, k_begin + g.k_chunk);
+    __shared__ float w[256 * 12];
+    for (int e = threadIdx.x; e < 256 * 12; e += blockDim.x) w[e] = __bfloat162float(W[e]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); r < n;
+         r += warps) {
+        const float4 *src = reinterpret_cast<const float4 *>(H + r * 256 + lane * 8);
+        const float4 a = src[0], c = src[1];
+        const float h[8] = {bf16r(a.x), bf16r(a.y), bf16r(a.z), bf16r(a.w),
+                            bf16r(c.x), bf16r(c.y), bf16r(c.z), bf16r(c.w)};
+        float acc[12];
+#pragma unroll
+        for (int o = 0; o < 12; ++o) acc[o] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int o = 0; o < 12; ++o) acc[o] = fmaf(h[k], w[(lane * 8 + k) * 12 + o], acc[o]);
+#pragma unroll
+        for (int o = 0; o < 12; ++o)
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) acc[o] += __shfl_xor_sync(0xffffffffu, acc[o], d);
+        if (lane == 0) {
+#pragma unroll
+            for (int o = 0; o < 12; ++o) out[r * 12 + o] = acc[o] + b[o];
+        }
     }
-    float acc[2][4][4];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.0f;
-    const bool a_rows = g.sAi == 1;  // A's rows are contiguous: map threads along i
-    const bool b_cols = g.sBj == 1;  // B's columns are contiguous: map threads along j
-    const int gq = lane >> 2, q = lane & 3;
-
-    for (int k0 = k_begin; k0 < k_end; k0 += BK) {
-#pragma unroll 4
-        for (int r = 0; r < (BM * BK) / kThreads; ++r) {
-            const int e = tid + r * kThreads;
-            const int row = a_rows ? (e % BM) : (e / BK), col = a_rows ? (e / BM) : (e % BK);
-            const int i = m0 + row, k = k0 + col;
-            float v = 0.0f;
-            if (i < g.M && k < k_end) v = g.A[(long long)i * g.sAi + (long long)k * g.sAk];
-            As[row][col] = __float2bfloat16_rn(v);
-        }
-#pragma unroll 4
-        for (int r = 0; r < (BN * BK) / kThreads; ++r) {
-            const int e = tid + r * kThreads;
-            const int col = b_cols ? (e % BN) : (e / BK), kr = b_cols ? (e / BN) : (e % BK);
-            const int j = n0 + col, k = k0 + kr;
-            __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
-            if (j < g.N && k < k_end) {
-                const long long o = (long long)k * g.sBk + (long long)j * g.sBj;
-                v = g.b_bf16 ? ((const __nv_bfloat16 *)g.B)[o]
-                             : __float2bfloat16_rn(((const float *)g.B)[o]);
-            }
-            Bt[col][kr] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t af[2][4], bf[4][2];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r = wm * 32 + mt * 16 + gq;
-                af[mt][0] = *(const uint32_t *)&As[r][kk + 2 * q];
-                af[mt][1] = *(const uint32_t *)&As[r + 8][kk + 2 * q];
-                af[mt][2] = *(const uint32_t *)&As[r][kk + 2 * q + 8];
-                af[mt][3] = *(const uint32_t *)&As[r + 8][kk + 2 * q + 8];
-            }
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const int c = wn * 32 + nt * 8 + gq;
-                bf[nt][0] = *(const uint32_t *)&Bt[c][kk + 2 * q];
-                bf[nt][1] = *(const uint32_t *)&Bt[c][kk + 2 * q + 8];
-            }
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bf[nt]);
-        }
-        __syncthreads();
-    }
-    // epilogue: accumulator (row gq / gq+8, columns 2q, 2q+1) of each 16 x 8 tile
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int i = m0 + wm * 32 + mt * 16 + gq + (h >= 2 ? 8 : 0);
-                const int j = n0 + wn * 32 + nt * 8 + 2 * q + (h & 1);
-                if (i >= g.M || j >= g.N) continue;
-                float v = acc[mt][nt][h];
-                const long long o = (long long)i * g.ldc + j;
-                if (EPI == EPI_ATOMIC) {
-                    atomicAdd(&g.C[o], v);
-                } else if (EPI == EPI_BIAS) {
-                    g.C[o] = v + g.bias[j];
-                } else if (EPI == EPI_BIAS_GELU) {
-                    v += g.bias[j];
-                    if (g.Z) g.Z[o] = v;
-                    g.H[o] = gelu_f(v);
-                } else {  // EPI_GELU_GRAD
-                    g.C[o] = v * gelu_grad_f(g.Z[o]);
-                }
-            }
 }
 
-// Loss (per sample: logistic loss of each slot's existence logit + y times half the squared
-// error of its five regression outputs) and its gradient with respect to the outputs.
+__global__ void __launch_bounds__(256) k_last_bwd(const float *__restrict__ G, long long n,
+                                                  const __nv_bfloat16 *__restrict__ W,
+                                                  const float *__restrict__ Zin,
+                                                  float *__restrict__ Gout)
+{
+    __shared__ float gb[kBwdRows * 12];
+    const int i = threadIdx.x;
+    float w[12];
+#pragma unroll
+    for (int o = 0; o < 12; ++o) w[o] = __bfloat162float(W[i * 12 + o]);
+    for (long long r0 = blockIdx.x * (long long)kBwdRows; r0 < n; r0 += (long long)gridDim.x * kBwdRows) {
+        const int rows = (int)min((long long)kBwdRows, n - r0);
+        __syncthreads();
+        for (int e = i; e < kBwdRows * 12; e += 256)
+            gb[e] = e / 12 < rows ? bf16r(G[(r0 + e / 12) * 12 + e % 12]) : 0.0f;
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < rows; ++r) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int o = 0; o < 12; ++o) acc = fmaf(gb[r * 12 + o], w[o], acc);
+            const long long e = (r0 + r) * 256 + i;
+            Gout[e] = acc * gelu_grad_f(Zin[e]);
+        }
+    }
+}
+
+// Weight and bias gradients of the thin layers, on the CUDA cores (BF16-rounded operands,
+// FP32 products and sums, as in the forward pass; bias gradients from the unrounded g):
+//   last layer (256 -> 12): dW[i][o] += sum_s H[s][i] g[s][o], db[o] += sum_s g[s][o]
+//     (thread i; the rows of g staged in shared memory 64 at a time);
+//   first layer (3 -> 256): dW[i][j] += sum_s x[s][i] g[s][j], db[j] += sum_s g[s][j]
+//     (thread j; the rows of x staged in shared memory 64 at a time).
+// Each CTA takes a contiguous range of rows and adds its sums with atomics.
+constexpr int kThinChunk = 64;
+__global__ void __launch_bounds__(256) k_wgrad_last(const float *__restrict__ H,
+                                                    const float *__restrict__ G, long long n,
+                                                    long long per, float *__restrict__ dW,
+                                                    float *__restrict__ db)
+{
+    __shared__ float gr[kThinChunk * 12], gb[kThinChunk * 12];
+    const int i = threadIdx.x;
+    const long long lo = blockIdx.x * per, hi = min(n, lo + per);
+    float acc[12], bs = 0.0f;
+#pragma unroll
+    for (int o = 0; o < 12; ++o) acc[o] = 0.0f;
+    for (long long r0 = lo; r0 < hi; r0 += kThinChunk) {
+        const int rows = (int)min((long long)kThinChunk, hi - r0);
+        __syncthreads();
+        for (int e = i; e < kThinChunk * 12; e += 256) {
+            const float v = e / 12 < rows ? G[(r0 + e / 12) * 12 + e % 12] : 0.0f;
+            gr[e] = v;
+            gb[e] = bf16r(v);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < rows; ++r) {
+            const float h = bf16r(H[(r0 + r) * 256 + i]);
+#pragma unroll
+            for (int o = 0; o < 12; ++o) acc[o] = fmaf(h, gb[r * 12 + o], acc[o]);
+        }
+        if (i < 12)
+            for (int r = 0; r < rows; ++r) bs += gr[r * 12 + i];
+    }
+#pragma unroll
+    for (int o = 0; o < 12; ++o) atomicAdd(&dW[i * 12 + o], acc[o]);
+    if (i < 12) atomicAdd(&db[i], bs);
+}
+__global__ void __launch_bounds__(256) k_wgrad_first(const float *__restrict__ X,
+                                                     const float *__restrict__ G, long long n,
+                                                     long long per, float *__restrict__ dW,
+                                                     float *__restrict__ db)
+{
+    __shared__ float xb[kThinChunk * 3];
+    const int j = threadIdx.x;
+    const long long lo = blockIdx.x * per, hi = min(n, lo + per);
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, s = 0.0f;
+    for (long long r0 = lo; r0 < hi; r0 += kThinChunk) {
+        const int rows = (int)min((long long)kThinChunk, hi - r0);
+        __syncthreads();
+        for (int e = j; e < kThinChunk * 3; e += 256)
+            xb[e] = e / 3 < rows ? bf16r(X[(r0 + e / 3) * 3 + e % 3]) : 0.0f;
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < rows; ++r) {
+            const float g = G[(r0 + r) * 256 + j];
+            s += g;
+            const float b = bf16r(g);
+            a0 = fmaf(xb[r * 3], b, a0);
+            a1 = fmaf(xb[r * 3 + 1], b, a1);
+            a2 = fmaf(xb[r * 3 + 2], b, a2);
+        }
+    }
+    atomicAdd(&dW[j], a0);
+    atomicAdd(&dW[256 + j], a1);
+    atomicAdd(&dW[512 + j], a2);
+    atomicAdd(&db[j], s);
+}
+
 __global__ void k_loss(const float *out, const float *y, const float *t, long long n, float *g,
                        double *loss)
 {
@@ -187,17 +220,6 @@ __global__ void k_loss(const float *out, const float *y, const float *t, long lo
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, (double)L);
 }
 
-// db[j] += sum over rows of g[row, j]
-__global__ void k_colsum(const float *g, long long n, int N, float *db)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
-    const long long per = (n + gridDim.y - 1) / gridDim.y;
-    const long long lo = blockIdx.y * per, hi = lo + per < n ? lo + per : n;
-    float s = 0.0f;
-    for (long long r = lo; r < hi; ++r) s += g[r * N + j];
-    atomicAdd(&db[j], s);
-}
 
 __global__ void k_adam(float *p, __nv_bfloat16 *pb, const float *gr, float *m, float *v,
                        long long n, float lr, float c1, float c2)
@@ -301,58 +323,27 @@ int ensure_acts(rp_surrogate_s *s, long long n)
     return RP_OK;
 }
 
-template <int EPI>
-static int gemm(const GemmArgs &g, cudaStream_t st)
-{
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, 1);
-    if (EPI == EPI_ATOMIC) grid.z = (g.K + g.k_chunk - 1) / g.k_chunk;
-    k_gemm<EPI><<<grid, kThreads, 0, st>>>(g);
-    RP_CUDA_TRY(cudaGetLastError());
-    return RP_OK;
-}
-
 // forward pass of n rows for training, keeping the pre-activations: layers 1..3 (256 -> 256)
-// on the tensor cores, layers 0 (3 -> 256) and 4 (256 -> 12) with the kernel above
+// on the tensor cores, the thin layers 0 (3 -> 256) and 4 (256 -> 12) on the CUDA cores
 int forward(rp_surrogate_s *s, long long n, const float *x, float *out, bool train,
                    cudaStream_t st)
 {
     int rc = ensure_pack(s, st);
     if (rc) return rc;
-    const float *h = x;
-    for (int l = 0; l < kLayers; ++l) {
-        if (l >= 1 && l <= 3) {
-            if ((rc = tc_dense(true, h, n, s->pack + (l - 1) * kPackW, s->p + layer_b(l), nullptr,
-                               train ? s->Z[l] : nullptr, s->H[l + 1], s->fflag, st)))
-                return rc;
-            h = s->H[l + 1];
-            continue;
-        }
-        GemmArgs g;
-        memset(&g, 0, sizeof g);
-        g.M = (int)n;
-        g.N = kDims[l + 1];
-        g.K = kDims[l];
-        g.A = h;
-        g.sAi = kDims[l];
-        g.sAk = 1;
-        g.B = s->pb + layer_w(l);
-        g.sBk = kDims[l + 1];
-        g.sBj = 1;
-        g.b_bf16 = 1;
-        g.ldc = kDims[l + 1];
-        g.bias = s->p + layer_b(l);
-        if (l < kLayers - 1) {
-            g.Z = train ? s->Z[l] : nullptr;
-            g.H = s->H[l + 1];
-            g.C = s->H[l + 1];
-            rc = gemm<EPI_BIAS_GELU>(g, st);
-            h = s->H[l + 1];
-        } else {
-            g.C = out;
-            rc = gemm<EPI_BIAS>(g, st);
-        }
-        if (rc) return rc;
-    }
+    const unsigned elem_grid = (unsigned)((n * 256 + 255) / 256);
+    k_first_fwd<<<elem_grid, 256, 0, st>>>(x, n, s->pb + layer_w(0), s->p + layer_b(0),
+                                           train ? s->Z[0] : nullptr, s->H[1]);
+    RP_CUDA_TRY(cudaGetLastError());
+    for (int l = 1; l <= 3; ++l)
+        if ((rc = tc_dense(true, s->H[l], n, s->pack + (l - 1) * kPackW, s->p + layer_b(l), nullptr,
+                           train ? s->Z[l] : nullptr, s->H[l + 1], s->fflag, st)))
+            return rc;
+    int dev;
+    RP_CUDA_TRY(cudaGetDevice(&dev));
+    const int sms = sm_count(dev);
+    const unsigned row_grid = (unsigned)std::min<long long>((n + 7) / 8, 2LL * sms);
+    k_last_fwd<<<row_grid, 256, 0, st>>>(s->H[4], n, s->pb + layer_w(4), s->p + layer_b(4), out);
+    RP_CUDA_TRY(cudaGetLastError());
     return RP_OK;
 }
 
@@ -368,17 +359,22 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
     float *g_cur = s->g0, *g_next = s->g1;
     k_loss<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->out, y, t, n, g_cur, s->loss);
     RP_CUDA_TRY(cudaGetLastError());
-    const int k_chunk = 512;
+    int dev;
+    RP_CUDA_TRY(cudaGetDevice(&dev));
+    const int sms = sm_count(dev);
+    // thin weight gradients: one 64-row chunk per CTA (the row loops are latency-bound, so
+    // many CTAs beat fewer atomics); last-layer backward: one chunk of kBwdRows rows per CTA
+    (void)sms;
+    const long long thin_per = kThinChunk;
+    const unsigned thin_grid = (unsigned)((n + kThinChunk - 1) / kThinChunk);
+    const unsigned bwd_grid = (unsigned)((n + kBwdRows - 1) / kBwdRows);
     for (int l = kLayers - 1; l >= 0; --l) {
-        const int in = kDims[l], outd = kDims[l + 1];
         const float *h = l == 0 ? x : s->H[l];
         if (l >= 1 && l <= 3) {
-            // hidden 256 x 256 layers on the tensor cores: dW_l = H_l^T g, then
+            // hidden 256 x 256 layers on the tensor cores: dW_l = H_l^T g and db_l, then
             // g_{l-1} = (g W_l^T) * GELU'(Z_{l-1})
-            if ((rc = tc_wgrad(h, g_cur, n, s->grad + layer_w(l), s->fflag, st))) return rc;
-            dim3 cg((outd + 127) / 128, 64);
-            k_colsum<<<cg, 128, 0, st>>>(g_cur, n, outd, s->grad + layer_b(l));
-            RP_CUDA_TRY(cudaGetLastError());
+            if ((rc = tc_wgrad(h, g_cur, n, s->grad + layer_w(l), s->grad + layer_b(l), s->fflag, st)))
+                return rc;
             if ((rc = tc_dense(false, g_cur, n, s->pack_t + (l - 1) * kPackW, nullptr, s->Z[l - 1],
                                nullptr, g_next, s->fflag, st)))
                 return rc;
@@ -387,44 +383,18 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
             g_next = tmp;
             continue;
         }
-        // dW_l = H_l^T g  (split over the batch)
-        GemmArgs g;
-        memset(&g, 0, sizeof g);
-        g.M = in;
-        g.N = outd;
-        g.K = (int)n;
-        g.A = h;
-        g.sAi = 1;
-        g.sAk = in;
-        g.B = g_cur;
-        g.sBk = outd;
-        g.sBj = 1;
-        g.b_bf16 = 0;
-        g.C = s->grad + layer_w(l);
-        g.ldc = outd;
-        g.k_chunk = k_chunk;
-        if ((rc = gemm<EPI_ATOMIC>(g, st))) return rc;
-        dim3 cg((outd + 127) / 128, 64);
-        k_colsum<<<cg, 128, 0, st>>>(g_cur, n, outd, s->grad + layer_b(l));
+        if (l == 0) {
+            k_wgrad_first<<<thin_grid, 256, 0, st>>>(x, g_cur, n, thin_per, s->grad + layer_w(0),
+                                                     s->grad + layer_b(0));
+            RP_CUDA_TRY(cudaGetLastError());
+            break;
+        }
+        // last layer: dW_4, db_4, then g_3 = (g W_4^T) * GELU'(Z_3)
+        k_wgrad_last<<<thin_grid, 256, 0, st>>>(h, g_cur, n, thin_per, s->grad + layer_w(l),
+                                                s->grad + layer_b(l));
         RP_CUDA_TRY(cudaGetLastError());
-        if (l == 0) break;
-        // g_{l-1} = (g W_l^T) * GELU'(Z_{l-1})
-        GemmArgs d;
-        memset(&d, 0, sizeof d);
-        d.M = (int)n;
-        d.N = in;
-        d.K = outd;
-        d.A = g_cur;
-        d.sAi = outd;
-        d.sAk = 1;
-        d.B = s->pb + layer_w(l);
-        d.sBk = 1;
-        d.sBj = outd;
-        d.b_bf16 = 1;
-        d.C = g_next;
-        d.ldc = in;
-        d.Z = s->Z[l - 1];
-        if ((rc = gemm<EPI_GELU_GRAD>(d, st))) return rc;
+        k_last_bwd<<<bwd_grid, 256, 0, st>>>(g_cur, n, s->pb + layer_w(l), s->Z[l - 1], g_next);
+        RP_CUDA_TRY(cudaGetLastError());
         float *tmp = g_cur;
         g_cur = g_next;
         g_next = tmp;

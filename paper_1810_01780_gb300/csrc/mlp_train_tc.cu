@@ -13,7 +13,8 @@
 //     128), N = out, K = rows.  A CTA runs over chunks of 128 rows, staging H^T and g^T as
 //     BF16 K-major images (each thread gathers 8 rows of one column into a 16-byte core row),
 //     accumulating both halves in tensor memory (512 columns), and adds its sums to dW with
-//     atomics at the end.
+//     vector atomics at the end; the bias gradient (column sums of g) comes along from the
+//     staging loads.
 // Arithmetic is that of the CUDA-core GEMMs they replace: BF16 operands, FP32 products and
 // sums, FP32 bias, GELU and GELU'.  Every mbarrier wait is bounded; a CTA that gives up sets the
 // error flag, waits (bounded) for its work in flight, frees its tensor memory and returns.
@@ -212,7 +213,7 @@ constexpr int kChunk = 128;  // rows (K) per chunk
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_wgrad(const float *__restrict__ H, const float *__restrict__ G, long long n,
-               float *__restrict__ dW, int *flag)
+               float *__restrict__ dW, float *__restrict__ db, int *flag)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + WG_BAR);  // MMAs done
@@ -241,6 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t ph = 0;
     bool mma_pending = false, failed = false;
     const int col = tid & 255, kc_base = tid >> 8;  // staging: column and first 8-row chunk
+    float gsum = 0.0f;  // this thread's part of the bias gradient sum_s g[s][col]
     int it = 0;
     for (long long chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x, ++it) {
         const long long r0 = chunk * kChunk;
@@ -254,6 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const long long r = r0 + kc * 8 + e;
                 h[e] = r < n ? __ldg(H + r * 256 + col) : 0.0f;
                 g[e] = r < n ? __ldg(G + r * 256 + col) : 0.0f;
+                gsum += g[e];
             }
             const int half = col >> 7, m = col & 127;
             *reinterpret_cast<uint4 *>(sm + WG_A + half * 32768 + (kc * 16 + (m >> 3)) * 128 + (m & 7) * 16) =
@@ -296,10 +299,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int tcol = ch * 128 + c * 32, n0 = tcol - half * 256;
             uint32_t v[32];
             tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)tcol, v);
-            float *d = dW + (long long)m * 256 + n0;
+            float *d = dW + (long long)m * 256 + n0;  // 16-byte aligned: n0 % 32 == 0
 #pragma unroll
-            for (int j = 0; j < 32; ++j) atomicAdd(d + j, __uint_as_float(v[j]));
+            for (int j = 0; j < 32; j += 4)
+                asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(d + j),
+                             "f"(__uint_as_float(v[j])), "f"(__uint_as_float(v[j + 1])),
+                             "f"(__uint_as_float(v[j + 2])), "f"(__uint_as_float(v[j + 3]))
+                             : "memory");
         }
+        atomicAdd(db + col, gsum);
     }
     if (failed && tid == 0) {
         atomicExch(flag, 1);
@@ -357,7 +365,8 @@ int tc_dense(bool forward, const float *A, long long n, const unsigned char *Bim
     return RP_OK;
 }
 
-int tc_wgrad(const float *H, const float *G, long long n, float *dW, int *flag, cudaStream_t st)
+int tc_wgrad(const float *H, const float *G, long long n, float *dW, float *db, int *flag,
+             cudaStream_t st)
 {
     if (n <= 0) return RP_OK;
     int dev;
@@ -368,7 +377,7 @@ int tc_wgrad(const float *H, const float *G, long long n, float *dW, int *flag, 
     const unsigned grid = (unsigned)std::min<long long>(want, (long long)sm_count(dev));
     RP_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)WG_TOTAL));
-    k_tc_wgrad<<<grid, kThreads, WG_TOTAL, st>>>(H, G, n, dW, flag);
+    k_tc_wgrad<<<grid, kThreads, WG_TOTAL, st>>>(H, G, n, dW, db, flag);
     RP_CUDA_TRY(cudaGetLastError());
     return RP_OK;
 }

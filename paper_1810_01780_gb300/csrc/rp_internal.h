@@ -168,7 +168,8 @@ int tc_pack_backward(const float *p, unsigned char *img, long long w1, long long
 int tc_dense(bool forward, const float *A, long long n, const unsigned char *Bimg,
              const float *bias, const float *Zin, float *Zout, float *Out, int *flag,
              cudaStream_t st);
-int tc_wgrad(const float *H, const float *G, long long n, float *dW, int *flag, cudaStream_t st);
+int tc_wgrad(const float *H, const float *G, long long n, float *dW, float *db, int *flag,
+             cudaStream_t st);
 int run_surrogate_paths(rp_surrogate_s *s, rp_medium_t m, int64_t n, const double *zs,
                         const double *zr, const double *dist, const int32_t *n_angles,
                         const rp_path_params *p, const rp_surrogate_params *sp,
