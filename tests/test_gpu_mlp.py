@@ -71,6 +71,28 @@ def test_loss_and_gradients_match_oracle(rp):
         assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b) + 1e-6, l
 
 
+@pytest.mark.parametrize("n", [1, 1000, 70_001])
+def test_gradients_match_oracle_at_ragged_sizes(rp, n):
+    """Row counts that leave partial tiles (128 rows), partial weight-gradient chunks (128 rows,
+    several per CTA at 70,001) and partial thin-layer chunks (64 rows)."""
+    net = rp.Surrogate(seed=17)
+    X, y, t = _batch(n, 18)
+    L, g = net.loss_grad(X, y, t)
+    g = g.cpu().numpy()
+    Wo, bo = _oracle_params(net.get_params())
+    Lr, dW, db = mlp.grads(Wo, bo, X.astype(np.float64), y.astype(np.float64),
+                           t.astype(np.float64).reshape(-1, 2, 5))
+    assert abs(L - Lr) <= 2e-2 * abs(Lr)
+    gW, gb = W.mlp_unflatten(g)
+    for l in range(5):
+        a, b = gW[l].ravel().astype(np.float64), dW[l].ravel()
+        assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b) + 1e-9, l
+        if n > 1:
+            assert a @ b / (np.linalg.norm(a) * np.linalg.norm(b)) >= 0.998, l
+        a, b = gb[l].astype(np.float64), db[l]
+        assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b) + 1e-6, l
+
+
 def test_adam_step_matches_oracle_and_training_learns(rp):
     import torch
 
@@ -125,7 +147,7 @@ def test_fused_inference_matches_oracle_with_bf16_activations(rp, n):
 
 def test_fused_inference_agrees_with_training_forward(rp):
     """The loss of the fused kernel's outputs (computed by the oracle's loss) equals the loss
-    that the training path's own forward pass (mma.sync GEMMs) reports."""
+    that the training path's own forward pass (its per-layer kernels) reports."""
     import torch
 
     net = rp.Surrogate(seed=13)
