@@ -103,10 +103,17 @@ def test_adam_step_matches_oracle_and_training_learns(rp):
     _, g = net.loss_grad(X, y, t)
     net.train_step(xd, yd, td, 1e-3)
     p1 = net.get_params()
-    # first Adam step: p1 = p0 - lr * g / (|g| + eps) elementwise (bias-corrected moments)
+    # first Adam step: p1 = p0 - lr * g / (|g| + eps) elementwise (bias-corrected moments m = g,
+    # v = g^2), so no parameter moves by more than lr.  The gradient is summed with atomics in
+    # no fixed order, so train_step's own evaluation differs from g in the last bits; where |g|
+    # is near eps that changes g / (|g| + eps), so the formula is checked where |g| >= 1e-6 and
+    # the bound everywhere.
     g = g.cpu().numpy().astype(np.float64)
     want = p0 - 1e-3 * g / (np.abs(g) + 1e-8)
-    assert np.max(np.abs(p1 - want)) <= 1e-6 + 1e-3 * 1e-3
+    big = np.abs(g) >= 1e-6
+    assert big.mean() > 0.5
+    assert np.max(np.abs(p1 - want)[big]) <= 1e-6 + 1e-3 * 1e-3
+    assert np.max(np.abs(p1.astype(np.float64) - p0)) <= 1e-3 * (1 + 1e-6) + 1e-7
     # a smooth target the network can fit: the loss must fall several-fold
     rng = np.random.default_rng(7)
     Xs = rng.uniform(-1, 1, (8192, 3)).astype(np.float32)
