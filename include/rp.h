@@ -166,11 +166,11 @@ typedef struct {
     int64_t max_steps;
 } rp_trace_params;
 
-/* Finished rays.  Primary i is written at index i; secondaries take the following indices
- * in the order they are created (the order between rays of one generation is not
- * deterministic).  Arrays of length `capacity` (pos/dir: (3, capacity)); every pointer except
- * end_pos may be NULL to skip that field.  A secondary is identified by (parent, seq): seq is
- * the index of the split on the parent that cast it. */
+/* Finished rays.  Primary i is written at index i; secondaries take the following indices as
+ * they are cast, in no fixed order (each record's content does not depend on it).  Arrays of
+ * length `capacity` (pos/dir: (3, capacity)); every pointer except end_pos may be NULL to skip
+ * that field.  A secondary is identified by (parent, seq): seq is the index of the split on the
+ * parent that cast it. */
 typedef struct {
     int64_t capacity;
     double *end_pos, *end_dir, *path, *time, *amp;
@@ -202,11 +202,17 @@ typedef struct {
     double warp_end_ms[3];   /* first launch: earliest, median and last warp end [ms] */
 } rp_stats;
 
-/* Traces in->n primaries and every secondary they spawn, in one persistent launch per ray
- * generation (max_generation + 1 launches).  `rx` and `hits` may be NULL, `stats` may be
- * NULL.  Returns RP_OK, RP_ERR_INVALID_ARG (parameters, null arrays, capacity < n),
- * RP_ERR_OVERFLOW (out, queue or hit capacity exceeded: rp_stats holds the sizes needed;
- * everything that fitted was written), RP_ERR_OOM, RP_ERR_CUDA. */
+/* Traces in->n primaries and every secondary they spawn, in max_generation + 1 persistent
+ * launches: a thread traces the secondaries it casts itself until the launch's input runs out;
+ * after that they go to a device queue that the next launch drains.  `rx` and `hits` may be
+ * NULL, `stats` may be NULL.  Returns RP_OK, RP_ERR_INVALID_ARG (parameters, null arrays,
+ * capacity < n), RP_ERR_OVERFLOW (out, queue or hit capacity exceeded: rp_stats holds the
+ * sizes needed; everything that fitted was written), RP_ERR_OOM, RP_ERR_CUDA.
+ * Scheduling knobs, read from the environment at each call (they change speed, not any ray's
+ * record): RP_SERVICE_IDLE (192) and RP_SERVICE_IDLE_F64 (8), the idle lane-iterations after
+ * which a warp serves its parked lanes (boundary splits, finished rays) in FP32-mixed and FP64
+ * mode; RP_FLUSH_MIN (2), the stacked secondaries a thread hands to the next launch once the
+ * input has run out. */
 int rp_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp_trace_params *p,
              rp_ray_out *out, rp_hits *hits, rp_stats *stats, void *stream);
 
