@@ -126,74 +126,86 @@ __global__ void __launch_bounds__(256) k_last_bwd(const float *__restrict__ G, l
 
 // Weight and bias gradients of the thin layers, on the CUDA cores (BF16-rounded operands,
 // FP32 products and sums, as in the forward pass; bias gradients from the unrounded g):
-//   last layer (256 -> 12): dW[i][o] += sum_s H[s][i] g[s][o], db[o] += sum_s g[s][o]
-//     (thread i; the rows of g staged in shared memory 64 at a time);
-//   first layer (3 -> 256): dW[i][j] += sum_s x[s][i] g[s][j], db[j] += sum_s g[s][j]
-//     (thread j; the rows of x staged in shared memory 64 at a time).
-// Each CTA takes a contiguous range of rows and adds its sums with atomics.
+//   last layer (256 -> 12): dW[i][o] = sum_s H[s][i] g[s][o], db[o] = sum_s g[s][o]
+//     (thread i; the CTA's rows of g staged in shared memory);
+//   first layer (3 -> 256): dW[i][j] = sum_s x[s][i] g[s][j], db[j] = sum_s g[s][j]
+//     (thread j; the CTA's rows of x staged in shared memory).
+// Each CTA takes kThinChunk rows and writes its sums to its row of a partial-sum buffer
+// (dW then db, kThinPart floats at most); k_sum_parts adds the rows in a fixed order, so
+// these gradients do not depend on scheduling.
 constexpr int kThinChunk = 64;
+constexpr int kThinPart = 256 * 12 + 12 > 3 * 256 + 256 ? 256 * 12 + 12 : 3 * 256 + 256;
 __global__ void __launch_bounds__(256) k_wgrad_last(const float *__restrict__ H,
                                                     const float *__restrict__ G, long long n,
-                                                    long long per, float *__restrict__ dW,
-                                                    float *__restrict__ db)
+                                                    float *__restrict__ part)
 {
     __shared__ float gr[kThinChunk * 12], gb[kThinChunk * 12];
     const int i = threadIdx.x;
-    const long long lo = blockIdx.x * per, hi = min(n, lo + per);
-    float acc[12], bs = 0.0f;
+    const long long r0 = (long long)blockIdx.x * kThinChunk;
+    const int rows = (int)min((long long)kThinChunk, n - r0);
+    for (int e = i; e < kThinChunk * 12; e += 256) {
+        const float v = e / 12 < rows ? G[(r0 + e / 12) * 12 + e % 12] : 0.0f;
+        gr[e] = v;
+        gb[e] = bf16r(v);
+    }
+    __syncthreads();
+    float acc[12];
 #pragma unroll
     for (int o = 0; o < 12; ++o) acc[o] = 0.0f;
-    for (long long r0 = lo; r0 < hi; r0 += kThinChunk) {
-        const int rows = (int)min((long long)kThinChunk, hi - r0);
-        __syncthreads();
-        for (int e = i; e < kThinChunk * 12; e += 256) {
-            const float v = e / 12 < rows ? G[(r0 + e / 12) * 12 + e % 12] : 0.0f;
-            gr[e] = v;
-            gb[e] = bf16r(v);
-        }
-        __syncthreads();
 #pragma unroll 4
-        for (int r = 0; r < rows; ++r) {
-            const float h = bf16r(H[(r0 + r) * 256 + i]);
+    for (int r = 0; r < rows; ++r) {
+        const float h = bf16r(H[(r0 + r) * 256 + i]);
 #pragma unroll
-            for (int o = 0; o < 12; ++o) acc[o] = fmaf(h, gb[r * 12 + o], acc[o]);
-        }
-        if (i < 12)
-            for (int r = 0; r < rows; ++r) bs += gr[r * 12 + i];
+        for (int o = 0; o < 12; ++o) acc[o] = fmaf(h, gb[r * 12 + o], acc[o]);
     }
+    float *p = part + (size_t)blockIdx.x * kThinPart;
 #pragma unroll
-    for (int o = 0; o < 12; ++o) atomicAdd(&dW[i * 12 + o], acc[o]);
-    if (i < 12) atomicAdd(&db[i], bs);
+    for (int o = 0; o < 12; ++o) p[i * 12 + o] = acc[o];
+    if (i < 12) {
+        float s = 0.0f;
+        for (int r = 0; r < rows; ++r) s += gr[r * 12 + i];
+        p[256 * 12 + i] = s;
+    }
 }
 __global__ void __launch_bounds__(256) k_wgrad_first(const float *__restrict__ X,
                                                      const float *__restrict__ G, long long n,
-                                                     long long per, float *__restrict__ dW,
-                                                     float *__restrict__ db)
+                                                     float *__restrict__ part)
 {
     __shared__ float xb[kThinChunk * 3];
     const int j = threadIdx.x;
-    const long long lo = blockIdx.x * per, hi = min(n, lo + per);
+    const long long r0 = (long long)blockIdx.x * kThinChunk;
+    const int rows = (int)min((long long)kThinChunk, n - r0);
+    for (int e = j; e < kThinChunk * 3; e += 256)
+        xb[e] = e / 3 < rows ? bf16r(X[(r0 + e / 3) * 3 + e % 3]) : 0.0f;
+    __syncthreads();
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, s = 0.0f;
-    for (long long r0 = lo; r0 < hi; r0 += kThinChunk) {
-        const int rows = (int)min((long long)kThinChunk, hi - r0);
-        __syncthreads();
-        for (int e = j; e < kThinChunk * 3; e += 256)
-            xb[e] = e / 3 < rows ? bf16r(X[(r0 + e / 3) * 3 + e % 3]) : 0.0f;
-        __syncthreads();
 #pragma unroll 4
-        for (int r = 0; r < rows; ++r) {
-            const float g = G[(r0 + r) * 256 + j];
-            s += g;
-            const float b = bf16r(g);
-            a0 = fmaf(xb[r * 3], b, a0);
-            a1 = fmaf(xb[r * 3 + 1], b, a1);
-            a2 = fmaf(xb[r * 3 + 2], b, a2);
-        }
+    for (int r = 0; r < rows; ++r) {
+        const float g = G[(r0 + r) * 256 + j];
+        s += g;
+        const float b = bf16r(g);
+        a0 = fmaf(xb[r * 3], b, a0);
+        a1 = fmaf(xb[r * 3 + 1], b, a1);
+        a2 = fmaf(xb[r * 3 + 2], b, a2);
     }
-    atomicAdd(&dW[j], a0);
-    atomicAdd(&dW[256 + j], a1);
-    atomicAdd(&dW[512 + j], a2);
-    atomicAdd(&db[j], s);
+    float *p = part + (size_t)blockIdx.x * kThinPart;
+    p[j] = a0;
+    p[256 + j] = a1;
+    p[512 + j] = a2;
+    p[768 + j] = s;
+}
+// dW[e] += sum over CTAs c of part[c][e] for e < nw, and db[e - nw] for nw <= e < nw + nb
+__global__ void k_sum_parts(const float *__restrict__ part, int n_parts, int nw, int nb,
+                            float *__restrict__ dW, float *__restrict__ db)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nw + nb) return;
+    float s = 0.0f;
+    for (int c = 0; c < n_parts; ++c) s += part[(size_t)c * kThinPart + e];
+    if (e < nw)
+        dW[e] += s;
+    else
+        db[e - nw] += s;
 }
 
 __global__ void k_loss(const float *out, const float *y, const float *t, long long n, float *g,
@@ -304,7 +316,8 @@ static void free_acts(rp_surrogate_s *s)
     cudaFree(s->out);
     cudaFree(s->g0);
     cudaFree(s->g1);
-    s->out = s->g0 = s->g1 = nullptr;
+    cudaFree(s->part);
+    s->out = s->g0 = s->g1 = s->part = nullptr;
     s->cap = 0;
 }
 
@@ -319,6 +332,7 @@ int ensure_acts(rp_surrogate_s *s, long long n)
     RP_CUDA_TRY(cudaMalloc(&s->out, sizeof(float) * cap * 12));
     RP_CUDA_TRY(cudaMalloc(&s->g0, sizeof(float) * cap * 256));
     RP_CUDA_TRY(cudaMalloc(&s->g1, sizeof(float) * cap * 256));
+    RP_CUDA_TRY(cudaMalloc(&s->part, sizeof(float) * (size_t)((cap + kThinChunk - 1) / kThinChunk) * kThinPart));
     s->cap = cap;
     return RP_OK;
 }
@@ -362,10 +376,9 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
     int dev;
     RP_CUDA_TRY(cudaGetDevice(&dev));
     const int sms = sm_count(dev);
-    // thin weight gradients: one 64-row chunk per CTA (the row loops are latency-bound, so
-    // many CTAs beat fewer atomics); last-layer backward: one chunk of kBwdRows rows per CTA
+    // thin weight gradients: one 64-row chunk per CTA, then a fixed-order sum of the CTAs'
+    // partial sums; last-layer backward: one chunk of kBwdRows rows per CTA
     (void)sms;
-    const long long thin_per = kThinChunk;
     const unsigned thin_grid = (unsigned)((n + kThinChunk - 1) / kThinChunk);
     const unsigned bwd_grid = (unsigned)((n + kBwdRows - 1) / kBwdRows);
     for (int l = kLayers - 1; l >= 0; --l) {
@@ -384,14 +397,16 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
             continue;
         }
         if (l == 0) {
-            k_wgrad_first<<<thin_grid, 256, 0, st>>>(x, g_cur, n, thin_per, s->grad + layer_w(0),
-                                                     s->grad + layer_b(0));
+            k_wgrad_first<<<thin_grid, 256, 0, st>>>(x, g_cur, n, s->part);
+            k_sum_parts<<<(3 * 256 + 256 + 255) / 256, 256, 0, st>>>(
+                s->part, (int)thin_grid, 3 * 256, 256, s->grad + layer_w(0), s->grad + layer_b(0));
             RP_CUDA_TRY(cudaGetLastError());
             break;
         }
         // last layer: dW_4, db_4, then g_3 = (g W_4^T) * GELU'(Z_3)
-        k_wgrad_last<<<thin_grid, 256, 0, st>>>(h, g_cur, n, thin_per, s->grad + layer_w(l),
-                                                s->grad + layer_b(l));
+        k_wgrad_last<<<thin_grid, 256, 0, st>>>(h, g_cur, n, s->part);
+        k_sum_parts<<<(256 * 12 + 12 + 255) / 256, 256, 0, st>>>(
+            s->part, (int)thin_grid, 256 * 12, 12, s->grad + layer_w(l), s->grad + layer_b(l));
         RP_CUDA_TRY(cudaGetLastError());
         k_last_bwd<<<bwd_grid, 256, 0, st>>>(g_cur, n, s->pb + layer_w(l), s->Z[l - 1], g_next);
         RP_CUDA_TRY(cudaGetLastError());

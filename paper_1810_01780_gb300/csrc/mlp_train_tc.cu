@@ -2,19 +2,20 @@
 // tensor cores (tcgen05).
 //
 // Two kernels cover the three hidden 256 -> 256 layers:
-//   k_tc_dense<EPI>: C[128 rows x 256] = A[128 x 256] B^T per CTA (one row tile each), with the
-//     FP32 rows of A converted to BF16 into the no-swizzle K-major image in shared memory, the
-//     packed BF16 B image (256 n x 256 k, 128 KB) brought in by bulk copy, 16 tcgen05.mma
-//     (M 128, N 256, K 16) into a 256-column tensor-memory accumulator, and an epilogue per
+//   k_tc_dense<EPI>: C[128 rows x 128 columns] = A[128 x 256] B^T per CTA (one row tile and one
+//     half of the 256 output columns each), with the FP32 rows of A converted to BF16 into the
+//     no-swizzle K-major image in shared memory, the packed BF16 B image (256 n x 256 k, 128 KB)
+//     brought in by bulk copy, 16 tcgen05.mma (M 128, N 128, K 16, reading the half's n-cores)
+//     into a 128-column tensor-memory accumulator, and an epilogue per
 //     row: forward (EPI_FWD) z = C + b, keeping z and gelu(z); backward (EPI_BWD)
 //     C * gelu'(z) of the layer below.  Forward takes B[n][k] = W[k][n] (the inference
 //     image), backward B[n][k] = W[n][k] (so that C = g W^T).
 //   k_tc_wgrad: dW[in][out] += sum over rows s of H[s][in] g[s][out]: M = in (two halves of
-//     128), N = out, K = rows.  A CTA runs over chunks of 128 rows, staging H^T and g^T as
-//     BF16 K-major images (each thread gathers 8 rows of one column into a 16-byte core row),
-//     accumulating both halves in tensor memory (512 columns), and adds its sums to dW with
-//     vector atomics at the end; the bias gradient (column sums of g) comes along from the
-//     staging loads.
+//     128), N = out (one half of 128 per CTA), K = rows.  A CTA runs over chunks of 128 rows,
+//     staging H^T and its half of g^T as BF16 K-major images (each thread gathers 8 rows of one
+//     column into a 16-byte core row), accumulating both M halves in tensor memory (256
+//     columns), and adds its sums to dW with vector atomics at the end; the bias gradient
+//     (column sums of g) comes along from the staging loads.
 // Arithmetic is that of the CUDA-core GEMMs they replace: BF16 operands, FP32 products and
 // sums, FP32 bias, GELU and GELU'.  Every mbarrier wait is bounded; a CTA that gives up sets the
 // error flag, waits (bounded) for its work in flight, frees its tensor memory and returns.
@@ -37,8 +38,9 @@ constexpr uint32_t kImgB = 256u * 256u * 2u;  // a packed 256 x 256 BF16 B image
 
 enum { EPI_FWD = 0, EPI_BWD = 1 };
 
-// instruction descriptor: D FP32, A and B BF16, both K-major, N = 256, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) |
+// instruction descriptor: D FP32, A and B BF16, both K-major, N = 128, M = 128 (each CTA
+// computes one half of the 256 output columns)
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) |
                             ((128u >> 4) << 24);
 
 __device__ __forceinline__ float gelu_grad(float x)
@@ -83,6 +85,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t bar_ld = su32(&bar[0]), bar_mma = su32(&bar[1]);
     const uint32_t a_base = su32(sm + DN_A), b_base = su32(sm + DN_B);
     const long long g0 = (long long)blockIdx.x * kRows;
+    const int half = (int)blockIdx.y;  // output columns 128 half .. + 127
 
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_ld) : "memory");
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)),
-                     "r"(256u)
+                     "r"(128u)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -128,10 +131,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         if (mbar_wait(bar_ld, 0)) {
             ld_pending = false;
+            // the half's 16 n-cores of each k-core row of the B image: start 2048 B further
 #pragma unroll
             for (int s = 0; s < 16; ++s)
                 mma_f16(tmem, sdesc(a_base + s * 4096u, 2048u, 128u),
-                        sdesc(b_base + s * 8192u, 4096u, 128u), (uint32_t)s);
+                        sdesc(b_base + (uint32_t)half * 2048u + s * 8192u, 4096u, 128u), (uint32_t)s);
             mma_commit(bar_mma);
             mma_pending = true;
         } else {
@@ -148,11 +152,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (tid == 0) mma_pending = false;
         const int q = warp & 3, ch = warp >> 2, row = q * 32 + lane;
         const long long gr = g0 + row;
-#pragma unroll 1
-        for (int c = 0; c < 2; ++c) {
-            const int col0 = ch * 64 + c * 32;
+        {
+            const int tcol = ch * 32, col0 = half * 128 + tcol;
             uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, v);
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)tcol, v);
             if (gr < n) {
                 float *o = Out + gr * 256 + col0;
                 if (EPI == EPI_FWD) {
@@ -197,20 +200,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (warp == 0) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u)
                      : "memory");
     }
 }
 
 // shared memory map of k_tc_wgrad (bytes): A = H^T chunk as two 128 x 128 halves (32 KB each;
-// core (k/8, m/8) at ((k/8) * 16 + m/8) * 128), B = g^T chunk, 256 x 128 (64 KB; core (k/8, n/8)
-// at ((k/8) * 32 + n/8) * 128)
+// core (k/8, m/8) at ((k/8) * 16 + m/8) * 128), B = the CTA's 128 columns of g^T, 128 x 128
+// (32 KB, same core layout)
 constexpr uint32_t WG_A = 0;
 constexpr uint32_t WG_B = 65536;
-constexpr uint32_t WG_BAR = WG_B + 65536;
+constexpr uint32_t WG_BAR = WG_B + 32768;
 constexpr uint32_t WG_TOTAL = WG_BAR + 32;
 constexpr int kChunk = 128;  // rows (K) per chunk
 
+// dW[:, 128 h .. 128 h + 127] (h = blockIdx.y) over the chunks blockIdx.x, + gridDim.x, ...
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_wgrad(const float *__restrict__ H, const float *__restrict__ G, long long n,
                float *__restrict__ dW, float *__restrict__ db, int *flag)
@@ -223,6 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t bar_mma = su32(&bar[0]);
     const uint32_t a_base = su32(sm + WG_A), b_base = su32(sm + WG_B);
     const long long n_chunks = (n + kChunk - 1) / kChunk;
+    const int half = (int)blockIdx.y;
 
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_mma) : "memory");
@@ -231,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)),
-                     "r"(512u)
+                     "r"(256u)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -241,27 +246,38 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = *slot;
     uint32_t ph = 0;
     bool mma_pending = false, failed = false;
-    const int col = tid & 255, kc_base = tid >> 8;  // staging: column and first 8-row chunk
-    float gsum = 0.0f;  // this thread's part of the bias gradient sum_s g[s][col]
+    // staging: H^T, column col (all 256) and 8-row chunks kc_a + 2 i; g^T, column gcol of the
+    // half and 8-row chunks kc_g + 4 i
+    const int col = tid & 255, kc_a = tid >> 8;
+    const int gl = tid & 127, gcol = half * 128 + gl, kc_g = tid >> 7;
+    float gsum = 0.0f;  // this thread's part of the bias gradient sum_s g[s][gcol]
     int it = 0;
     for (long long chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x, ++it) {
         const long long r0 = chunk * kChunk;
-        // gather 8 rows of one column into a 16-byte core row, for H^T and for g^T
 #pragma unroll 2
         for (int i = 0; i < 8; ++i) {
-            const int kc = kc_base + 2 * i;  // 8-row chunk 0..15
-            float h[8], g[8];
+            const int kc = kc_a + 2 * i;  // 8-row chunk 0..15
+            float h[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const long long r = r0 + kc * 8 + e;
                 h[e] = r < n ? __ldg(H + r * 256 + col) : 0.0f;
-                g[e] = r < n ? __ldg(G + r * 256 + col) : 0.0f;
+            }
+            const int mh = col >> 7, m = col & 127;
+            *reinterpret_cast<uint4 *>(sm + WG_A + mh * 32768 + (kc * 16 + (m >> 3)) * 128 + (m & 7) * 16) =
+                make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+        }
+#pragma unroll 2
+        for (int i = 0; i < 4; ++i) {
+            const int kc = kc_g + 4 * i;
+            float g[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const long long r = r0 + kc * 8 + e;
+                g[e] = r < n ? __ldg(G + r * 256 + gcol) : 0.0f;
                 gsum += g[e];
             }
-            const int half = col >> 7, m = col & 127;
-            *reinterpret_cast<uint4 *>(sm + WG_A + half * 32768 + (kc * 16 + (m >> 3)) * 128 + (m & 7) * 16) =
-                make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
-            *reinterpret_cast<uint4 *>(sm + WG_B + (kc * 32 + (col >> 3)) * 128 + (col & 7) * 16) =
+            *reinterpret_cast<uint4 *>(sm + WG_B + (kc * 16 + (gl >> 3)) * 128 + (gl & 7) * 16) =
                 make_uint4(pack2(g[0], g[1]), pack2(g[2], g[3]), pack2(g[4], g[5]), pack2(g[6], g[7]));
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -270,12 +286,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_after();
         if (tid == 0) {
 #pragma unroll
-            for (int half = 0; half < 2; ++half)
+            for (int mh = 0; mh < 2; ++mh)
 #pragma unroll
                 for (int s = 0; s < 8; ++s)
-                    mma_f16(tmem + (uint32_t)(half * 256),
-                            sdesc(a_base + half * 32768u + s * 4096u, 2048u, 128u),
-                            sdesc(b_base + s * 8192u, 4096u, 128u), (uint32_t)(it > 0 || s > 0));
+                    mma_f16(tmem + (uint32_t)(mh * 128),
+                            sdesc(a_base + mh * 32768u + s * 4096u, 2048u, 128u),
+                            sdesc(b_base + s * 4096u, 2048u, 128u), (uint32_t)(it > 0 || s > 0));
             mma_commit(bar_mma);
             mma_pending = true;
         }
@@ -291,12 +307,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (tid == 0) mma_pending = false;
     }
     if (!failed && it > 0) {
-        // rows m = 128 half + 32 q + lane, columns: group ch covers 128 of the 512 TMEM columns
-        const int q = warp & 3, ch = warp >> 2, half = ch >> 1;
-        const int m = half * 128 + q * 32 + lane;
+        // TMEM column t: M half t / 128, output column 128 half + t % 128; rows m of the half
+        // are the lanes (lane quarter q = warp % 4)
+        const int q = warp & 3, ch = warp >> 2;
 #pragma unroll 1
-        for (int c = 0; c < 4; ++c) {
-            const int tcol = ch * 128 + c * 32, n0 = tcol - half * 256;
+        for (int c = 0; c < 2; ++c) {
+            const int tcol = ch * 64 + c * 32, mh = tcol >> 7;
+            const int m = mh * 128 + q * 32 + lane, n0 = half * 128 + (tcol & 127);
             uint32_t v[32];
             tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)tcol, v);
             float *d = dW + (long long)m * 256 + n0;  // 16-byte aligned: n0 % 32 == 0
@@ -307,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                              "f"(__uint_as_float(v[j + 2])), "f"(__uint_as_float(v[j + 3]))
                              : "memory");
         }
-        atomicAdd(db + col, gsum);
+        atomicAdd(db + gcol, gsum);
     }
     if (failed && tid == 0) {
         atomicExch(flag, 1);
@@ -317,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (warp == 0) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u)
                      : "memory");
     }
 }
@@ -351,7 +368,7 @@ int tc_dense(bool forward, const float *A, long long n, const unsigned char *Bim
              cudaStream_t st)
 {
     if (n <= 0) return RP_OK;
-    const unsigned grid = (unsigned)((n + kRows - 1) / kRows);
+    const dim3 grid((unsigned)((n + kRows - 1) / kRows), 2);  // row tiles x column halves
     if (forward) {
         RP_CUDA_TRY(cudaFuncSetAttribute(k_tc_dense<EPI_FWD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DN_TOTAL));
@@ -372,9 +389,8 @@ int tc_wgrad(const float *H, const float *G, long long n, float *dW, float *db, 
     int dev;
     RP_CUDA_TRY(cudaGetDevice(&dev));
     const long long chunks = (n + kChunk - 1) / kChunk;
-    // two or more chunks per CTA halve the atomics of the final sums; never more CTAs than SMs
-    const long long want = std::max(1LL, (chunks + 1) / 2);
-    const unsigned grid = (unsigned)std::min<long long>(want, (long long)sm_count(dev));
+    // chunks x column halves, at most two CTAs per SM in all
+    const dim3 grid((unsigned)std::min<long long>(chunks, (long long)sm_count(dev)), 2);
     RP_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)WG_TOTAL));
     k_tc_wgrad<<<grid, kThreads, WG_TOTAL, st>>>(H, G, n, dW, db, flag);

@@ -21,6 +21,7 @@ struct rp_surrogate_s {
     // activations for a batch of up to `cap` rows
     long long cap;
     float *Z[4], *H[5], *out, *g0, *g1;
+    float *part;  // per-CTA partial sums of the thin layers' weight and bias gradients
     double *loss;
     void *pipe;  // buffers of the surrogate path-finding pipeline (pathfind.cu)
     // inference operands for the fused kernel (mlp_fused.cu), rebuilt when the weights change
