@@ -258,7 +258,7 @@ def surrogate(n_train=4_194_304, n_query=1_048_576, seed=5):
     return dict(name="surrogate", medium=base["medium"], params=base["params"],
                 train=pairs(n_train, seed), queries=pairs(n_query, seed + 1),
                 label_hit_tol=0.1, hit_tol=0.005, max_iter=60, max_sol=4,
-                schedule=dict(epochs=12, batch=8192, lr=2e-3, lr_final=2e-5, seed=seed),
+                schedule=dict(epochs=36, batch=8192, lr=4e-3, lr_final=2e-5, seed=seed),
                 infer=dict(conf=0.99, refine_tol=0.005, refine_step=1e-3, max_step=0.05,
                            refine_iters=16, deflate=True))
 
