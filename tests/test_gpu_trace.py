@@ -246,3 +246,31 @@ def test_full_size_batched_sampled(rp):
     assert ok.mean() >= 0.99
     dp, dd, ds, dT, dA = errors(sub, o, gi[ok], oi[ok])
     assert np.quantile(dp, 0.99) <= 1e-3 and np.quantile(dT, 0.99) <= 1e-11
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_scheduling_knobs_do_not_change_records(rp, monkeypatch, precision):
+    """RP_SERVICE_IDLE(_F64) and RP_FLUSH_MIN change when lanes are served and which thread
+    traces a secondary, never a ray's arithmetic: the same rays (matched by their split tree)
+    with bit-identical records at extreme settings."""
+    cfg = W.batched(n=20_000)
+    med = rp.Medium(cfg["medium"])
+    knob = "RP_SERVICE_IDLE" if precision == "fp32" else "RP_SERVICE_IDLE_F64"
+    runs = []
+    for idle, flush in ((None, None), ("1", "1"), ("100000", "1000000")):
+        for name, val in ((knob, idle), ("RP_FLUSH_MIN", flush)):
+            if val is None:
+                monkeypatch.delenv(name, raising=False)
+            else:
+                monkeypatch.setenv(name, val)
+        res = rp.trace(med, *cfg["rays"], params=cfg["params"], receivers=cfg["receivers"],
+                       precision=precision)
+        runs.append(gpu_rays(res))
+    base = runs[0]
+    assert np.any(base["generation"] > 0)
+    for g in runs[1:]:
+        gi, bi, only_g, only_b = match(g, base)
+        assert not only_g and not only_b
+        for k in ("pos", "dir", "path", "time", "amp", "status", "layer", "n_acc", "n_rej",
+                  "n_root", "n_refl", "n_turn"):
+            np.testing.assert_array_equal(g[k][gi], base[k][bi], err_msg=k)
