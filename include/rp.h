@@ -209,7 +209,7 @@ typedef struct {
  * capacity < n), RP_ERR_OVERFLOW (out, queue or hit capacity exceeded: rp_stats holds the
  * sizes needed; everything that fitted was written), RP_ERR_OOM, RP_ERR_CUDA.
  * Scheduling knobs, read from the environment at each call (they change speed, not any ray's
- * record): RP_SERVICE_IDLE (192) and RP_SERVICE_IDLE_F64 (8), the idle lane-iterations after
+ * record): RP_SERVICE_IDLE (256) and RP_SERVICE_IDLE_F64 (8), the idle lane-iterations after
  * which a warp serves its parked lanes (boundary splits, finished rays) in FP32-mixed and FP64
  * mode; RP_FLUSH_MIN (2), the stacked secondaries a thread hands to the next launch once the
  * input has run out. */

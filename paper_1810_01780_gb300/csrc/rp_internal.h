@@ -93,7 +93,7 @@ inline int env_int(const char *name, int dflt, int lo, int hi)
 }
 inline int service_idle(bool fp32)
 {
-    return fp32 ? env_int("RP_SERVICE_IDLE", 192, 1, 1 << 20)
+    return fp32 ? env_int("RP_SERVICE_IDLE", 256, 1, 1 << 20)
                 : env_int("RP_SERVICE_IDLE_F64", 8, 1, 1 << 20);
 }
 
