@@ -211,7 +211,7 @@ MLP_FLOPS_FWD = 2 * (3 * 256 + 3 * 256 * 256 + 256 * 12)  # per row, multiply-ad
 # DRAM bytes (read + write) of the four k_trace_wave<PrecF32, MediumLayered> launches of one
 # step of the 1,048,576-ray batched workload, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the current kernel; to be re-measured whenever the kernel changes
-TRACE_DRAM_BYTES_PER_STEP = 523_831_296
+TRACE_DRAM_BYTES_PER_STEP = 525_434_880
 
 
 def _sync_time(fn):
