@@ -504,14 +504,15 @@ __device__ __forceinline__ void ck_step_momentum(const M &med, const LayerR<P> &
     et = h * sqrt(dp_e[0] * dp_e[0] + dp_e[1] * dp_e[1] + dp_e[2] * dp_e[2]) / n0;
 }
 
-// FP32-mixed Cash-Karp step for stratified media (planes and spheres whose regions have
-// z-only index profiles), where grad n = (0, 0, g).  The horizontal direction components
+// Cash-Karp step for stratified media (planes and spheres whose regions have z-only index
+// profiles), where grad n = (0, 0, g), in both precisions.  The horizontal direction components
 // then obey the same linear equation, t_c' = kap t_c with kap = -(g t_z / n) (projected form;
 // 0 for the paraxial one), so every stage's horizontal components are the step's start
 // values times one common factor, t_c,i = t0_c phi_i with phi_i = 1 + h sum_j a_ij kap_j, and
 // their slopes are t0_c kap_i.  The stages carry the scalars (phi, kap, t_z, t_z') instead of
 // two more vector components: the same Runge-Kutta step in exact arithmetic, with fewer
-// operations and registers.  The error measures are returned squared, as by ck_step.
+// operations and registers (in FP64 its results differ from the general form's by rounding
+// only).  The error measures are returned as ck_step returns them: squared in FP32-mixed mode.
 template <class P, class M>
 __device__ __forceinline__ void ck_step_vgrad(const M &med, const LayerR<P> &lc, int form,
                                               const typename P::V &r0, const typename P::V &t0v,
@@ -568,14 +569,22 @@ __device__ __forceinline__ void ck_step_vgrad(const M &med, const LayerR<P> &lc,
     dt[0] = tx * hkap;
     dt[1] = ty * hkap;
     dt[2] = h * s_ktz;
-    // the stages used the high word of the direction; since sum_i b5_i = 1 its low word
-    // contributes exactly h * t_lo to the position increment
+    if constexpr (P::kFF) {
+        // the stages used the high word of the direction; since sum_i b5_i = 1 its low word
+        // contributes exactly h * t_lo to the position increment
 #pragma unroll
-    for (int c = 0; c < 3; ++c) dr[c] = __fmaf_rn(h, t0v.lo[c], dr[c]);
+        for (int c = 0; c < 3; ++c) dr[c] = __fmaf_rn(h, t0v.lo[c], dr[c]);
+    }
     dT = h * (sT * P::c(kInvC0));
     const R th2 = tx * tx + ty * ty;
-    er = th2 * (e_phi * e_phi) + e_tz * e_tz;
-    et = (h * h) * (th2 * (e_kap * e_kap) + e_ktz * e_ktz);
+    if constexpr (P::kFF) {
+        // squared error measures, as ck_step returns them in FP32-mixed mode
+        er = th2 * (e_phi * e_phi) + e_tz * e_tz;
+        et = (h * h) * (th2 * (e_kap * e_kap) + e_ktz * e_ktz);
+    } else {
+        er = P::sqrt_(th2 * (e_phi * e_phi) + e_tz * e_tz);
+        et = h * P::sqrt_(th2 * (e_kap * e_kap) + e_ktz * e_ktz);
+    }
 }
 
 template <class P, class M>
@@ -592,7 +601,7 @@ __device__ __forceinline__ void ck_step(const M &med, const LayerR<P> &lc, int f
             return;
         }
     }
-    if constexpr (P::kFF && is_layered_v<M>) {
+    if constexpr (is_layered_v<M>) {
         ck_step_vgrad<P, M>(med, lc, form, r0, t0v, h, dr, dt, dT, er, et);
         return;
     }
