@@ -156,7 +156,13 @@ struct PrecF64 {
     __device__ static __forceinline__ R rcp(R x) { return 1.0 / x; }
     __device__ static __forceinline__ R exp_(R x) { return exp(x); }
     __device__ static __forceinline__ R sqrt_(R x) { return sqrt(x); }
-    __device__ static __forceinline__ R pow_(R x, R y) { return pow(x, y); }
+    // the step-size factor of the step control (a heuristic: its last bits do not matter) in
+    // single precision on the FP32 pipe and the special-function unit: a double pow costs
+    // about as many FP64 instructions as a third of a Runge-Kutta step
+    __device__ static __forceinline__ R pow_(R x, R y)
+    {
+        return (double)exp2f((float)y * __log2f((float)x));
+    }
     __device__ static __forceinline__ R c(double x) { return x; }
     // scalar accumulators (travel time, arc length)
     typedef double S;
