@@ -131,11 +131,16 @@ int rp_medium_create(const rp_medium_desc *d, void *stream, rp_medium_t *out)
     memset(&m->layered, 0, sizeof m->layered);
     memset(&m->grid, 0, sizeof m->grid);
     m->grid_dev = nullptr;
-    cudaError_t e = cudaGetDevice(&m->device);
-    if (e != cudaSuccess) {
-        delete m;
-        return cuda_fail(e, "cudaGetDevice");
-    }
+    // the descriptor is checked on the host before any CUDA call; the medium belongs to the
+    // current device
+    auto bind_device = [&]() -> int {
+        cudaError_t e = cudaGetDevice(&m->device);
+        if (e != cudaSuccess) {
+            delete m;
+            return cuda_fail(e, "cudaGetDevice");
+        }
+        return RP_OK;
+    };
     m->kind = d->kind;
     if (d->kind == RP_MEDIUM_LAYERED) {
         if (d->n_layers < 1 || d->n_layers > RP_MAX_LAYERS) {
@@ -246,6 +251,7 @@ int rp_medium_create(const rp_medium_desc *d, void *stream, rp_medium_t *out)
             B.Rf = (float)S.radius;
             B.pad = 0.0f;
         }
+        if (int rc = bind_device()) return rc;
     } else if (d->kind == RP_MEDIUM_GRID) {
         if (d->nx < 2 || d->ny < 2 || d->nz < 2 || !(d->spacing > 0.0) || !d->grid_n) {
             delete m;
@@ -266,6 +272,7 @@ int rp_medium_create(const rp_medium_desc *d, void *stream, rp_medium_t *out)
         }
         g.inv_sp = 1.0 / d->spacing;
         g.inv_spf = (float)g.inv_sp;
+        if (int rc = bind_device()) return rc;
         int rc = build_grid(m, d->grid_n, d->spacing, (cudaStream_t)stream);
         if (rc) {
             if (m->grid_dev) cudaFree(m->grid_dev);
