@@ -86,3 +86,61 @@ def test_invalid_descriptors_are_refused_on_the_host(case):
     rc, msg = _create(d)
     assert rc == RP_ERR_INVALID_ARG, (case, rc, msg)
     assert msg.startswith("rp_medium_create:"), msg
+
+
+# rp_trace refuses bad calls before it touches the medium or the device: a zeroed block stands
+# in for the medium handle (never read on these paths) and the batch is empty.
+_FAKE_MEDIUM = (C.c_char * 65536)()
+_ANCHOR = (C.c_double * 4)()
+
+
+def _trace(params, n=0, capacity=1, end_pos=True):
+    rays = A.Rays()
+    rays.n = n
+    out = A.RayOut()
+    out.capacity = capacity
+    out.end_pos = C.cast(_ANCHOR, C.c_void_p) if end_pos else None
+    st = A.Stats()
+    rc = A.lib().rp_trace(C.cast(_FAKE_MEDIUM, C.c_void_p), C.byref(rays), None, C.byref(params),
+                          C.byref(out), None, C.byref(st), None)
+    return rc, A.last_error()
+
+
+def _params(**kw):
+    from paper_1810_01780_gb300 import api
+
+    base = dict(tol=1e-6, h_min=1e-3, h_max=10.0, h0=1.0, max_path=100.0, max_generation=3)
+    p = api.make_params({k: v for k, v in base.items()}, kw.pop("precision", "fp64"))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("bad", [dict(tol=0.0), dict(h_min=0.0), dict(h_max=1e-4),
+                                 dict(h0=0.0), dict(max_path=0.0), dict(eps_b=0.0),
+                                 dict(max_steps=0), dict(max_generation=16),
+                                 dict(max_generation=-1), dict(precision=7),
+                                 dict(polarization=9), dict(rhs_form=9),
+                                 dict(rhs_form=A.RHS_FORM["momentum"],
+                                      precision=A.PRECISION["fp32"])])
+def test_rp_trace_refuses_bad_parameters(bad):
+    p = _params()
+    for k, v in bad.items():
+        setattr(p, k, v)
+    rc, msg = _trace(p)
+    assert rc == RP_ERR_INVALID_ARG, (bad, rc, msg)
+    assert msg.startswith("params:"), msg
+
+
+def test_rp_trace_refuses_bad_stop_planes_and_buffers():
+    p = _params()
+    p.use_stop = 1
+    p.stop_n[0], p.stop_n[1] = 1.0, 1.0  # not a coordinate axis
+    assert _trace(p)[0] == RP_ERR_INVALID_ARG
+    p.stop_n[1] = 0.0
+    p.stop_n[0] = 0.5  # not unit
+    assert _trace(p)[0] == RP_ERR_INVALID_ARG
+    q = _params()
+    assert _trace(q, end_pos=False)[0] == RP_ERR_INVALID_ARG  # no end_pos array
+    rc, msg = _trace(q, n=4, capacity=4)  # rays without arrays
+    assert rc == RP_ERR_INVALID_ARG and "ray arrays" in msg
