@@ -144,3 +144,57 @@ def test_rp_trace_refuses_bad_stop_planes_and_buffers():
     assert _trace(q, end_pos=False)[0] == RP_ERR_INVALID_ARG  # no end_pos array
     rc, msg = _trace(q, n=4, capacity=4)  # rays without arrays
     assert rc == RP_ERR_INVALID_ARG and "ray arrays" in msg
+
+
+def _find_paths(pp, n=4, count=True):
+    arr = (C.c_double * 4)()
+    ang = (C.c_int32 * 4)()
+    sol = A.Solutions()
+    sol.count = C.cast(ang, C.c_void_p) if count else None
+    st = A.Stats()
+    p = C.cast(arr, C.c_void_p)
+    rc = A.lib().rp_find_paths(C.cast(_FAKE_MEDIUM, C.c_void_p), n, p, p, p,
+                               C.cast(ang, C.c_void_p), C.byref(pp), C.byref(sol), C.byref(st),
+                               None)
+    return rc, A.last_error()
+
+
+def _path_params(**kw):
+    pp = A.PathParams()
+    pp.trace = _params()
+    pp.trace.max_path = 0.0  # the path finder sets its own per-pair budget
+    pp.hit_tol, pp.max_iter, pp.max_sol = 0.1, 60, 4
+    for k, v in kw.items():
+        setattr(pp, k, v)
+    return pp
+
+
+@pytest.mark.parametrize("bad", [dict(hit_tol=0.0), dict(max_iter=0), dict(max_iter=201),
+                                 dict(max_sol=0), dict(max_sol=9)])
+def test_rp_find_paths_refuses_bad_parameters(bad):
+    rc, msg = _find_paths(_path_params(**bad))
+    assert rc == RP_ERR_INVALID_ARG and msg.startswith("rp_find_paths:"), (bad, rc, msg)
+
+
+def test_rp_find_paths_refuses_bad_trace_parameters_and_arrays():
+    pp = _path_params()
+    pp.trace.tol = -1.0
+    assert _find_paths(pp)[0] == RP_ERR_INVALID_ARG
+    rc, msg = _find_paths(_path_params(), count=False)
+    assert rc == RP_ERR_INVALID_ARG and "null" in msg
+    assert _find_paths(_path_params(), n=-1)[0] == RP_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("bad", [dict(epochs=0), dict(batch=0), dict(batch=1 << 20),
+                                 dict(lr=0.0), dict(lr_final=-1.0)])
+def test_rp_surrogate_train_refuses_bad_schedules(bad):
+    tp = A.TrainParams()
+    tp.epochs, tp.batch, tp.lr, tp.lr_final, tp.seed = 1, 256, 1e-3, 0.0, 1
+    for k, v in bad.items():
+        setattr(tp, k, v)
+    buf = C.cast((C.c_float * 16)(), C.c_void_p)
+    loss = C.c_double()
+    rc = A.lib().rp_surrogate_train(C.cast(_FAKE_MEDIUM, C.c_void_p), 1024, buf, buf, buf,
+                                    C.byref(tp), C.byref(loss), None)
+    assert rc == RP_ERR_INVALID_ARG, (bad, rc)
+    assert A.last_error().startswith("rp_surrogate_train:")
