@@ -422,6 +422,66 @@ def test_grid_leaves_domain(oracle_lib):
     assert 9.0 < rays[0]["pos"][0] <= 10.0 + 1e-9
 
 
+def _optical_length(om, P, sub=40):
+    """(1/c0) times the integral of n along the polyline P, Simpson's rule on each segment."""
+    T = 0.0
+    for a, b in zip(P[:-1], P[1:]):
+        u = np.linspace(0.0, 1.0, sub + 1)
+        q = a[None, :] + u[:, None] * (b - a)[None, :]
+        n = np.array([om.eval(x)[0] for x in q])
+        T += np.linalg.norm(b - a) * (n[0] + n[-1] + 4 * n[1:-1:2].sum() + 2 * n[2:-1:2].sum()) \
+            / (3 * sub) / C0
+    return T
+
+
+def test_grid_ray_in_random_field_obeys_fermat(oracle_lib):
+    """Random-perturbation grid (no closed form): the traced ray is a path of stationary,
+    minimal travel time (Fermat).  Points on the ray come from tracing to 40 path lengths; the
+    optical length of polylines through them is evaluated with the grid's own (separately
+    pinned) interpolation of n.  The ray's first variation under a smooth transverse bump is
+    under 2 % of the straight chord's between the same end points (about 0.3 % when right; a
+    ray traced through another seed's field, or through the field with its perturbation
+    doubled, gives 8-13 %), its second variation is positive, the chord takes longer, and the
+    tracer's T equals the ray's optical length."""
+    gmed = W.grid_medium(40, 40, 60, spacing=4.0, sigma=5e-3, corr_len=20.0, seed=3)
+    om = oracle.OracleMedium(gmed)
+    start = np.array([-40.0, -10.0, 40.0])
+    th, ph = np.radians(80.0), np.radians(20.0)
+    d = np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+    S, K = 60.0, 40
+    prm = dict(W.TRACE_DEFAULTS, tol=1e-10, h_min=1e-4, h_max=0.5, h0=0.1, max_generation=0)
+    pts = [start]
+    for k in range(1, K + 1):
+        rays, _ = oracle.trace(gmed, dict(prm, max_path=S * k / K), start.reshape(3, 1),
+                               d.reshape(3, 1))
+        assert rays[0]["status"] == oracle.STATUS["MAX_PATH"]
+        pts.append(rays[0]["pos"])
+    T_traced = rays[0]["time"]
+    ray = np.array(pts)
+    s = np.linspace(0.0, 1.0, K + 1)
+    chord = ray[0][None, :] + s[:, None] * (ray[-1] - ray[0])[None, :]
+    bump = np.sin(np.pi * s)[:, None]
+    v = (ray[-1] - ray[0]) / np.linalg.norm(ray[-1] - ray[0])
+    u1 = np.cross(v, [0.0, 0.0, 1.0])
+    u1 /= np.linalg.norm(u1)
+    u2 = np.cross(v, u1)
+    E = 0.05
+    first, second, T0 = {}, {}, {}
+    for name, P in (("ray", ray), ("chord", chord)):
+        T0[name] = _optical_length(om, P)
+        f, q = [], []
+        for u in (u1, u2):
+            Tp = _optical_length(om, P + E * bump * u[None, :])
+            Tm = _optical_length(om, P - E * bump * u[None, :])
+            f.append(abs(Tp - Tm) / 2)
+            q.append(Tp + Tm - 2 * T0[name])
+        first[name], second[name] = max(f), min(q)
+    assert first["ray"] <= 0.02 * first["chord"], (first, second)
+    assert second["ray"] > 0.0
+    assert T0["ray"] < T0["chord"]
+    assert abs(T_traced - T0["ray"]) <= 1e-5 * T_traced
+
+
 # --------------------------------------------------------------------------------------
 # source-receiver path finding: the paper's accuracy study
 # --------------------------------------------------------------------------------------
