@@ -31,7 +31,9 @@ def _rank_main(rank, world, port, out):
         t, (steps, rays) = bench.reduce_over_ranks(10.0 * (rank + 1), [1000 * (rank + 1),
                                                                       10 * (rank + 1)], "cpu")
         r, w, _ = bench._env_rank()
-        out[rank] = (t, steps, rays, r, w)
+        # a rejected clock record on rank 1 alone makes both ranks measure again
+        again = bench.any_rank(rank == 1, "cpu")
+        out[rank] = (t, steps, rays, r, w, again)
         dist.barrier()
     finally:
         dist.destroy_process_group()
@@ -42,8 +44,9 @@ def test_two_gloo_ranks_reduce_like_the_bench():
     out = mp.Manager().dict()
     mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
     for rank in range(world):
-        t, steps, rays, r, w = out[rank]
+        t, steps, rays, r, w, again = out[rank]
         assert (r, w) == (rank, world)
+        assert again
         assert t == 20.0  # the slowest rank
         assert steps == 3000.0 and rays == 30.0  # all ranks' work
     # the bench's value: all ranks' steps over the slowest time
@@ -67,3 +70,21 @@ def test_reference_arm_runs_on_rank_zero_only():
     out = mp.Manager().dict()
     mp.spawn(_ref_rank, args=(2, out), nprocs=2, join=True)
     assert out[0] == 2 and out[1] == 0  # rank 0: warm-up + one step; rank 1: nothing
+
+
+def test_clock_records_that_reject_a_timing():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    assert bench.clocks_reject(ok) is None
+    assert bench.clocks_reject(dict(ok, sm_mhz=1800.0, reasons=["sw_power_cap"])) is None
+    assert bench.clocks_reject(dict(ok, reasons=["sw_power_cap", "hw_slowdown"])) == "hw_slowdown"
+    assert bench.clocks_reject(dict(ok, reasons=["sw_thermal_slowdown"])) is not None
+    assert bench.clocks_reject(dict(ok, reasons=["hw_thermal_slowdown"])) is not None
+    # a clock held low with nothing active: a leftover lock
+    assert "no reason" in bench.clocks_reject(dict(ok, sm_mhz=1200.0))
+    # no samples at all: nothing to judge by
+    assert bench.clocks_reject({"sm_mhz": None, "sm_max_mhz": None,
+                                "reasons": ["unsampled"]}) is None
+    assert bench.any_rank(True, "cpu") and not bench.any_rank(False, "cpu")
