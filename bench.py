@@ -106,12 +106,13 @@ def run_reference(args):
         wall_tot += w
     v = steps_tot / wall_tot
     line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "ray-steps/s", "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ray-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall_tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "rays_per_s": rays_tot / wall_tot,
         "config": {"workload": WORKLOAD, "rays": N_RAYS, "precision": "fp64 (CPU oracle)",
-                   "sample": f"first {sample} primaries (+ their secondaries) per step"},
+                   "sample": f"first {sample} primaries (+ their secondaries) per step",
+                   "device": f"{cores} host cores on rank 0; the launch's GPUs are not used"},
         "cpu_baseline": {"value": v, "unit": "ray-steps/s", "cores": cores, "kind": "oracle",
                          "sample": f"first {sample} primaries of the workload, all secondaries"},
         "e2e": {"value": v, "unit": "ray-steps/s", "h2d_bytes_per_step": 0,
