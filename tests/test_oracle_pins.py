@@ -98,6 +98,21 @@ def test_ray_step_local_order(oracle_lib):
     assert all(5.0 < s < 7.0 for s in slopes), (errs, slopes)
 
 
+@pytest.mark.parametrize("theta_deg", [60.0, 100.0, 170.0])
+def test_error_measure_is_per_unit_step(oracle_lib, theta_deg):
+    """The step's error measure takes the position part of the embedded difference per unit
+    step length (|dr| / h) beside the direction part (|dt|).  The difference of a fifth- and
+    a fourth-order solution is O(h^5) in every component, so the measure falls like h^4 as h
+    halves (like h^5 if the position part were not divided by h)."""
+    med = oracle.OracleMedium(W.single_profile())
+    th = math.radians(theta_deg)
+    y0 = np.array([0.0, 0.0, 30.0, math.sin(th), 0.0, math.cos(th), 0.0])
+    hs = [4.0, 2.0, 1.0, 0.5]
+    es = [oracle.ck_step(med, y0, h)[1] for h in hs]
+    slopes = [math.log2(es[i] / es[i + 1]) for i in range(len(hs) - 1)]
+    assert all(3.8 < q < 4.2 for q in slopes), (es, slopes)
+
+
 # --------------------------------------------------------------------------------------
 # ray equations
 # --------------------------------------------------------------------------------------
@@ -170,6 +185,64 @@ def test_closed_form_range_path_time(oracle_lib, form):
         assert abs(r["pos"][0] - X) < lim, i
         assert abs(r["path"] - S) < lim, i
         assert abs(r["time"] - T) < 1e-15, i
+
+
+def test_layer_offset_shifts_the_profile(oracle_lib):
+    """A layer's index n0 - dn exp(-z/z0) + off: the profile written with n0 lowered by 0.02
+    and off = +0.02 is the same medium, so its rays lie on the closed-form curves of a = n0."""
+    prof = ExpProfile()
+    med = {"kind": "layered", "layers": [dict(n0=prof.a - 0.02, dn=prof.b, z0=prof.zeta,
+                                              off=0.02)]}
+    pos, d, a = W.fan_xz(9, 200.0, 3.0, 177.0)
+    prm = dict(W.TRACE_DEFAULTS, tol=1e-9, max_path=1500.0, max_generation=0)
+    rays, _ = oracle.trace(med, prm, pos, d, a)
+    th = np.arctan2(d[0], d[2])
+    for i, r in enumerate(rays):
+        X, S, T = prof.ray_to_depth(pos[2, i], th[i], r["pos"][2], ends_down=r["dir"][2] > 0)
+        assert abs(r["pos"][0] - X) < 2e-7 and abs(r["time"] - T) < 1e-15, i
+    # a constant layer (dn = 0) with an offset: n = n0 + off along a straight line
+    med = {"kind": "layered", "layers": [dict(n0=1.3, dn=0.0, off=0.2)]}
+    rays, _ = oracle.trace(med, dict(prm, max_path=100.0), pos[:, :1], d[:, :1])
+    assert abs(rays[0]["time"] - 1.5 * 100.0 / C0) < 1e-18
+
+
+def test_start_layer_from_depth(oracle_lib):
+    """A ray starts in the layer that holds its depth: a boundary depth itself belongs to the
+    layer below it.  Straight vertical rays in constant layers (n 1.3 above 100 m, 1.5
+    below) started at 99.5, 100 and 100.5 m, going down 50 m: T = n s / c0 of their layer."""
+    med = {"kind": "layered", "layers": [dict(n0=1.3), dict(z_top=100.0, n0=1.5)]}
+    z = np.array([99.5, 100.0, 100.5])
+    pos = np.stack([np.zeros(3), np.zeros(3), z])
+    d = np.stack([np.zeros(3), np.zeros(3), np.ones(3)])
+    prm = dict(W.TRACE_DEFAULTS, max_path=50.0, max_generation=0)
+    rays, _ = oracle.trace(med, prm, pos, d)
+    # the first ray crosses the boundary after 0.5 m (n_refl = 1, reflected back up); the
+    # others never meet a boundary
+    assert list(rays["n_refl"]) == [1, 0, 0]
+    for i in (1, 2):
+        assert abs(rays[i]["time"] - 1.5 * 50.0 / C0) < 1e-18
+        assert rays[i]["pos"][2] == pytest.approx(z[i] + 50.0, abs=1e-9)
+
+
+def test_step_growth_and_inherited_step(oracle_lib):
+    """The step law at zero error (constant index): every accepted step grows the next by the
+    growth limit 5, up to h_max.  From h0 = 0.01 m with h_max = 10 m the steps are 0.01,
+    0.05, 0.25, 1.25, 6.25, then 10 m; 100 m of path take 5 + 10 (the last one shortened to
+    the path limit) = 15 accepted steps.  A secondary starts with its parent's step at the
+    split: a ray across an internal plane at 50 m depth (normal incidence, constant indices)
+    has taken 0.01..6.25 (7.81 m) and four more steps of 10 m (47.81 m) before the 2.19 m
+    step that lands on the plane; its next step (10 m) is the secondary's first, so the
+    secondary covers the remaining 50 m in 5 steps."""
+    med = {"kind": "layered", "layers": [dict(n0=1.5)]}
+    prm = dict(W.TRACE_DEFAULTS, h0=0.01, h_max=10.0, max_path=100.0, max_generation=0)
+    rays, _ = oracle.trace(med, prm, np.zeros((3, 1)), np.array([[0.0], [0.0], [1.0]]))
+    assert rays[0]["n_acc"] == 15 and rays[0]["n_rej"] == 0
+    med = {"kind": "layered", "layers": [dict(n0=1.5), dict(z_top=50.0, n0=1.6)]}
+    rays, _ = oracle.trace(med, dict(prm, max_generation=1), np.zeros((3, 1)),
+                           np.array([[0.0], [0.0], [1.0]]))
+    sec = rays[rays["parent"] == 0]
+    assert len(sec) == 1 and sec[0]["status"] == oracle.STATUS["MAX_PATH"]
+    assert sec[0]["n_acc"] == 5
 
 
 def test_error_shrinks_with_tolerance(oracle_lib):
@@ -310,6 +383,7 @@ def test_boundary_split_constant_layers(oracle_lib):
         assert len(sec) == 1
         s = sec[0]
         assert s["status"] == oracle.STATUS["TRANSMITTED"] and s["gen"] == 1
+        assert s["pos"][2] == 0.0  # the landing point is put on the plane exactly
         assert abs(s["amp"] - ts) < 1e-12
         assert np.allclose(s["pos"], [x_hit, 0.0, 0.0], atol=1e-8)
         assert abs(s["path"] - s_hit) < 1e-8
@@ -340,6 +414,22 @@ def test_internal_boundary_secondary_traced(oracle_lib):
                        atol=1e-8)
 
 
+def test_earliest_of_two_surfaces_in_one_step(oracle_lib):
+    """One step (h = 10 m) that crosses both the surface z = 0 and a stop plane x = 4 m: the
+    ray meets the surface first (at x = 2 m), reflects there, and only then reaches the stop
+    plane, below the surface.  Straight rays in constant ice, so the geometry is exact."""
+    med = {"kind": "layered", "layers": [dict(n0=1.0, absorb=True), dict(z_top=0.0, n0=1.5)]}
+    d = np.array([1.0, 0.0, -1.0]) / math.sqrt(2.0)  # 45 degrees upward
+    pos = np.array([[0.0], [0.0], [2.0]])
+    prm = dict(W.TRACE_DEFAULTS, h0=10.0, max_path=100.0, max_generation=0,
+               stop=((1.0, 0.0, 0.0), 4.0))
+    rays, _ = oracle.trace(med, prm, pos, d.reshape(3, 1))
+    r = rays[0]
+    assert r["status"] == oracle.STATUS["REACHED_STOP"] and r["n_refl"] == 1
+    assert np.allclose(r["pos"], [4.0, 0.0, 2.0], atol=1e-9)
+    assert abs(r["path"] - 4.0 * math.sqrt(2.0)) < 1e-9
+
+
 def test_receiver_entry_point(oracle_lib):
     med = {"kind": "layered", "layers": [dict(n0=1.7)]}
     pos = np.array([[0.0, 0.0], [0.0, 0.0], [0.0, 0.0]])
@@ -358,6 +448,24 @@ def test_receiver_entry_point(oracle_lib):
         assert abs(h["time"] - 1.7 * h["path"] / C0) < 1e-18
 
 
+def test_receiver_hit_carries_the_current_amplitude(oracle_lib):
+    """A receiver met before and after a reflection: straight up from 10 m depth in constant
+    ice (n 1.5) under absorbing air, a receiver of radius 1 m at 5 m depth.  Entry going up
+    at 6 m (path 4 m, amplitude A0), back down after the surface's normal-incidence
+    reflection (r = 0.2) at 4 m (path 14 m, amplitude 0.2 A0)."""
+    med = {"kind": "layered", "layers": [dict(n0=1.0, absorb=True), dict(z_top=0.0, n0=1.5)]}
+    prm = dict(W.TRACE_DEFAULTS, max_path=20.0, max_generation=0)
+    rays, hits = oracle.trace(med, prm, np.array([[0.0], [0.0], [10.0]]),
+                              np.array([[0.0], [0.0], [-1.0]]), np.array([3.0]),
+                              receivers=(np.array([[0.0, 0.0, 5.0]]), np.array([1.0])))
+    h = np.sort(hits, order="path")
+    assert len(h) == 2
+    assert np.allclose(h["path"], [4.0, 14.0], atol=1e-9)
+    assert np.allclose(h["amp"], [3.0, 0.6], rtol=1e-12, atol=0)
+    assert np.allclose(h["pos"][:, 2], [6.0, 4.0], atol=1e-9)
+    assert np.allclose(h["time"], 1.5 * h["path"] / C0, rtol=1e-12, atol=0)
+
+
 def test_break_conditions(oracle_lib):
     med = {"kind": "layered", "layers": [dict(n0=1.0, absorb=True), dict(z_top=0.0, n0=1.5)]}
     pos = np.array([[0.0], [0.0], [10.5]])
@@ -367,9 +475,17 @@ def test_break_conditions(oracle_lib):
     assert rays[0]["status"] == oracle.STATUS["MAX_TIME"]
     assert 3e-7 <= rays[0]["time"] < 3e-7 + 10.0 * 1.5 / C0
     prm = dict(W.TRACE_DEFAULTS, max_path=1e4, min_amp=0.5)
-    rays, _ = oracle.trace(med, prm, pos, d)
-    assert rays[0]["status"] == oracle.STATUS["MIN_AMP"]  # |r| = 0.2 < 0.5
-    assert abs(rays[0]["path"] - 10.5) < 1e-9
+    for a0 in (1.0, 4.0, -3.0):
+        # the threshold is on A / A0 (Sec. 2, Fig. 1 text): |r| = 0.2 < 0.5 whatever A0 is
+        rays, _ = oracle.trace(med, prm, pos, d, np.array([a0]))
+        assert rays[0]["status"] == oracle.STATUS["MIN_AMP"], a0
+        assert abs(rays[0]["path"] - 10.5) < 1e-9
+        assert rays[0]["amp"] == pytest.approx(0.2 * a0, rel=1e-12)
+        # the transmitted ray (|t| = 1.2 >= 0.5) is still cast; only weaker ones are not
+        sec = rays[rays["parent"] == 0]
+        assert len(sec) == 1 and sec[0]["amp"] == pytest.approx(1.2 * a0, rel=1e-12)
+    rays, _ = oracle.trace(med, dict(prm, min_amp=1.25), pos, d)
+    assert len(rays) == 1  # |t| = 1.2 < 1.25: no secondary
 
 
 # --------------------------------------------------------------------------------------
@@ -508,6 +624,8 @@ def test_path_finding_reproduces_paper_accuracy(oracle_lib):
             s = sol[i, j]
             assert s["type"] == oracle.SOL_TYPE[r["type"]]
             assert abs(math.degrees(s["launch"] - r["launch"])) < acc["launch_angle_deg"]
+            # the arrival angle obeys the same Snell invariant: n(z_r) sin(receive) = p
+            assert abs(math.degrees(s["receive"] - r["receive"])) < acc["launch_angle_deg"]
             assert abs(s["path"] - r["path"]) < acc["path_length_m"]
             assert abs(s["time"] - r["time"]) < acc["travel_time_s"]
             assert abs(s["amp"] - r["amp"]) < 1e-6
@@ -539,8 +657,31 @@ def test_path_finder_matches_closed_forms_on_workload_pairs(oracle_lib):
             assert s["type"] == oracle.SOL_TYPE[r["type"]], (i, j)
             assert abs(s["time"] - r["time"]) < 1e-12, (i, j)
             assert abs(s["launch"] - r["launch"]) < 1e-6, (i, j)
+            assert abs(s["receive"] - r["receive"]) < 1e-6, (i, j)
             n_sol += 1
     assert n_sol >= 60
+
+
+def test_path_finder_vertical_pairs(oracle_lib):
+    """Receiver straight above or below the source (horizontal distance under the receiver
+    tolerance): the one solution is the vertical direct ray, launched down (0) toward a deeper
+    receiver and up (pi) toward a shallower one, with T = (1/c0) * integral of n dz =
+    (a dz - b zeta (exp(-z1/zeta) - exp(-z2/zeta))) / c0 and path dz."""
+    prof = ExpProfile(W.ICE["n0"], W.ICE["dn"], W.ICE["z0"])
+    a, b, zeta = prof.a, prof.b, prof.zeta
+    med = W.ice_with_surface()
+    zs, zr = np.array([100.0, 500.0, 30.0]), np.array([500.0, 100.0, 31.0])
+    prm = dict(W.TRACE_DEFAULTS, tol=1e-9, max_generation=0, max_path=1e4)
+    count, sol = oracle.find_paths(med, prm, zs, zr, np.zeros(3), np.full(3, 64, np.int32),
+                                   hit_tol=1e-4)
+    for i in range(3):
+        z1, z2 = min(zs[i], zr[i]), max(zs[i], zr[i])
+        T = (a * (z2 - z1) - b * zeta * (math.exp(-z1 / zeta) - math.exp(-z2 / zeta))) / C0
+        assert count[i] == 1, i
+        s = sol[i, 0]
+        assert s["type"] == oracle.SOL_TYPE["DIRECT"]
+        assert s["launch"] == (0.0 if zr[i] > zs[i] else math.pi)
+        assert abs(s["path"] - (z2 - z1)) < 1e-8 and abs(s["time"] - T) < 1e-15, i
 
 
 def _sphere_medium(n_out, n_in, ctr, R, absorb=False):
@@ -562,7 +703,9 @@ def test_sphere_entry_reflection_refraction_exact(oracle_lib):
     pos[2] = ctr[2] + b
     d = np.tile(np.array([[1.0], [0.0], [0.0]]), (1, n))
     S = 200.0  # every ray reaches the sphere; no refracted ray reaches the far side
-    prm = dict(W.TRACE_DEFAULTS, tol=1e-9, max_path=S, max_generation=1)
+    # a step budget far above the few dozen steps these straight rays need, so that a ray
+    # caught at the surface ends (and fails) instead of running on
+    prm = dict(W.TRACE_DEFAULTS, tol=1e-9, max_path=S, max_generation=1, max_steps=10_000)
     rays, _ = oracle.trace(med, prm, pos, d)
     for i in range(n):
         xe = -math.sqrt(R * R - b[i] ** 2)
@@ -594,6 +737,31 @@ def test_sphere_entry_reflection_refraction_exact(oracle_lib):
         assert np.linalg.norm(s["pos"] - ctr) < R
 
 
+def test_sphere_exit_into_the_layer_below_and_start_region(oracle_lib):
+    """Rays leaving a sphere (n 1.8, radius 50 m, centre at 500 m depth) that sits in the lower
+    of two constant layers (n 1.3 above 100 m, 1.5 below) at normal incidence: the
+    transmitted ray continues with the index of the layer that holds it (1.5), with
+    amplitude 2 n_in / (n_in + n_out).  One starts at the centre, one 1.5 m inside the
+    surface: a start point inside the sphere belongs to it however close to the surface."""
+    n_in, n_lo = 1.8, 1.5
+    ctr = np.array([0.0, 0.0, 500.0])
+    med = {"kind": "layered", "layers": [dict(n0=1.3), dict(z_top=100.0, n0=n_lo)],
+           "spheres": [dict(center=ctr, radius=50.0, n0=n_in)]}
+    S = 90.0  # the reflected primaries do not reach the sphere's far side
+    prm = dict(W.TRACE_DEFAULTS, max_path=S, max_generation=1, max_steps=10_000)
+    for r0 in (0.0, 48.5):
+        pos = (ctr + np.array([r0, 0.0, 0.0])).reshape(3, 1)
+        rays, _ = oracle.trace(med, prm, pos, np.array([[1.0], [0.0], [0.0]]))
+        sec = rays[rays["parent"] == 0]
+        assert len(sec) == 1 and sec[0]["layer"] == 1, r0
+        s_exit = 50.0 - r0
+        assert abs(sec[0]["amp"] - 2 * n_in / (n_in + n_lo)) < 1e-12
+        assert abs(rays[0]["amp"] - (n_in - n_lo) / (n_in + n_lo)) < 1e-12
+        assert abs(sec[0]["time"] - (n_in * s_exit + n_lo * (S - s_exit)) / C0) < 1e-15
+        assert np.allclose(sec[0]["pos"], ctr + np.array([50.0 + S - s_exit, 0.0, 0.0]),
+                           atol=1e-8)
+
+
 def test_sphere_total_internal_reflection_and_exit(oracle_lib):
     """A ray inside a sphere of higher index: beyond the critical angle it reflects totally
     (amplitude kept, nothing transmitted); at normal incidence it leaves through the surface
@@ -605,7 +773,8 @@ def test_sphere_total_internal_reflection_and_exit(oracle_lib):
     pos = np.array([[0.0], [0.0], [ctr[2] + a]])
     d = np.array([[1.0], [0.0], [0.0]])
     x_hit = math.sqrt(R * R - a * a)
-    prm = dict(W.TRACE_DEFAULTS, tol=1e-9, max_path=x_hit + 40.0, max_generation=3)
+    prm = dict(W.TRACE_DEFAULTS, tol=1e-9, max_path=x_hit + 40.0, max_generation=3,
+               max_steps=10_000)
     rays, _ = oracle.trace(med, prm, pos, d)
     assert len(rays) == 1
     r = rays[0]
