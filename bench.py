@@ -393,9 +393,9 @@ def run_gpu(args):
     else:
         torch.cuda.set_device(0)
 
-    # CPU baseline first (spawned pool), before this process does heavy GPU work
+    # CPU baseline first (spawned pool), before this process does heavy GPU work; one GPU only
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s, r, w, cores = oracle_sample(args.cpu_sample)
         cpu = {"value": s / w, "unit": "ray-steps/s", "cores": cores, "kind": "oracle",
                "sample": f"first {args.cpu_sample} primaries of the workload with all their "
