@@ -12,9 +12,10 @@ BASE_KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_ste
              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "e2e"}
 
 _FAKE_GPU_ARM = r'''
-import argparse, sys, types
+import argparse, os, sys, types
 import numpy as np
 import torch
+import torch.distributed as dist
 
 torch.cuda.set_device = lambda *a, **k: None
 torch.cuda.synchronize = lambda *a, **k: None
@@ -51,6 +52,10 @@ torch.Tensor.pin_memory = lambda self: self
 
 import bench
 
+_init = dist.init_process_group
+dist.init_process_group = lambda backend, **k: _init("gloo", **k)
+THROTTLED_RANK = int(os.environ.get("THROTTLED_RANK", "0"))
+
 
 class Sampler:
     calls = 0
@@ -66,7 +71,8 @@ class Sampler:
         pass
 
     def summary(self):
-        r = ["hw_slowdown"] if Sampler.calls == 1 else ["sw_power_cap"]
+        first = Sampler.calls == 1 and int(os.environ.get("RANK", "0")) == THROTTLED_RANK
+        r = ["hw_slowdown"] if first else ["sw_power_cap"]
         return {"sm_mhz": 2000.0, "sm_max_mhz": 2070.0, "reasons": r, "samples": 5}
 
 
@@ -105,7 +111,8 @@ pkg.trace_into = lambda med, rays, prm, buf, stream=None: Stats(rays.n)
 
 off = dict(no_fp64=True, no_grid=True, no_paths=True, no_surrogate=True, no_fig1=True,
            no_spheres=True, no_cpu_baseline=True)
-bench.run_gpu(argparse.Namespace(gpus=1, steps=2, warmup=3, impl="ours", paths_steps=1,
+bench.run_gpu(argparse.Namespace(gpus=int(os.environ.get("WORLD_SIZE", "1")), steps=2, warmup=3,
+                                 impl="ours", paths_steps=1,
                                  rays=4096, sur_train=0, sur_queries=0, sur_check=0,
                                  grid_steps=1, fp64_steps=1, cpu_sample=0, ref_sample=0, **off))
 '''
@@ -161,3 +168,41 @@ def test_gpu_arm_line_with_fakes():
     assert abs(r["achieved"] - 364 * 335 * 4096 / 9e-3 / 1e12) <= 1e-9 * r["achieved"]
     assert r["traffic"] is None  # measured for the full-size workload only
     assert "workload" in d["config"]
+
+
+def test_gpu_arm_two_ranks_with_fakes():
+    """Two replicas (gloo in place of NCCL): the value sums both ranks' steps over the slowest
+    rank's time, the CPU baseline is skipped, and a throttled clock record on rank 1 alone
+    makes both ranks measure again."""
+    import socket
+
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), THROTTLED_RANK="1")
+        procs.append(subprocess.Popen(
+            [sys.executable, "-c", "import sys; sys.path.insert(0, '.'); exec(sys.stdin.read())"],
+            cwd=ROOT, env=env, stdin=subprocess.PIPE, stdout=subprocess.PIPE,
+            stderr=subprocess.PIPE, text=True))
+    for p in procs:  # both ranks get their script before either is waited on
+        p.stdin.write(_FAKE_GPU_ARM)
+        p.stdin.close()
+    try:
+        outs = [(p.stdout.read(), p.stderr.read()) for p in procs]
+        for p in procs:
+            p.wait(timeout=600)
+    finally:
+        for p in procs:
+            if p.poll() is None:
+                p.kill()
+    for p, (o, e) in zip(procs, outs):
+        assert p.returncode == 0, e[-3000:]
+    assert not [ln for ln in outs[1][0].splitlines() if ln.startswith("{")]  # rank 1 is silent
+    d = _last_json(outs[0][0])
+    assert d["n_gpus"] == 2 and d["scaling"] == "weak"
+    assert abs(d["value"] - 2 * 4096 * 300 / 10e-3) <= 1e-6 * d["value"]
+    assert d["cpu_baseline"] is None
+    assert d["clocks"]["remeasured_after"] == "a throttled clock record on another rank"
