@@ -25,3 +25,19 @@ def test_library_exports_every_declared_function():
     # the binding knows the same entry points
     assert set(names) <= set(_abi.SIGNATURES), sorted(set(names) - set(_abi.SIGNATURES))
     assert lib.rp_version  # a symbol lookup only
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with the library absent every entry point of the binding raises."""
+    import pytest
+
+    from paper_1810_01780_gb300 import _abi, api, workloads as W
+
+    monkeypatch.setattr(_abi, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_abi, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        api.Medium(W.ice_with_surface())
+    with pytest.raises(RuntimeError, match="not built"):
+        api.Surrogate(seed=0)
+    with pytest.raises(RuntimeError, match="not built"):
+        _abi.lib()
