@@ -46,3 +46,28 @@ def test_ctypes_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == C.sizeof(cls), cname
         for f in cls._fields_:
             assert got[(cname, f[0])] == getattr(cls, f[0]).offset, (cname, f[0])
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    """Every enum value and limit the binding mirrors, printed by a C program built from the
+    header."""
+    want = {"RP_OK": A.RP_OK, "RP_MAX_LAYERS": A.MAX_LAYERS, "RP_MAX_SPHERES": A.MAX_SPHERES}
+    want.update({name: code for code, name in A.ERRORS.items()})
+    want.update({f"RP_MEDIUM_{k.upper()}": v for k, v in A.MEDIUM_KIND.items()})
+    want.update({"RP_FP64": A.PRECISION["fp64"], "RP_FP32_MIXED": A.PRECISION["fp32"]})
+    want.update({f"RP_POL_{k.upper()}": v for k, v in A.POLARIZATION.items()})
+    want.update({f"RP_RHS_{k.upper()}": v for k, v in A.RHS_FORM.items()})
+    want.update({f"RP_ST_{k}": v for k, v in A.STATUS.items()})
+    want.update({f"RP_SOL_{k}": v for k, v in A.SOL_TYPE.items()})
+    lines = ['#include <stdio.h>', '#include "rp.h"', 'int main(void) {']
+    lines += [f'printf("{n} %lld\\n", (long long)({n}));' for n in want]
+    lines += ['return 0;', '}']
+    src, exe = tmp_path / "consts.c", tmp_path / "consts"
+    src.write_text("\n".join(lines))
+    r = subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                        str(exe)], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.fail("constants program does not build:\n" + r.stderr)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = {k: int(v) for k, v in (ln.split() for ln in out.splitlines())}
+    assert got == want
