@@ -90,6 +90,23 @@ def oracle_sample(n_primaries: int, seed: int = 2, cores: int | None = None):
     return sum(r[0] for r in res), sum(r[1] for r in res), wall, cores
 
 
+def host_cpu() -> str:
+    """Architecture and CPU model of this host (lscpu's model name where it reports one)."""
+    import platform
+    import subprocess
+
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return f"{platform.machine()}{', ' + model if model else ''}, {os.cpu_count()} logical CPUs"
+
+
 def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
@@ -114,7 +131,8 @@ def run_reference(args):
                    "sample": f"first {sample} primaries (+ their secondaries) per step",
                    "device": f"{cores} host cores on rank 0; the launch's GPUs are not used"},
         "cpu_baseline": {"value": v, "unit": "ray-steps/s", "cores": cores, "kind": "oracle",
-                         "sample": f"first {sample} primaries of the workload, all secondaries"},
+                         "sample": f"first {sample} primaries of the workload, all secondaries",
+                         "host": host_cpu()},
         "e2e": {"value": v, "unit": "ray-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -398,6 +416,7 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s, r, w, cores = oracle_sample(args.cpu_sample)
         cpu = {"value": s / w, "unit": "ray-steps/s", "cores": cores, "kind": "oracle",
+               "host": host_cpu(),
                "sample": f"first {args.cpu_sample} primaries of the workload with all their "
                          f"secondaries ({r} rays, {s} accepted steps, {w:.2f} s wall)"}
 
