@@ -2,8 +2,8 @@
 
 The surrogate maps a source-receiver geometry (z_s, z_r, D) to, for up to two solutions
 (sorted by travel time), an existence logit and five regression targets (launch angle,
-receive angle, travel time, path length, amplitude; see ``paper_1810_01780_gb300.surrogate`` for
-the normalisation).  Network: 3 -> 256 -> 256 -> 256 -> 256 -> 12, GELU (erf form) after every
+receive angle, travel time, path length, amplitude; the normalisation is stated with
+rp_surrogate_encode in include/rp.h).  Network: 3 -> 256 -> 256 -> 256 -> 256 -> 12, GELU (erf form) after every
 hidden layer, linear output.  Loss per sample: for each slot k, the logistic loss of the
 existence logit against y_k in [0, 1], plus y_k times half the squared error of the five
 regression outputs.  Mean over the batch.
