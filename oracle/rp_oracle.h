@@ -10,8 +10,8 @@
  * c0 = 299 792 458 m/s; a ray state is y = (r, t, T) with r the position, t the unit tangent
  * dr/ds, T the travel time, s the arc length (Sec. 2, Eq. 1).
  *
- * Parity status of every function is stated beside it; all are pinned by the CPU tests
- * (closed forms, invariants, brute force) except where "parity unpinned" is written.
+ * Parity status of every function is stated beside it: each is pinned by the CPU tests
+ * (closed forms, invariants, brute force, exact geometry); none is unpinned.
  */
 #ifndef RP_ORACLE_H
 #define RP_ORACLE_H
@@ -95,37 +95,46 @@ typedef struct {
 extern "C" {
 #endif
 
-/* Cash-Karp tableau as used by the stepper (exported for the order-condition tests). */
+/* Cash-Karp tableau as used by the stepper (exported for the order-condition tests).
+ * Pinned: the 17 order conditions to order 5 (b5) and the 8 to order 4 (b4). */
 extern const double or_ck_c[6];
 extern const double or_ck_a[6][5];
 extern const double or_ck_b5[6];
 extern const double or_ck_b4[6];
 
 /* One Cash-Karp step of the scalar quadrature y' = sum_k coef[k] x^k from (x0, y0) with
- * step h, returning the 5th- and 4th-order results (tableau exactness tests). */
+ * step h, returning the 5th- and 4th-order results (tableau exactness tests).
+ * Pinned: exact for polynomials up to the order of each weight set. */
 void or_ck_poly_step(const double *coef, int32_t n_coef, double x0, double y0, double h,
                      double *y5, double *y4);
 
 /* n and grad n of the medium at r for a ray in region `layer` (layered: that region's
- * formula, continued smoothly beyond its boundaries; grid: trilinear, clamped to the box). */
+ * formula, continued smoothly beyond its boundaries; grid: trilinear, clamped to the box).
+ * Pinned: the profile and its derivative at a point; exact on linear grid fields; offsets. */
 void or_medium_eval(const or_medium *m, int32_t layer, const double *r, double *n, double *g);
 
-/* Layer index containing depth z. */
+/* Layer index containing depth z (a boundary depth belongs to the layer below).
+ * Pinned: start layer of rays just above, at and just below a boundary. */
 int32_t or_layer_of(const or_medium *m, double z);
 
-/* Region containing r: OR_MAX_LAYERS + j inside sphere j, else the layer of r[2]. */
+/* Region containing r: OR_MAX_LAYERS + j inside sphere j, else the layer of r[2].
+ * Pinned: rays started at the centre and just inside the surface of a sphere. */
 int32_t or_region_of(const or_medium *m, const double *r);
 
 /* FP32 node samples (n, grad n) from FP32 node values of n: central differences inside,
- * one-sided differences on the faces, evaluated in double and rounded to float. */
+ * one-sided differences on the faces, evaluated in double and rounded to float.
+ * Pinned: exact gradients of linear fields on every node, faces included. */
 void or_grid_prepare(const float *n, int32_t nx, int32_t ny, int32_t nz, double spacing,
                      float *out4);
 
 /* Right-hand side of the ray equations (PROJECTED = Eq. 1 for unit t; PARAXIAL = Eq. 2;
- * MOMENTUM = Eq. 1 as written, on the state (r, p = n t, T): r' = p / |p|, p' = grad n). */
+ * MOMENTUM = Eq. 1 as written, on the state (r, p = n t, T): r' = p / |p|, p' = grad n).
+ * Pinned: values at a point; t' orthogonal to t; Snell invariant and closed forms along
+ * whole rays for PROJECTED and MOMENTUM; PARAXIAL shown less accurate. */
 void or_rhs(const or_medium *m, int32_t layer, int32_t form, const double *y, double *k);
 
-/* One Cash-Karp step of the ray system; returns the unscaled error measure
+/* One Cash-Karp step of the ray system (pinned: local error ~ h^6; the error measure
+ * ~ h^4, its position part per unit step); returns the unscaled error measure
  * max(|sum (b5-b4) k_r|, h |sum (b5-b4) k_t|); y5 is the 5th-order state (t not normalised).
  * MOMENTUM: the stages run on p = n(r0) t0; y5 holds p5 in place of t (its direction is t) and
  * the direction error is h |sum (b5-b4) k_p| / n(r0). */
@@ -134,16 +143,22 @@ double or_ck_step(const or_medium *m, int32_t layer, int32_t form, const double 
 
 /* Boundary split (Snell + Fresnel) at a plane with unit normal nrm pointing toward the
  * incident side.  Outputs reflected and refracted unit directions, amplitude factors r, tau
- * and tir (1 = total internal reflection). */
+ * and tir (1 = total internal reflection).
+ * Pinned: vector Snell law, plane of incidence, total internal reflection past the critical
+ * angle, matched media, exact geometry of splits at constant layers and spheres. */
 void or_split_dirs(const double *t, const double *nrm, double n1, double n2, int32_t pol,
                    double *t_refl, double *t_refr, double *r, double *tau, int32_t *tir);
 
 /* Fresnel coefficients: amplitude reflection r and transmission tau for incidence cosine
- * cos_i and refraction cosine cos_t (Sec. 2, last paragraph of the boundary module). */
+ * cos_i and refraction cosine cos_t (Sec. 2, last paragraph of the boundary module).
+ * Pinned: R + T = 1 (s, p, unpolarised), normal incidence, Brewster angle, matched media. */
 void or_fresnel(double n1, double n2, double cos_i, double cos_t, int32_t pol, double *r,
                 double *tau);
 
 /* Trace n primaries (SoA: pos[3][n], dir[3][n], amp[n]) with every secondary they spawn.
+ * Pinned: straight lines at constant n; closed-form range, path and time in the exponential
+ * profile; Fermat's principle in the random grid; splits, receivers, break conditions, step
+ * law and landing against exact geometry (the CPU pin tests list each one).
  * Receivers: n_rx spheres, centre AoS rx_c[n_rx][3], radius rx_r[n_rx].
  * Writes up to out_cap rays and hit_cap hits; returns the total number of rays (may exceed
  * out_cap), *n_hits the total number of hits (may exceed hit_cap). */
@@ -152,9 +167,10 @@ int64_t or_trace(const or_medium *m, const or_params *p, int64_t n, const double
                  const double *rx_r, or_ray *out, int64_t out_cap, or_hit *hits,
                  int64_t hit_cap, int64_t *n_hits);
 
-/* Source-receiver path finding: for each pair (z_s, z_r, D) scan n_angles launch angles in
- * [0, pi], bracket sign changes of the vertical miss at x = D and bisect in the launch angle
- * until |miss| < hit_tol.  Solutions sorted by travel time, at most max_sol per pair;
+/* Source-receiver path finding (pinned: the paper's accuracy study and closed-form roots in
+ * the Snell invariant, launch and receive angles; vertical pairs): for each pair
+ * (z_s, z_r, D) scan n_angles launch angles in [0, pi], bracket sign changes of the vertical
+ * miss at x = D and bisect in the launch angle until |miss| < hit_tol.  Solutions sorted by travel time, at most max_sol per pair;
  * count[i] receives their number.  Returns 0. */
 int32_t or_find_paths(const or_medium *m, const or_params *p, int64_t n_pairs,
                       const double *zs, const double *zr, const double *dist,
