@@ -20,6 +20,10 @@ A = b^2, B = -2ab, C = a^2 - p^2 > 0):
 A ray launched upward turns where w = 0, i.e. n(z_t) = p.  ``quad_branch`` evaluates the same
 three integrals by adaptive quadrature in z so that the closed forms are not trusted blindly.
 
+Parity: pinned by adaptive Gauss-Kronrod quadrature of the same integrals (with the
+turning-point substitution), the b -> 0 straight-line limit, and solutions that, traced by
+the oracle, hit their receivers (tests/test_analytic_pins.py).
+
 This module is test infrastructure: only tests, the smoke check and the benchmark's CPU
 baseline import it.
 """

@@ -11,6 +11,11 @@ regression outputs.  Mean over the batch.
 Everything here is plain numpy in float64, layer by layer, with no fusion; weights are taken
 as given (the GPU keeps FP32 master weights and multiplies with their BF16 rounding: pass
 ``bf16_round(W)`` to compare).  Only the test suite imports this module.
+
+Parity: pinned by central finite differences of the loss for every layer's weights and
+biases, GELU identities (odd part, Phi(1) and its derivative), the loss at known points, the
+first Adam step (-lr sign(g)) and BF16 rounding of hand-made bit patterns
+(tests/test_mlp_oracle_pins.py).
 """
 from __future__ import annotations
 
