@@ -1,0 +1,94 @@
+"""The helpers the GPU parity tests rely on (tests/parity.py), on the CPU: rays are matched by
+their place in the split tree whatever order the secondaries come in, identical records pass,
+and a moved end point, a missing subtree or swapped siblings fail."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_01780_gb300 import workloads as W
+from parity import check_fp64, match, oracle_rays, subtree_of_roots, tilt
+
+
+@pytest.fixture(scope="module")
+def rays(oracle_lib):
+    cfg = W.batched(n=300, seed=11)
+    ref, _ = oracle.trace(cfg["medium"], cfg["params"], *cfg["rays"])
+    o = oracle_rays(ref)
+    assert (o["generation"] >= 2).any()  # secondaries of secondaries
+    return o, cfg["params"]["tol"], 300
+
+
+def _shuffled(o, n_prim, seed):
+    """The same records with the secondaries in another order that keeps every parent before
+    its secondaries (by generation, random within one), parents renumbered."""
+    rng = np.random.default_rng(seed)
+    sec = np.arange(n_prim, len(o["parent"]))
+    order = np.concatenate([np.arange(n_prim),
+                            sec[np.lexsort((rng.random(len(sec)), o["generation"][sec]))]])
+    new_of = np.empty_like(order)
+    new_of[order] = np.arange(len(order))
+    g = {k: v[order].copy() for k, v in o.items()}
+    g["parent"] = np.where(g["parent"] < 0, -1, new_of[np.maximum(g["parent"], 0)])
+    return g
+
+
+def test_identical_records_in_another_order_match(rays):
+    o, tol, n = rays
+    g = _shuffled(o, n, 1)
+    assert not np.array_equal(g["pos"], o["pos"])  # really reordered
+    gi, oi, only_g, only_o = match(g, o)
+    assert not only_g and not only_o and len(gi) == len(o["path"])
+    for k in o:
+        if k != "parent":
+            np.testing.assert_array_equal(g[k][gi], o[k][oi], err_msg=k)
+    assert check_fp64(g, o, tol) == 1.0
+
+
+def test_a_moved_end_point_fails(rays):
+    o, tol, n = rays
+    g = _shuffled(o, n, 2)
+    j = len(g["path"]) - 1
+    g["pos"][j] += 1e-6 * (g["path"][j] + 1.0) * np.array([1.0, 0.0, 0.0]) * 5
+    with pytest.raises(AssertionError):
+        check_fp64(g, o, tol)
+
+
+def test_a_missing_subtree_fails(rays):
+    o, tol, n = rays
+    g = _shuffled(o, n, 3)
+    last = len(g["path"]) - 1  # a ray of the last generation: no secondaries of its own
+    keep = np.arange(len(g["path"])) != last
+    h = {k: v[keep] for k, v in g.items()}
+    gi, oi, only_g, only_o = match(h, o)
+    assert not only_g and len(only_o) == 1
+    with pytest.raises(AssertionError):
+        check_fp64(h, o, tol)
+
+
+def test_swapped_siblings_fail(rays):
+    o, tol, n = rays
+    g = _shuffled(o, n, 4)
+    # two secondaries of one parent, cast at different splits
+    par = g["parent"]
+    for p in np.unique(par[par >= 0]):
+        kids = np.nonzero(par == p)[0]
+        if len(kids) >= 2 and g["path"][kids[0]] != g["path"][kids[1]]:
+            a, b = kids[:2]
+            break
+    else:
+        pytest.skip("no parent with two secondaries")
+    g["seq"][[a, b]] = g["seq"][[b, a]]
+    with pytest.raises(AssertionError):
+        check_fp64(g, o, tol)
+
+
+def test_subtrees_and_tilt(rays):
+    o, _, n = rays
+    idx, root = subtree_of_roots(o["parent"], np.array([3, 7]))
+    assert set(root[idx]) == {3, 7} and 3 in idx and 7 in idx
+    others = np.setdiff1d(np.arange(len(root)), idx)
+    assert not np.isin(root[others], [3, 7]).any()
+    d = W.isotropic_dirs(np.random.default_rng(0), 1000)
+    t = tilt(d, 1e-3, 5)
+    assert np.allclose(np.linalg.norm(t, axis=0), 1.0, atol=1e-12)
+    assert np.allclose(np.arccos(np.clip((t * d).sum(0), -1, 1)), 1e-3, rtol=1e-5)
