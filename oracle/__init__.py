@@ -61,6 +61,11 @@ class Medium(C.Structure):
         ("sph_n0", C.c_double * MAX_SPHERES), ("sph_dn", C.c_double * MAX_SPHERES),
         ("sph_z0", C.c_double * MAX_SPHERES), ("sph_off", C.c_double * MAX_SPHERES),
         ("sph_absorb", C.c_int32 * MAX_SPHERES),
+        ("srf_on", C.c_int32 * MAX_LAYERS), ("srf_sx", C.c_double * MAX_LAYERS),
+        ("srf_sy", C.c_double * MAX_LAYERS), ("hf_nx", C.c_int32 * MAX_LAYERS),
+        ("hf_ny", C.c_int32 * MAX_LAYERS), ("hf_ox", C.c_double * MAX_LAYERS),
+        ("hf_oy", C.c_double * MAX_LAYERS), ("hf_dx", C.c_double * MAX_LAYERS),
+        ("hf_dy", C.c_double * MAX_LAYERS), ("hf", C.POINTER(C.c_double) * MAX_LAYERS),
     ]
 
 
@@ -115,6 +120,11 @@ def lib():
             L.or_medium_eval.argtypes = [C.POINTER(Medium), C.c_int32, dp, dp, dp]
             L.or_layer_of.restype = C.c_int32
             L.or_layer_of.argtypes = [C.POINTER(Medium), C.c_double]
+            L.or_layer_at.restype = C.c_int32
+            L.or_layer_at.argtypes = [C.POINTER(Medium), dp]
+            L.or_boundary_depth.restype = C.c_double
+            L.or_boundary_depth.argtypes = [C.POINTER(Medium), C.c_int32, C.c_double,
+                                            C.c_double, dp, dp]
             L.or_grid_prepare.argtypes = [C.POINTER(C.c_float), C.c_int32, C.c_int32, C.c_int32,
                                           C.c_double, C.POINTER(C.c_float)]
             L.or_rhs.argtypes = [C.POINTER(Medium), C.c_int32, C.c_int32, dp, dp]
@@ -164,6 +174,26 @@ class OracleMedium:
                 m.sph_z0[j] = float(S.get("z0", 1.0))
                 m.sph_off[j] = float(S.get("off", 0.0))
                 m.sph_absorb[j] = int(bool(S.get("absorb", False)))
+            # non-horizontal boundaries: a tilted plane of unit normal N (N_z > 0) through
+            # (0, 0, z_top), slopes -N_x / N_z and -N_y / N_z, plus an optional height field
+            self.heights = []
+            for srf in desc.get("surfaces", []):
+                k = int(srf["layer"])
+                if not 1 <= k < len(layers):
+                    raise ValueError("a surface replaces the boundary of layer 1..n_layers-1")
+                N = np.asarray(srf.get("normal", (0.0, 0.0, 1.0)), dtype=np.float64)
+                if not N[2] > 0.0:
+                    raise ValueError("surface normal needs a positive z component")
+                m.srf_on[k] = 1
+                m.srf_sx[k] = -N[0] / N[2]
+                m.srf_sy[k] = -N[1] / N[2]
+                if srf.get("height") is not None:
+                    h = np.ascontiguousarray(srf["height"], dtype=np.float64)  # (ny, nx)
+                    m.hf_ny[k], m.hf_nx[k] = h.shape
+                    m.hf_ox[k], m.hf_oy[k] = (float(v) for v in srf["origin"])
+                    m.hf_dx[k], m.hf_dy[k] = (float(v) for v in srf["spacing"])
+                    m.hf[k] = _dptr(h)
+                    self.heights.append(h)
             self.grid4 = None
         elif desc["kind"] == "grid":
             n = np.ascontiguousarray(desc["n"], dtype=np.float32)  # (nz, ny, nx)
@@ -192,6 +222,17 @@ class OracleMedium:
 
     def layer_of(self, z):
         return lib().or_layer_of(C.byref(self.c), float(z))
+
+    def layer_at(self, r):
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        return lib().or_layer_at(C.byref(self.c), _dptr(r))
+
+    def boundary_depth(self, k, x, y):
+        """(depth, dz/dx, dz/dy) of boundary k at (x, y)."""
+        gx, gy = C.c_double(), C.c_double()
+        z = lib().or_boundary_depth(C.byref(self.c), int(k), float(x), float(y), C.byref(gx),
+                                    C.byref(gy))
+        return z, gx.value, gy.value
 
 
 def make_params(p: dict) -> Params:

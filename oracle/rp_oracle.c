@@ -71,7 +71,65 @@ int32_t or_layer_of(const or_medium *m, double z)
     return k;
 }
 
-/* Region containing r: inside sphere j -> OR_MAX_LAYERS + j, else the layer of its depth. */
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Bilinear height field H_k at (x, y) and its partial derivatives (zero where the point lies
+ * beyond the nodes along that axis: the field is held at its edge values there). */
+static double height_field(const or_medium *m, int32_t k, double x, double y, double *hx,
+                           double *hy)
+{
+    const int32_t nx = m->hf_nx[k], ny = m->hf_ny[k];
+    const double u_raw = (x - m->hf_ox[k]) / m->hf_dx[k];
+    const double v_raw = (y - m->hf_oy[k]) / m->hf_dy[k];
+    const double u = clampd(u_raw, 0.0, (double)(nx - 1));
+    const double v = clampd(v_raw, 0.0, (double)(ny - 1));
+    int32_t i = (int32_t)floor(u), j = (int32_t)floor(v);
+    if (i > nx - 2) i = nx - 2;
+    if (j > ny - 2) j = ny - 2;
+    const double fu = u - i, fv = v - j;
+    const double *h = m->hf[k];
+    const double h00 = h[(int64_t)j * nx + i], h10 = h[(int64_t)j * nx + i + 1];
+    const double h01 = h[(int64_t)(j + 1) * nx + i], h11 = h[(int64_t)(j + 1) * nx + i + 1];
+    *hx = (u_raw >= 0.0 && u_raw <= nx - 1)
+              ? ((1.0 - fv) * (h10 - h00) + fv * (h11 - h01)) / m->hf_dx[k] : 0.0;
+    *hy = (v_raw >= 0.0 && v_raw <= ny - 1)
+              ? ((1.0 - fu) * (h01 - h00) + fu * (h11 - h10)) / m->hf_dy[k] : 0.0;
+    return (1.0 - fu) * (1.0 - fv) * h00 + fu * (1.0 - fv) * h10 + (1.0 - fu) * fv * h01 +
+           fu * fv * h11;
+}
+
+/* Depth of boundary k at (x, y): the plane z_top[k], or the tilted plane plus the height
+ * field of a non-horizontal boundary; its slopes in *dzdx, *dzdy (may be NULL). */
+double or_boundary_depth(const or_medium *m, int32_t k, double x, double y, double *dzdx,
+                         double *dzdy)
+{
+    double z = m->z_top[k], gx = 0.0, gy = 0.0;
+    if (m->srf_on[k]) {
+        z += m->srf_sx[k] * x + m->srf_sy[k] * y;
+        gx = m->srf_sx[k];
+        gy = m->srf_sy[k];
+        if (m->hf[k]) {
+            double hx, hy;
+            z += height_field(m, k, x, y, &hx, &hy);
+            gx += hx;
+            gy += hy;
+        }
+    }
+    if (dzdx) *dzdx = gx;
+    if (dzdy) *dzdy = gy;
+    return z;
+}
+
+/* Layer containing the point r: the last boundary at or above it, at its (x, y). */
+int32_t or_layer_at(const or_medium *m, const double *r)
+{
+    int32_t k = 0;
+    for (int32_t j = 1; j < m->n_layers; ++j)
+        if (r[2] >= or_boundary_depth(m, j, r[0], r[1], NULL, NULL)) k = j;
+    return k;
+}
+
+/* Region containing r: inside sphere j -> OR_MAX_LAYERS + j, else the layer of the point. */
 int32_t or_region_of(const or_medium *m, const double *r)
 {
     for (int32_t j = 0; j < m->n_spheres; ++j) {
@@ -79,7 +137,7 @@ int32_t or_region_of(const or_medium *m, const double *r)
         for (int a = 0; a < 3; ++a) d2 += (r[a] - m->sph_c[j][a]) * (r[a] - m->sph_c[j][a]);
         if (d2 < m->sph_R[j] * m->sph_R[j]) return OR_MAX_LAYERS + j;
     }
-    return or_layer_of(m, r[2]);
+    return or_layer_at(m, r);
 }
 
 /* n(z) = n0 - dn exp(-z/z0) + off and dn/dz = (dn/z0) exp(-z/z0) of region k (a layer, or
@@ -113,8 +171,6 @@ static int32_t region_absorbs(const or_medium *m, int32_t k)
 {
     return k >= OR_MAX_LAYERS ? m->sph_absorb[k - OR_MAX_LAYERS] : m->absorb[k];
 }
-
-static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 static void grid_eval(const or_medium *m, const double *r, double *n, double *g)
 {
@@ -358,8 +414,8 @@ static double event_g(const trace_ctx *c, int32_t layer, int kind, double stop_s
 {
     const or_medium *m = c->m;
     const or_params *p = c->p;
-    if (kind == EV_TOP) return y[2] - m->z_top[layer];
-    if (kind == EV_BOTTOM) return m->z_top[layer + 1] - y[2];
+    if (kind == EV_TOP) return y[2] - or_boundary_depth(m, layer, y[0], y[1], NULL, NULL);
+    if (kind == EV_BOTTOM) return or_boundary_depth(m, layer + 1, y[0], y[1], NULL, NULL) - y[2];
     if (kind >= EV_SPHERE) {
         const int32_t j = kind - EV_SPHERE;
         const double g = sphere_dist(m, j, y) - m->sph_R[j];
@@ -369,15 +425,15 @@ static double event_g(const trace_ctx *c, int32_t layer, int kind, double stop_s
     return stop_sign * f;
 }
 
-/* Puts the landing point exactly on the surface: the plane's depth, the stop plane by its
- * normal, the sphere radially. */
+/* Puts the landing point exactly on the surface: a layer boundary at the point's (x, y)
+ * depth, the stop plane by its normal, the sphere radially. */
 static void snap_to_plane(const trace_ctx *c, int32_t layer, int kind, double *y)
 {
     const or_params *p = c->p;
     if (kind == EV_TOP) {
-        y[2] = c->m->z_top[layer];
+        y[2] = or_boundary_depth(c->m, layer, y[0], y[1], NULL, NULL);
     } else if (kind == EV_BOTTOM) {
-        y[2] = c->m->z_top[layer + 1];
+        y[2] = or_boundary_depth(c->m, layer + 1, y[0], y[1], NULL, NULL);
     } else if (kind >= EV_SPHERE) {
         const int32_t j = kind - EV_SPHERE;
         const double q = c->m->sph_R[j] / sphere_dist(c->m, j, y);
@@ -628,9 +684,21 @@ static void trace_one(trace_ctx *c, const start_state *st)
                 const double d = sphere_dist(m, j, y);
                 for (int a = 0; a < 3; ++a)
                     nrm[a] = (inside ? -1.0 : 1.0) * (y[a] - m->sph_c[j][a]) / d;
-                other = inside ? or_layer_of(m, y[2]) : OR_MAX_LAYERS + j;
+                other = inside ? or_layer_at(m, y) : OR_MAX_LAYERS + j;
             } else {
                 other = (ev == EV_TOP) ? layer - 1 : layer + 1;
+                const int32_t kb = (ev == EV_TOP) ? layer : layer + 1;
+                if (m->srf_on[kb]) {
+                    /* the surface z - zb(x, y) = 0: normal (-dzb/dx, -dzb/dy, 1) / |...|,
+                     * pointing into the layer below; toward the incident side */
+                    double bx, by;
+                    or_boundary_depth(m, kb, y[0], y[1], &bx, &by);
+                    const double q = sqrt(bx * bx + by * by + 1.0);
+                    const double sg = (ev == EV_TOP) ? 1.0 : -1.0;
+                    nrm[0] = -sg * bx / q;
+                    nrm[1] = -sg * by / q;
+                    nrm[2] = sg / q;
+                }
             }
             double zb = y[2], n1, n2, dd;
             layer_eval(m, layer, zb, &n1, &dd);

@@ -53,6 +53,20 @@ typedef struct {
     double sph_c[OR_MAX_SPHERES][3], sph_R[OR_MAX_SPHERES], sph_n0[OR_MAX_SPHERES],
            sph_dn[OR_MAX_SPHERES], sph_z0[OR_MAX_SPHERES], sph_off[OR_MAX_SPHERES];
     int32_t sph_absorb[OR_MAX_SPHERES];
+    /* Non-horizontal boundaries (boundary shapes beyond the plane, the paragraph after Fig. 1):
+     * with srf_on[k] != 0 the boundary between layers k-1 and k (k >= 1) is the surface
+     *   z = zb_k(x, y) = z_top[k] + srf_sx[k] x + srf_sy[k] y + H_k(x, y)
+     * instead of the plane z = z_top[k]: a tilted plane of slopes (srf_sx, srf_sy) through
+     * (0, 0, z_top[k]) plus, if hf[k] != NULL, the height field H_k, the bilinear interpolant
+     * of hf_nx[k] x hf_ny[k] node heights hf[k] (x fastest; node (i, j) at
+     * (hf_ox[k] + i hf_dx[k], hf_oy[k] + j hf_dy[k])), held at its edge values outside the
+     * nodes.  Layer k is zb_k(x, y) <= z < zb_{k+1}(x, y); the caller keeps the surfaces
+     * from crossing where rays travel.  Not combined with spheres. */
+    int32_t srf_on[OR_MAX_LAYERS];
+    double srf_sx[OR_MAX_LAYERS], srf_sy[OR_MAX_LAYERS];
+    int32_t hf_nx[OR_MAX_LAYERS], hf_ny[OR_MAX_LAYERS];
+    double hf_ox[OR_MAX_LAYERS], hf_oy[OR_MAX_LAYERS], hf_dx[OR_MAX_LAYERS], hf_dy[OR_MAX_LAYERS];
+    const double *hf[OR_MAX_LAYERS];
 } or_medium;
 
 /* Integration and termination parameters. */
@@ -116,6 +130,16 @@ void or_medium_eval(const or_medium *m, int32_t layer, const double *r, double *
 /* Layer index containing depth z (a boundary depth belongs to the layer below).
  * Pinned: start layer of rays just above, at and just below a boundary. */
 int32_t or_layer_of(const or_medium *m, double z);
+
+/* Depth zb_k(x, y) of boundary k (1 <= k < n_layers) and its slopes dzb/dx, dzb/dy (the
+ * plane z_top[k], or the tilted plane plus height field of or_medium).
+ * Pinned: a height field sampled from a plane reproduces that plane; slopes of a bump. */
+double or_boundary_depth(const or_medium *m, int32_t k, double x, double y, double *dzdx,
+                         double *dzdy);
+
+/* Layer containing the point r: the last k with r[2] >= zb_k(r[0], r[1]) (0 if none).
+ * Pinned: start layer above, on and below a tilted boundary and a height field. */
+int32_t or_layer_at(const or_medium *m, const double *r);
 
 /* Region containing r: OR_MAX_LAYERS + j inside sphere j, else the layer of r[2].
  * Pinned: rays started at the centre and just inside the surface of a sphere. */
