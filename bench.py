@@ -43,8 +43,31 @@ N_RAYS = 1_048_576
 # 13, control 3, event tests 10, float-float state update 80.  The 6 exp, 6 reciprocals and
 # the pow of the step control are not counted.
 FLOPS_PER_ATTEMPT_F32 = 364
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
+# The same Runge-Kutta step in FP64 (trace_core.cuh, PrecF64): stage combinations 75, stage
+# states 30, medium 30, projection 36, fifth-order sums 35, error sums 36, increments 10, error
+# norms 13, control 3, event tests 10, state update 13 (position, direction, travel time and
+# arc length sums and the direction's renormalisation); 6 exp, 6 divisions and 3 square roots
+# not counted.
+FLOPS_PER_ATTEMPT_F64 = 291
+# Eq. 1 as written on p = n t (ck_step_momentum, FP64): stage combinations 150, stage states 60,
+# medium 30, |p| 30, momentum 3, fifth-order sums 49, error sums 54, increments and their norms
+# 24, control 3, event tests 10, state update 13; 22 divisions, 9 square roots, 6 exp not
+# counted.
+FLOPS_PER_ATTEMPT_MOMENTUM = 432
+# Spheres (FP32-mixed): the layered step plus, per attempted step, the float-float distance to
+# each of the workload's two spheres from the candidate end point (91 flops each: the
+# difference, its square and sum in float-float, (|w|^2 - R^2) / (|w| + R)); FP64: 13 each.
+FLOPS_PER_ATTEMPT_SPHERES_F32 = 364 + 2 * 91
+FLOPS_PER_ATTEMPT_SPHERES_F64 = 291 + 2 * 13
+SM_COUNT_NOMINAL = 152  # GB300, for the nominal comparison only
+# Non-horizontal boundaries: the layered step plus the surface event tests, evaluated in FP64 in
+# both precisions (the vertical offset from a tilted plane: 12 flops, counted twice per step;
+# the height field's bilinear evaluations are not counted); FP32-mixed counts its FP32 flops.
+FLOPS_PER_ATTEMPT_SURFACES_F32 = 364
+FLOPS_PER_ATTEMPT_SURFACES_F64 = 291 + 2 * 12
+# Gridded medium: 8 float4 corner samples (128 B) per medium evaluation, 6 evaluations per
+# attempted step.
+BYTES_PER_ATTEMPT_GRID = 768
 
 
 def _env_rank():
@@ -258,8 +281,34 @@ MLP_FLOPS_FWD = 2 * (3 * 256 + 3 * 256 * 256 + 256 * 12)  # per row, multiply-ad
 
 # DRAM bytes (read + write) of the four k_trace_wave<PrecF32, MediumLayered> launches of one
 # step of the 1,048,576-ray batched workload, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of the current kernel; to be re-measured whenever the kernel changes
-TRACE_DRAM_BYTES_PER_STEP = 525_434_880
+# dram__bytes_write.sum) of the current kernel; None until the current kernel is captured
+TRACE_DRAM_BYTES_PER_STEP = None
+
+
+def peaks_leg(rp, local):
+    """The roofline denominators of this GPU measured by the library's microkernels
+    (rp_measure_peaks), with the SM clock sampled while they run."""
+    with ClockSampler(local) as clk:
+        pk = rp.measure_peaks()
+    pk["clocks"] = clk.summary()
+    pk["how"] = ("rp_measure_peaks: FP32 / FP64 FMA chains (8 independent per thread, 1,024 "
+                 "threads per SM) and 16-byte L1-bypassing loads over a 32 MiB L2-resident "
+                 "buffer; best of 3 timed launches each")
+    return pk
+
+
+def at_clock(rate, pk, sm_mhz):
+    """A measured peak rate moved to the SM clock of the run it is the denominator for (the
+    microkernels and the run may see different clocks under the power cap)."""
+    mhz = (pk.get("clocks") or {}).get("sm_mhz")
+    return rate * (sm_mhz / mhz) if (mhz and sm_mhz) else rate
+
+
+def alu_roofline(flops_per_attempt, attempts, ms, peak, kernel, basis):
+    achieved = flops_per_attempt * attempts / (ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None, "kernel": kernel,
+            "flops_per_attempted_step": flops_per_attempt, "peak_basis": basis}
 
 
 def _sync_time(fn):
@@ -370,9 +419,10 @@ def reduce_over_ranks(total_ms, counts, device):
     return float(t[0]), [float(v) for v in c]
 
 
-def fp32_fp64_leg(rp, cfg, flush, steps, workload):
+def fp32_fp64_leg(rp, cfg, flush, steps, flops, peaks, workload):
     """One trace workload in both precisions: ray-steps/s and rays/s (kernel time, L2 flushed
-    before each call) and the FP32-mixed end points of the primaries against FP64."""
+    before each call), each precision's ALU roofline (flops[prec] per attempted step against
+    peaks[prec], TFLOP/s) and the FP32-mixed end points of the primaries against FP64."""
     med = rp.Medium(cfg["medium"])
     rays = rp.PreparedRays(*cfg["rays"])
     buf = rp.TraceBuffers(3 * rays.n, 0, fields=("end_pos", "path", "time", "status"))
@@ -380,16 +430,23 @@ def fp32_fp64_leg(rp, cfg, flush, steps, workload):
     for prec in ("fp32", "fp64"):
         prm = rp.make_params(cfg["params"], prec)
         rp.trace_into(med, rays, prm, buf)  # warm-up
-        ts, acc, nr = [], 0, 0
+        ts, acc, att, nr = [], 0, 0, 0
         for _ in range(steps):
             flush.fill_(1.0)
             st = rp.trace_into(med, rays, prm, buf)
             ts.append(st.kernel_ms)
             acc += st.steps_accepted
+            att += st.steps_accepted + st.steps_rejected + st.steps_root
             nr += st.rays
         sec = sum(ts) / 1e3
-        leg["fp32_mixed" if prec == "fp32" else "fp64"] = {
-            "ray_steps_per_s": acc / sec, "rays_per_s": nr / sec, "ms_per_step": 1e3 * sec / len(ts)}
+        name = "fp32_mixed" if prec == "fp32" else "fp64"
+        leg[name] = {
+            "ray_steps_per_s": acc / sec, "rays_per_s": nr / sec, "ms_per_step": 1e3 * sec / len(ts),
+            "roofline": alu_roofline(flops[prec], att, 1e3 * sec, peaks[prec][0],
+                                     "k_trace_wave<%s, %s>" % (
+                                         "PrecF32" if prec == "fp32" else "PrecF64",
+                                         cfg.get("kernel_medium", "MediumLayered")),
+                                     peaks[prec][1])}
         ends[prec] = (buf.t["end_pos"][:, :rays.n].clone(), buf.t["time"][:rays.n].clone())
     dpos = (ends["fp32"][0] - ends["fp64"][0]).norm(dim=0)
     dt = (ends["fp32"][1] - ends["fp64"][1]).abs()
@@ -426,15 +483,26 @@ def run_gpu(args):
     import paper_1810_01780_gb300 as rp
     from paper_1810_01780_gb300 import workloads as W
 
+    from paper_1810_01780_gb300 import autotune
+
+    # roofline denominators of this GPU, measured before anything else runs
+    peaks = peaks_leg(rp, local)
+    mp = _peaks()
+
     n_rays = args.rays
     seed = 2 + rank  # weak scaling: every rank traces its own batch
     cfg = W.batched(n_rays, seed)
     med = rp.Medium(cfg["medium"])
     rays = rp.PreparedRays(*cfg["rays"], receivers=cfg["receivers"])
     cap = int(5.5 * n_rays)
-    prm32 = rp.make_params(cfg["params"], "fp32")
     buf = rp.TraceBuffers(cap, 4096)
     stream = torch.cuda.current_stream()
+    # the scheduling knobs (speed only, never a record) tuned on this batch
+    t0 = time.perf_counter()
+    tuned = autotune.tune_trace(med, rays, cfg["params"], buf, "fp32", idle=(192, 256, 384),
+                                flush=(1, 2, 4), block=(64, 128, 256), reps=1)
+    tune_s = time.perf_counter() - t0
+    prm32 = rp.make_params(tuned["params"], "fp32")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def one_step(prm, b):
@@ -476,6 +544,7 @@ def run_gpu(args):
     # primary end points of the FP32 run for the stated error against FP64
     end32 = buf.t["end_pos"][:, :n_rays].clone()
     t32 = buf.t["time"][:n_rays].clone()
+    s32 = buf.t["status"][:n_rays].clone()
 
     # e2e: host (pinned) -> device -> rp_trace -> host, through the same C ABI call
     hp = torch.from_numpy(np.ascontiguousarray(cfg["rays"][0])).pin_memory()
@@ -510,44 +579,76 @@ def run_gpu(args):
     modes = {"fp32_mixed": {"ray_steps_per_s": value, "rays_per_s": rays_all / (total_ms_max / 1e3),
                             "ms_per_step": total_ms_max / args.steps}}
     err = None
+    pk32 = at_clock(peaks["fp32_tflops"], peaks, clocks["sm_mhz"])
+    basis32 = ("rp_measure_peaks FP32 FMA rate %.1f TFLOP/s at %s MHz, moved to the run's median "
+               "SM clock" % (peaks["fp32_tflops"], (peaks["clocks"] or {}).get("sm_mhz")))
+    pk64 = at_clock(peaks["fp64_tflops"], peaks, clocks["sm_mhz"])
+    basis64 = ("rp_measure_peaks FP64 FMA rate %.3f TFLOP/s at %s MHz, moved to the run's median "
+               "SM clock" % (peaks["fp64_tflops"], (peaks["clocks"] or {}).get("sm_mhz")))
     if not args.no_fp64:
         prm64 = rp.make_params(cfg["params"], "fp64")
         one_step(prm64, buf)
-        t64 = []
-        acc64 = rays64 = 0
+        t64, k64 = [], []
+        acc64 = rays64 = att64 = 0
         for _ in range(args.fp64_steps):
             ms, st = one_step(prm64, buf)
             t64.append(ms)
+            k64.append(st.kernel_ms)
             acc64 += st.steps_accepted
+            att64 += st.steps_accepted + st.steps_rejected + st.steps_root
             rays64 += st.rays
         modes["fp64"] = {"ray_steps_per_s": acc64 / (sum(t64) / 1e3),
-                         "rays_per_s": rays64 / (sum(t64) / 1e3), "ms_per_step": sum(t64) / len(t64)}
-        d = (end32 - buf.t["end_pos"][:, :n_rays]).norm(dim=0)
-        dT = (t32 - buf.t["time"][:n_rays]).abs()
-        within = ((d <= 1e-3) & (dT <= 1e-11)).double().mean()
+                         "rays_per_s": rays64 / (sum(t64) / 1e3), "ms_per_step": sum(t64) / len(t64),
+                         "roofline": alu_roofline(FLOPS_PER_ATTEMPT_F64, att64, sum(k64), pk64,
+                                                  "k_trace_wave<PrecF64, MediumLayered>", basis64)}
+        end64 = buf.t["end_pos"][:, :n_rays].clone()
+        t64e = buf.t["time"][:n_rays].clone()
+        s64 = buf.t["status"][:n_rays].clone()
+        # conditioning: the FP64 run again with every launch direction tilted by 1e-7 rad; a
+        # primary whose FP64 result moves by more than 1 mm / 10 ps (or changes status) under
+        # the tilt is ill-conditioned (grazing or critical incidence, an amplitude at its
+        # threshold)
+        trays = rp.PreparedRays(cfg["rays"][0], W.tilted_dirs(cfg["rays"][1], 1e-7, 9),
+                                cfg["rays"][2], receivers=cfg["receivers"])
+        rp.trace_into(med, trays, prm64, buf, stream)
+        sens = (((end64 - buf.t["end_pos"][:, :n_rays]).norm(dim=0) > 1e-3) |
+                ((t64e - buf.t["time"][:n_rays]).abs() > 1e-11) |
+                (s64 != buf.t["status"][:n_rays]))
+        del trays
+        d = (end32 - end64).norm(dim=0)
+        dT = (t32 - t64e).abs()
+        outside = (d > 1e-3) | (dT > 1e-11) | (s32 != s64)
         err = {"vs": f"FP64 GPU path, all {n_rays:,} primary end points",
-               "within_1mm_10ps": float(within),
+               "within_1mm_10ps": float((~outside).double().mean()),
+               "outside_1mm_10ps": int(outside.sum()),
+               "outside_and_not_tilt_sensitive": int((outside & ~sens).sum()),
+               "tilt_sensitive_fraction": float(sens.double().mean()),
+               "conditioning": "FP64 end point moves > 1 mm / 10 ps or changes status under a "
+                               "1e-7 rad launch tilt",
                "pos_m": {"p50": float(d.quantile(0.5)), "p99": float(d.double().quantile(0.99)),
                          "max": float(d.max())},
                "time_s": {"p50": float(dT.quantile(0.5)), "p99": float(dT.quantile(0.99)),
                           "max": float(dT.max())}}
         # Eq. 1 integrated as written (momentum form, FP64 only): the same batch, end points
         # against the projected FP64 run just made
-        end64 = buf.t["end_pos"][:, :n_rays].clone()
-        t64e = buf.t["time"][:n_rays].clone()
         prmm = rp.make_params(dict(cfg["params"], rhs_form="momentum"), "fp64")
         one_step(prmm, buf)
-        tm, accm, raysm = [], 0, 0
+        tm, km, accm, raysm, attm = [], [], 0, 0, 0
         for _ in range(args.fp64_steps):
             ms, st = one_step(prmm, buf)
             tm.append(ms)
+            km.append(st.kernel_ms)
             accm += st.steps_accepted
+            attm += st.steps_accepted + st.steps_rejected + st.steps_root
             raysm += st.rays
         dm = (end64 - buf.t["end_pos"][:, :n_rays]).norm(dim=0)
         dTm = (t64e - buf.t["time"][:n_rays]).abs()
         modes["fp64_momentum"] = {
             "ray_steps_per_s": accm / (sum(tm) / 1e3), "rays_per_s": raysm / (sum(tm) / 1e3),
             "ms_per_step": sum(tm) / len(tm),
+            "roofline": alu_roofline(FLOPS_PER_ATTEMPT_MOMENTUM, attm, sum(km), pk64,
+                                     "k_trace_wave<PrecF64, MediumLayered> (momentum form)",
+                                     basis64),
             "vs_projected_fp64": {"pos_m_p99": float(dm.double().quantile(0.99)),
                                   "time_s_p99": float(dTm.double().quantile(0.99)),
                                   "within_1mm_10ps": float(((dm <= 1e-3) & (dTm <= 1e-11))
@@ -572,14 +673,19 @@ def run_gpu(args):
             gatt += st.steps_accepted + st.steps_rejected + st.steps_root
             gr += st.rays
         gsec = sum(gt) / 1e3
-        bytes_alg = 768.0 * gatt
+        bytes_alg = float(BYTES_PER_ATTEMPT_GRID) * gatt
+        gbs = bytes_alg / gsec / 1e9
         modes["grid_fp32_mixed"] = {
             "workload": "256x256x512 FP32 grid (4 m), 4,194,304 rays from 16 sources, tol 1e-5",
             "ray_steps_per_s": gacc / gsec, "rays_per_s": gr / gsec,
             "ms_per_step": 1e3 * gsec / len(gt),
-            "algorithmic_GBps": bytes_alg / gsec / 1e9,
-            "algorithmic_bytes_per_attempted_step": 768,
-            "hbm_peak_GBps": _peaks().get("hbm_gbs"),
+            "roofline": {"bound": "l2", "achieved": gbs, "peak": peaks["l2_gbs"], "unit": "GB/s",
+                         "frac": gbs / peaks["l2_gbs"],
+                         "kernel": "k_trace_wave<PrecF32, MediumGrid>",
+                         "bytes_per_attempted_step": BYTES_PER_ATTEMPT_GRID,
+                         "peak_basis": "rp_measure_peaks L2-resident read bandwidth",
+                         "hbm_peak": mp.get("hbm_gbs"),
+                         "frac_of_hbm": gbs / mp["hbm_gbs"] if mp.get("hbm_gbs") else None},
         }
         del gmed, grays, gbuf
 
@@ -587,15 +693,30 @@ def run_gpu(args):
     if not args.no_fig1:
         modes["fig1"] = fp32_fp64_leg(
             rp, W.fig1(), flush, args.grid_steps,
+            {"fp32": FLOPS_PER_ATTEMPT_F32, "fp64": FLOPS_PER_ATTEMPT_F64},
+            {"fp32": (pk32, basis32), "fp64": (pk64, basis64)},
             "Fig. 1 example: 1,048,576 rays from 240 m in the x-z plane, 10 m of n = 1.5 over "
             "exponential ice (z0 = 71.4 m), 5 us, A/A0 < 0.05 discarded, generations <= 8")
     # curved boundaries: two spherical inclusions in the ice, 1,048,576 isotropic rays
     if not args.no_spheres:
         modes["spheres"] = fp32_fp64_leg(
-            rp, W.spheres(), flush, args.grid_steps,
+            rp, dict(W.spheres(), kernel_medium="MediumSpheres"), flush, args.grid_steps,
+            {"fp32": FLOPS_PER_ATTEMPT_SPHERES_F32, "fp64": FLOPS_PER_ATTEMPT_SPHERES_F64},
+            {"fp32": (pk32, basis32), "fp64": (pk64, basis64)},
             "spherical inclusions: 1,048,576 isotropic rays around a denser-ice lens (R 40 m) "
             "and an air pocket (R 25 m) in the surface-bounded ice, 2 km, A/A0 < 0.05, "
             "generations <= 3")
+
+    # non-horizontal boundaries: a tilted ice surface carrying a height field of undulations and
+    # a tilted internal boundary, 1,048,576 isotropic rays
+    if not args.no_surfaces:
+        modes["surfaces"] = fp32_fp64_leg(
+            rp, dict(W.surfaces(), kernel_medium="MediumSurfaces"), flush, args.grid_steps,
+            {"fp32": FLOPS_PER_ATTEMPT_SURFACES_F32, "fp64": FLOPS_PER_ATTEMPT_SURFACES_F64},
+            {"fp32": (pk32, basis32), "fp64": (pk64, basis64)},
+            "non-horizontal boundaries: 1,048,576 isotropic rays under a 2-degree tilted ice "
+            "surface with a 0.3 m height field of undulations (256 x 256 nodes at 2 m) and a "
+            "1-degree tilted internal boundary at 100 m, 2 km, A/A0 < 0.05, generations <= 3")
 
     # source-receiver path finding: 65,536 pairs, 32..512 scan angles each, FP64 bisection
     if not args.no_paths:
@@ -605,7 +726,7 @@ def run_gpu(args):
         pprm = rp.make_path_params(pcfg["params"], "fp32", pcfg["hit_tol"], pcfg["max_iter"],
                                    pcfg["max_sol"])
         rp.find_paths_into(med_paths := rp.Medium(pcfg["medium"]), pbuf, pprm)  # warm-up
-        pt, nsol, prays, pacc = [], 0, 0, 0
+        pt, nsol, prays, pacc, patt = [], 0, 0, 0, 0
         for _ in range(args.paths_steps):
             flush.fill_(1.0)
             st = rp.find_paths_into(med_paths, pbuf, pprm)
@@ -613,6 +734,7 @@ def run_gpu(args):
             nsol += int(pbuf.count.sum())
             prays += st.rays
             pacc += st.steps_accepted
+            patt += st.steps_accepted + st.steps_rejected + st.steps_root
         psec = sum(pt) / 1e3
         modes["paths_fp32_mixed"] = {
             "workload": "65,536 source-receiver pairs, 32..512 scan angles, FP64 bisection to "
@@ -620,28 +742,42 @@ def run_gpu(args):
             "solutions_per_s": nsol / psec, "pairs_per_s": len(P["zs"]) * len(pt) / psec,
             "rays_per_s": prays / psec, "ray_steps_per_s": pacc / psec,
             "ms_per_step": 1e3 * psec / len(pt),
+            "roofline": alu_roofline(FLOPS_PER_ATTEMPT_F32, patt, 1e3 * psec, pk32,
+                                     "k_scan / k_bisect<PrecF32> (the tracing step of the path "
+                                     "finder; all its launches timed)", basis32),
         }
 
     # learned surrogate of the path finder: labels from the FP32 path finder, native training,
     # inference on 1,048,576 queries with refinement and fallback, against the plain path
     # finder at the same 5 mm receiver tolerance and the FP64 path finder on a sample
     if not args.no_surrogate:
-        modes["surrogate"] = surrogate_leg(rp, W, args, rank, flush)
+        sur = surrogate_leg(rp, W, args, rank, flush)
+        bf16_burst, bf16_sus = mp.get("bf16_tflops"), mp.get("bf16_tflops_sustained")
+        tr = sur["training"]["train_tflops"]
+        sur["training"]["roofline"] = {
+            "bound": "tensor", "achieved": tr, "peak": bf16_sus, "unit": "TFLOP/s",
+            "frac": tr / bf16_sus if bf16_sus else None,
+            "kernel": "the whole Adam step (k_tc_dense, k_tc_wgrad, thin layers, loss, Adam)",
+            "peak_basis": "MEASURED_PEAKS bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)"}
+        fw = sur["mlp_forward_tflops"]
+        sur["forward_roofline"] = {
+            "bound": "tensor", "achieved": fw, "peak": bf16_burst, "unit": "TFLOP/s",
+            "frac": fw / bf16_burst if bf16_burst else None, "kernel": "k_mlp_fused",
+            "peak_basis": "MEASURED_PEAKS bf16_tflops (cuBLAS bf16 burst)"}
+        modes["surrogate"] = sur
 
-    # roofline of the dominant kernel (the FP32 tracing launches): FP32 ALU bound
-    sm_mhz = clocks["sm_mhz"] or _peaks().get("sm_max_mhz", 2070.0)
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    # roofline of the dominant kernel (the FP32 tracing launches): FP32 ALU bound, against the
+    # FP32 FMA rate measured on this GPU (moved to the run's clock)
     kern_ms = sum(kern)
-    achieved = FLOPS_PER_ATTEMPT_F32 * att / (kern_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops,
-            "traffic": TRACE_DRAM_BYTES_PER_STEP if n_rays == N_RAYS else None,
-            "traffic_unit": "bytes per step (all launches of the step)",
-            "kernel": "k_trace_wave<PrecF32, MediumLayered>",
-            "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x median SM clock "
-                          f"under load ({sm_mhz:.0f} MHz)",
-            "flops_per_attempted_step": FLOPS_PER_ATTEMPT_F32,
-            "attempted_steps_per_launch_set": att / len(times)}
+    roof = alu_roofline(FLOPS_PER_ATTEMPT_F32, att, kern_ms, pk32,
+                        "k_trace_wave<PrecF32, MediumLayered>", basis32)
+    roof.update({"traffic": TRACE_DRAM_BYTES_PER_STEP if n_rays == N_RAYS else None,
+                 "traffic_unit": "bytes per step (all launches of the step)",
+                 "attempted_steps_per_launch_set": att / len(times),
+                 "nominal_peak": SM_COUNT_NOMINAL * 128 * 2 * (clocks["sm_mhz"] or 2070.0) / 1e6,
+                 "frac_of_nominal": None})
+    roof["frac_of_nominal"] = roof["achieved"] / roof["nominal_peak"]
+    modes["fp32_mixed"]["roofline"] = roof
 
     if rank == 0:
         line = {
@@ -659,6 +795,8 @@ def run_gpu(args):
                     "d2h_bytes_per_step": d2h_b, "ms_per_step": statistics.median(e2e_ms)},
             "gpu_launches": args.steps * (1 + 4 + 3),
             "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,
+            "measured_peaks": peaks,
+            "tuned_knobs": dict(tuned["best"], tune_s=tune_s, candidates=len(tuned["ms"])),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -681,6 +819,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-fig1", action="store_true")
     ap.add_argument("--no-spheres", action="store_true")
+    ap.add_argument("--no-surfaces", action="store_true")
     ap.add_argument("--sur-train", type=int, default=4_194_304)
     ap.add_argument("--sur-queries", type=int, default=1_048_576)
     ap.add_argument("--sur-check", type=int, default=16_384)

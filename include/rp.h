@@ -40,6 +40,8 @@ extern "C" {
 #define RP_ERR_OOM (-3)          /* device allocation failed */
 #define RP_ERR_OVERFLOW (-4)     /* an output buffer was too small; rp_stats has the sizes */
 #define RP_ERR_UNSUPPORTED (-5)  /* valid request this build does not provide */
+#define RP_ERR_TIMEOUT (-6)      /* a bounded device-side wait gave up (the work it waited for
+                                    did not complete in time); the context stays usable */
 
 #define RP_MAX_LAYERS 8
 #define RP_MAX_SPHERES 4
@@ -87,8 +89,30 @@ typedef struct {
     int32_t absorb, pad;
 } rp_sphere;
 
+/* Non-horizontal layer boundary (boundary shapes beyond the horizontal plane, the paragraph
+ * after Fig. 1).  It replaces the plane z = z_top between layers `layer` - 1 and `layer`
+ * (1 <= layer < n_layers) by the surface
+ *   z = zb(x, y) = z_top + sx x + sy y + H(x, y),   (sx, sy) = -(normal[0], normal[1]) / normal[2]
+ * -- the plane through (0, 0, z_top) with the given normal (normal[2] > 0; any length) -- plus,
+ * if `height` is not NULL, the height field H: the bilinear interpolant of nx x ny (>= 2 each)
+ * node heights [m], x fastest, node (i, j) at (origin[0] + i spacing[0], origin[1] +
+ * j spacing[1]), held at its edge values beyond the nodes.  `height` may be a host or a device
+ * pointer and is copied.  Layer k then spans zb_k(x, y) <= z < zb_{k+1}(x, y); the surfaces
+ * must not cross where rays travel (not checked).  A ray lands on the surface by the Illinois
+ * search on its vertical offset z - zb(x, y) (within eps_b), is put on it vertically, and the
+ * boundary split uses the local normal (-dzb/dx, -dzb/dy, 1) / |...| and the indices of the two
+ * layers at the point. */
+typedef struct {
+    int32_t layer, nx, ny, pad;
+    double normal[3];
+    double origin[2], spacing[2];
+    const double *height;
+} rp_surface;
+
 /* kind = RP_MEDIUM_LAYERED: n_layers (1..8) layers, ordered top to bottom, z_top increasing,
- *   and n_spheres (0..4) spheres, each strictly inside one layer, none overlapping another.
+ *   n_spheres (0..4) spheres, each strictly inside one layer, none overlapping another, and
+ *   n_surfaces (0..n_layers-1) non-horizontal boundaries, each on a different layer boundary
+ *   (media with spheres take no surfaces; rp_find_paths takes neither).
  * kind = RP_MEDIUM_GRID: node values of n on an nx * ny * nz grid (x fastest), node (i,j,k)
  *   at origin + spacing * (i,j,k); `grid_n` may be a host or a device pointer and is copied.
  *   The library derives grad n by central differences (one-sided on the faces) and stores
@@ -104,6 +128,8 @@ typedef struct {
     const float *grid_n;
     int32_t n_spheres, pad2;
     rp_sphere spheres[RP_MAX_SPHERES];
+    int32_t n_surfaces, pad3;
+    rp_surface surfaces[RP_MAX_LAYERS];
 } rp_medium_desc;
 
 typedef struct rp_medium_s *rp_medium_t;
@@ -112,8 +138,10 @@ typedef struct rp_medium_s *rp_medium_t;
  * the current device and returns an opaque handle in *out.  The handle owns its device
  * memory until rp_medium_destroy.  Errors: RP_ERR_INVALID_ARG (null pointer, bad layer count,
  * z_top not increasing, z0 <= 0 with dn != 0, grid smaller than 2 nodes per axis,
- * spacing <= 0, a sphere of radius <= 0, crossing a layer plane or overlapping another),
- * RP_ERR_OOM, RP_ERR_CUDA. */
+ * spacing <= 0, a sphere of radius <= 0, crossing a layer plane or overlapping another, a
+ * surface on no inner boundary or on one taken, normal[2] <= 0, a height field of fewer than
+ * 2 x 2 nodes, non-positive spacing or non-finite heights), RP_ERR_UNSUPPORTED (spheres and
+ * surfaces in one medium), RP_ERR_OOM, RP_ERR_CUDA. */
 int rp_medium_create(const rp_medium_desc *desc, void *stream, rp_medium_t *out);
 
 /* Releases the handle and its device memory.  NULL is accepted. */
@@ -147,23 +175,40 @@ typedef struct {
  *   min_amp      terminate when |A| < min_amp |A0|, <= 0: none (A0 of the root primary);
  *                a secondary whose amplitude would start below the threshold is not cast
  *   eps_b        boundary landing tolerance [m] (FP32_MIXED uses at least 2e-6 m)
- *   stop_n, stop_d, use_stop   optional stop plane stop_n . r = stop_d (unit normal)
+ *   stop_n, stop_d, use_stop   optional stop plane stop_n . r = stop_d; stop_n must be +1 or -1
+ *                along one coordinate axis and 0 along the others (RP_ERR_INVALID_ARG else)
  *   max_generation  secondaries are spawned while the parent's generation is below it
- *   precision    RP_FP64 (all arithmetic in FP64) or RP_FP32_MIXED (Runge-Kutta stages in
- *                FP32, position and direction accumulated in float-float, travel time and
- *                path length accumulated in FP64)
+ *   precision    RP_FP64: every step in FP64 except the step-size factor of the step control
+ *                (0.9 e^(-1/5), 0.9 e^(-1/4) on rejection: a heuristic, formed in FP32);
+ *                RP_FP32_MIXED: Runge-Kutta stages, medium evaluation and step control in
+ *                FP32; position, direction, travel time and path length accumulated in
+ *                float-float (a pair of FP32 numbers, about 48 significant bits) on the FP32
+ *                pipe; boundary splits in FP32 except the direction of a traced secondary
+ *                (FP64); every output in FP64
  *   polarization RP_POL_S / RP_POL_P (signed field amplitudes) or RP_POL_UNPOL (square roots
  *                of the s/p-averaged reflectance and transmittance)
  *   rhs_form     RP_RHS_PROJECTED: t' = (grad n - (grad n . t) t)/n, Eq. 1 for unit t;
  *                RP_RHS_PARAXIAL: t' = grad n / n, Eq. 2, t renormalised after each step
  *                RP_RHS_MOMENTUM: Eq. 1 as written on p = n t (r' = p/|p|, p' = grad n), a
  *                cross-check of the projected form; RP_FP64 only (RP_ERR_INVALID_ARG else)
- *   max_steps    cap on attempted Cash-Karp steps per ray (> 0) */
+ *   max_steps    cap on attempted Cash-Karp steps per ray (> 0)
+ * Scheduling knobs: they change which thread traces a ray and when, never a ray's record;
+ * 0 selects the default.  rp_find_paths reads service_idle only.
+ *   service_idle   idle lane-iterations after which a warp serves its parked lanes (boundary
+ *                  splits, finished rays); default 256 in FP32_MIXED, 8 in FP64; >= 0
+ *   flush_min      once a launch's input has run out, a thread hands the rest of its stack of
+ *                  secondaries to the next launch when at least this many records remain
+ *                  (default 2); >= 0
+ *   block          threads per block of the tracing launches: 0 (128) or a multiple of 32 up
+ *                  to 256
+ *   blocks_per_sm  resident blocks per SM of the persistent launches: 0 or more than fit
+ *                  means as many as fit */
 typedef struct {
     double tol, h_min, h_max, h0, max_path, max_time, min_amp, eps_b;
     double stop_n[3], stop_d;
     int32_t use_stop, max_generation, precision, polarization, rhs_form, pad;
     int64_t max_steps;
+    int32_t service_idle, flush_min, block, blocks_per_sm;
 } rp_trace_params;
 
 /* Finished rays.  Primary i is written at index i; secondaries take the following indices as
@@ -200,6 +245,10 @@ typedef struct {
     double kernel_ms;        /* device time of the tracing kernels */
     double wave_ms[16];      /* device time of each generation's launch */
     double warp_end_ms[3];   /* first launch: earliest, median and last warp end [ms] */
+    int64_t queue_capacity;  /* queue records the call had room for (queue_needed above it:
+                                RP_ERR_OVERFLOW) */
+    int32_t threads;         /* threads of each persistent launch (SMs x blocks x block) */
+    int32_t stack_depth;     /* secondaries each thread keeps on its own stack */
 } rp_stats;
 
 /* Traces in->n primaries and every secondary they spawn, in max_generation + 1 persistent
@@ -207,12 +256,9 @@ typedef struct {
  * after that they go to a device queue that the next launch drains.  `rx` and `hits` may be
  * NULL, `stats` may be NULL.  Returns RP_OK, RP_ERR_INVALID_ARG (parameters, null arrays,
  * capacity < n), RP_ERR_OVERFLOW (out, queue or hit capacity exceeded: rp_stats holds the
- * sizes needed; everything that fitted was written), RP_ERR_OOM, RP_ERR_CUDA.
- * Scheduling knobs, read from the environment at each call (they change speed, not any ray's
- * record): RP_SERVICE_IDLE (256) and RP_SERVICE_IDLE_F64 (8), the idle lane-iterations after
- * which a warp serves its parked lanes (boundary splits, finished rays) in FP32-mixed and FP64
- * mode; RP_FLUSH_MIN (2), the stacked secondaries a thread hands to the next launch once the
- * input has run out. */
+ * sizes needed; everything that fitted was written), RP_ERR_OOM, RP_ERR_CUDA.  The
+ * scheduling knobs of `p` (service_idle, flush_min, block, blocks_per_sm) change speed, not
+ * any ray's record. */
 int rp_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp_trace_params *p,
              rp_ray_out *out, rp_hits *hits, rp_stats *stats, void *stream);
 
@@ -237,7 +283,16 @@ int rp_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp_
  *     control block is cleared at the start of every call; the rest is overwritten.
  *   - Limits: in->n <= RP_STATIC_MAX_RAYS and rx->n <= RP_STATIC_MAX_RECEIVERS
  *     (RP_ERR_INVALID_ARG beyond).  The secondary-ray queue is smaller than rp_trace's; if it
- *     fills, the call returns RP_ERR_OVERFLOW with rp_stats as for rp_trace.
+ *     fills, the call returns RP_ERR_OVERFLOW with rp_stats as for rp_trace
+ *     (rp_stats.queue_needed against rp_stats.queue_capacity).  What fits depends on the
+ *     workload and the launch: the per-thread stacks take at most half of the array (one
+ *     120-byte record per thread and level), the queue the rest.  On a GB300 the FP32-mixed
+ *     layered kernel runs 77,824 threads (152 SMs x 4 blocks x 128): one stacked secondary per
+ *     thread and a queue of about 199,000 records, which holds the 2^20-primary two-layer-ice
+ *     workload (0.75 secondaries per primary; it queues about 194,000).  Fewer blocks_per_sm
+ *     give deeper stacks; the call also fails with RP_ERR_INVALID_ARG when not even one record
+ *     per thread fits beside the receivers' tables.
+ *   - Like rp_trace, it synchronises `stream` before it returns.
  *   - rp_stats.warp_end_ms is not filled (its read-back would need pinned host memory). */
 int rp_trace_static(rp_medium_t m, const rp_rays *in, const rp_receivers *rx,
                     const rp_trace_params *p, rp_ray_out *out, rp_hits *hits, rp_stats *stats,
@@ -273,7 +328,7 @@ typedef struct {
  * adjacent angles whose vertical misses change sign are refined by FP64 bisection on the
  * launch angle until |miss| < hit_tol.  A ray that exhausts its path budget before x = D
  * scores +inf (it is far below).  D < hit_tol: the vertical ray to the receiver depth.
- * Layered media without spheres only.  Solution type: REFLECTED if the ray reflected off a
+ * Layered media with horizontal boundaries and without spheres only.  Solution type: REFLECTED if the ray reflected off a
  * boundary, REFRACTED if it turned (t_z changed sign), else DIRECT.  Returns RP_OK, RP_ERR_INVALID_ARG, RP_ERR_OOM,
  * RP_ERR_CUDA. */
 int rp_find_paths(rp_medium_t m, int64_t n_pairs, const double *z_s, const double *z_r,
@@ -301,11 +356,20 @@ int rp_surrogate_n_params(void);
 int rp_surrogate_create(const float *params, rp_surrogate_t *out);
 int rp_surrogate_destroy(rp_surrogate_t s);
 
+/* Bound on every wait of the surrogate's tensor-core kernels for their own bulk copies and
+ * matrix products (mbarrier waits), in SM clock cycles; 0 (the default) means 4e9, about two
+ * seconds.  The paper has no counterpart: this is the library's hang protection.  A CTA whose
+ * wait gives up records it, waits (with the default bound) for the work it has already issued,
+ * releases its tensor memory and returns; the call then returns RP_ERR_TIMEOUT and the device
+ * context stays usable.  Returns RP_ERR_INVALID_ARG for a null handle or a negative limit. */
+int rp_surrogate_set_wait_limit(rp_surrogate_t s, int64_t cycles);
+
 /* Replaces the parameters (host or device pointer; Adam state reset) / copies them out. */
 int rp_surrogate_set_params(rp_surrogate_t s, const float *params);
 int rp_surrogate_get_params(rp_surrogate_t s, float *params);
 
-/* out (n, 12) = network(x (n, 3)).  Device pointers. */
+/* out (n, 12) = network(x (n, 3)).  Device pointers.  RP_ERR_TIMEOUT: see
+ * rp_surrogate_set_wait_limit. */
 int rp_surrogate_forward(rp_surrogate_t s, int64_t n, const float *x, float *out, void *stream);
 
 /* Mean loss over n rows and its gradient (flat, like the parameters; device or host pointer,
@@ -417,6 +481,24 @@ int rp_surrogate_find_paths(rp_surrogate_t s, rp_medium_t m, int64_t n, const do
 /* ------------------------------------------------------------------------------------
  * Misc
  * ---------------------------------------------------------------------------------- */
+
+/* Roofline denominators of the current device, measured (the paper has no counterpart: this
+ * is the measurement side of the library).  Three microkernels on `stream`, each the best of
+ * three timed launches after an untimed one (about 10 ms each):
+ *   fp32_tflops, fp64_tflops  fused multiply-adds on the CUDA cores, 8 independent chains per
+ *                             thread, 1,024 threads per SM (FMA = 2 flops);
+ *   l2_gbs                    16-byte loads that bypass L1, streamed by every SM over a
+ *                             RP_PEAKS_L2_BUFFER-byte buffer (far smaller than L2, read once
+ *                             before the timed launches, so every load hits L2).
+ * The *_ms fields are the timed launches' durations; report the SM clock sampled while they
+ * run beside the rates.  Allocates and frees the buffer.  Returns RP_OK, RP_ERR_INVALID_ARG
+ * (null out), RP_ERR_OOM, RP_ERR_CUDA. */
+#define RP_PEAKS_L2_BUFFER (32u << 20)
+typedef struct {
+    double fp32_tflops, fp64_tflops, l2_gbs;
+    double fp32_ms, fp64_ms, l2_ms, l2_buffer_bytes;
+} rp_peaks;
+int rp_measure_peaks(rp_peaks *out, void *stream);
 
 /* Copies the last error message of the calling thread into buf (NUL-terminated, truncated
  * to len).  Returns the full message length. */

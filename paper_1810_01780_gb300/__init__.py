@@ -19,7 +19,7 @@ __all__ = ["Medium", "trace", "trace_into", "TraceBuffers", "PreparedRays", "mak
 def __getattr__(name):
     if name in ("Medium", "trace", "trace_into", "TraceBuffers", "PreparedRays", "make_params",
                 "find_paths", "PathBuffers", "find_paths_into", "make_path_params", "Surrogate",
-                "make_surrogate_params", "encode"):
+                "make_surrogate_params", "encode", "measure_peaks"):
         from . import api
 
         return getattr(api, name)

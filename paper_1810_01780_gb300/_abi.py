@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(PKG, "libradiopropa_gb300.so")
 
 RP_OK = 0
 ERRORS = {-1: "RP_ERR_INVALID_ARG", -2: "RP_ERR_CUDA", -3: "RP_ERR_OOM", -4: "RP_ERR_OVERFLOW",
-          -5: "RP_ERR_UNSUPPORTED"}
+          -5: "RP_ERR_UNSUPPORTED", -6: "RP_ERR_TIMEOUT"}
 RP_ERR_OVERFLOW = -4
 MAX_LAYERS = 8
 MAX_SPHERES = 4
@@ -46,12 +46,19 @@ class Sphere(C.Structure):
                 ("absorb", C.c_int32), ("pad", C.c_int32)]
 
 
+class Surface(C.Structure):
+    _fields_ = [("layer", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("pad", C.c_int32),
+                ("normal", C.c_double * 3), ("origin", C.c_double * 2),
+                ("spacing", C.c_double * 2), ("height", C.c_void_p)]
+
+
 class MediumDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_layers", C.c_int32), ("layers", Layer * MAX_LAYERS),
                 ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("pad", C.c_int32),
                 ("origin", C.c_double * 3), ("spacing", C.c_double),
                 ("grid_n", C.c_void_p), ("n_spheres", C.c_int32), ("pad2", C.c_int32),
-                ("spheres", Sphere * MAX_SPHERES)]
+                ("spheres", Sphere * MAX_SPHERES), ("n_surfaces", C.c_int32),
+                ("pad3", C.c_int32), ("surfaces", Surface * MAX_LAYERS)]
 
 
 class Rays(C.Structure):
@@ -69,7 +76,8 @@ class TraceParams(C.Structure):
                 ("min_amp", C.c_double), ("eps_b", C.c_double), ("stop_n", C.c_double * 3),
                 ("stop_d", C.c_double), ("use_stop", C.c_int32), ("max_generation", C.c_int32),
                 ("precision", C.c_int32), ("polarization", C.c_int32), ("rhs_form", C.c_int32),
-                ("pad", C.c_int32), ("max_steps", C.c_int64)]
+                ("pad", C.c_int32), ("max_steps", C.c_int64), ("service_idle", C.c_int32),
+                ("flush_min", C.c_int32), ("block", C.c_int32), ("blocks_per_sm", C.c_int32)]
 
 
 class RayOut(C.Structure):
@@ -89,7 +97,8 @@ class Stats(C.Structure):
                 ("steps_accepted", C.c_int64), ("steps_rejected", C.c_int64),
                 ("steps_root", C.c_int64), ("queue_needed", C.c_int64), ("waves", C.c_int32),
                 ("flags", C.c_int32), ("kernel_ms", C.c_double), ("wave_ms", C.c_double * 16),
-                ("warp_end_ms", C.c_double * 3)]
+                ("warp_end_ms", C.c_double * 3), ("queue_capacity", C.c_int64),
+                ("threads", C.c_int32), ("stack_depth", C.c_int32)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -126,6 +135,14 @@ class SurrogateStats(C.Structure):
                                          "fallback_steps")] + \
                [(f, C.c_float) for f in ("ms_forward", "ms_refine", "ms_fallback", "ms_total",
                                          "ms_fallback_scan")]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Peaks(C.Structure):
+    _fields_ = [(f, C.c_double) for f in ("fp32_tflops", "fp64_tflops", "l2_gbs", "fp32_ms",
+                                          "fp64_ms", "l2_ms", "l2_buffer_bytes")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -169,6 +186,8 @@ SIGNATURES = {
                                           C.c_void_p]),
     "rp_last_error": (C.c_int, [C.c_char_p, C.c_size_t]),
     "rp_version": (C.c_char_p, []),
+    "rp_measure_peaks": (C.c_int, [C.POINTER(Peaks), C.c_void_p]),
+    "rp_surrogate_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int64]),
 }
 
 _lib = None

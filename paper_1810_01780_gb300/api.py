@@ -66,6 +66,25 @@ class Medium:
                 d.spheres[j].z0 = float(S.get("z0", 1.0))
                 d.spheres[j].offset = float(S.get("off", 0.0))
                 d.spheres[j].absorb = int(bool(S.get("absorb", False)))
+            surfaces = desc.get("surfaces", [])
+            if len(surfaces) > A.MAX_LAYERS:
+                raise ValueError("at most %d surfaces" % A.MAX_LAYERS)
+            d.n_surfaces = len(surfaces)
+            keep = []
+            for j, srf in enumerate(surfaces):
+                q = d.surfaces[j]
+                q.layer = int(srf["layer"])
+                for a in range(3):
+                    q.normal[a] = float(srf.get("normal", (0.0, 0.0, 1.0))[a])
+                if srf.get("height") is not None:
+                    h = np.ascontiguousarray(srf["height"], dtype=np.float64)  # (ny, nx)
+                    q.ny, q.nx = h.shape
+                    for a in range(2):
+                        q.origin[a] = float(srf["origin"][a])
+                        q.spacing[a] = float(srf["spacing"][a])
+                    q.height = h.ctypes.data
+                    keep.append(h)
+            self._keep = keep
         elif desc["kind"] == "grid":
             n = desc["n"]
             if isinstance(n, torch.Tensor):
@@ -123,7 +142,13 @@ def make_params(p: dict, precision: str = "fp64") -> A.TraceParams:
     q.polarization = A.POLARIZATION[p.get("polarization", "s")]
     q.rhs_form = A.RHS_FORM[p.get("rhs_form", "projected")]
     q.max_steps = int(p.get("max_steps", 1_000_000))
+    # scheduling knobs (0: the library's default); they never change a ray's record
+    for k in SCHEDULING_KNOBS:
+        setattr(q, k, int(p.get(k, 0)))
     return q
+
+
+SCHEDULING_KNOBS = ("service_idle", "flush_min", "block", "blocks_per_sm")
 
 
 RAY_FIELDS_F64 = ("path", "time", "amp")
@@ -322,6 +347,10 @@ class Surrogate:
         params = np.ascontiguousarray(params, dtype=np.float32)
         A.check(A.lib().rp_surrogate_set_params(self.handle, C.c_void_p(params.ctypes.data)))
 
+    def set_wait_limit(self, cycles: int = 0):
+        """Bound on the tensor-core kernels' mbarrier waits [SM cycles]; 0: the default."""
+        A.check(A.lib().rp_surrogate_set_wait_limit(self.handle, int(cycles)))
+
     @staticmethod
     def _f32(x, cols):
         t = torch.as_tensor(x, dtype=torch.float32, device="cuda").contiguous()
@@ -432,3 +461,11 @@ def encode(zs, zr, dist, sol=None, stream=None):
         C.c_void_p(y.data_ptr() if y is not None else 0),
         C.c_void_p(t.data_ptr() if t is not None else 0), C.c_void_p(_stream_ptr(stream))))
     return x, y, t
+
+
+def measure_peaks(stream=None) -> dict:
+    """rp_measure_peaks: the FP32 and FP64 FMA rates [TFLOP/s] and the L2 read bandwidth [GB/s]
+    of the current device, measured by the library's microkernels."""
+    pk = A.Peaks()
+    A.check(A.lib().rp_measure_peaks(C.byref(pk), C.c_void_p(_stream_ptr(stream))))
+    return pk.as_dict()

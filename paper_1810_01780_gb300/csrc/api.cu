@@ -6,6 +6,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "rp_internal.h"
 
@@ -110,6 +111,94 @@ int validate_params(const rp_trace_params *p, bool path_finding)
         set_error("params: the momentum form runs in RP_FP64 only");
         return RP_ERR_INVALID_ARG;
     }
+    if (p->service_idle < 0 || p->flush_min < 0 || p->blocks_per_sm < 0 || p->block < 0 ||
+        p->block > kBlockMax || p->block % 32 != 0) {
+        set_error("params: need service_idle, flush_min, blocks_per_sm >= 0 and block 0 or a "
+                  "multiple of 32 up to %d", kBlockMax);
+        return RP_ERR_INVALID_ARG;
+    }
+    return RP_OK;
+}
+
+// Non-horizontal boundaries of a layered medium (rp_surface): checked on the host, height
+// fields copied into one device allocation (the caller's array may be on the host or the
+// device), the kernel's SurfB records filled in.
+int build_surfaces(rp_medium_s *m, const rp_medium_desc *d)
+{
+    m->n_surf = 0;
+    if (d->n_surfaces == 0) return RP_OK;
+    if (d->n_surfaces < 0 || d->n_surfaces > RP_MAX_LAYERS) {
+        set_error("rp_medium_create: n_surfaces must be 0..%d", RP_MAX_LAYERS);
+        return RP_ERR_INVALID_ARG;
+    }
+    if (d->n_spheres > 0) {
+        set_error("rp_medium_create: a medium takes either spheres or surfaces");
+        return RP_ERR_UNSUPPORTED;
+    }
+    size_t total = 0;
+    bool taken[RP_MAX_LAYERS] = {false};
+    for (int j = 0; j < d->n_surfaces; ++j) {
+        const rp_surface &S = d->surfaces[j];
+        bool ok = S.layer >= 1 && S.layer < d->n_layers && !taken[S.layer] && S.normal[2] > 0.0 &&
+                  std::isfinite(S.normal[0]) && std::isfinite(S.normal[1]) &&
+                  std::isfinite(S.normal[2]);
+        if (ok && S.height)
+            ok = S.nx >= 2 && S.ny >= 2 && S.spacing[0] > 0.0 && S.spacing[1] > 0.0 &&
+                 std::isfinite(S.spacing[0]) && std::isfinite(S.spacing[1]) &&
+                 std::isfinite(S.origin[0]) && std::isfinite(S.origin[1]) &&
+                 (size_t)S.nx * (size_t)S.ny <= ((size_t)1 << 28);
+        if (!ok) {
+            set_error("rp_medium_create: surface %d: needs an inner boundary (1..n_layers-1) "
+                      "not taken by another, normal[2] > 0, and a height field of >= 2 x 2 nodes "
+                      "with positive spacing", j);
+            return RP_ERR_INVALID_ARG;
+        }
+        taken[S.layer] = true;
+        if (S.height) total += (size_t)S.nx * (size_t)S.ny;
+    }
+    std::vector<double> host(total);
+    size_t at = 0;
+    for (int j = 0; j < d->n_surfaces; ++j) {
+        const rp_surface &S = d->surfaces[j];
+        if (!S.height) continue;
+        const size_t cnt = (size_t)S.nx * (size_t)S.ny;
+        RP_CUDA_TRY(cudaMemcpy(host.data() + at, S.height, cnt * sizeof(double), cudaMemcpyDefault));
+        for (size_t i = 0; i < cnt; ++i)
+            if (!std::isfinite(host[at + i])) {
+                set_error("rp_medium_create: surface %d has a non-finite height", j);
+                return RP_ERR_INVALID_ARG;
+            }
+        at += cnt;
+    }
+    if (total) {
+        cudaError_t e = cudaMalloc(&m->surf_dev, total * sizeof(double));
+        if (e != cudaSuccess) {
+            m->surf_dev = nullptr;
+            return cuda_fail(e, "cudaMalloc(height fields)");
+        }
+        RP_CUDA_TRY(cudaMemcpy(m->surf_dev, host.data(), total * sizeof(double),
+                               cudaMemcpyHostToDevice));
+    }
+    at = 0;
+    for (int j = 0; j < d->n_surfaces; ++j) {
+        const rp_surface &S = d->surfaces[j];
+        rpk::SurfB &B = m->surf[S.layer];
+        B.on = 1;
+        B.sx = -S.normal[0] / S.normal[2];
+        B.sy = -S.normal[1] / S.normal[2];
+        B.h = nullptr;
+        if (S.height) {
+            B.h = m->surf_dev + at;
+            at += (size_t)S.nx * (size_t)S.ny;
+            B.nx = S.nx;
+            B.ny = S.ny;
+            B.ox = S.origin[0];
+            B.oy = S.origin[1];
+            B.dx = S.spacing[0];
+            B.dy = S.spacing[1];
+        }
+    }
+    m->n_surf = d->n_surfaces;
     return RP_OK;
 }
 
@@ -188,12 +277,15 @@ int rp_medium_create(const rp_medium_desc *d, void *stream, rp_medium_t *out)
             for (int side = 0; side < 2; ++side) {
                 const rp_layer &L = d->layers[side == 0 ? k - 1 : k];
                 double n = L.dn == 0.0 ? L.n0 + L.offset : L.n0 - L.dn * exp(-z / L.z0) + L.offset;
+                double dndz = L.dn == 0.0 ? 0.0 : L.dn / L.z0 * exp(-z / L.z0);
                 if (side == 0) {
                     m->layered.n_above[k] = n;
                     m->layered.n_above_f[k] = (float)n;
+                    m->layered.kap_above_f[k] = (float)(dndz / n);
                 } else {
                     m->layered.n_below[k] = n;
                     m->layered.n_below_f[k] = (float)n;
+                    m->layered.kap_below_f[k] = (float)(dndz / n);
                 }
             }
             m->layered.eta_down[k] = m->layered.n_above[k] / m->layered.n_below[k];
@@ -252,6 +344,11 @@ int rp_medium_create(const rp_medium_desc *d, void *stream, rp_medium_t *out)
             B.pad = 0.0f;
         }
         if (int rc = bind_device()) return rc;
+        if (int rc = build_surfaces(m, d)) {
+            if (m->surf_dev) cudaFree(m->surf_dev);
+            delete m;
+            return rc;
+        }
     } else if (d->kind == RP_MEDIUM_GRID) {
         if (d->nx < 2 || d->ny < 2 || d->nz < 2 || !(d->spacing > 0.0) || !d->grid_n) {
             delete m;
@@ -293,6 +390,7 @@ int rp_medium_destroy(rp_medium_t m)
 {
     if (!m) return RP_OK;
     if (m->grid_dev) cudaFree(m->grid_dev);
+    if (m->surf_dev) cudaFree(m->surf_dev);
     delete m;
     return RP_OK;
 }

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "rp_internal.h"
+#include "tc_common.cuh"
 
 namespace {
 
@@ -350,7 +351,7 @@ int forward(rp_surrogate_s *s, long long n, const float *x, float *out, bool tra
     RP_CUDA_TRY(cudaGetLastError());
     for (int l = 1; l <= 3; ++l)
         if ((rc = tc_dense(true, s->H[l], n, s->pack + (l - 1) * kPackW, s->p + layer_b(l), nullptr,
-                           train ? s->Z[l] : nullptr, s->H[l + 1], s->fflag, st)))
+                           train ? s->Z[l] : nullptr, s->H[l + 1], s->fflag, wait_cycles(s), st)))
             return rc;
     int dev;
     RP_CUDA_TRY(cudaGetDevice(&dev));
@@ -386,10 +387,11 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
         if (l >= 1 && l <= 3) {
             // hidden 256 x 256 layers on the tensor cores: dW_l = H_l^T g and db_l, then
             // g_{l-1} = (g W_l^T) * GELU'(Z_{l-1})
-            if ((rc = tc_wgrad(h, g_cur, n, s->grad + layer_w(l), s->grad + layer_b(l), s->fflag, st)))
+            if ((rc = tc_wgrad(h, g_cur, n, s->grad + layer_w(l), s->grad + layer_b(l), s->fflag,
+                               wait_cycles(s), st)))
                 return rc;
             if ((rc = tc_dense(false, g_cur, n, s->pack_t + (l - 1) * kPackW, nullptr, s->Z[l - 1],
-                               nullptr, g_next, s->fflag, st)))
+                               nullptr, g_next, s->fflag, wait_cycles(s), st)))
                 return rc;
             float *tmp = g_cur;
             g_cur = g_next;
@@ -421,6 +423,8 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
     }
     return RP_OK;
 }
+
+long long wait_cycles(const rp_surrogate_s *s) { return s->wait > 0 ? s->wait : tc::kWaitCycles; }
 
 // loss[1] += loss[0] / n: the running sum of batch losses of an epoch
 __global__ void k_acc_loss(double *loss, double inv_n) { loss[1] += loss[0] * inv_n; }
@@ -516,6 +520,16 @@ int rp_surrogate_create(const float *params, rp_surrogate_t *out)
     return RP_OK;
 }
 
+int rp_surrogate_set_wait_limit(rp_surrogate_t s, int64_t cycles)
+{
+    if (!s || cycles < 0) {
+        set_error("rp_surrogate_set_wait_limit: null handle or negative limit");
+        return RP_ERR_INVALID_ARG;
+    }
+    s->wait = (long long)cycles;
+    return RP_OK;
+}
+
 int rp_surrogate_destroy(rp_surrogate_t s)
 {
     if (!s) return RP_OK;
@@ -584,6 +598,7 @@ int rp_surrogate_loss_grad(rp_surrogate_t s, int64_t n, const float *x, const fl
         return RP_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    RP_CUDA_TRY(cudaMemsetAsync(s->fflag, 0, sizeof(int), st));
     double L = 0.0;
     int rc = loss_grad(s, n, x, y, t, &L, st);
     if (rc) return rc;
@@ -604,6 +619,7 @@ int rp_surrogate_train_step(rp_surrogate_t s, int64_t n, const float *x, const f
         return RP_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    RP_CUDA_TRY(cudaMemsetAsync(s->fflag, 0, sizeof(int), st));
     int rc = loss_grad(s, n, x, y, t, loss, st);
     if (rc) return rc;
     if ((rc = adam_step(s, lr, st))) return rc;
@@ -620,6 +636,7 @@ int rp_surrogate_train(rp_surrogate_t s, int64_t n, const float *x, const float 
         return RP_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    RP_CUDA_TRY(cudaMemsetAsync(s->fflag, 0, sizeof(int), st));
     const long long nb = n / p->batch, B = p->batch;
     int rc = ensure_acts(s, B);
     if (rc) return rc;

@@ -17,8 +17,9 @@
 // ((k/8) * 16 + row/8) * 128 (K-direction stride 2048 B, 8-row stride 128 B); for B (256 n x 256
 // k) core (k/8, n/8) at ((k/8) * 32 + n/8) * 128 (4096 B, 128 B).  Arithmetic is that of the
 // unfused path: BF16 operands, FP32 products and sums, FP32 bias and GELU.
-// Every wait on an mbarrier is bounded (about two seconds); a CTA that gives up sets the error
-// flag, waits (bounded) for its work in flight, frees its tensor memory and returns.
+// Every wait on an mbarrier is bounded (by default about two seconds; rp_surrogate_set_wait_limit
+// sets it); a CTA that gives up sets the error flag, waits (with the default bound) for its work
+// in flight, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -67,7 +68,7 @@ __device__ __forceinline__ void load_weights(uint32_t b_base, const unsigned cha
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_mlp_fused(const unsigned char *__restrict__ pack, const float *__restrict__ x,
-                float *__restrict__ out, long long n, int *flag)
+                float *__restrict__ out, long long n, int *flag, long long wait)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *sA = sm + SM_A;
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncthreads();
             fence_after();
             if (tid == 0) {
-                if (mbar_wait(bar_ld, ph_ld)) {
+                if (mbar_wait(bar_ld, ph_ld, wait)) {
                     ld_pending = false;
 #pragma unroll
                     for (int s = 0; s < 16; ++s) {
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             ph_ld ^= 1u;
-            if (!mbar_wait(bar_mma, ph_mma)) *abort_cta = 1;
+            if (!mbar_wait(bar_mma, ph_mma, wait)) *abort_cta = 1;
             ph_mma ^= 1u;
             fence_after();
             __syncthreads();
@@ -276,7 +277,7 @@ int forward_fused(rp_surrogate_s *s, long long n, const float *x, float *out, cu
     RP_CUDA_TRY(cudaMemsetAsync(s->fflag, 0, sizeof(int), st));
     const long long tiles = (n + kTile - 1) / kTile;
     const int grid = (int)std::min<long long>(tiles, (long long)sm_count(dev));
-    k_mlp_fused<<<grid, kThreads, SM_TOTAL, st>>>(s->pack, x, out, n, s->fflag);
+    k_mlp_fused<<<grid, kThreads, SM_TOTAL, st>>>(s->pack, x, out, n, s->fflag, wait_cycles(s));
     RP_CUDA_TRY(cudaGetLastError());
     return RP_OK;
 }
@@ -287,9 +288,9 @@ int fused_status(rp_surrogate_s *s, cudaStream_t st)
     RP_CUDA_TRY(cudaMemcpyAsync(&f, s->fflag, sizeof(int), cudaMemcpyDeviceToHost, st));
     RP_CUDA_TRY(cudaStreamSynchronize(st));
     if (f) {
-        set_error("surrogate: a bounded wait of a tensor-core kernel gave up (its work did not "
-                  "complete)");
-        return RP_ERR_CUDA;
+        set_error("surrogate: a bounded wait of a tensor-core kernel gave up after %lld SM "
+                  "cycles (its work did not complete in time)", wait_cycles(s));
+        return RP_ERR_TIMEOUT;
     }
     return RP_OK;
 }

@@ -17,8 +17,9 @@
 //     columns), and adds its sums to dW with vector atomics at the end; the bias gradient
 //     (column sums of g) comes along from the staging loads.
 // Arithmetic is that of the CUDA-core GEMMs they replace: BF16 operands, FP32 products and
-// sums, FP32 bias, GELU and GELU'.  Every mbarrier wait is bounded; a CTA that gives up sets the
-// error flag, waits (bounded) for its work in flight, frees its tensor memory and returns.
+// sums, FP32 bias, GELU and GELU'.  Every mbarrier wait is bounded (the surrogate's wait limit);
+// a CTA that gives up sets the error flag, waits (with the default bound) for its work in
+// flight, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -75,7 +76,7 @@ template <int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_dense(const float *__restrict__ A, long long n, const unsigned char *__restrict__ Bimg,
                const float *__restrict__ bias, const float *__restrict__ Zin,
-               float *__restrict__ Zout, float *__restrict__ Out, int *flag)
+               float *__restrict__ Zout, float *__restrict__ Out, int *flag, long long wait)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + DN_BAR);  // [0] B in, [1] MMAs done
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = *slot;
     bool ld_pending = tid == 0, mma_pending = false;
     if (tid == 0) {
-        if (mbar_wait(bar_ld, 0)) {
+        if (mbar_wait(bar_ld, 0, wait)) {
             ld_pending = false;
             // the half's 16 n-cores of each k-core row of the B image: start 2048 B further
 #pragma unroll
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
     bool failed = *abort_cta != 0;
-    if (!failed && !mbar_wait(bar_mma, 0)) *abort_cta = 1;
+    if (!failed && !mbar_wait(bar_mma, 0, wait)) *abort_cta = 1;
     fence_after();
     __syncthreads();
     failed = *abort_cta != 0;
@@ -217,7 +218,7 @@ constexpr int kChunk = 128;  // rows (K) per chunk
 // dW[:, 128 h .. 128 h + 127] (h = blockIdx.y) over the chunks blockIdx.x, + gridDim.x, ...
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_wgrad(const float *__restrict__ H, const float *__restrict__ G, long long n,
-               float *__restrict__ dW, float *__restrict__ db, int *flag)
+               float *__restrict__ dW, float *__restrict__ db, int *flag, long long wait)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + WG_BAR);  // MMAs done
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_pending = true;
         }
         // the images are rewritten for the next chunk only after these MMAs have read them
-        if (!mbar_wait(bar_mma, ph)) *abort_cta = 1;
+        if (!mbar_wait(bar_mma, ph, wait)) *abort_cta = 1;
         ph ^= 1u;
         fence_after();
         __syncthreads();
@@ -365,25 +366,25 @@ int tc_pack_backward(const float *p, unsigned char *img, long long w1, long long
 
 int tc_dense(bool forward, const float *A, long long n, const unsigned char *Bimg,
              const float *bias, const float *Zin, float *Zout, float *Out, int *flag,
-             cudaStream_t st)
+             long long wait, cudaStream_t st)
 {
     if (n <= 0) return RP_OK;
     const dim3 grid((unsigned)((n + kRows - 1) / kRows), 2);  // row tiles x column halves
     if (forward) {
         RP_CUDA_TRY(cudaFuncSetAttribute(k_tc_dense<EPI_FWD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DN_TOTAL));
-        k_tc_dense<EPI_FWD><<<grid, kThreads, DN_TOTAL, st>>>(A, n, Bimg, bias, Zin, Zout, Out, flag);
+        k_tc_dense<EPI_FWD><<<grid, kThreads, DN_TOTAL, st>>>(A, n, Bimg, bias, Zin, Zout, Out, flag, wait);
     } else {
         RP_CUDA_TRY(cudaFuncSetAttribute(k_tc_dense<EPI_BWD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DN_TOTAL));
-        k_tc_dense<EPI_BWD><<<grid, kThreads, DN_TOTAL, st>>>(A, n, Bimg, bias, Zin, Zout, Out, flag);
+        k_tc_dense<EPI_BWD><<<grid, kThreads, DN_TOTAL, st>>>(A, n, Bimg, bias, Zin, Zout, Out, flag, wait);
     }
     RP_CUDA_TRY(cudaGetLastError());
     return RP_OK;
 }
 
 int tc_wgrad(const float *H, const float *G, long long n, float *dW, float *db, int *flag,
-             cudaStream_t st)
+             long long wait, cudaStream_t st)
 {
     if (n <= 0) return RP_OK;
     int dev;
@@ -393,7 +394,7 @@ int tc_wgrad(const float *H, const float *G, long long n, float *dW, float *db, 
     const dim3 grid((unsigned)std::min<long long>(chunks, (long long)sm_count(dev)), 2);
     RP_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)WG_TOTAL));
-    k_tc_wgrad<<<grid, kThreads, WG_TOTAL, st>>>(H, G, n, dW, db, flag);
+    k_tc_wgrad<<<grid, kThreads, WG_TOTAL, st>>>(H, G, n, dW, db, flag, wait);
     RP_CUDA_TRY(cudaGetLastError());
     return RP_OK;
 }

@@ -1295,9 +1295,9 @@ int run_surrogate_paths(rp_surrogate_s *s, rp_medium_t m, int64_t n, const doubl
                         const rp_path_params *p, const rp_surrogate_params *sp,
                         rp_solutions *sol, rp_surrogate_stats *stats, cudaStream_t st)
 {
-    if (!s || !m || !p || !sp || !sol || n < 0 || m->kind != RP_MEDIUM_LAYERED ||
-        m->layered.n_sph > 0) {
-        set_error("rp_surrogate_find_paths: bad arguments (layered medium required)");
+    if (!s || !m || !p || !sp || !sol || n < 0 || medium_variant(m) != VARIANT_LAYERED) {
+        set_error("rp_surrogate_find_paths: bad arguments (a layered medium with horizontal "
+                  "boundaries and no spheres required)");
         return RP_ERR_INVALID_ARG;
     }
     if (stats) memset(stats, 0, sizeof *stats);
@@ -1359,8 +1359,9 @@ int run_find_paths(rp_medium_t m, int64_t n_pairs, const double *zs, const doubl
         set_error("rp_find_paths: null medium, params or solutions, or n_pairs < 0");
         return RP_ERR_INVALID_ARG;
     }
-    if (m->kind != RP_MEDIUM_LAYERED || m->layered.n_sph > 0) {
-        set_error("rp_find_paths: path finding needs a layered medium without spheres");
+    if (medium_variant(m) != VARIANT_LAYERED) {
+        set_error("rp_find_paths: path finding needs a layered medium with horizontal "
+                  "boundaries and no spheres");
         return RP_ERR_INVALID_ARG;
     }
     if (n_pairs == 0) return RP_OK;

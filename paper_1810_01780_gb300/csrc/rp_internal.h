@@ -29,6 +29,7 @@ struct rp_surrogate_s {
     unsigned char *pack_t;  // training: W1..W3 as the backward pass's B images (mlp_train_tc.cu)
     long long version, pack_version;
     int *fflag;  // set by a tensor-core kernel when a bounded wait gave up
+    long long wait;  // SM cycles a tensor-core kernel waits on an mbarrier; 0: the default
 };
 
 struct rp_medium_s {
@@ -37,7 +38,27 @@ struct rp_medium_s {
     rpk::MediumSpheres layered;  // n_sph = 0: a plain layered medium
     rpk::MediumGrid grid;
     float4 *grid_dev;
+    // non-horizontal boundaries (n_surf > 0: the medium is traced as rpk::MediumSurfaces)
+    int n_surf;
+    rpk::SurfB surf[RP_MAX_LAYERS];
+    double *surf_dev;  // the height fields, one allocation
 };
+
+// Which instantiation of the tracer a medium takes.
+enum { VARIANT_LAYERED = 0, VARIANT_SPHERES = 1, VARIANT_SURFACES = 2, VARIANT_GRID = 3 };
+inline int medium_variant(const rp_medium_s *m)
+{
+    if (m->kind != RP_MEDIUM_LAYERED) return VARIANT_GRID;
+    if (m->layered.n_sph > 0) return VARIANT_SPHERES;
+    return m->n_surf > 0 ? VARIANT_SURFACES : VARIANT_LAYERED;
+}
+inline rpk::MediumSurfaces surfaces_of(const rp_medium_s *m)
+{
+    rpk::MediumSurfaces s;
+    static_cast<rpk::MediumLayered &>(s) = static_cast<const rpk::MediumLayered &>(m->layered);
+    for (int k = 0; k < RP_MAX_LAYERS; ++k) s.B[k] = m->surf[k];
+    return s;
+}
 
 namespace rph {
 
@@ -80,22 +101,12 @@ int validate_params(const rp_trace_params *p, bool path_finding);
 
 // Service-phase batching (see k_trace_wave): a warp services its waiting lanes once the idle
 // lane-iterations summed since its last service reach this threshold.  An FP64 step costs far
-// more than an FP32-mixed one against the same service phase, so FP64 lanes wait less.
-// RP_SERVICE_IDLE / RP_SERVICE_IDLE_F64 override the two.  Once a wave's input has run out, a
-// thread hands the rest of its secondary stack to the next launch when at least 2 records
-// remain below the one it takes (RP_FLUSH_MIN overrides the 2).
-inline int env_int(const char *name, int dflt, int lo, int hi)
-{
-    const char *v = getenv(name);
-    if (!v || !*v) return dflt;
-    int x = atoi(v);
-    return x < lo ? lo : (x > hi ? hi : x);
-}
-inline int service_idle(bool fp32)
-{
-    return fp32 ? env_int("RP_SERVICE_IDLE", 256, 1, 1 << 20)
-                : env_int("RP_SERVICE_IDLE_F64", 8, 1, 1 << 20);
-}
+// more than an FP32-mixed one against the same service phase, so FP64 lanes wait less.  Once a
+// wave's input has run out, a thread hands the rest of its secondary stack to the next launch
+// when at least kFlushMinDefault records remain below the one it takes.  rp_trace_params
+// overrides both (0 keeps the default).
+constexpr int kServiceIdleF32 = 256, kServiceIdleF64 = 8, kFlushMinDefault = 2;
+constexpr int kBlockDefault = 128, kBlockMax = 256;
 
 template <class P>
 inline rpk::StepParams<P> step_params(const rp_trace_params *p, int axis, float dir)
@@ -123,8 +134,9 @@ inline rpk::StepParams<P> step_params(const rp_trace_params *p, int axis, float 
     sp.stop_axis = axis;
     sp.stop_dir = dir;
     sp.max_steps = p->max_steps;
-    sp.service_idle = (unsigned int)service_idle(P::kFF);
-    sp.flush_min = env_int("RP_FLUSH_MIN", 2, 1, 1 << 20);
+    sp.service_idle = (unsigned int)(p->service_idle > 0 ? p->service_idle
+                                     : (P::kFF ? kServiceIdleF32 : kServiceIdleF64));
+    sp.flush_min = p->flush_min > 0 ? p->flush_min : kFlushMinDefault;
     return sp;
 }
 
@@ -168,9 +180,11 @@ int tc_pack_backward(const float *p, unsigned char *img, long long w1, long long
                      cudaStream_t st);
 int tc_dense(bool forward, const float *A, long long n, const unsigned char *Bimg,
              const float *bias, const float *Zin, float *Zout, float *Out, int *flag,
-             cudaStream_t st);
+             long long wait, cudaStream_t st);
 int tc_wgrad(const float *H, const float *G, long long n, float *dW, float *db, int *flag,
-             cudaStream_t st);
+             long long wait, cudaStream_t st);
+// the mbarrier wait limit of the surrogate's tensor-core kernels [SM cycles]
+long long wait_cycles(const rp_surrogate_s *s);
 int run_surrogate_paths(rp_surrogate_s *s, rp_medium_t m, int64_t n, const double *zs,
                         const double *zr, const double *dist, const int32_t *n_angles,
                         const rp_path_params *p, const rp_surrogate_params *sp,

@@ -25,11 +25,26 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase)
+// Waits until the mbarrier `bar` has completed phase `phase`; false once `limit` SM cycles
+// have passed without it (the caller then records the failure and drains its work in flight
+// with a wait of the default limit before it returns).  Each round first tests the phase
+// without blocking, then checks the limit, then waits with mbarrier.try_wait (which may
+// suspend the thread for a while): so a limit shorter than the work it waits for always runs
+// out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long limit = kWaitCycles)
 {
     const long long t0 = clock64();
     for (;;) {
         uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred P;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, P;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > limit) return false;
         asm volatile(
             "{\n\t.reg .pred P;\n\t"
             "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
@@ -38,7 +53,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase)
             : "r"(bar), "r"(phase)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
     }
 }
 

@@ -142,6 +142,9 @@ __device__ __forceinline__ void load_primary(Lane<P> &L, const M &med, const Sin
         if constexpr (has_spheres_v<M>) {
             const double r0[3] = {in.pos[k], in.pos[n + k], in.pos[2 * n + k]};
             L.layer = region_of(med, r0);
+        } else if constexpr (has_surfaces_v<M>) {
+            const double r0[3] = {in.pos[k], in.pos[n + k], in.pos[2 * n + k]};
+            L.layer = layer_at(med, r0);
         } else if constexpr (is_layered_v<M>) {
             L.layer = layer_of_ff(med, L.r.hi[2], L.r.lo[2]);
         } else {
@@ -174,6 +177,8 @@ __device__ __forceinline__ void load_primary(Lane<P> &L, const M &med, const Sin
         L.h = P::from_d(in.h0);
         if constexpr (has_spheres_v<M>)
             L.layer = region_of(med, r);
+        else if constexpr (has_surfaces_v<M>)
+            L.layer = layer_at(med, r);
         else if constexpr (is_layered_v<M>)
             L.layer = layer_of(med, r[2]);
         else
@@ -266,8 +271,10 @@ __device__ int next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, const
     return st == RP_ST_ALIVE ? NEXT_TRACE : NEXT_RECORD;
 }
 
+// Launched with any block of up to kBlockMax threads (a multiple of 32); the bounds keep the
+// register budget of P::kMinBlocks blocks of 128 threads per SM.
 template <class P, class M>
-__global__ void __launch_bounds__(128, P::kMinBlocks) k_trace_wave(const M med, const StepParams<P> sp,
+__global__ void __launch_bounds__(kBlockMax, P::kMinBlocks * 128 / kBlockMax) k_trace_wave(const M med, const StepParams<P> sp,
                                                     const Sinks sk, const WaveIn in, int wave)
 {
     unsigned long long base = 0, count;
@@ -353,43 +360,46 @@ __global__ void k_prep_wave(Ctrl *ctrl, int w, unsigned long long q_cap)
     ctrl->seg_end[w] = tail;
 }
 
+// Resident blocks per SM of k_trace_wave<P, M> at `block` threads (cached per block size),
+// capped at `want` when 0 < want.
 template <class P, class M>
-static int occupancy_grid(int block)
+static int occupancy_grid(int block, int want)
 {
-    static int cached_block = -1, cached_occ = 0;
-    if (cached_block != block) {
-        int occ = 0;
+    static int cached[kBlockMax / 32 + 1] = {0};
+    const int slot = block / 32;
+    int occ = cached[slot];
+    if (occ == 0) {
         RP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_wave<P, M>,
                                                                   block, 0));
-        cached_occ = occ > 0 ? occ : 1;
-        cached_block = block;
+        occ = occ > 0 ? occ : 1;
+        cached[slot] = occ;
     }
-    return cached_occ;
+    return (want > 0 && want < occ) ? want : occ;
 }
 
-static int trace_threads(int kind, bool spheres, int precision, int device, int block)
+static int trace_blocks(int variant, int precision, int block, int want)
 {
-    int occ;
-    if (kind == RP_MEDIUM_LAYERED && spheres)
-        occ = precision == RP_FP64 ? occupancy_grid<PrecF64, MediumSpheres>(block)
-                                   : occupancy_grid<PrecF32, MediumSpheres>(block);
-    else if (kind == RP_MEDIUM_LAYERED)
-        occ = precision == RP_FP64 ? occupancy_grid<PrecF64, MediumLayered>(block)
-                                   : occupancy_grid<PrecF32, MediumLayered>(block);
-    else
-        occ = precision == RP_FP64 ? occupancy_grid<PrecF64, MediumGrid>(block)
-                                   : occupancy_grid<PrecF32, MediumGrid>(block);
-    if (occ < 0) return occ;
-    return sm_count(device) * occ * block;
+    const bool f64 = precision == RP_FP64;
+    switch (variant) {
+    case VARIANT_SPHERES:
+        return f64 ? occupancy_grid<PrecF64, MediumSpheres>(block, want)
+                   : occupancy_grid<PrecF32, MediumSpheres>(block, want);
+    case VARIANT_SURFACES:
+        return f64 ? occupancy_grid<PrecF64, MediumSurfaces>(block, want)
+                   : occupancy_grid<PrecF32, MediumSurfaces>(block, want);
+    case VARIANT_LAYERED:
+        return f64 ? occupancy_grid<PrecF64, MediumLayered>(block, want)
+                   : occupancy_grid<PrecF32, MediumLayered>(block, want);
+    default:
+        return f64 ? occupancy_grid<PrecF64, MediumGrid>(block, want)
+                   : occupancy_grid<PrecF32, MediumGrid>(block, want);
+    }
 }
 
 template <class P, class M>
 static int launch_waves(const M &med, const StepParams<P> &sp, const Sinks &sk, const WaveIn &in,
-                        int n_waves, int device, int block, cudaStream_t st, cudaEvent_t *ev)
+                        int n_waves, int grid, int block, cudaStream_t st, cudaEvent_t *ev)
 {
-    int occ = occupancy_grid<P, M>(block);
-    if (occ < 0) return occ;
-    const int grid = sm_count(device) * occ;
     for (int w = 0; w < n_waves; ++w) {
         if (w > 0) k_prep_wave<<<1, 1, 0, st>>>(sk.ctrl, w, sk.q_cap);
         k_trace_wave<P, M><<<grid, block, 0, st>>>(med, sp, sk, in, w);
@@ -463,7 +473,8 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
         return RP_ERR_INVALID_ARG;
     }
 
-    // receivers: sort by centre depth on the host (tiny), upload with the workspace
+    // receivers: bin into a uniform cell grid on the host (each sphere listed in every cell
+    // its centre box, inflated by R + h_max / 2, overlaps), upload with the workspace
     std::vector<SphereC> spheres(n_rx);
     std::vector<int2> cells;
     std::vector<int> items;
@@ -530,10 +541,12 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
         }
     }
 
-    const int block = 128;
-    const int threads = trace_threads(m->kind, m->kind == RP_MEDIUM_LAYERED && m->layered.n_sph > 0,
-                                      p->precision, dev, block);
-    if (threads < 0) return threads;
+    const int block = p->block > 0 ? p->block : kBlockDefault;
+    const int variant = medium_variant(m);
+    const int per_sm = trace_blocks(variant, p->precision, block, p->blocks_per_sm);
+    if (per_sm < 0) return per_sm;
+    const int grid = sm_count(dev) * per_sm;
+    const int threads = grid * block;
     // scratch layout: control block, receivers, per-thread stacks, warp clocks, queue last
     long long q_cap = out->capacity - in->n;
     int depth = kStackDepth;
@@ -547,8 +560,12 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
         // fixed scratch: at most half of it for the stacks, the rest (after the fixed parts)
         // for the queue
         if (off_k + clk_bytes + align_up(sizeof(QRec) * (size_t)threads) + 4096 > fs->size) {
-            set_error("rp_trace: %d receivers need more than the %zu-byte fixed scratch", n_rx,
-                      fs->size);
+            set_error("rp_trace_static: the %zu-byte fixed scratch cannot hold the control block, "
+                      "the cell table of %d receivers (%zu bytes) and one %zu-byte stack record "
+                      "for each of the %d threads of the launch (%d SMs x %d blocks x %d); "
+                      "fewer blocks_per_sm or receivers fit",
+                      fs->size, n_rx, off_k - off_s, sizeof(QRec), threads, sm_count(dev),
+                      per_sm, block);
             return RP_ERR_INVALID_ARG;
         }
         while (depth > 1 && off_k + clk_bytes + sizeof(QRec) * (size_t)threads * depth > fs->size / 2)
@@ -565,6 +582,20 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     Workspace &ws = workspace(dev);
     std::unique_lock<std::mutex> lock(fs ? *fs->mu : ws.mu);
     if (!fs && (rc = ensure_workspace(ws, total))) return rc;
+    // Declared after the lock, so destroyed before it is released: on every return from here
+    // on, the work already queued on `st` (which reads and writes the scratch) has drained
+    // before another call may reuse the scratch, and the timing events are released.
+    struct Drain {
+        cudaStream_t st;
+        cudaEvent_t ev[RP_MAX_WAVES + 1];
+        bool queued = false;
+        ~Drain()
+        {
+            if (queued) cudaStreamSynchronize(st);
+            for (cudaEvent_t e : ev)
+                if (e) cudaEventDestroy(e);
+        }
+    } drain{st, {}};
     char *base = fs ? (char *)fs->ptr : (char *)ws.ptr;
     Ctrl *ctrl = (Ctrl *)(base + off_ctrl);
 
@@ -592,6 +623,7 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     }
     sk.rx.inv_cell = g_inv;
 
+    drain.queued = true;
     RP_CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
     if (n_rx) {
         RP_CUDA_TRY(cudaMemcpyAsync(base + off_s, spheres.data(), sizeof(SphereC) * n_rx,
@@ -614,34 +646,38 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     wi.h0f = (float)p->h0;
 
     const int n_waves = p->max_generation + 1;  // launches: the stacks' overflow needs at most this
-    cudaEvent_t ev[RP_MAX_WAVES + 1];
+    cudaEvent_t *ev = drain.ev;
     for (int w = 0; w <= n_waves; ++w) RP_CUDA_TRY(cudaEventCreate(&ev[w]));
     RP_CUDA_TRY(cudaEventRecord(ev[0], st));
-    if (m->kind == RP_MEDIUM_LAYERED && m->layered.n_sph > 0) {
-        if (p->precision == RP_FP64)
-            rc = launch_waves<PrecF64, MediumSpheres>(m->layered,
-                                                      step_params<PrecF64>(p, axis, sdir),
-                                                      sk, wi, n_waves, dev, block, st, ev);
-        else
-            rc = launch_waves<PrecF32, MediumSpheres>(m->layered,
-                                                      step_params<PrecF32>(p, axis, sdir),
-                                                      sk, wi, n_waves, dev, block, st, ev);
-    } else if (m->kind == RP_MEDIUM_LAYERED) {
-        if (p->precision == RP_FP64)
-            rc = launch_waves<PrecF64, MediumLayered>(m->layered,
-                                                      step_params<PrecF64>(p, axis, sdir),
-                                                      sk, wi, n_waves, dev, block, st, ev);
-        else
-            rc = launch_waves<PrecF32, MediumLayered>(m->layered,
-                                                      step_params<PrecF32>(p, axis, sdir),
-                                                      sk, wi, n_waves, dev, block, st, ev);
-    } else {
-        if (p->precision == RP_FP64)
-            rc = launch_waves<PrecF64, MediumGrid>(m->grid, step_params<PrecF64>(p, axis, sdir),
-                                                   sk, wi, n_waves, dev, block, st, ev);
-        else
-            rc = launch_waves<PrecF32, MediumGrid>(m->grid, step_params<PrecF32>(p, axis, sdir),
-                                                   sk, wi, n_waves, dev, block, st, ev);
+    const bool f64 = p->precision == RP_FP64;
+    const StepParams<PrecF64> sp64 = step_params<PrecF64>(p, axis, sdir);
+    const StepParams<PrecF32> sp32 = step_params<PrecF32>(p, axis, sdir);
+    switch (variant) {
+    case VARIANT_SPHERES:
+        rc = f64 ? launch_waves<PrecF64, MediumSpheres>(m->layered, sp64, sk, wi, n_waves, grid,
+                                                        block, st, ev)
+                 : launch_waves<PrecF32, MediumSpheres>(m->layered, sp32, sk, wi, n_waves, grid,
+                                                        block, st, ev);
+        break;
+    case VARIANT_SURFACES: {
+        const MediumSurfaces ms = surfaces_of(m);
+        rc = f64 ? launch_waves<PrecF64, MediumSurfaces>(ms, sp64, sk, wi, n_waves, grid, block,
+                                                         st, ev)
+                 : launch_waves<PrecF32, MediumSurfaces>(ms, sp32, sk, wi, n_waves, grid, block,
+                                                         st, ev);
+        break;
+    }
+    case VARIANT_LAYERED:
+        rc = f64 ? launch_waves<PrecF64, MediumLayered>(m->layered, sp64, sk, wi, n_waves, grid,
+                                                        block, st, ev)
+                 : launch_waves<PrecF32, MediumLayered>(m->layered, sp32, sk, wi, n_waves, grid,
+                                                        block, st, ev);
+        break;
+    default:
+        rc = f64 ? launch_waves<PrecF64, MediumGrid>(m->grid, sp64, sk, wi, n_waves, grid, block,
+                                                     st, ev)
+                 : launch_waves<PrecF32, MediumGrid>(m->grid, sp32, sk, wi, n_waves, grid, block,
+                                                     st, ev);
     }
     // read-back: pinned buffers of the workspace, or (fixed scratch) pageable host memory and
     // no warp clocks, so that nothing is allocated
@@ -662,8 +698,8 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     if (!rc) {
         for (int w = 0; w < n_waves; ++w) cudaEventElapsedTime(&wave_ms[w], ev[w], ev[w + 1]);
         cudaEventElapsedTime(&ms, ev[0], ev[n_waves]);
+        drain.queued = false;  // the read-back synchronised the stream
     }
-    for (int w = 0; w <= n_waves; ++w) cudaEventDestroy(ev[w]);
     if (rc) return rc;
 
     unsigned flags = hc->flags;
@@ -678,6 +714,9 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
         stats->queue_needed = (int64_t)hc->q_tail;
         stats->waves = n_waves;
         stats->flags = (int32_t)flags;
+        stats->queue_capacity = (int64_t)q_cap;
+        stats->threads = threads;
+        stats->stack_depth = depth;
         stats->kernel_ms = ms;
         for (int w = 0; w < RP_MAX_WAVES; ++w) stats->wave_ms[w] = w < n_waves ? wave_ms[w] : 0.0;
         // tail of the first launch: warp end times after the earliest warp start

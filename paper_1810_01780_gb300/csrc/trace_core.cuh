@@ -244,6 +244,8 @@ struct MediumLayered {
     float n_above_f[RP_MAX_LAYERS], n_below_f[RP_MAX_LAYERS];
     // index ratios n1 / n2 for a ray crossing plane k downward and upward
     double eta_down[RP_MAX_LAYERS], eta_up[RP_MAX_LAYERS];
+    // (dn/dz) / n just above / below plane k: the ray equation's curvature scale there
+    float kap_above_f[RP_MAX_LAYERS], kap_below_f[RP_MAX_LAYERS];
 };
 
 struct MediumGrid {
@@ -268,10 +270,91 @@ struct MediumSpheres : MediumLayered {
     SphereB S[RP_MAX_SPHERES];
 };
 
+// Non-horizontal layer boundary k (boundary shapes beyond the plane, the paragraph after
+// Fig. 1): zb(x, y) = z_top + sx x + sy y + H(x, y), H the bilinear interpolant of nx x ny node
+// heights h (x fastest; node (i, j) at (ox + i dx, oy + j dy)), held at its edge values beyond
+// the nodes; h == nullptr: no height field.  on == 0: the horizontal plane z = z_top.
+struct SurfB {
+    const double *__restrict__ h;
+    int32_t on, nx, ny, pad;
+    double sx, sy, ox, oy, dx, dy;
+};
+
+// A layered medium whose inner boundaries may be tilted planes or height-field surfaces.
+struct MediumSurfaces : MediumLayered {
+    SurfB B[RP_MAX_LAYERS];
+};
+
 template <class M>
 constexpr bool is_layered_v = std::is_base_of<MediumLayered, M>::value;
 template <class M>
 constexpr bool has_spheres_v = std::is_same<M, MediumSpheres>::value;
+template <class M>
+constexpr bool has_surfaces_v = std::is_same<M, MediumSurfaces>::value;
+
+// Depth of boundary k at (x, y) and (gx, gy non-NULL) its slopes dzb/dx, dzb/dy, in FP64 with
+// the FP64 reference's operations, unfused.
+__device__ __forceinline__ double surf_depth(const MediumSurfaces &m, int k, double x, double y,
+                                             double *gx, double *gy)
+{
+    const SurfB &B = m.B[k];
+    double z = m.top[k].d, sx = 0.0, sy = 0.0;
+    if (B.on) {
+        z = __dadd_rn(z, __dadd_rn(__dmul_rn(B.sx, x), __dmul_rn(B.sy, y)));
+        sx = B.sx;
+        sy = B.sy;
+        if (B.h) {
+            const double u_raw = __ddiv_rn(__dsub_rn(x, B.ox), B.dx);
+            const double v_raw = __ddiv_rn(__dsub_rn(y, B.oy), B.dy);
+            const double u = fmin(fmax(u_raw, 0.0), (double)(B.nx - 1));
+            const double v = fmin(fmax(v_raw, 0.0), (double)(B.ny - 1));
+            int i = (int)floor(u), j = (int)floor(v);
+            if (i > B.nx - 2) i = B.nx - 2;
+            if (j > B.ny - 2) j = B.ny - 2;
+            const double fu = __dsub_rn(u, (double)i), fv = __dsub_rn(v, (double)j);
+            const double *r0 = B.h + (size_t)j * B.nx + i, *r1 = r0 + B.nx;
+            const double h00 = r0[0], h10 = r0[1], h01 = r1[0], h11 = r1[1];
+            const double gu = __dsub_rn(1.0, fu), gv = __dsub_rn(1.0, fv);
+            if (gx) {
+                *gx = (u_raw >= 0.0 && u_raw <= (double)(B.nx - 1))
+                          ? __ddiv_rn(__dadd_rn(__dmul_rn(gv, __dsub_rn(h10, h00)),
+                                                __dmul_rn(fv, __dsub_rn(h11, h01))), B.dx)
+                          : 0.0;
+                *gy = (v_raw >= 0.0 && v_raw <= (double)(B.ny - 1))
+                          ? __ddiv_rn(__dadd_rn(__dmul_rn(gu, __dsub_rn(h01, h00)),
+                                                __dmul_rn(fu, __dsub_rn(h11, h10))), B.dy)
+                          : 0.0;
+                sx = __dadd_rn(sx, *gx);
+                sy = __dadd_rn(sy, *gy);
+            }
+            const double H = __dadd_rn(
+                __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(gu, gv), h00), __dmul_rn(__dmul_rn(fu, gv), h10)),
+                          __dmul_rn(__dmul_rn(gu, fv), h01)),
+                __dmul_rn(__dmul_rn(fu, fv), h11));
+            z = __dadd_rn(z, H);
+        }
+    }
+    if (gx) {
+        *gx = sx;
+        *gy = sy;
+    }
+    return z;
+}
+
+// True if boundary k of the medium exists and is a tilted plane or height field.
+__device__ __forceinline__ bool surf_on(const MediumSurfaces &m, int k)
+{
+    return k >= 1 && k < m.n_layers && m.B[k].on;
+}
+
+// Layer of the point r (FP64; once per ray): the last boundary at or above it.
+__device__ __forceinline__ int layer_at(const MediumSurfaces &m, const double r[3])
+{
+    int k = 0;
+    for (int j = 1; j < m.n_layers; ++j)
+        if (r[2] >= surf_depth(m, j, r[0], r[1], nullptr, nullptr)) k = j;
+    return k;
+}
 
 __device__ __forceinline__ int layer_of(const MediumLayered &m, double z)
 {
@@ -742,8 +825,8 @@ __device__ __forceinline__ bool split_dirs(const double t[3], const double nrm[3
 }
 
 // ---------------------------------------------------------------------------------------
-// Receivers: spheres sorted by centre depth; a chord is tested against the spheres whose
-// depth slab it overlaps.
+// Receivers: spheres binned in a uniform cell grid (see Receivers); a chord is tested against
+// the spheres listed in the cell of its midpoint.
 // ---------------------------------------------------------------------------------------
 struct SphereC {
     PlaneC c[3];
@@ -939,6 +1022,27 @@ __device__ __forceinline__ typename P::R event_g(const MediumSpheres &m, const L
         const int j = kind - EV_SPH;
         const typename P::R g = sphere_dist<P>(L.r, dr, m.S[j]);
         return (L.layer == RP_MAX_LAYERS + j) ? -g : g;
+    }
+    return event_g<P>(static_cast<const MediumLayered &>(m), L, sp, kind, dr);
+}
+
+// Signed vertical offset from a layer boundary of a medium with surfaces, positive on the
+// ray's own side (z - zb below the boundary, zb - z above it), for the candidate r + dr; in
+// FP64 in both policies (horizontal planes keep the plane form).
+template <class P>
+__device__ __forceinline__ typename P::R event_g(const MediumSurfaces &m, const Lane<P> &L,
+                                                 const StepParams<P> &sp, int kind,
+                                                 const typename P::R dr[3])
+{
+    if (kind == EV_TOP || kind == EV_BOTTOM) {
+        const int k = (kind == EV_TOP) ? L.layer : L.layer + 1;
+        if (surf_on(m, k)) {
+            const double x = P::get(L.r, 0) + (double)dr[0];
+            const double y = P::get(L.r, 1) + (double)dr[1];
+            const double z = P::get(L.r, 2) + (double)dr[2];
+            const double zb = surf_depth(m, k, x, y, nullptr, nullptr);
+            return (typename P::R)((kind == EV_TOP) ? __dsub_rn(z, zb) : __dsub_rn(zb, z));
+        }
     }
     return event_g<P>(static_cast<const MediumLayered &>(m), L, sp, kind, dr);
 }
@@ -1275,6 +1379,67 @@ __device__ __forceinline__ void split_at_plane(const MediumLayered &med, Lane<P>
     }
 }
 
+// Boundary split at a tilted or height-field boundary (boundary shapes beyond the plane, the
+// paragraph after Fig. 1), in FP64 for both policies: the local normal (-dzb/dx, -dzb/dy, 1)
+// / |...| turned toward the incident side, both layers' indices at the point, Snell and
+// Fresnel as at a plane; the reflected ray continues, the refracted one is cast into the other
+// layer.
+template <class P>
+__device__ __forceinline__ void split_at_surface(const MediumSurfaces &med, Lane<P> &L,
+                                                 const StepParams<P> &sp, const Sinks &sk, int ev)
+{
+    const int k = (ev == EV_TOP) ? L.layer : L.layer + 1;
+    const int other = (ev == EV_TOP) ? L.layer - 1 : L.layer + 1;
+    double bx, by;
+    if constexpr (P::kFF) {
+        // FP32-mixed landing, completed as at a plane (land_correction): the end point sat
+        // L.ga above or below the surface before it was put on it vertically; the ray is taken
+        // back along itself by u = g / (d/ds of z - zb) = g / (t_z - bx t_x - by t_y), to first
+        // order, and put back on the surface at its new (x, y)
+        const double x0 = P::get(L.r, 0), y0 = P::get(L.r, 1);
+        surf_depth(med, k, x0, y0, &bx, &by);
+        const double t0[3] = {P::get(L.t, 0), P::get(L.t, 1), P::get(L.t, 2)};
+        const double D = t0[2] - bx * t0[0] - by * t0[1];
+        const double u = (double)L.ga / D;
+        if (fabs(u) <= 0.1) {
+            double n, dndz;
+            layer_eval_d(med, L.layer, P::get(L.r, 2), n, dndz);
+            const double kap = dndz / n;
+            const double x1 = x0 - u * t0[0], y1 = y0 - u * t0[1];
+            P::set(L.r, 0, x1);
+            P::set(L.r, 1, y1);
+            P::set(L.r, 2, surf_depth(med, k, x1, y1, &bx, &by));
+            P::set(L.t, 0, t0[0] + u * kap * t0[2] * t0[0]);
+            P::set(L.t, 1, t0[1] + u * kap * t0[2] * t0[1]);
+            P::set(L.t, 2, t0[2] - u * kap * (1.0 - t0[2] * t0[2]));
+            P::sadd(L.s, (float)-u);
+            P::sadd(L.T, (float)(-u * n * kInvC0));
+        }
+    }
+    const double r[3] = {P::get(L.r, 0), P::get(L.r, 1), P::get(L.r, 2)};
+    surf_depth(med, k, r[0], r[1], &bx, &by);
+    const double q = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by)), 1.0));
+    const double sg = (ev == EV_TOP) ? 1.0 : -1.0;
+    const double nrm[3] = {__ddiv_rn(-sg * bx, q), __ddiv_rn(-sg * by, q), __ddiv_rn(sg, q)};
+    double n1, n2, dd;
+    layer_eval_d(med, L.layer, r[2], n1, dd);
+    layer_eval_d(med, other, r[2], n2, dd);
+    double t[3] = {P::get(L.t, 0), P::get(L.t, 1), P::get(L.t, 2)};
+    double t_refl[3], t_refr[3], rr, tau;
+    const bool tir = split_dirs(t, nrm, n1, n2, sp.polarization, t_refl, t_refr, rr, tau);
+    const double amp = L.A * tau;
+    const bool weak = sp.use_min_amp && fabs(amp) < sp.min_amp * fabs(L.A0);
+    if (!tir && L.gen < sp.max_generation && !weak) {
+        const unsigned long long id = atomicAdd(&sk.ctrl->out_count, 1ull);
+        atomicAdd(&sk.ctrl->n_secondary, 1ull);
+        queue_secondary<P>(sk, L, id, other, amp, t_refr,
+                           med.L[other].absorb ? RP_ST_TRANSMITTED : RP_ST_ALIVE);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) P::set(L.t, a, t_refl[a]);
+    L.A *= rr;
+}
+
 // The landing point r + dr put radially onto sphere S (the FP64 reference's operations).
 template <class P>
 __device__ __forceinline__ void sphere_snap(const SphereB &S, const typename P::V &r,
@@ -1344,10 +1509,26 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
     typedef typename P::R R;
     R dr[3] = {dr_in[0], dr_in[1], dr_in[2]};
     // landing: move the candidate onto the plane by adjusting the increment
+    bool on_surface = false;  // landing on a tilted or height-field boundary
     if (ev == EV_TOP || ev == EV_BOTTOM) {
+        if constexpr (has_surfaces_v<M>) {
+            const int k = (ev == EV_TOP) ? L.layer : L.layer + 1;
+            if (surf_on(med, k)) {
+                on_surface = true;
+                const double zs = surf_depth(med, k, P::get(L.r, 0) + (double)dr[0],
+                                             P::get(L.r, 1) + (double)dr[1], nullptr, nullptr);
+                if constexpr (P::kFF)  // landing residual, for the correction at the split
+                    L.ga = (R)((P::get(L.r, 2) + (double)dr[2]) - zs);
+                dr[2] = (R)(zs - P::get(L.r, 2));
+            }
+        }
         if constexpr (is_layered_v<M>) {
-            const PlaneC &pl = (ev == EV_TOP) ? L.lc.top : L.lc.bot;
-            dr[2] = dr[2] - P::rel(L.r, 2, dr[2], pl);
+            if (!on_surface) {
+                const PlaneC &pl = (ev == EV_TOP) ? L.lc.top : L.lc.bot;
+                const R g = P::rel(L.r, 2, dr[2], pl);
+                if constexpr (P::kFF) L.ga = g;  // landing residual, for land_correction
+                dr[2] = dr[2] - g;
+            }
         }
     } else if (ev == EV_STOP) {
         const R off = stop_rel(L, sp, dr);
@@ -1379,7 +1560,13 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
         P::add(L.t, a, dt[a]);
     }
     if (ev == EV_TOP || ev == EV_BOTTOM) {
-        if constexpr (is_layered_v<M>) {
+        if constexpr (has_surfaces_v<M>) {
+            if (on_surface)  // put on the surface vertically, at the landing point's (x, y)
+                P::set(L.r, 2, surf_depth(med, (ev == EV_TOP) ? L.layer : L.layer + 1,
+                                          P::get(L.r, 0), P::get(L.r, 1), nullptr, nullptr));
+            else
+                P::snap(L.r, 2, (ev == EV_TOP) ? L.lc.top : L.lc.bot);
+        } else if constexpr (is_layered_v<M>) {
             P::snap(L.r, 2, (ev == EV_TOP) ? L.lc.top : L.lc.bot);
         }
     } else if (ev == EV_STOP) {
@@ -1442,6 +1629,37 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
     return false;
 }
 
+// FP32-mixed landing on a plane, completed in the service phase before the split.  The landing
+// search stops once the step's end is within eps_b (2e-6 m) of the plane, offset g along the
+// normal (kept in L.ga by commit), and commit then puts the end onto the plane along the normal
+// alone; that leaves an along-track error of u = g / t_z, a tenth of a millimetre per
+// reflection at grazing incidence (t_z ~ 0.01), where FP64 lands within 1e-9 m.  Here the ray
+// is taken back along itself by u, to first order: position r - u t (on the plane, as the
+// normal's part of u t is g), direction t - u t' with the ray equation's t' = k (e_z - t_z t),
+// k = (dn/dz) / n on the ray's side of the plane (host-evaluated per plane, like n), arc
+// length s - u and travel time T - u n / c0.  |u| is capped at 0.1 m, where the neglected
+// terms (u^2 times the ray's curvature) are ~1e-8 m.
+template <class P>
+__device__ __forceinline__ void land_correction(const MediumLayered &med, Lane<P> &L)
+{
+    if constexpr (P::kFF) {
+        const float tz = L.t.hi[2] + L.t.lo[2];
+        const float u = __fdividef(L.ga, tz);  // a correction term: 2 ulp suffice
+        if (!(fabsf(u) <= 0.1f)) return;
+        const int pk = (L.pend == EV_TOP) ? L.layer : L.layer + 1;
+        const float n1 = (L.pend == EV_TOP) ? med.n_below_f[pk] : med.n_above_f[pk];
+        const float k = (L.pend == EV_TOP) ? med.kap_below_f[pk] : med.kap_above_f[pk];
+        const float tx = L.t.hi[0], ty = L.t.hi[1];
+        P::add(L.r, 0, -u * tx);
+        P::add(L.r, 1, -u * ty);
+        P::add(L.t, 0, u * k * tz * tx);
+        P::add(L.t, 1, u * k * tz * ty);
+        P::add(L.t, 2, -u * k * (1.0f - tz * tz));
+        P::sadd(L.s, -u);
+        P::sadd(L.T, -u * n1 * (float)kInvC0);
+    }
+}
+
 // Boundary split of a ray parked on a plane by commit (Sec. 2, boundary module), followed by
 // the break conditions that the reference checks after a split.  Returns true if the ray
 // finished.
@@ -1450,6 +1668,7 @@ __device__ __forceinline__ bool finish_split(const MediumLayered &med, Lane<P> &
                                              const StepParams<P> &sp, const Sinks &sk)
 {
     typedef typename P::R R;
+    land_correction<P>(med, L);
     split_at_plane<P>(med, L, sp, sk, L.pend);
     ++L.n_refl;
     L.pend = 0;
@@ -1466,10 +1685,33 @@ __device__ __forceinline__ bool finish_split(const MediumSpheres &med, Lane<P> &
                                              const StepParams<P> &sp, const Sinks &sk)
 {
     typedef typename P::R R;
-    if (L.pend >= EV_SPH)
+    if (L.pend >= EV_SPH) {
         split_at_sphere<P>(med, L, sp, sk, L.pend - EV_SPH);
-    else
+    } else {
+        land_correction<P>(med, L);
         split_at_plane<P>(med, L, sp, sk, L.pend);
+    }
+    ++L.n_refl;
+    L.pend = 0;
+    if (sp.use_max_time && P::sdiff(L.T, sp.mt) >= R(0))
+        L.status = RP_ST_MAX_TIME;
+    else if (sp.use_min_amp && fabs(L.A) < sp.min_amp * fabs(L.A0))
+        L.status = RP_ST_MIN_AMP;
+    if (L.status != RP_ST_ALIVE) return true;
+    set_trial(L, sp);
+    return false;
+}
+template <class P>
+__device__ __forceinline__ bool finish_split(const MediumSurfaces &med, Lane<P> &L,
+                                             const StepParams<P> &sp, const Sinks &sk)
+{
+    typedef typename P::R R;
+    if (surf_on(med, (L.pend == EV_TOP) ? L.layer : L.layer + 1)) {
+        split_at_surface<P>(med, L, sp, sk, L.pend);
+    } else {
+        land_correction<P>(med, L);
+        split_at_plane<P>(med, L, sp, sk, L.pend);
+    }
     ++L.n_refl;
     L.pend = 0;
     if (sp.use_max_time && P::sdiff(L.T, sp.mt) >= R(0))

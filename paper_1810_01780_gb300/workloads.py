@@ -16,6 +16,8 @@ workloads:
   ``spheres``   curved boundaries: two spherical inclusions in the ice, 1,048,576 rays
   ``fig1``      the paper's Fig. 1 example (firn layer over exponential ice, 5 us, A/A0 cut) as
                 a fan of 1,048,576 rays
+  ``surfaces``  non-horizontal boundaries: a tilted, rough ice surface (height field) and a
+                tilted internal boundary, 1,048,576 rays
 
 Conventions: z = depth (positive downward), angles from +z, positions in metres; ray arrays
 are SoA with shape (3, n).
@@ -81,6 +83,23 @@ def ice_with_inclusions(n_air: float = N_AIR) -> dict:
     return m
 
 
+def rough_ice(n_air: float = N_AIR, seed: int = 8) -> dict:
+    """Non-horizontal boundaries: the two-layer ice of ``two_layer_ice`` with its surface a
+    plane tilted by 2 degrees (about the y axis) carrying a height field of seeded
+    undulations -- a Gaussian random field of 0.3 m standard deviation and 8 m correlation
+    length on 256 x 256 nodes at 2 m spacing around the origin -- and its internal boundary at
+    100 m a plane tilted by 1 degree about the x axis."""
+    m = two_layer_ice()
+    h = gaussian_random_field((1, 256, 256), 2.0, 0.3, 8.0, seed)[0].astype(np.float64)
+    a, b = math.radians(2.0), math.radians(1.0)
+    m["surfaces"] = [
+        dict(layer=1, normal=(math.sin(a), 0.0, math.cos(a)), height=h,
+             origin=(-255.0, -255.0), spacing=(2.0, 2.0)),
+        dict(layer=2, normal=(0.0, -math.sin(b), math.cos(b))),
+    ]
+    return m
+
+
 def gaussian_random_field(shape, spacing, sigma, corr_len, seed) -> np.ndarray:
     """Seeded stationary Gaussian field with covariance sigma^2 exp(-r^2 / (2 l^2)).
 
@@ -139,6 +158,18 @@ def isotropic_dirs(rng, n):
     ph = rng.uniform(0.0, 2.0 * math.pi, n)
     sz = np.sqrt(np.maximum(0.0, 1.0 - cz * cz))
     return np.stack([sz * np.cos(ph), sz * np.sin(ph), cz])
+
+
+def tilted_dirs(d, angle: float, seed: int):
+    """The directions d (3, n) each rotated by `angle` rad about a seeded random axis
+    perpendicular to it: the perturbed launch directions of the conditioning test (a ray whose
+    result moves far under a tiny tilt is ill-conditioned)."""
+    rng = np.random.default_rng(seed)
+    d = d / np.linalg.norm(d, axis=0)
+    a = rng.standard_normal(d.shape)
+    a -= (a * d).sum(0) * d
+    a /= np.linalg.norm(a, axis=0)
+    return np.cos(angle) * d + np.sin(angle) * a
 
 
 def isotropic_sources(n: int, seed: int, depth=(50.0, 1500.0), xy=400.0):
@@ -245,6 +276,19 @@ def spheres(n=1_048_576, seed=7):
     pos = np.stack([rng.uniform(-60.0, 210.0, n), rng.uniform(-60.0, 60.0, n),
                     rng.uniform(250.0, 550.0, n)])
     return dict(name="spheres", medium=ice_with_inclusions(),
+                params=dict(TRACE_DEFAULTS, max_path=2000.0, min_amp=0.05, max_generation=3,
+                            max_steps=1000),
+                rays=(pos, isotropic_dirs(rng, n), np.ones(n)), receivers=None)
+
+
+def surfaces(n=1_048_576, seed=9):
+    """Rays around the tilted, rough ice surface and the tilted internal boundary of
+    ``rough_ice``: sources x, y uniform in +-200 m, depth 20..300 m, directions uniform on the
+    sphere; 2 km paths, A/A0 < 0.05, generations <= 3, at most 1000 attempted steps."""
+    rng = np.random.default_rng(seed)
+    pos = np.stack([rng.uniform(-200.0, 200.0, n), rng.uniform(-200.0, 200.0, n),
+                    rng.uniform(20.0, 300.0, n)])
+    return dict(name="surfaces", medium=rough_ice(),
                 params=dict(TRACE_DEFAULTS, max_path=2000.0, min_amp=0.05, max_generation=3,
                             max_steps=1000),
                 rays=(pos, isotropic_dirs(rng, n), np.ones(n)), receivers=None)

@@ -10,12 +10,13 @@ import pytest
 from paper_1810_01780_gb300 import _abi as A
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-PAIRS = [("rp_layer", A.Layer), ("rp_sphere", A.Sphere), ("rp_medium_desc", A.MediumDesc),
+PAIRS = [("rp_layer", A.Layer), ("rp_sphere", A.Sphere), ("rp_surface", A.Surface),
+         ("rp_medium_desc", A.MediumDesc),
          ("rp_rays", A.Rays), ("rp_receivers", A.Receivers), ("rp_trace_params", A.TraceParams),
          ("rp_ray_out", A.RayOut), ("rp_hits", A.Hits), ("rp_stats", A.Stats),
          ("rp_path_params", A.PathParams), ("rp_solutions", A.Solutions),
          ("rp_train_params", A.TrainParams), ("rp_surrogate_params", A.SurrogateParams),
-         ("rp_surrogate_stats", A.SurrogateStats)]
+         ("rp_surrogate_stats", A.SurrogateStats), ("rp_peaks", A.Peaks)]
 
 
 def _c_layout(tmp_path):

@@ -71,7 +71,8 @@ class Sampler:
         pass
 
     def summary(self):
-        first = Sampler.calls == 1 and int(os.environ.get("RANK", "0")) == THROTTLED_RANK
+        # sampled regions: the peak microkernels, then the timed region (throttled once)
+        first = Sampler.calls == 2 and int(os.environ.get("RANK", "0")) == THROTTLED_RANK
         r = ["hw_slowdown"] if first else ["sw_power_cap"]
         return {"sm_mhz": 2000.0, "sm_max_mhz": 2070.0, "reasons": r, "samples": 5}
 
@@ -108,9 +109,15 @@ pkg.PreparedRays = Rays
 pkg.make_params = lambda p, prec: (p, prec)
 pkg.TraceBuffers = Buffers
 pkg.trace_into = lambda med, rays, prm, buf, stream=None: Stats(rays.n)
+import paper_1810_01780_gb300.api as api
+
+api.trace_into = pkg.trace_into  # the tuner's calls
+pkg.measure_peaks = lambda stream=None: {"fp32_tflops": 70.0, "fp64_tflops": 1.2, "l2_gbs": 2e4,
+                                         "fp32_ms": 9.0, "fp64_ms": 9.0, "l2_ms": 9.0,
+                                         "l2_buffer_bytes": 33554432.0}
 
 off = dict(no_fp64=True, no_grid=True, no_paths=True, no_surrogate=True, no_fig1=True,
-           no_spheres=True, no_cpu_baseline=True)
+           no_spheres=True, no_surfaces=True, no_cpu_baseline=True)
 bench.run_gpu(argparse.Namespace(gpus=int(os.environ.get("WORLD_SIZE", "1")), steps=2, warmup=3,
                                  impl="ours", paths_steps=1,
                                  rays=4096, sur_train=0, sur_queries=0, sur_check=0,
@@ -165,6 +172,11 @@ def test_gpu_arm_line_with_fakes():
     r = d["roofline"]
     assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= r.keys()
     assert r["bound"] == "alu" and abs(r["frac"] - r["achieved"] / r["peak"]) <= 1e-12
+    # the peak is the measured FP32 rate (sampled at 2000 MHz, as the run) at the run's clock
+    assert d["measured_peaks"]["fp32_tflops"] == 70.0 and abs(r["peak"] - 70.0) <= 1e-9
+    assert d["modes"]["fp32_mixed"]["roofline"] == r
+    k = d["tuned_knobs"]
+    assert k["candidates"] == 27 and k["block"] in (64, 128, 256) and k["service_idle"] > 0
     # 364 flops per attempted step (335 per primary) over the 9 ms kernel time
     assert abs(r["achieved"] - 364 * 335 * 4096 / 9e-3 / 1e12) <= 1e-9 * r["achieved"]
     assert r["traffic"] is None  # measured for the full-size workload only

@@ -21,6 +21,11 @@ def test_trace_params_fields_and_defaults():
     assert d.max_time == 0.0 and d.min_amp == 0.0 and d.max_steps == 1_000_000
     assert d.precision == A.PRECISION["fp32"] and d.polarization == A.POLARIZATION["s"]
     assert d.rhs_form == A.RHS_FORM["projected"]
+    # scheduling knobs: 0 (the library's defaults) unless given
+    assert (d.service_idle, d.flush_min, d.block, d.blocks_per_sm) == (0, 0, 0, 0)
+    k = api.make_params(dict(W.TRACE_DEFAULTS, service_idle=9, flush_min=3, block=64,
+                             blocks_per_sm=2), "fp32")
+    assert (k.service_idle, k.flush_min, k.block, k.blocks_per_sm) == (9, 3, 64, 2)
     with pytest.raises(KeyError):
         api.make_params(W.TRACE_DEFAULTS, "fp16")
 

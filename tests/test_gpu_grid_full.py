@@ -1,17 +1,18 @@
 """Gridded medium at full size: 256 x 256 x 512 FP32 grid (4 m, exponential profile + Gaussian
 perturbations sigma 1e-3, correlation 20 m), 4,194,304 rays from 16 sources, tol 1e-5.
 
-- FP32-mixed, all rays in one call: every ray ends with a valid status; 40 sampled rays
+- FP32-mixed, all rays in one call: every ray ends with a valid status; 512 sampled rays
   against the FP64 oracle: same status, and within 1 mm / 0.01 ns unless the oracle's own
-  result moves by more than that under a 1e-7 rad launch tilt (ill-conditioned ray).
+  result moves by more than that under a 1e-7 rad launch tilt (ill-conditioned ray; at most
+  10 % of the sample).
 - FP64 path on 4096 rays against the oracle: 1e-9 relative for rays with identical step
   sequences (the grid samples are bit-identical on both sides: central differences in FP64
-  rounded to FP32)."""
+  rounded to FP32), 10 tol s for the others."""
 import numpy as np
 import pytest
 
 import oracle
-from parity import errors, gpu_rays, match, oracle_rays, same_steps
+from parity import check_fp64, check_within, gpu_rays, oracle_rays, sensitive_keys, tilt
 from paper_1810_01780_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -32,16 +33,11 @@ def setup():
     return rp, cfg, rp.Medium(cfg["medium"]), oracle.OracleMedium(cfg["medium"])
 
 
-def _tilt(d, angle, seed):
-    rng = np.random.default_rng(seed)
-    d = d / np.linalg.norm(d, axis=0)
-    a = rng.standard_normal(d.shape)
-    a -= (a * d).sum(0) * d
-    a /= np.linalg.norm(a, axis=0)
-    return np.cos(angle) * d + np.sin(angle) * a
-
-
 def test_grid_full_fp32_sampled(setup):
+    """FP32-mixed, all 4,194,304 rays in one call; 512 sampled rays against the FP64 oracle,
+    ray by ray: every ray whose oracle result does not move by more than 1 mm / 0.01 ns (or
+    change status) under a 1e-7 rad launch tilt has the oracle's status and is within 1 mm and
+    0.01 ns; at most 10 % of the sample is excused as ill-conditioned."""
     rp, cfg, med, omed = setup
     pos, d, a = cfg["rays"]
     n = pos.shape[1]
@@ -50,34 +46,29 @@ def test_grid_full_fp32_sampled(setup):
     assert len(g["path"]) == n
     assert np.all(np.isin(g["status"], [1, 4]))  # path limit or left the grid
     rng = np.random.default_rng(11)
-    idx = np.sort(rng.choice(n, 40, replace=False))
-    sub = W.subsample(cfg["rays"], idx)
-    ref, _ = oracle.trace(omed, cfg["params"], *sub)
-    tilt, _ = oracle.trace(omed, cfg["params"], sub[0], _tilt(sub[1], 1e-7, 3), sub[2])
-    ok_status = g["status"][idx] == ref["status"]
-    assert ok_status.mean() >= 0.95
-    dp = np.linalg.norm(g["pos"][idx] - ref["pos"], axis=1)
-    dT = np.abs(g["time"][idx] - ref["time"])
-    sens = (np.linalg.norm(tilt["pos"] - ref["pos"], axis=1) > 1e-3) | (
-        np.abs(tilt["time"] - ref["time"]) > 1e-11) | (tilt["status"] != ref["status"])
-    good = ok_status & ~sens
-    print("grid fp32 vs oracle: %d sampled, %d ill-conditioned, p50 |dr| %.2e m" % (
-        len(idx), sens.sum(), np.median(dp)))
-    assert good.sum() >= 20
-    assert np.all(dp[good] <= 1e-3) and np.all(dT[good] <= 1e-11)
+    idx = np.sort(rng.choice(n, 512, replace=False))
+    sp, sd, sa = W.subsample(cfg["rays"], idx)
+    o = oracle_rays(oracle.trace(omed, cfg["params"], sp, sd, sa)[0])
+    oT = oracle_rays(oracle.trace(omed, cfg["params"], sp, tilt(sd, 1e-7, 3), sa)[0])
+    sub = {k: v[idx] for k, v in g.items()}
+    sub["parent"] = np.full(len(idx), -1, dtype=np.int64)  # primaries only (no boundaries)
+    sens = sensitive_keys(o, oT)
+    n_checked, n_excused = check_within(sub, o, sens)
+    dp = np.linalg.norm(sub["pos"] - o["pos"], axis=1)
+    ok = np.array([(i,) not in sens for i in range(len(idx))])
+    print("grid fp32 vs oracle: %d sampled, %d checked, %d ill-conditioned, p50/max |dr| of the "
+          "checked %.2e/%.2e m" % (len(idx), n_checked, n_excused, np.median(dp[ok]),
+                                   dp[ok].max()))
+    assert n_excused <= 0.10 * len(idx)
 
 
 def test_grid_full_fp64_subset(setup):
+    """FP64 on 4,096 rays of the workload against the oracle: 1e-9 relative for rays whose step
+    sequence is identical (at least 90 %), within 10 tol s for the rest (an accept/reject
+    decision flipped on a last-bit difference), same status for all."""
     rp, cfg, med, omed = setup
     sub = W.subsample(cfg["rays"], np.arange(0, 4194304, 1024))
     res = rp.trace(med, *sub, params=cfg["params"], precision="fp64")
     ref, _ = oracle.trace(omed, cfg["params"], *sub)
-    g, o = gpu_rays(res), oracle_rays(ref)
-    gi, oi, a, b = match(g, o)
-    assert not a and not b
-    same = same_steps(g, o, gi, oi) & (g["status"][gi] == o["status"][oi])
-    assert same.mean() >= 0.9
-    dp, dd, ds, dT, dA = errors(g, o, gi, oi)
-    s = o["path"][oi]
-    assert np.all(dp[same] <= 1e-9 * (s[same] + 1.0))
-    assert np.all(dT[same] <= 1e-9 * o["time"][oi][same] + 1e-18)
+    frac = check_fp64(gpu_rays(res), oracle_rays(ref), cfg["params"]["tol"], min_tier1=0.9)
+    print("grid fp64 vs oracle: tier-1 fraction %.4f" % frac)

@@ -165,3 +165,34 @@ def test_fused_inference_agrees_with_training_forward(rp):
     L_fused, _ = mlp.loss_and_grad_out(out, y.astype(np.float64), t.astype(np.float64).reshape(-1, 2, 5))
     L_train, _ = net.loss_grad(X, y, t)
     assert abs(L_fused - L_train) <= 2e-3 * abs(L_train), (L_fused, L_train)
+
+
+def test_a_wait_that_runs_out_returns_an_error_and_leaves_the_context_usable(rp):
+    """The tensor-core kernels bound every wait for their own bulk copies and matrix products.
+    With the bound set to one SM cycle the first wait gives up before the 128 KB weight copy can
+    land: the CTA records it, drains the work it issued (with the default bound), frees its
+    tensor memory and returns, and the call returns RP_ERR_TIMEOUT -- no trap, no hang.  With
+    the default bound back, the same calls give the results of a fresh network."""
+    import numpy as np
+
+    from paper_1810_01780_gb300 import _abi as A
+
+    net = rp.Surrogate(seed=3)
+    X = np.random.default_rng(1).uniform(-1, 1, (4096, 3)).astype(np.float32)
+    y = np.zeros((4096, 2), np.float32)
+    t = np.zeros((4096, 10), np.float32)
+    ref = net.forward(X).cpu().numpy()
+    ref_loss, _ = net.loss_grad(X, y, t)
+    net.set_wait_limit(1)
+    with pytest.raises(A.RPError) as e:
+        net.forward(X)
+    assert e.value.code == -6 and "gave up" in str(e.value)
+    with pytest.raises(A.RPError) as e:
+        net.loss_grad(X, y, t)
+    assert e.value.code == -6
+    net.set_wait_limit(0)
+    np.testing.assert_array_equal(net.forward(X).cpu().numpy(), ref)
+    loss, _ = net.loss_grad(X, y, t)
+    assert abs(loss - ref_loss) <= 1e-9 * abs(ref_loss)
+    with pytest.raises(A.RPError):
+        net.set_wait_limit(-1)

@@ -4,14 +4,16 @@ Tolerances (FP64 path): rays whose step sequence is identical to the oracle's (s
 and rejected counts) agree to 1e-9 relative: |dr| <= 1e-9 (s + 1 m), |ds| <= 1e-9 s,
 |dT| <= 1e-9 T, |dt|, |dA| <= 1e-9.  Rays whose adaptive step sequence took a different
 branch (an accept/reject decision that flipped on a last-bit difference) must still agree
-within the integration tolerance, 10 tol s.  FP32-mixed path vs FP64 path: 1 mm in position
-and 0.01 ns in travel time over paths up to 3 km."""
+within the integration tolerance, 10 tol s.  FP32-mixed path vs FP64 (GPU or oracle): every
+ray within 1 mm in position and 0.01 ns in travel time over paths up to 3 km, with the same
+status, unless the FP64 result of the ray or of an ancestor is itself ill-conditioned (moves
+by more than that under a 1e-7 rad launch tilt)."""
 import numpy as np
 import pytest
 
 import oracle
-from parity import (check_fp64, errors, gpu_rays, match, oracle_rays, same_steps,
-                    subtree_of_roots, tilt)
+from parity import (check_fp64, check_within, errors, gpu_rays, match, oracle_rays,
+                    same_steps, sensitive_keys, subset_by_roots, tilt)
 from paper_1810_01780_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -88,49 +90,30 @@ def test_batched_subset_fp64_rays_and_hits(rp):
 
 
 def test_fp32_mixed_vs_fp64(rp):
-    """FP32-mixed against FP64 on 20,000 primaries of the batched workload.
+    """FP32-mixed against FP64 on 20,000 primaries of the batched workload, ray by ray.
 
-    Rays whose FP64 result itself moves by more than 1 mm / 0.01 ns when the launch direction
-    is tilted by 1e-7 rad (grazing incidence, critical angles: the problem, not the
-    arithmetic, is ill-conditioned there) are counted separately; every other ray must be
-    within 1 mm / 0.01 ns."""
+    A ray (or a ray whose ancestor) whose FP64 result itself moves by more than 1 mm / 0.01 ns,
+    changes status or disappears when every launch direction is tilted by 1e-7 rad (grazing
+    incidence, critical angles, an amplitude at its threshold: the problem, not the
+    arithmetic, is ill-conditioned there) is excused; every other ray must exist in both runs
+    with the same status and generation, within 1 mm and 0.01 ns.  At most 1 % of the rays are
+    ill-conditioned, at most 2.5 % excused together with their secondaries."""
     cfg = W.batched()
     pos, d, a = W.subsample(cfg["rays"], np.arange(20000))
     g64 = gpu_rays(_run(rp, cfg["medium"], cfg["params"], (pos, d, a), precision="fp64"))
     g32 = gpu_rays(_run(rp, cfg["medium"], cfg["params"], (pos, d, a), precision="fp32"))
     gpt = gpu_rays(_run(rp, cfg["medium"], cfg["params"], (pos, tilt(d, 1e-7, 9), a),
                         precision="fp64"))
-    gi, oi, only32, only64 = match(g32, g64)
-    n = max(len(g32["path"]), len(g64["path"]))
-    assert len(only32) + len(only64) <= 0.002 * n
-    ok = g32["status"][gi] == g64["status"][oi]
-    assert ok.mean() > 0.998
-    gi, oi = gi[ok], oi[ok]
+    sens = sensitive_keys(g64, gpt)
+    n_checked, n_excused = check_within(g32, g64, sens)
+    n = len(g64["path"])
+    gi, oi, _, _ = match(g32, g64)
     dp, dd, ds, dT, dA = errors(g32, g64, gi, oi)
-    # sensitivity of the FP64 result to a 1e-7 rad launch tilt
-    pi, qi, _, _ = match(gpt, g64)
-    sens = np.ones(len(g64["path"]), dtype=bool)
-    sp, _, _, sT, _ = errors(gpt, g64, pi, qi)
-    same_status = gpt["status"][pi] == g64["status"][qi]
-    sens[qi] = ~same_status | (sp > 1e-3) | (sT > 1e-11)
-    s_ok = ~sens[oi]
-    good = (dp <= 1e-3) & (dT <= 1e-11)
-    print("fp32 vs fp64: %d rays, p50/p99/max |dr| %.2e/%.2e/%.2e m, p99 |dT| %.2e s; "
-          "within 1 mm / 0.01 ns: all %.5f, well-conditioned %.5f (%.4f of rays sensitive)" % (
-              len(gi), np.median(dp), np.quantile(dp, 0.99), dp.max(), np.quantile(dT, 0.99),
-              good.mean(), good[s_ok].mean(), 1 - s_ok.mean()))
-    bad = ~good & s_ok
-    if bad.any():
-        j = np.nonzero(bad)[0][:10]
-        for k in j:
-            print("  bad: gen %d refl %d acc %d/%d rej %d/%d path %.1f |dr| %.3e |dT| %.3e" % (
-                g64["generation"][oi[k]], g64["n_refl"][oi[k]], g32["n_acc"][gi[k]],
-                g64["n_acc"][oi[k]], g32["n_rej"][gi[k]], g64["n_rej"][oi[k]],
-                g64["path"][oi[k]], dp[k], dT[k]))
-    assert np.quantile(dp, 0.99) <= 1e-3
-    assert np.quantile(dT, 0.99) <= 1e-11
-    assert 1 - s_ok.mean() <= 0.05
-    assert good[s_ok].mean() >= 0.999
+    print("fp32 vs fp64: %d rays checked, %d ill-conditioned (%.4f), %d excused with their "
+          "secondaries (%.4f); p50/p99 |dr| %.2e/%.2e m, p99 |dT| %.2e s" % (
+              n_checked, len(sens), len(sens) / n, n_excused, n_excused / n, np.median(dp),
+              np.quantile(dp, 0.99), np.quantile(dT, 0.99)))
+    assert len(sens) <= 0.01 * n and n_excused <= 0.025 * n
 
 
 def test_grid_medium_fp64_and_fp32(rp):
@@ -216,8 +199,12 @@ def test_edge_cases(rp):
 
 
 def test_full_size_batched_sampled(rp):
-    """The full 1,048,576-ray workload in the benchmark's configuration (FP32-mixed): sampled
-    primaries and their secondaries against the oracle."""
+    """The full 1,048,576-ray workload in the benchmark's configuration (FP32-mixed, receivers,
+    one call): 4,096 sampled primaries and all their secondaries against the FP64 oracle, ray by
+    ray.  Every ray not excused as ill-conditioned by the oracle's own 1e-7 rad tilt test (see
+    test_fp32_mixed_vs_fp64) has the oracle's status and generation and is within 1 mm and
+    0.01 ns; at most 1 % of the oracle's rays are ill-conditioned, and at most 2.5 % are
+    excused together with the secondaries of ill-conditioned rays."""
     cfg = W.batched()
     res = _run(rp, cfg["medium"], cfg["params"], cfg["rays"], receivers=cfg["receivers"],
                precision="fp32")
@@ -225,46 +212,36 @@ def test_full_size_batched_sampled(rp):
     n = cfg["rays"][0].shape[1]
     assert np.all(g["status"] != 0)
     rng = np.random.default_rng(123)
-    roots = np.sort(rng.choice(n, 256, replace=False))
-    gsel, groot = subtree_of_roots(g["parent"], roots)
-    ref, _ = oracle.trace(cfg["medium"], cfg["params"], *W.subsample(cfg["rays"], roots))
-    o = oracle_rays(ref)
-    # re-key the GPU subset so that its primaries are numbered like the oracle's
-    remap = {int(r): i for i, r in enumerate(roots)}
-    sub = {k: v[gsel] for k, v in g.items()}
-    idx = {int(j): i for i, j in enumerate(gsel)}
-    sub["parent"] = np.array([-1 if p < 0 else idx[int(p)] for p in sub["parent"]])
-    order = np.argsort([remap[int(groot[j])] if g["parent"][j] < 0 else 10**9 + j for j in gsel],
-                       kind="stable")
-    # primaries first in root order, then secondaries in their original (creation) order
-    perm = {int(old): new for new, old in enumerate(order)}
-    sub = {k: v[order] for k, v in sub.items()}
-    sub["parent"] = np.array([-1 if p < 0 else perm[int(p)] for p in sub["parent"]])
-    gi, oi, a, b = match(sub, o)
-    assert len(a) + len(b) <= 2
-    ok = sub["status"][gi] == o["status"][oi]
-    assert ok.mean() >= 0.99
-    dp, dd, ds, dT, dA = errors(sub, o, gi[ok], oi[ok])
-    assert np.quantile(dp, 0.99) <= 1e-3 and np.quantile(dT, 0.99) <= 1e-11
+    roots = np.sort(rng.choice(n, 4096, replace=False))
+    pos, d, a = W.subsample(cfg["rays"], roots)
+    ref, _ = oracle.trace(cfg["medium"], cfg["params"], pos, d, a)
+    refT, _ = oracle.trace(cfg["medium"], cfg["params"], pos, tilt(d, 1e-7, 9), a)
+    o, oT = oracle_rays(ref), oracle_rays(refT)
+    sub, _ = subset_by_roots(g, roots)
+    sens = sensitive_keys(o, oT)
+    n_checked, n_excused = check_within(sub, o, sens)
+    n = len(o["path"])
+    print("full size fp32 vs oracle: %d rays checked, %d ill-conditioned (%.4f), %d excused with "
+          "their secondaries (%.4f)" % (n_checked, len(sens), len(sens) / n, n_excused,
+                                        n_excused / n))
+    assert len(sens) <= 0.01 * n and n_excused <= 0.025 * n
+    assert n_checked >= 6000 and (o["generation"] >= 2).any()
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_scheduling_knobs_do_not_change_records(rp, monkeypatch, precision):
-    """RP_SERVICE_IDLE(_F64) and RP_FLUSH_MIN change when lanes are served and which thread
-    traces a secondary, never a ray's arithmetic: the same rays (matched by their split tree)
-    with bit-identical records at extreme settings."""
+def test_scheduling_knobs_do_not_change_records(rp, precision):
+    """The scheduling knobs of rp_trace_params (service_idle, flush_min, block, blocks_per_sm)
+    change when lanes are served, which thread traces a secondary and the launch shape, never
+    a ray's arithmetic: the same rays (matched by their split tree) with bit-identical records
+    at extreme settings."""
     cfg = W.batched(n=20_000)
     med = rp.Medium(cfg["medium"])
-    knob = "RP_SERVICE_IDLE" if precision == "fp32" else "RP_SERVICE_IDLE_F64"
     runs = []
-    for idle, flush in ((None, None), ("1", "1"), ("100000", "1000000")):
-        for name, val in ((knob, idle), ("RP_FLUSH_MIN", flush)):
-            if val is None:
-                monkeypatch.delenv(name, raising=False)
-            else:
-                monkeypatch.setenv(name, val)
-        res = rp.trace(med, *cfg["rays"], params=cfg["params"], receivers=cfg["receivers"],
-                       precision=precision)
+    for knobs in ({}, dict(service_idle=1, flush_min=1, block=64),
+                  dict(service_idle=100000, flush_min=1000000, block=256, blocks_per_sm=1),
+                  dict(block=96, blocks_per_sm=3)):
+        res = rp.trace(med, *cfg["rays"], params=dict(cfg["params"], **knobs),
+                       receivers=cfg["receivers"], precision=precision)
         runs.append(gpu_rays(res))
     base = runs[0]
     assert np.any(base["generation"] > 0)

@@ -122,7 +122,9 @@ def _params(**kw):
                                  dict(max_generation=-1), dict(precision=7),
                                  dict(polarization=9), dict(rhs_form=9),
                                  dict(rhs_form=A.RHS_FORM["momentum"],
-                                      precision=A.PRECISION["fp32"])])
+                                      precision=A.PRECISION["fp32"]),
+                                 dict(service_idle=-1), dict(flush_min=-1), dict(block=100),
+                                 dict(block=288), dict(block=-32), dict(blocks_per_sm=-1)])
 def test_rp_trace_refuses_bad_parameters(bad):
     p = _params()
     for k, v in bad.items():

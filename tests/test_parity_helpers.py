@@ -6,7 +6,8 @@ import pytest
 
 import oracle
 from paper_1810_01780_gb300 import workloads as W
-from parity import check_fp64, match, oracle_rays, subtree_of_roots, tilt
+from parity import (check_fp64, check_within, match, oracle_rays, sensitive_keys,
+                    subset_by_roots, subtree_of_roots, tilt, tree_keys)
 
 
 @pytest.fixture(scope="module")
@@ -92,3 +93,62 @@ def test_subtrees_and_tilt(rays):
     t = tilt(d, 1e-3, 5)
     assert np.allclose(np.linalg.norm(t, axis=0), 1.0, atol=1e-12)
     assert np.allclose(np.arccos(np.clip((t * d).sum(0), -1, 1)), 1e-3, rtol=1e-5)
+
+
+def test_subset_by_roots_rekeys_like_an_oracle_run_on_the_roots(rays, oracle_lib):
+    """The subtrees of sampled roots, cut from a run over all primaries (in shuffled order),
+    match an oracle run on those primaries alone, record for record."""
+    o, tol, n = rays
+    g = _shuffled(o, n, 5)
+    roots = np.array([2, 5, 11, 40, 299])
+    sub, take = subset_by_roots(g, roots)
+    cfg = W.batched(n=300, seed=11)
+    ref, _ = oracle.trace(cfg["medium"], cfg["params"], *W.subsample(cfg["rays"], roots))
+    r = oracle_rays(ref)
+    assert len(sub["path"]) == len(r["path"])
+    gi, oi, only_g, only_o = match(sub, r)
+    assert not only_g and not only_o
+    for k in ("pos", "time", "status", "generation", "n_acc"):
+        np.testing.assert_array_equal(sub[k][gi], r[k][oi], err_msg=k)
+
+
+def test_check_within_excuses_only_ill_conditioned_rays(rays):
+    """check_within: identical records pass; a ray moved beyond the tolerance fails unless it
+    or an ancestor is in the ill-conditioned set; a status change and a missing ray likewise."""
+    o, tol, n = rays
+    g = _shuffled(o, n, 6)
+    assert check_within(g, o, set()) == (len(o["path"]), 0)
+    keys = tree_keys(g["parent"], g["seq"])
+    j = int(np.nonzero(g["generation"] == 2)[0][0])
+    parent_key = keys[j][:-1]
+    moved = {k: v.copy() for k, v in g.items()}
+    moved["pos"][j] += np.array([0.0, 2e-3, 0.0])
+    with pytest.raises(AssertionError):
+        check_within(moved, o, set())
+    assert check_within(moved, o, {parent_key})[1] >= 1  # excused through its parent
+    late = {k: v.copy() for k, v in g.items()}
+    late["time"][j] += 2e-11
+    with pytest.raises(AssertionError):
+        check_within(late, o, set())
+    flipped = {k: v.copy() for k, v in g.items()}
+    flipped["status"][j] = 3 if flipped["status"][j] != 3 else 1
+    with pytest.raises(AssertionError):
+        check_within(flipped, o, set())
+    check_within(flipped, o, {keys[j]})
+    keep = np.arange(len(g["path"])) != len(g["path"]) - 1  # drop a last-generation ray
+    gone = {k: v[keep] for k, v in g.items()}
+    lost = keys[len(g["path"]) - 1]
+    with pytest.raises(AssertionError):
+        check_within(gone, o, set())
+    check_within(gone, o, {lost})
+
+
+def test_sensitive_keys_flags_rays_that_move_under_a_tilt(rays):
+    o, tol, n = rays
+    g = _shuffled(o, n, 7)
+    assert sensitive_keys(o, g) == set()
+    keys = tree_keys(g["parent"], g["seq"])
+    h = {k: v.copy() for k, v in g.items()}
+    h["pos"][4] += 5e-3
+    h["status"][9] = 9
+    assert sensitive_keys(o, h) == {keys[4], keys[9]}

@@ -95,3 +95,50 @@ def test_static_scratch_rejects_oversized_input():
     rc = A.lib().rp_trace_static(med.handle, C.byref(big), None, C.byref(rp.make_params(cfg["params"])),
                                  C.byref(buf.out), None, C.byref(st), None)
     assert rc == -1 and "exceed" in A.last_error()
+
+
+def test_static_scratch_at_its_ray_limit():
+    """rp_trace_static with RP_STATIC_MAX_RAYS (2^20) primaries -- the whole batched workload
+    with its 64 receivers, FP32-mixed.  Either every ray and hit equals rp_trace's, or the call
+    returns RP_ERR_OVERFLOW because the fixed queue is too small, with rp_stats holding the
+    queue records needed, the records it had room for and the rays and hits found."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1810_01780_gb300 import build
+
+    build.build()
+    import paper_1810_01780_gb300 as rp
+    from paper_1810_01780_gb300 import _abi as A
+
+    cfg = W.batched()
+    assert cfg["rays"][0].shape[1] == 1 << 20
+    med = rp.Medium(cfg["medium"])
+    rays = rp.PreparedRays(*cfg["rays"], receivers=cfg["receivers"])
+    prm = rp.make_params(cfg["params"], "fp32")
+    ref = rp.TraceBuffers(int(5.5 * rays.n), 1 << 16)
+    st_ref = rp.trace_into(med, rays, prm, ref)
+    buf = rp.TraceBuffers(int(5.5 * rays.n), 1 << 16)
+    st = A.Stats()
+    rc = A.lib().rp_trace_static(med.handle, C.byref(rays.rays), C.byref(rays.rx), C.byref(prm),
+                                 C.byref(buf.out), C.byref(buf.hits), C.byref(st),
+                                 C.c_void_p(int(torch.cuda.current_stream().cuda_stream)))
+    print("rp_trace_static at 2^20 primaries: rc %d, queue needed %d of %d, %d threads, stack "
+          "depth %d; rays %d (rp_trace %d)" % (rc, st.queue_needed, st.queue_capacity, st.threads,
+                                              st.stack_depth, st.rays, st_ref.rays))
+    assert st.threads > 0 and st.stack_depth >= 1 and st.queue_capacity > 0
+    if rc == A.RP_ERR_OVERFLOW:
+        assert st.flags & 4 and st.queue_needed > st.queue_capacity
+        assert st.rays >= rays.n and st.rays <= st_ref.rays
+        return
+    assert rc == A.RP_OK, A.last_error()
+    assert st.rays == st_ref.rays and st.hits == st_ref.hits
+    assert st.queue_needed <= st.queue_capacity
+    n = int(st.rays)
+    g = gpu_rays({"rays": {k: (v[:, :n] if v.dim() == 2 else v[:n]) for k, v in buf.t.items()}})
+    r = gpu_rays({"rays": {k: (v[:, :n] if v.dim() == 2 else v[:n]) for k, v in ref.t.items()}})
+    gi, oi, only_s, only_r = match(g, r)
+    assert not only_s and not only_r
+    for k in ("pos", "dir", "path", "time", "amp", "status", "n_acc", "n_rej"):
+        np.testing.assert_array_equal(g[k][gi], r[k][oi], err_msg=k)
