@@ -379,6 +379,25 @@ def surrogate_leg(rp, W, args, rank, flush):
             k = int(np.argmin(np.abs(tl[i, :tc[i]] - sur["launch"][i, j])))
             errs.append(abs(sur["time"][i, j] - tt[i, k]))
     errs = np.array(errs) if errs else np.zeros(1)
+    # the network on its own, before any refinement trace: predicted existence and launch angle
+    # of the two earliest solutions against the FP64 path finder on the same queries
+    xq, _, _ = rp.encode(q["zs"][:m], q["zr"][:m], q["dist"][:m])
+    pred = net.forward(xq).cpu().numpy().astype(np.float64)
+    two = tc <= 2
+    exist_ok, ang = [], []
+    for k in range(2):
+        p_exist = 1.0 / (1.0 + np.exp(-pred[:, 6 * k]))
+        has = tc > k
+        exist_ok.append(((p_exist > 0.5) == has)[two])
+        both = two & has & (p_exist > 0.5)
+        ang.append(np.abs((pred[both, 6 * k + 1] + 1.0) * (np.pi / 2) - tl[both, k]))
+    ang = np.concatenate(ang) if ang else np.zeros(1)
+    network_alone = {
+        "vs": f"FP64 path finder on the first {m:,} queries with at most two solutions",
+        "existence_accuracy": float(np.concatenate(exist_ok).mean()),
+        "launch_angle_error_rad": {"p50": float(np.median(ang)), "p99": float(np.percentile(ang, 99)),
+                                   "max": float(ang.max())},
+        "note": "the refinement starts from these angles; each returned solution is a traced ray"}
     nq = len(q["zs"]) * len(t_inf)
     return {
         "workload": f"MLP 3-256x4-12 trained on {len(tr['zs']):,} path-finder-labelled pairs; "
@@ -399,6 +418,7 @@ def surrogate_leg(rp, W, args, rank, flush):
                              "max": float(errs.max())},
                   "count_agreement_adjudicated": float((sur_count == adj).mean()),
                   "count_agreement_vs_coarse_scan": float((sur_count == tc).mean())},
+        "network_alone": network_alone,
         "training": {"label_s": t_lab, "train_s": t_train, "adam_steps": n_steps,
                      "batch": sch["batch"], "epochs": sch["epochs"], "final_loss": loss,
                      "train_tflops": 3 * MLP_FLOPS_FWD * sch["batch"] * n_steps / t_train / 1e12},
@@ -499,8 +519,12 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     # the scheduling knobs (speed only, never a record) tuned on this batch
     t0 = time.perf_counter()
-    tuned = autotune.tune_trace(med, rays, cfg["params"], buf, "fp32", idle=(192, 256, 384),
-                                flush=(1, 2, 4), block=(64, 128, 256), reps=1)
+    if args.no_tune:
+        tuned = {"best": dict.fromkeys(("service_idle", "flush_min", "block", "blocks_per_sm"), 0),
+                 "ms": {}, "params": dict(cfg["params"])}
+    else:
+        tuned = autotune.tune_trace(med, rays, cfg["params"], buf, "fp32", idle=(192, 256, 384),
+                                    flush=(1, 2, 4), block=(64, 128, 256), reps=1)
     tune_s = time.perf_counter() - t0
     prm32 = rp.make_params(tuned["params"], "fp32")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -658,7 +682,7 @@ def run_gpu(args):
     # figures (memory-bound path: algorithmic bytes = 8 float4 corner samples per medium
     # evaluation, 6 evaluations per attempted step)
     if not args.no_grid:
-        gcfg = W.gridded()
+        gcfg = W.gridded(per_src=args.grid_rays // 16)
         gmed = rp.Medium(gcfg["medium"])
         grays = rp.PreparedRays(*gcfg["rays"])
         gbuf = rp.TraceBuffers(grays.n + 16, 0, fields=("end_pos", "path", "time", "status"))
@@ -676,7 +700,7 @@ def run_gpu(args):
         bytes_alg = float(BYTES_PER_ATTEMPT_GRID) * gatt
         gbs = bytes_alg / gsec / 1e9
         modes["grid_fp32_mixed"] = {
-            "workload": "256x256x512 FP32 grid (4 m), 4,194,304 rays from 16 sources, tol 1e-5",
+            "workload": "256x256x512 FP32 grid (4 m), %d rays from 16 sources, tol 1e-5" % grays.n,
             "ray_steps_per_s": gacc / gsec, "rays_per_s": gr / gsec,
             "ms_per_step": 1e3 * gsec / len(gt),
             "roofline": {"bound": "l2", "achieved": gbs, "peak": peaks["l2_gbs"], "unit": "GB/s",
@@ -820,6 +844,10 @@ def main():
     ap.add_argument("--no-fig1", action="store_true")
     ap.add_argument("--no-spheres", action="store_true")
     ap.add_argument("--no-surfaces", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the library's default scheduling knobs (for profiling runs)")
+    ap.add_argument("--grid-rays", type=int, default=4_194_304,
+                    help="rays of the gridded leg (the workload is 4,194,304)")
     ap.add_argument("--sur-train", type=int, default=4_194_304)
     ap.add_argument("--sur-queries", type=int, default=1_048_576)
     ap.add_argument("--sur-check", type=int, default=16_384)
