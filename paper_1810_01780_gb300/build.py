@@ -14,7 +14,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libradiopropa_gb300.so")
 SOURCES = ["api.cu", "trace.cu", "trace_static.cu", "medium.cu", "pathfind.cu", "mlp.cu",
-           "mlp_fused.cu", "mlp_train_tc.cu", "peaks.cu"]
+           "mlp_fused.cu", "mlp_train_tc.cu", "mlp_train_fused.cu",
+           "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", INCLUDE, "-I", CSRC]

@@ -23,107 +23,7 @@ namespace {
 constexpr int kLayers = 5;
 constexpr int kDims[kLayers + 1] = {3, 256, 256, 256, 256, 12};
 
-enum { EPI_BIAS = 0, EPI_BIAS_GELU = 1, EPI_GELU_GRAD = 2 };
-
-__device__ __forceinline__ float gelu_f(float x)
-{
-    return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
-}
-
-__device__ __forceinline__ float gelu_grad_f(float x)
-{
-    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) +
-           x * expf(-0.5f * x * x) * 0.39894228040143268f;
-}
-
-// Forward and backward-data passes of the thin layers on the CUDA cores (BF16-rounded
-// operands, FP32 products and sums):
-//   first layer (3 -> 256): z[s][j] = sum_i x[s][i] W0[i][j] + b0[j], keeping z and gelu(z)
-//     (one thread per output element);
-//   last layer (256 -> 12) forward: out[s][o] = sum_i H[s][i] W4[i][o] + b4[o] (one warp per
-//     row, W4 in shared memory, each lane 8 inputs, the 12 sums reduced across the warp);
-//   last layer backward: g[s][i] = (sum_o g4[s][o] W4[i][o]) gelu'(Z3[s][i]) (thread i with
-//     row i of W4 in registers, the rows of g4 staged in shared memory).
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
-constexpr int kBwdRows = 32;  // rows of g4 a CTA of k_last_bwd stages at a time
-
-__global__ void __launch_bounds__(256) k_first_fwd(const float *__restrict__ x, long long n,
-                                                   const __nv_bfloat16 *__restrict__ W,
-                                                   const float *__restrict__ b,
-                                                   float *__restrict__ Z, float *__restrict__ H)
-{
-    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e >= n * 256) return;
-    const long long r = e >> 8;
-    const int j = (int)(e & 255);
-    float z = bf16r(x[3 * r]) * __bfloat162float(W[j]);
-    z = fmaf(bf16r(x[3 * r + 1]), __bfloat162float(W[256 + j]), z);
-    z = fmaf(bf16r(x[3 * r + 2]), __bfloat162float(W[512 + j]), z);
-    z += b[j];
-    if (Z) Z[e] = z;
-    H[e] = gelu_f(z);
-}
-
-__global__ void __launch_bounds__(256) k_last_fwd(const float *__restrict__ H, long long n,
-                                                  const __nv_bfloat16 *__restrict__ W,
-                                                  const float *__restrict__ b,
-                                                  float *__restrict__ out)
-{
-    __shared__ float w[256 * 12];
-    for (int e = threadIdx.x; e < 256 * 12; e += blockDim.x) w[e] = __bfloat162float(W[e]);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long r = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); r < n;
-         r += warps) {
-        const float4 *src = reinterpret_cast<const float4 *>(H + r * 256 + lane * 8);
-        const float4 a = src[0], c = src[1];
-        const float h[8] = {bf16r(a.x), bf16r(a.y), bf16r(a.z), bf16r(a.w),
-                            bf16r(c.x), bf16r(c.y), bf16r(c.z), bf16r(c.w)};
-        float acc[12];
-#pragma unroll
-        for (int o = 0; o < 12; ++o) acc[o] = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-#pragma unroll
-            for (int o = 0; o < 12; ++o) acc[o] = fmaf(h[k], w[(lane * 8 + k) * 12 + o], acc[o]);
-#pragma unroll
-        for (int o = 0; o < 12; ++o)
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) acc[o] += __shfl_xor_sync(0xffffffffu, acc[o], d);
-        if (lane == 0) {
-#pragma unroll
-            for (int o = 0; o < 12; ++o) out[r * 12 + o] = acc[o] + b[o];
-        }
-    }
-}
-
-__global__ void __launch_bounds__(256) k_last_bwd(const float *__restrict__ G, long long n,
-                                                  const __nv_bfloat16 *__restrict__ W,
-                                                  const float *__restrict__ Zin,
-                                                  float *__restrict__ Gout)
-{
-    __shared__ float gb[kBwdRows * 12];
-    const int i = threadIdx.x;
-    float w[12];
-#pragma unroll
-    for (int o = 0; o < 12; ++o) w[o] = __bfloat162float(W[i * 12 + o]);
-    for (long long r0 = blockIdx.x * (long long)kBwdRows; r0 < n; r0 += (long long)gridDim.x * kBwdRows) {
-        const int rows = (int)min((long long)kBwdRows, n - r0);
-        __syncthreads();
-        for (int e = i; e < kBwdRows * 12; e += 256)
-            gb[e] = e / 12 < rows ? bf16r(G[(r0 + e / 12) * 12 + e % 12]) : 0.0f;
-        __syncthreads();
-#pragma unroll 4
-        for (int r = 0; r < rows; ++r) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int o = 0; o < 12; ++o) acc = fmaf(gb[r * 12 + o], w[o], acc);
-            const long long e = (r0 + r) * 256 + i;
-            Gout[e] = acc * gelu_grad_f(Zin[e]);
-        }
-    }
-}
 
 // Weight and bias gradients of the thin layers, on the CUDA cores (BF16-rounded operands,
 // FP32 products and sums, as in the forward pass; bias gradients from the unrounded g):
@@ -209,31 +109,6 @@ __global__ void k_sum_parts(const float *__restrict__ part, int n_parts, int nw,
         db[e - nw] += s;
 }
 
-__global__ void k_loss(const float *out, const float *y, const float *t, long long n, float *g,
-                       double *loss)
-{
-    const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    float L = 0.0f;
-    if (b < n) {
-        const float inv_n = 1.0f / (float)n;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const float z = out[b * 12 + 6 * k], yk = y[b * 2 + k];
-            L += fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z))) - yk * z;
-            g[b * 12 + 6 * k] = (1.0f / (1.0f + expf(-z)) - yk) * inv_n;
-#pragma unroll
-            for (int j = 0; j < 5; ++j) {
-                const float d = out[b * 12 + 6 * k + 1 + j] - t[b * 10 + 5 * k + j];
-                L += 0.5f * yk * d * d;
-                g[b * 12 + 6 * k + 1 + j] = yk * d * inv_n;
-            }
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) L += __shfl_xor_sync(0xffffffffu, L, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, (double)L);
-}
-
-
 __global__ void k_adam(float *p, __nv_bfloat16 *pb, const float *gr, float *m, float *v,
                        long long n, float lr, float c1, float c2)
 {
@@ -315,10 +190,12 @@ static void free_acts(rp_surrogate_s *s)
         s->H[l] = nullptr;
     }
     cudaFree(s->out);
-    cudaFree(s->g0);
-    cudaFree(s->g1);
+    for (int l = 0; l < 4; ++l) {
+        cudaFree(s->gl[l]);
+        s->gl[l] = nullptr;
+    }
     cudaFree(s->part);
-    s->out = s->g0 = s->g1 = s->part = nullptr;
+    s->out = s->part = nullptr;
     s->cap = 0;
 }
 
@@ -331,91 +208,44 @@ int ensure_acts(rp_surrogate_s *s, long long n)
     for (int l = 0; l < 4; ++l) RP_CUDA_TRY(cudaMalloc(&s->Z[l], sizeof(float) * cap * 256));
     for (int l = 1; l < 5; ++l) RP_CUDA_TRY(cudaMalloc(&s->H[l], sizeof(float) * cap * 256));
     RP_CUDA_TRY(cudaMalloc(&s->out, sizeof(float) * cap * 12));
-    RP_CUDA_TRY(cudaMalloc(&s->g0, sizeof(float) * cap * 256));
-    RP_CUDA_TRY(cudaMalloc(&s->g1, sizeof(float) * cap * 256));
+    for (int l = 0; l < 4; ++l) RP_CUDA_TRY(cudaMalloc(&s->gl[l], sizeof(float) * cap * 256));
     RP_CUDA_TRY(cudaMalloc(&s->part, sizeof(float) * (size_t)((cap + kThinChunk - 1) / kThinChunk) * kThinPart));
     s->cap = cap;
     return RP_OK;
 }
 
-// forward pass of n rows for training, keeping the pre-activations: layers 1..3 (256 -> 256)
-// on the tensor cores, the thin layers 0 (3 -> 256) and 4 (256 -> 12) on the CUDA cores
-int forward(rp_surrogate_s *s, long long n, const float *x, float *out, bool train,
-                   cudaStream_t st)
-{
-    int rc = ensure_pack(s, st);
-    if (rc) return rc;
-    const unsigned elem_grid = (unsigned)((n * 256 + 255) / 256);
-    k_first_fwd<<<elem_grid, 256, 0, st>>>(x, n, s->pb + layer_w(0), s->p + layer_b(0),
-                                           train ? s->Z[0] : nullptr, s->H[1]);
-    RP_CUDA_TRY(cudaGetLastError());
-    for (int l = 1; l <= 3; ++l)
-        if ((rc = tc_dense(true, s->H[l], n, s->pack + (l - 1) * kPackW, s->p + layer_b(l), nullptr,
-                           train ? s->Z[l] : nullptr, s->H[l + 1], s->fflag, wait_cycles(s), st)))
-            return rc;
-    int dev;
-    RP_CUDA_TRY(cudaGetDevice(&dev));
-    const int sms = sm_count(dev);
-    const unsigned row_grid = (unsigned)std::min<long long>((n + 7) / 8, 2LL * sms);
-    k_last_fwd<<<row_grid, 256, 0, st>>>(s->H[4], n, s->pb + layer_w(4), s->p + layer_b(4), out);
-    RP_CUDA_TRY(cudaGetLastError());
-    return RP_OK;
-}
-
-// loss and parameter gradient (into s->grad) of n rows
+// Loss and parameter gradient (into s->grad) of n rows: the fused forward pass with the loss
+// and the last layer's backward data pass, the hidden layers' backward data chain, the three
+// hidden layers' weight gradients on the tensor cores (one launch), and the thin layers' weight
+// gradients on the CUDA cores.
 static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float *y,
                      const float *t, double *loss_host, cudaStream_t st)
 {
     int rc = ensure_acts(s, n);
     if (rc) return rc;
-    if ((rc = forward(s, n, x, s->out, true, st))) return rc;
+    if ((rc = ensure_pack(s, st))) return rc;
     RP_CUDA_TRY(cudaMemsetAsync(s->loss, 0, sizeof(double), st));
     RP_CUDA_TRY(cudaMemsetAsync(s->grad, 0, sizeof(float) * n_params(), st));
-    float *g_cur = s->g0, *g_next = s->g1;
-    k_loss<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->out, y, t, n, g_cur, s->loss);
-    RP_CUDA_TRY(cudaGetLastError());
-    int dev;
-    RP_CUDA_TRY(cudaGetDevice(&dev));
-    const int sms = sm_count(dev);
-    // thin weight gradients: one 64-row chunk per CTA, then a fixed-order sum of the CTAs'
-    // partial sums; last-layer backward: one chunk of kBwdRows rows per CTA
-    (void)sms;
-    const unsigned thin_grid = (unsigned)((n + kThinChunk - 1) / kThinChunk);
-    const unsigned bwd_grid = (unsigned)((n + kBwdRows - 1) / kBwdRows);
-    for (int l = kLayers - 1; l >= 0; --l) {
-        const float *h = l == 0 ? x : s->H[l];
-        if (l >= 1 && l <= 3) {
-            // hidden 256 x 256 layers on the tensor cores: dW_l = H_l^T g and db_l, then
-            // g_{l-1} = (g W_l^T) * GELU'(Z_{l-1})
-            if ((rc = tc_wgrad(h, g_cur, n, s->grad + layer_w(l), s->grad + layer_b(l), s->fflag,
-                               wait_cycles(s), st)))
-                return rc;
-            if ((rc = tc_dense(false, g_cur, n, s->pack_t + (l - 1) * kPackW, nullptr, s->Z[l - 1],
-                               nullptr, g_next, s->fflag, wait_cycles(s), st)))
-                return rc;
-            float *tmp = g_cur;
-            g_cur = g_next;
-            g_next = tmp;
-            continue;
-        }
-        if (l == 0) {
-            k_wgrad_first<<<thin_grid, 256, 0, st>>>(x, g_cur, n, s->part);
-            k_sum_parts<<<(3 * 256 + 256 + 255) / 256, 256, 0, st>>>(
-                s->part, (int)thin_grid, 3 * 256, 256, s->grad + layer_w(0), s->grad + layer_b(0));
-            RP_CUDA_TRY(cudaGetLastError());
-            break;
-        }
-        // last layer: dW_4, db_4, then g_3 = (g W_4^T) * GELU'(Z_3)
-        k_wgrad_last<<<thin_grid, 256, 0, st>>>(h, g_cur, n, s->part);
-        k_sum_parts<<<(256 * 12 + 12 + 255) / 256, 256, 0, st>>>(
-            s->part, (int)thin_grid, 256 * 12, 12, s->grad + layer_w(l), s->grad + layer_b(l));
-        RP_CUDA_TRY(cudaGetLastError());
-        k_last_bwd<<<bwd_grid, 256, 0, st>>>(g_cur, n, s->pb + layer_w(l), s->Z[l - 1], g_next);
-        RP_CUDA_TRY(cudaGetLastError());
-        float *tmp = g_cur;
-        g_cur = g_next;
-        g_next = tmp;
+    if ((rc = train_fwd(s, n, x, y, t, st))) return rc;
+    if ((rc = train_bwd(s, n, st))) return rc;
+    WgradArgs wa;
+    for (int l = 1; l <= 3; ++l) {  // layer l: input H_l, output gradient g_l
+        wa.H[l - 1] = s->H[l];
+        wa.G[l - 1] = s->gl[l];
+        wa.dW[l - 1] = s->grad + layer_w(l);
+        wa.db[l - 1] = s->grad + layer_b(l);
     }
+    if ((rc = tc_wgrad3(wa, n, s->fflag, wait_cycles(s), st))) return rc;
+    // thin weight gradients: one 64-row chunk per CTA, then a fixed-order sum of the CTAs'
+    // partial sums
+    const unsigned thin_grid = (unsigned)((n + kThinChunk - 1) / kThinChunk);
+    k_wgrad_last<<<thin_grid, 256, 0, st>>>(s->H[4], s->out, n, s->part);
+    k_sum_parts<<<(256 * 12 + 12 + 255) / 256, 256, 0, st>>>(
+        s->part, (int)thin_grid, 256 * 12, 12, s->grad + layer_w(4), s->grad + layer_b(4));
+    k_wgrad_first<<<thin_grid, 256, 0, st>>>(x, s->gl[0], n, s->part);
+    k_sum_parts<<<(3 * 256 + 256 + 255) / 256, 256, 0, st>>>(
+        s->part, (int)thin_grid, 3 * 256, 256, s->grad + layer_w(0), s->grad + layer_b(0));
+    RP_CUDA_TRY(cudaGetLastError());
     if (loss_host) {
         RP_CUDA_TRY(cudaMemcpyAsync(loss_host, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
         if ((rc = fused_status(s, st))) return rc;  // syncs st

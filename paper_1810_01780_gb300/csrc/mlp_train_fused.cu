@@ -1,0 +1,515 @@
+// mlp_train_fused.cu -- one training step of the surrogate network in two fused tensor-core
+// kernels per batch: the whole forward pass with the loss and the last layer's backward pass,
+// then the backward-data chain through the three hidden layers.
+//
+// k_train_fwd: per tile of 128 rows a CTA of 512 threads runs layer 0 (3 -> 256) on the CUDA
+//   cores into the BF16 A tile in shared memory, then the three 256 -> 256 layers on the
+//   tensor cores exactly as the fused inference kernel does (weights by bulk copy, 16
+//   tcgen05.mma of M 128, N 256, K 16 into a 256-column TMEM accumulator, epilogue by sixteen
+//   warps), keeping the activations in shared memory between layers; each epilogue also stores
+//   the layer's pre-activations z and activations gelu(z) in FP32 (the backward pass and the
+//   weight gradients read them).  The last layer (256 -> 12) comes out of the third epilogue's
+//   partial sums; the loss and its gradient g4 follow per row, and the last layer's backward
+//   data pass g3 = (g4 W4^T) gelu'(z3) re-reads z3 from tensor memory.
+// k_train_bwd: per tile, g3 (FP32) as the BF16 A tile, then for the hidden layers 3, 2, 1 the
+//   backward images B[n][k] = W[n][k] by bulk copy, 16 tcgen05.mma (N 256) and an epilogue
+//   g_{l-1} = (g_l W_l^T) gelu'(z_{l-1}) that stores g_{l-1} in FP32 and, but for the last,
+//   feeds it back as the next A tile.
+// Arithmetic is that of the per-layer path: BF16 operands (weights, activations and
+// gradients rounded to BF16 where they enter a product), FP32 products and sums, FP32 bias,
+// GELU and GELU'.  Every mbarrier wait is bounded (the surrogate's wait limit); a CTA that
+// gives up sets the error flag, waits (with the default bound) for the work it issued, frees
+// its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "rp_internal.h"
+#include "tc_common.cuh"
+
+namespace rph {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kTile = 128;
+constexpr int kThreads = 512;            // 16 warps: lane quarter (warp % 4) x column group (warp / 4)
+constexpr int kGroups = kThreads / 128;  // column groups of a row
+constexpr int kGroupCols = 256 / kGroups;
+constexpr uint32_t kWBytes = (uint32_t)kPackW;
+// shared memory map (bytes): A tile, B tile, FP32 constants, barriers
+constexpr uint32_t SM_A = 0;
+constexpr uint32_t SM_B = 65536;
+constexpr uint32_t SM_F = SM_B + kWBytes;
+constexpr uint32_t SM_BAR = SM_F + kPackF * 4;
+constexpr uint32_t SM_TOTAL = SM_BAR + 32;
+static_assert(SM_TOTAL <= 227 * 1024, "shared memory map exceeds a CTA's limit");
+static_assert(SM_F % 16 == 0 && SM_BAR % 8 == 0, "alignment");
+// after the last MMA of a tile the A tile holds the last layer's partial sums (3 groups x 128
+// rows x 12) and then the rows' output gradients g4 (128 x 12)
+constexpr uint32_t SM_P = 0, SM_G4 = (kGroups - 1) * kTile * 12 * 4;
+static_assert(SM_G4 + kTile * 12 * 4 <= 65536, "partial sums and g4 fit in the A tile");
+
+// instruction descriptor: D FP32, A and B BF16, both K-major, N = 256, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) |
+                            ((128u >> 4) << 24);
+
+__device__ __forceinline__ void load_image(uint32_t b_base, const unsigned char *src, uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kWBytes)
+                 : "memory");
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                b_base + c * 32768u),
+            "l"(src + c * 32768), "r"(32768u), "r"(bar)
+            : "memory");
+}
+
+// 16 MMAs of one 256 x 256 layer (A tile x B image) into the accumulator, committed to bar_mma
+__device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a_base, uint32_t b_base,
+                                            uint32_t bar_mma)
+{
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const uint64_t ad = sdesc(a_base + s * 4096u, 2048u, 128u);
+        const uint64_t bd = sdesc(b_base + s * 8192u, 4096u, 128u);
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(kIdesc), "r"(s)
+            : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     bar_mma)
+                 : "memory");
+}
+
+__device__ __forceinline__ void store8(float *dst, const float (&v)[8])
+{
+    reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+// Shared setup of both kernels: barriers, abort word, tensor memory (256 columns).
+__device__ __forceinline__ uint32_t setup_cta(unsigned char *sm, int tid, int warp)
+{
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + SM_BAR);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(sm + SM_BAR + 16);
+    volatile int *abort_cta = reinterpret_cast<volatile int *>(sm + SM_BAR + 20);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_cta = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)),
+                     "r"(256u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    return *slot;
+}
+
+// Shared teardown: on failure record it and drain the issued work, then free tensor memory.
+__device__ __forceinline__ void teardown_cta(unsigned char *sm, int tid, int warp, uint32_t tmem,
+                                             bool failed, bool ld_pending, uint32_t ph_ld,
+                                             bool mma_pending, uint32_t ph_mma, int *flag)
+{
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + SM_BAR);
+    if (failed && tid == 0) {
+        atomicExch(flag, 1);
+        if (ld_pending) mbar_wait(su32(&bar[0]), ph_ld);
+        if (mma_pending) mbar_wait(su32(&bar[1]), ph_mma);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u)
+                     : "memory");
+    }
+}
+
+// Forward pass, loss and last-layer backward of n rows (x (n, 3), targets y (n, 2), t (n, 10)).
+// Writes Z[l] (n, 256) for l = 0..3 (pre-activations), H[l] (n, 256) for l = 1..4 (activations),
+// g4 (n, 12), g3 (n, 256), and adds the loss sum to *loss.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_train_fwd(const unsigned char *__restrict__ pack, const float *__restrict__ x,
+                const float *__restrict__ y, const float *__restrict__ t, long long n,
+                float *__restrict__ Z0, float *__restrict__ Z1, float *__restrict__ Z2,
+                float *__restrict__ Z3, float *__restrict__ H1, float *__restrict__ H2,
+                float *__restrict__ H3, float *__restrict__ H4, float *__restrict__ g4,
+                float *__restrict__ g3, double *loss, int *flag, long long wait)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *sA = sm + SM_A;
+    float *sF = reinterpret_cast<float *>(sm + SM_F);
+    float *sP = reinterpret_cast<float *>(sm + SM_P);
+    float *sG = reinterpret_cast<float *>(sm + SM_G4);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + SM_BAR);
+    volatile int *abort_cta = reinterpret_cast<volatile int *>(sm + SM_BAR + 20);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t bar_ld = su32(&bar[0]), bar_mma = su32(&bar[1]);
+    const uint32_t a_base = su32(sm + SM_A), b_base = su32(sm + SM_B);
+
+    const float4 *gF = reinterpret_cast<const float4 *>(pack + 3 * kPackW);
+    for (int i = tid; i < kPackF / 4; i += kThreads) reinterpret_cast<float4 *>(sF)[i] = gF[i];
+    const uint32_t tmem = setup_cta(sm, tid, warp);
+
+    uint32_t ph_ld = 0, ph_mma = 0;
+    bool ld_pending = false, mma_pending = false;
+    const long long n_tiles = (n + kTile - 1) / kTile;
+    const int row0 = tid & 127, grp0 = tid >> 7;
+    const int q = warp & 3, ch = warp >> 2;
+    const int erow = q * 32 + lane;
+    const float inv_n = 1.0f / (float)n;
+    float *Zs[4] = {Z0, Z1, Z2, Z3};
+    float *Hs[4] = {H1, H2, H3, H4};
+    bool failed = false;
+    if (tid == 0 && blockIdx.x < n_tiles) {
+        load_image(b_base, pack, bar_ld);
+        ld_pending = true;
+    }
+
+    for (long long tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+        const long long g0 = tile * kTile;
+        {  // layer 0 on the CUDA cores: z0, gelu(z0) to global and, in BF16, to the A tile
+            const long long gr = g0 + row0;
+            float x0 = 0.0f, x1 = 0.0f, x2 = 0.0f;
+            if (gr < n) {
+                x0 = bf16r(x[3 * gr]);
+                x1 = bf16r(x[3 * gr + 1]);
+                x2 = bf16r(x[3 * gr + 2]);
+            }
+#pragma unroll 1
+            for (int c = 0; c < kGroupCols / 8; ++c) {
+                const int k0 = grp0 * kGroupCols + c * 8;
+                float zz[8], hh[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int j = k0 + e;
+                    float z = x0 * sF[PF_W0 + j];
+                    z = fmaf(x1, sF[PF_W0 + 256 + j], z);
+                    z = fmaf(x2, sF[PF_W0 + 512 + j], z);
+                    zz[e] = z + sF[PF_B0 + j];
+                    hh[e] = gelu(zz[e]);
+                }
+                if (gr < n) {
+                    store8(Z0 + gr * 256 + k0, zz);
+                    store8(H1 + gr * 256 + k0, hh);
+                }
+                *reinterpret_cast<uint4 *>(sA + a_off(row0, k0)) =
+                    make_uint4(pack2(hh[0], hh[1]), pack2(hh[2], hh[3]), pack2(hh[4], hh[5]),
+                               pack2(hh[6], hh[7]));
+            }
+        }
+        float acc[12];
+#pragma unroll
+        for (int o = 0; o < 12; ++o) acc[o] = 0.0f;
+
+        for (int l = 0; l < 3; ++l) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            fence_before();
+            __syncthreads();
+            fence_after();
+            if (tid == 0) {
+                if (mbar_wait(bar_ld, ph_ld, wait)) {
+                    ld_pending = false;
+                    issue_layer(tmem, a_base, b_base, bar_mma);
+                    mma_pending = true;
+                } else {
+                    *abort_cta = 1;
+                }
+            }
+            ph_ld ^= 1u;
+            if (!mbar_wait(bar_mma, ph_mma, wait)) *abort_cta = 1;
+            ph_mma ^= 1u;
+            fence_after();
+            __syncthreads();
+            if (*abort_cta) {
+                failed = true;
+                break;
+            }
+            if (tid == 0) {
+                mma_pending = false;
+                if (l < 2) {
+                    load_image(b_base, pack + (l + 1) * kPackW, bar_ld);
+                    ld_pending = true;
+                } else if (tile + gridDim.x < n_tiles) {
+                    load_image(b_base, pack, bar_ld);
+                    ld_pending = true;
+                }
+            }
+            const float *bias = sF + PF_B1 + l * 256;
+            float *Zl = Zs[l + 1], *Hl = Hs[l + 1];
+            const long long gr = g0 + erow;
+#pragma unroll 1
+            for (int c = 0; c < kGroupCols / 32; ++c) {
+                const int col0 = ch * kGroupCols + c * 32;
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, v);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float zz[8], hh[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        zz[u] = __uint_as_float(v[e * 8 + u]) + bias[col0 + e * 8 + u];
+                        hh[u] = gelu(zz[u]);
+                    }
+                    if (gr < n) {
+                        store8(Zl + gr * 256 + col0 + e * 8, zz);
+                        store8(Hl + gr * 256 + col0 + e * 8, hh);
+                    }
+                    if (l < 2) {
+                        *reinterpret_cast<uint4 *>(sA + a_off(erow, col0 + e * 8)) =
+                            make_uint4(pack2(hh[0], hh[1]), pack2(hh[2], hh[3]),
+                                       pack2(hh[4], hh[5]), pack2(hh[6], hh[7]));
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const float h = bf16r(hh[u]);
+                            const float *w4 = sF + PF_W4 + (col0 + e * 8 + u) * 12;
+#pragma unroll
+                            for (int o = 0; o < 12; ++o) acc[o] = fmaf(h, w4[o], acc[o]);
+                        }
+                    }
+                }
+            }
+            fence_before();
+        }
+        if (failed) break;
+        // last layer: the column groups' partial sums of each row meet in shared memory
+        if (ch > 0) {
+#pragma unroll
+            for (int o = 0; o < 12; ++o) sP[((ch - 1) * kTile + erow) * 12 + o] = acc[o];
+        }
+        __syncthreads();
+        if (ch == 0) {
+            // output, loss and its gradient g4 per row (logistic loss of the existence logits,
+            // half the squared error of the regression outputs of existing slots, over n)
+            const long long gr = g0 + erow;
+            float L = 0.0f;
+            float gg[12];
+#pragma unroll
+            for (int o = 0; o < 12; ++o) gg[o] = 0.0f;
+            if (gr < n) {
+                float out[12];
+#pragma unroll
+                for (int o = 0; o < 12; ++o) {
+                    float v = acc[o];
+                    for (int g = 1; g < kGroups; ++g) v += sP[((g - 1) * kTile + erow) * 12 + o];
+                    out[o] = v + sF[PF_B4 + o];
+                }
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const float z = out[6 * k], yk = y[gr * 2 + k];
+                    L += fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z))) - yk * z;
+                    gg[6 * k] = (1.0f / (1.0f + expf(-z)) - yk) * inv_n;
+#pragma unroll
+                    for (int j = 0; j < 5; ++j) {
+                        const float d = out[6 * k + 1 + j] - t[gr * 10 + 5 * k + j];
+                        L += 0.5f * yk * d * d;
+                        gg[6 * k + 1 + j] = yk * d * inv_n;
+                    }
+                }
+#pragma unroll
+                for (int o = 0; o < 12; ++o) g4[gr * 12 + o] = gg[o];
+            }
+#pragma unroll
+            for (int o = 0; o < 12; ++o) sG[erow * 12 + o] = bf16r(gg[o]);
+            for (int d = 16; d > 0; d >>= 1) L += __shfl_xor_sync(0xffffffffu, L, d);
+            if (lane == 0) atomicAdd(loss, (double)L);
+        }
+        __syncthreads();
+        fence_after();
+        {  // last layer backward: g3 = (g4 W4^T) gelu'(z3), z3 read again from tensor memory
+            const long long gr = g0 + erow;
+            const float *bias = sF + PF_B1 + 2 * 256;
+            float gr4[12];
+#pragma unroll
+            for (int o = 0; o < 12; ++o) gr4[o] = sG[erow * 12 + o];
+#pragma unroll 1
+            for (int c = 0; c < kGroupCols / 32; ++c) {
+                const int col0 = ch * kGroupCols + c * 32;
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, v);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float gg[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int col = col0 + e * 8 + u;
+                        const float *w4 = sF + PF_W4 + col * 12;
+                        float s = 0.0f;
+#pragma unroll
+                        for (int o = 0; o < 12; ++o) s = fmaf(gr4[o], w4[o], s);
+                        gg[u] = s * gelu_prime(__uint_as_float(v[e * 8 + u]) + bias[col]);
+                    }
+                    if (gr < n) store8(g3 + gr * 256 + col0 + e * 8, gg);
+                }
+            }
+        }
+        fence_before();
+        __syncthreads();
+    }
+    teardown_cta(sm, tid, warp, tmem, failed, ld_pending, ph_ld ^ 1u, mma_pending, ph_mma ^ 1u, flag);
+}
+
+// Backward-data chain of the hidden layers for n rows: from g3 (n, 256) and the
+// pre-activations Z0..Z2, writes g2, g1, g0 (n, 256) with g_{l-1} = (g_l W_l^T) gelu'(z_{l-1}).
+// pack_t: the backward images of W1, W2, W3 (B[n][k] = W[n][k]).
+__global__ void __launch_bounds__(kThreads, 1)
+    k_train_bwd(const unsigned char *__restrict__ pack_t, const float *__restrict__ g3,
+                const float *__restrict__ Z0, const float *__restrict__ Z1,
+                const float *__restrict__ Z2, long long n, float *__restrict__ g2,
+                float *__restrict__ g1, float *__restrict__ g0, int *flag, long long wait)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *sA = sm + SM_A;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + SM_BAR);
+    volatile int *abort_cta = reinterpret_cast<volatile int *>(sm + SM_BAR + 20);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t bar_ld = su32(&bar[0]), bar_mma = su32(&bar[1]);
+    const uint32_t a_base = su32(sm + SM_A), b_base = su32(sm + SM_B);
+    const uint32_t tmem = setup_cta(sm, tid, warp);
+
+    uint32_t ph_ld = 0, ph_mma = 0;
+    bool ld_pending = false, mma_pending = false;
+    const long long n_tiles = (n + kTile - 1) / kTile;
+    const int q = warp & 3, ch = warp >> 2;
+    const int erow = q * 32 + lane;
+    const float *Zin[3] = {Z2, Z1, Z0};  // gelu' of the layer below layers 3, 2, 1
+    float *Gout[3] = {g2, g1, g0};
+    bool failed = false;
+    if (tid == 0 && blockIdx.x < n_tiles) {  // layer 3's image first
+        load_image(b_base, pack_t + 2 * kPackW, bar_ld);
+        ld_pending = true;
+    }
+
+    for (long long tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+        const long long gb = tile * kTile;
+        // g3 rows -> BF16 A tile: 128 rows x 32 chunks of 8 columns, 8 chunks per thread
+#pragma unroll 2
+        for (int i = 0; i < 8; ++i) {
+            const int c = tid + i * kThreads, row = c >> 5, k0 = (c & 31) * 8;
+            const long long gr = gb + row;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+            if (gr < n) {
+                const float4 *src = reinterpret_cast<const float4 *>(g3 + gr * 256 + k0);
+                a = __ldg(src);
+                b = __ldg(src + 1);
+            }
+            *reinterpret_cast<uint4 *>(sA + a_off(row, k0)) =
+                make_uint4(pack2(a.x, a.y), pack2(a.z, a.w), pack2(b.x, b.y), pack2(b.z, b.w));
+        }
+        for (int l = 0; l < 3; ++l) {  // hidden layers 3, 2, 1
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            fence_before();
+            __syncthreads();
+            fence_after();
+            if (tid == 0) {
+                if (mbar_wait(bar_ld, ph_ld, wait)) {
+                    ld_pending = false;
+                    issue_layer(tmem, a_base, b_base, bar_mma);
+                    mma_pending = true;
+                } else {
+                    *abort_cta = 1;
+                }
+            }
+            ph_ld ^= 1u;
+            if (!mbar_wait(bar_mma, ph_mma, wait)) *abort_cta = 1;
+            ph_mma ^= 1u;
+            fence_after();
+            __syncthreads();
+            if (*abort_cta) {
+                failed = true;
+                break;
+            }
+            if (tid == 0) {
+                mma_pending = false;
+                if (l < 2) {
+                    load_image(b_base, pack_t + (1 - l) * kPackW, bar_ld);
+                    ld_pending = true;
+                } else if (tile + gridDim.x < n_tiles) {
+                    load_image(b_base, pack_t + 2 * kPackW, bar_ld);
+                    ld_pending = true;
+                }
+            }
+            const float *Zl = Zin[l];
+            float *Gl = Gout[l];
+            const long long gr = gb + erow;
+#pragma unroll 1
+            for (int c = 0; c < kGroupCols / 32; ++c) {
+                const int col0 = ch * kGroupCols + c * 32;
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, v);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gg[8];
+                    if (gr < n) {
+                        const float4 *zs = reinterpret_cast<const float4 *>(Zl + gr * 256 + col0 + e * 8);
+                        const float4 z0 = __ldg(zs), z1 = __ldg(zs + 1);
+                        z[0] = z0.x; z[1] = z0.y; z[2] = z0.z; z[3] = z0.w;
+                        z[4] = z1.x; z[5] = z1.y; z[6] = z1.z; z[7] = z1.w;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) gg[u] = __uint_as_float(v[e * 8 + u]) * gelu_prime(z[u]);
+                    if (gr < n) store8(Gl + gr * 256 + col0 + e * 8, gg);
+                    if (l < 2)
+                        *reinterpret_cast<uint4 *>(sA + a_off(erow, col0 + e * 8)) =
+                            make_uint4(pack2(gg[0], gg[1]), pack2(gg[2], gg[3]),
+                                       pack2(gg[4], gg[5]), pack2(gg[6], gg[7]));
+                }
+            }
+            fence_before();
+        }
+        if (failed) break;
+        __syncthreads();  // the next tile's staging overwrites the A tile
+    }
+    teardown_cta(sm, tid, warp, tmem, failed, ld_pending, ph_ld ^ 1u, mma_pending, ph_mma ^ 1u, flag);
+}
+
+}  // namespace
+
+int train_fwd(rp_surrogate_s *s, long long n, const float *x, const float *y, const float *t,
+              cudaStream_t st)
+{
+    if (n <= 0) return RP_OK;
+    int dev;
+    RP_CUDA_TRY(cudaGetDevice(&dev));
+    RP_CUDA_TRY(cudaFuncSetAttribute(k_train_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SM_TOTAL));
+    const long long tiles = (n + kTile - 1) / kTile;
+    const int grid = (int)std::min<long long>(tiles, (long long)sm_count(dev));
+    k_train_fwd<<<grid, kThreads, SM_TOTAL, st>>>(s->pack, x, y, t, n, s->Z[0], s->Z[1], s->Z[2],
+                                                  s->Z[3], s->H[1], s->H[2], s->H[3], s->H[4],
+                                                  s->out, s->gl[3], s->loss, s->fflag,
+                                                  wait_cycles(s));
+    RP_CUDA_TRY(cudaGetLastError());
+    return RP_OK;
+}
+
+int train_bwd(rp_surrogate_s *s, long long n, cudaStream_t st)
+{
+    if (n <= 0) return RP_OK;
+    int dev;
+    RP_CUDA_TRY(cudaGetDevice(&dev));
+    RP_CUDA_TRY(cudaFuncSetAttribute(k_train_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SM_TOTAL));
+    const long long tiles = (n + kTile - 1) / kTile;
+    const int grid = (int)std::min<long long>(tiles, (long long)sm_count(dev));
+    k_train_bwd<<<grid, kThreads, SM_TOTAL, st>>>(s->pack_t, s->gl[3], s->Z[0], s->Z[1], s->Z[2],
+                                                  n, s->gl[2], s->gl[1], s->gl[0], s->fflag,
+                                                  wait_cycles(s));
+    RP_CUDA_TRY(cudaGetLastError());
+    return RP_OK;
+}
+
+}  // namespace rph

@@ -1,25 +1,16 @@
-// mlp_train_tc.cu -- the surrogate's 256 x 256 layers in training, on the 5th-generation
-// tensor cores (tcgen05).
+// mlp_train_tc.cu -- the weight gradients of the surrogate's three hidden 256 x 256 layers in
+// training, on the 5th-generation tensor cores (tcgen05), all three layers in one launch.
 //
-// Two kernels cover the three hidden 256 -> 256 layers:
-//   k_tc_dense<EPI>: C[128 rows x 128 columns] = A[128 x 256] B^T per CTA (one row tile and one
-//     half of the 256 output columns each), with the FP32 rows of A converted to BF16 into the
-//     no-swizzle K-major image in shared memory, the packed BF16 B image (256 n x 256 k, 128 KB)
-//     brought in by bulk copy, 16 tcgen05.mma (M 128, N 128, K 16, reading the half's n-cores)
-//     into a 128-column tensor-memory accumulator, and an epilogue per
-//     row: forward (EPI_FWD) z = C + b, keeping z and gelu(z); backward (EPI_BWD)
-//     C * gelu'(z) of the layer below.  Forward takes B[n][k] = W[k][n] (the inference
-//     image), backward B[n][k] = W[n][k] (so that C = g W^T).
 //   k_tc_wgrad: dW[in][out] += sum over rows s of H[s][in] g[s][out]: M = in (two halves of
-//     128), N = out (one half of 128 per CTA), K = rows.  A CTA runs over chunks of 128 rows,
-//     staging H^T and its half of g^T as BF16 K-major images (each thread gathers 8 rows of one
-//     column into a 16-byte core row), accumulating both M halves in tensor memory (256
-//     columns), and adds its sums to dW with vector atomics at the end; the bias gradient
-//     (column sums of g) comes along from the staging loads.
-// Arithmetic is that of the CUDA-core GEMMs they replace: BF16 operands, FP32 products and
-// sums, FP32 bias, GELU and GELU'.  Every mbarrier wait is bounded (the surrogate's wait limit);
-// a CTA that gives up sets the error flag, waits (with the default bound) for its work in
-// flight, frees its tensor memory and returns.
+//     128), N = out (one half of 128 per CTA), K = rows; blockIdx.z selects the layer.  A CTA
+//     runs over chunks of 128 rows, staging H^T and its half of g^T as BF16 K-major images (each
+//     thread gathers 8 rows of one column into a 16-byte core row), accumulating both M halves
+//     in tensor memory (256 columns), and adds its sums to dW with vector atomics at the end;
+//     the bias gradient (column sums of g) comes along from the staging loads.
+//   k_pack_t: the backward data pass's B images of W1..W3 (B[n][k] = W[n][k]).
+// Arithmetic: BF16 operands, FP32 products and sums.  Every mbarrier wait is bounded (the
+// surrogate's wait limit); a CTA that gives up sets the error flag, waits (with the default
+// bound) for its work in flight, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -37,18 +28,10 @@ constexpr int kThreads = 512;  // 16 warps: lane quarter (warp % 4) x column gro
 constexpr int kRows = 128;     // rows per tile (M of one MMA)
 constexpr uint32_t kImgB = 256u * 256u * 2u;  // a packed 256 x 256 BF16 B image
 
-enum { EPI_FWD = 0, EPI_BWD = 1 };
-
 // instruction descriptor: D FP32, A and B BF16, both K-major, N = 128, M = 128 (each CTA
 // computes one half of the 256 output columns)
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) |
                             ((128u >> 4) << 24);
-
-__device__ __forceinline__ float gelu_grad(float x)
-{
-    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) +
-           x * expf(-0.5f * x * x) * 0.39894228040143268f;
-}
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc)
 {
@@ -65,147 +48,6 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
-// shared memory map of k_tc_dense (bytes)
-constexpr uint32_t DN_A = 0;                  // 128 x 256 BF16 A image (64 KB)
-constexpr uint32_t DN_B = 65536;              // 256 x 256 BF16 B image (128 KB)
-constexpr uint32_t DN_BAR = DN_B + kImgB;     // two mbarriers, TMEM slot, abort word
-constexpr uint32_t DN_TOTAL = DN_BAR + 32;
-static_assert(DN_TOTAL <= 227 * 1024, "shared memory map exceeds a CTA's limit");
-
-template <int EPI>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_tc_dense(const float *__restrict__ A, long long n, const unsigned char *__restrict__ Bimg,
-               const float *__restrict__ bias, const float *__restrict__ Zin,
-               float *__restrict__ Zout, float *__restrict__ Out, int *flag, long long wait)
-{
-    extern __shared__ __align__(1024) unsigned char sm[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + DN_BAR);  // [0] B in, [1] MMAs done
-    uint32_t *slot = reinterpret_cast<uint32_t *>(sm + DN_BAR + 16);
-    volatile int *abort_cta = reinterpret_cast<volatile int *>(sm + DN_BAR + 20);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t bar_ld = su32(&bar[0]), bar_mma = su32(&bar[1]);
-    const uint32_t a_base = su32(sm + DN_A), b_base = su32(sm + DN_B);
-    const long long g0 = (long long)blockIdx.x * kRows;
-    const int half = (int)blockIdx.y;  // output columns 128 half .. + 127
-
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_ld) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_mma) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *abort_cta = 0;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_ld), "r"(kImgB)
-                     : "memory");
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    b_base + c * 32768u),
-                "l"(Bimg + c * 32768), "r"(32768u), "r"(bar_ld)
-                : "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)),
-                     "r"(128u)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    // A rows -> BF16 K-major image: 128 rows x 32 chunks of 8 columns, 8 chunks per thread
-#pragma unroll 2
-    for (int i = 0; i < 8; ++i) {
-        const int c = tid + i * kThreads, row = c >> 5, k0 = (c & 31) * 8;
-        const long long gr = g0 + row;
-        float4 lo = make_float4(0.0f, 0.0f, 0.0f, 0.0f), hi = lo;
-        if (gr < n) {
-            const float4 *src = reinterpret_cast<const float4 *>(A + gr * 256 + k0);
-            lo = __ldg(src);
-            hi = __ldg(src + 1);
-        }
-        *reinterpret_cast<uint4 *>(sm + DN_A + a_off(row, k0)) =
-            make_uint4(pack2(lo.x, lo.y), pack2(lo.z, lo.w), pack2(hi.x, hi.y), pack2(hi.z, hi.w));
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    fence_before();
-    __syncthreads();
-    fence_after();
-    const uint32_t tmem = *slot;
-    bool ld_pending = tid == 0, mma_pending = false;
-    if (tid == 0) {
-        if (mbar_wait(bar_ld, 0, wait)) {
-            ld_pending = false;
-            // the half's 16 n-cores of each k-core row of the B image: start 2048 B further
-#pragma unroll
-            for (int s = 0; s < 16; ++s)
-                mma_f16(tmem, sdesc(a_base + s * 4096u, 2048u, 128u),
-                        sdesc(b_base + (uint32_t)half * 2048u + s * 8192u, 4096u, 128u), (uint32_t)s);
-            mma_commit(bar_mma);
-            mma_pending = true;
-        } else {
-            *abort_cta = 1;
-        }
-    }
-    __syncthreads();
-    bool failed = *abort_cta != 0;
-    if (!failed && !mbar_wait(bar_mma, 0, wait)) *abort_cta = 1;
-    fence_after();
-    __syncthreads();
-    failed = *abort_cta != 0;
-    if (!failed) {
-        if (tid == 0) mma_pending = false;
-        const int q = warp & 3, ch = warp >> 2, row = q * 32 + lane;
-        const long long gr = g0 + row;
-        {
-            const int tcol = ch * 32, col0 = half * 128 + tcol;
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)tcol, v);
-            if (gr < n) {
-                float *o = Out + gr * 256 + col0;
-                if (EPI == EPI_FWD) {
-                    float *zo = Zout + gr * 256 + col0;
-#pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        float4 z, h;
-                        z.x = __uint_as_float(v[j]) + bias[col0 + j];
-                        z.y = __uint_as_float(v[j + 1]) + bias[col0 + j + 1];
-                        z.z = __uint_as_float(v[j + 2]) + bias[col0 + j + 2];
-                        z.w = __uint_as_float(v[j + 3]) + bias[col0 + j + 3];
-                        h.x = gelu(z.x);
-                        h.y = gelu(z.y);
-                        h.z = gelu(z.z);
-                        h.w = gelu(z.w);
-                        if (zo) *reinterpret_cast<float4 *>(zo + j) = z;
-                        *reinterpret_cast<float4 *>(o + j) = h;
-                    }
-                } else {
-                    const float *zi = Zin + gr * 256 + col0;
-#pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        const float4 z = *reinterpret_cast<const float4 *>(zi + j);
-                        float4 g;
-                        g.x = __uint_as_float(v[j]) * gelu_grad(z.x);
-                        g.y = __uint_as_float(v[j + 1]) * gelu_grad(z.y);
-                        g.z = __uint_as_float(v[j + 2]) * gelu_grad(z.z);
-                        g.w = __uint_as_float(v[j + 3]) * gelu_grad(z.w);
-                        *reinterpret_cast<float4 *>(o + j) = g;
-                    }
-                }
-            }
-        }
-    }
-    if (failed && tid == 0) {
-        atomicExch(flag, 1);
-        // let work already issued finish before the memory it targets goes away
-        if (ld_pending) mbar_wait(bar_ld, 0);
-        if (mma_pending) mbar_wait(bar_mma, 0);
-    }
-    fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u)
-                     : "memory");
-    }
-}
-
 // shared memory map of k_tc_wgrad (bytes): A = H^T chunk as two 128 x 128 halves (32 KB each;
 // core (k/8, m/8) at ((k/8) * 16 + m/8) * 128), B = the CTA's 128 columns of g^T, 128 x 128
 // (32 KB, same core layout)
@@ -217,9 +59,12 @@ constexpr int kChunk = 128;  // rows (K) per chunk
 
 // dW[:, 128 h .. 128 h + 127] (h = blockIdx.y) over the chunks blockIdx.x, + gridDim.x, ...
 __global__ void __launch_bounds__(kThreads, 1)
-    k_tc_wgrad(const float *__restrict__ H, const float *__restrict__ G, long long n,
-               float *__restrict__ dW, float *__restrict__ db, int *flag, long long wait)
+    k_tc_wgrad(const WgradArgs args, long long n, int *flag, long long wait)
 {
+    const float *__restrict__ H = args.H[blockIdx.z];
+    const float *__restrict__ G = args.G[blockIdx.z];
+    float *__restrict__ dW = args.dW[blockIdx.z];
+    float *__restrict__ db = args.db[blockIdx.z];
     extern __shared__ __align__(1024) unsigned char sm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + WG_BAR);  // MMAs done
     uint32_t *slot = reinterpret_cast<uint32_t *>(sm + WG_BAR + 16);
@@ -364,37 +209,17 @@ int tc_pack_backward(const float *p, unsigned char *img, long long w1, long long
     return RP_OK;
 }
 
-int tc_dense(bool forward, const float *A, long long n, const unsigned char *Bimg,
-             const float *bias, const float *Zin, float *Zout, float *Out, int *flag,
-             long long wait, cudaStream_t st)
-{
-    if (n <= 0) return RP_OK;
-    const dim3 grid((unsigned)((n + kRows - 1) / kRows), 2);  // row tiles x column halves
-    if (forward) {
-        RP_CUDA_TRY(cudaFuncSetAttribute(k_tc_dense<EPI_FWD>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DN_TOTAL));
-        k_tc_dense<EPI_FWD><<<grid, kThreads, DN_TOTAL, st>>>(A, n, Bimg, bias, Zin, Zout, Out, flag, wait);
-    } else {
-        RP_CUDA_TRY(cudaFuncSetAttribute(k_tc_dense<EPI_BWD>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DN_TOTAL));
-        k_tc_dense<EPI_BWD><<<grid, kThreads, DN_TOTAL, st>>>(A, n, Bimg, bias, Zin, Zout, Out, flag, wait);
-    }
-    RP_CUDA_TRY(cudaGetLastError());
-    return RP_OK;
-}
-
-int tc_wgrad(const float *H, const float *G, long long n, float *dW, float *db, int *flag,
-             long long wait, cudaStream_t st)
+int tc_wgrad3(const WgradArgs &a, long long n, int *flag, long long wait, cudaStream_t st)
 {
     if (n <= 0) return RP_OK;
     int dev;
     RP_CUDA_TRY(cudaGetDevice(&dev));
     const long long chunks = (n + kChunk - 1) / kChunk;
-    // chunks x column halves, at most two CTAs per SM in all
-    const dim3 grid((unsigned)std::min<long long>(chunks, (long long)sm_count(dev)), 2);
+    // chunks x column halves x layers
+    const dim3 grid((unsigned)std::min<long long>(chunks, (long long)sm_count(dev)), 2, 3);
     RP_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)WG_TOTAL));
-    k_tc_wgrad<<<grid, kThreads, WG_TOTAL, st>>>(H, G, n, dW, db, flag, wait);
+    k_tc_wgrad<<<grid, kThreads, WG_TOTAL, st>>>(a, n, flag, wait);
     RP_CUDA_TRY(cudaGetLastError());
     return RP_OK;
 }

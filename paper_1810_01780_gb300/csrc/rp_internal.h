@@ -20,7 +20,7 @@ struct rp_surrogate_s {
     __nv_bfloat16 *pb;
     // activations for a batch of up to `cap` rows
     long long cap;
-    float *Z[4], *H[5], *out, *g0, *g1;
+    float *Z[4], *H[5], *out, *gl[4];  // pre-activations, activations, g4, g0..g3
     float *part;  // per-CTA partial sums of the thin layers' weight and bias gradients
     double *loss;
     void *pipe;  // buffers of the surrogate path-finding pipeline (pathfind.cu)
@@ -168,21 +168,23 @@ enum { PF_W0 = 0, PF_B0 = 768, PF_B1 = 1024, PF_W4 = 1792, PF_B4 = 4864 };
 
 // Surrogate network (mlp.cu) and its path-finding pipeline buffers (pathfind.cu).
 int ensure_acts(rp_surrogate_s *s, long long n);
-int forward(rp_surrogate_s *s, long long n, const float *x, float *out, bool train,
-            cudaStream_t st);
 void free_pipe(rp_surrogate_s *s);
 int ensure_pack(rp_surrogate_s *s, cudaStream_t st);
 int forward_fused(rp_surrogate_s *s, long long n, const float *x, float *out, cudaStream_t st);
-int fused_status(rp_surrogate_s *s, cudaStream_t st);  // syncs st; RP_ERR_CUDA if flagged
-// training on the tensor cores (mlp_train_tc.cu): the hidden layers' forward (z = A W + b,
-// gelu(z)) or backward data pass (C = g W^T times gelu'(Zin)), and their weight gradients
+int fused_status(rp_surrogate_s *s, cudaStream_t st);  // syncs st; RP_ERR_TIMEOUT if flagged
+// training on the tensor cores: the fused forward pass with the loss and the last layer's
+// backward data pass, and the hidden layers' backward data chain (mlp_train_fused.cu); the
+// weight gradients of the hidden layers (mlp_train_tc.cu)
+int train_fwd(rp_surrogate_s *s, long long n, const float *x, const float *y, const float *t,
+              cudaStream_t st);
+int train_bwd(rp_surrogate_s *s, long long n, cudaStream_t st);
 int tc_pack_backward(const float *p, unsigned char *img, long long w1, long long w2, long long w3,
                      cudaStream_t st);
-int tc_dense(bool forward, const float *A, long long n, const unsigned char *Bimg,
-             const float *bias, const float *Zin, float *Zout, float *Out, int *flag,
-             long long wait, cudaStream_t st);
-int tc_wgrad(const float *H, const float *G, long long n, float *dW, float *db, int *flag,
-             long long wait, cudaStream_t st);
+struct WgradArgs {
+    const float *H[3], *G[3];  // per hidden layer: its input activations and output gradients
+    float *dW[3], *db[3];
+};
+int tc_wgrad3(const WgradArgs &a, long long n, int *flag, long long wait, cudaStream_t st);
 // the mbarrier wait limit of the surrogate's tensor-core kernels [SM cycles]
 long long wait_cycles(const rp_surrogate_s *s);
 int run_surrogate_paths(rp_surrogate_s *s, rp_medium_t m, int64_t n, const double *zs,

@@ -121,7 +121,8 @@ off = dict(no_fp64=True, no_grid=True, no_paths=True, no_surrogate=True, no_fig1
 bench.run_gpu(argparse.Namespace(gpus=int(os.environ.get("WORLD_SIZE", "1")), steps=2, warmup=3,
                                  impl="ours", paths_steps=1,
                                  rays=4096, sur_train=0, sur_queries=0, sur_check=0,
-                                 grid_steps=1, fp64_steps=1, cpu_sample=0, ref_sample=0, **off))
+                                 grid_steps=1, fp64_steps=1, cpu_sample=0, ref_sample=0,
+                                 no_tune=False, grid_rays=4_194_304, **off))
 '''
 
 
