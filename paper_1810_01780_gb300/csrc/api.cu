@@ -178,6 +178,15 @@ int build_surfaces(rp_medium_s *m, const rp_medium_desc *d)
         }
         RP_CUDA_TRY(cudaMemcpy(m->surf_dev, host.data(), total * sizeof(double),
                                cudaMemcpyHostToDevice));
+        std::vector<float> hostf(total);
+        for (size_t i = 0; i < total; ++i) hostf[i] = (float)host[i];
+        e = cudaMalloc(&m->surf_dev_f, total * sizeof(float));
+        if (e != cudaSuccess) {
+            m->surf_dev_f = nullptr;
+            return cuda_fail(e, "cudaMalloc(height fields)");
+        }
+        RP_CUDA_TRY(cudaMemcpy(m->surf_dev_f, hostf.data(), total * sizeof(float),
+                               cudaMemcpyHostToDevice));
     }
     at = 0;
     for (int j = 0; j < d->n_surfaces; ++j) {
@@ -186,9 +195,15 @@ int build_surfaces(rp_medium_s *m, const rp_medium_desc *d)
         B.on = 1;
         B.sx = -S.normal[0] / S.normal[2];
         B.sy = -S.normal[1] / S.normal[2];
+        B.sxh = (float)B.sx;
+        B.sxl = (float)(B.sx - (double)B.sxh);
+        B.syh = (float)B.sy;
+        B.syl = (float)(B.sy - (double)B.syh);
         B.h = nullptr;
+        B.hf = nullptr;
         if (S.height) {
             B.h = m->surf_dev + at;
+            B.hf = m->surf_dev_f + at;
             at += (size_t)S.nx * (size_t)S.ny;
             B.nx = S.nx;
             B.ny = S.ny;
@@ -196,6 +211,12 @@ int build_surfaces(rp_medium_s *m, const rp_medium_desc *d)
             B.oy = S.origin[1];
             B.dx = S.spacing[0];
             B.dy = S.spacing[1];
+            B.oxf = (float)B.ox;
+            B.oyf = (float)B.oy;
+            B.dxf = (float)B.dx;
+            B.dyf = (float)B.dy;
+            B.inv_dxf = (float)(1.0 / B.dx);
+            B.inv_dyf = (float)(1.0 / B.dy);
         }
     }
     m->n_surf = d->n_surfaces;
@@ -346,6 +367,7 @@ int rp_medium_create(const rp_medium_desc *d, void *stream, rp_medium_t *out)
         if (int rc = bind_device()) return rc;
         if (int rc = build_surfaces(m, d)) {
             if (m->surf_dev) cudaFree(m->surf_dev);
+            if (m->surf_dev_f) cudaFree(m->surf_dev_f);
             delete m;
             return rc;
         }
@@ -391,6 +413,7 @@ int rp_medium_destroy(rp_medium_t m)
     if (!m) return RP_OK;
     if (m->grid_dev) cudaFree(m->grid_dev);
     if (m->surf_dev) cudaFree(m->surf_dev);
+    if (m->surf_dev_f) cudaFree(m->surf_dev_f);
     delete m;
     return RP_OK;
 }

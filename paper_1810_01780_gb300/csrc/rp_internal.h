@@ -42,6 +42,7 @@ struct rp_medium_s {
     int n_surf;
     rpk::SurfB surf[RP_MAX_LAYERS];
     double *surf_dev;  // the height fields, one allocation
+    float *surf_dev_f; // the same in FP32 (the FP32-mixed event tests)
 };
 
 // Which instantiation of the tracer a medium takes.

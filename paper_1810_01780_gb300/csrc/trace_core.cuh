@@ -278,6 +278,10 @@ struct SurfB {
     const double *__restrict__ h;
     int32_t on, nx, ny, pad;
     double sx, sy, ox, oy, dx, dy;
+    // the same in FP32 for the FP32-mixed event tests: the heights, the slopes as float-float
+    // pairs, the node origin, spacing and its inverse
+    const float *__restrict__ hf;
+    float sxh, sxl, syh, syl, oxf, oyf, dxf, dyf, inv_dxf, inv_dyf;
 };
 
 // A layered medium whose inner boundaries may be tilted planes or height-field surfaces.
@@ -1026,9 +1030,71 @@ __device__ __forceinline__ typename P::R event_g(const MediumSpheres &m, const L
     return event_g<P>(static_cast<const MediumLayered &>(m), L, sp, kind, dr);
 }
 
+// Bilinear height field of SurfB B at the point x = xh + xl, y = yh + yl (float-float), in FP32:
+// the cell is found from the point's offset from the node origin, and the offset within the
+// cell is formed exactly (TwoSum, FMA residual) before it is scaled, so that the interpolation
+// weights are accurate to ~1e-7 of a cell whatever the distance from the origin; held at the
+// edge values beyond the nodes, as the FP64 form.
+__device__ __forceinline__ float cell_coord(float ph, float pl, float o, float d, float inv_d,
+                                            int n, int &i)
+{
+    float a, e;
+    two_sum(ph, -o, a, e);
+    e += pl;
+    const float u = (a + e) * inv_d;
+    if (!(u > 0.0f)) {  // below the first node (or NaN): the edge value
+        i = 0;
+        return 0.0f;
+    }
+    if (u >= (float)(n - 1)) {
+        i = n - 2;
+        return 1.0f;
+    }
+    i = min((int)floorf(u), n - 2);
+    const float c = (float)i * d, ce = fmaf((float)i, d, -c);  // i d = c + ce exactly
+    const float f = (((a - c) - ce) + e) * inv_d;
+    return fminf(fmaxf(f, 0.0f), 1.0f);
+}
+
+__device__ __forceinline__ float height_ff(const SurfB &B, float xh, float xl, float yh, float yl)
+{
+    int i, j;
+    const float fu = cell_coord(xh, xl, B.oxf, B.dxf, B.inv_dxf, B.nx, i);
+    const float fv = cell_coord(yh, yl, B.oyf, B.dyf, B.inv_dyf, B.ny, j);
+    const float *r0 = B.hf + (size_t)j * B.nx + i, *r1 = r0 + B.nx;
+    const float gu = 1.0f - fu, gv = 1.0f - fv;
+    return gv * (gu * __ldg(r0) + fu * __ldg(r0 + 1)) + fv * (gu * __ldg(r1) + fu * __ldg(r1 + 1));
+}
+
+// Vertical offset z - zb(x, y) of the candidate point r + dr from boundary k, for the
+// FP32-mixed policy: float-float arithmetic on the FP32 pipe (TwoSum for the large terms
+// z - z_top - s_x x - s_y y, which nearly cancel near the surface; FMA residuals of the slope
+// products), the height field in FP32 relative to its cell.
+__device__ __forceinline__ float surf_offset_ff(const MediumSurfaces &m, int k,
+                                                const PrecF32::V &r, const float dr[3])
+{
+    const SurfB &B = m.B[k];
+    const PlaneC &zt = m.top[k];
+    float s, e, p, pe, s2, e2;
+    two_sum(r.hi[2], -zt.hi, s, e);
+    float small = e + (r.lo[2] - zt.lo) + dr[2];
+    p = B.sxh * r.hi[0];
+    pe = fmaf(B.sxh, r.hi[0], -p);
+    two_sum(s, -p, s2, e2);
+    small += e2 - pe - (B.sxh * (r.lo[0] + dr[0]) + B.sxl * r.hi[0]);
+    p = B.syh * r.hi[1];
+    pe = fmaf(B.syh, r.hi[1], -p);
+    two_sum(s2, -p, s, e);
+    small += e - pe - (B.syh * (r.lo[1] + dr[1]) + B.syl * r.hi[1]);
+    float g = s + small;
+    if (B.hf) g -= height_ff(B, r.hi[0], r.lo[0] + dr[0], r.hi[1], r.lo[1] + dr[1]);
+    return g;
+}
+
 // Signed vertical offset from a layer boundary of a medium with surfaces, positive on the
-// ray's own side (z - zb below the boundary, zb - z above it), for the candidate r + dr; in
-// FP64 in both policies (horizontal planes keep the plane form).
+// ray's own side (z - zb below the boundary, zb - z above it), for the candidate r + dr: in
+// FP64 with the FP64 reference's operations (FP64 policy), in float-float on the FP32 pipe
+// (FP32-mixed policy); horizontal planes keep the plane form.
 template <class P>
 __device__ __forceinline__ typename P::R event_g(const MediumSurfaces &m, const Lane<P> &L,
                                                  const StepParams<P> &sp, int kind,
@@ -1037,11 +1103,16 @@ __device__ __forceinline__ typename P::R event_g(const MediumSurfaces &m, const 
     if (kind == EV_TOP || kind == EV_BOTTOM) {
         const int k = (kind == EV_TOP) ? L.layer : L.layer + 1;
         if (surf_on(m, k)) {
-            const double x = P::get(L.r, 0) + (double)dr[0];
-            const double y = P::get(L.r, 1) + (double)dr[1];
-            const double z = P::get(L.r, 2) + (double)dr[2];
-            const double zb = surf_depth(m, k, x, y, nullptr, nullptr);
-            return (typename P::R)((kind == EV_TOP) ? __dsub_rn(z, zb) : __dsub_rn(zb, z));
+            if constexpr (P::kFF) {
+                const float g = surf_offset_ff(m, k, L.r, dr);
+                return (kind == EV_TOP) ? g : -g;
+            } else {
+                const double x = P::get(L.r, 0) + (double)dr[0];
+                const double y = P::get(L.r, 1) + (double)dr[1];
+                const double z = P::get(L.r, 2) + (double)dr[2];
+                const double zb = surf_depth(m, k, x, y, nullptr, nullptr);
+                return (typename P::R)((kind == EV_TOP) ? __dsub_rn(z, zb) : __dsub_rn(zb, z));
+            }
         }
     }
     return event_g<P>(static_cast<const MediumLayered &>(m), L, sp, kind, dr);
