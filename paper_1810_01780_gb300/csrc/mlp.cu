@@ -21,107 +21,110 @@
 namespace {
 
 constexpr int kLayers = 5;
-constexpr int kDims[kLayers + 1] = {3, 256, 256, 256, 256, 12};
+// widths of the network's layers: 3 -> 256 -> 256 -> 256 -> 256 -> 12
+__host__ __device__ constexpr int kDim(int i) { return i == 0 ? 3 : (i == kLayers ? 12 : 256); }
 
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 // Weight and bias gradients of the thin layers, on the CUDA cores (BF16-rounded operands,
-// FP32 products and sums, as in the forward pass; bias gradients from the unrounded g):
-//   last layer (256 -> 12): dW[i][o] = sum_s H[s][i] g[s][o], db[o] = sum_s g[s][o]
+// FP32 products and sums, as in the forward pass; bias gradients from the unrounded g), one
+// launch for both (blockIdx.y):
+//   y = 0, last layer (256 -> 12): dW[i][o] = sum_s H[s][i] g[s][o], db[o] = sum_s g[s][o]
 //     (thread i; the CTA's rows of g staged in shared memory);
-//   first layer (3 -> 256): dW[i][j] = sum_s x[s][i] g[s][j], db[j] = sum_s g[s][j]
+//   y = 1, first layer (3 -> 256): dW[i][j] = sum_s x[s][i] g[s][j], db[j] = sum_s g[s][j]
 //     (thread j; the CTA's rows of x staged in shared memory).
-// Each CTA takes kThinChunk rows and writes its sums to its row of a partial-sum buffer
-// (dW then db, kThinPart floats at most); k_sum_parts adds the rows in a fixed order, so
-// these gradients do not depend on scheduling.
+// Each CTA takes kThinChunk rows and writes its sums to its row of its layer's partial-sum
+// block (dW then db); k_sum_parts adds the rows in a fixed order, so these gradients do not
+// depend on scheduling.
 constexpr int kThinChunk = 64;
-constexpr int kThinPart = 256 * 12 + 12 > 3 * 256 + 256 ? 256 * 12 + 12 : 3 * 256 + 256;
-__global__ void __launch_bounds__(256) k_wgrad_last(const float *__restrict__ H,
-                                                    const float *__restrict__ G, long long n,
+constexpr int kThinLast = 256 * 12 + 12, kThinFirst = 3 * 256 + 256;
+constexpr int kThinPart = kThinLast > kThinFirst ? kThinLast : kThinFirst;
+__global__ void __launch_bounds__(256) k_wgrad_thin(const float *__restrict__ H4,
+                                                    const float *__restrict__ G4,
+                                                    const float *__restrict__ X,
+                                                    const float *__restrict__ G0, long long n,
                                                     float *__restrict__ part)
 {
     __shared__ float gr[kThinChunk * 12], gb[kThinChunk * 12];
     const int i = threadIdx.x;
     const long long r0 = (long long)blockIdx.x * kThinChunk;
     const int rows = (int)min((long long)kThinChunk, n - r0);
-    for (int e = i; e < kThinChunk * 12; e += 256) {
-        const float v = e / 12 < rows ? G[(r0 + e / 12) * 12 + e % 12] : 0.0f;
-        gr[e] = v;
-        gb[e] = bf16r(v);
-    }
-    __syncthreads();
-    float acc[12];
+    float *p = part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kThinPart;
+    if (blockIdx.y == 0) {
+        for (int e = i; e < kThinChunk * 12; e += 256) {
+            const float v = e / 12 < rows ? G4[(r0 + e / 12) * 12 + e % 12] : 0.0f;
+            gr[e] = v;
+            gb[e] = bf16r(v);
+        }
+        __syncthreads();
+        float acc[12];
 #pragma unroll
-    for (int o = 0; o < 12; ++o) acc[o] = 0.0f;
+        for (int o = 0; o < 12; ++o) acc[o] = 0.0f;
 #pragma unroll 4
-    for (int r = 0; r < rows; ++r) {
-        const float h = bf16r(H[(r0 + r) * 256 + i]);
+        for (int r = 0; r < rows; ++r) {
+            const float h = bf16r(H4[(r0 + r) * 256 + i]);
 #pragma unroll
-        for (int o = 0; o < 12; ++o) acc[o] = fmaf(h, gb[r * 12 + o], acc[o]);
-    }
-    float *p = part + (size_t)blockIdx.x * kThinPart;
+            for (int o = 0; o < 12; ++o) acc[o] = fmaf(h, gb[r * 12 + o], acc[o]);
+        }
 #pragma unroll
-    for (int o = 0; o < 12; ++o) p[i * 12 + o] = acc[o];
-    if (i < 12) {
-        float s = 0.0f;
-        for (int r = 0; r < rows; ++r) s += gr[r * 12 + i];
-        p[256 * 12 + i] = s;
+        for (int o = 0; o < 12; ++o) p[i * 12 + o] = acc[o];
+        if (i < 12) {
+            float s = 0.0f;
+            for (int r = 0; r < rows; ++r) s += gr[r * 12 + i];
+            p[256 * 12 + i] = s;
+        }
+        return;
     }
-}
-__global__ void __launch_bounds__(256) k_wgrad_first(const float *__restrict__ X,
-                                                     const float *__restrict__ G, long long n,
-                                                     float *__restrict__ part)
-{
-    __shared__ float xb[kThinChunk * 3];
-    const int j = threadIdx.x;
-    const long long r0 = (long long)blockIdx.x * kThinChunk;
-    const int rows = (int)min((long long)kThinChunk, n - r0);
-    for (int e = j; e < kThinChunk * 3; e += 256)
+    float *xb = gr;  // the CTA's rows of x, BF16-rounded
+    for (int e = i; e < kThinChunk * 3; e += 256)
         xb[e] = e / 3 < rows ? bf16r(X[(r0 + e / 3) * 3 + e % 3]) : 0.0f;
     __syncthreads();
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, s = 0.0f;
 #pragma unroll 4
     for (int r = 0; r < rows; ++r) {
-        const float g = G[(r0 + r) * 256 + j];
+        const float g = G0[(r0 + r) * 256 + i];
         s += g;
         const float b = bf16r(g);
         a0 = fmaf(xb[r * 3], b, a0);
         a1 = fmaf(xb[r * 3 + 1], b, a1);
         a2 = fmaf(xb[r * 3 + 2], b, a2);
     }
-    float *p = part + (size_t)blockIdx.x * kThinPart;
-    p[j] = a0;
-    p[256 + j] = a1;
-    p[512 + j] = a2;
-    p[768 + j] = s;
+    p[i] = a0;
+    p[256 + i] = a1;
+    p[512 + i] = a2;
+    p[768 + i] = s;
 }
-// dW[e] += sum over CTAs c of part[c][e] for e < nw, and db[e - nw] for nw <= e < nw + nb
-__global__ void k_sum_parts(const float *__restrict__ part, int n_parts, int nw, int nb,
-                            float *__restrict__ dW, float *__restrict__ db)
+// Both thin layers' sums over the CTAs' partial sums, in CTA order: element e < kThinLast of
+// the last layer's block (dW4 then db4), then the first layer's (dW0 then db0).
+__global__ void k_sum_parts(const float *__restrict__ part, int n_parts, float *__restrict__ dW4,
+                            float *__restrict__ db4, float *__restrict__ dW0,
+                            float *__restrict__ db0)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nw + nb) return;
-    float s = 0.0f;
-    for (int c = 0; c < n_parts; ++c) s += part[(size_t)c * kThinPart + e];
-    if (e < nw)
-        dW[e] += s;
-    else
-        db[e - nw] += s;
-}
-
-__global__ void k_adam(float *p, __nv_bfloat16 *pb, const float *gr, float *m, float *v,
-                       long long n, float lr, float c1, float c2)
-{
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float g = gr[i];
-    const float mi = 0.9f * m[i] + 0.1f * g;
-    const float vi = 0.999f * v[i] + 0.001f * g * g;
-    m[i] = mi;
-    v[i] = vi;
-    const float pi = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
-    p[i] = pi;
-    pb[i] = __float2bfloat16_rn(pi);
+    if (e >= kThinLast + kThinFirst) return;
+    const int y = e < kThinLast ? 0 : 1, f = y ? e - kThinLast : e;
+    const float *src = part + (size_t)y * n_parts * kThinPart + f;
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;  // four independent chains, then in order
+    int c = 0;
+    for (; c + 4 <= n_parts; c += 4) {
+        s0 += src[(size_t)c * kThinPart];
+        s1 += src[(size_t)(c + 1) * kThinPart];
+        s2 += src[(size_t)(c + 2) * kThinPart];
+        s3 += src[(size_t)(c + 3) * kThinPart];
+    }
+    for (; c < n_parts; ++c) s0 += src[(size_t)c * kThinPart];
+    const float s = (s0 + s1) + (s2 + s3);
+    if (y == 0) {
+        if (f < 256 * 12)
+            dW4[f] += s;
+        else
+            db4[f - 256 * 12] += s;
+    } else {
+        if (f < 3 * 256)
+            dW0[f] += s;
+        else
+            db0[f - 3 * 256] += s;
+    }
 }
 
 __global__ void k_to_bf16(const float *p, __nv_bfloat16 *pb, long long n)
@@ -130,13 +133,16 @@ __global__ void k_to_bf16(const float *p, __nv_bfloat16 *pb, long long n)
     if (i < n) pb[i] = __float2bfloat16_rn(p[i]);
 }
 
-long long layer_w(int l)
+__host__ __device__ constexpr long long layer_w(int l)
 {
     long long o = 0;
-    for (int i = 0; i < l; ++i) o += (long long)kDims[i] * kDims[i + 1] + kDims[i + 1];
+    for (int i = 0; i < l; ++i) o += (long long)kDim(i) * kDim(i + 1) + kDim(i + 1);
     return o;
 }
-long long layer_b(int l) { return layer_w(l) + (long long)kDims[l] * kDims[l + 1]; }
+__host__ __device__ constexpr long long layer_b(int l)
+{
+    return layer_w(l) + (long long)kDim(l) * kDim(l + 1);
+}
 
 struct LayerOffs {
     long long w[kLayers], b[kLayers];  // offsets of W_l and b_l in the flat parameter vector
@@ -175,6 +181,62 @@ __global__ void k_pack(const float *__restrict__ p, unsigned char *__restrict__ 
 }
 long long n_params() { return layer_w(kLayers); }
 
+// One Adam step that also leaves behind what the next training step reads: the BF16 copy of
+// the weights, both operand images of the hidden layers (the inference pack of k_pack and the
+// backward image of k_pack_t, same layouts) and the pack's FP32 block, the gradient zeroed for
+// the next accumulation, and, for acc != 0, the epoch's loss sum loss[1] += loss[0] acc, with
+// loss[0] zeroed.  The pack's padding (after b4) is never written here: zero since the pack
+// was allocated.
+__global__ void k_adam_pack(float *__restrict__ p, __nv_bfloat16 *__restrict__ pb,
+                            float *__restrict__ gr, float *__restrict__ m, float *__restrict__ v,
+                            long long n, float lr, float c1, float c2,
+                            unsigned char *__restrict__ pack, unsigned char *__restrict__ pack_t,
+                            double *loss, double acc)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i == 0) {
+        if (acc != 0.0) loss[1] += loss[0] * acc;
+        loss[0] = 0.0;
+    }
+    if (i >= n) return;
+    const float g = gr[i];
+    const float mi = 0.9f * m[i] + 0.1f * g;
+    const float vi = 0.999f * v[i] + 0.001f * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+    p[i] = pi;
+    const __nv_bfloat16 b = __float2bfloat16_rn(pi);
+    pb[i] = b;
+    gr[i] = 0.0f;
+    float *pf = reinterpret_cast<float *>(pack + 3 * kPackW);
+    constexpr long long kW1 = layer_w(1), kW4 = layer_w(4), kHidden = 256LL * 256 + 256;
+    if (i < kW1) {  // W0 (BF16-rounded), b0
+        if (i < 3 * 256)
+            pf[rph::PF_W0 + i] = __bfloat162float(b);
+        else
+            pf[rph::PF_B0 + (i - 3 * 256)] = pi;
+    } else if (i < kW4) {  // W1..W3 as both images, b1..b3
+        const int l = (int)((i - kW1) / kHidden), e = (int)((i - kW1) % kHidden);
+        if (e < 65536) {
+            const int row = e >> 8, col = e & 255;  // W[row][col]: input row, output col
+            *(__nv_bfloat16 *)(pack + l * kPackW + ((row >> 3) * 32 + (col >> 3)) * 128 +
+                               (col & 7) * 16 + (row & 7) * 2) = b;
+            *(__nv_bfloat16 *)(pack_t + l * kPackW + ((col >> 3) * 32 + (row >> 3)) * 128 +
+                               (row & 7) * 16 + (col & 7) * 2) = b;
+        } else {
+            pf[rph::PF_B1 + l * 256 + (e - 65536)] = pi;
+        }
+    } else {  // W4 (BF16-rounded), b4
+        const int e = (int)(i - kW4);
+        if (e < 256 * 12)
+            pf[rph::PF_W4 + e] = __bfloat162float(b);
+        else
+            pf[rph::PF_B4 + (e - 256 * 12)] = pi;
+    }
+}
+
+
 }  // namespace
 
 namespace rph {
@@ -209,7 +271,7 @@ int ensure_acts(rp_surrogate_s *s, long long n)
     for (int l = 1; l < 5; ++l) RP_CUDA_TRY(cudaMalloc(&s->H[l], sizeof(float) * cap * 256));
     RP_CUDA_TRY(cudaMalloc(&s->out, sizeof(float) * cap * 12));
     for (int l = 0; l < 4; ++l) RP_CUDA_TRY(cudaMalloc(&s->gl[l], sizeof(float) * cap * 256));
-    RP_CUDA_TRY(cudaMalloc(&s->part, sizeof(float) * (size_t)((cap + kThinChunk - 1) / kThinChunk) * kThinPart));
+    RP_CUDA_TRY(cudaMalloc(&s->part, sizeof(float) * 2 * (size_t)((cap + kThinChunk - 1) / kThinChunk) * kThinPart));
     s->cap = cap;
     return RP_OK;
 }
@@ -224,8 +286,11 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
     int rc = ensure_acts(s, n);
     if (rc) return rc;
     if ((rc = ensure_pack(s, st))) return rc;
-    RP_CUDA_TRY(cudaMemsetAsync(s->loss, 0, sizeof(double), st));
-    RP_CUDA_TRY(cudaMemsetAsync(s->grad, 0, sizeof(float) * n_params(), st));
+    if (!s->clean) {  // the fused Adam step leaves both zeroed
+        RP_CUDA_TRY(cudaMemsetAsync(s->loss, 0, sizeof(double), st));
+        RP_CUDA_TRY(cudaMemsetAsync(s->grad, 0, sizeof(float) * n_params(), st));
+    }
+    s->clean = false;
     if ((rc = train_fwd(s, n, x, y, t, st))) return rc;
     if ((rc = train_bwd(s, n, st))) return rc;
     WgradArgs wa;
@@ -236,15 +301,13 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
         wa.db[l - 1] = s->grad + layer_b(l);
     }
     if ((rc = tc_wgrad3(wa, n, s->fflag, wait_cycles(s), st))) return rc;
-    // thin weight gradients: one 64-row chunk per CTA, then a fixed-order sum of the CTAs'
-    // partial sums
+    // thin weight gradients: one 64-row chunk per CTA and layer, then a fixed-order sum of
+    // the CTAs' partial sums
     const unsigned thin_grid = (unsigned)((n + kThinChunk - 1) / kThinChunk);
-    k_wgrad_last<<<thin_grid, 256, 0, st>>>(s->H[4], s->out, n, s->part);
-    k_sum_parts<<<(256 * 12 + 12 + 255) / 256, 256, 0, st>>>(
-        s->part, (int)thin_grid, 256 * 12, 12, s->grad + layer_w(4), s->grad + layer_b(4));
-    k_wgrad_first<<<thin_grid, 256, 0, st>>>(x, s->gl[0], n, s->part);
-    k_sum_parts<<<(3 * 256 + 256 + 255) / 256, 256, 0, st>>>(
-        s->part, (int)thin_grid, 3 * 256, 256, s->grad + layer_w(0), s->grad + layer_b(0));
+    k_wgrad_thin<<<dim3(thin_grid, 2), 256, 0, st>>>(s->H[4], s->out, x, s->gl[0], n, s->part);
+    k_sum_parts<<<(kThinLast + kThinFirst + 255) / 256, 256, 0, st>>>(
+        s->part, (int)thin_grid, s->grad + layer_w(4), s->grad + layer_b(4), s->grad + layer_w(0),
+        s->grad + layer_b(0));
     RP_CUDA_TRY(cudaGetLastError());
     if (loss_host) {
         RP_CUDA_TRY(cudaMemcpyAsync(loss_host, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -256,13 +319,11 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
 
 long long wait_cycles(const rp_surrogate_s *s) { return s->wait > 0 ? s->wait : tc::kWaitCycles; }
 
-// loss[1] += loss[0] / n: the running sum of batch losses of an epoch
-__global__ void k_acc_loss(double *loss, double inv_n) { loss[1] += loss[0] * inv_n; }
-
 int ensure_pack(rp_surrogate_s *s, cudaStream_t st)
 {
     if (!s->pack) {
         RP_CUDA_TRY(cudaMalloc(&s->pack, 3 * kPackW + sizeof(float) * kPackF));
+        RP_CUDA_TRY(cudaMemsetAsync(s->pack, 0, 3 * kPackW + sizeof(float) * kPackF, st));
         s->pack_version = -1;
     }
     if (!s->pack_t) {
@@ -284,16 +345,23 @@ int ensure_pack(rp_surrogate_s *s, cudaStream_t st)
     return RP_OK;
 }
 
-// one Adam step at learning rate lr on the gradient in s->grad
-static int adam_step(rp_surrogate_s *s, float lr, cudaStream_t st)
+// One Adam step at learning rate lr on the gradient in s->grad.  The fused kernel brings the
+// operand images (current before the step: ensure_pack) and the BF16 copy to the new weights
+// and zeroes the gradient and the batch loss in the same pass; acc != 0 also adds the batch
+// loss, scaled by acc, to the epoch's sum.
+static int adam_step(rp_surrogate_s *s, float lr, double acc, cudaStream_t st)
 {
     s->step += 1;
-    s->version += 1;
     const float c1 = (float)(1.0 / (1.0 - pow(0.9, (double)s->step)));
     const float c2 = (float)(1.0 / (1.0 - pow(0.999, (double)s->step)));
     const long long np = n_params();
-    k_adam<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(s->p, s->pb, s->grad, s->m, s->v, np, lr,
-                                                          c1, c2);
+    int rc = ensure_pack(s, st);  // current after a loss_grad: then a no-op
+    if (rc) return rc;
+    s->version += 1;
+    k_adam_pack<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(
+        s->p, s->pb, s->grad, s->m, s->v, np, lr, c1, c2, s->pack, s->pack_t, s->loss, acc);
+    s->pack_version = s->version;
+    s->clean = true;
     RP_CUDA_TRY(cudaGetLastError());
     return RP_OK;
 }
@@ -452,7 +520,7 @@ int rp_surrogate_train_step(rp_surrogate_t s, int64_t n, const float *x, const f
     RP_CUDA_TRY(cudaMemsetAsync(s->fflag, 0, sizeof(int), st));
     int rc = loss_grad(s, n, x, y, t, loss, st);
     if (rc) return rc;
-    if ((rc = adam_step(s, lr, st))) return rc;
+    if ((rc = adam_step(s, lr, 0.0, st))) return rc;
     if (!loss) return fused_status(s, st);  // syncs st
     return RP_OK;
 }
@@ -486,9 +554,7 @@ int rp_surrogate_train(rp_surrogate_t s, int64_t n, const float *x, const float 
             const double c = 0.5 * (1.0 + cos(3.14159265358979323846 * (double)k / total));
             const float lr = (float)(p->lr_final + (p->lr - p->lr_final) * c);
             if ((rc = loss_grad(s, B, x + 3 * r0, y + 2 * r0, t + 10 * r0, nullptr, st))) return rc;
-            k_acc_loss<<<1, 1, 0, st>>>(s->loss, 1.0 / ((double)B * (double)nb));
-            RP_CUDA_TRY(cudaGetLastError());
-            if ((rc = adam_step(s, lr, st))) return rc;
+            if ((rc = adam_step(s, lr, 1.0 / ((double)B * (double)nb), st))) return rc;
         }
     }
     double L = 0.0;

@@ -30,6 +30,7 @@ struct rp_surrogate_s {
     long long version, pack_version;
     int *fflag;  // set by a tensor-core kernel when a bounded wait gave up
     long long wait;  // SM cycles a tensor-core kernel waits on an mbarrier; 0: the default
+    bool clean;      // the gradient and the batch loss are zero (as the fused Adam step leaves them)
 };
 
 struct rp_medium_s {
