@@ -26,24 +26,31 @@ __host__ __device__ constexpr int kDim(int i) { return i == 0 ? 3 : (i == kLayer
 
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
-// Weight and bias gradients of the thin layers, on the CUDA cores (BF16-rounded operands,
-// FP32 products and sums, as in the forward pass; bias gradients from the unrounded g), one
-// launch for both (blockIdx.y):
-//   y = 0, last layer (256 -> 12): dW[i][o] = sum_s H[s][i] g[s][o], db[o] = sum_s g[s][o]
-//     (thread i; the CTA's rows of g staged in shared memory);
-//   y = 1, first layer (3 -> 256): dW[i][j] = sum_s x[s][i] g[s][j], db[j] = sum_s g[s][j]
-//     (thread j; the CTA's rows of x staged in shared memory).
-// Each CTA takes kThinChunk rows and writes its sums to its row of its layer's partial-sum
-// block (dW then db); k_sum_parts adds the rows in a fixed order, so these gradients do not
-// depend on scheduling.
+// Weight gradients of the thin layers (and the last layer's bias gradient), on the CUDA cores
+// (BF16-rounded operands, FP32 products and sums, as in the forward pass), one launch for
+// both (blockIdx.y):
+//   y = 0, last layer (256 -> 12): dW[i][o] = sum_s H4[s][i] g4[s][o], db[o] = sum_s g4[s][o]
+//     (unrounded g4) (thread i; the CTA's rows of g4 staged in shared memory);
+//   y = 1, first layer (3 -> 256): dW[i][j] = sum_s x[s][i] g0[s][j] (thread j; the CTA's rows
+//     of x staged in shared memory; db0 is summed by the backward pass).
+// H4 and g0 are read from their BF16 operand images (already rounded).  Each CTA takes
+// kThinChunk rows (within one 128-row tile) and writes its sums to its row of its layer's
+// partial-sum block (dW then db); k_sum_parts adds the rows in a fixed order, so these
+// gradients do not depend on scheduling.
 constexpr int kThinChunk = 64;
-constexpr int kThinLast = 256 * 12 + 12, kThinFirst = 3 * 256 + 256;
+constexpr int kThinLast = 256 * 12 + 12, kThinFirst = 3 * 256;
 constexpr int kThinPart = kThinLast > kThinFirst ? kThinLast : kThinFirst;
-__global__ void __launch_bounds__(256) k_wgrad_thin(const float *__restrict__ H4,
+// the BF16 element (row r, column j) of an operand image buffer, as float
+__device__ __forceinline__ float img_at(const unsigned char *img, long long r, int j)
+{
+    const unsigned char *p = img + (r >> 7) * (long long)rph::tc::kImage + rph::tc::a_off((int)(r & 127), j & ~7) + (j & 7) * 2;
+    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(p));
+}
+__global__ void __launch_bounds__(256) k_wgrad_thin(const unsigned char *__restrict__ H4,
                                                     const float *__restrict__ G4,
                                                     const float *__restrict__ X,
-                                                    const float *__restrict__ G0, long long n,
-                                                    float *__restrict__ part)
+                                                    const unsigned char *__restrict__ G0,
+                                                    long long n, float *__restrict__ part)
 {
     __shared__ float gr[kThinChunk * 12], gb[kThinChunk * 12];
     const int i = threadIdx.x;
@@ -62,7 +69,7 @@ __global__ void __launch_bounds__(256) k_wgrad_thin(const float *__restrict__ H4
         for (int o = 0; o < 12; ++o) acc[o] = 0.0f;
 #pragma unroll 4
         for (int r = 0; r < rows; ++r) {
-            const float h = bf16r(H4[(r0 + r) * 256 + i]);
+            const float h = img_at(H4, r0 + r, i);
 #pragma unroll
             for (int o = 0; o < 12; ++o) acc[o] = fmaf(h, gb[r * 12 + o], acc[o]);
         }
@@ -79,12 +86,10 @@ __global__ void __launch_bounds__(256) k_wgrad_thin(const float *__restrict__ H4
     for (int e = i; e < kThinChunk * 3; e += 256)
         xb[e] = e / 3 < rows ? bf16r(X[(r0 + e / 3) * 3 + e % 3]) : 0.0f;
     __syncthreads();
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, s = 0.0f;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
 #pragma unroll 4
     for (int r = 0; r < rows; ++r) {
-        const float g = G0[(r0 + r) * 256 + i];
-        s += g;
-        const float b = bf16r(g);
+        const float b = img_at(G0, r0 + r, i);
         a0 = fmaf(xb[r * 3], b, a0);
         a1 = fmaf(xb[r * 3 + 1], b, a1);
         a2 = fmaf(xb[r * 3 + 2], b, a2);
@@ -92,13 +97,11 @@ __global__ void __launch_bounds__(256) k_wgrad_thin(const float *__restrict__ H4
     p[i] = a0;
     p[256 + i] = a1;
     p[512 + i] = a2;
-    p[768 + i] = s;
 }
 // Both thin layers' sums over the CTAs' partial sums, in CTA order: element e < kThinLast of
-// the last layer's block (dW4 then db4), then the first layer's (dW0 then db0).
+// the last layer's block (dW4 then db4), then the first layer's (dW0).
 __global__ void k_sum_parts(const float *__restrict__ part, int n_parts, float *__restrict__ dW4,
-                            float *__restrict__ db4, float *__restrict__ dW0,
-                            float *__restrict__ db0)
+                            float *__restrict__ db4, float *__restrict__ dW0)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= kThinLast + kThinFirst) return;
@@ -120,10 +123,7 @@ __global__ void k_sum_parts(const float *__restrict__ part, int n_parts, float *
         else
             db4[f - 256 * 12] += s;
     } else {
-        if (f < 3 * 256)
-            dW0[f] += s;
-        else
-            db0[f - 3 * 256] += s;
+        dW0[f] += s;
     }
 }
 
@@ -243,7 +243,7 @@ namespace rph {
 
 static void free_acts(rp_surrogate_s *s)
 {
-    for (int l = 0; l < 4; ++l) {
+    for (int l = 0; l < 3; ++l) {
         cudaFree(s->Z[l]);
         s->Z[l] = nullptr;
     }
@@ -251,11 +251,11 @@ static void free_acts(rp_surrogate_s *s)
         cudaFree(s->H[l]);
         s->H[l] = nullptr;
     }
-    cudaFree(s->out);
     for (int l = 0; l < 4; ++l) {
         cudaFree(s->gl[l]);
         s->gl[l] = nullptr;
     }
+    cudaFree(s->out);
     cudaFree(s->part);
     s->out = s->part = nullptr;
     s->cap = 0;
@@ -267,10 +267,11 @@ int ensure_acts(rp_surrogate_s *s, long long n)
     RP_CUDA_TRY(cudaDeviceSynchronize());
     free_acts(s);
     const long long cap = n + n / 4;
-    for (int l = 0; l < 4; ++l) RP_CUDA_TRY(cudaMalloc(&s->Z[l], sizeof(float) * cap * 256));
-    for (int l = 1; l < 5; ++l) RP_CUDA_TRY(cudaMalloc(&s->H[l], sizeof(float) * cap * 256));
+    const size_t tiles = (size_t)((cap + 127) / 128);
+    for (int l = 0; l < 3; ++l) RP_CUDA_TRY(cudaMalloc(&s->Z[l], tiles * 128 * 256 * sizeof(float)));
+    for (int l = 1; l < 5; ++l) RP_CUDA_TRY(cudaMalloc(&s->H[l], tiles * rph::tc::kImage));
+    for (int l = 0; l < 4; ++l) RP_CUDA_TRY(cudaMalloc(&s->gl[l], tiles * rph::tc::kImage));
     RP_CUDA_TRY(cudaMalloc(&s->out, sizeof(float) * cap * 12));
-    for (int l = 0; l < 4; ++l) RP_CUDA_TRY(cudaMalloc(&s->gl[l], sizeof(float) * cap * 256));
     RP_CUDA_TRY(cudaMalloc(&s->part, sizeof(float) * 2 * (size_t)((cap + kThinChunk - 1) / kThinChunk) * kThinPart));
     s->cap = cap;
     return RP_OK;
@@ -291,14 +292,14 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
         RP_CUDA_TRY(cudaMemsetAsync(s->grad, 0, sizeof(float) * n_params(), st));
     }
     s->clean = false;
-    if ((rc = train_fwd(s, n, x, y, t, st))) return rc;
-    if ((rc = train_bwd(s, n, st))) return rc;
+    if ((rc = train_fwd(s, n, x, y, t, s->grad + layer_b(3), st))) return rc;
+    if ((rc = train_bwd(s, n, s->grad + layer_b(2), s->grad + layer_b(1), s->grad + layer_b(0), st)))
+        return rc;
     WgradArgs wa;
     for (int l = 1; l <= 3; ++l) {  // layer l: input H_l, output gradient g_l
         wa.H[l - 1] = s->H[l];
         wa.G[l - 1] = s->gl[l];
         wa.dW[l - 1] = s->grad + layer_w(l);
-        wa.db[l - 1] = s->grad + layer_b(l);
     }
     if ((rc = tc_wgrad3(wa, n, s->fflag, wait_cycles(s), st))) return rc;
     // thin weight gradients: one 64-row chunk per CTA and layer, then a fixed-order sum of
@@ -306,8 +307,7 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
     const unsigned thin_grid = (unsigned)((n + kThinChunk - 1) / kThinChunk);
     k_wgrad_thin<<<dim3(thin_grid, 2), 256, 0, st>>>(s->H[4], s->out, x, s->gl[0], n, s->part);
     k_sum_parts<<<(kThinLast + kThinFirst + 255) / 256, 256, 0, st>>>(
-        s->part, (int)thin_grid, s->grad + layer_w(4), s->grad + layer_b(4), s->grad + layer_w(0),
-        s->grad + layer_b(0));
+        s->part, (int)thin_grid, s->grad + layer_w(4), s->grad + layer_b(4), s->grad + layer_w(0));
     RP_CUDA_TRY(cudaGetLastError());
     if (loss_host) {
         RP_CUDA_TRY(cudaMemcpyAsync(loss_host, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st));

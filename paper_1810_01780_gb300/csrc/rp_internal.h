@@ -18,9 +18,13 @@ struct rp_surrogate_s {
     long long step;
     float *p, *m, *v, *grad;
     __nv_bfloat16 *pb;
-    // activations for a batch of up to `cap` rows
+    // training buffers for a batch of up to `cap` rows, per 128-row tile: the pre-activations
+    // z0..z2 (FP32, tiled), the activations H1..H4 and the gradients g0..g3 as BF16 operand
+    // images (64 KB per tile; H[0] unused), and g4 (FP32, 12 per row)
     long long cap;
-    float *Z[4], *H[5], *out, *gl[4];  // pre-activations, activations, g4, g0..g3
+    float *Z[3];
+    unsigned char *H[5], *gl[4];
+    float *out;
     float *part;  // per-CTA partial sums of the thin layers' weight and bias gradients
     double *loss;
     void *pipe;  // buffers of the surrogate path-finding pipeline (pathfind.cu)
@@ -175,16 +179,18 @@ int ensure_pack(rp_surrogate_s *s, cudaStream_t st);
 int forward_fused(rp_surrogate_s *s, long long n, const float *x, float *out, cudaStream_t st);
 int fused_status(rp_surrogate_s *s, cudaStream_t st);  // syncs st; RP_ERR_TIMEOUT if flagged
 // training on the tensor cores: the fused forward pass with the loss and the last layer's
-// backward data pass, and the hidden layers' backward data chain (mlp_train_fused.cu); the
-// weight gradients of the hidden layers (mlp_train_tc.cu)
+// backward data pass, and the hidden layers' backward data chain (mlp_train_fused.cu; they add
+// the hidden layers' bias gradients to db0..db3); the weight gradients of the hidden layers
+// (mlp_train_tc.cu)
 int train_fwd(rp_surrogate_s *s, long long n, const float *x, const float *y, const float *t,
-              cudaStream_t st);
-int train_bwd(rp_surrogate_s *s, long long n, cudaStream_t st);
+              float *db3, cudaStream_t st);
+int train_bwd(rp_surrogate_s *s, long long n, float *db2, float *db1, float *db0, cudaStream_t st);
 int tc_pack_backward(const float *p, unsigned char *img, long long w1, long long w2, long long w3,
                      cudaStream_t st);
 struct WgradArgs {
-    const float *H[3], *G[3];  // per hidden layer: its input activations and output gradients
-    float *dW[3], *db[3];
+    // per hidden layer: the operand images of its input activations and output gradients
+    const unsigned char *H[3], *G[3];
+    float *dW[3];
 };
 int tc_wgrad3(const WgradArgs &a, long long n, int *flag, long long wait, cudaStream_t st);
 // the mbarrier wait limit of the surrogate's tensor-core kernels [SM cycles]

@@ -72,10 +72,51 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi)
     __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t *>(&h);
 }
-// byte offset of the 8 consecutive k (k0 % 8 == 0) of row `row` in the A tile
+// Byte offset of the 8 consecutive k (k0 % 8 == 0) of row `row` in the A tile: 128 rows x 256
+// BF16 columns as 8 x 8 core matrices of 128 contiguous bytes (a row's 8 columns in 16 bytes),
+// core (row / 8, k / 8) at ((k / 8) * 16 + row / 8) * 128.  Read as an operand with K = row
+// and M (or N) = column, the same bytes are the MN-major no-swizzle image of the transposed
+// tile, so training stores each 128-row tile of activations and gradients in this layout
+// ("operand image", 64 KB): the forward and backward passes write it with coalesced 16-byte
+// stores (a warp's 32 rows of one 8-column group are 512 contiguous bytes) and the weight
+// gradients load it whole with bulk copies.
 __device__ __forceinline__ uint32_t a_off(int row, int k0)
 {
     return (uint32_t)(((k0 >> 3) * 16 + (row >> 3)) * 128 + (row & 7) * 16);
+}
+constexpr uint32_t kImage = 128u * 256u * 2u;  // bytes of one 128-row operand image
+
+// Column sums over a warp's 32 lanes: lane L returns sum over the lanes of v[L] (recursive
+// halving: at each of the 5 rounds a lane keeps the half of its columns its lane bit selects
+// and adds the partner's copy of them).  v is consumed.
+__device__ __forceinline__ float warp_colsum32(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) {
+        const bool up = (lane & k) != 0;
+#pragma unroll
+        for (int j = 0; j < k; ++j) {
+            const float send = up ? v[j] : v[j + k];
+            const float keep = up ? v[j + k] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, k);
+        }
+    }
+    return v[0];
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from global memory
+// to shared memory, completing on the mbarrier `bar` (whose transaction count the caller arms).
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
