@@ -24,108 +24,6 @@ constexpr int kLayers = 5;
 // widths of the network's layers: 3 -> 256 -> 256 -> 256 -> 256 -> 12
 __host__ __device__ constexpr int kDim(int i) { return i == 0 ? 3 : (i == kLayers ? 12 : 256); }
 
-__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
-
-// Weight gradients of the thin layers (and the last layer's bias gradient), on the CUDA cores
-// (BF16-rounded operands, FP32 products and sums, as in the forward pass), one launch for
-// both (blockIdx.y):
-//   y = 0, last layer (256 -> 12): dW[i][o] = sum_s H4[s][i] g4[s][o], db[o] = sum_s g4[s][o]
-//     (unrounded g4) (thread i; the CTA's rows of g4 staged in shared memory);
-//   y = 1, first layer (3 -> 256): dW[i][j] = sum_s x[s][i] g0[s][j] (thread j; the CTA's rows
-//     of x staged in shared memory; db0 is summed by the backward pass).
-// H4 and g0 are read from their BF16 operand images (already rounded).  Each CTA takes
-// kThinChunk rows (within one 128-row tile) and writes its sums to its row of its layer's
-// partial-sum block (dW then db); k_sum_parts adds the rows in a fixed order, so these
-// gradients do not depend on scheduling.
-constexpr int kThinChunk = 64;
-constexpr int kThinLast = 256 * 12 + 12, kThinFirst = 3 * 256;
-constexpr int kThinPart = kThinLast > kThinFirst ? kThinLast : kThinFirst;
-// the BF16 element (row r, column j) of an operand image buffer, as float
-__device__ __forceinline__ float img_at(const unsigned char *img, long long r, int j)
-{
-    const unsigned char *p = img + (r >> 7) * (long long)rph::tc::kImage + rph::tc::a_off((int)(r & 127), j & ~7) + (j & 7) * 2;
-    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(p));
-}
-__global__ void __launch_bounds__(256) k_wgrad_thin(const unsigned char *__restrict__ H4,
-                                                    const float *__restrict__ G4,
-                                                    const float *__restrict__ X,
-                                                    const unsigned char *__restrict__ G0,
-                                                    long long n, float *__restrict__ part)
-{
-    __shared__ float gr[kThinChunk * 12], gb[kThinChunk * 12];
-    const int i = threadIdx.x;
-    const long long r0 = (long long)blockIdx.x * kThinChunk;
-    const int rows = (int)min((long long)kThinChunk, n - r0);
-    float *p = part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kThinPart;
-    if (blockIdx.y == 0) {
-        for (int e = i; e < kThinChunk * 12; e += 256) {
-            const float v = e / 12 < rows ? G4[(r0 + e / 12) * 12 + e % 12] : 0.0f;
-            gr[e] = v;
-            gb[e] = bf16r(v);
-        }
-        __syncthreads();
-        float acc[12];
-#pragma unroll
-        for (int o = 0; o < 12; ++o) acc[o] = 0.0f;
-#pragma unroll 4
-        for (int r = 0; r < rows; ++r) {
-            const float h = img_at(H4, r0 + r, i);
-#pragma unroll
-            for (int o = 0; o < 12; ++o) acc[o] = fmaf(h, gb[r * 12 + o], acc[o]);
-        }
-#pragma unroll
-        for (int o = 0; o < 12; ++o) p[i * 12 + o] = acc[o];
-        if (i < 12) {
-            float s = 0.0f;
-            for (int r = 0; r < rows; ++r) s += gr[r * 12 + i];
-            p[256 * 12 + i] = s;
-        }
-        return;
-    }
-    float *xb = gr;  // the CTA's rows of x, BF16-rounded
-    for (int e = i; e < kThinChunk * 3; e += 256)
-        xb[e] = e / 3 < rows ? bf16r(X[(r0 + e / 3) * 3 + e % 3]) : 0.0f;
-    __syncthreads();
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
-#pragma unroll 4
-    for (int r = 0; r < rows; ++r) {
-        const float b = img_at(G0, r0 + r, i);
-        a0 = fmaf(xb[r * 3], b, a0);
-        a1 = fmaf(xb[r * 3 + 1], b, a1);
-        a2 = fmaf(xb[r * 3 + 2], b, a2);
-    }
-    p[i] = a0;
-    p[256 + i] = a1;
-    p[512 + i] = a2;
-}
-// Both thin layers' sums over the CTAs' partial sums, in CTA order: element e < kThinLast of
-// the last layer's block (dW4 then db4), then the first layer's (dW0).
-__global__ void k_sum_parts(const float *__restrict__ part, int n_parts, float *__restrict__ dW4,
-                            float *__restrict__ db4, float *__restrict__ dW0)
-{
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= kThinLast + kThinFirst) return;
-    const int y = e < kThinLast ? 0 : 1, f = y ? e - kThinLast : e;
-    const float *src = part + (size_t)y * n_parts * kThinPart + f;
-    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;  // four independent chains, then in order
-    int c = 0;
-    for (; c + 4 <= n_parts; c += 4) {
-        s0 += src[(size_t)c * kThinPart];
-        s1 += src[(size_t)(c + 1) * kThinPart];
-        s2 += src[(size_t)(c + 2) * kThinPart];
-        s3 += src[(size_t)(c + 3) * kThinPart];
-    }
-    for (; c < n_parts; ++c) s0 += src[(size_t)c * kThinPart];
-    const float s = (s0 + s1) + (s2 + s3);
-    if (y == 0) {
-        if (f < 256 * 12)
-            dW4[f] += s;
-        else
-            db4[f - 256 * 12] += s;
-    } else {
-        dW0[f] += s;
-    }
-}
 
 __global__ void k_to_bf16(const float *p, __nv_bfloat16 *pb, long long n)
 {
@@ -255,9 +153,9 @@ static void free_acts(rp_surrogate_s *s)
         cudaFree(s->gl[l]);
         s->gl[l] = nullptr;
     }
-    cudaFree(s->out);
-    cudaFree(s->part);
-    s->out = s->part = nullptr;
+    cudaFree(s->ximg);
+    cudaFree(s->g4img);
+    s->ximg = s->g4img = nullptr;
     s->cap = 0;
 }
 
@@ -271,16 +169,16 @@ int ensure_acts(rp_surrogate_s *s, long long n)
     for (int l = 0; l < 3; ++l) RP_CUDA_TRY(cudaMalloc(&s->Z[l], tiles * 128 * 256 * sizeof(float)));
     for (int l = 1; l < 5; ++l) RP_CUDA_TRY(cudaMalloc(&s->H[l], tiles * rph::tc::kImage));
     for (int l = 0; l < 4; ++l) RP_CUDA_TRY(cudaMalloc(&s->gl[l], tiles * rph::tc::kImage));
-    RP_CUDA_TRY(cudaMalloc(&s->out, sizeof(float) * cap * 12));
-    RP_CUDA_TRY(cudaMalloc(&s->part, sizeof(float) * 2 * (size_t)((cap + kThinChunk - 1) / kThinChunk) * kThinPart));
+    RP_CUDA_TRY(cudaMalloc(&s->ximg, tiles * rph::tc::kImage16));
+    RP_CUDA_TRY(cudaMalloc(&s->g4img, tiles * rph::tc::kImage16));
     s->cap = cap;
     return RP_OK;
 }
 
 // Loss and parameter gradient (into s->grad) of n rows: the fused forward pass with the loss
-// and the last layer's backward data pass, the hidden layers' backward data chain, the three
-// hidden layers' weight gradients on the tensor cores (one launch), and the thin layers' weight
-// gradients on the CUDA cores.
+// and the last layer's backward data pass, the hidden layers' backward data chain (these two
+// also sum the bias gradients), and all five layers' weight gradients on the tensor cores (one
+// launch).
 static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float *y,
                      const float *t, double *loss_host, cudaStream_t st)
 {
@@ -292,22 +190,16 @@ static int loss_grad(rp_surrogate_s *s, long long n, const float *x, const float
         RP_CUDA_TRY(cudaMemsetAsync(s->grad, 0, sizeof(float) * n_params(), st));
     }
     s->clean = false;
-    if ((rc = train_fwd(s, n, x, y, t, s->grad + layer_b(3), st))) return rc;
-    if ((rc = train_bwd(s, n, s->grad + layer_b(2), s->grad + layer_b(1), s->grad + layer_b(0), st)))
-        return rc;
+    float *g = s->grad;
+    if ((rc = train_fwd(s, n, x, y, t, g + layer_b(3), g + layer_b(4), st))) return rc;
+    if ((rc = train_bwd(s, n, g + layer_b(2), g + layer_b(1), g + layer_b(0), st))) return rc;
     WgradArgs wa;
-    for (int l = 1; l <= 3; ++l) {  // layer l: input H_l, output gradient g_l
-        wa.H[l - 1] = s->H[l];
-        wa.G[l - 1] = s->gl[l];
-        wa.dW[l - 1] = s->grad + layer_w(l);
-    }
-    if ((rc = tc_wgrad3(wa, n, s->fflag, wait_cycles(s), st))) return rc;
-    // thin weight gradients: one 64-row chunk per CTA and layer, then a fixed-order sum of
-    // the CTAs' partial sums
-    const unsigned thin_grid = (unsigned)((n + kThinChunk - 1) / kThinChunk);
-    k_wgrad_thin<<<dim3(thin_grid, 2), 256, 0, st>>>(s->H[4], s->out, x, s->gl[0], n, s->part);
-    k_sum_parts<<<(kThinLast + kThinFirst + 255) / 256, 256, 0, st>>>(
-        s->part, (int)thin_grid, s->grad + layer_w(4), s->grad + layer_b(4), s->grad + layer_w(0));
+    memset(&wa, 0, sizeof wa);
+    for (int l = 1; l <= 3; ++l)  // layer l: input H_l, output gradient g_l
+        wa.job[l - 1] = WgradJob{s->H[l], s->gl[l], g + layer_w(l), 256, WG_OUT_SQUARE, 0, 0};
+    wa.job[3] = WgradJob{s->H[4], s->g4img, g + layer_w(4), 16, WG_OUT_LAST, 0, 0};
+    wa.job[4] = WgradJob{s->gl[0], s->ximg, g + layer_w(0), 16, WG_OUT_FIRST_T, 0, 0};
+    if ((rc = tc_wgrad(wa, n, s->fflag, wait_cycles(s), st))) return rc;
     RP_CUDA_TRY(cudaGetLastError());
     if (loss_host) {
         RP_CUDA_TRY(cudaMemcpyAsync(loss_host, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st));

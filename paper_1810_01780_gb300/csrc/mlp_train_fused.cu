@@ -10,8 +10,9 @@
 //   store what the later kernels read: the pre-activations z0..z2 in FP32 (tiled: a tile's 8
 //   columns k..k+7 of its 128 rows are 4 KB contiguous, so a warp's stores and the backward
 //   pass's loads of one 8-column group are 1 KB contiguous) and the activations H1..H4 as BF16
-//   operand images (tc_common.cuh).  The last layer (256 -> 12) comes out of the third
-//   epilogue's partial sums; the loss and its gradient g4 follow per row, and the last layer's
+//   operand images (tc_common.cuh), and x as a 16-column image.  The last layer (256 -> 12)
+//   comes out of the third epilogue's partial sums; the loss and its gradient g4 follow per row
+//   (g4 stored as a 16-column image, its column sums added to db4), and the last layer's
 //   backward data pass g3 = (g4 W4^T) gelu'(z3) re-reads z3 from tensor memory, stores g3 as a
 //   BF16 image and adds its column sums to the bias gradient db3.
 // k_train_bwd: per tile, the g3 image by bulk copy as the A tile, then for the hidden layers
@@ -160,16 +161,17 @@ __device__ __forceinline__ void teardown_cta(unsigned char *sm, int tid, int war
 }
 
 // Forward pass, loss and last-layer backward of n rows (x (n, 3), targets y (n, 2), t (n, 10)).
-// Writes z0, z1, z2 (tiled FP32), the images of H1..H4 and g3, g4 (n, 12), adds the loss sum to
-// *loss and the column sums of g3 to db3.
+// Writes z0, z1, z2 (tiled FP32), the images of x, H1..H4, g4 and g3, adds the loss sum to
+// *loss and the column sums of g4 and g3 to db4 and db3.
 __global__ void __launch_bounds__(kThreads, 1)
     k_train_fwd(const unsigned char *__restrict__ pack, const float *__restrict__ x,
                 const float *__restrict__ y, const float *__restrict__ t, long long n,
                 float *__restrict__ Z0, float *__restrict__ Z1, float *__restrict__ Z2,
                 unsigned char *__restrict__ H1, unsigned char *__restrict__ H2,
                 unsigned char *__restrict__ H3, unsigned char *__restrict__ H4,
-                float *__restrict__ g4, unsigned char *__restrict__ G3, float *__restrict__ db3,
-                double *loss, int *flag, long long wait)
+                unsigned char *__restrict__ Xi, unsigned char *__restrict__ G4,
+                unsigned char *__restrict__ G3, float *__restrict__ db4,
+                float *__restrict__ db3, double *loss, int *flag, long long wait)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *sA = sm + SM_A;
@@ -210,6 +212,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 x0 = bf16r(x[3 * gr]);
                 x1 = bf16r(x[3 * gr + 1]);
                 x2 = bf16r(x[3 * gr + 2]);
+            }
+            if (grp0 < 2) {  // the x image: columns 0..2, zero-padded to 16
+                const uint4 pk = grp0 == 0 ? make_uint4(pack2(x0, x1), pack2(x2, 0.0f), 0u, 0u)
+                                           : make_uint4(0u, 0u, 0u, 0u);
+                *reinterpret_cast<uint4 *>(Xi + tile * kImage16 + a_off(row0, grp0 * 8)) = pk;
             }
 #pragma unroll 1
             for (int c = 0; c < kGroupCols / 8; ++c) {
@@ -336,11 +343,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                         gg[6 * k + 1 + j] = yk * d * inv_n;
                     }
                 }
-#pragma unroll
-                for (int o = 0; o < 12; ++o) g4[gr * 12 + o] = gg[o];
             }
 #pragma unroll
             for (int o = 0; o < 12; ++o) sG[erow * 12 + o] = bf16r(gg[o]);
+            {  // g4 as a 16-column image, and its column sums
+                float cs[16];
+#pragma unroll
+                for (int o = 0; o < 16; ++o) cs[o] = o < 12 ? gg[o] : 0.0f;
+                unsigned char *G4t = G4 + tile * kImage16;
+                *reinterpret_cast<uint4 *>(G4t + a_off(erow, 0)) =
+                    make_uint4(pack2(gg[0], gg[1]), pack2(gg[2], gg[3]), pack2(gg[4], gg[5]),
+                               pack2(gg[6], gg[7]));
+                *reinterpret_cast<uint4 *>(G4t + a_off(erow, 8)) =
+                    make_uint4(pack2(gg[8], gg[9]), pack2(gg[10], gg[11]), 0u, 0u);
+                const float sum = warp_colsum<16>(cs, lane);
+                if (lane < 12) atomicAdd(db4 + lane, sum);
+            }
             for (int d = 16; d > 0; d >>= 1) L += __shfl_xor_sync(0xffffffffu, L, d);
             if (lane == 0) atomicAdd(loss, (double)L);
         }
@@ -373,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     *reinterpret_cast<uint4 *>(G3t + a_off(erow, col0 + e * 8)) = pack8(gg);
                 }
-                atomicAdd(db3 + col0 + lane, warp_colsum32(cs, lane));
+                atomicAdd(db3 + col0 + lane, warp_colsum<32>(cs, lane));
             }
         }
         fence_before();
@@ -490,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     *reinterpret_cast<uint4 *>(Gl + a_off(erow, k0)) = pk;
                     if (l < 2) *reinterpret_cast<uint4 *>(sA + a_off(erow, k0)) = pk;
                 }
-                atomicAdd(dbl + col0 + lane, warp_colsum32(cs, lane));
+                atomicAdd(dbl + col0 + lane, warp_colsum<32>(cs, lane));
             }
             fence_before();
         }
@@ -504,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 }  // namespace
 
 int train_fwd(rp_surrogate_s *s, long long n, const float *x, const float *y, const float *t,
-              float *db3, cudaStream_t st)
+              float *db3, float *db4, cudaStream_t st)
 {
     if (n <= 0) return RP_OK;
     int dev;
@@ -514,8 +532,8 @@ int train_fwd(rp_surrogate_s *s, long long n, const float *x, const float *y, co
     const long long tiles = (n + kTile - 1) / kTile;
     const int grid = (int)std::min<long long>(tiles, (long long)sm_count(dev));
     k_train_fwd<<<grid, kThreads, SM_TOTAL, st>>>(s->pack, x, y, t, n, s->Z[0], s->Z[1], s->Z[2],
-                                                  s->H[1], s->H[2], s->H[3], s->H[4], s->out,
-                                                  s->gl[3], db3, s->loss, s->fflag,
+                                                  s->H[1], s->H[2], s->H[3], s->H[4], s->ximg,
+                                                  s->g4img, s->gl[3], db4, db3, s->loss, s->fflag,
                                                   wait_cycles(s));
     RP_CUDA_TRY(cudaGetLastError());
     return RP_OK;

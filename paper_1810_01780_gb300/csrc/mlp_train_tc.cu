@@ -1,15 +1,18 @@
-// mlp_train_tc.cu -- the weight gradients of the surrogate's three hidden 256 x 256 layers in
-// training, on the 5th-generation tensor cores (tcgen05), all three layers in one launch.
+// mlp_train_tc.cu -- the weight gradients of all five layers of the surrogate in training, on
+// the 5th-generation tensor cores (tcgen05), in one launch.
 //
-//   k_tc_wgrad: dW[in][out] += sum over rows s of H[s][in] g[s][out] with M = in (one half of
-//     128 per CTA), N = out (256), K = rows; blockIdx.z selects the layer, blockIdx.y the M half,
-//     and blockIdx.x one of gridDim.x interleaved shares of the 128-row tiles.  The forward and
-//     backward passes leave H and g as BF16 operand images (tc_common.cuh), which are the
-//     MN-major no-swizzle images of H^T and g^T: a CTA bulk-copies its half of each tile's H
-//     image (32 KB) and the whole g image (64 KB) into one of two shared-memory stages, so the
-//     copy of the next tile overlaps the MMAs of this one, accumulates over its tiles in tensor
-//     memory (256 columns) and adds its sums to dW with vector atomics at the end.  (The bias
-//     gradients are summed by the passes that produce g.)
+//   k_tc_wgrad: D = A^T B over the batch's rows with M = A's 256 columns (one half of 128 per
+//     CTA), N = B's columns, K = rows; blockIdx.z selects the job, blockIdx.y the M half, and
+//     blockIdx.x one of the job's interleaved shares of the 128-row tiles (CTAs past a job's
+//     shares return at once).  The jobs: dW_l = H_l^T g_l of the hidden layers (N 256), the
+//     last layer's dW4 = H4^T g4 (N 16: g4's 12 columns zero-padded) and the first layer's
+//     dW0^T = g0^T x (N 16: x's 3 columns zero-padded).  The forward and backward passes leave
+//     these matrices as BF16 operand images (tc_common.cuh), which are the MN-major no-swizzle
+//     images of their transposes: a CTA bulk-copies its half of each tile's A image (32 KB) and
+//     the B image (64 or 4 KB) into one of two shared-memory stages, so the copy of the next
+//     tile overlaps the MMAs of this one, accumulates over its tiles in tensor memory and adds
+//     its sums to dW with atomics at the end.  (The bias gradients are summed by the passes
+//     that produce the g.)
 //   k_pack_t: the backward data pass's B images of W1..W3 (B[n][k] = W[n][k]).
 // Arithmetic: BF16 operands, FP32 products and sums.  Every mbarrier wait is bounded (the
 // surrogate's wait limit); a CTA that gives up sets the error flag, waits (with the default
@@ -30,33 +33,40 @@ using namespace tc;
 constexpr int kThreads = 512;  // 16 warps: lane quarter (warp % 4) x column group (warp / 4)
 constexpr uint32_t kImgB = 256u * 256u * 2u;  // a packed 256 x 256 BF16 B image
 
-// instruction descriptor: D FP32, A and B BF16, both MN-major (bits 15 and 16), N = 256,
-// M = 128
+// instruction descriptor: D FP32, A and B BF16, both MN-major (bits 15 and 16), M = 128; N
+// (bits 17..22, N / 8) per job
 constexpr uint32_t kIdescT = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
-                             ((256u >> 3) << 17) | ((128u >> 4) << 24);
+                             ((128u >> 4) << 24);
 
-// shared memory map of k_tc_wgrad (bytes): two stages of (the H image's M half, 32 KB; the g
-// image, 64 KB), then the barriers: full[2] (copies landed), done[2] (MMAs read the stage)
+// shared memory map of k_tc_wgrad (bytes): two stages of (the A image's M half, 32 KB; the B
+// image, up to 64 KB), then the barriers: full[2] (copies landed), done[2] (MMAs read the
+// stage)
 constexpr uint32_t WG_HALF = kImage / 2;
 constexpr uint32_t WG_STAGE = WG_HALF + kImage;
 constexpr uint32_t WG_BAR = 2 * WG_STAGE;
 constexpr uint32_t WG_TOTAL = WG_BAR + 64;
 static_assert(WG_TOTAL <= 227 * 1024, "shared memory map exceeds a CTA's limit");
 
-// dW[128 h .. 128 h + 127][:] (h = blockIdx.y) over the tiles blockIdx.x, + gridDim.x, ...
+// rows 128 h .. 128 h + 127 (h = blockIdx.y) of D over the tiles blockIdx.x, + shares, ...
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_wgrad(const WgradArgs args, long long n_tiles, int *flag, long long wait)
 {
-    const unsigned char *__restrict__ H = args.H[blockIdx.z];
-    const unsigned char *__restrict__ G = args.G[blockIdx.z];
-    float *__restrict__ dW = args.dW[blockIdx.z];
+    const WgradJob &J = args.job[blockIdx.z];
+    const long long shares = J.shares;
+    if ((long long)blockIdx.x >= shares) return;  // uniform over the CTA
+    const unsigned char *__restrict__ H = J.A;
+    const unsigned char *__restrict__ G = J.B;
+    float *__restrict__ dW = J.dW;
+    const int nb = J.n;                                      // 256 or 16
+    const uint32_t b_bytes = nb == 256 ? kImage : kImage16;  // B image of a tile
+    const uint32_t idesc = kIdescT | ((uint32_t)(nb >> 3) << 17);
     extern __shared__ __align__(1024) unsigned char sm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + WG_BAR);  // full[0..1], done[0..1]
     uint32_t *slot = reinterpret_cast<uint32_t *>(sm + WG_BAR + 32);
     volatile int *abort_cta = reinterpret_cast<volatile int *>(sm + WG_BAR + 36);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int half = (int)blockIdx.y;
-    const long long cnt = (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;  // >= 1
+    const long long cnt = (n_tiles - blockIdx.x + shares - 1) / shares;  // >= 1
 
     if (tid == 0) {
         for (int b = 0; b < 4; ++b)
@@ -84,12 +94,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool failed = false;
         auto load = [&](long long i) {
             const int st = (int)(i & 1);
-            const long long t = blockIdx.x + i * gridDim.x;
+            const long long t = blockIdx.x + i * shares;
             const uint32_t base = su32(sm + st * WG_STAGE), fb = su32(&bar[st]);
-            mbar_expect(fb, WG_STAGE);
+            mbar_expect(fb, WG_HALF + b_bytes);
             bulk_g2s(base, H + t * kImage + half * WG_HALF, WG_HALF, fb);
-            bulk_g2s(base + WG_HALF, G + t * kImage, WG_HALF, fb);
-            bulk_g2s(base + 2 * WG_HALF, G + t * kImage + WG_HALF, WG_HALF, fb);
+            for (uint32_t o = 0; o < b_bytes; o += WG_HALF)
+                bulk_g2s(base + WG_HALF + o, G + t * b_bytes + o, b_bytes - o < WG_HALF ? b_bytes - o : WG_HALF, fb);
             ld[st] = i;
         };
         auto par = [](long long i) { return (uint32_t)((i >> 1) & 1); };
@@ -112,7 +122,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 asm volatile(
                     "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(kIdescT), "r"((uint32_t)(i > 0 || k > 0))
+                    "l"(ad), "l"(bd), "r"(idesc), "r"((uint32_t)(i > 0 || k > 0))
                     : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -150,22 +160,39 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     fence_after();
     if (!*abort_cta) {
-        // TMEM lane m: input row 128 half + m; column t: output column t (quarter q = warp % 4
-        // reads lanes 32 q .. 32 q + 31, column group warp / 4 columns 64 (warp / 4) ..)
+        // TMEM lane m: row 128 half + m of D; column c: column c (quarter q = warp % 4 reads
+        // lanes 32 q .. 32 q + 31)
         const int q = warp & 3, ch = warp >> 2;
         const int m = half * 128 + q * 32 + lane;
+        if (nb == 256) {  // column group warp / 4: columns 64 (warp / 4) ..
 #pragma unroll 1
-        for (int c = 0; c < 2; ++c) {
-            const int n0 = ch * 64 + c * 32;
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)n0, v);
-            float *d = dW + (long long)m * 256 + n0;  // 16-byte aligned: n0 % 32 == 0
+            for (int c = 0; c < 2; ++c) {
+                const int n0 = ch * 64 + c * 32;
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)n0, v);
+                float *d = dW + (long long)m * 256 + n0;  // 16-byte aligned: n0 % 32 == 0
 #pragma unroll
-            for (int j = 0; j < 32; j += 4)
-                asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(d + j),
-                             "f"(__uint_as_float(v[j])), "f"(__uint_as_float(v[j + 1])),
-                             "f"(__uint_as_float(v[j + 2])), "f"(__uint_as_float(v[j + 3]))
-                             : "memory");
+                for (int j = 0; j < 32; j += 4)
+                    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(d + j),
+                                 "f"(__uint_as_float(v[j])), "f"(__uint_as_float(v[j + 1])),
+                                 "f"(__uint_as_float(v[j + 2])), "f"(__uint_as_float(v[j + 3]))
+                                 : "memory");
+            }
+        } else if (ch == 0) {  // 16 columns, warps 0..3
+            uint32_t v[16];
+            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16), v);
+            if (J.out == WG_OUT_LAST) {
+                float *d = dW + (long long)m * 12;  // 16-byte aligned: 48 m bytes
+#pragma unroll
+                for (int j = 0; j < 12; j += 4)
+                    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(d + j),
+                                 "f"(__uint_as_float(v[j])), "f"(__uint_as_float(v[j + 1])),
+                                 "f"(__uint_as_float(v[j + 2])), "f"(__uint_as_float(v[j + 3]))
+                                 : "memory");
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) atomicAdd(dW + c * 256 + m, __uint_as_float(v[c]));
+            }
         }
     }
     fence_before();
@@ -201,15 +228,19 @@ int tc_pack_backward(const float *p, unsigned char *img, long long w1, long long
     return RP_OK;
 }
 
-int tc_wgrad3(const WgradArgs &a, long long n, int *flag, long long wait, cudaStream_t st)
+int tc_wgrad(WgradArgs &a, long long n, int *flag, long long wait, cudaStream_t st)
 {
     if (n <= 0) return RP_OK;
     int dev;
     RP_CUDA_TRY(cudaGetDevice(&dev));
     const long long tiles = (n + 127) / 128;
-    // tile shares x M halves x layers: about one CTA per SM
-    const long long shares = std::max(1LL, std::min(tiles, (long long)sm_count(dev) / 6));
-    const dim3 grid((unsigned)shares, 2, 3);
+    // one CTA per SM: a few for each thin job (little to copy and multiply), the rest split
+    // evenly among the three hidden layers' two M halves
+    const long long sms = sm_count(dev);
+    const long long thin = std::max(1LL, std::min(tiles, std::min(4LL, sms / 32)));
+    const long long wide = std::max(1LL, std::min(tiles, (sms - 4 * thin) / 6));
+    for (int j = 0; j < 5; ++j) a.job[j].shares = (int32_t)(j < 3 ? wide : thin);
+    const dim3 grid((unsigned)std::max(wide, thin), 2, 5);
     RP_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)WG_TOTAL));
     k_tc_wgrad<<<grid, kThreads, WG_TOTAL, st>>>(a, tiles, flag, wait);

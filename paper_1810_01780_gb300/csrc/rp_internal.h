@@ -20,12 +20,11 @@ struct rp_surrogate_s {
     __nv_bfloat16 *pb;
     // training buffers for a batch of up to `cap` rows, per 128-row tile: the pre-activations
     // z0..z2 (FP32, tiled), the activations H1..H4 and the gradients g0..g3 as BF16 operand
-    // images (64 KB per tile; H[0] unused), and g4 (FP32, 12 per row)
+    // images (64 KB per tile; H[0] unused), and x and g4 as 16-column images (4 KB per tile)
     long long cap;
     float *Z[3];
     unsigned char *H[5], *gl[4];
-    float *out;
-    float *part;  // per-CTA partial sums of the thin layers' weight and bias gradients
+    unsigned char *ximg, *g4img;
     double *loss;
     void *pipe;  // buffers of the surrogate path-finding pipeline (pathfind.cu)
     // inference operands for the fused kernel (mlp_fused.cu), rebuilt when the weights change
@@ -180,19 +179,30 @@ int forward_fused(rp_surrogate_s *s, long long n, const float *x, float *out, cu
 int fused_status(rp_surrogate_s *s, cudaStream_t st);  // syncs st; RP_ERR_TIMEOUT if flagged
 // training on the tensor cores: the fused forward pass with the loss and the last layer's
 // backward data pass, and the hidden layers' backward data chain (mlp_train_fused.cu; they add
-// the hidden layers' bias gradients to db0..db3); the weight gradients of the hidden layers
-// (mlp_train_tc.cu)
+// the bias gradients to db0..db4); the weight gradients of all five layers (mlp_train_tc.cu)
 int train_fwd(rp_surrogate_s *s, long long n, const float *x, const float *y, const float *t,
-              float *db3, cudaStream_t st);
+              float *db3, float *db4, cudaStream_t st);
 int train_bwd(rp_surrogate_s *s, long long n, float *db2, float *db1, float *db0, cudaStream_t st);
 int tc_pack_backward(const float *p, unsigned char *img, long long w1, long long w2, long long w3,
                      cudaStream_t st);
-struct WgradArgs {
-    // per hidden layer: the operand images of its input activations and output gradients
-    const unsigned char *H[3], *G[3];
-    float *dW[3];
+// One weight-gradient product D = A^T B over the rows of a batch (k_tc_wgrad): A the operand
+// images of a layer's 256 input columns (M, two halves), B those of its N output columns (256,
+// or 16 for the thin layers' zero-padded images), D added to dW as `out` says.
+enum { WG_OUT_SQUARE = 0, WG_OUT_LAST = 1, WG_OUT_FIRST_T = 2 };
+struct WgradJob {
+    const unsigned char *A, *B;
+    float *dW;
+    int32_t n;       // N: 256 or 16
+    int32_t out;     // WG_OUT_SQUARE: dW[m * 256 + c]; WG_OUT_LAST: dW[m * 12 + c] (c < 12);
+                     // WG_OUT_FIRST_T: dW[c * 256 + m] (c < 3, the first layer's W0 transposed)
+    int32_t shares;  // CTAs that split this job's tiles among them
+    int32_t pad;
 };
-int tc_wgrad3(const WgradArgs &a, long long n, int *flag, long long wait, cudaStream_t st);
+struct WgradArgs {
+    WgradJob job[5];  // the hidden layers 1..3, the last layer, the first layer (transposed)
+};
+// Launches the five jobs of `a` (their shares filled in here) over n rows.
+int tc_wgrad(WgradArgs &a, long long n, int *flag, long long wait, cudaStream_t st);
 // the mbarrier wait limit of the surrogate's tensor-core kernels [SM cycles]
 long long wait_cycles(const rp_surrogate_s *s);
 int run_surrogate_paths(rp_surrogate_s *s, rp_medium_t m, int64_t n, const double *zs,

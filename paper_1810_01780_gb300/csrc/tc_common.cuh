@@ -85,14 +85,17 @@ __device__ __forceinline__ uint32_t a_off(int row, int k0)
     return (uint32_t)(((k0 >> 3) * 16 + (row >> 3)) * 128 + (row & 7) * 16);
 }
 constexpr uint32_t kImage = 128u * 256u * 2u;  // bytes of one 128-row operand image
+constexpr uint32_t kImage16 = 128u * 16u * 2u;  // the same of 16 columns (x and g4, zero-padded)
 
-// Column sums over a warp's 32 lanes: lane L returns sum over the lanes of v[L] (recursive
-// halving: at each of the 5 rounds a lane keeps the half of its columns its lane bit selects
-// and adds the partner's copy of them).  v is consumed.
-__device__ __forceinline__ float warp_colsum32(float (&v)[32], int lane)
+// Column sums over a warp's 32 lanes of W (16 or 32) columns: lane L returns the sum over the
+// lanes of v[L % W] (recursive halving: at each round a lane keeps the half of its columns its
+// lane bit selects and adds the partner's copy of them; for W = 16 a last exchange adds the
+// other 16 lanes).  v is consumed.
+template <int W>
+__device__ __forceinline__ float warp_colsum(float (&v)[W], int lane)
 {
 #pragma unroll
-    for (int k = 16; k >= 1; k >>= 1) {
+    for (int k = W / 2; k >= 1; k >>= 1) {
         const bool up = (lane & k) != 0;
 #pragma unroll
         for (int j = 0; j < k; ++j) {
@@ -101,6 +104,8 @@ __device__ __forceinline__ float warp_colsum32(float (&v)[32], int lane)
             v[j] = keep + __shfl_xor_sync(0xffffffffu, send, k);
         }
     }
+#pragma unroll
+    for (int k = W; k < 32; k <<= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], k);
     return v[0];
 }
 
@@ -129,6 +134,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
           "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
           "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
           "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
