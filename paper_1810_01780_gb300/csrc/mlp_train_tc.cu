@@ -38,13 +38,17 @@ constexpr uint32_t kImgB = 256u * 256u * 2u;  // a packed 256 x 256 BF16 B image
 constexpr uint32_t kIdescT = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
                              ((128u >> 4) << 24);
 
-// shared memory map of k_tc_wgrad (bytes): two stages of (the A image's M half, 32 KB; the B
-// image, up to 64 KB), then the barriers: full[2] (copies landed), done[2] (MMAs read the
-// stage)
+// shared memory map of k_tc_wgrad (bytes): stages of (the A image's M half, 32 KB; the B
+// image, 64 or 4 KB): two of 96 KB for N = 256, five of 36 KB for N = 16 (whose short MMAs
+// leave the copies' latency exposed unless more tiles are in flight); then the barriers
+// full[s] (the copies into stage s landed) and done[s] (the MMAs have read stage s)
 constexpr uint32_t WG_HALF = kImage / 2;
 constexpr uint32_t WG_STAGE = WG_HALF + kImage;
+constexpr int kStagesWide = 2, kStagesThin = 5, kMaxStages = 6;
 constexpr uint32_t WG_BAR = 2 * WG_STAGE;
-constexpr uint32_t WG_TOTAL = WG_BAR + 64;
+constexpr uint32_t WG_SLOT = WG_BAR + 2 * kMaxStages * 8;  // TMEM address, abort word
+constexpr uint32_t WG_TOTAL = WG_SLOT + 32;
+static_assert(kStagesThin * (WG_HALF + kImage16) <= WG_BAR, "thin stages fit the wide ones' room");
 static_assert(WG_TOTAL <= 227 * 1024, "shared memory map exceeds a CTA's limit");
 
 // rows 128 h .. 128 h + 127 (h = blockIdx.y) of D over the tiles blockIdx.x, + shares, ...
@@ -60,16 +64,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int nb = J.n;                                      // 256 or 16
     const uint32_t b_bytes = nb == 256 ? kImage : kImage16;  // B image of a tile
     const uint32_t idesc = kIdescT | ((uint32_t)(nb >> 3) << 17);
+    const int S = nb == 256 ? kStagesWide : kStagesThin;  // pipeline stages
+    const uint32_t stage_bytes = WG_HALF + b_bytes;
     extern __shared__ __align__(1024) unsigned char sm[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + WG_BAR);  // full[0..1], done[0..1]
-    uint32_t *slot = reinterpret_cast<uint32_t *>(sm + WG_BAR + 32);
-    volatile int *abort_cta = reinterpret_cast<volatile int *>(sm + WG_BAR + 36);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + WG_BAR);  // full[0..S), done at +kMaxStages
+    uint64_t *done = bar + kMaxStages;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(sm + WG_SLOT);
+    volatile int *abort_cta = reinterpret_cast<volatile int *>(sm + WG_SLOT + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int half = (int)blockIdx.y;
     const long long cnt = (n_tiles - blockIdx.x + shares - 1) / shares;  // >= 1
 
     if (tid == 0) {
-        for (int b = 0; b < 4; ++b)
+        for (int b = 0; b < 2 * kMaxStages; ++b)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[b])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *abort_cta = 0;
@@ -86,33 +93,34 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = *slot;
 
     if (tid == 0) {
-        // One thread copies and issues.  Tile i (the i-th of this CTA) uses stage i % 2, as
-        // that stage's (i / 2)-th use: its copies complete phase i / 2 of full[i % 2] and its
-        // MMAs commit phase i / 2 of done[i % 2].  ld[s] / mm[s]: the tile whose copies / MMAs
+        // One thread copies and issues.  Tile i (the i-th of this CTA) uses stage i % S, as
+        // that stage's (i / S)-th use: its copies complete phase i / S of full[i % S] and its
+        // MMAs commit phase i / S of done[i % S].  ld[s] / mm[s]: the tile whose copies / MMAs
         // on stage s are in flight, -1 if none (drained on failure).
-        long long ld[2] = {-1, -1}, mm[2] = {-1, -1};
+        long long ld[kMaxStages], mm[kMaxStages];
+        for (int s2 = 0; s2 < kMaxStages; ++s2) ld[s2] = mm[s2] = -1;
         bool failed = false;
         auto load = [&](long long i) {
-            const int st = (int)(i & 1);
+            const int st = (int)(i % S);
             const long long t = blockIdx.x + i * shares;
-            const uint32_t base = su32(sm + st * WG_STAGE), fb = su32(&bar[st]);
-            mbar_expect(fb, WG_HALF + b_bytes);
+            const uint32_t base = su32(sm + st * stage_bytes), fb = su32(&bar[st]);
+            mbar_expect(fb, stage_bytes);
             bulk_g2s(base, H + t * kImage + half * WG_HALF, WG_HALF, fb);
             for (uint32_t o = 0; o < b_bytes; o += WG_HALF)
-                bulk_g2s(base + WG_HALF + o, G + t * b_bytes + o, b_bytes - o < WG_HALF ? b_bytes - o : WG_HALF, fb);
+                bulk_g2s(base + WG_HALF + o, G + t * b_bytes + o,
+                         b_bytes - o < WG_HALF ? b_bytes - o : WG_HALF, fb);
             ld[st] = i;
         };
-        auto par = [](long long i) { return (uint32_t)((i >> 1) & 1); };
-        load(0);
-        if (cnt > 1) load(1);
+        auto par = [S](long long i) { return (uint32_t)((i / S) & 1); };
+        for (long long j = 0; j < cnt && j < S; ++j) load(j);
         for (long long i = 0; i < cnt && !failed; ++i) {
-            const int st = (int)(i & 1);
+            const int st = (int)(i % S);
             if (!mbar_wait(su32(&bar[st]), par(i), wait)) {
                 failed = true;
                 break;
             }
             ld[st] = -1;
-            const uint32_t a0 = su32(sm + st * WG_STAGE), b0 = a0 + WG_HALF;
+            const uint32_t a0 = su32(sm + st * stage_bytes), b0 = a0 + WG_HALF;
             // K step k: rows 16 k .. 16 k + 15, two 8-row core groups 128 bytes apart (the
             // K-direction stride); 8-column groups 2048 bytes apart (the M / N-direction stride)
 #pragma unroll
@@ -126,33 +134,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                     : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             su32(&bar[2 + st]))
+                             su32(&done[st]))
                          : "memory");
             mm[st] = i;
-            // the other stage's MMAs (tile i - 1) done: refill it with tile i + 1
-            if (i >= 1 && i + 1 < cnt) {
-                const int o = st ^ 1;
-                if (!mbar_wait(su32(&bar[2 + o]), par(i - 1), wait)) {
+            // the stage of tile i - 1, once its MMAs are done, takes tile i - 1 + S
+            if (i >= 1 && i - 1 + S < cnt) {
+                const int o = (int)((i - 1) % S);
+                if (!mbar_wait(su32(&done[o]), par(i - 1), wait)) {
                     failed = true;
                     break;
                 }
                 mm[o] = -1;
-                load(i + 1);
+                load(i - 1 + S);
             }
         }
         if (!failed) {  // the last tile's MMAs, and with them all before, done
-            const int st = (int)((cnt - 1) & 1);
-            if (mbar_wait(su32(&bar[2 + st]), par(cnt - 1), wait))
-                mm[0] = mm[1] = -1;
-            else
+            if (mbar_wait(su32(&done[(cnt - 1) % S]), par(cnt - 1), wait)) {
+                for (int s2 = 0; s2 < kMaxStages; ++s2) mm[s2] = -1;
+            } else {
                 failed = true;
+            }
         }
         if (failed) {
             atomicExch(flag, 1);
             *abort_cta = 1;
-            for (int s2 = 0; s2 < 2; ++s2) {  // drain with the default bound
+            for (int s2 = 0; s2 < S; ++s2) {  // drain with the default bound
                 if (ld[s2] >= 0) mbar_wait(su32(&bar[s2]), par(ld[s2]));
-                if (mm[s2] >= 0) mbar_wait(su32(&bar[2 + s2]), par(mm[s2]));
+                if (mm[s2] >= 0) mbar_wait(su32(&done[s2]), par(mm[s2]));
             }
         }
     }
@@ -237,7 +245,7 @@ int tc_wgrad(WgradArgs &a, long long n, int *flag, long long wait, cudaStream_t 
     // one CTA per SM: a few for each thin job (little to copy and multiply), the rest split
     // evenly among the three hidden layers' two M halves
     const long long sms = sm_count(dev);
-    const long long thin = std::max(1LL, std::min(tiles, std::min(4LL, sms / 32)));
+    const long long thin = std::max(1LL, std::min(tiles, std::min(8LL, sms / 19)));
     const long long wide = std::max(1LL, std::min(tiles, (sms - 4 * thin) / 6));
     for (int j = 0; j < 5; ++j) a.job[j].shares = (int32_t)(j < 3 ? wide : thin);
     const dim3 grid((unsigned)std::max(wide, thin), 2, 5);
