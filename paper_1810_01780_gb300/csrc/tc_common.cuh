@@ -1,6 +1,6 @@
 // tc_common.cuh -- helpers shared by the kernels that run on the 5th-generation tensor cores
 // (tcgen05): shared-memory matrix descriptors of the no-swizzle K-major layout, bounded
-// mbarrier waits, tensor-memory loads, BF16 packing and the erf-form GELU.
+// mbarrier waits, tensor-memory loads, BF16 packing and the erf-form GELU and its derivative.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -59,12 +59,40 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long lon
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-// d/dz gelu(z) = Phi(z) + z phi(z)
+// The erf-form GELU, gelu(z) = z Phi(z) with Phi(z) = (1 + erf(z / sqrt 2)) / 2, and its
+// derivative gelu'(z) = Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi).  erf is taken
+// from Abramowitz and Stegun, Handbook of Mathematical Functions, formula 7.1.26 (Hastings'
+// rational approximation, absolute error <= 1.5e-7): for x >= 0,
+//   erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),  t = 1 / (1 + p x),
+// so one exponential exp(-z^2 / 2) = exp(-x^2) (x = |z| / sqrt 2) serves both Phi and phi.
+// Every activation is rounded to BF16 (relative precision 2^-9) before it enters a product,
+// far coarser than this error.
+struct PhiE {
+    float phi;  // Phi(z)
+    float e;    // exp(-z^2 / 2)
+};
+__device__ __forceinline__ PhiE phi_e(float z)
+{
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    float p = fmaf(t, 1.061405429f, -1.453152027f);
+    p = fmaf(t, p, 1.421413741f);
+    p = fmaf(t, p, -0.284496736f);
+    p = fmaf(t, p, 0.254829592f);
+    p *= t;
+    float e;  // 2^(-z^2 log2(e) / 2)
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(z * z * -0.72134752044448170f));
+    const float q = 0.5f * p * e;  // (1 - erf(x)) / 2
+    PhiE r;
+    r.phi = z >= 0.0f ? 1.0f - q : q;
+    r.e = e;
+    return r;
+}
+__device__ __forceinline__ float gelu(float z) { return z * phi_e(z).phi; }
 __device__ __forceinline__ float gelu_prime(float z)
 {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
-           z * expf(-0.5f * z * z) * 0.39894228040143268f;
+    const PhiE r = phi_e(z);
+    return fmaf(z * r.e, 0.39894228040143268f, r.phi);
 }
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 __device__ __forceinline__ uint32_t pack2(float lo, float hi)
