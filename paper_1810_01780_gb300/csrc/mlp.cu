@@ -46,10 +46,11 @@ struct LayerOffs {
     long long w[kLayers], b[kLayers];  // offsets of W_l and b_l in the flat parameter vector
 };
 
-// Inference operands of the fused kernel (layout: kPackW, kPackF and PF_* in rp_internal.h):
-// the hidden layers' weights W1..W3 as BF16 B operands (B[n][k] = W[k][n]) in the tensor
-// cores' no-swizzle K-major shared-memory image (8 x 8 core matrices of 128 contiguous bytes;
-// core (k/8, n/8) at ((k/8) * 32 + n/8) * 128), then the FP32 block.
+// Operands of the fused kernels (layout: kPackW, kPackF, PF_* and kPackW4F / kPackW4B in
+// rp_internal.h): the hidden layers' weights W1..W3 as BF16 B operands (B[n][k] = W[k][n]) in
+// the tensor cores' no-swizzle K-major shared-memory image (8 x 8 core matrices of 128
+// contiguous bytes; core (k/8, n/8) at ((k/8) * 32 + n/8) * 128), then the FP32 block, then
+// the last layer's two BF16 images (their padding stays zero from the pack's allocation).
 using rph::kPackF;
 using rph::kPackW;
 __global__ void k_pack(const float *__restrict__ p, unsigned char *__restrict__ pack, const LayerOffs L)
@@ -63,7 +64,15 @@ __global__ void k_pack(const float *__restrict__ p, unsigned char *__restrict__ 
         return;
     }
     const long long j = i - 3 * 65536;
-    if (j >= kPackF) return;
+    if (j >= kPackF) {
+        const long long e = j - kPackF;  // the last layer's images
+        if (e >= 256 * 12) return;
+        const int k = (int)(e / 12), o = (int)(e % 12);
+        const __nv_bfloat16 b = __float2bfloat16_rn(p[L.w[4] + e]);
+        *(__nv_bfloat16 *)(pack + rph::kPackW4F + rph::w4f_off(k, o)) = b;
+        *(__nv_bfloat16 *)(pack + rph::kPackW4B + rph::w4b_off(k, o)) = b;
+        return;
+    }
     float v = 0.0f;
     if (j < rph::PF_B0)
         v = __bfloat162float(__float2bfloat16_rn(p[L.w[0] + (j - rph::PF_W0)]));
@@ -127,9 +136,12 @@ __global__ void k_adam_pack(float *__restrict__ p, __nv_bfloat16 *__restrict__ p
         }
     } else {  // W4 (BF16-rounded), b4
         const int e = (int)(i - kW4);
-        if (e < 256 * 12)
+        if (e < 256 * 12) {
             pf[rph::PF_W4 + e] = __bfloat162float(b);
-        else
+            const int k = e / 12, o = e % 12;
+            *(__nv_bfloat16 *)(pack + rph::kPackW4F + rph::w4f_off(k, o)) = b;
+            *(__nv_bfloat16 *)(pack + rph::kPackW4B + rph::w4b_off(k, o)) = b;
+        } else
             pf[rph::PF_B4 + (e - 256 * 12)] = pi;
     }
 }
@@ -214,8 +226,8 @@ long long wait_cycles(const rp_surrogate_s *s) { return s->wait > 0 ? s->wait : 
 int ensure_pack(rp_surrogate_s *s, cudaStream_t st)
 {
     if (!s->pack) {
-        RP_CUDA_TRY(cudaMalloc(&s->pack, 3 * kPackW + sizeof(float) * kPackF));
-        RP_CUDA_TRY(cudaMemsetAsync(s->pack, 0, 3 * kPackW + sizeof(float) * kPackF, st));
+        RP_CUDA_TRY(cudaMalloc(&s->pack, kPackBytes));
+        RP_CUDA_TRY(cudaMemsetAsync(s->pack, 0, kPackBytes, st));
         s->pack_version = -1;
     }
     if (!s->pack_t) {
@@ -223,7 +235,7 @@ int ensure_pack(rp_surrogate_s *s, cudaStream_t st)
         s->pack_version = -1;
     }
     if (s->pack_version == s->version) return RP_OK;
-    const long long total = 3 * 65536 + kPackF;
+    const long long total = 3 * 65536 + kPackF + 256 * 12;
     LayerOffs L;
     for (int l = 0; l < kLayers; ++l) {
         L.w[l] = layer_w(l);

@@ -66,17 +66,13 @@ constexpr uint32_t SM_SLOT = SM_BAR + 32;        // TMEM address, then the abort
 constexpr uint32_t SM_TOTAL = SM_BAR + 64;
 static_assert(SM_TOTAL <= 227 * 1024, "shared memory map exceeds a CTA's limit");
 static_assert(SM_F % 16 == 0 && SM_BAR % 8 == 0, "alignment");
-// after the third MMA of a tile A tile 1 is free: it takes the last layer's partial sums of
-// column groups 1..3 (3 x 128 rows x 12), both CTAs' per-row sums (2 x 128 x 12; the peer
-// writes its own into slot [peer rank]) and the rows' output gradients g4 (128 x 12)
-constexpr uint32_t SM_P = SM_A1, SM_X = SM_P + (kGroups - 1) * kTile * 12 * 4;
-constexpr uint32_t SM_G4 = SM_X + 2 * kTile * 12 * 4;
-static_assert(SM_G4 + kTile * 12 * 4 <= SM_A1 + 65536, "the last layer's scratch fits A tile 1");
-static_assert(SM_X % 16 == 0, "alignment");
 
-// instruction descriptor: D FP32, A and B BF16, both K-major, N = 128, M = 128
+// instruction descriptors: D FP32, A and B BF16, both K-major, M = 128; N = 128 (a CTA's
+// columns of a layer) and N = 16 (the last layer, 12 outputs zero-padded)
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) |
                             ((128u >> 4) << 24);
+constexpr uint32_t kIdescN16 = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) |
+                               ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t cluster_rank()
 {
@@ -178,9 +174,9 @@ struct Pending {
     uint32_t ph_ld = 0, ph_mma = 0, ph_a = 0;
 };
 
-// Shared setup of both kernels: barriers, abort word, tensor memory (128 columns), then a
+// Shared setup of both kernels: barriers, abort word, `cols` columns of tensor memory, then a
 // cluster barrier (the peer's shared memory is in use only after it).
-__device__ __forceinline__ uint32_t setup_cta(unsigned char *sm, int tid, int warp)
+__device__ __forceinline__ uint32_t setup_cta(unsigned char *sm, int tid, int warp, uint32_t cols)
 {
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + SM_BAR);
     uint32_t *slot = reinterpret_cast<uint32_t *>(sm + SM_SLOT);
@@ -193,7 +189,7 @@ __device__ __forceinline__ uint32_t setup_cta(unsigned char *sm, int tid, int wa
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)),
-                     "r"(128u)
+                     "r"(cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -205,11 +201,42 @@ __device__ __forceinline__ uint32_t setup_cta(unsigned char *sm, int tid, int wa
     return tmem;
 }
 
+// the last layer's two images into the B region: the forward image (8 KB) at b_base and the
+// CTA's half of the backward image (two K groups of 2 KB, 2 KB apart) at b_base + 8 KB
+__device__ __forceinline__ void load_w4(uint32_t b_base, const unsigned char *pack, int h,
+                                        uint32_t bar)
+{
+    mbar_expect(bar, 8192u + 4096u);
+    bulk_g2s(b_base, pack + kPackW4F, 8192u, bar);
+    for (int kg = 0; kg < 2; ++kg)
+        bulk_g2s(b_base + 8192u + kg * 2048u, pack + kPackW4B + kg * 4096 + h * 2048, 2048u, bar);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     bar)
+                 : "memory");
+}
+
+// What thread 0 copies into the B region once a layer's MMAs are done.
+enum { NEXT_NONE = 0, NEXT_HALF = 1, NEXT_W4 = 2 };
+
 // Thread 0: wait for the B image, issue the layer's MMAs from A tile `a_base`, wait for them
-// and start the copy of the next B image (img_next, or none); false once a wait gives up.
+// and start the next copy into the B region (a half image of `img`, the last layer's images
+// from the pack `img`, or none); false once a wait gives up.
 __device__ __forceinline__ bool run_layer(Pending &pd, uint32_t tmem, uint32_t a_base,
                                           uint32_t b_base, uint32_t bar_ld, uint32_t bar_mma,
-                                          const unsigned char *img_next, int h, long long wait)
+                                          int next, const unsigned char *img, int h, long long wait)
 {
     if (!mbar_wait(bar_ld, pd.ph_ld, wait)) return false;
     pd.ld = false;
@@ -219,17 +246,17 @@ __device__ __forceinline__ bool run_layer(Pending &pd, uint32_t tmem, uint32_t a
     if (!mbar_wait(bar_mma, pd.ph_mma, wait)) return false;
     pd.mma = false;
     pd.ph_mma ^= 1u;
-    if (img_next) {
-        load_half_image(b_base, img_next, h, bar_ld);
-        pd.ld = true;
-    }
+    if (next == NEXT_HALF) load_half_image(b_base, img, h, bar_ld);
+    if (next == NEXT_W4) load_w4(b_base, img, h, bar_ld);
+    pd.ld = next != NEXT_NONE;
     return true;
 }
 
 // Shared teardown: on failure record it and drain the issued work (default bound), pass the
 // last cluster barrier, free tensor memory.
 __device__ __forceinline__ void teardown_cta(unsigned char *sm, int tid, int warp, uint32_t tmem,
-                                             bool failed, const Pending &pd, int *flag)
+                                             uint32_t cols, bool failed, const Pending &pd,
+                                             int *flag)
 {
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + SM_BAR);
     if (tid == 0) {
@@ -241,7 +268,7 @@ __device__ __forceinline__ void teardown_cta(unsigned char *sm, int tid, int war
     __syncthreads();
     cluster_sync();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols)
                      : "memory");
     }
 }
@@ -261,9 +288,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     float *sF = reinterpret_cast<float *>(sm + SM_F);
-    float *sP = reinterpret_cast<float *>(sm + SM_P);
-    float *sX = reinterpret_cast<float *>(sm + SM_X);
-    float *sG = reinterpret_cast<float *>(sm + SM_G4);
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + SM_BAR);
     volatile int *abort_cta = reinterpret_cast<volatile int *>(sm + SM_SLOT + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -274,7 +298,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 
     const float4 *gF = reinterpret_cast<const float4 *>(pack + 3 * kPackW);
     for (int i = tid; i < kPackF / 4; i += kThreads) reinterpret_cast<float4 *>(sF)[i] = gF[i];
-    const uint32_t tmem = setup_cta(sm, tid, warp);
+    const uint32_t tmem = setup_cta(sm, tid, warp, 256u);
 
     Pending pd;
     const long long n_tiles = (n + kTile - 1) / kTile;
@@ -328,17 +352,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             }
         }
         cluster_sync();
-        float acc[12];
-#pragma unroll
-        for (int o = 0; o < 12; ++o) acc[o] = 0.0f;
 
         for (int l = 0; l < 3; ++l) {
             if (!failed) {
                 if (tid == 0) {
-                    const unsigned char *next =
-                        l < 2 ? pack + (l + 1) * kPackW : (tile + stride < n_tiles ? pack : nullptr);
+                    const int next = l < 2 ? NEXT_HALF : NEXT_W4;
+                    const unsigned char *img = l < 2 ? pack + (l + 1) * kPackW : pack;
                     if (!run_layer(pd, tmem, local + (l & 1) * 65536u, b_base, bar_ld, bar_mma,
-                                   next, h, wait))
+                                   next, img, h, wait))
                         *abort_cta = 1;
                 }
                 __syncthreads();
@@ -363,57 +384,48 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     }
                     const uint4 pk = pack8(hh);
                     *reinterpret_cast<uint4 *>(Hl + a_off(erow, k0)) = pk;
-                    if (l < 2) {
-                        store8(zt_at(Zs[l], tile, erow, k0), zz);
-                        const uint32_t off = abuf + a_off(erow, k0);
-                        *reinterpret_cast<uint4 *>(sm + off) = pk;
-                        st_cluster(remote + off, pk);
-                    } else {
+                    if (l < 2) store8(zt_at(Zs[l], tile, erow, k0), zz);
+                    const uint32_t off = abuf + a_off(erow, k0);
+                    *reinterpret_cast<uint4 *>(sm + off) = pk;
+                    st_cluster(remote + off, pk);
+                }
+            }
+            cluster_sync();
+        }
+        // the last layer (256 -> 12, as N = 16) from A tile 1 (H4) into TMEM columns 128..143
+        if (!failed) {
+            if (tid == 0) {
+                bool ok = mbar_wait(bar_ld, pd.ph_ld, wait);
+                if (ok) {
+                    pd.ld = false;
+                    pd.ph_ld ^= 1u;
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            const float hv = bf16r(hh[u]);
-                            const float *w4 = sF + PF_W4 + (k0 + u) * 12;
-#pragma unroll
-                            for (int o = 0; o < 12; ++o) acc[o] = fmaf(hv, w4[o], acc[o]);
-                        }
+                    for (int k = 0; k < 16; ++k)
+                        mma_bf16(tmem + 128u, sdesc(local + SM_A1 + k * 4096u, 2048u, 128u),
+                                 sdesc(b_base + k * 512u, 256u, 128u), kIdescN16, (uint32_t)k);
+                    mma_commit(bar_mma);
+                    pd.mma = true;
+                    ok = mbar_wait(bar_mma, pd.ph_mma, wait);
+                    if (ok) {
+                        pd.mma = false;
+                        pd.ph_mma ^= 1u;
                     }
                 }
-            }
-            if (l < 2) cluster_sync();
-        }
-        // last layer: the column groups' partial sums of each row meet in shared memory, then
-        // the two CTAs' sums in both CTAs' slots
-        if (!failed) {
-            if (ch > 0) {
-#pragma unroll
-                for (int o = 0; o < 12; ++o) sP[((ch - 1) * kTile + erow) * 12 + o] = acc[o];
+                if (!ok) *abort_cta = 1;
             }
             __syncthreads();
-            if (ch == 0) {
-                float ps[12];
-#pragma unroll
-                for (int o = 0; o < 12; ++o) {
-                    float v = acc[o];
-                    for (int g = 1; g < kGroups; ++g) v += sP[((g - 1) * kTile + erow) * 12 + o];
-                    ps[o] = v;
-                }
-                const uint32_t off = SM_X + (uint32_t)((h * kTile + erow) * 48);
-#pragma unroll
-                for (int o = 0; o < 12; o += 4) {
-                    const uint4 pk = make_uint4(__float_as_uint(ps[o]), __float_as_uint(ps[o + 1]),
-                                                __float_as_uint(ps[o + 2]), __float_as_uint(ps[o + 3]));
-                    *reinterpret_cast<uint4 *>(sm + off + o * 4) = pk;
-                    st_cluster(remote + off + o * 4, pk);
-                }
-            }
+            fence_after();
+            failed = *abort_cta != 0;
         }
-        cluster_sync();
         if (!failed) {
             if (ch == 0) {
                 // output, loss and its gradient g4 per row (logistic loss of the existence
                 // logits, half the squared error of the regression outputs of existing slots,
-                // over n); both CTAs compute them alike, CTA 0 stores them
+                // over n); both CTAs compute them alike, CTA 0 stores them.  g4 in BF16 goes to
+                // A tile 1 (free now) as the next MMA's A operand (K = 16).
                 const long long gr = g0 + erow;
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + 128u, v);
                 float L = 0.0f;
                 float gg[12];
 #pragma unroll
@@ -421,8 +433,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 if (gr < n) {
                     float out[12];
 #pragma unroll
-                    for (int o = 0; o < 12; ++o)
-                        out[o] = (sX[erow * 12 + o] + sX[(kTile + erow) * 12 + o]) + sF[PF_B4 + o];
+                    for (int o = 0; o < 12; ++o) out[o] = __uint_as_float(v[o]) + sF[PF_B4 + o];
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
                         const float z = out[6 * k], yk = y[gr * 2 + k];
@@ -436,56 +447,81 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                         }
                     }
                 }
-#pragma unroll
-                for (int o = 0; o < 12; ++o) sG[erow * 12 + o] = bf16r(gg[o]);
+                const uint4 p0 = make_uint4(pack2(gg[0], gg[1]), pack2(gg[2], gg[3]),
+                                            pack2(gg[4], gg[5]), pack2(gg[6], gg[7]));
+                const uint4 p1 = make_uint4(pack2(gg[8], gg[9]), pack2(gg[10], gg[11]), 0u, 0u);
+                *reinterpret_cast<uint4 *>(sm + SM_A1 + a_off(erow, 0)) = p0;
+                *reinterpret_cast<uint4 *>(sm + SM_A1 + a_off(erow, 8)) = p1;
                 if (h == 0) {  // g4 as a 16-column image, its column sums, the loss
+                    unsigned char *G4t = G4 + tile * kImage16;
+                    *reinterpret_cast<uint4 *>(G4t + a_off(erow, 0)) = p0;
+                    *reinterpret_cast<uint4 *>(G4t + a_off(erow, 8)) = p1;
                     float cs[16];
 #pragma unroll
                     for (int o = 0; o < 16; ++o) cs[o] = o < 12 ? gg[o] : 0.0f;
-                    unsigned char *G4t = G4 + tile * kImage16;
-                    *reinterpret_cast<uint4 *>(G4t + a_off(erow, 0)) =
-                        make_uint4(pack2(gg[0], gg[1]), pack2(gg[2], gg[3]), pack2(gg[4], gg[5]),
-                                   pack2(gg[6], gg[7]));
-                    *reinterpret_cast<uint4 *>(G4t + a_off(erow, 8)) =
-                        make_uint4(pack2(gg[8], gg[9]), pack2(gg[10], gg[11]), 0u, 0u);
                     const float sum = warp_colsum<16>(cs, lane);
                     if (lane < 12) atomicAdd(db4 + lane, sum);
                     for (int d = 16; d > 0; d >>= 1) L += __shfl_xor_sync(0xffffffffu, L, d);
                     if (lane == 0) atomicAdd(loss, (double)L);
                 }
             }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            fence_before();
             __syncthreads();
+            fence_after();
+            // g4 W4^T for the CTA's 128 columns: one MMA (K = 16) into TMEM columns 128..255
+            if (tid == 0) {
+                mma_bf16(tmem + 128u, sdesc(local + SM_A1, 2048u, 128u),
+                         sdesc(b_base + 8192u, 2048u, 128u), kIdesc, 0u);
+                mma_commit(bar_mma);
+                pd.mma = true;
+                bool ok = mbar_wait(bar_mma, pd.ph_mma, wait);
+                if (ok) {
+                    pd.mma = false;
+                    pd.ph_mma ^= 1u;
+                    if (tile + stride < n_tiles) {
+                        load_half_image(b_base, pack, h, bar_ld);
+                        pd.ld = true;
+                    }
+                } else {
+                    *abort_cta = 1;
+                }
+            }
+            __syncthreads();
+            fence_after();
+            failed = *abort_cta != 0;
+        }
+        if (!failed) {
             // last layer backward: g3 = (g4 W4^T) gelu'(z3), z3 read again from tensor memory
-            const int col0 = ch * kGroupCols, gc0 = h * kHalf + col0;
             const float *bias = sF + PF_B1 + 2 * 256;
             unsigned char *G3t = G3 + tile * kImage;
-            float gr4[12];
+#pragma unroll 1
+            for (int c = 0; c < 2; ++c) {
+                const int col0 = ch * kGroupCols + c * 16, gc0 = h * kHalf + col0;
+                uint32_t vz[16], vd[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, vz);
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + 128u + (uint32_t)col0, vd);
+                float cs[16];  // this row's g3 of the 16 columns, for the column sums
 #pragma unroll
-            for (int o = 0; o < 12; ++o) gr4[o] = sG[erow * 12 + o];
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, v);
-            float cs[32];  // this row's g3 of the 32 columns, for the column sums
+                for (int e = 0; e < 2; ++e) {
+                    float gg[8];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                float gg[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int col = gc0 + e * 8 + u;
-                    const float *w4 = sF + PF_W4 + col * 12;
-                    float s = 0.0f;
-#pragma unroll
-                    for (int o = 0; o < 12; ++o) s = fmaf(gr4[o], w4[o], s);
-                    gg[u] = s * gelu_prime(__uint_as_float(v[e * 8 + u]) + bias[col]);
-                    cs[e * 8 + u] = gg[u];
+                    for (int u = 0; u < 8; ++u) {
+                        const int j = e * 8 + u;
+                        gg[u] = __uint_as_float(vd[j]) *
+                                gelu_prime(__uint_as_float(vz[j]) + bias[gc0 + j]);
+                        cs[j] = gg[u];
+                    }
+                    *reinterpret_cast<uint4 *>(G3t + a_off(erow, gc0 + e * 8)) = pack8(gg);
                 }
-                *reinterpret_cast<uint4 *>(G3t + a_off(erow, gc0 + e * 8)) = pack8(gg);
+                const float sum = warp_colsum<16>(cs, lane);
+                if (lane < 16) atomicAdd(db3 + gc0 + lane, sum);
             }
-            atomicAdd(db3 + gc0 + lane, warp_colsum<32>(cs, lane));
             fence_before();
             __syncthreads();
         }
     }
-    teardown_cta(sm, tid, warp, tmem, failed, pd, flag);
+    teardown_cta(sm, tid, warp, tmem, 256u, failed, pd, flag);
 }
 
 // Backward-data chain of the hidden layers for n rows: from the g3 image and the tiled
@@ -508,7 +544,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const uint32_t b_base = su32(sm + SM_B);
     const int h = (int)cluster_rank(), peer = h ^ 1;
     const uint32_t local = su32(sm), remote = peer_addr(local, (uint32_t)peer);
-    const uint32_t tmem = setup_cta(sm, tid, warp);
+    const uint32_t tmem = setup_cta(sm, tid, warp, 128u);
 
     Pending pd;
     const long long n_tiles = (n + kTile - 1) / kTile;
@@ -541,11 +577,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                             pd.ph_a ^= 1u;
                         }
                     }
-                    const unsigned char *next =
-                        l < 2 ? pack_t + (1 - l) * kPackW
-                              : (tile + stride < n_tiles ? pack_t + 2 * kPackW : nullptr);
+                    const int next = l < 2 || tile + stride < n_tiles ? NEXT_HALF : NEXT_NONE;
+                    const unsigned char *img = pack_t + (l < 2 ? 1 - l : 2) * kPackW;
                     if (!ok || !run_layer(pd, tmem, local + (l & 1) * 65536u, b_base, bar_ld,
-                                          bar_mma, next, h, wait))
+                                          bar_mma, next, img, h, wait))
                         *abort_cta = 1;
                 }
                 __syncthreads();
@@ -589,7 +624,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             __syncthreads();
         }
     }
-    teardown_cta(sm, tid, warp, tmem, failed, pd, flag);
+    teardown_cta(sm, tid, warp, tmem, 128u, failed, pd, flag);
 }
 
 }  // namespace

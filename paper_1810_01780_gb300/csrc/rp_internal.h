@@ -170,6 +170,23 @@ int run_find_paths(rp_medium_t m, int64_t n_pairs, const double *zs, const doubl
 constexpr long long kPackW = 256LL * 256 * 2;
 constexpr int kPackF = 768 + 4 * 256 + 3072 + 16;
 enum { PF_W0 = 0, PF_B0 = 768, PF_B1 = 1024, PF_W4 = 1792, PF_B4 = 4864 };
+// Then the last layer's weights as two BF16 tensor-core images (8 KB each, outputs zero-padded
+// from 12 to 16), for training: at kPackW4F the forward B image B[o][k] = W4[k][o] (K = 256
+// hidden inputs, N = 16; core (k / 8, o / 8) at ((k / 8) * 2 + o / 8) * 128), at kPackW4B the
+// backward one B[n][o] = W4[n][o] (K = 16, N = 256; core (o / 8, n / 8) at
+// ((o / 8) * 32 + n / 8) * 128).
+constexpr long long kPackW4F = 3 * kPackW + 4LL * kPackF;
+constexpr long long kPackW4B = kPackW4F + 8192;
+constexpr long long kPackBytes = kPackW4B + 8192;
+static_assert(kPackW4F % 16 == 0, "bulk-copy alignment");
+__host__ __device__ constexpr long long w4f_off(int k, int o)
+{
+    return ((k >> 3) * 2 + (o >> 3)) * 128 + (o & 7) * 16 + (k & 7) * 2;
+}
+__host__ __device__ constexpr long long w4b_off(int n, int o)
+{
+    return ((o >> 3) * 32 + (n >> 3)) * 128 + (n & 7) * 16 + (o & 7) * 2;
+}
 
 // Surrogate network (mlp.cu) and its path-finding pipeline buffers (pathfind.cu).
 int ensure_acts(rp_surrogate_s *s, long long n);
