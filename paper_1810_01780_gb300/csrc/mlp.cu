@@ -48,9 +48,9 @@ struct LayerOffs {
 
 // Operands of the fused kernels (layout: kPackW, kPackF, PF_* and kPackW4F / kPackW4B in
 // rp_internal.h): the hidden layers' weights W1..W3 as BF16 B operands (B[n][k] = W[k][n]) in
-// the tensor cores' no-swizzle K-major shared-memory image (8 x 8 core matrices of 128
-// contiguous bytes; core (k/8, n/8) at ((k/8) * 32 + n/8) * 128), then the FP32 block, then
-// the last layer's two BF16 images (their padding stays zero from the pack's allocation).
+// the tensor cores' no-swizzle K-major shared-memory image, the two halves of n one after the
+// other (bimg_off), then the FP32 block, then the last layer's two BF16 images (their padding
+// stays zero from the pack's allocation).
 using rph::kPackF;
 using rph::kPackW;
 __global__ void k_pack(const float *__restrict__ p, unsigned char *__restrict__ pack, const LayerOffs L)
@@ -59,8 +59,7 @@ __global__ void k_pack(const float *__restrict__ p, unsigned char *__restrict__ 
     if (i < 3 * 65536) {
         const int l = (int)(i / 65536), e = (int)(i % 65536), k = e / 256, n = e % 256;
         const float w = p[L.w[l + 1] + (long long)k * 256 + n];
-        const long long off = l * kPackW + ((k >> 3) * 32 + (n >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2;
-        *(__nv_bfloat16 *)(pack + off) = __float2bfloat16_rn(w);
+        *(__nv_bfloat16 *)(pack + l * kPackW + rph::bimg_off(k, n)) = __float2bfloat16_rn(w);
         return;
     }
     const long long j = i - 3 * 65536;
@@ -127,10 +126,8 @@ __global__ void k_adam_pack(float *__restrict__ p, __nv_bfloat16 *__restrict__ p
         const int l = (int)((i - kW1) / kHidden), e = (int)((i - kW1) % kHidden);
         if (e < 65536) {
             const int row = e >> 8, col = e & 255;  // W[row][col]: input row, output col
-            *(__nv_bfloat16 *)(pack + l * kPackW + ((row >> 3) * 32 + (col >> 3)) * 128 +
-                               (col & 7) * 16 + (row & 7) * 2) = b;
-            *(__nv_bfloat16 *)(pack_t + l * kPackW + ((col >> 3) * 32 + (row >> 3)) * 128 +
-                               (row & 7) * 16 + (col & 7) * 2) = b;
+            *(__nv_bfloat16 *)(pack + l * kPackW + rph::bimg_off(row, col)) = b;
+            *(__nv_bfloat16 *)(pack_t + l * kPackW + rph::bimg_off(col, row)) = b;
         } else {
             pf[rph::PF_B1 + l * 256 + (e - 65536)] = pi;
         }

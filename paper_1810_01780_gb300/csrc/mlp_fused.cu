@@ -7,15 +7,16 @@
 //   layers 1..3 (256 -> 256): the layer's packed BF16 weights (128 KB) arrive in shared memory
 //     by bulk copy (cp.async.bulk, completion on an mbarrier), issued as soon as the previous
 //     layer's MMAs have released the B tile so that the copy overlaps the epilogue; one thread
-//     issues 16 tcgen05.mma (M = 128, N = 256, K = 16 each, FP32 accumulators in tensor memory)
-//     and commits them to a second mbarrier; the sixteen warps read the accumulators back
+//     issues 2 x 16 tcgen05.mma (M = 128, N = 128 (one half of the output columns each),
+//     K = 16, FP32 accumulators in tensor memory, 256 columns) and commits them to a second
+//     mbarrier; the sixteen warps read the accumulators back
 //     (tcgen05.ld, warp w reads lanes 32 (w % 4) .. + 31 and columns 64 (w / 4) .. + 63),
 //     add the bias, apply GELU and write the BF16 result into the A tile for the next layer;
 //   layer 4 (256 -> 12) on the CUDA cores from the last layer's BF16-rounded activations.
 // Operand images use the no-swizzle K-major layout of the tensor cores: 8 x 8 core matrices of
 // 128 contiguous bytes; for A (128 rows x 256 k) core (k/8, row/8) sits at
-// ((k/8) * 16 + row/8) * 128 (K-direction stride 2048 B, 8-row stride 128 B); for B (256 n x 256
-// k) core (k/8, n/8) at ((k/8) * 32 + n/8) * 128 (4096 B, 128 B).  Arithmetic is that of the
+// ((k/8) * 16 + row/8) * 128 (K-direction stride 2048 B, 8-row stride 128 B); B (256 n x 256 k)
+// holds its two halves of n one after the other, each laid out like A.  Arithmetic is that of the
 // unfused path: BF16 operands, FP32 products and sums, FP32 bias and GELU.
 // Every wait on an mbarrier is bounded (by default about two seconds; rp_surrogate_set_wait_limit
 // sets it); a CTA that gives up sets the error flag, waits (with the default bound) for its work
@@ -48,8 +49,9 @@ static_assert(SM_TOTAL <= 227 * 1024, "shared memory map exceeds a CTA's limit")
 static_assert(SM_F % 16 == 0 && SM_BAR % 8 == 0, "alignment");
 static_assert((kGroups - 1) * kTile * 12 * 4 <= 65536, "layer-4 partial sums reuse the A tile");
 
-// instruction descriptor: D FP32, A and B BF16, both K-major, N = 256, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) |
+// instruction descriptor: D FP32, A and B BF16, both K-major, N = 128 (one half of the
+// layer's output columns), M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) |
                             ((128u >> 4) << 24);
 
 // one hidden layer's packed weights (kWBytes) into the B tile, completion on `bar`
@@ -156,14 +158,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (mbar_wait(bar_ld, ph_ld, wait)) {
                     ld_pending = false;
 #pragma unroll
-                    for (int s = 0; s < 16; ++s) {
-                        const uint64_t ad = sdesc(a_base + s * 4096u, 2048u, 128u);
-                        const uint64_t bd = sdesc(b_base + s * 8192u, 4096u, 128u);
-                        asm volatile(
-                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                            "l"(ad), "l"(bd), "r"(kIdesc), "r"(s)
-                            : "memory");
+                    for (int hf = 0; hf < 2; ++hf) {  // output columns 128 hf .. 128 hf + 127
+#pragma unroll
+                        for (int s = 0; s < 16; ++s) {
+                            const uint64_t ad = sdesc(a_base + s * 4096u, 2048u, 128u);
+                            const uint64_t bd = sdesc(b_base + hf * 65536u + s * 4096u, 2048u, 128u);
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                                    tmem + hf * 128u),
+                                "l"(ad), "l"(bd), "r"(kIdesc), "r"(s)
+                                : "memory");
+                        }
                     }
                     asm volatile(
                         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(

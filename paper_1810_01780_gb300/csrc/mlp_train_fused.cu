@@ -117,15 +117,14 @@ __device__ __forceinline__ void cluster_sync()
     fence_after();
 }
 
-// the CTA's half (output columns 128 h ..) of a 256 x 256 B image: per 8-row K group, 16 core
-// matrices of 128 bytes (2 KB contiguous in the image) -> K groups 2 KB apart in shared memory
+// the CTA's half (output columns 128 h ..) of a 256 x 256 B image: 64 KB contiguous in the
+// half-major image (bimg_off), laid out like the A tile (K groups 2 KB apart)
 __device__ __forceinline__ void load_half_image(uint32_t b_base, const unsigned char *img, int h,
                                                 uint32_t bar)
 {
     mbar_expect(bar, kHalfImage);
-#pragma unroll 4
-    for (int kg = 0; kg < 32; ++kg)
-        bulk_g2s(b_base + kg * 2048u, img + (kg * 32 + 16 * h) * 128, 2048u, bar);
+    bulk_g2s(b_base, img + h * 65536, 32768u, bar);
+    bulk_g2s(b_base + 32768u, img + h * 65536 + 32768, 32768u, bar);
 }
 
 // 16 MMAs of one layer (A tile x half B image) into the accumulator, committed to bar_mma

@@ -222,7 +222,7 @@ __global__ void k_pack_t(const float *__restrict__ p, unsigned char *__restrict_
     const int l = (int)(i / 65536), e = (int)(i % 65536), nn = e / 256, k = e % 256;
     const long long w = l == 0 ? w1 : (l == 1 ? w2 : w3);
     const float v = p[w + (long long)nn * 256 + k];
-    const long long off = l * (long long)kImgB + ((k >> 3) * 32 + (nn >> 3)) * 128 + (nn & 7) * 16 + (k & 7) * 2;
+    const long long off = l * (long long)kImgB + bimg_off(k, nn);
     *(__nv_bfloat16 *)(img + off) = __float2bfloat16_rn(v);
 }
 

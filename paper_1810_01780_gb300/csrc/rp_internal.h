@@ -163,11 +163,22 @@ int run_find_paths(rp_medium_t m, int64_t n_pairs, const double *zs, const doubl
                    const double *dist, const int32_t *n_angles, const rp_path_params *p,
                    rp_solutions *sol, rp_stats *stats, cudaStream_t st);
 
-// Operands of the fused inference kernel (built by mlp.cu, read by mlp_fused.cu): the hidden
-// layers' weights W1..W3 as three BF16 images of kPackW bytes, then kPackF floats: W0 (3 x 256,
+// Operands of the fused kernels (built by mlp.cu, read by mlp_fused.cu and
+// mlp_train_fused.cu): the hidden layers' weights W1..W3 as three BF16 B images of kPackW bytes
+// (layout: bimg_off), then kPackF floats: W0 (3 x 256,
 // BF16-rounded) at PF_W0, b0 at PF_B0, b1..b3 from PF_B1 (256 each), W4 (256 x 12,
 // BF16-rounded) at PF_W4, b4 at PF_B4 (12, padded to 16).
 constexpr long long kPackW = 256LL * 256 * 2;
+// Byte offset of element (k, n) (K index k, N index n) in a 256 x 256 BF16 B image: the two
+// halves of the N columns one after the other (64 KB each, so a CTA that computes one half
+// copies it whole), each in the no-swizzle K-major layout of 8 x 8 core matrices of 128 bytes,
+// core (k / 8, (n % 128) / 8) at ((k / 8) * 16 + (n % 128) / 8) * 128 (K-direction stride
+// 2048 B, 8-column stride 128 B).
+__host__ __device__ constexpr long long bimg_off(int k, int n)
+{
+    return (long long)(n >> 7) * 65536 + ((k >> 3) * 16 + ((n & 127) >> 3)) * 128 + (n & 7) * 16 +
+           (k & 7) * 2;
+}
 constexpr int kPackF = 768 + 4 * 256 + 3072 + 16;
 enum { PF_W0 = 0, PF_B0 = 768, PF_B1 = 1024, PF_W4 = 1792, PF_B4 = 4864 };
 // Then the last layer's weights as two BF16 tensor-core images (8 KB each, outputs zero-padded
