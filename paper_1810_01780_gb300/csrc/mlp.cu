@@ -49,8 +49,8 @@ struct LayerOffs {
 // Operands of the fused kernels (layout: kPackW, kPackF, PF_* and kPackW4F / kPackW4B in
 // rp_internal.h): the hidden layers' weights W1..W3 as BF16 B operands (B[n][k] = W[k][n]) in
 // the tensor cores' no-swizzle K-major shared-memory image, the two halves of n one after the
-// other (bimg_off), then the FP32 block, then the last layer's two BF16 images (their padding
-// stays zero from the pack's allocation).
+// other (bimg_off), then the FP32 block, then the last layer's two BF16 images and the first
+// layer's (their padding stays zero from the pack's allocation).
 using rph::kPackF;
 using rph::kPackW;
 __global__ void k_pack(const float *__restrict__ p, unsigned char *__restrict__ pack, const LayerOffs L)
@@ -73,8 +73,12 @@ __global__ void k_pack(const float *__restrict__ p, unsigned char *__restrict__ 
         return;
     }
     float v = 0.0f;
-    if (j < rph::PF_B0)
-        v = __bfloat162float(__float2bfloat16_rn(p[L.w[0] + (j - rph::PF_W0)]));
+    if (j < rph::PF_B0) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(p[L.w[0] + (j - rph::PF_W0)]);
+        v = __bfloat162float(b);
+        const int e = (int)(j - rph::PF_W0);
+        *(__nv_bfloat16 *)(pack + rph::kPackW0 + rph::w0_off(e >> 8, e & 255)) = b;
+    }
     else if (j < rph::PF_B1)
         v = p[L.b[0] + (j - rph::PF_B0)];
     else if (j < rph::PF_W4)
@@ -118,9 +122,10 @@ __global__ void k_adam_pack(float *__restrict__ p, __nv_bfloat16 *__restrict__ p
     float *pf = reinterpret_cast<float *>(pack + 3 * kPackW);
     constexpr long long kW1 = layer_w(1), kW4 = layer_w(4), kHidden = 256LL * 256 + 256;
     if (i < kW1) {  // W0 (BF16-rounded), b0
-        if (i < 3 * 256)
+        if (i < 3 * 256) {
             pf[rph::PF_W0 + i] = __bfloat162float(b);
-        else
+            *(__nv_bfloat16 *)(pack + rph::kPackW0 + rph::w0_off((int)(i >> 8), (int)(i & 255))) = b;
+        } else
             pf[rph::PF_B0 + (i - 3 * 256)] = pi;
     } else if (i < kW4) {  // W1..W3 as both images, b1..b3
         const int l = (int)((i - kW1) / kHidden), e = (int)((i - kW1) % kHidden);

@@ -22,7 +22,8 @@
 //   image, its column sums added to db4), and the last layer's backward data pass
 //   g3 = (g4 W4^T) gelu'(z3) re-reads z3 from tensor memory, stores g3 as a BF16 image and
 //   adds its column sums to the bias gradient db3.
-// k_train_bwd: per tile, the g3 image by bulk copy as the A tile, then for the hidden layers
+// k_train_bwd: per tile, the g3 image by bulk copy as the A tile (prefetched while the previous
+//   tile's last epilogue runs), then for the hidden layers
 //   3, 2, 1 the backward images B[n][k] = W[n][k] and an epilogue
 //   g_{l-1} = (g_l W_l^T) gelu'(z_{l-1}) that stores g_{l-1} as a BF16 image, adds its column
 //   sums to db_{l-1} and, but for the last, feeds it to both CTAs' next A tile.
@@ -61,9 +62,12 @@ constexpr uint32_t SM_A0 = 0;
 constexpr uint32_t SM_A1 = 65536;
 constexpr uint32_t SM_B = 131072;
 constexpr uint32_t SM_F = SM_B + kHalfImage;
-constexpr uint32_t SM_BAR = SM_F + kPackF * 4;  // barriers: B image, MMAs, A tile (backward)
+constexpr uint32_t SM_BAR = SM_F + kPackF * 4;  // barriers: B image, MMAs, A tile / W0 image
 constexpr uint32_t SM_SLOT = SM_BAR + 32;        // TMEM address, then the abort word
-constexpr uint32_t SM_TOTAL = SM_BAR + 64;
+// forward only: the CTA's half of the W0 image (4 KB) and the x operand (128 rows x 16, 4 KB)
+constexpr uint32_t SM_W0 = (SM_BAR + 64 + 1023) / 1024 * 1024;
+constexpr uint32_t SM_XA = SM_W0 + 4096;
+constexpr uint32_t SM_TOTAL = SM_XA + 4096;
 static_assert(SM_TOTAL <= 227 * 1024, "shared memory map exceeds a CTA's limit");
 static_assert(SM_F % 16 == 0 && SM_BAR % 8 == 0, "alignment");
 
@@ -306,60 +310,77 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const int q = warp & 3, ch = warp >> 2;
     const int erow = q * 32 + lane;
     const float inv_n = 1.0f / (float)n;
-    float *Zs[2] = {Z1, Z2};
-    unsigned char *Hs[3] = {H2, H3, H4};
+    float *Zs[3] = {Z0, Z1, Z2};
+    unsigned char *Hs[4] = {H1, H2, H3, H4};
     bool failed = false;
+    const uint32_t bar_w0 = su32(&bar[2]);
     if (tid == 0 && first < n_tiles) {
         load_half_image(b_base, pack, h, bar_ld);
         pd.ld = true;
+        mbar_expect(bar_w0, 4096u);  // the W0 half, once
+        bulk_g2s(local + SM_W0, pack + kPackW0 + h * 4096, 4096u, bar_w0);
+        pd.a = true;
     }
 
     for (long long tile = first; tile < n_tiles; tile += stride) {
         const long long g0 = tile * kTile;
-        if (!failed) {  // layer 0 on the CUDA cores: z0, and gelu(z0) to both A tiles 0
-            const long long gr = g0 + row0;
-            float x0 = 0.0f, x1 = 0.0f, x2 = 0.0f;
-            if (gr < n) {
-                x0 = bf16r(x[3 * gr]);
-                x1 = bf16r(x[3 * gr + 1]);
-                x2 = bf16r(x[3 * gr + 2]);
-            }
-            if (h == 0 && grp0 < 2) {  // the x image: columns 0..2, zero-padded to 16
-                const uint4 pk = grp0 == 0 ? make_uint4(pack2(x0, x1), pack2(x2, 0.0f), 0u, 0u)
-                                           : make_uint4(0u, 0u, 0u, 0u);
-                *reinterpret_cast<uint4 *>(Xi + tile * kImage16 + a_off(row0, grp0 * 8)) = pk;
-            }
-#pragma unroll 1
-            for (int c = 0; c < kGroupCols / 8; ++c) {
-                const int k0 = h * kHalf + grp0 * kGroupCols + c * 8;
-                float zz[8], hh[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int j = k0 + e;
-                    float z = x0 * sF[PF_W0 + j];
-                    z = fmaf(x1, sF[PF_W0 + 256 + j], z);
-                    z = fmaf(x2, sF[PF_W0 + 512 + j], z);
-                    zz[e] = z + sF[PF_B0 + j];
-                    hh[e] = gelu(zz[e]);
+        if (!failed) {
+            if (grp0 == 0) {  // one thread per row: x in BF16 as the layer-0 A operand (K 16)
+                const long long gr = g0 + row0;
+                float x0 = 0.0f, x1 = 0.0f, x2 = 0.0f;
+                if (gr < n) {
+                    x0 = x[3 * gr];
+                    x1 = x[3 * gr + 1];
+                    x2 = x[3 * gr + 2];
                 }
-                store8(zt_at(Z0, tile, row0, k0), zz);
-                const uint4 pk = pack8(hh);
-                const uint32_t off = SM_A0 + a_off(row0, k0);
-                *reinterpret_cast<uint4 *>(sm + off) = pk;
-                st_cluster(remote + off, pk);
-                *reinterpret_cast<uint4 *>(H1 + tile * kImage + a_off(row0, k0)) = pk;
+                const uint4 p0 = make_uint4(pack2(x0, x1), pack2(x2, 0.0f), 0u, 0u);
+                const uint4 p1 = make_uint4(0u, 0u, 0u, 0u);
+                *reinterpret_cast<uint4 *>(sm + SM_XA + a_off(row0, 0)) = p0;
+                *reinterpret_cast<uint4 *>(sm + SM_XA + a_off(row0, 8)) = p1;
+                if (h == 0) {  // the x image, zero-padded to 16 columns
+                    *reinterpret_cast<uint4 *>(Xi + tile * kImage16 + a_off(row0, 0)) = p0;
+                    *reinterpret_cast<uint4 *>(Xi + tile * kImage16 + a_off(row0, 8)) = p1;
+                }
             }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
-        cluster_sync();
 
-        for (int l = 0; l < 3; ++l) {
+        // layer 0 (one MMA, K = 16) and the hidden layers 1..3 (16 MMAs each) into TMEM columns
+        // 0..127; the epilogue of layer l writes gelu(z_l) (H_{l+1}) to A tile l % 2 of both CTAs
+        for (int l = 0; l < 4; ++l) {
             if (!failed) {
+                fence_before();
+                __syncthreads();
+                fence_after();
                 if (tid == 0) {
-                    const int next = l < 2 ? NEXT_HALF : NEXT_W4;
-                    const unsigned char *img = l < 2 ? pack + (l + 1) * kPackW : pack;
-                    if (!run_layer(pd, tmem, local + (l & 1) * 65536u, b_base, bar_ld, bar_mma,
-                                   next, img, h, wait))
-                        *abort_cta = 1;
+                    bool ok;
+                    if (l == 0) {
+                        ok = true;
+                        if (pd.a) {
+                            ok = mbar_wait(bar_w0, pd.ph_a, wait);
+                            if (ok) {
+                                pd.a = false;
+                                pd.ph_a ^= 1u;
+                            }
+                        }
+                        if (ok) {
+                            mma_bf16(tmem, sdesc(local + SM_XA, 2048u, 128u),
+                                     sdesc(local + SM_W0, 2048u, 128u), kIdesc, 0u);
+                            mma_commit(bar_mma);
+                            pd.mma = true;
+                            ok = mbar_wait(bar_mma, pd.ph_mma, wait);
+                            if (ok) {
+                                pd.mma = false;
+                                pd.ph_mma ^= 1u;
+                            }
+                        }
+                    } else {
+                        const int next = l < 3 ? NEXT_HALF : NEXT_W4;
+                        const unsigned char *img = l < 3 ? pack + l * kPackW : pack;
+                        ok = run_layer(pd, tmem, local + ((l - 1) & 1) * 65536u, b_base, bar_ld,
+                                       bar_mma, next, img, h, wait);
+                    }
+                    if (!ok) *abort_cta = 1;
                 }
                 __syncthreads();
                 fence_after();
@@ -367,9 +388,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             }
             if (!failed) {
                 const int col0 = ch * kGroupCols, gc0 = h * kHalf + col0;
-                const float *bias = sF + PF_B1 + l * 256;
+                const float *bias = sF + (l == 0 ? PF_B0 : PF_B1 + (l - 1) * 256);
                 unsigned char *Hl = Hs[l] + tile * kImage;
-                const uint32_t abuf = ((l + 1) & 1) * 65536u;
+                const uint32_t abuf = (l & 1) * 65536u;
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, v);
 #pragma unroll
@@ -383,7 +404,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     }
                     const uint4 pk = pack8(hh);
                     *reinterpret_cast<uint4 *>(Hl + a_off(erow, k0)) = pk;
-                    if (l < 2) store8(zt_at(Zs[l], tile, erow, k0), zz);
+                    if (l < 3) store8(zt_at(Zs[l], tile, erow, k0), zz);
                     const uint32_t off = abuf + a_off(erow, k0);
                     *reinterpret_cast<uint4 *>(sm + off) = pk;
                     st_cluster(remote + off, pk);
@@ -554,9 +575,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     unsigned char *Gout[3] = {G2, G1, G0};
     float *dbs[3] = {db2, db1, db0};
     bool failed = false;
+    // the g3 image of a tile is the first A tile: copied as soon as A tile 0 is free (at the
+    // start, then once the previous tile's last MMAs are done)
+    auto load_g3 = [&](long long tl) {
+        mbar_expect(bar_a, kImage);
+        bulk_g2s(local + SM_A0, G3 + tl * kImage, kImage / 2, bar_a);
+        bulk_g2s(local + SM_A0 + kImage / 2, G3 + tl * kImage + kImage / 2, kImage / 2, bar_a);
+        pd.a = true;
+    };
     if (tid == 0 && first < n_tiles) {  // layer 3's image first
         load_half_image(b_base, pack_t + 2 * kPackW, h, bar_ld);
         pd.ld = true;
+        load_g3(first);
     }
 
     for (long long tile = first; tile < n_tiles; tile += stride) {
@@ -564,12 +594,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             if (!failed) {
                 if (tid == 0) {
                     bool ok = true;
-                    if (l == 0) {  // the tile's g3 image is the first A tile
-                        mbar_expect(bar_a, kImage);
-                        bulk_g2s(local + SM_A0, G3 + tile * kImage, kImage / 2, bar_a);
-                        bulk_g2s(local + SM_A0 + kImage / 2, G3 + tile * kImage + kImage / 2,
-                                 kImage / 2, bar_a);
-                        pd.a = true;
+                    if (l == 0) {
                         ok = mbar_wait(bar_a, pd.ph_a, wait);
                         if (ok) {
                             pd.a = false;
@@ -581,6 +606,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     if (!ok || !run_layer(pd, tmem, local + (l & 1) * 65536u, b_base, bar_ld,
                                           bar_mma, next, img, h, wait))
                         *abort_cta = 1;
+                    else if (l == 2 && tile + stride < n_tiles)
+                        load_g3(tile + stride);  // A tile 0 read for the last time this tile
                 }
                 __syncthreads();
                 fence_after();

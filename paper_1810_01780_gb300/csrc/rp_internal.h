@@ -188,7 +188,11 @@ enum { PF_W0 = 0, PF_B0 = 768, PF_B1 = 1024, PF_W4 = 1792, PF_B4 = 4864 };
 // ((o / 8) * 32 + n / 8) * 128).
 constexpr long long kPackW4F = 3 * kPackW + 4LL * kPackF;
 constexpr long long kPackW4B = kPackW4F + 8192;
-constexpr long long kPackBytes = kPackW4B + 8192;
+// Then the first layer's weights as a BF16 B image for training, B[n][k] = W0[k][n] (K = 3
+// inputs zero-padded to 16, N = 256), half-major like the hidden layers' (4 KB per half; core
+// (k / 8, (n % 128) / 8) at ((k / 8) * 16 + (n % 128) / 8) * 128 within its half).
+constexpr long long kPackW0 = kPackW4B + 8192;
+constexpr long long kPackBytes = kPackW0 + 8192;
 static_assert(kPackW4F % 16 == 0, "bulk-copy alignment");
 __host__ __device__ constexpr long long w4f_off(int k, int o)
 {
@@ -197,6 +201,11 @@ __host__ __device__ constexpr long long w4f_off(int k, int o)
 __host__ __device__ constexpr long long w4b_off(int n, int o)
 {
     return ((o >> 3) * 32 + (n >> 3)) * 128 + (n & 7) * 16 + (o & 7) * 2;
+}
+__host__ __device__ constexpr long long w0_off(int k, int n)
+{
+    return (long long)(n >> 7) * 4096 + ((k >> 3) * 16 + ((n & 127) >> 3)) * 128 + (n & 7) * 16 +
+           (k & 7) * 2;
 }
 
 // Surrogate network (mlp.cu) and its path-finding pipeline buffers (pathfind.cu).
