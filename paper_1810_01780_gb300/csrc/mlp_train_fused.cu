@@ -6,11 +6,14 @@
 // rows at a time and CTA h of the pair (its rank in the cluster) computes output columns
 // 128 h .. 128 h + 127 of every 256-wide layer: 16 tcgen05.mma of M 128, N 128, K 16 from the
 // whole 128 x 256 BF16 A tile and its half of the layer's B image (bulk-copied, 64 KB) into a
-// 128-column TMEM accumulator, then an epilogue by sixteen warps.  The epilogue stores its half
-// of the layer's output, in BF16, both into its own next A tile and into the peer's (a
-// distributed shared-memory store), so that after one cluster barrier each CTA holds the whole
-// next A tile.  The A tile is double-buffered (layer l reads buffer l % 2, its epilogue writes
-// buffer (l + 1) % 2), so no CTA writes a buffer its peer's MMAs may still be reading.
+// 128-column TMEM accumulator, then an epilogue by sixteen warps.  The epilogue writes its half
+// of the layer's output, in BF16, into its own next A tile, and one thread copies that half
+// (32 KB, contiguous) into the peer's (a shared-to-shared bulk copy that completes on an
+// mbarrier of the peer), so that each CTA holds the whole next A tile without a cluster-wide
+// barrier.  The A tile is double-buffered (the MMAs read one buffer while the epilogue fills
+// the other) with one exchange barrier per buffer; a CTA sends a layer's half only after its
+// MMAs used the peer's half of the layer before, which the peer sent after its own MMAs had
+// read the buffer the new half goes to, so no copy lands in a buffer still being read.
 //
 // k_train_fwd: layer 0 (3 -> 256) on the CUDA cores, then the three 256 -> 256 layers.  The
 //   epilogues also store what the later kernels read: the pre-activations z0..z2 in FP32
@@ -33,11 +36,12 @@
 // tile is computed whole: its rows past n have zero output gradients, so they add nothing to
 // any gradient.
 // Synchronisation and failure: every mbarrier wait is bounded (the surrogate's wait limit).
-// The two CTAs of a cluster run the same tiles and pass the same sequence of cluster barriers
-// whatever happens: a CTA whose wait gives up sets the error flag and skips all further work
-// but keeps passing the barriers, and before it exits waits (with the default bound) for the
-// copies and MMAs it issued, passes one last cluster barrier (so that no CTA leaves while its
-// peer may still write into its shared memory) and frees its tensor memory.
+// A CTA whose wait gives up sets the error flag and skips all further work (sending no more
+// halves).  Before it exits each CTA waits (with the default bound) for the copies and MMAs it
+// issued, tells its peer how many halves it sent, waits for the peer's halves it has not
+// consumed, and passes a last cluster barrier, so that no CTA leaves while a copy into its
+// shared memory is in flight; the two CTAs pass the same three cluster barriers (one at the
+// start, two at the end) whatever happens.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -62,8 +66,9 @@ constexpr uint32_t SM_A0 = 0;
 constexpr uint32_t SM_A1 = 65536;
 constexpr uint32_t SM_B = 131072;
 constexpr uint32_t SM_F = SM_B + kHalfImage;
-constexpr uint32_t SM_BAR = SM_F + kPackF * 4;  // barriers: B image, MMAs, A tile / W0 image
-constexpr uint32_t SM_SLOT = SM_BAR + 32;        // TMEM address, then the abort word
+// barriers: B image, MMAs, A tile / W0 image, then the peer's halves of A tiles 0 and 1
+constexpr uint32_t SM_BAR = SM_F + kPackF * 4;
+constexpr uint32_t SM_SLOT = SM_BAR + 48;  // TMEM address, abort word, copies the peer sent
 // forward only: the CTA's half of the W0 image (4 KB) and the x operand (128 rows x 16, 4 KB)
 constexpr uint32_t SM_W0 = (SM_BAR + 64 + 1023) / 1024 * 1024;
 constexpr uint32_t SM_XA = SM_W0 + 4096;
@@ -103,15 +108,8 @@ __device__ __forceinline__ uint32_t peer_addr(uint32_t saddr, uint32_t rank)
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
     return r;
 }
-__device__ __forceinline__ void st_cluster(uint32_t addr, uint4 v)
-{
-    asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x),
-                 "r"(v.y), "r"(v.z), "r"(v.w)
-                 : "memory");
-}
-// All threads of both CTAs: the generic-proxy writes to either CTA's A tiles before it are
-// visible to both CTAs' MMAs (async proxy) and loads after it; tensor-memory accesses are
-// ordered across it.
+// All threads of both CTAs (at the start and the end of a kernel only): memory accesses of
+// either CTA before it happen before those after it.
 __device__ __forceinline__ void cluster_sync()
 {
     asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
@@ -171,23 +169,30 @@ __device__ __forceinline__ const float *zt_at(const float *Z, long long tile, in
 }
 
 // One CTA's state of the bounded waits: whether a copy (or MMAs) is in flight and the phase
-// its completion has.
+// its completion has; and of the exchange with the peer (thread 0 only): copy c of the
+// sequence of halves sent each way goes to A tile (c + off) % 2 and completes phase c / 2 of
+// barrier 3 + (c + off) % 2 of the receiver.
 struct Pending {
     bool ld = false, mma = false, a = false;
     uint32_t ph_ld = 0, ph_mma = 0, ph_a = 0;
+    long long sent = 0, recv = 0;
+    int off = 0;
 };
 
-// Shared setup of both kernels: barriers, abort word, `cols` columns of tensor memory, then a
-// cluster barrier (the peer's shared memory is in use only after it).
+// Shared setup of both kernels: barriers (each exchange barrier armed for its first copy),
+// abort word, `cols` columns of tensor memory, then a cluster barrier (the peer's shared memory
+// is in use only after it).
 __device__ __forceinline__ uint32_t setup_cta(unsigned char *sm, int tid, int warp, uint32_t cols)
 {
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + SM_BAR);
     uint32_t *slot = reinterpret_cast<uint32_t *>(sm + SM_SLOT);
     volatile int *abort_cta = reinterpret_cast<volatile int *>(sm + SM_SLOT + 4);
     if (tid == 0) {
-        for (int b = 0; b < 3; ++b)
+        for (int b = 0; b < 5; ++b)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[b])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect(su32(&bar[3]), kImage / 2);
+        mbar_expect(su32(&bar[4]), kImage / 2);
         *abort_cta = 0;
     }
     if (warp == 0) {
@@ -202,6 +207,36 @@ __device__ __forceinline__ uint32_t setup_cta(unsigned char *sm, int tid, int wa
     const uint32_t tmem = *slot;
     cluster_sync();
     return tmem;
+}
+
+// Thread 0, after every thread wrote its part of this CTA's half (columns 128 h ..) of A tile
+// `buf` and passed a proxy fence and a CTA barrier: the half (32 KB, contiguous) to the same
+// place in the peer, completing on the peer's exchange barrier of that tile.
+__device__ __forceinline__ void send_half(Pending &pd, uint32_t local, uint32_t remote,
+                                          uint32_t remote_bar0, int buf, int h)
+{
+    const uint32_t o = (uint32_t)buf * 65536u + (uint32_t)h * 32768u;
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            remote + o),
+        "r"(local + o), "r"(32768u), "r"(remote_bar0 + (uint32_t)buf * 8u)
+        : "memory");
+    ++pd.sent;
+}
+
+// Thread 0: wait for the peer's next half (bounded); then arm its barrier for the copy after
+// next.  The peer sends a copy only after it used the one this CTA sent before (each layer's
+// MMAs need both halves of their input), so the copy after next finds the barrier armed for
+// it, and a tile's buffer is never overwritten while this CTA's MMAs may still read it.
+__device__ __forceinline__ bool recv_half(Pending &pd, unsigned char *sm, long long wait)
+{
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + SM_BAR);
+    const long long c = pd.recv;
+    const uint32_t xb = su32(&bar[3 + ((c + pd.off) & 1)]);
+    if (!mbar_wait(xb, (uint32_t)((c >> 1) & 1), wait)) return false;
+    ++pd.recv;
+    mbar_expect(xb, kImage / 2);
+    return true;
 }
 
 // the last layer's two images into the B region: the forward image (8 KB) at b_base and the
@@ -255,11 +290,13 @@ __device__ __forceinline__ bool run_layer(Pending &pd, uint32_t tmem, uint32_t a
     return true;
 }
 
-// Shared teardown: on failure record it and drain the issued work (default bound), pass the
-// last cluster barrier, free tensor memory.
+// Shared teardown: on failure record it and drain the issued work (default bound); then tell
+// the peer how many halves this CTA sent it, wait (default bound) for those the peer sent that
+// have not been waited for, and pass a last cluster barrier, so that no CTA leaves while a copy
+// into its shared memory is in flight; free tensor memory.
 __device__ __forceinline__ void teardown_cta(unsigned char *sm, int tid, int warp, uint32_t tmem,
-                                             uint32_t cols, bool failed, const Pending &pd,
-                                             int *flag)
+                                             uint32_t cols, bool failed, Pending &pd, int *flag,
+                                             uint32_t remote)
 {
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + SM_BAR);
     if (tid == 0) {
@@ -267,6 +304,16 @@ __device__ __forceinline__ void teardown_cta(unsigned char *sm, int tid, int war
         if (pd.ld) mbar_wait(su32(&bar[0]), pd.ph_ld);
         if (pd.mma) mbar_wait(su32(&bar[1]), pd.ph_mma);
         if (pd.a) mbar_wait(su32(&bar[2]), pd.ph_a);
+        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(remote + SM_SLOT + 8),
+                     "r"((uint32_t)pd.sent)
+                     : "memory");
+    }
+    __syncthreads();
+    cluster_sync();
+    if (tid == 0) {
+        const long long peer_sent = *reinterpret_cast<volatile uint32_t *>(sm + SM_SLOT + 8);
+        while (pd.recv < peer_sent && recv_half(pd, sm, kWaitCycles)) {
+        }
     }
     __syncthreads();
     cluster_sync();
@@ -298,6 +345,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const uint32_t b_base = su32(sm + SM_B);
     const int h = (int)cluster_rank(), peer = h ^ 1;
     const uint32_t local = su32(sm), remote = peer_addr(local, (uint32_t)peer);
+    const uint32_t remote_xbar = peer_addr(su32(&bar[3]), (uint32_t)peer);
 
     const float4 *gF = reinterpret_cast<const float4 *>(pack + 3 * kPackW);
     for (int i = tid; i < kPackF / 4; i += kThreads) reinterpret_cast<float4 *>(sF)[i] = gF[i];
@@ -374,10 +422,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                                 pd.ph_mma ^= 1u;
                             }
                         }
-                    } else {
+                    } else {  // the peer's half of this layer's input first
                         const int next = l < 3 ? NEXT_HALF : NEXT_W4;
                         const unsigned char *img = l < 3 ? pack + l * kPackW : pack;
-                        ok = run_layer(pd, tmem, local + ((l - 1) & 1) * 65536u, b_base, bar_ld,
+                        ok = recv_half(pd, sm, wait) &&
+                             run_layer(pd, tmem, local + ((l - 1) & 1) * 65536u, b_base, bar_ld,
                                        bar_mma, next, img, h, wait);
                     }
                     if (!ok) *abort_cta = 1;
@@ -405,17 +454,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     const uint4 pk = pack8(hh);
                     *reinterpret_cast<uint4 *>(Hl + a_off(erow, k0)) = pk;
                     if (l < 3) store8(zt_at(Zs[l], tile, erow, k0), zz);
-                    const uint32_t off = abuf + a_off(erow, k0);
-                    *reinterpret_cast<uint4 *>(sm + off) = pk;
-                    st_cluster(remote + off, pk);
+                    *reinterpret_cast<uint4 *>(sm + abuf + a_off(erow, k0)) = pk;
                 }
+                // the half to the peer's A tile l % 2
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                if (tid == 0) send_half(pd, local, remote, remote_xbar, l & 1, h);
             }
-            cluster_sync();
         }
         // the last layer (256 -> 12, as N = 16) from A tile 1 (H4) into TMEM columns 128..143
         if (!failed) {
             if (tid == 0) {
-                bool ok = mbar_wait(bar_ld, pd.ph_ld, wait);
+                bool ok = recv_half(pd, sm, wait) && mbar_wait(bar_ld, pd.ph_ld, wait);
                 if (ok) {
                     pd.ld = false;
                     pd.ph_ld ^= 1u;
@@ -541,7 +591,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             __syncthreads();
         }
     }
-    teardown_cta(sm, tid, warp, tmem, 256u, failed, pd, flag);
+    teardown_cta(sm, tid, warp, tmem, 256u, failed, pd, flag, remote);
 }
 
 // Backward-data chain of the hidden layers for n rows: from the g3 image and the tiled
@@ -564,9 +614,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const uint32_t b_base = su32(sm + SM_B);
     const int h = (int)cluster_rank(), peer = h ^ 1;
     const uint32_t local = su32(sm), remote = peer_addr(local, (uint32_t)peer);
+    const uint32_t remote_xbar = peer_addr(su32(&bar[3]), (uint32_t)peer);
     const uint32_t tmem = setup_cta(sm, tid, warp, 128u);
 
     Pending pd;
+    pd.off = 1;  // the halves alternate between A tiles 1 (g2) and 0 (g1)
     const long long n_tiles = (n + kTile - 1) / kTile;
     const long long first = cluster_id(), stride = cluster_count();
     const int q = warp & 3, ch = warp >> 2;
@@ -592,14 +644,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     for (long long tile = first; tile < n_tiles; tile += stride) {
         for (int l = 0; l < 3; ++l) {  // hidden layers 3, 2, 1
             if (!failed) {
+                fence_before();
+                __syncthreads();
+                fence_after();
                 if (tid == 0) {
-                    bool ok = true;
+                    bool ok;
                     if (l == 0) {
                         ok = mbar_wait(bar_a, pd.ph_a, wait);
                         if (ok) {
                             pd.a = false;
                             pd.ph_a ^= 1u;
                         }
+                    } else {  // the peer's half of this layer's input
+                        ok = recv_half(pd, sm, wait);
                     }
                     const int next = l < 2 || tile + stride < n_tiles ? NEXT_HALF : NEXT_NONE;
                     const unsigned char *img = pack_t + (l < 2 ? 1 - l : 2) * kPackW;
@@ -635,22 +692,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     }
                     const uint4 pk = pack8(gg);
                     *reinterpret_cast<uint4 *>(Gl + a_off(erow, k0)) = pk;
-                    if (l < 2) {
-                        const uint32_t off = abuf + a_off(erow, k0);
-                        *reinterpret_cast<uint4 *>(sm + off) = pk;
-                        st_cluster(remote + off, pk);
-                    }
+                    if (l < 2) *reinterpret_cast<uint4 *>(sm + abuf + a_off(erow, k0)) = pk;
                 }
                 atomicAdd(dbs[l] + gc0 + lane, warp_colsum<32>(cs, lane));
+                if (l < 2) {  // the half to the peer's A tile (l + 1) % 2
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncthreads();
+                    if (tid == 0) send_half(pd, local, remote, remote_xbar, (l + 1) & 1, h);
+                }
             }
-            if (l < 2) cluster_sync();
         }
         if (!failed) {  // the next tile's copy overwrites A tile 0, its MMAs the accumulator
             fence_before();
             __syncthreads();
         }
     }
-    teardown_cta(sm, tid, warp, tmem, 128u, failed, pd, flag);
+    teardown_cta(sm, tid, warp, tmem, 128u, failed, pd, flag, remote);
 }
 
 }  // namespace
