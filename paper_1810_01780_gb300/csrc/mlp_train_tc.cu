@@ -2,16 +2,18 @@
 // the 5th-generation tensor cores (tcgen05), in one launch.
 //
 //   k_tc_wgrad: D = A^T B over the batch's rows with M = A's 256 columns (one half of 128 per
-//     CTA), N = B's columns, K = rows; blockIdx.z selects the job, blockIdx.y the M half, and
+//     CTA), N = B's columns (one half of 128 per CTA for the hidden layers), K = rows;
+//     blockIdx.z selects the job, blockIdx.y the M half and N half, and
 //     blockIdx.x one of the job's interleaved shares of the 128-row tiles (CTAs past a job's
 //     shares return at once).  The jobs: dW_l = H_l^T g_l of the hidden layers (N 256), the
 //     last layer's dW4 = H4^T g4 (N 16: g4's 12 columns zero-padded) and the first layer's
 //     dW0^T = g0^T x (N 16: x's 3 columns zero-padded).  The forward and backward passes leave
 //     these matrices as BF16 operand images (tc_common.cuh), which are the MN-major no-swizzle
 //     images of their transposes: a CTA bulk-copies its half of each tile's A image (32 KB) and
-//     the B image (64 or 4 KB) into one of two shared-memory stages, so the copy of the next
-//     tile overlaps the MMAs of this one, accumulates over its tiles in tensor memory and adds
-//     its sums to dW with atomics at the end.  (The bias gradients are summed by the passes
+//     its part of the B image (32 or 4 KB) into one of several shared-memory stages, so the
+//     copies of the next tiles overlap the MMAs of this one, accumulates over its tiles in
+//     tensor memory and adds its sums to dW with atomics at the end (the fewer tile shares, the
+//     less atomic traffic: it is one copy of dW per share).  (The bias gradients are summed by the passes
 //     that produce the g.)
 //   k_pack_t: the backward data pass's B images of W1..W3 (B[n][k] = W[n][k]).
 // Arithmetic: BF16 operands, FP32 products and sums.  Every mbarrier wait is bounded (the
@@ -39,32 +41,38 @@ constexpr uint32_t kIdescT = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (
                              ((128u >> 4) << 24);
 
 // shared memory map of k_tc_wgrad (bytes): stages of (the A image's M half, 32 KB; the B
-// image, 64 or 4 KB): two of 96 KB for N = 256, five of 36 KB for N = 16 (whose short MMAs
-// leave the copies' latency exposed unless more tiles are in flight); then the barriers
-// full[s] (the copies into stage s landed) and done[s] (the MMAs have read stage s)
+// image's N half, 32 KB, or the 16-column image, 4 KB): three of 64 KB for the hidden layers,
+// five of 36 KB for the thin ones (whose short MMAs leave the copies' latency exposed unless
+// more tiles are in flight); then the barriers full[s] (the copies into stage s landed) and
+// done[s] (the MMAs have read stage s)
 constexpr uint32_t WG_HALF = kImage / 2;
 constexpr uint32_t WG_STAGE = WG_HALF + kImage;
-constexpr int kStagesWide = 2, kStagesThin = 5, kMaxStages = 6;
+constexpr int kStagesWide = 3, kStagesThin = 5, kMaxStages = 6;
 constexpr uint32_t WG_BAR = 2 * WG_STAGE;
 constexpr uint32_t WG_SLOT = WG_BAR + 2 * kMaxStages * 8;  // TMEM address, abort word
 constexpr uint32_t WG_TOTAL = WG_SLOT + 32;
-static_assert(kStagesThin * (WG_HALF + kImage16) <= WG_BAR, "thin stages fit the wide ones' room");
+static_assert(kStagesThin * (WG_HALF + kImage16) <= WG_BAR && kStagesWide * 2 * WG_HALF <= WG_BAR,
+              "the stages fit");
 static_assert(WG_TOTAL <= 227 * 1024, "shared memory map exceeds a CTA's limit");
 
-// rows 128 h .. 128 h + 127 (h = blockIdx.y) of D over the tiles blockIdx.x, + shares, ...
+// rows 128 h .. 128 h + 127 (h = blockIdx.y % 2) of D, and for the hidden layers columns
+// 128 nh .. 128 nh + 127 (nh = blockIdx.y / 2), over the tiles blockIdx.x, + shares, ...
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_wgrad(const WgradArgs args, long long n_tiles, int *flag, long long wait)
 {
     const WgradJob &J = args.job[blockIdx.z];
     const long long shares = J.shares;
-    if ((long long)blockIdx.x >= shares) return;  // uniform over the CTA
+    const bool wide = J.n == 256;
+    const int half = (int)(blockIdx.y & 1), nh = (int)(blockIdx.y >> 1);
+    if ((long long)blockIdx.x >= shares || (!wide && nh)) return;  // uniform over the CTA
     const unsigned char *__restrict__ H = J.A;
     const unsigned char *__restrict__ G = J.B;
     float *__restrict__ dW = J.dW;
-    const int nb = J.n;                                      // 256 or 16
-    const uint32_t b_bytes = nb == 256 ? kImage : kImage16;  // B image of a tile
-    const uint32_t idesc = kIdescT | ((uint32_t)(nb >> 3) << 17);
-    const int S = nb == 256 ? kStagesWide : kStagesThin;  // pipeline stages
+    const uint32_t b_bytes = wide ? WG_HALF : kImage16;  // the B operand of a tile
+    const uint32_t b_stride = wide ? kImage : kImage16;  // bytes per tile of the B image
+    const uint32_t b_skip = wide ? (uint32_t)nh * WG_HALF : 0u;
+    const uint32_t idesc = kIdescT | ((wide ? 128u : 16u) >> 3) << 17;
+    const int S = wide ? kStagesWide : kStagesThin;  // pipeline stages
     const uint32_t stage_bytes = WG_HALF + b_bytes;
     extern __shared__ __align__(1024) unsigned char sm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + WG_BAR);  // full[0..S), done at +kMaxStages
@@ -72,7 +80,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t *slot = reinterpret_cast<uint32_t *>(sm + WG_SLOT);
     volatile int *abort_cta = reinterpret_cast<volatile int *>(sm + WG_SLOT + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int half = (int)blockIdx.y;
     const long long cnt = (n_tiles - blockIdx.x + shares - 1) / shares;  // >= 1
 
     if (tid == 0) {
@@ -106,9 +113,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t base = su32(sm + st * stage_bytes), fb = su32(&bar[st]);
             mbar_expect(fb, stage_bytes);
             bulk_g2s(base, H + t * kImage + half * WG_HALF, WG_HALF, fb);
-            for (uint32_t o = 0; o < b_bytes; o += WG_HALF)
-                bulk_g2s(base + WG_HALF + o, G + t * b_bytes + o,
-                         b_bytes - o < WG_HALF ? b_bytes - o : WG_HALF, fb);
+            bulk_g2s(base + WG_HALF, G + t * b_stride + b_skip, b_bytes, fb);
             ld[st] = i;
         };
         auto par = [S](long long i) { return (uint32_t)((i / S) & 1); };
@@ -172,20 +177,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         // lanes 32 q .. 32 q + 31)
         const int q = warp & 3, ch = warp >> 2;
         const int m = half * 128 + q * 32 + lane;
-        if (nb == 256) {  // column group warp / 4: columns 64 (warp / 4) ..
-#pragma unroll 1
-            for (int c = 0; c < 2; ++c) {
-                const int n0 = ch * 64 + c * 32;
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)n0, v);
-                float *d = dW + (long long)m * 256 + n0;  // 16-byte aligned: n0 % 32 == 0
+        if (wide) {  // column group warp / 4: columns 128 nh + 32 (warp / 4) ..
+            const int n0 = nh * 128 + ch * 32;
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 32), v);
+            float *d = dW + (long long)m * 256 + n0;  // 16-byte aligned: n0 % 32 == 0
 #pragma unroll
-                for (int j = 0; j < 32; j += 4)
-                    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(d + j),
-                                 "f"(__uint_as_float(v[j])), "f"(__uint_as_float(v[j + 1])),
-                                 "f"(__uint_as_float(v[j + 2])), "f"(__uint_as_float(v[j + 3]))
-                                 : "memory");
-            }
+            for (int j = 0; j < 32; j += 4)
+                asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(d + j),
+                             "f"(__uint_as_float(v[j])), "f"(__uint_as_float(v[j + 1])),
+                             "f"(__uint_as_float(v[j + 2])), "f"(__uint_as_float(v[j + 3]))
+                             : "memory");
         } else if (ch == 0) {  // 16 columns, warps 0..3
             uint32_t v[16];
             tmem_ld16(tmem + ((uint32_t)(q * 32) << 16), v);
@@ -243,12 +245,12 @@ int tc_wgrad(WgradArgs &a, long long n, int *flag, long long wait, cudaStream_t 
     RP_CUDA_TRY(cudaGetDevice(&dev));
     const long long tiles = (n + 127) / 128;
     // one CTA per SM: a few for each thin job (little to copy and multiply), the rest split
-    // evenly among the three hidden layers' two M halves
+    // evenly among the three hidden layers' four (M half, N half) blocks
     const long long sms = sm_count(dev);
     const long long thin = std::max(1LL, std::min(tiles, std::min(8LL, sms / 19)));
-    const long long wide = std::max(1LL, std::min(tiles, (sms - 4 * thin) / 6));
+    const long long wide = std::max(1LL, std::min(tiles, (sms - 4 * thin) / 12));
     for (int j = 0; j < 5; ++j) a.job[j].shares = (int32_t)(j < 3 ? wide : thin);
-    const dim3 grid((unsigned)std::max(wide, thin), 2, 5);
+    const dim3 grid((unsigned)std::max(wide, thin), 4, 5);  // y: M half + 2 x N half
     RP_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)WG_TOTAL));
     k_tc_wgrad<<<grid, kThreads, WG_TOTAL, st>>>(a, tiles, flag, wait);
