@@ -781,7 +781,7 @@ def run_gpu(args):
         sur["training"]["roofline"] = {
             "bound": "tensor", "achieved": tr, "peak": bf16_sus, "unit": "TFLOP/s",
             "frac": tr / bf16_sus if bf16_sus else None,
-            "kernel": "the whole Adam step (k_tc_dense, k_tc_wgrad, thin layers, loss, Adam)",
+            "kernel": "the whole Adam step (k_train_fwd, k_train_bwd, k_tc_wgrad, k_adam_pack)",
             "peak_basis": "MEASURED_PEAKS bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)"}
         fw = sur["mlp_forward_tflops"]
         sur["forward_roofline"] = {

@@ -1,11 +1,14 @@
 // mlp.cu -- the surrogate network: 3 -> 256 -> 256 -> 256 -> 256 -> 12, GELU (erf form),
-// BF16 weights and operands, FP32 accumulation, FP32 master weights with Adam: the thin layers'
-// kernels, the loss, the optimiser step, the native training loop and checkpoints.
+// BF16 weights and operands, FP32 accumulation, FP32 master weights with Adam: the operand
+// images of the weights, the optimiser step, the loss-and-gradient driver, the native training
+// loop and checkpoints.
 //
-// The three hidden 256 x 256 layers run on the 5th-generation tensor cores (mlp_fused.cu for
-// inference, mlp_train_tc.cu for training).  The thin first (3 -> 256) and last (256 -> 12)
-// layers, whose contractions are too narrow for a tensor-core tile, run on the CUDA cores
-// with the same arithmetic: BF16-rounded operands, FP32 products and sums.
+// Inference runs in one fused kernel (mlp_fused.cu: the hidden 256 x 256 layers on the
+// 5th-generation tensor cores, the thin first (3 -> 256) and last (256 -> 12) layers on the
+// CUDA cores).  A training step runs every layer on the tensor cores (the thin ones with their
+// narrow side zero-padded to 16): the forward and backward kernels of mlp_train_fused.cu, the
+// weight gradients of mlp_train_tc.cu, then one Adam kernel here.  Arithmetic everywhere:
+// BF16-rounded operands, FP32 products and sums.
 #include <cuda_bf16.h>
 
 #include <algorithm>

@@ -15,16 +15,17 @@
 // MMAs used the peer's half of the layer before, which the peer sent after its own MMAs had
 // read the buffer the new half goes to, so no copy lands in a buffer still being read.
 //
-// k_train_fwd: layer 0 (3 -> 256) on the CUDA cores, then the three 256 -> 256 layers.  The
-//   epilogues also store what the later kernels read: the pre-activations z0..z2 in FP32
+// k_train_fwd: layer 0 (3 -> 256) as one MMA of K = 16 (x zero-padded, from a 16-column A
+//   operand the CTA writes), then the three 256 -> 256 layers.  The epilogues also store what the later kernels read: the pre-activations z0..z2 in FP32
 //   (tiled: a tile's 8 columns k..k+7 of its 128 rows are 4 KB contiguous, so a warp's stores
 //   and the backward pass's loads of one 8-column group are 1 KB contiguous) and the
 //   activations H1..H4 as BF16 operand images (tc_common.cuh), and x as a 16-column image.
-//   The last layer (256 -> 12) comes out of the third epilogue's partial sums, exchanged
-//   between the pair; the loss and its gradient g4 follow per row (g4 stored as a 16-column
-//   image, its column sums added to db4), and the last layer's backward data pass
-//   g3 = (g4 W4^T) gelu'(z3) re-reads z3 from tensor memory, stores g3 as a BF16 image and
-//   adds its column sums to the bias gradient db3.
+//   The last layer (256 -> 12) is 16 MMAs of N = 16 (outputs zero-padded) from the whole H4 tile,
+//   done alike by both CTAs; the loss and its gradient g4 follow per row (g4 stored as a
+//   16-column image, its column sums added to db4), and the last layer's backward data pass
+//   g3 = (g4 W4^T) gelu'(z3) is one MMA of K = 16 from g4 for the CTA's 128 columns, with z3
+//   read again from tensor memory; g3 is stored as a BF16 image and its column sums are added
+//   to the bias gradient db3.
 // k_train_bwd: per tile, the g3 image by bulk copy as the A tile (prefetched while the previous
 //   tile's last epilogue runs), then for the hidden layers
 //   3, 2, 1 the backward images B[n][k] = W[n][k] and an epilogue
