@@ -130,23 +130,22 @@ __device__ __forceinline__ void load_half_image(uint32_t b_base, const unsigned 
     bulk_g2s(b_base + 32768u, img + h * 65536 + 32768, 32768u, bar);
 }
 
-// 16 MMAs of one layer (A tile x half B image) into the accumulator, committed to bar_mma
-__device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a_base, uint32_t b_base,
-                                            uint32_t bar_mma)
+// K steps s0 .. s0 + 7 (16 K each) of one layer (A tile x half B image) into the accumulator;
+// the first of them starts the accumulation if `fresh`
+__device__ __forceinline__ void issue_ksteps(uint32_t tmem, uint32_t a_base, uint32_t b_base,
+                                             int s0, bool fresh)
 {
 #pragma unroll
-    for (int s = 0; s < 16; ++s) {
+    for (int i = 0; i < 8; ++i) {
+        const int s = s0 + i;
         const uint64_t ad = sdesc(a_base + s * 4096u, 2048u, 128u);
         const uint64_t bd = sdesc(b_base + s * 4096u, 2048u, 128u);
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(kIdesc), "r"(s)
+            "l"(ad), "l"(bd), "r"(kIdesc), "r"((uint32_t)(!fresh || i > 0))
             : "memory");
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     bar_mma)
-                 : "memory");
 }
 
 __device__ __forceinline__ void store8(float *dst, const float (&v)[8])
@@ -270,18 +269,27 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
 // What thread 0 copies into the B region once a layer's MMAs are done.
 enum { NEXT_NONE = 0, NEXT_HALF = 1, NEXT_W4 = 2 };
 
-// Thread 0: wait for the B image, issue the layer's MMAs from A tile `a_base`, wait for them
-// and start the next copy into the B region (a half image of `img`, the last layer's images
-// from the pack `img`, or none); false once a wait gives up.
-__device__ __forceinline__ bool run_layer(Pending &pd, uint32_t tmem, uint32_t a_base,
-                                          uint32_t b_base, uint32_t bar_ld, uint32_t bar_mma,
-                                          int next, const unsigned char *img, int h, long long wait)
+// Thread 0: wait for the B image, issue the layer's MMAs from A tile `a_base` (first the K steps
+// over this CTA's own half of the input, then, once the peer's half has arrived if `exchange`,
+// the others), wait for them and start the next copy into the B region (a half image of `img`,
+// the last layer's images from the pack `img`, or none); false once a wait gives up (MMAs
+// issued are committed first, so that the drain can wait for them).
+__device__ __forceinline__ bool run_layer(Pending &pd, unsigned char *sm, uint32_t tmem,
+                                          uint32_t a_base, uint32_t b_base, uint32_t bar_ld,
+                                          uint32_t bar_mma, int next, const unsigned char *img,
+                                          int h, bool exchange, long long wait)
 {
     if (!mbar_wait(bar_ld, pd.ph_ld, wait)) return false;
     pd.ld = false;
     pd.ph_ld ^= 1u;
-    issue_layer(tmem, a_base, b_base, bar_mma);
+    issue_ksteps(tmem, a_base, b_base, 8 * h, true);
     pd.mma = true;
+    if (exchange && !recv_half(pd, sm, wait)) {
+        mma_commit(bar_mma);
+        return false;
+    }
+    issue_ksteps(tmem, a_base, b_base, 8 * (h ^ 1), false);
+    mma_commit(bar_mma);
     if (!mbar_wait(bar_mma, pd.ph_mma, wait)) return false;
     pd.mma = false;
     pd.ph_mma ^= 1u;
@@ -423,12 +431,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                                 pd.ph_mma ^= 1u;
                             }
                         }
-                    } else {  // the peer's half of this layer's input first
+                    } else {
                         const int next = l < 3 ? NEXT_HALF : NEXT_W4;
                         const unsigned char *img = l < 3 ? pack + l * kPackW : pack;
-                        ok = recv_half(pd, sm, wait) &&
-                             run_layer(pd, tmem, local + ((l - 1) & 1) * 65536u, b_base, bar_ld,
-                                       bar_mma, next, img, h, wait);
+                        ok = run_layer(pd, sm, tmem, local + ((l - 1) & 1) * 65536u, b_base,
+                                       bar_ld, bar_mma, next, img, h, true, wait);
                     }
                     if (!ok) *abort_cta = 1;
                 }
@@ -466,17 +473,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         // the last layer (256 -> 12, as N = 16) from A tile 1 (H4) into TMEM columns 128..143
         if (!failed) {
             if (tid == 0) {
-                bool ok = recv_half(pd, sm, wait) && mbar_wait(bar_ld, pd.ph_ld, wait);
-                if (ok) {
+                bool ok = mbar_wait(bar_ld, pd.ph_ld, wait);
+                if (ok) {  // the K steps over the own half of H4 first, then the peer's
                     pd.ld = false;
                     pd.ph_ld ^= 1u;
+                    for (int half = 0; half < 2 && ok; ++half) {
+                        if (half == 1) ok = recv_half(pd, sm, wait);
+                        if (!ok) break;
+                        const int k0 = 8 * (h ^ half);
 #pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        mma_bf16(tmem + 128u, sdesc(local + SM_A1 + k * 4096u, 2048u, 128u),
-                                 sdesc(b_base + k * 512u, 256u, 128u), kIdescN16, (uint32_t)k);
+                        for (int k = k0; k < k0 + 8; ++k)
+                            mma_bf16(tmem + 128u, sdesc(local + SM_A1 + k * 4096u, 2048u, 128u),
+                                     sdesc(b_base + k * 512u, 256u, 128u), kIdescN16,
+                                     (uint32_t)(half > 0 || k > k0));
+                    }
                     mma_commit(bar_mma);
                     pd.mma = true;
-                    ok = mbar_wait(bar_mma, pd.ph_mma, wait);
+                    if (ok) ok = mbar_wait(bar_mma, pd.ph_mma, wait);
                     if (ok) {
                         pd.mma = false;
                         pd.ph_mma ^= 1u;
@@ -656,13 +669,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                             pd.a = false;
                             pd.ph_a ^= 1u;
                         }
-                    } else {  // the peer's half of this layer's input
-                        ok = recv_half(pd, sm, wait);
+                    } else {
+                        ok = true;
                     }
                     const int next = l < 2 || tile + stride < n_tiles ? NEXT_HALF : NEXT_NONE;
                     const unsigned char *img = pack_t + (l < 2 ? 1 - l : 2) * kPackW;
-                    if (!ok || !run_layer(pd, tmem, local + (l & 1) * 65536u, b_base, bar_ld,
-                                          bar_mma, next, img, h, wait))
+                    if (!ok || !run_layer(pd, sm, tmem, local + (l & 1) * 65536u, b_base, bar_ld,
+                                          bar_mma, next, img, h, l > 0, wait))
                         *abort_cta = 1;
                     else if (l == 2 && tile + stride < n_tiles)
                         load_g3(tile + stride);  // A tile 0 read for the last time this tile
