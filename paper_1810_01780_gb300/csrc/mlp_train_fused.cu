@@ -356,8 +356,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const uint32_t local = su32(sm), remote = peer_addr(local, (uint32_t)peer);
     const uint32_t remote_xbar = peer_addr(su32(&bar[3]), (uint32_t)peer);
 
-    const float4 *gF = reinterpret_cast<const float4 *>(pack + 3 * kPackW);
-    for (int i = tid; i < kPackF / 4; i += kThreads) reinterpret_cast<float4 *>(sF)[i] = gF[i];
     const uint32_t tmem = setup_cta(sm, tid, warp, 256u);
 
     Pending pd;
@@ -374,8 +372,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     if (tid == 0 && first < n_tiles) {
         load_half_image(b_base, pack, h, bar_ld);
         pd.ld = true;
-        mbar_expect(bar_w0, 4096u);  // the W0 half, once
+        // the W0 half and the FP32 constants, once (read after the first layer-0 MMA, whose
+        // issue waits for this copy)
+        mbar_expect(bar_w0, 4096u + kPackF * 4u);
         bulk_g2s(local + SM_W0, pack + kPackW0 + h * 4096, 4096u, bar_w0);
+        bulk_g2s(local + SM_F, pack + 3 * kPackW, kPackF * 4u, bar_w0);
         pd.a = true;
     }
 
