@@ -16,16 +16,18 @@
 // read the buffer the new half goes to, so no copy lands in a buffer still being read.
 //
 // k_train_fwd: layer 0 (3 -> 256) as one MMA of K = 16 (x zero-padded, from a 16-column A
-//   operand the CTA writes), then the three 256 -> 256 layers.  The epilogues also store what the later kernels read: the pre-activations z0..z2 in FP32
-//   (tiled: a tile's 8 columns k..k+7 of its 128 rows are 4 KB contiguous, so a warp's stores
-//   and the backward pass's loads of one 8-column group are 1 KB contiguous) and the
-//   activations H1..H4 as BF16 operand images (tc_common.cuh), and x as a 16-column image.
-//   The last layer (256 -> 12) is 16 MMAs of N = 16 (outputs zero-padded) from the whole H4 tile,
-//   done alike by both CTAs; the loss and its gradient g4 follow per row (g4 stored as a
-//   16-column image, its column sums added to db4), and the last layer's backward data pass
-//   g3 = (g4 W4^T) gelu'(z3) is one MMA of K = 16 from g4 for the CTA's 128 columns, with z3
-//   read again from tensor memory; g3 is stored as a BF16 image and its column sums are added
-//   to the bias gradient db3.
+//   operand the CTA writes), then the three 256 -> 256 layers.  An epilogue evaluates GELU and
+//   its derivative from one Phi and one exponential, and also stores what the later kernels
+//   read: gelu'(z) of the pre-activations z0..z2 in FP32 (tiled: a tile's 8 columns k..k+7 of
+//   its 128 rows are 4 KB contiguous, so a warp's stores and the backward pass's loads of one
+//   8-column group are 1 KB contiguous) and the activations H1..H4 as BF16 operand images
+//   (tc_common.cuh), and x as a 16-column image.  The last layer (256 -> 12) is 16 MMAs of
+//   N = 16 (outputs zero-padded) from the whole H4 tile, done alike by both CTAs; the loss and
+//   its gradient g4 follow per row (g4 stored as a 16-column image, its column sums added to
+//   db4), and the last layer's backward data pass g3 = (g4 W4^T) gelu'(z3) is one MMA of K = 16
+//   from g4 for the CTA's 128 columns, with gelu'(z3) written into tensor memory over z3 by the
+//   fourth epilogue; g3 is stored as a BF16 image and its column sums are added to the bias
+//   gradient db3.
 // k_train_bwd: per tile, the g3 image by bulk copy as the A tile (prefetched while the previous
 //   tile's last epilogue runs), then for the hidden layers
 //   3, 2, 1 the backward images B[n][k] = W[n][k] and an epilogue
@@ -333,7 +335,7 @@ __device__ __forceinline__ void teardown_cta(unsigned char *sm, int tid, int war
 }
 
 // Forward pass, loss and last-layer backward of n rows (x (n, 3), targets y (n, 2), t (n, 10)).
-// Writes z0, z1, z2 (tiled FP32), the images of x, H1..H4, g4 and g3, adds the loss sum to
+// Writes gelu'(z0), gelu'(z1), gelu'(z2) (tiled FP32), the images of x, H1..H4, g4 and g3, adds the loss sum to
 // *loss and the column sums of g4 and g3 to db4 and db3.
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     k_train_fwd(const unsigned char *__restrict__ pack, const float *__restrict__ x,
@@ -449,22 +451,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 const float *bias = sF + (l == 0 ? PF_B0 : PF_B1 + (l - 1) * 256);
                 unsigned char *Hl = Hs[l] + tile * kImage;
                 const uint32_t abuf = (l & 1) * 65536u;
+                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
                 uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, v);
+                tmem_ld32(ta, v);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int k0 = gc0 + e * 8;
-                    float zz[8], hh[8];
+                    float hh[8], dd[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        zz[u] = __uint_as_float(v[e * 8 + u]) + bias[k0 + u];
-                        hh[u] = gelu(zz[u]);
+                    for (int u = 0; u < 8; ++u) {  // gelu(z) and gelu'(z) from one Phi, one exp
+                        const float z = __uint_as_float(v[e * 8 + u]) + bias[k0 + u];
+                        const PhiE pe = phi_e(z);
+                        hh[u] = z * pe.phi;
+                        dd[u] = fmaf(z * pe.e, 0.39894228040143268f, pe.phi);
+                        v[e * 8 + u] = __float_as_uint(dd[u]);
                     }
                     const uint4 pk = pack8(hh);
                     *reinterpret_cast<uint4 *>(Hl + a_off(erow, k0)) = pk;
-                    if (l < 3) store8(zt_at(Zs[l], tile, erow, k0), zz);
+                    if (l < 3) store8(zt_at(Zs[l], tile, erow, k0), dd);
                     *reinterpret_cast<uint4 *>(sm + abuf + a_off(erow, k0)) = pk;
                 }
+                if (l == 3) tmem_st32(ta, v);  // gelu'(z3) in place of z3, for the g3 pass
                 // the half to the peer's A tile l % 2
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncthreads();
@@ -577,8 +584,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             failed = *abort_cta != 0;
         }
         if (!failed) {
-            // last layer backward: g3 = (g4 W4^T) gelu'(z3), z3 read again from tensor memory
-            const float *bias = sF + PF_B1 + 2 * 256;
+            // last layer backward: g3 = (g4 W4^T) gelu'(z3), gelu'(z3) from tensor memory (the
+            // fourth epilogue left it there)
             unsigned char *G3t = G3 + tile * kImage;
 #pragma unroll 1
             for (int c = 0; c < 2; ++c) {
@@ -593,8 +600,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int j = e * 8 + u;
-                        gg[u] = __uint_as_float(vd[j]) *
-                                gelu_prime(__uint_as_float(vz[j]) + bias[gc0 + j]);
+                        gg[u] = __uint_as_float(vd[j]) * __uint_as_float(vz[j]);
                         cs[j] = gg[u];
                     }
                     *reinterpret_cast<uint4 *>(G3t + a_off(erow, gc0 + e * 8)) = pack8(gg);
@@ -610,8 +616,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 }
 
 // Backward-data chain of the hidden layers for n rows: from the g3 image and the tiled
-// pre-activations z0..z2, writes the images of g2, g1, g0 with g_{l-1} = (g_l W_l^T)
-// gelu'(z_{l-1}) and adds their column sums to db2, db1, db0.  pack_t: the backward images of
+// gelu'(z0..z2), writes the images of g2, g1, g0 with g_{l-1} = (g_l W_l^T) gelu'(z_{l-1}) and
+// adds their column sums to db2, db1, db0.  pack_t: the backward images of
 // W1, W2, W3 (B[n][k] = W[n][k]).
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     k_train_bwd(const unsigned char *__restrict__ pack_t, const unsigned char *__restrict__ G3,
@@ -638,7 +644,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const long long first = cluster_id(), stride = cluster_count();
     const int q = warp & 3, ch = warp >> 2;
     const int erow = q * 32 + lane;
-    const float *Zin[3] = {Z2, Z1, Z0};  // gelu' of the layer below layers 3, 2, 1
+    const float *Zin[3] = {Z2, Z1, Z0};  // gelu'(z) of the layer below layers 3, 2, 1
     unsigned char *Gout[3] = {G2, G1, G0};
     float *dbs[3] = {db2, db1, db0};
     bool failed = false;
@@ -698,11 +704,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     const int k0 = gc0 + e * 8;
                     const float4 *zs = reinterpret_cast<const float4 *>(zt_at(Zl, tile, erow, k0));
                     const float4 z0 = __ldg(zs), z1 = __ldg(zs + 1);
-                    const float z[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+                    const float d[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
                     float gg[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        gg[u] = __uint_as_float(v[e * 8 + u]) * gelu_prime(z[u]);
+                        gg[u] = __uint_as_float(v[e * 8 + u]) * d[u];
                         cs[e * 8 + u] = gg[u];
                     }
                     const uint4 pk = pack8(gg);
