@@ -664,6 +664,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 
     for (long long tile = first; tile < n_tiles; tile += stride) {
         for (int l = 0; l < 3; ++l) {  // hidden layers 3, 2, 1
+            // this thread's gelu'(z) of the layer below (its row, its 32 columns), loaded while
+            // the layer's MMAs run
+            float dz[32];
+            if (!failed) {
+                const float4 *zs = reinterpret_cast<const float4 *>(
+                    zt_at(Zin[l], tile, erow, h * kHalf + ch * kGroupCols));
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {  // 8-column group e: 1 KB further on
+                    const float4 a = __ldg(zs + e * 256), c = __ldg(zs + e * 256 + 1);
+                    dz[e * 8 + 0] = a.x; dz[e * 8 + 1] = a.y; dz[e * 8 + 2] = a.z; dz[e * 8 + 3] = a.w;
+                    dz[e * 8 + 4] = c.x; dz[e * 8 + 5] = c.y; dz[e * 8 + 6] = c.z; dz[e * 8 + 7] = c.w;
+                }
+            }
             if (!failed) {
                 fence_before();
                 __syncthreads();
@@ -693,7 +706,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             }
             if (!failed) {
                 const int col0 = ch * kGroupCols, gc0 = h * kHalf + col0;
-                const float *Zl = Zin[l];
                 unsigned char *Gl = Gout[l] + tile * kImage;
                 const uint32_t abuf = ((l + 1) & 1) * 65536u;
                 uint32_t v[32];
@@ -702,13 +714,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int k0 = gc0 + e * 8;
-                    const float4 *zs = reinterpret_cast<const float4 *>(zt_at(Zl, tile, erow, k0));
-                    const float4 z0 = __ldg(zs), z1 = __ldg(zs + 1);
-                    const float d[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
                     float gg[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        gg[u] = __uint_as_float(v[e * 8 + u]) * d[u];
+                        gg[u] = __uint_as_float(v[e * 8 + u]) * dz[e * 8 + u];
                         cs[e * 8 + u] = gg[u];
                     }
                     const uint4 pk = pack8(gg);
