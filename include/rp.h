@@ -202,14 +202,22 @@ typedef struct {
  *   block          threads per block of the tracing launches: 0 (128) or a multiple of 32 up
  *                  to 256
  *   blocks_per_sm  resident blocks per SM of the persistent launches: 0 or more than fit
- *                  means as many as fit */
+ *                  means as many as fit
+ *   ray_order      RP_ORDER_COHERENT (0, the default): rp_trace takes the primaries up in the
+ *                  order of a counting sort on (launch direction's z component in 64 bins,
+ *                  then start depth in 64 bins over the batch's range), so that the lanes of
+ *                  a warp trace rays that follow similar paths and stay in step; each
+ *                  primary is still written at its own index.  RP_ORDER_GIVEN (1): in the
+ *                  order given.  rp_trace_static and rp_find_paths take the order given. */
 typedef struct {
     double tol, h_min, h_max, h0, max_path, max_time, min_amp, eps_b;
     double stop_n[3], stop_d;
-    int32_t use_stop, max_generation, precision, polarization, rhs_form, pad;
+    int32_t use_stop, max_generation, precision, polarization, rhs_form, ray_order;
     int64_t max_steps;
     int32_t service_idle, flush_min, block, blocks_per_sm;
 } rp_trace_params;
+
+enum { RP_ORDER_COHERENT = 0, RP_ORDER_GIVEN = 1 };
 
 /* Finished rays.  Primary i is written at index i; secondaries take the following indices as
  * they are cast, in no fixed order (each record's content does not depend on it).  Arrays of

@@ -76,7 +76,7 @@ class TraceParams(C.Structure):
                 ("min_amp", C.c_double), ("eps_b", C.c_double), ("stop_n", C.c_double * 3),
                 ("stop_d", C.c_double), ("use_stop", C.c_int32), ("max_generation", C.c_int32),
                 ("precision", C.c_int32), ("polarization", C.c_int32), ("rhs_form", C.c_int32),
-                ("pad", C.c_int32), ("max_steps", C.c_int64), ("service_idle", C.c_int32),
+                ("ray_order", C.c_int32), ("max_steps", C.c_int64), ("service_idle", C.c_int32),
                 ("flush_min", C.c_int32), ("block", C.c_int32), ("blocks_per_sm", C.c_int32)]
 
 

@@ -148,7 +148,7 @@ def make_params(p: dict, precision: str = "fp64") -> A.TraceParams:
     return q
 
 
-SCHEDULING_KNOBS = ("service_idle", "flush_min", "block", "blocks_per_sm")
+SCHEDULING_KNOBS = ("service_idle", "flush_min", "block", "blocks_per_sm", "ray_order")
 
 
 RAY_FIELDS_F64 = ("path", "time", "amp")

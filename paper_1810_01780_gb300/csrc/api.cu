@@ -117,6 +117,10 @@ int validate_params(const rp_trace_params *p, bool path_finding)
                   "multiple of 32 up to %d", kBlockMax);
         return RP_ERR_INVALID_ARG;
     }
+    if (p->ray_order != RP_ORDER_COHERENT && p->ray_order != RP_ORDER_GIVEN) {
+        set_error("params: ray_order must be RP_ORDER_COHERENT (0) or RP_ORDER_GIVEN (1)");
+        return RP_ERR_INVALID_ARG;
+    }
     return RP_OK;
 }
 

@@ -30,7 +30,104 @@ struct WaveIn {
     PlaneC stop;
     double h0;
     float h0f;
+    const uint32_t *ord;  // primary taken up k-th: ray ord[k] (null: ray k)
 };
+
+// Coherent order of the primaries (rp_trace_params.ray_order == RP_ORDER_COHERENT): a counting
+// sort on a 12-bit key, the launch direction's z component in 64 bins over [-1, 1] (high bits)
+// and the start depth in 64 bins over the batch's range (low bits).  Rays that start near one
+// another in the same direction follow similar paths -- the same boundaries, the same step
+// sizes -- so the lanes of a warp that take them up together stay in step.  Four launches:
+// the depth range, the keys with their histogram, its exclusive scan, the scatter (within a
+// key the order follows the atomics; no record depends on it).
+constexpr int kOrderBins = 4096;
+__device__ __forceinline__ uint32_t ordered_bits(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float from_ordered_bits(uint32_t u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+__global__ void k_order_range(const double *__restrict__ z, long long n, uint32_t *range)
+{
+    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float f = (float)z[i];
+        if (isfinite(f)) {
+            const uint32_t u = ordered_bits(f);
+            lo = min(lo, u);
+            hi = max(hi, u);
+        }
+    }
+    lo = __reduce_min_sync(0xFFFFFFFFu, lo);
+    hi = __reduce_max_sync(0xFFFFFFFFu, hi);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&range[0], lo);
+        atomicMax(&range[1], hi);
+    }
+}
+__global__ void __launch_bounds__(256) k_order_keys(const double *__restrict__ pos,
+                                                    const double *__restrict__ dir, long long n,
+                                                    const uint32_t *range, uint16_t *key,
+                                                    uint32_t *hist)
+{
+    __shared__ uint32_t h[kOrderBins];
+    for (int b = threadIdx.x; b < kOrderBins; b += blockDim.x) h[b] = 0u;
+    __syncthreads();
+    const float z0 = range[1] >= range[0] ? from_ordered_bits(range[0]) : 0.0f;
+    const float z1 = range[1] >= range[0] ? from_ordered_bits(range[1]) : 0.0f;
+    const float scale = z1 > z0 ? 64.0f / (z1 - z0) : 0.0f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float dx = (float)dir[i], dy = (float)dir[n + i], dz = (float)dir[2 * n + i];
+        const float q = dx * dx + dy * dy + dz * dz;
+        const float tz = q > 0.0f ? dz * rsqrtf(q) : 0.0f;
+        const float ft = (tz + 1.0f) * 32.0f, fz = ((float)pos[2 * n + i] - z0) * scale;
+        const int tb = ft >= 0.0f ? min(63, (int)ft) : 0;  // NaN -> bin 0
+        const int zb = fz >= 0.0f ? min(63, (int)fz) : 0;
+        const uint32_t k = (uint32_t)(tb * 64 + zb);
+        key[i] = (uint16_t)k;
+        atomicAdd(&h[k], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kOrderBins; b += blockDim.x)
+        if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+__global__ void __launch_bounds__(1024) k_order_scan(uint32_t *hist)  // in place, exclusive
+{
+    __shared__ uint32_t part[1024];
+    const int t = threadIdx.x;
+    uint32_t v[4], s = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        v[j] = hist[4 * t + j];
+        s += v[j];
+    }
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan of the per-thread sums
+        const uint32_t add = t >= off ? part[t - off] : 0u;
+        __syncthreads();
+        part[t] += add;
+        __syncthreads();
+    }
+    uint32_t run = t ? part[t - 1] : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        hist[4 * t + j] = run;
+        run += v[j];
+    }
+}
+__global__ void k_order_scatter(const uint16_t *__restrict__ key, long long n, uint32_t *cursor,
+                                uint32_t *ord)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        ord[atomicAdd(&cursor[key[i]], 1u)] = (uint32_t)i;
+}
 
 __device__ __forceinline__ long long claim_index(unsigned long long *counter)
 {
@@ -78,6 +175,7 @@ __device__ __forceinline__ void prefetch_ray(const Sinks &sk, const WaveIn &in, 
 {
     if (wave == 0) {
         const long long n = in.n;
+        if (in.ord) k = (long long)__ldg(&in.ord[k]);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             prefetch_l1(&in.pos[a * n + k]);
@@ -122,6 +220,7 @@ __device__ __forceinline__ void load_primary(Lane<P> &L, const M &med, const Sin
                                              const WaveIn &in, long long k)
 {
     const long long n = in.n;
+    if (in.ord) k = (long long)__ldg(&in.ord[k]);  // the ray taken up k-th
     L.A = in.amp ? in.amp[k] : 1.0;
     L.A0 = L.A;
     L.id = k;
@@ -572,7 +671,15 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
             --depth;
     }
     const size_t off_w = off_k + align_up(sizeof(QRec) * (size_t)threads * depth);
-    const size_t off_q = off_w + clk_bytes;
+    // the coherent order of the primaries (not with the fixed scratch): order, keys, the
+    // histogram and the depth range
+    const long long n_in = in->n;
+    const bool order = !fs && p->ray_order == RP_ORDER_COHERENT && n_in > 1;
+    const size_t ord_keys = align_up(sizeof(uint32_t) * (size_t)n_in);
+    const size_t ord_hist = ord_keys + align_up(sizeof(uint16_t) * (size_t)n_in);
+    const size_t ord_bytes = order ? ord_hist + align_up(sizeof(uint32_t) * (kOrderBins + 2)) : 0;
+    const size_t off_o = off_w + clk_bytes;
+    const size_t off_q = off_o + ord_bytes;
     if (fs) {
         const long long fit = (long long)((fs->size - off_q) / sizeof(QRec));
         q_cap = std::min(q_cap, fit);
@@ -649,6 +756,22 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     cudaEvent_t *ev = drain.ev;
     for (int w = 0; w <= n_waves; ++w) RP_CUDA_TRY(cudaEventCreate(&ev[w]));
     RP_CUDA_TRY(cudaEventRecord(ev[0], st));
+    wi.ord = nullptr;
+    if (order) {  // inside the timed region
+        uint32_t *ord = (uint32_t *)(base + off_o);
+        uint16_t *key = (uint16_t *)(base + off_o + ord_keys);
+        uint32_t *hist = (uint32_t *)(base + off_o + ord_hist), *range = hist + kOrderBins;
+        // histogram and the range's maximum start at 0, its minimum at all ones
+        RP_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (kOrderBins + 2), st));
+        RP_CUDA_TRY(cudaMemsetAsync(range, 0xFF, sizeof(uint32_t), st));
+        const unsigned g = (unsigned)std::min<long long>((n_in + 255) / 256, 8LL * sm_count(dev));
+        k_order_range<<<g, 256, 0, st>>>(in->pos + 2 * n_in, n_in, range);
+        k_order_keys<<<g, 256, 0, st>>>(in->pos, in->dir, n_in, range, key, hist);
+        k_order_scan<<<1, 1024, 0, st>>>(hist);
+        k_order_scatter<<<g, 256, 0, st>>>(key, n_in, hist, ord);
+        RP_CUDA_TRY(cudaGetLastError());
+        wi.ord = ord;
+    }
     const bool f64 = p->precision == RP_FP64;
     const StepParams<PrecF64> sp64 = step_params<PrecF64>(p, axis, sdir);
     const StepParams<PrecF32> sp32 = step_params<PrecF32>(p, axis, sdir);

@@ -230,16 +230,18 @@ def test_full_size_batched_sampled(rp):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_scheduling_knobs_do_not_change_records(rp, precision):
-    """The scheduling knobs of rp_trace_params (service_idle, flush_min, block, blocks_per_sm)
-    change when lanes are served, which thread traces a secondary and the launch shape, never
-    a ray's arithmetic: the same rays (matched by their split tree) with bit-identical records
-    at extreme settings."""
+    """The scheduling knobs of rp_trace_params (service_idle, flush_min, block, blocks_per_sm,
+    ray_order) change when lanes are served, which thread traces a ray, in which order the
+    primaries are taken up and the launch shape, never a ray's arithmetic: the same rays
+    (matched by their split tree) with bit-identical records at extreme settings, the primaries
+    at their own indices whatever the order."""
     cfg = W.batched(n=20_000)
     med = rp.Medium(cfg["medium"])
     runs = []
     for knobs in ({}, dict(service_idle=1, flush_min=1, block=64),
                   dict(service_idle=100000, flush_min=1000000, block=256, blocks_per_sm=1),
-                  dict(block=96, blocks_per_sm=3)):
+                  dict(block=96, blocks_per_sm=3), dict(ray_order=1),
+                  dict(ray_order=1, service_idle=1, block=64)):
         res = rp.trace(med, *cfg["rays"], params=dict(cfg["params"], **knobs),
                        receivers=cfg["receivers"], precision=precision)
         runs.append(gpu_rays(res))
@@ -251,3 +253,5 @@ def test_scheduling_knobs_do_not_change_records(rp, precision):
         for k in ("pos", "dir", "path", "time", "amp", "status", "layer", "n_acc", "n_rej",
                   "n_root", "n_refl", "n_turn"):
             np.testing.assert_array_equal(g[k][gi], base[k][bi], err_msg=k)
+        n = cfg["rays"][0].shape[1]  # primary i at index i
+        np.testing.assert_array_equal(g["pos"][:n], base["pos"][:n])
