@@ -204,8 +204,8 @@ typedef struct {
  *   blocks_per_sm  resident blocks per SM of the persistent launches: 0 or more than fit
  *                  means as many as fit
  *   ray_order      RP_ORDER_COHERENT (0, the default): rp_trace takes the primaries up in the
- *                  order of a counting sort on (launch direction's z component in 64 bins,
- *                  then start depth in 64 bins over the batch's range), so that the lanes of
+ *                  order of a counting sort on (launch direction's z component in 256 bins,
+ *                  then start depth in 256 bins over the batch's range), so that the lanes of
  *                  a warp trace rays that follow similar paths and stay in step; each
  *                  primary is still written at its own index.  RP_ORDER_GIVEN (1): in the
  *                  order given.  rp_trace_static and rp_find_paths take the order given. */

@@ -34,13 +34,15 @@ struct WaveIn {
 };
 
 // Coherent order of the primaries (rp_trace_params.ray_order == RP_ORDER_COHERENT): a counting
-// sort on a 12-bit key, the launch direction's z component in 64 bins over [-1, 1] (high bits)
-// and the start depth in 64 bins over the batch's range (low bits).  Rays that start near one
-// another in the same direction follow similar paths -- the same boundaries, the same step
-// sizes -- so the lanes of a warp that take them up together stay in step.  Four launches:
-// the depth range, the keys with their histogram, its exclusive scan, the scatter (within a
-// key the order follows the atomics; no record depends on it).
-constexpr int kOrderBins = 4096;
+// sort on a 16-bit key, the launch direction's z component in 256 bins over [-1, 1] (high
+// bits) and the start depth in 256 bins over the batch's range (low bits).  Rays that start
+// near one another in nearly the same direction follow similar paths -- the same boundaries,
+// the same step sizes -- so the lanes of a warp that take them up together stay in step
+// (coarser bins leave more spread within a warp; a full sort on direction and depth lines up
+// rays of equal direction but scattered depths).  Four launches: the depth range, the keys
+// with their histogram, its exclusive scan, the scatter (within a key the order follows the
+// atomics; no record depends on it).
+constexpr int kOrderAxis = 256, kOrderBins = kOrderAxis * kOrderAxis;
 __device__ __forceinline__ uint32_t ordered_bits(float f)
 {
     const uint32_t u = __float_as_uint(f);
@@ -69,43 +71,34 @@ __global__ void k_order_range(const double *__restrict__ z, long long n, uint32_
         atomicMax(&range[1], hi);
     }
 }
-__global__ void __launch_bounds__(256) k_order_keys(const double *__restrict__ pos,
-                                                    const double *__restrict__ dir, long long n,
-                                                    const uint32_t *range, uint16_t *key,
-                                                    uint32_t *hist)
+__global__ void k_order_keys(const double *__restrict__ pos, const double *__restrict__ dir,
+                             long long n, const uint32_t *range, uint16_t *key, uint32_t *hist)
 {
-    __shared__ uint32_t h[kOrderBins];
-    for (int b = threadIdx.x; b < kOrderBins; b += blockDim.x) h[b] = 0u;
-    __syncthreads();
     const float z0 = range[1] >= range[0] ? from_ordered_bits(range[0]) : 0.0f;
     const float z1 = range[1] >= range[0] ? from_ordered_bits(range[1]) : 0.0f;
-    const float scale = z1 > z0 ? 64.0f / (z1 - z0) : 0.0f;
+    const float half = 0.5f * (float)kOrderAxis;
+    const float scale = z1 > z0 ? (float)kOrderAxis / (z1 - z0) : 0.0f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const float dx = (float)dir[i], dy = (float)dir[n + i], dz = (float)dir[2 * n + i];
         const float q = dx * dx + dy * dy + dz * dz;
         const float tz = q > 0.0f ? dz * rsqrtf(q) : 0.0f;
-        const float ft = (tz + 1.0f) * 32.0f, fz = ((float)pos[2 * n + i] - z0) * scale;
-        const int tb = ft >= 0.0f ? min(63, (int)ft) : 0;  // NaN -> bin 0
-        const int zb = fz >= 0.0f ? min(63, (int)fz) : 0;
-        const uint32_t k = (uint32_t)(tb * 64 + zb);
+        const float ft = (tz + 1.0f) * half, fz = ((float)pos[2 * n + i] - z0) * scale;
+        const int tb = ft >= 0.0f ? min(kOrderAxis - 1, (int)ft) : 0;  // NaN -> bin 0
+        const int zb = fz >= 0.0f ? min(kOrderAxis - 1, (int)fz) : 0;
+        const uint32_t k = (uint32_t)(tb * kOrderAxis + zb);
         key[i] = (uint16_t)k;
-        atomicAdd(&h[k], 1u);
+        atomicAdd(&hist[k], 1u);
     }
-    __syncthreads();
-    for (int b = threadIdx.x; b < kOrderBins; b += blockDim.x)
-        if (h[b]) atomicAdd(&hist[b], h[b]);
 }
-__global__ void __launch_bounds__(1024) k_order_scan(uint32_t *hist)  // in place, exclusive
+// in place, exclusive: 1,024 threads of 64 consecutive bins each
+__global__ void __launch_bounds__(1024) k_order_scan(uint32_t *hist)
 {
+    constexpr int kPer = kOrderBins / 1024;
     __shared__ uint32_t part[1024];
     const int t = threadIdx.x;
-    uint32_t v[4], s = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        v[j] = hist[4 * t + j];
-        s += v[j];
-    }
+    uint32_t s = 0;
+    for (int j = 0; j < kPer; ++j) s += hist[kPer * t + j];
     part[t] = s;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan of the per-thread sums
@@ -115,10 +108,10 @@ __global__ void __launch_bounds__(1024) k_order_scan(uint32_t *hist)  // in plac
         __syncthreads();
     }
     uint32_t run = t ? part[t - 1] : 0u;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        hist[4 * t + j] = run;
-        run += v[j];
+    for (int j = 0; j < kPer; ++j) {
+        const uint32_t v = hist[kPer * t + j];
+        hist[kPer * t + j] = run;
+        run += v;
     }
 }
 __global__ void k_order_scatter(const uint16_t *__restrict__ key, long long n, uint32_t *cursor,
