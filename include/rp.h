@@ -205,9 +205,10 @@ typedef struct {
  *                  means as many as fit
  *   ray_order      RP_ORDER_COHERENT (0, the default): rp_trace takes the primaries up in the
  *                  order of a counting sort on (launch direction's z component in 256 bins,
- *                  then start depth in 256 bins over the batch's range), so that the lanes of
- *                  a warp trace rays that follow similar paths and stay in step; each
- *                  primary is still written at its own index.  RP_ORDER_GIVEN (1): in the
+ *                  then start depth in 256 bins over the batch's range; 65,536 direction bins
+ *                  if all rays start at one depth), so that the lanes of a warp trace rays that
+ *                  follow similar paths and stay in step; each primary is still written at its
+ *                  own index.  RP_ORDER_GIVEN (1): in the
  *                  order given.  rp_trace_static and rp_find_paths take the order given. */
 typedef struct {
     double tol, h_min, h_max, h0, max_path, max_time, min_amp, eps_b;

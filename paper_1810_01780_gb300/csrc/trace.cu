@@ -39,7 +39,8 @@ struct WaveIn {
 // near one another in nearly the same direction follow similar paths -- the same boundaries,
 // the same step sizes -- so the lanes of a warp that take them up together stay in step
 // (coarser bins leave more spread within a warp; a full sort on direction and depth lines up
-// rays of equal direction but scattered depths).  Four launches: the depth range, the keys
+// rays of equal direction but scattered depths).  A batch with a single start depth gives all
+// 16 bits to the direction.  Four launches: the depth range, the keys
 // with their histogram, its exclusive scan, the scatter (within a key the order follows the
 // atomics; no record depends on it).
 constexpr int kOrderAxis = 256, kOrderBins = kOrderAxis * kOrderAxis;
@@ -76,17 +77,20 @@ __global__ void k_order_keys(const double *__restrict__ pos, const double *__res
 {
     const float z0 = range[1] >= range[0] ? from_ordered_bits(range[0]) : 0.0f;
     const float z1 = range[1] >= range[0] ? from_ordered_bits(range[1]) : 0.0f;
-    const float half = 0.5f * (float)kOrderAxis;
-    const float scale = z1 > z0 ? (float)kOrderAxis / (z1 - z0) : 0.0f;
+    // no depth spread (one start depth): all 16 bits of the key for the direction
+    const bool flat = !(z1 > z0);
+    const float half = 0.5f * (float)(flat ? kOrderBins : kOrderAxis);
+    const float scale = flat ? 0.0f : (float)kOrderAxis / (z1 - z0);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const float dx = (float)dir[i], dy = (float)dir[n + i], dz = (float)dir[2 * n + i];
         const float q = dx * dx + dy * dy + dz * dz;
         const float tz = q > 0.0f ? dz * rsqrtf(q) : 0.0f;
         const float ft = (tz + 1.0f) * half, fz = ((float)pos[2 * n + i] - z0) * scale;
-        const int tb = ft >= 0.0f ? min(kOrderAxis - 1, (int)ft) : 0;  // NaN -> bin 0
-        const int zb = fz >= 0.0f ? min(kOrderAxis - 1, (int)fz) : 0;
-        const uint32_t k = (uint32_t)(tb * kOrderAxis + zb);
+        const int zb = fz >= 0.0f ? min(kOrderAxis - 1, (int)fz) : 0;  // NaN -> bin 0
+        const uint32_t k = flat ? (uint32_t)(ft >= 0.0f ? min(kOrderBins - 1, (int)ft) : 0)
+                                : (uint32_t)((ft >= 0.0f ? min(kOrderAxis - 1, (int)ft) : 0) *
+                                                 kOrderAxis + zb);
         key[i] = (uint16_t)k;
         atomicAdd(&hist[k], 1u);
     }
