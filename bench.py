@@ -282,7 +282,7 @@ MLP_FLOPS_FWD = 2 * (3 * 256 + 3 * 256 * 256 + 256 * 12)  # per row, multiply-ad
 # DRAM bytes (read + write) of the four k_trace_wave<PrecF32, MediumLayered> launches of one
 # step of the 1,048,576-ray batched workload, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the current kernel (profiles/k_trace_wave_f32_layered_1M_dram.md)
-TRACE_DRAM_BYTES_PER_STEP = 526_214_400
+TRACE_DRAM_BYTES_PER_STEP = 1_970_997_248
 
 
 def peaks_leg(rp, local):
