@@ -41,8 +41,8 @@ struct WaveIn {
 // (coarser bins leave more spread within a warp; a full sort on direction and depth lines up
 // rays of equal direction but scattered depths).  A batch with a single start depth gives all
 // 16 bits to the direction.  Four launches: the depth range, the keys
-// with their histogram, its exclusive scan, the scatter (within a key the order follows the
-// atomics; no record depends on it).
+// with their histogram, its exclusive scan (two launches), the scatter (within a key the
+// order follows the atomics; no record depends on it).
 constexpr int kOrderAxis = 256, kOrderBins = kOrderAxis * kOrderAxis;
 __device__ __forceinline__ uint32_t ordered_bits(float f)
 {
@@ -95,28 +95,36 @@ __global__ void k_order_keys(const double *__restrict__ pos, const double *__res
         atomicAdd(&hist[k], 1u);
     }
 }
-// in place, exclusive: 1,024 threads of 64 consecutive bins each
-__global__ void __launch_bounds__(1024) k_order_scan(uint32_t *hist)
+// Exclusive scan of the histogram in place, in two launches of kOrderBins / 1024 blocks: each
+// block scans its 1,024 bins (one per thread) and leaves its total in sums[block]; then each
+// block adds the totals of the blocks before it.
+constexpr int kOrderScanBlocks = kOrderBins / 1024;
+__global__ void __launch_bounds__(1024) k_order_scan(uint32_t *hist, uint32_t *sums)
 {
-    constexpr int kPer = kOrderBins / 1024;
     __shared__ uint32_t part[1024];
-    const int t = threadIdx.x;
-    uint32_t s = 0;
-    for (int j = 0; j < kPer; ++j) s += hist[kPer * t + j];
-    part[t] = s;
+    const int t = threadIdx.x, i = blockIdx.x * 1024 + t;
+    const uint32_t v = hist[i];
+    part[t] = v;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan of the per-thread sums
+    for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan
         const uint32_t add = t >= off ? part[t - off] : 0u;
         __syncthreads();
         part[t] += add;
         __syncthreads();
     }
-    uint32_t run = t ? part[t - 1] : 0u;
-    for (int j = 0; j < kPer; ++j) {
-        const uint32_t v = hist[kPer * t + j];
-        hist[kPer * t + j] = run;
-        run += v;
+    hist[i] = part[t] - v;
+    if (t == 1023) sums[blockIdx.x] = part[1023];
+}
+__global__ void __launch_bounds__(1024) k_order_offsets(uint32_t *hist, const uint32_t *sums)
+{
+    __shared__ uint32_t before;
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int b = 0; b < (int)blockIdx.x; ++b) s += sums[b];
+        before = s;
     }
+    __syncthreads();
+    hist[blockIdx.x * 1024 + threadIdx.x] += before;
 }
 __global__ void k_order_scatter(const uint16_t *__restrict__ key, long long n, uint32_t *cursor,
                                 uint32_t *ord)
@@ -674,7 +682,8 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     const bool order = !fs && p->ray_order == RP_ORDER_COHERENT && n_in > 1;
     const size_t ord_keys = align_up(sizeof(uint32_t) * (size_t)n_in);
     const size_t ord_hist = ord_keys + align_up(sizeof(uint16_t) * (size_t)n_in);
-    const size_t ord_bytes = order ? ord_hist + align_up(sizeof(uint32_t) * (kOrderBins + 2)) : 0;
+    const size_t ord_bytes =
+        order ? ord_hist + align_up(sizeof(uint32_t) * (kOrderBins + 2 + kOrderScanBlocks)) : 0;
     const size_t off_o = off_w + clk_bytes;
     const size_t off_q = off_o + ord_bytes;
     if (fs) {
@@ -764,7 +773,8 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
         const unsigned g = (unsigned)std::min<long long>((n_in + 255) / 256, 8LL * sm_count(dev));
         k_order_range<<<g, 256, 0, st>>>(in->pos + 2 * n_in, n_in, range);
         k_order_keys<<<g, 256, 0, st>>>(in->pos, in->dir, n_in, range, key, hist);
-        k_order_scan<<<1, 1024, 0, st>>>(hist);
+        k_order_scan<<<kOrderScanBlocks, 1024, 0, st>>>(hist, range + 2);
+        k_order_offsets<<<kOrderScanBlocks, 1024, 0, st>>>(hist, range + 2);
         k_order_scatter<<<g, 256, 0, st>>>(key, n_in, hist, ord);
         RP_CUDA_TRY(cudaGetLastError());
         wi.ord = ord;
