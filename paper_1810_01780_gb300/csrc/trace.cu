@@ -348,6 +348,12 @@ __device__ int next_ray(Lane<P> &L, const M &med, const StepParams<P> &sp, const
     bool input_out = ahead >= (long long)count;
     if (!input_out)
         input_out = *(volatile const unsigned long long *)&sk.ctrl->claim[wave] >= count;
+    // once the input has run out, a ray this lane claimed but has not started (nobody else can
+    // take it) starts now, and the lane's stack goes to the next launch: taken depth first, the
+    // stack would hold the claimed ray back and make it the launch's last
+    if (L.stk > 0 && input_out && ahead < (long long)count &&
+        flush_to_queue(sk, thread_stack(sk), L.stk))
+        L.stk = 0;
     if (L.stk > 0) {
         // depth first: the secondaries this thread cast itself come before new input
         const int top = --L.stk;
