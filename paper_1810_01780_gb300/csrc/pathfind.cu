@@ -220,8 +220,10 @@ __device__ __forceinline__ void drive(const MediumLayered &med, const StepParams
         const bool waits = done || fetch || (active && L.pend != 0);
         const unsigned int wait = __ballot_sync(0xffffffffu, waits);
         const unsigned int step_mask = __ballot_sync(0xffffffffu, active && L.pend == 0);
+        // a ray bouncing in a duct is served at once, as in k_trace_wave
+        const bool hot = __any_sync(0xffffffffu, active && L.pend != 0 && L.n_refl >= kHotSplits);
         idle += (unsigned int)__popc(wait);
-        if (wait != 0u && (idle >= sp.service_idle || step_mask == 0u)) {
+        if (wait != 0u && (idle >= sp.service_idle || step_mask == 0u || hot)) {
             idle = 0;
             if (active && L.pend != 0 && finish_split<P>(med, L, sp, sk)) {
                 active = false;

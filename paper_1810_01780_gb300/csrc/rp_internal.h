@@ -109,8 +109,10 @@ int validate_params(const rp_trace_params *p, bool path_finding);
 // more than an FP32-mixed one against the same service phase, so FP64 lanes wait less.  Once a
 // wave's input has run out, a thread hands the rest of its secondary stack to the next launch
 // when at least kFlushMinDefault records remain below the one it takes.  rp_trace_params
-// overrides both (0 keeps the default).
+// overrides both (0 keeps the default).  A lane whose ray has split kHotSplits times already
+// is served at its next boundary without waiting for the threshold.
 constexpr int kServiceIdleF32 = 256, kServiceIdleF64 = 8, kFlushMinDefault = 2;
+constexpr int kHotSplits = 4;
 constexpr int kBlockDefault = 128, kBlockMax = 256;
 
 template <class P>

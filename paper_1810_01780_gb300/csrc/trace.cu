@@ -407,9 +407,9 @@ __global__ void __launch_bounds__(kBlockMax, P::kMinBlocks * 128 / kBlockMax) k_
     // ray is stepping.  The rare, long code paths -- a boundary split with its secondary,
     // writing a finished ray and loading the next one -- are parked and serviced together:
     // once the lane-iterations spent waiting since the last service reach sp.service_idle
-    // (many waiting lanes are served soon, a single one waits longer), or when no lane can
-    // step; so they run seldom, with many lanes at once, and stay out of the hot loop's
-    // instruction working set.
+    // (many waiting lanes are served soon, a single one waits longer), when no lane can step,
+    // or at once for a ray bouncing in a duct; so they run seldom, with many lanes at once,
+    // and stay out of the hot loop's instruction working set.
     while (__any_sync(0xffffffffu, active || done || fetch)) {
         __syncwarp();
         const bool stepping = active && L.pend == 0;
@@ -420,8 +420,12 @@ __global__ void __launch_bounds__(kBlockMax, P::kMinBlocks * 128 / kBlockMax) k_
         const bool waits = done || fetch || (active && L.pend != 0);
         const unsigned int wait = __ballot_sync(0xffffffffu, waits);
         const unsigned int step_mask = __ballot_sync(0xffffffffu, active && L.pend == 0);
+        // a ray that has already split kHotSplits times is bouncing in a duct: it reaches the
+        // next boundary within a few steps, and made to wait for the batch at every bounce it
+        // would outlast the launch
+        const bool hot = __any_sync(0xffffffffu, active && L.pend != 0 && L.n_refl >= kHotSplits);
         idle += (unsigned int)__popc(wait);
-        if (wait != 0u && (idle >= sp.service_idle || step_mask == 0u)) {
+        if (wait != 0u && (idle >= sp.service_idle || step_mask == 0u || hot)) {
             idle = 0;
             if (active && L.pend != 0 && finish_split<P>(med, L, sp, sk)) {
                 active = false;
