@@ -282,7 +282,7 @@ MLP_FLOPS_FWD = 2 * (3 * 256 + 3 * 256 * 256 + 256 * 12)  # per row, multiply-ad
 # DRAM bytes (read + write) of the four k_trace_wave<PrecF32, MediumLayered> launches of one
 # step of the 1,048,576-ray batched workload, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the current kernel (profiles/k_trace_wave_f32_layered_1M_dram.md)
-TRACE_DRAM_BYTES_PER_STEP = 1_970_997_248
+TRACE_DRAM_BYTES_PER_STEP = 1_966_933_248
 
 
 def peaks_leg(rp, local):
@@ -386,10 +386,10 @@ def surrogate_leg(rp, W, args, rank, flush):
     two = tc <= 2
     exist_ok, ang = [], []
     for k in range(2):
-        p_exist = 1.0 / (1.0 + np.exp(-pred[:, 6 * k]))
+        said = pred[:, 6 * k] > 0.0  # the existence logit: sigmoid > 1/2 exactly when it is > 0
         has = tc > k
-        exist_ok.append(((p_exist > 0.5) == has)[two])
-        both = two & has & (p_exist > 0.5)
+        exist_ok.append((said == has)[two])
+        both = two & has & said
         ang.append(np.abs((pred[both, 6 * k + 1] + 1.0) * (np.pi / 2) - tl[both, k]))
     ang = np.concatenate(ang) if ang else np.zeros(1)
     network_alone = {
