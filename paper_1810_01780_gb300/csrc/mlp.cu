@@ -106,6 +106,7 @@ __global__ void k_adam_pack(float *__restrict__ p, __nv_bfloat16 *__restrict__ p
                             unsigned char *__restrict__ pack, unsigned char *__restrict__ pack_t,
                             double *loss, double acc)
 {
+    rph::tc::chain_wait_release();  // the gradient comes from the weight-gradient kernel
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i == 0) {
         if (acc != 0.0) loss[1] += loss[0] * acc;
@@ -267,8 +268,10 @@ static int adam_step(rp_surrogate_s *s, float lr, double acc, cudaStream_t st)
     int rc = ensure_pack(s, st);  // current after a loss_grad: then a no-op
     if (rc) return rc;
     s->version += 1;
-    k_adam_pack<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(
-        s->p, s->pb, s->grad, s->m, s->v, np, lr, c1, c2, s->pack, s->pack_t, s->loss, acc);
+    if ((rc = launch_chained(k_adam_pack, dim3((unsigned)((np + 255) / 256)), dim3(256), 0, st,
+                             s->p, s->pb, s->grad, s->m, s->v, np, lr, c1, c2, s->pack,
+                             s->pack_t, s->loss, acc)))
+        return rc;
     s->pack_version = s->version;
     s->clean = true;
     RP_CUDA_TRY(cudaGetLastError());

@@ -78,6 +78,7 @@ constexpr uint32_t SM_XA = SM_W0 + 4096;
 constexpr uint32_t SM_TOTAL = SM_XA + 4096;
 static_assert(SM_TOTAL <= 227 * 1024, "shared memory map exceeds a CTA's limit");
 static_assert(SM_F % 16 == 0 && SM_BAR % 8 == 0, "alignment");
+static_assert(PF_B0 % 4 == 0 && PF_B1 % 4 == 0, "bias blocks load as float4");
 
 // instruction descriptors: D FP32, A and B BF16, both K-major, M = 128; N = 128 (a CTA's
 // columns of a layer) and N = 16 (the last layer, 12 outputs zero-padded)
@@ -359,6 +360,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const uint32_t remote_xbar = peer_addr(su32(&bar[3]), (uint32_t)peer);
 
     const uint32_t tmem = setup_cta(sm, tid, warp, 256u);
+    chain_wait_release();  // the weight images come from the previous Adam step
 
     Pending pd;
     const long long n_tiles = (n + kTile - 1) / kTile;
@@ -458,12 +460,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 for (int e = 0; e < 4; ++e) {
                     const int k0 = gc0 + e * 8;
                     float hh[8], dd[8];
+                    // 16-byte aligned: the bias blocks start at multiples of 4 floats, k0 % 8 == 0
+                    const float4 bl = *reinterpret_cast<const float4 *>(bias + k0);
+                    const float4 bh = *reinterpret_cast<const float4 *>(bias + k0 + 4);
+                    const float bv[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {  // gelu(z) and gelu'(z) from one Phi, one exp
-                        const float z = __uint_as_float(v[e * 8 + u]) + bias[k0 + u];
+                    for (int u = 0; u < 8; ++u) {  // gelu(z) and gelu'(z) from one Phi, one phi
+                        const float z = __uint_as_float(v[e * 8 + u]) + bv[u];
                         const PhiE pe = phi_e(z);
                         hh[u] = z * pe.phi;
-                        dd[u] = fmaf(z * pe.e, 0.39894228040143268f, pe.phi);
+                        dd[u] = fmaf(z, pe.d, pe.phi);
                         v[e * 8 + u] = __float_as_uint(dd[u]);
                     }
                     const uint4 pk = pack8(hh);
@@ -637,6 +643,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const uint32_t local = su32(sm), remote = peer_addr(local, (uint32_t)peer);
     const uint32_t remote_xbar = peer_addr(su32(&bar[3]), (uint32_t)peer);
     const uint32_t tmem = setup_cta(sm, tid, warp, 128u);
+    chain_wait_release();  // g3 and gelu'(z) come from the forward pass
 
     Pending pd;
     pd.off = 1;  // the halves alternate between A tiles 1 (g2) and 0 (g1)
@@ -752,11 +759,10 @@ int train_fwd(rp_surrogate_s *s, long long n, const float *x, const float *y, co
                                      (int)SM_TOTAL));
     const long long tiles = (n + kTile - 1) / kTile;
     const int clusters = (int)std::min<long long>(tiles, (long long)sm_count(dev) / 2);
-    k_train_fwd<<<2 * clusters, kThreads, SM_TOTAL, st>>>(
-        s->pack, x, y, t, n, s->Z[0], s->Z[1], s->Z[2], s->H[1], s->H[2], s->H[3], s->H[4],
-        s->ximg, s->g4img, s->gl[3], db4, db3, s->loss, s->fflag, wait_cycles(s));
-    RP_CUDA_TRY(cudaGetLastError());
-    return RP_OK;
+    return launch_chained(k_train_fwd, dim3(2 * clusters), dim3(kThreads), SM_TOTAL, st,
+                          (const unsigned char *)s->pack, x, y, t, n, s->Z[0], s->Z[1], s->Z[2],
+                          s->H[1], s->H[2], s->H[3], s->H[4], s->ximg, s->g4img, s->gl[3], db4,
+                          db3, s->loss, s->fflag, wait_cycles(s));
 }
 
 int train_bwd(rp_surrogate_s *s, long long n, float *db2, float *db1, float *db0, cudaStream_t st)
@@ -768,11 +774,11 @@ int train_bwd(rp_surrogate_s *s, long long n, float *db2, float *db1, float *db0
                                      (int)SM_TOTAL));
     const long long tiles = (n + kTile - 1) / kTile;
     const int clusters = (int)std::min<long long>(tiles, (long long)sm_count(dev) / 2);
-    k_train_bwd<<<2 * clusters, kThreads, SM_TOTAL, st>>>(
-        s->pack_t, s->gl[3], s->Z[0], s->Z[1], s->Z[2], n, s->gl[2], s->gl[1], s->gl[0], db2,
-        db1, db0, s->fflag, wait_cycles(s));
-    RP_CUDA_TRY(cudaGetLastError());
-    return RP_OK;
+    return launch_chained(k_train_bwd, dim3(2 * clusters), dim3(kThreads), SM_TOTAL, st,
+                          (const unsigned char *)s->pack_t, (const unsigned char *)s->gl[3],
+                          (const float *)s->Z[0], (const float *)s->Z[1], (const float *)s->Z[2],
+                          n, s->gl[2], s->gl[1], s->gl[0], db2, db1, db0, s->fflag,
+                          wait_cycles(s));
 }
 
 }  // namespace rph

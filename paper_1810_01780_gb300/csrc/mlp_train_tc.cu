@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = *slot;
+    chain_wait_release();  // the images come from the forward and backward passes
 
     if (tid == 0) {
         // One thread copies and issues.  Tile i (the i-th of this CTA) uses stage i % S, as
@@ -253,9 +254,8 @@ int tc_wgrad(WgradArgs &a, long long n, int *flag, long long wait, cudaStream_t 
     const dim3 grid((unsigned)std::max(wide, thin), 4, 5);  // y: M half + 2 x N half
     RP_CUDA_TRY(cudaFuncSetAttribute(k_tc_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)WG_TOTAL));
-    k_tc_wgrad<<<grid, kThreads, WG_TOTAL, st>>>(a, tiles, flag, wait);
-    RP_CUDA_TRY(cudaGetLastError());
-    return RP_OK;
+    return launch_chained(k_tc_wgrad, grid, dim3(kThreads), WG_TOTAL, st, (const WgradArgs)a,
+                          tiles, flag, wait);
 }
 
 }  // namespace rph

@@ -7,6 +7,7 @@
 #include <cstddef>
 #include <cstdlib>
 #include <mutex>
+#include <utility>
 
 #include "rp.h"
 #include "trace_core.cuh"
@@ -76,6 +77,27 @@ int cuda_fail(cudaError_t e, const char *what);
         cudaError_t _e = (expr);                                  \
         if (_e != cudaSuccess) return rph::cuda_fail(_e, #expr);  \
     } while (0)
+
+// Launches k on st as a programmatic dependent launch: k may be scheduled while the kernel
+// before it in the stream still runs, and must call tc::chain_wait_release() in every thread
+// before it touches global memory that earlier work in the stream writes or reads.
+template <typename... P, typename... A>
+int launch_chained(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                   A &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    RP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...));
+    return RP_OK;
+}
 
 // Grow-only device workspace, one per device; the lock serialises calls on that device.
 struct Workspace {

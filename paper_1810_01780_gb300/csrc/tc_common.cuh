@@ -12,6 +12,19 @@ namespace tc {
 
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at the maximum SM clock
 
+// Programmatic dependent launch (a kernel launched with launch_chained): waits until the
+// kernel before this one in the stream has completed and its writes are visible, then lets the
+// next chained kernel be scheduled, so that its launch and its CTAs' setup overlap this
+// kernel's work.  Every thread calls it before its first access to global memory that earlier
+// work in the stream writes or reads; in a kernel launched without the attribute it returns at
+// once.  As each chained kernel releases its successor only after its own wait, a kernel past
+// the wait also follows every earlier kernel of the stream.
+__device__ __forceinline__ void chain_wait_release()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t su32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -59,40 +72,43 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long lon
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// The erf-form GELU, gelu(z) = z Phi(z) with Phi(z) = (1 + erf(z / sqrt 2)) / 2, and its
-// derivative gelu'(z) = Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi).  erf is taken
-// from Abramowitz and Stegun, Handbook of Mathematical Functions, formula 7.1.26 (Hastings'
-// rational approximation, absolute error <= 1.5e-7): for x >= 0,
-//   erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),  t = 1 / (1 + p x),
-// so one exponential exp(-z^2 / 2) = exp(-x^2) (x = |z| / sqrt 2) serves both Phi and phi.
+// The erf-form GELU, gelu(z) = z Phi(z) with Phi the standard normal distribution function,
+// and its derivative gelu'(z) = Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi) the
+// normal density.  Phi is taken from Abramowitz and Stegun, Handbook of Mathematical
+// Functions, formula 26.2.17 (Hastings' rational approximation, absolute error < 7.5e-8): for
+// x >= 0,
+//   1 - Phi(x) = phi(x) t (b1 + t (b2 + t (b3 + t (b4 + t b5)))),  t = 1 / (1 + p x),
+// so one density phi(z) = 2^(-z^2 log2(e) / 2 - log2 sqrt(2 pi)) serves both Phi and gelu'.
 // Every activation is rounded to BF16 (relative precision 2^-9) before it enters a product,
 // far coarser than this error.
 struct PhiE {
     float phi;  // Phi(z)
-    float e;    // exp(-z^2 / 2)
+    float d;    // phi(z), the normal density
 };
 __device__ __forceinline__ PhiE phi_e(float z)
 {
-    const float x = fabsf(z) * 0.70710678118654752f;
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
-    float p = fmaf(t, 1.061405429f, -1.453152027f);
-    p = fmaf(t, p, 1.421413741f);
-    p = fmaf(t, p, -0.284496736f);
-    p = fmaf(t, p, 0.254829592f);
+    float t;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(fmaf(0.2316419f, fabsf(z), 1.0f)));
+    float p = fmaf(t, 1.330274429f, -1.821255978f);
+    p = fmaf(t, p, 1.781477937f);
+    p = fmaf(t, p, -0.356563782f);
+    p = fmaf(t, p, 0.319381530f);
     p *= t;
-    float e;  // 2^(-z^2 log2(e) / 2)
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(z * z * -0.72134752044448170f));
-    const float q = 0.5f * p * e;  // (1 - erf(x)) / 2
+    float d;
+    asm("ex2.approx.ftz.f32 %0, %1;"
+        : "=f"(d)
+        : "f"(fmaf(z * z, -0.72134752044448170f, -1.3257480647361594f)));
+    const float q = p * d;  // 1 - Phi(|z|)
     PhiE r;
     r.phi = z >= 0.0f ? 1.0f - q : q;
-    r.e = e;
+    r.d = d;
     return r;
 }
 __device__ __forceinline__ float gelu(float z) { return z * phi_e(z).phi; }
 __device__ __forceinline__ float gelu_prime(float z)
 {
     const PhiE r = phi_e(z);
-    return fmaf(z * r.e, 0.39894228040143268f, r.phi);
+    return fmaf(z, r.d, r.phi);
 }
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 __device__ __forceinline__ uint32_t pack2(float lo, float hi)
