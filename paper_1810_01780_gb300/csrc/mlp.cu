@@ -184,7 +184,7 @@ int ensure_acts(rp_surrogate_s *s, long long n)
     free_acts(s);
     const long long cap = n + n / 4;
     const size_t tiles = (size_t)((cap + 127) / 128);
-    for (int l = 0; l < 3; ++l) RP_CUDA_TRY(cudaMalloc(&s->Z[l], tiles * 128 * 256 * sizeof(float)));
+    for (int l = 0; l < 3; ++l) RP_CUDA_TRY(cudaMalloc(&s->Z[l], tiles * 128 * 256 * 2));
     for (int l = 1; l < 5; ++l) RP_CUDA_TRY(cudaMalloc(&s->H[l], tiles * rph::tc::kImage));
     for (int l = 0; l < 4; ++l) RP_CUDA_TRY(cudaMalloc(&s->gl[l], tiles * rph::tc::kImage));
     RP_CUDA_TRY(cudaMalloc(&s->ximg, tiles * rph::tc::kImage16));

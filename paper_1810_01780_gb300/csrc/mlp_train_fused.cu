@@ -17,10 +17,10 @@
 //
 // k_train_fwd: layer 0 (3 -> 256) as one MMA of K = 16 (x zero-padded, from a 16-column A
 //   operand the CTA writes), then the three 256 -> 256 layers.  An epilogue evaluates GELU and
-//   its derivative from one Phi and one exponential, and also stores what the later kernels
-//   read: gelu'(z) of the pre-activations z0..z2 in FP32 (tiled: a tile's 8 columns k..k+7 of
-//   its 128 rows are 4 KB contiguous, so a warp's stores and the backward pass's loads of one
-//   8-column group are 1 KB contiguous) and the activations H1..H4 as BF16 operand images
+//   its derivative from one Phi and one density, and also stores what the later kernels
+//   read: gelu'(z) of the pre-activations z0..z2 in BF16 (tiled: a tile's 8 columns k..k+7 of
+//   its 128 rows are 2 KB contiguous, so a warp's stores of one 8-column group are 512 B
+//   contiguous and a CTA's 128 columns are one 32 KB block) and the activations H1..H4 as BF16 operand images
 //   (tc_common.cuh), and x as a 16-column image.  The last layer (256 -> 12) is 16 MMAs of
 //   N = 16 (outputs zero-padded) from the whole H4 tile, done alike by both CTAs; the loss and
 //   its gradient g4 follow per row (g4 stored as a 16-column image, its column sums added to
@@ -30,12 +30,14 @@
 //   gradient db3.
 // k_train_bwd: per tile, the g3 image by bulk copy as the A tile (prefetched while the previous
 //   tile's last epilogue runs), then for the hidden layers
-//   3, 2, 1 the backward images B[n][k] = W[n][k] and an epilogue
+//   3, 2, 1 the backward images B[n][k] = W[n][k], gelu'(z) of the CTA's columns by bulk copy
+//   while the MMAs run, and an epilogue
 //   g_{l-1} = (g_l W_l^T) gelu'(z_{l-1}) that stores g_{l-1} as a BF16 image, adds its column
 //   sums to db_{l-1} and, but for the last, feeds it to both CTAs' next A tile.
 // Arithmetic is that of the per-layer path: BF16 operands (weights, activations and
-// gradients rounded to BF16 where they enter a product), FP32 products and sums, FP32 bias,
-// GELU and GELU'; bias gradients are sums of the unrounded FP32 g.  A batch's last, partial
+// gradients rounded to BF16 where they enter a product, gelu'(z) rounded to BF16 between the
+// passes), FP32 products and sums, FP32 bias, GELU and GELU'; bias gradients are sums of the
+// FP32 g before its rounding.  A batch's last, partial
 // tile is computed whole: its rows past n have zero output gradients, so they add nothing to
 // any gradient.
 // Synchronisation and failure: every mbarrier wait is bounded (the surrogate's wait limit).
@@ -64,20 +66,26 @@ constexpr int kHalf = 128;     // output columns of a CTA
 constexpr int kGroups = kThreads / 128;     // column groups of a row
 constexpr int kGroupCols = kHalf / kGroups; // 32: one TMEM load per warp
 constexpr uint32_t kHalfImage = kImage;     // bytes of a half B image (N 128 x K 256, BF16)
-// shared memory map (bytes): A tiles 0 and 1, the half B image, FP32 constants, barriers
+// shared memory map (bytes): A tiles 0 and 1, the half B image, barriers, then per kernel
 constexpr uint32_t SM_A0 = 0;
 constexpr uint32_t SM_A1 = 65536;
 constexpr uint32_t SM_B = 131072;
-constexpr uint32_t SM_F = SM_B + kHalfImage;
-// barriers: B image, MMAs, A tile / W0 image, then the peer's halves of A tiles 0 and 1
-constexpr uint32_t SM_BAR = SM_F + kPackF * 4;
+// barriers: B image, MMAs, A tile / W0 image, the peer's halves of A tiles 0 and 1, gelu'(z)
+constexpr uint32_t SM_BAR = SM_B + kHalfImage;
 constexpr uint32_t SM_SLOT = SM_BAR + 48;  // TMEM address, abort word, copies the peer sent
-// forward only: the CTA's half of the W0 image (4 KB) and the x operand (128 rows x 16, 4 KB)
-constexpr uint32_t SM_W0 = (SM_BAR + 64 + 1023) / 1024 * 1024;
+constexpr uint32_t SM_OWN = SM_BAR + 1024;
+// forward: the FP32 constants, the CTA's half of the W0 image (4 KB) and the x operand (128
+// rows x 16, 4 KB)
+constexpr uint32_t SM_F = SM_OWN;
+constexpr uint32_t SM_W0 = (SM_F + kPackF * 4 + 1023) / 1024 * 1024;
 constexpr uint32_t SM_XA = SM_W0 + 4096;
-constexpr uint32_t SM_TOTAL = SM_XA + 4096;
-static_assert(SM_TOTAL <= 227 * 1024, "shared memory map exceeds a CTA's limit");
-static_assert(SM_F % 16 == 0 && SM_BAR % 8 == 0, "alignment");
+constexpr uint32_t SM_TOTAL_FWD = SM_XA + 4096;
+// backward: gelu'(z) of the tile's rows and the CTA's 128 columns (BF16, 16 groups of 2 KB)
+constexpr uint32_t SM_DZ = SM_OWN;
+constexpr uint32_t SM_TOTAL_BWD = SM_DZ + 32768;
+static_assert(SM_TOTAL_FWD <= 227 * 1024 && SM_TOTAL_BWD <= 227 * 1024,
+              "shared memory map exceeds a CTA's limit");
+static_assert(SM_F % 16 == 0 && SM_DZ % 16 == 0 && SM_BAR % 8 == 0, "alignment");
 static_assert(PF_B0 % 4 == 0 && PF_B1 % 4 == 0, "bias blocks load as float4");
 
 // instruction descriptors: D FP32, A and B BF16, both K-major, M = 128; N = 128 (a CTA's
@@ -151,24 +159,15 @@ __device__ __forceinline__ void issue_ksteps(uint32_t tmem, uint32_t a_base, uin
     }
 }
 
-__device__ __forceinline__ void store8(float *dst, const float (&v)[8])
-{
-    reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
-    reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
-}
 __device__ __forceinline__ uint4 pack8(const float (&v)[8])
 {
     return make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
 }
-// the 8 FP32 values of columns k0..k0+7 (k0 % 8 == 0) of row `row` of tile `tile` in a tiled
-// pre-activation buffer
-__device__ __forceinline__ float *zt_at(float *Z, long long tile, int row, int k0)
+// byte offset of the 8 BF16 values of columns k0..k0+7 (k0 % 8 == 0) of row `row` of tile
+// `tile` in a tiled gelu'(z) buffer: 2 KB per 8-column group, the groups in column order
+__device__ __forceinline__ long long zb_off(long long tile, int row, int k0)
 {
-    return Z + tile * (128LL * 256) + (k0 >> 3) * 1024 + row * 8;
-}
-__device__ __forceinline__ const float *zt_at(const float *Z, long long tile, int row, int k0)
-{
-    return Z + tile * (128LL * 256) + (k0 >> 3) * 1024 + row * 8;
+    return tile * 65536LL + (long long)(k0 >> 3) * 2048 + row * 16;
 }
 
 // One CTA's state of the bounded waits: whether a copy (or MMAs) is in flight and the phase
@@ -176,8 +175,8 @@ __device__ __forceinline__ const float *zt_at(const float *Z, long long tile, in
 // sequence of halves sent each way goes to A tile (c + off) % 2 and completes phase c / 2 of
 // barrier 3 + (c + off) % 2 of the receiver.
 struct Pending {
-    bool ld = false, mma = false, a = false;
-    uint32_t ph_ld = 0, ph_mma = 0, ph_a = 0;
+    bool ld = false, mma = false, a = false, dz = false;
+    uint32_t ph_ld = 0, ph_mma = 0, ph_a = 0, ph_dz = 0;
     long long sent = 0, recv = 0;
     int off = 0;
 };
@@ -191,7 +190,7 @@ __device__ __forceinline__ uint32_t setup_cta(unsigned char *sm, int tid, int wa
     uint32_t *slot = reinterpret_cast<uint32_t *>(sm + SM_SLOT);
     volatile int *abort_cta = reinterpret_cast<volatile int *>(sm + SM_SLOT + 4);
     if (tid == 0) {
-        for (int b = 0; b < 5; ++b)
+        for (int b = 0; b < 6; ++b)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[b])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         mbar_expect(su32(&bar[3]), kImage / 2);
@@ -316,6 +315,7 @@ __device__ __forceinline__ void teardown_cta(unsigned char *sm, int tid, int war
         if (pd.ld) mbar_wait(su32(&bar[0]), pd.ph_ld);
         if (pd.mma) mbar_wait(su32(&bar[1]), pd.ph_mma);
         if (pd.a) mbar_wait(su32(&bar[2]), pd.ph_a);
+        if (pd.dz) mbar_wait(su32(&bar[5]), pd.ph_dz);
         asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(remote + SM_SLOT + 8),
                      "r"((uint32_t)pd.sent)
                      : "memory");
@@ -336,13 +336,13 @@ __device__ __forceinline__ void teardown_cta(unsigned char *sm, int tid, int war
 }
 
 // Forward pass, loss and last-layer backward of n rows (x (n, 3), targets y (n, 2), t (n, 10)).
-// Writes gelu'(z0), gelu'(z1), gelu'(z2) (tiled FP32), the images of x, H1..H4, g4 and g3, adds the loss sum to
+// Writes gelu'(z0), gelu'(z1), gelu'(z2) (tiled BF16), the images of x, H1..H4, g4 and g3, adds the loss sum to
 // *loss and the column sums of g4 and g3 to db4 and db3.
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     k_train_fwd(const unsigned char *__restrict__ pack, const float *__restrict__ x,
                 const float *__restrict__ y, const float *__restrict__ t, long long n,
-                float *__restrict__ Z0, float *__restrict__ Z1, float *__restrict__ Z2,
-                unsigned char *__restrict__ H1, unsigned char *__restrict__ H2,
+                unsigned char *__restrict__ Z0, unsigned char *__restrict__ Z1,
+                unsigned char *__restrict__ Z2, unsigned char *__restrict__ H1, unsigned char *__restrict__ H2,
                 unsigned char *__restrict__ H3, unsigned char *__restrict__ H4,
                 unsigned char *__restrict__ Xi, unsigned char *__restrict__ G4,
                 unsigned char *__restrict__ G3, float *__restrict__ db4,
@@ -369,7 +369,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const int q = warp & 3, ch = warp >> 2;
     const int erow = q * 32 + lane;
     const float inv_n = 1.0f / (float)n;
-    float *Zs[3] = {Z0, Z1, Z2};
+    unsigned char *Zs[3] = {Z0, Z1, Z2};
     unsigned char *Hs[4] = {H1, H2, H3, H4};
     bool failed = false;
     const uint32_t bar_w0 = su32(&bar[2]);
@@ -474,7 +474,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     }
                     const uint4 pk = pack8(hh);
                     *reinterpret_cast<uint4 *>(Hl + a_off(erow, k0)) = pk;
-                    if (l < 3) store8(zt_at(Zs[l], tile, erow, k0), dd);
+                    if (l < 3) *reinterpret_cast<uint4 *>(Zs[l] + zb_off(tile, erow, k0)) = pack8(dd);
                     *reinterpret_cast<uint4 *>(sm + abuf + a_off(erow, k0)) = pk;
                 }
                 if (l == 3) tmem_st32(ta, v);  // gelu'(z3) in place of z3, for the g3 pass
@@ -621,14 +621,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     teardown_cta(sm, tid, warp, tmem, 256u, failed, pd, flag, remote);
 }
 
-// Backward-data chain of the hidden layers for n rows: from the g3 image and the tiled
+// Backward-data chain of the hidden layers for n rows: from the g3 image and the tiled BF16
 // gelu'(z0..z2), writes the images of g2, g1, g0 with g_{l-1} = (g_l W_l^T) gelu'(z_{l-1}) and
 // adds their column sums to db2, db1, db0.  pack_t: the backward images of
 // W1, W2, W3 (B[n][k] = W[n][k]).
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     k_train_bwd(const unsigned char *__restrict__ pack_t, const unsigned char *__restrict__ G3,
-                const float *__restrict__ Z0, const float *__restrict__ Z1,
-                const float *__restrict__ Z2, long long n, unsigned char *__restrict__ G2,
+                const unsigned char *__restrict__ Z0, const unsigned char *__restrict__ Z1,
+                const unsigned char *__restrict__ Z2, long long n, unsigned char *__restrict__ G2,
                 unsigned char *__restrict__ G1, unsigned char *__restrict__ G0,
                 float *__restrict__ db2, float *__restrict__ db1, float *__restrict__ db0,
                 int *flag, long long wait)
@@ -638,6 +638,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     volatile int *abort_cta = reinterpret_cast<volatile int *>(sm + SM_SLOT + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t bar_ld = su32(&bar[0]), bar_mma = su32(&bar[1]), bar_a = su32(&bar[2]);
+    const uint32_t bar_dz = su32(&bar[5]);
     const uint32_t b_base = su32(sm + SM_B);
     const int h = (int)cluster_rank(), peer = h ^ 1;
     const uint32_t local = su32(sm), remote = peer_addr(local, (uint32_t)peer);
@@ -651,7 +652,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const long long first = cluster_id(), stride = cluster_count();
     const int q = warp & 3, ch = warp >> 2;
     const int erow = q * 32 + lane;
-    const float *Zin[3] = {Z2, Z1, Z0};  // gelu'(z) of the layer below layers 3, 2, 1
+    const unsigned char *Zin[3] = {Z2, Z1, Z0};  // gelu'(z) of the layer below layers 3, 2, 1
     unsigned char *Gout[3] = {G2, G1, G0};
     float *dbs[3] = {db2, db1, db0};
     bool failed = false;
@@ -671,24 +672,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 
     for (long long tile = first; tile < n_tiles; tile += stride) {
         for (int l = 0; l < 3; ++l) {  // hidden layers 3, 2, 1
-            // this thread's gelu'(z) of the layer below (its row, its 32 columns), loaded while
-            // the layer's MMAs run
-            float dz[32];
-            if (!failed) {
-                const float4 *zs = reinterpret_cast<const float4 *>(
-                    zt_at(Zin[l], tile, erow, h * kHalf + ch * kGroupCols));
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {  // 8-column group e: 1 KB further on
-                    const float4 a = __ldg(zs + e * 256), c = __ldg(zs + e * 256 + 1);
-                    dz[e * 8 + 0] = a.x; dz[e * 8 + 1] = a.y; dz[e * 8 + 2] = a.z; dz[e * 8 + 3] = a.w;
-                    dz[e * 8 + 4] = c.x; dz[e * 8 + 5] = c.y; dz[e * 8 + 6] = c.z; dz[e * 8 + 7] = c.w;
-                }
-            }
             if (!failed) {
                 fence_before();
                 __syncthreads();
                 fence_after();
                 if (tid == 0) {
+                    // gelu'(z) of the layer below for the CTA's 128 columns (32 KB), copied
+                    // while the MMAs run; the buffer's last readers, the previous epilogue,
+                    // have passed the barrier above after a proxy fence
+                    mbar_expect(bar_dz, 32768u);
+                    bulk_g2s(local + SM_DZ, Zin[l] + zb_off(tile, 0, h * kHalf), 32768u, bar_dz);
+                    pd.dz = true;
                     bool ok;
                     if (l == 0) {
                         ok = mbar_wait(bar_a, pd.ph_a, wait);
@@ -703,9 +697,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     const unsigned char *img = pack_t + (l < 2 ? 1 - l : 2) * kPackW;
                     if (!ok || !run_layer(pd, sm, tmem, local + (l & 1) * 65536u, b_base, bar_ld,
                                           bar_mma, next, img, h, l > 0, wait))
-                        *abort_cta = 1;
+                        ok = false;
                     else if (l == 2 && tile + stride < n_tiles)
                         load_g3(tile + stride);  // A tile 0 read for the last time this tile
+                    if (ok) {
+                        ok = mbar_wait(bar_dz, pd.ph_dz, wait);
+                        if (ok) {
+                            pd.dz = false;
+                            pd.ph_dz ^= 1u;
+                        }
+                    }
+                    if (!ok) *abort_cta = 1;
                 }
                 __syncthreads();
                 fence_after();
@@ -718,13 +720,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0, v);
                 float cs[32];  // this row's g of the 32 columns, for the column sums
+                // this row's gelu'(z) of the 32 columns: group ch * 4 + e of the CTA's 16
+                const unsigned char *dzs = sm + SM_DZ + ch * 4 * 2048 + erow * 16;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int k0 = gc0 + e * 8;
+                    const uint4 w = *reinterpret_cast<const uint4 *>(dzs + e * 2048);
+                    const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
                     float gg[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        gg[u] = __uint_as_float(v[e * 8 + u]) * dz[e * 8 + u];
+                    for (int u = 0; u < 8; ++u) {  // BF16 pairs: column k0 + u in half u % 2
+                        const uint32_t b = wv[u >> 1];
+                        const float dz = __uint_as_float((u & 1) ? (b & 0xffff0000u) : (b << 16));
+                        gg[u] = __uint_as_float(v[e * 8 + u]) * dz;
                         cs[e * 8 + u] = gg[u];
                     }
                     const uint4 pk = pack8(gg);
@@ -739,7 +747,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 }
             }
         }
-        if (!failed) {  // the next tile's copy overwrites A tile 0, its MMAs the accumulator
+        if (!failed) {  // the next tile's copies overwrite A tile 0 and gelu'(z), its MMAs
+                        // the accumulator
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             fence_before();
             __syncthreads();
         }
@@ -756,10 +766,10 @@ int train_fwd(rp_surrogate_s *s, long long n, const float *x, const float *y, co
     int dev;
     RP_CUDA_TRY(cudaGetDevice(&dev));
     RP_CUDA_TRY(cudaFuncSetAttribute(k_train_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)SM_TOTAL));
+                                     (int)SM_TOTAL_FWD));
     const long long tiles = (n + kTile - 1) / kTile;
     const int clusters = (int)std::min<long long>(tiles, (long long)sm_count(dev) / 2);
-    return launch_chained(k_train_fwd, dim3(2 * clusters), dim3(kThreads), SM_TOTAL, st,
+    return launch_chained(k_train_fwd, dim3(2 * clusters), dim3(kThreads), SM_TOTAL_FWD, st,
                           (const unsigned char *)s->pack, x, y, t, n, s->Z[0], s->Z[1], s->Z[2],
                           s->H[1], s->H[2], s->H[3], s->H[4], s->ximg, s->g4img, s->gl[3], db4,
                           db3, s->loss, s->fflag, wait_cycles(s));
@@ -771,12 +781,13 @@ int train_bwd(rp_surrogate_s *s, long long n, float *db2, float *db1, float *db0
     int dev;
     RP_CUDA_TRY(cudaGetDevice(&dev));
     RP_CUDA_TRY(cudaFuncSetAttribute(k_train_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)SM_TOTAL));
+                                     (int)SM_TOTAL_BWD));
     const long long tiles = (n + kTile - 1) / kTile;
     const int clusters = (int)std::min<long long>(tiles, (long long)sm_count(dev) / 2);
-    return launch_chained(k_train_bwd, dim3(2 * clusters), dim3(kThreads), SM_TOTAL, st,
+    return launch_chained(k_train_bwd, dim3(2 * clusters), dim3(kThreads), SM_TOTAL_BWD, st,
                           (const unsigned char *)s->pack_t, (const unsigned char *)s->gl[3],
-                          (const float *)s->Z[0], (const float *)s->Z[1], (const float *)s->Z[2],
+                          (const unsigned char *)s->Z[0], (const unsigned char *)s->Z[1],
+                          (const unsigned char *)s->Z[2],
                           n, s->gl[2], s->gl[1], s->gl[0], db2, db1, db0, s->fflag,
                           wait_cycles(s));
 }

@@ -20,10 +20,11 @@ struct rp_surrogate_s {
     float *p, *m, *v, *grad;
     __nv_bfloat16 *pb;
     // training buffers for a batch of up to `cap` rows, per 128-row tile: gelu'(z) of the
-    // pre-activations z0..z2 (FP32, tiled), the activations H1..H4 and the gradients g0..g3 as BF16 operand
-    // images (64 KB per tile; H[0] unused), and x and g4 as 16-column images (4 KB per tile)
+    // pre-activations z0..z2 (BF16, tiled, 64 KB per tile), the activations H1..H4 and the
+    // gradients g0..g3 as BF16 operand images (64 KB per tile; H[0] unused), and x and g4 as
+    // 16-column images (4 KB per tile)
     long long cap;
-    float *Z[3];
+    unsigned char *Z[3];
     unsigned char *H[5], *gl[4];
     unsigned char *ximg, *g4img;
     double *loss;
