@@ -72,7 +72,7 @@ constexpr uint32_t SM_A1 = 65536;
 constexpr uint32_t SM_B = 131072;
 // barriers: B image, MMAs, A tile / W0 image, the peer's halves of A tiles 0 and 1, gelu'(z)
 constexpr uint32_t SM_BAR = SM_B + kHalfImage;
-constexpr uint32_t SM_SLOT = SM_BAR + 48;  // TMEM address, abort word, copies the peer sent
+constexpr uint32_t SM_SLOT = SM_BAR + 48;  // TMEM address, abort word; the peer's sent count, failure
 constexpr uint32_t SM_OWN = SM_BAR + 1024;
 // forward: the FP32 constants, the CTA's half of the W0 image (4 KB) and the x operand (128
 // rows x 16, 4 KB)
@@ -146,11 +146,14 @@ __device__ __forceinline__ void load_half_image(uint32_t b_base, const unsigned 
 __device__ __forceinline__ void issue_ksteps(uint32_t tmem, uint32_t a_base, uint32_t b_base,
                                              int s0, bool fresh)
 {
+    // a K step is 4 KB further on in both operands: 256 in the descriptors' address field
+    // (address / 16, 14 bits, which shared addresses below 256 KB never carry out of)
+    const uint64_t ad0 = sdesc(a_base + s0 * 4096u, 2048u, 128u);
+    const uint64_t bd0 = sdesc(b_base + s0 * 4096u, 2048u, 128u);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        const int s = s0 + i;
-        const uint64_t ad = sdesc(a_base + s * 4096u, 2048u, 128u);
-        const uint64_t bd = sdesc(b_base + s * 4096u, 2048u, 128u);
+        const uint64_t ad = ad0 + (uint64_t)(i * 256);
+        const uint64_t bd = bd0 + (uint64_t)(i * 256);
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
@@ -302,9 +305,13 @@ __device__ __forceinline__ bool run_layer(Pending &pd, unsigned char *sm, uint32
 }
 
 // Shared teardown: on failure record it and drain the issued work (default bound); then tell
-// the peer how many halves this CTA sent it, wait (default bound) for those the peer sent that
-// have not been waited for, and pass a last cluster barrier, so that no CTA leaves while a copy
-// into its shared memory is in flight; free tensor memory.
+// the peer how many halves this CTA sent it and whether it failed, and pass a cluster barrier.
+// Without a failure in the cluster each CTA has waited for every half the peer sent (each
+// layer's MMAs wait for the peer's half of their input), so no copy is in flight any more.
+// After a failure each CTA waits (default bound) for the halves the peer sent that it has not
+// waited for, and passes a second cluster barrier, so that no CTA leaves while a copy into or
+// out of its shared memory is in flight; both CTAs take the same branch, as both know both
+// failure flags.  Then tensor memory is freed.
 __device__ __forceinline__ void teardown_cta(unsigned char *sm, int tid, int warp, uint32_t tmem,
                                              uint32_t cols, bool failed, Pending &pd, int *flag,
                                              uint32_t remote)
@@ -319,16 +326,22 @@ __device__ __forceinline__ void teardown_cta(unsigned char *sm, int tid, int war
         asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(remote + SM_SLOT + 8),
                      "r"((uint32_t)pd.sent)
                      : "memory");
+        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(remote + SM_SLOT + 12),
+                     "r"((uint32_t)failed)
+                     : "memory");
     }
     __syncthreads();
     cluster_sync();
-    if (tid == 0) {
-        const long long peer_sent = *reinterpret_cast<volatile uint32_t *>(sm + SM_SLOT + 8);
-        while (pd.recv < peer_sent && recv_half(pd, sm, kWaitCycles)) {
+    const bool peer_failed = *reinterpret_cast<volatile uint32_t *>(sm + SM_SLOT + 12) != 0u;
+    if (failed || peer_failed) {
+        if (tid == 0) {
+            const long long peer_sent = *reinterpret_cast<volatile uint32_t *>(sm + SM_SLOT + 8);
+            while (pd.recv < peer_sent && recv_half(pd, sm, kWaitCycles)) {
+            }
         }
+        __syncthreads();
+        cluster_sync();
     }
-    __syncthreads();
-    cluster_sync();
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols)
                      : "memory");
