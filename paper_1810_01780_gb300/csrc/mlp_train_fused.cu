@@ -497,6 +497,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 if (tid == 0) send_half(pd, local, remote, remote_xbar, l & 1, h);
             }
         }
+        // the targets of the loss phase's rows (one per thread of column group 0), loaded while
+        // the last layer's MMAs run
+        float yr[2], tr[10];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) yr[k] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 10; ++j) tr[j] = 0.0f;
+        if (!failed && ch == 0 && g0 + erow < n) {
+            const long long gr = g0 + erow;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) yr[k] = y[gr * 2 + k];
+#pragma unroll
+            for (int j = 0; j < 10; ++j) tr[j] = t[gr * 10 + j];
+        }
         // the last layer (256 -> 12, as N = 16) from A tile 1 (H4) into TMEM columns 128..143
         if (!failed) {
             if (tid == 0) {
@@ -547,12 +561,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     for (int o = 0; o < 12; ++o) out[o] = __uint_as_float(v[o]) + sF[PF_B4 + o];
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
-                        const float z = out[6 * k], yk = y[gr * 2 + k];
+                        const float z = out[6 * k], yk = yr[k];
                         L += fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z))) - yk * z;
                         gg[6 * k] = (1.0f / (1.0f + expf(-z)) - yk) * inv_n;
 #pragma unroll
                         for (int j = 0; j < 5; ++j) {
-                            const float d = out[6 * k + 1 + j] - t[gr * 10 + 5 * k + j];
+                            const float d = out[6 * k + 1 + j] - tr[5 * k + j];
                             L += 0.5f * yk * d * d;
                             gg[6 * k + 1 + j] = yk * d * inv_n;
                         }
