@@ -48,6 +48,7 @@ constexpr uint32_t SM_TOTAL = SM_BAR + 32;
 static_assert(SM_TOTAL <= 227 * 1024, "shared memory map exceeds a CTA's limit");
 static_assert(SM_F % 16 == 0 && SM_BAR % 8 == 0, "alignment");
 static_assert((kGroups - 1) * kTile * 12 * 4 <= 65536, "layer-4 partial sums reuse the A tile");
+static_assert(PF_W4 % 4 == 0, "W4 rows load as float4");
 
 // instruction descriptor: D FP32, A and B BF16, both K-major, N = 128 (one half of the
 // layer's output columns), M = 128
@@ -144,9 +145,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 *reinterpret_cast<uint4 *>(sA + a_off(row0, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
-        float acc[12];
+        float2 acc2[6];  // the 12 outputs of the last layer as pairs (o, o + 1)
 #pragma unroll
-        for (int o = 0; o < 12; ++o) acc[o] = 0.0f;
+        for (int o = 0; o < 6; ++o) acc2[o] = make_float2(0.0f, 0.0f);
 
         for (int l = 0; l < 3; ++l) {
             // the A tile written by this CTA's threads becomes visible to the tensor cores
@@ -214,19 +215,35 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const int j = e * 8 + 2 * u;
-                            w[u] = pack2(gelu(__uint_as_float(v[j]) + bias[col0 + j]),
-                                         gelu(__uint_as_float(v[j + 1]) + bias[col0 + j + 1]));
+                            const float2 g = gelu2(__fadd2_rn(
+                                make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])),
+                                make_float2(bias[col0 + j], bias[col0 + j + 1])));
+                            w[u] = pack2(g.x, g.y);
                         }
                         *reinterpret_cast<uint4 *>(sA + a_off(erow, col0 + e * 8)) =
                             make_uint4(w[0], w[1], w[2], w[3]);
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float h = bf16r(gelu(__uint_as_float(v[j]) + bias[col0 + j]));
-                        const float *w4 = sF + PF_W4 + (col0 + j) * 12;
+                    for (int j = 0; j < 32; j += 2) {
+                        const float2 g = gelu2(__fadd2_rn(
+                            make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])),
+                            make_float2(bias[col0 + j], bias[col0 + j + 1])));
+                        const float hs[2] = {bf16r(g.x), bf16r(g.y)};
 #pragma unroll
-                        for (int o = 0; o < 12; ++o) acc[o] = fmaf(h, w4[o], acc[o]);
+                        for (int s = 0; s < 2; ++s) {
+                            // W4 row col0 + j + s: 12 floats, 16-byte aligned (PF_W4 % 4 == 0)
+                            const float4 *w4 =
+                                reinterpret_cast<const float4 *>(sF + PF_W4 + (col0 + j + s) * 12);
+                            const float2 h2 = make_float2(hs[s], hs[s]);
+#pragma unroll
+                            for (int c4 = 0; c4 < 3; ++c4) {
+                                const float4 w = w4[c4];
+                                acc2[2 * c4] = __ffma2_rn(h2, make_float2(w.x, w.y), acc2[2 * c4]);
+                                acc2[2 * c4 + 1] =
+                                    __ffma2_rn(h2, make_float2(w.z, w.w), acc2[2 * c4 + 1]);
+                            }
+                        }
                     }
                 }
             }
@@ -237,7 +254,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         // tile, free once the last MMA has completed)
         if (ch > 0) {
 #pragma unroll
-            for (int o = 0; o < 12; ++o) sP[((ch - 1) * kTile + erow) * 12 + o] = acc[o];
+            for (int o = 0; o < 12; ++o)
+                sP[((ch - 1) * kTile + erow) * 12 + o] = (o & 1) ? acc2[o >> 1].y : acc2[o >> 1].x;
         }
         __syncthreads();
         if (ch == 0) {
@@ -245,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (gr < n) {
 #pragma unroll
                 for (int o = 0; o < 12; ++o) {
-                    float v = acc[o];
+                    float v = (o & 1) ? acc2[o >> 1].y : acc2[o >> 1].x;
                     for (int g = 1; g < kGroups; ++g) v += sP[((g - 1) * kTile + erow) * 12 + o];
                     out[gr * 12 + o] = v + sF[PF_B4 + o];
                 }

@@ -478,12 +478,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     const float4 bh = *reinterpret_cast<const float4 *>(bias + k0 + 4);
                     const float bv[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {  // gelu(z) and gelu'(z) from one Phi, one phi
-                        const float z = __uint_as_float(v[e * 8 + u]) + bv[u];
-                        const PhiE pe = phi_e(z);
-                        hh[u] = z * pe.phi;
-                        dd[u] = fmaf(z, pe.d, pe.phi);
-                        v[e * 8 + u] = __float_as_uint(dd[u]);
+                    for (int u = 0; u < 8; u += 2) {  // gelu(z), gelu'(z) from one Phi, one phi
+                        const float2 z = __fadd2_rn(make_float2(__uint_as_float(v[e * 8 + u]),
+                                                                __uint_as_float(v[e * 8 + u + 1])),
+                                                    make_float2(bv[u], bv[u + 1]));
+                        float2 phi, d;
+                        phi_e2(z, phi, d);
+                        const float2 g = __fmul2_rn(z, phi), gp = __ffma2_rn(z, d, phi);
+                        hh[u] = g.x;
+                        hh[u + 1] = g.y;
+                        dd[u] = gp.x;
+                        dd[u + 1] = gp.y;
+                        v[e * 8 + u] = __float_as_uint(gp.x);
+                        v[e * 8 + u + 1] = __float_as_uint(gp.y);
                     }
                     const uint4 pk = pack8(hh);
                     *reinterpret_cast<uint4 *>(Hl + a_off(erow, k0)) = pk;

@@ -104,7 +104,35 @@ __device__ __forceinline__ PhiE phi_e(float z)
     r.d = d;
     return r;
 }
+// phi_e of two values with the same operations, the FMA-pipe ones as packed FP32 pairs (one
+// instruction for both lanes, each rounded as the scalar operation): the same results
+__device__ __forceinline__ void phi_e2(float2 z, float2 &phi, float2 &d)
+{
+    float2 t;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t.x) : "f"(fmaf(0.2316419f, fabsf(z.x), 1.0f)));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t.y) : "f"(fmaf(0.2316419f, fabsf(z.y), 1.0f)));
+    float2 p = __ffma2_rn(t, make_float2(1.330274429f, 1.330274429f),
+                          make_float2(-1.821255978f, -1.821255978f));
+    p = __ffma2_rn(t, p, make_float2(1.781477937f, 1.781477937f));
+    p = __ffma2_rn(t, p, make_float2(-0.356563782f, -0.356563782f));
+    p = __ffma2_rn(t, p, make_float2(0.319381530f, 0.319381530f));
+    p = __fmul2_rn(p, t);
+    const float2 a = __ffma2_rn(__fmul2_rn(z, z), make_float2(-0.72134752044448170f, -0.72134752044448170f),
+                                make_float2(-1.3257480647361594f, -1.3257480647361594f));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(d.x) : "f"(a.x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(d.y) : "f"(a.y));
+    const float2 q = __fmul2_rn(p, d);  // 1 - Phi(|z|)
+    const float2 r = __ffma2_rn(q, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
+    phi.x = z.x >= 0.0f ? r.x : q.x;
+    phi.y = z.y >= 0.0f ? r.y : q.y;
+}
 __device__ __forceinline__ float gelu(float z) { return z * phi_e(z).phi; }
+__device__ __forceinline__ float2 gelu2(float2 z)
+{
+    float2 phi, d;
+    phi_e2(z, phi, d);
+    return __fmul2_rn(z, phi);
+}
 __device__ __forceinline__ float gelu_prime(float z)
 {
     const PhiE r = phi_e(z);
