@@ -548,6 +548,97 @@ int stop_axis_of(const rp_trace_params *p, int *axis, float *dir, double *offset
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// A receiver set binned into a uniform grid of cells (Receivers in trace_core.cuh), with the
+// receivers and the h_max it was built for.
+struct RxGrid {
+    bool valid = false;
+    double h_max = 0.0;
+    std::vector<double> c, rad;
+    std::vector<SphereC> spheres;
+    std::vector<int2> cells;  // per cell: [first, last) in items
+    std::vector<int> items;   // receiver indices, ascending within a cell
+    float org[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, inv = 1.0f;
+    int dims[3] = {1, 1, 1};
+};
+
+// Bins receivers (centres c, 3 per receiver; radii rad) for steps of at most h_max: each
+// sphere is listed in every cell that its centre box, inflated by R + h_max / 2 and a rounding
+// pad, overlaps; cells are at least twice the inflation wide, so a sphere meets at most two
+// cells per axis.  A counting sort over the cells keeps each cell's receivers in ascending
+// order.
+static int bin_receivers(const std::vector<double> &c, const std::vector<double> &rad,
+                         double h_max, RxGrid &g)
+{
+    const int n_rx = (int)rad.size();
+    g.spheres.assign(n_rx, SphereC{});
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, r_max = 0.0;
+    for (int j = 0; j < n_rx; ++j) {
+        if (!(rad[j] > 0.0)) {
+            set_error("rp_trace: receiver radius must be > 0");
+            return RP_ERR_INVALID_ARG;
+        }
+        for (int a = 0; a < 3; ++a) {
+            g.spheres[j].c[a] = plane_const(c[3 * j + a]);
+            lo[a] = std::min(lo[a], c[3 * j + a]);
+            hi[a] = std::max(hi[a], c[3 * j + a]);
+        }
+        g.spheres[j].R = rad[j];
+        g.spheres[j].Rf = (float)rad[j];
+        g.spheres[j].idx = j;
+        r_max = std::max(r_max, rad[j]);
+    }
+    // inflation: radius + half the longest chord + a pad far above FP32 rounding
+    double amax = 0.0;
+    for (int a = 0; a < 3; ++a) amax = std::max(amax, std::max(std::fabs(lo[a]), std::fabs(hi[a])));
+    const double infl = r_max + 0.5 * h_max + 1e-2 + 1e-6 * amax;
+    double ext = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        lo[a] -= infl;
+        hi[a] += infl;
+        ext = std::max(ext, hi[a] - lo[a]);
+    }
+    const double cell = std::max(2.0 * infl, ext / 64.0);
+    for (int a = 0; a < 3; ++a) {
+        g.dims[a] = std::max(1, std::min(64, (int)std::ceil((hi[a] - lo[a]) / cell)));
+        g.org[a] = (float)lo[a];
+        g.hi[a] = (float)(lo[a] + cell * g.dims[a]);
+    }
+    g.inv = (float)(1.0 / cell);
+    const size_t n_cells = (size_t)g.dims[0] * g.dims[1] * g.dims[2];
+    // the cells a receiver's box spans, in (z, y, x) order
+    auto span = [&](int j, int (&i0)[3], int (&i1)[3]) {
+        for (int a = 0; a < 3; ++a) {
+            i0[a] = std::max(0, (int)std::floor((c[3 * j + a] - infl - lo[a]) / cell));
+            i1[a] = std::min(g.dims[a] - 1, (int)std::floor((c[3 * j + a] + infl - lo[a]) / cell));
+        }
+    };
+    auto cell_of = [&](int x, int y, int z) { return ((size_t)z * g.dims[1] + y) * g.dims[0] + x; };
+    std::vector<int> start(n_cells + 1, 0);
+    for (int j = 0; j < n_rx; ++j) {
+        int i0[3], i1[3];
+        span(j, i0, i1);
+        for (int z = i0[2]; z <= i1[2]; ++z)
+            for (int y = i0[1]; y <= i1[1]; ++y)
+                for (int x = i0[0]; x <= i1[0]; ++x) ++start[cell_of(x, y, z) + 1];
+    }
+    for (size_t q = 0; q < n_cells; ++q) start[q + 1] += start[q];
+    g.cells.resize(n_cells);
+    for (size_t q = 0; q < n_cells; ++q) g.cells[q] = make_int2(start[q], start[q + 1]);
+    g.items.assign((size_t)start[n_cells], 0);
+    for (int j = 0; j < n_rx; ++j) {  // ascending j: each cell's list in receiver order
+        int i0[3], i1[3];
+        span(j, i0, i1);
+        for (int z = i0[2]; z <= i1[2]; ++z)
+            for (int y = i0[1]; y <= i1[1]; ++y)
+                for (int x = i0[0]; x <= i1[0]; ++x) g.items[start[cell_of(x, y, z)]++] = j;
+    }
+    g.c = c;
+    g.rad = rad;
+    g.h_max = h_max;
+    g.valid = true;
+    return RP_OK;
+}
+
 int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp_trace_params *p,
               rp_ray_out *out, rp_hits *hits, rp_stats *stats, cudaStream_t st,
               const FixedScratch *fs)
@@ -588,12 +679,10 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     }
 
     // receivers: bin into a uniform cell grid on the host (each sphere listed in every cell
-    // its centre box, inflated by R + h_max / 2, overlaps), upload with the workspace
-    std::vector<SphereC> spheres(n_rx);
-    std::vector<int2> cells;
-    std::vector<int> items;
-    float g_org[3] = {0, 0, 0}, g_hi[3] = {0, 0, 0}, g_inv = 1.0f;
-    int g_dims[3] = {1, 1, 1};
+    // its centre box, inflated by R + h_max / 2, overlaps), upload with the workspace; the
+    // calling thread keeps the last receiver set and its grid, so that a call with the same
+    // receivers and h_max skips the binning
+    static thread_local RxGrid rxg;
     if (n_rx) {
         std::vector<double> c(3 * (size_t)n_rx), rad(n_rx);
         RP_CUDA_TRY(cudaMemcpyAsync(c.data(), rx->center, c.size() * sizeof(double),
@@ -601,59 +690,17 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
         RP_CUDA_TRY(cudaMemcpyAsync(rad.data(), rx->radius, rad.size() * sizeof(double),
                                     cudaMemcpyDeviceToHost, st));
         RP_CUDA_TRY(cudaStreamSynchronize(st));
-        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, r_max = 0.0;
-        for (int j = 0; j < n_rx; ++j) {
-            if (!(rad[j] > 0.0)) {
-                set_error("rp_trace: receiver radius must be > 0");
-                return RP_ERR_INVALID_ARG;
-            }
-            for (int a = 0; a < 3; ++a) {
-                spheres[j].c[a] = plane_const(c[3 * j + a]);
-                lo[a] = std::min(lo[a], c[3 * j + a]);
-                hi[a] = std::max(hi[a], c[3 * j + a]);
-            }
-            spheres[j].R = rad[j];
-            spheres[j].Rf = (float)rad[j];
-            spheres[j].idx = j;
-            r_max = std::max(r_max, rad[j]);
-        }
-        // inflation: radius + half the longest chord + a pad far above FP32 rounding
-        double amax = 0.0;
-        for (int a = 0; a < 3; ++a) amax = std::max(amax, std::max(std::fabs(lo[a]), std::fabs(hi[a])));
-        const double infl = r_max + 0.5 * p->h_max + 1e-2 + 1e-6 * amax;
-        double ext = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            lo[a] -= infl;
-            hi[a] += infl;
-            ext = std::max(ext, hi[a] - lo[a]);
-        }
-        const double cell = std::max(2.0 * infl, ext / 64.0);
-        for (int a = 0; a < 3; ++a) {
-            g_dims[a] = std::max(1, std::min(64, (int)std::ceil((hi[a] - lo[a]) / cell)));
-            g_org[a] = (float)lo[a];
-            g_hi[a] = (float)(lo[a] + cell * g_dims[a]);
-        }
-        g_inv = (float)(1.0 / cell);
-        const size_t n_cells = (size_t)g_dims[0] * g_dims[1] * g_dims[2];
-        std::vector<std::vector<int>> lists(n_cells);
-        for (int j = 0; j < n_rx; ++j) {
-            int i0[3], i1[3];
-            for (int a = 0; a < 3; ++a) {
-                i0[a] = std::max(0, (int)std::floor((c[3 * j + a] - infl - lo[a]) / cell));
-                i1[a] = std::min(g_dims[a] - 1, (int)std::floor((c[3 * j + a] + infl - lo[a]) / cell));
-            }
-            for (int z = i0[2]; z <= i1[2]; ++z)
-                for (int y = i0[1]; y <= i1[1]; ++y)
-                    for (int x = i0[0]; x <= i1[0]; ++x)
-                        lists[((size_t)z * g_dims[1] + y) * g_dims[0] + x].push_back(j);
-        }
-        cells.resize(n_cells);
-        for (size_t q = 0; q < n_cells; ++q) {
-            cells[q].x = (int)items.size();
-            items.insert(items.end(), lists[q].begin(), lists[q].end());
-            cells[q].y = (int)items.size();
+        if (!(rxg.valid && rxg.h_max == p->h_max && rxg.c == c && rxg.rad == rad)) {
+            rxg.valid = false;
+            if ((rc = bin_receivers(c, rad, p->h_max, rxg))) return rc;
         }
     }
+    const std::vector<SphereC> &spheres = rxg.spheres;
+    const std::vector<int2> &cells = rxg.cells;
+    const std::vector<int> &items = rxg.items;
+    const float *g_org = rxg.org, *g_hi = rxg.hi;
+    const float g_inv = n_rx ? rxg.inv : 1.0f;
+    const int g_dims[3] = {n_rx ? rxg.dims[0] : 1, n_rx ? rxg.dims[1] : 1, n_rx ? rxg.dims[2] : 1};
 
     const int block = p->block > 0 ? p->block : kBlockDefault;
     const int variant = medium_variant(m);
@@ -667,8 +714,9 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     const size_t off_ctrl = 0;
     const size_t off_s = align_up(sizeof(Ctrl));
     const size_t off_z = off_s + align_up(sizeof(SphereC) * (size_t)std::max(n_rx, 1));
-    const size_t off_b = off_z + align_up(sizeof(int2) * std::max<size_t>(cells.size(), 1));
-    const size_t off_k = off_b + align_up(sizeof(int) * std::max<size_t>(items.size(), 1));
+    const size_t n_cells = n_rx ? cells.size() : 0, n_items = n_rx ? items.size() : 0;
+    const size_t off_b = off_z + align_up(sizeof(int2) * std::max<size_t>(n_cells, 1));
+    const size_t off_k = off_b + align_up(sizeof(int) * std::max<size_t>(n_items, 1));
     const size_t clk_bytes = align_up(sizeof(unsigned long long) * 2 * (size_t)(threads / 32));
     if (fs) {
         // fixed scratch: at most half of it for the stacks, the rest (after the fixed parts)
@@ -866,10 +914,11 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
             std::vector<double> ends(nw);
             for (size_t w = 0; w < nw; ++w) t0 = std::min(t0, wclk[2 * w]);
             for (size_t w = 0; w < nw; ++w) ends[w] = (double)(wclk[2 * w + 1] - t0) * 1e-6;
-            std::sort(ends.begin(), ends.end());
-            stats->warp_end_ms[0] = ends.front();
+            const auto mm = std::minmax_element(ends.begin(), ends.end());
+            stats->warp_end_ms[0] = *mm.first;
+            stats->warp_end_ms[2] = *mm.second;
+            std::nth_element(ends.begin(), ends.begin() + nw / 2, ends.end());
             stats->warp_end_ms[1] = ends[nw / 2];
-            stats->warp_end_ms[2] = ends.back();
         }
     }
     if (flags & (FLAG_OUT_OVERFLOW | FLAG_QUEUE_OVERFLOW | FLAG_HIT_OVERFLOW)) {
