@@ -158,8 +158,9 @@ typedef struct {
     const double *pos, *dir, *amp;
 } rp_rays;
 
-/* Receiver spheres: center (n, 3) row-major, radius (n).  Device pointers; n = 0 or a NULL
- * rp_receivers pointer means none.  A hit is recorded when a committed step chord enters a
+/* Receiver spheres: center (n, 3) row-major, radius (n).  Host or device pointers (when both
+ * are host arrays they are read during the call; otherwise they are read back with a
+ * synchronisation of the stream); n = 0 or a NULL rp_receivers pointer means none.  A hit is recorded when a committed step chord enters a
  * sphere (chord starts outside, entry point on the chord); receivers do not absorb. */
 typedef struct {
     int32_t n, pad;

@@ -214,8 +214,12 @@ class PreparedRays:
                            0 if self.amp is None else self.amp.data_ptr())
         self.rx = None
         if receivers is not None and len(receivers[1]) > 0:
-            self.rx_c = _dev_f64(receivers[0], (-1, 3))
-            self.rx_r = _dev_f64(receivers[1])
+            if all(isinstance(a, torch.Tensor) and a.is_cuda for a in receivers[:2]):
+                self.rx_c = _dev_f64(receivers[0], (-1, 3))
+                self.rx_r = _dev_f64(receivers[1])
+            else:  # host arrays: the library reads them during each call, no read-back
+                self.rx_c = torch.as_tensor(receivers[0], dtype=torch.float64).reshape(-1, 3).contiguous()
+                self.rx_r = torch.as_tensor(receivers[1], dtype=torch.float64).contiguous()
             self.rx = A.Receivers(len(self.rx_r), 0, self.rx_c.data_ptr(), self.rx_r.data_ptr())
 
 

@@ -685,11 +685,25 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     static thread_local RxGrid rxg;
     if (n_rx) {
         std::vector<double> c(3 * (size_t)n_rx), rad(n_rx);
-        RP_CUDA_TRY(cudaMemcpyAsync(c.data(), rx->center, c.size() * sizeof(double),
-                                    cudaMemcpyDeviceToHost, st));
-        RP_CUDA_TRY(cudaMemcpyAsync(rad.data(), rx->radius, rad.size() * sizeof(double),
-                                    cudaMemcpyDeviceToHost, st));
-        RP_CUDA_TRY(cudaStreamSynchronize(st));
+        // host arrays are read directly; device arrays are read back (a stream synchronisation)
+        auto on_host = [](const void *q) {
+            cudaPointerAttributes attr;
+            memset(&attr, 0, sizeof attr);
+            const bool dev = cudaPointerGetAttributes(&attr, q) == cudaSuccess &&
+                             (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+            cudaGetLastError();
+            return !dev;
+        };
+        if (on_host(rx->center) && on_host(rx->radius)) {
+            std::memcpy(c.data(), rx->center, c.size() * sizeof(double));
+            std::memcpy(rad.data(), rx->radius, rad.size() * sizeof(double));
+        } else {
+            RP_CUDA_TRY(cudaMemcpyAsync(c.data(), rx->center, c.size() * sizeof(double),
+                                        cudaMemcpyDefault, st));
+            RP_CUDA_TRY(cudaMemcpyAsync(rad.data(), rx->radius, rad.size() * sizeof(double),
+                                        cudaMemcpyDefault, st));
+            RP_CUDA_TRY(cudaStreamSynchronize(st));
+        }
         if (!(rxg.valid && rxg.h_max == p->h_max && rxg.c == c && rxg.rad == rad)) {
             rxg.valid = false;
             if ((rc = bin_receivers(c, rad, p->h_max, rxg))) return rc;

@@ -255,3 +255,47 @@ def test_scheduling_knobs_do_not_change_records(rp, precision):
             np.testing.assert_array_equal(g[k][gi], base[k][bi], err_msg=k)
         n = cfg["rays"][0].shape[1]  # primary i at index i
         np.testing.assert_array_equal(g["pos"][:n], base["pos"][:n])
+
+
+def test_receivers_from_host_or_device_and_the_cached_grid(rp):
+    """Receivers given as host arrays (read during the call) or as device arrays (read back)
+    bin into the same grid and give bit-identical hits; a repeated call reuses the grid, and
+    changed radii rebuild it (more hits for larger spheres)."""
+    import torch
+
+    cfg = W.batched(n=20_000)
+    med = rp.Medium(cfg["medium"])
+    c, r = cfg["receivers"]
+
+    def hits_of(rx):
+        res = rp.trace(med, *cfg["rays"], params=cfg["params"], receivers=rx, precision="fp32")
+        g = gpu_rays(res)
+        from parity import tree_keys
+
+        keys = tree_keys(g["parent"], g["seq"])
+        h = res["hits"]
+        return g, sorted((keys[int(i)], int(j), float(t), float(s)) for i, j, t, s in zip(
+            h["ray"].cpu().numpy(), h["receiver"].cpu().numpy(), h["time"].cpu().numpy(),
+            h["path"].cpu().numpy()))
+
+    big = (c, r * 25.0)
+    g_host, h_host = hits_of(big)
+    g_again, h_again = hits_of(big)  # the same set: the grid of the previous call
+    g_dev, h_dev = hits_of((torch.as_tensor(c, device="cuda"), torch.as_tensor(r * 25.0, device="cuda")))
+    assert len(h_host) > 20
+    assert h_host == h_again == h_dev
+    for g in (g_again, g_dev):
+        gi, bi, only_g, only_b = match(g, g_host)
+        assert not only_g and not only_b
+        np.testing.assert_array_equal(g["pos"][gi], g_host["pos"][bi])
+    # changed radii: a new grid, whose hits lie on the new spheres (entry points on the
+    # sphere of the receiver hit; a stale grid would carry the old radii)
+    for scale in (5.0, 25.0):
+        res = rp.trace(med, *cfg["rays"], params=cfg["params"], receivers=(c, r * scale),
+                       precision="fp32")
+        h = res["hits"]
+        j = h["receiver"].cpu().numpy()
+        dist = np.linalg.norm(h["pos"].cpu().numpy().T - np.asarray(c)[j], axis=1)
+        np.testing.assert_allclose(dist, (np.asarray(r) * scale)[j], rtol=0, atol=1e-3)
+        if scale == 5.0:
+            assert len(j) < len(h_host)
