@@ -12,14 +12,26 @@ BASE_KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_ste
              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "e2e"}
 
 _FAKE_GPU_ARM = r'''
-import argparse, os, sys, types
+import argparse, contextlib, os, sys, types
 import numpy as np
 import torch
 import torch.distributed as dist
 
 torch.cuda.set_device = lambda *a, **k: None
 torch.cuda.synchronize = lambda *a, **k: None
-torch.cuda.current_stream = lambda *a, **k: None
+
+
+class Stream:
+    def __init__(self, *a, **k):
+        pass
+
+    def wait_event(self, event):
+        pass
+
+
+torch.cuda.Stream = Stream
+torch.cuda.current_stream = lambda *a, **k: Stream()
+torch.cuda.stream = lambda s: contextlib.nullcontext()
 
 
 class Event:
