@@ -1511,10 +1511,12 @@ __device__ __forceinline__ void split_at_surface(const MediumSurfaces &med, Lane
     L.A *= rr;
 }
 
-// The landing point r + dr put radially onto sphere S (the FP64 reference's operations).
+// The landing point r + dr put radially onto sphere S (the FP64 reference's operations); *g,
+// if given, receives the point's signed distance from the surface before it was moved.
 template <class P>
 __device__ __forceinline__ void sphere_snap(const SphereB &S, const typename P::V &r,
-                                            const typename P::R dr[3], double out[3])
+                                            const typename P::R dr[3], double out[3],
+                                            double *g = nullptr)
 {
     double w[3], d2 = 0.0;
 #pragma unroll
@@ -1522,7 +1524,9 @@ __device__ __forceinline__ void sphere_snap(const SphereB &S, const typename P::
         w[a] = __dsub_rn(__dadd_rn(P::get(r, a), (double)dr[a]), S.c[a]);
         d2 = __dadd_rn(d2, __dmul_rn(w[a], w[a]));
     }
-    const double q = S.R / sqrt(d2);
+    const double d = sqrt(d2);
+    if (g) *g = d - S.R;
+    const double q = S.R / d;
 #pragma unroll
     for (int a = 0; a < 3; ++a) out[a] = __dadd_rn(S.c[a], __dmul_rn(q, w[a]));
 }
@@ -1537,6 +1541,36 @@ __device__ __forceinline__ void split_at_sphere(const MediumSpheres &med, Lane<P
 {
     const SphereB &S = med.S[j];
     const bool inside = L.layer == RP_MAX_LAYERS + j;
+    if constexpr (P::kFF) {
+        // FP32-mixed landing, completed as at a plane (land_correction): the end point sat
+        // L.ga outside (> 0) or inside the sphere before it was put on it radially; the ray is
+        // taken back along itself by u = g / (d/ds of |r - c|) = g / (t . m), m the outward
+        // normal, to first order (the point stays on the sphere within u^2 / 2R); direction,
+        // arc length and travel time follow as at a plane (t' = k (e_z - t_z t),
+        // k = (dn/dz) / n on the ray's side).  Small corrections: FP32 on the float-float state.
+        const float invR = __fdividef(1.0f, S.Rf);
+        float m[3], t0[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            m[a] = ((L.r.hi[a] - S.cc[a].hi) + (L.r.lo[a] - S.cc[a].lo)) * invR;
+            t0[a] = L.t.hi[a] + L.t.lo[a];
+        }
+        const float D = t0[0] * m[0] + t0[1] * m[1] + t0[2] * m[2];
+        const float u = __fdividef(L.ga, D);  // a correction term: 2 ulp suffice
+        if (fabsf(u) <= 0.1f) {
+            float n, gr[3];
+            const float z3[3] = {0.0f, 0.0f, L.r.hi[2] + L.r.lo[2]};
+            medium_eval<P>(med, L.lc, z3, n, gr);
+            const float k = __fdividef(gr[2], n);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) P::add(L.r, a, L.ga * m[a] - u * t0[a]);
+            P::add(L.t, 0, u * k * t0[2] * t0[0]);
+            P::add(L.t, 1, u * k * t0[2] * t0[1]);
+            P::add(L.t, 2, -u * k * (1.0f - t0[2] * t0[2]));
+            P::sadd(L.s, -u);
+            P::sadd(L.T, -u * n * (float)kInvC0);
+        }
+    }
     double r[3], w[3], d2 = 0.0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -1613,7 +1647,9 @@ __device__ __forceinline__ bool commit(const M &med, Lane<P> &L, const StepParam
     double sn[3] = {0.0, 0.0, 0.0};  // a sphere landing: the point put on the surface
     if constexpr (has_spheres_v<M>) {
         if (ev >= EV_SPH) {
-            sphere_snap<P>(med.S[ev - EV_SPH], L.r, dr, sn);
+            double g;
+            sphere_snap<P>(med.S[ev - EV_SPH], L.r, dr, sn, &g);
+            if constexpr (P::kFF) L.ga = (R)g;  // landing residual, for the split's correction
 #pragma unroll
             for (int a = 0; a < 3; ++a) dr[a] = (R)(sn[a] - P::get(L.r, a));
         }

@@ -144,6 +144,24 @@ def sensitive_keys(o: dict, o_tilted: dict, pos_tol=1e-3, time_tol=1e-11) -> set
     return {ko[i] for i in oi[moved]} | set(only_o)
 
 
+def step_capped_keys(g: dict, o: dict) -> set:
+    """Split-tree keys of the rays that ran into the attempted-step cap (status 7) in either
+    run.  Rejected steps and the root-finding iterations of boundary landings count against
+    the cap, and their number differs between two precisions, so where the cap falls on a ray
+    that needs about that many attempts is arbitrary: such a ray is excused like an
+    ill-conditioned one.  The excuse is checked: where only one run was capped, the other got
+    at least as far along the same ray (at least as many accepted steps and reflections)."""
+    gi, oi, _, _ = match(g, o)
+    ko = tree_keys(o["parent"], o["seq"])
+    cg, co = g["status"][gi] == 7, o["status"][oi] == 7
+    ahead_g = (g["n_acc"][gi] >= o["n_acc"][oi]) & (g["n_refl"][gi] >= o["n_refl"][oi])
+    ahead_o = (o["n_acc"][oi] >= g["n_acc"][gi]) & (o["n_refl"][oi] >= g["n_refl"][gi])
+    bad = (cg & ~co & ~ahead_o) | (co & ~cg & ~ahead_g)
+    assert not bad.any(), [(ko[i], int(g["n_acc"][j]), int(o["n_acc"][i]))
+                           for j, i in zip(gi[bad], oi[bad])][:5]
+    return {ko[i] for i in oi[cg | co]}
+
+
 def excused(key, sens: set) -> bool:
     """True if the ray `key` or one of its ancestors is ill-conditioned (in `sens`)."""
     return any(key[:m] in sens for m in range(1, len(key) + 1))

@@ -8,7 +8,8 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import check_fp64, errors, gpu_rays, match, oracle_rays, tilt
+from parity import (check_fp64, check_within, errors, gpu_rays, match,
+                    oracle_rays, sensitive_keys, step_capped_keys, tilt)
 from paper_1810_01780_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -48,31 +49,38 @@ def test_spheres_fp64_matches_oracle(rp):
 
 
 def test_spheres_fp32_mixed_vs_fp64(rp):
+    """FP32-mixed against FP64, ray by ray: every ray that is not excused as ill-conditioned
+    (its FP64 result, or an ancestor's, moves by more than 1 mm / 0.01 ns, changes status or
+    disappears when every launch direction is tilted by 1e-7 rad, in either of two independent
+    tilt directions) exists in both runs with the
+    same status and generation, within 1 mm and 0.01 ns.  At most 5 % of the rays are
+    ill-conditioned or excused with their secondaries.  Rays that reach the workload's cap of
+    1,000 attempted steps in either run are excused too: rays trapped in the lens by total
+    internal reflection spend the budget on the root iterations of about a hundred landings,
+    whose number differs between the precisions; where only one run was capped the other must
+    have got at least as far along the ray.  At most 0.2 % of the rays."""
     cfg = W.spheres(65536)
     pos, d, a = cfg["rays"]
     g64 = _run(rp, cfg["medium"], cfg["params"], (pos, d, a), "fp64")
     g32 = _run(rp, cfg["medium"], cfg["params"], (pos, d, a), "fp32")
-    gpt = _run(rp, cfg["medium"], cfg["params"], (pos, tilt(d, 1e-7, 5), a), "fp64")
-    gi, oi, only32, only64 = match(g32, g64)
-    n = max(len(g32["path"]), len(g64["path"]))
-    assert len(only32) + len(only64) <= 0.005 * n
-    ok = g32["status"][gi] == g64["status"][oi]
-    assert ok.mean() > 0.995
-    gi, oi = gi[ok], oi[ok]
+    # behind reflections off a convex sphere the sensitivity depends on the tilt's direction:
+    # a ray is ill-conditioned if either of two independent 1e-7 rad tilts moves it
+    sens = set()
+    for seed in (5, 11):
+        gpt = _run(rp, cfg["medium"], cfg["params"], (pos, tilt(d, 1e-7, seed), a), "fp64")
+        sens |= sensitive_keys(g64, gpt)
+    capped = step_capped_keys(g32, g64)
+    n_checked, n_excused = check_within(g32, g64, sens | capped)
+    n = len(g64["path"])
+    assert len(capped) <= 0.002 * n
+    gi, oi, _, _ = match(g32, g64)
     dp, dd, ds, dT, dA = errors(g32, g64, gi, oi)
-    pi, qi, _, _ = match(gpt, g64)
-    sens = np.ones(len(g64["path"]), dtype=bool)
-    sp, _, _, sT, _ = errors(gpt, g64, pi, qi)
-    sens[qi] = ~(gpt["status"][pi] == g64["status"][qi]) | (sp > 1e-3) | (sT > 1e-11)
-    s_ok = ~sens[oi]
-    good = (dp <= 1e-3) & (dT <= 1e-11)
-    print("spheres fp32 vs fp64: %d rays, p99 |dr| %.2e m, p99 |dT| %.2e s, well-conditioned "
-          "within 1 mm / 0.01 ns %.5f (%.4f sensitive)" % (
-              len(gi), np.quantile(dp, 0.99), np.quantile(dT, 0.99), good[s_ok].mean(),
-              1 - s_ok.mean()))
-    assert np.quantile(dp, 0.99) <= 1e-3
-    assert good[s_ok].mean() >= 0.999
-    assert (1 - s_ok.mean()) <= 0.05
+    print("spheres fp32 vs fp64: %d rays checked, %d ill-conditioned (%.4f), %d excused with their "
+          "secondaries (%.4f); p50/p99 |dr| %.2e/%.2e m" % (
+              n_checked, len(sens), len(sens) / n, n_excused, n_excused / n, np.median(dp),
+              np.quantile(dp, 0.99)))
+    assert len(sens) <= 0.05 * n and n_excused <= 0.05 * n
+    assert n_checked >= 0.9 * n
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

@@ -124,12 +124,13 @@ def test_grid_medium_fp64_and_fp32(rp):
     g = gpu_rays(_run(rp, med, prm, rays, precision="fp64"))
     check_fp64(g, oracle_rays(ref), prm["tol"], min_tier1=0.9)
     assert np.any(g["status"] == 4)  # some rays leave the box
+    # FP32-mixed against FP64 ray by ray, rays ill-conditioned under a 1e-7 rad tilt excused
     g32 = gpu_rays(_run(rp, med, prm, rays, precision="fp32"))
-    gi, oi, a, b = match(g32, g)
-    ok = g32["status"][gi] == g["status"][oi]
-    assert ok.mean() > 0.99
-    dp, dd, ds, dT, dA = errors(g32, g, gi[ok], oi[ok])
-    assert np.quantile(dp, 0.99) <= 1e-3
+    pos, d, a = rays
+    gpt = gpu_rays(_run(rp, med, prm, (pos, tilt(d, 1e-7, 9), a), precision="fp64"))
+    sens = sensitive_keys(g, gpt)
+    n_checked, n_excused = check_within(g32, g, sens)
+    assert n_excused <= 0.05 * len(g["path"]) and n_checked >= 0.9 * len(g["path"])
 
 
 def test_paraxial_form_fp64(rp):

@@ -152,3 +152,23 @@ def test_sensitive_keys_flags_rays_that_move_under_a_tilt(rays):
     h["pos"][4] += 5e-3
     h["status"][9] = 9
     assert sensitive_keys(o, h) == {keys[4], keys[9]}
+
+
+def test_step_capped_keys_checks_the_excuse(rays):
+    """A ray capped (status 7) in one run only is excused when the other run got at least as
+    far along it (accepted steps and reflections); one that stopped short fails; rays capped in
+    both runs are excused as they are."""
+    from parity import step_capped_keys
+
+    o, _, _ = rays
+    ko = tree_keys(o["parent"], o["seq"])
+    g = {k: v.copy() for k, v in o.items()}
+    assert step_capped_keys(g, o) == set()
+    o2 = {k: v.copy() for k, v in o.items()}
+    o2["status"][0] = 7  # capped in the reference only, the other run equally far: excused
+    o2["status"][1] = 7
+    g["status"][1] = 7  # capped in both
+    assert step_capped_keys(g, o2) == {ko[0], ko[1]}
+    g["n_acc"][0] = o2["n_acc"][0] - 1  # the uncapped run stopped short of the capped one
+    with pytest.raises(AssertionError):
+        step_capped_keys(g, o2)
