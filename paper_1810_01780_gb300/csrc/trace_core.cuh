@@ -1892,8 +1892,17 @@ __device__ __forceinline__ bool advance(const M &med, Lane<P> &L, const StepPara
         for (int kind = EV_TOP; kind <= EV_STOP; ++kind) {
             if ((kind == EV_TOP || kind == EV_BOTTOM) && !is_layered(med)) continue;
             if (kind == EV_STOP && !sp.use_stop) continue;
-            R g0 = event_g<P>(med, L, sp, kind, zero3);
-            R g1 = event_g<P>(med, L, sp, kind, dr);
+            R g0, g1;
+            if constexpr (has_surfaces_v<M>) {
+                // a surface's offset costs a height-field lookup: the start's is needed only
+                // when the end could trigger an event (the same events as evaluating both)
+                g1 = event_g<P>(med, L, sp, kind, dr);
+                if (g1 > sp.eps_b) continue;
+                g0 = event_g<P>(med, L, sp, kind, zero3);
+            } else {
+                g0 = event_g<P>(med, L, sp, kind, zero3);
+                g1 = event_g<P>(med, L, sp, kind, dr);
+            }
             if (g1 < R(0) || (g1 <= sp.eps_b && g0 > sp.eps_b)) {
                 R fr = (g0 > R(0)) ? g0 / (g0 - g1) : R(0);
                 if (fr < ev_frac) {
