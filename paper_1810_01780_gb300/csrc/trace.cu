@@ -552,6 +552,7 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 // receivers and the h_max it was built for.
 struct RxGrid {
     bool valid = false;
+    long long version = 0;  // bumped by every rebuild
     double h_max = 0.0;
     std::vector<double> c, rad;
     std::vector<SphereC> spheres;
@@ -559,7 +560,48 @@ struct RxGrid {
     std::vector<int> items;   // receiver indices, ascending within a cell
     float org[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, inv = 1.0f;
     int dims[3] = {1, 1, 1};
+    // device copies (spheres, cells, items), one per device, current while version matches
+    struct DevCopy {
+        char *ptr = nullptr;
+        size_t bytes = 0;
+        long long version = -1;
+    };
+    static constexpr int kDevices = 16;
+    DevCopy dev[kDevices];
 };
+
+// The device copy of grid g on device `d` (uploaded on `st` when the grid was rebuilt since):
+// spheres at *ps, cells at *pz, items at *pb.  No kernel of an earlier call can still read a
+// copy being replaced, as every call drains its stream before it returns.
+static int rx_device_copy(RxGrid &g, int d, cudaStream_t st, const char **ps, const char **pz,
+                          const char **pb)
+{
+    const size_t o_z = align_up(sizeof(SphereC) * g.spheres.size());
+    const size_t o_b = o_z + align_up(sizeof(int2) * g.cells.size());
+    const size_t bytes = o_b + align_up(sizeof(int) * std::max<size_t>(g.items.size(), 1));
+    RxGrid::DevCopy &c = g.dev[d];
+    if (c.version != g.version) {
+        if (c.bytes < bytes) {
+            if (c.ptr) cudaFree(c.ptr);
+            c.ptr = nullptr;
+            c.bytes = 0;
+            RP_CUDA_TRY(cudaMalloc(&c.ptr, bytes));
+            c.bytes = bytes;
+        }
+        RP_CUDA_TRY(cudaMemcpyAsync(c.ptr, g.spheres.data(), sizeof(SphereC) * g.spheres.size(),
+                                    cudaMemcpyHostToDevice, st));
+        RP_CUDA_TRY(cudaMemcpyAsync(c.ptr + o_z, g.cells.data(), sizeof(int2) * g.cells.size(),
+                                    cudaMemcpyHostToDevice, st));
+        if (!g.items.empty())
+            RP_CUDA_TRY(cudaMemcpyAsync(c.ptr + o_b, g.items.data(), sizeof(int) * g.items.size(),
+                                        cudaMemcpyHostToDevice, st));
+        c.version = g.version;
+    }
+    *ps = c.ptr;
+    *pz = c.ptr + o_z;
+    *pb = c.ptr + o_b;
+    return RP_OK;
+}
 
 // Bins receivers (centres c, 3 per receiver; radii rad) for steps of at most h_max: each
 // sphere is listed in every cell that its centre box, inflated by R + h_max / 2 and a rounding
@@ -636,6 +678,7 @@ static int bin_receivers(const std::vector<double> &c, const std::vector<double>
     g.rad = rad;
     g.h_max = h_max;
     g.valid = true;
+    ++g.version;
     return RP_OK;
 }
 
@@ -795,6 +838,9 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     sk.out = *out;
     if (hits) sk.hits = *hits;
     sk.has_rx = n_rx > 0;
+    // the receiver grid: the calling thread's device copy, or (fixed scratch, which allocates
+    // nothing) a copy in the scratch made by every call
+    const bool rx_cached = n_rx && !fs && dev < RxGrid::kDevices;
     sk.rx.s = (const SphereC *)(base + off_s);
     sk.rx.cell = (const int2 *)(base + off_z);
     sk.rx.items = (const int *)(base + off_b);
@@ -810,7 +856,13 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
 
     drain.queued = true;
     RP_CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
-    if (n_rx) {
+    if (rx_cached) {
+        const char *ps, *pz, *pb;
+        if ((rc = rx_device_copy(rxg, dev, st, &ps, &pz, &pb))) return rc;
+        sk.rx.s = (const SphereC *)ps;
+        sk.rx.cell = (const int2 *)pz;
+        sk.rx.items = (const int *)pb;
+    } else if (n_rx) {
         RP_CUDA_TRY(cudaMemcpyAsync(base + off_s, spheres.data(), sizeof(SphereC) * n_rx,
                                     cudaMemcpyHostToDevice, st));
         RP_CUDA_TRY(cudaMemcpyAsync(base + off_z, cells.data(), sizeof(int2) * cells.size(),
