@@ -439,16 +439,25 @@ def reduce_over_ranks(total_ms, counts, device):
     return float(t[0]), [float(v) for v in c]
 
 
-def fp32_fp64_leg(rp, cfg, flush, steps, flops, peaks, workload):
+def fp32_fp64_leg(rp, cfg, flush, steps, flops, peaks, workload, tune=True):
     """One trace workload in both precisions: ray-steps/s and rays/s (kernel time, L2 flushed
     before each call), each precision's ALU roofline (flops[prec] per attempted step against
-    peaks[prec], TFLOP/s) and the FP32-mixed end points of the primaries against FP64."""
+    peaks[prec], TFLOP/s) and the FP32-mixed end points of the primaries against FP64.  The
+    FP32-mixed scheduling knobs (speed only, never a record) are tuned on the workload first."""
+    from paper_1810_01780_gb300 import autotune
+
     med = rp.Medium(cfg["medium"])
     rays = rp.PreparedRays(*cfg["rays"])
     buf = rp.TraceBuffers(3 * rays.n, 0, fields=("end_pos", "path", "time", "status"))
     leg, ends = {"workload": workload}, {}
+    params = {"fp32": dict(cfg["params"]), "fp64": dict(cfg["params"])}
+    if tune:
+        t = autotune.tune_trace(med, rays, cfg["params"], buf, "fp32", idle=(256, 512),
+                                flush=(1, 2), block=(128, 256), reps=1)
+        params["fp32"] = t["params"]
+        leg["tuned_knobs_fp32"] = t["best"]
     for prec in ("fp32", "fp64"):
-        prm = rp.make_params(cfg["params"], prec)
+        prm = rp.make_params(params[prec], prec)
         rp.trace_into(med, rays, prm, buf)  # warm-up
         ts, acc, att, nr = [], 0, 0, 0
         for _ in range(steps):
@@ -758,7 +767,8 @@ def run_gpu(args):
             {"fp32": FLOPS_PER_ATTEMPT_F32, "fp64": FLOPS_PER_ATTEMPT_F64},
             {"fp32": (pk32, basis32), "fp64": (pk64, basis64)},
             "Fig. 1 example: 1,048,576 rays from 240 m in the x-z plane, 10 m of n = 1.5 over "
-            "exponential ice (z0 = 71.4 m), 5 us, A/A0 < 0.05 discarded, generations <= 8")
+            "exponential ice (z0 = 71.4 m), 5 us, A/A0 < 0.05 discarded, generations <= 8",
+            tune=not args.no_tune)
     # curved boundaries: two spherical inclusions in the ice, 1,048,576 isotropic rays
     if not args.no_spheres:
         modes["spheres"] = fp32_fp64_leg(
@@ -767,7 +777,7 @@ def run_gpu(args):
             {"fp32": (pk32, basis32), "fp64": (pk64, basis64)},
             "spherical inclusions: 1,048,576 isotropic rays around a denser-ice lens (R 40 m) "
             "and an air pocket (R 25 m) in the surface-bounded ice, 2 km, A/A0 < 0.05, "
-            "generations <= 3")
+            "generations <= 3", tune=not args.no_tune)
 
     # non-horizontal boundaries: a tilted ice surface carrying a height field of undulations and
     # a tilted internal boundary, 1,048,576 isotropic rays
@@ -778,7 +788,8 @@ def run_gpu(args):
             {"fp32": (pk32, basis32), "fp64": (pk64, basis64)},
             "non-horizontal boundaries: 1,048,576 isotropic rays under a 2-degree tilted ice "
             "surface with a 0.3 m height field of undulations (256 x 256 nodes at 2 m) and a "
-            "1-degree tilted internal boundary at 100 m, 2 km, A/A0 < 0.05, generations <= 3")
+            "1-degree tilted internal boundary at 100 m, 2 km, A/A0 < 0.05, generations <= 3",
+            tune=not args.no_tune)
 
     # source-receiver path finding: 65,536 pairs, 32..512 scan angles each, FP64 bisection
     if not args.no_paths:
