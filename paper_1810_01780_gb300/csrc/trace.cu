@@ -722,9 +722,10 @@ int run_trace(rp_medium_t m, const rp_rays *in, const rp_receivers *rx, const rp
     }
 
     // receivers: bin into a uniform cell grid on the host (each sphere listed in every cell
-    // its centre box, inflated by R + h_max / 2, overlaps), upload with the workspace; the
-    // calling thread keeps the last receiver set and its grid, so that a call with the same
-    // receivers and h_max skips the binning
+    // its centre box, inflated by R + h_max / 2, overlaps); the calling thread keeps the last
+    // receiver set, its grid and the grid's device copy, so that a call with the same
+    // receivers and h_max skips the binning and the upload (a call with a fixed scratch
+    // copies the grid into the scratch instead)
     static thread_local RxGrid rxg;
     if (n_rx) {
         std::vector<double> c(3 * (size_t)n_rx), rad(n_rx);
